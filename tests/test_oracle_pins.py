@@ -1,0 +1,402 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it follows.  None of these retypes the oracle's
+own formula: they use brute-force loops, closed forms, invariants, library
+routines for special cases, or the paper's printed unit-condition tensors.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import cpals_oracle as O
+from paper_1811_10573_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_factors(dims, R, seed):
+    g = np.random.default_rng(seed)
+    return [g.standard_normal((s, R)) for s in dims]
+
+
+def _brute_partial(X, A, keep):
+    """Element-wise Eq. 1 by nested Python loops (tiny tensors only)."""
+    N = X.ndim
+    R = A[0].shape[1]
+    out = np.zeros([X.shape[k] for k in keep] + [R])
+    for idx in itertools.product(*[range(s) for s in X.shape]):
+        for r in range(R):
+            w = X[idx]
+            for k in range(N):
+                if k not in keep:
+                    w *= A[k][idx[k], r]
+            out[tuple(idx[k] for k in keep) + (r,)] += w
+    return out
+
+
+# --- T1: MTTKRP equals its element-wise definition (Sec. 2.3, Eq. 1) -------
+
+@pytest.mark.parametrize("dims,R", [((3, 4, 5), 1), ((3, 4, 5), 3),
+                                    ((2, 3, 2, 3), 2), ((2, 2, 3, 2, 2), 2)])
+def test_mttkrp_brute_force(dims, R):
+    g = np.random.default_rng(1)
+    X = g.standard_normal(dims)
+    A = _rand_factors(dims, R, 2)
+    for n in range(len(dims)):
+        np.testing.assert_allclose(O.mttkrp(X, A, n), _brute_partial(X, A, [n]),
+                                   rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("dims,keep", [((3, 4, 5), [0, 2]), ((2, 3, 2, 3), [1, 3]),
+                                       ((2, 3, 2, 3), [0, 1, 3])])
+def test_partial_mttkrp_brute_force(dims, keep):
+    g = np.random.default_rng(3)
+    X = g.standard_normal(dims)
+    A = _rand_factors(dims, 2, 4)
+    np.testing.assert_allclose(O.partial_mttkrp(X, A, keep), _brute_partial(X, A, keep),
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_khatri_rao_is_columnwise_kron():
+    g = np.random.default_rng(5)
+    A, B, C = g.standard_normal((3, 2)), g.standard_normal((4, 2)), g.standard_normal((2, 2))
+    K = O.khatri_rao([A, B, C])
+    for r in range(2):
+        np.testing.assert_allclose(K[:, r], np.kron(np.kron(A[:, r], B[:, r]), C[:, r]))
+
+
+# --- dimension-tree consistency: contracting an intermediate further gives
+# the lower intermediate (Sec. 2.5); pins the mode bookkeeping of Eq. 1 -------
+
+def test_intermediate_chain():
+    dims = (3, 4, 2, 5)
+    g = np.random.default_rng(6)
+    X = g.standard_normal(dims)
+    A = _rand_factors(dims, 3, 7)
+    M123 = O.partial_mttkrp(X, A, [0, 1, 2])        # contract mode 3
+    M13 = np.einsum("ijkr,jr->ikr", M123, A[1])      # then mode 1
+    np.testing.assert_allclose(M13, O.partial_mttkrp(X, A, [0, 2]), rtol=1e-12)
+    M1 = np.einsum("ikr,kr->ir", M13, A[2])
+    np.testing.assert_allclose(M1, O.mttkrp(X, A, 0), rtol=1e-12)
+
+
+# --- T9: Hurwitz unit-condition tensors (appendix) --------------------------
+
+def _load_hurwitz(s):
+    rows = [list(map(float, l.split())) for l in open(os.path.join(GOLD, f"hurwitz_s{s}.txt"))
+            if l.strip() and not l.startswith("#")]
+    if s in (2, 4):
+        return np.array(rows).reshape(s, s, s)
+    M, Nn = np.array(rows[:8], dtype=int), np.array(rows[8:])
+    T = np.zeros((8, 8, 8))
+    for i in range(8):
+        for j in range(8):
+            T[i, j, M[i, j] - 1] = Nn[i, j]
+    return T
+
+
+@pytest.mark.parametrize("s", [2, 4, 8])
+def test_hurwitz_norm_preserving(s):
+    T = _load_hurwitz(s)
+    g = np.random.default_rng(s)
+    for n in range(3):
+        for _ in range(10):
+            A = [g.standard_normal((s, 1)) for _ in range(3)]
+            z = O.mttkrp(T, A, n)[:, 0]
+            others = [k for k in range(3) if k != n]
+            expect = np.linalg.norm(A[others[0]]) * np.linalg.norm(A[others[1]])
+            assert abs(np.linalg.norm(z) - expect) < 1e-12 * max(1.0, expect)
+    # the property is sharp: flipping one sign breaks it
+    T2 = T.copy()
+    T2[0, 0, 0] *= -1.0
+    A = [np.ones((s, 1)) for _ in range(3)]
+    z = O.mttkrp(T2, A, 0)[:, 0]
+    assert abs(np.linalg.norm(z) - s) > 1e-6
+
+
+# --- normal-equation solve (Sec. 2.3, Algorithm 1 line 7) --------------------
+
+def test_solve_matches_library_spd():
+    g = np.random.default_rng(8)
+    B = g.standard_normal((12, 7))
+    G = B.T @ B + 0.1 * np.eye(7)
+    M = g.standard_normal((9, 7))
+    X = O.solve_normal(M, G)
+    np.testing.assert_allclose(X, np.linalg.solve(G, M.T).T, rtol=1e-11, atol=1e-12)
+
+
+def test_solve_orthonormal_factors_identity():
+    """T11: orthonormal columns give S = I, Gamma = I, so A_new = M."""
+    g = np.random.default_rng(9)
+    A = [np.linalg.qr(g.standard_normal((s, 4)))[0] for s in (6, 7, 8)]
+    S = [O.gram(a) for a in A]
+    for n in range(3):
+        np.testing.assert_allclose(O.gamma(S, n), np.eye(4), atol=1e-14)
+    M = g.standard_normal((6, 4))
+    np.testing.assert_allclose(O.solve_normal(M, O.gamma(S, 0)), M, atol=1e-14)
+
+
+def test_solve_singular_falls_back_to_pinv():
+    g = np.random.default_rng(10)
+    B = g.standard_normal((3, 6))           # rank 3 Gram of size 6
+    G = B.T @ B
+    M = g.standard_normal((5, 6)) @ G       # consistent right-hand sides
+    info = O.SolveInfo()
+    X = O.solve_normal(M, G, info)
+    assert info.singular
+    np.testing.assert_allclose(X, M @ np.linalg.pinv(G, rcond=1e-13), rtol=1e-8, atol=1e-9)
+
+
+# --- T10: fitness formula equals explicit reconstruction (Sec. 5) -------------
+
+def test_fitness_formula_vs_reconstruction():
+    g = np.random.default_rng(11)
+    dims = (5, 6, 7)
+    X = g.standard_normal(dims)
+    A = _rand_factors(dims, 3, 12)
+    assert abs(O.fitness(X, A) - O.fitness_explicit(X, A)) < 1e-12
+
+
+def test_norm_model_sq_is_reconstruction_norm():
+    A = _rand_factors((4, 5, 3, 2), 3, 13)
+    assert abs(O.norm_model_sq(A) - np.linalg.norm(O.reconstruct(A)) ** 2) < 1e-10
+
+
+# --- T8: exact low-rank recovery and the noise floor (Sec. 5.1) -------------
+
+def test_als_recovers_exact_low_rank():
+    At = _rand_factors((8, 9, 10), 3, 14)
+    X = O.reconstruct(At)
+    g = np.random.default_rng(15)
+    A0 = [a + 1e-2 * g.standard_normal(a.shape) for a in At]
+    _, tr = O.cp_als(X, A0, 60)
+    assert tr[-1] > 1.0 - 1e-9
+    # ALS never increases the residual (checked on explicit reconstructions:
+    # the formula saturates once the residual falls below sqrt(eps) ||X||)
+    A = [a.copy() for a in A0]
+    S = [O.gram(a) for a in A]
+    res = []
+    for _ in range(20):
+        O.als_sweep(X, A, S)
+        res.append(np.linalg.norm(X - O.reconstruct(A)))
+    assert all(b <= a * (1 + 1e-9) + 1e-13 for a, b in zip(res, res[1:]))
+
+
+def test_als_noise_floor():
+    """At the least-squares optimum the residual is the noise projected off
+    the model's tangent space: ||E|| sqrt(1 - dof / entries), dof = R(sum s - N + 1)."""
+    dims, R = (20, 20, 20), 3
+    At = _rand_factors(dims, R, 16)
+    X0 = O.reconstruct(At)
+    E = np.random.default_rng(17).standard_normal(dims) * 1e-3
+    X = X0 + E
+    _, tr = O.cp_als(X, [a.copy() for a in At], 30)
+    res = (1.0 - tr[-1]) * np.linalg.norm(X)
+    dof = R * (sum(dims) - len(dims) + 1)
+    expect = np.linalg.norm(E) * math.sqrt(1.0 - dof / np.prod(dims))
+    assert abs(res / expect - 1.0) < 0.03
+
+
+# --- T3, T4, T5, T6: pairwise perturbation (Sec. 3.1.1, 3.2.1, Eq. 2-3) ------
+
+def _pp_setup(dims, R, seed):
+    g = np.random.default_rng(seed)
+    X = g.standard_normal(dims)
+    Ap = _rand_factors(dims, R, seed + 1)
+    ops, Mp = O.pp_operators(X, Ap)
+    return g, X, Ap, ops, Mp
+
+
+@pytest.mark.parametrize("dims", [(4, 5, 6), (3, 4, 3, 5), (2, 3, 2, 3, 2)])
+def test_pp_zero_perturbation_is_exact(dims):
+    """T3: with dA = 0, M~^(n) = M_p^(n) = exact MTTKRP at A_p."""
+    _, X, Ap, ops, Mp = _pp_setup(dims, 3, 20)
+    dA = [np.zeros_like(a) for a in Ap]
+    for n in range(len(dims)):
+        exact = O.mttkrp(X, Ap, n)
+        np.testing.assert_allclose(O.pp_mttkrp(ops, Mp, Ap, dA, n, True), exact, rtol=1e-12)
+        np.testing.assert_allclose(Mp[n], exact, rtol=1e-12)
+
+
+@pytest.mark.parametrize("dims", [(4, 5, 6), (3, 4, 3, 5)])
+def test_pp_single_perturbation_is_exact(dims):
+    """T4a: the MTTKRP is linear in each factor, so with one dA^(i) != 0 the
+    first-order terms of Eq. 3 are exact."""
+    g, X, Ap, ops, Mp = _pp_setup(dims, 3, 21)
+    N = len(dims)
+    for i in range(N):
+        dA = [np.zeros_like(a) for a in Ap]
+        dA[i] = g.standard_normal(Ap[i].shape)
+        A = [a + d for a, d in zip(Ap, dA)]
+        for n in range(N):
+            np.testing.assert_allclose(O.pp_first_order(ops, Mp, dA, n), O.mttkrp(X, A, n),
+                                       rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("dims", [(5, 6, 7), (4, 3, 5, 4)])
+def test_pp_error_scales_quadratically(dims):
+    """T4b: the dropped terms carry >= 2 factors dA, so scaling every dA by t
+    scales the error by t^2 (Sec. 3.2.1)."""
+    g, X, Ap, ops, Mp = _pp_setup(dims, 3, 22)
+    D = [g.standard_normal(a.shape) for a in Ap]
+    N = len(dims)
+    for n in range(N):
+        errs = []
+        ts = [1e-1, 1e-2, 1e-3]
+        for t in ts:
+            dA = [t * d for d in D]
+            A = [a + d for a, d in zip(Ap, dA)]
+            errs.append(np.linalg.norm(O.pp_first_order(ops, Mp, dA, n) - O.mttkrp(X, A, n)))
+        slopes = np.diff(np.log(errs)) / np.diff(np.log(ts))
+        assert np.all(np.abs(slopes - 2.0) < 0.05), slopes
+
+
+def test_pp_order3_with_V_exact_on_cp_tensor():
+    """T5: for N = 3 and X = [[A]] (A the current factors), Eq. 2's dropped
+    term is exactly V^(1); PP with V reproduces the exact MTTKRP for every
+    mode, whatever A_p.  Counting each pair twice would not."""
+    g = np.random.default_rng(23)
+    dims, R = (5, 6, 7), 3
+    A = _rand_factors(dims, R, 24)
+    X = O.reconstruct(A)
+    Ap = [a + 0.3 * g.standard_normal(a.shape) for a in A]
+    ops, Mp = O.pp_operators(X, Ap)
+    dA = [a - b for a, b in zip(A, Ap)]
+    for n in range(3):
+        exact = O.mttkrp(X, A, n)
+        np.testing.assert_allclose(O.pp_mttkrp(ops, Mp, A, dA, n, True), exact,
+                                   rtol=1e-10, atol=1e-10)
+        doubled = O.pp_first_order(ops, Mp, dA, n) + 2 * O.pp_second_order(A, dA, n)
+        assert np.linalg.norm(doubled - exact) > 1e-3 * np.linalg.norm(exact)
+
+
+@pytest.mark.parametrize("dims", [(4, 3, 5, 4), (3, 4, 3, 2, 3)])
+def test_pp_with_V_third_order_on_cp_tensor(dims):
+    """For N >= 4 and X = [[A]], the second-order terms of the expansion in
+    Sec. 3.2.1 equal V^(n,i,j) up to one more factor dA (V takes A^(k)T A^(k)
+    where the expansion has A^(k)T A_p^(k)), so PP with V is exact to second
+    order: scaling dA by t scales its error by t^3 (and without V by t^2)."""
+    g = np.random.default_rng(31)
+    R = 2
+    Ap = _rand_factors(dims, R, 32)
+    D = [g.standard_normal(a.shape) for a in Ap]
+    ts = [1e-2, 5e-3, 2.5e-3]
+    for n in range(len(dims)):
+        ev, e0 = [], []
+        for t in ts:
+            dA = [t * d for d in D]
+            A = [a + d for a, d in zip(Ap, dA)]
+            X = O.reconstruct(A)
+            ops, Mp = O.pp_operators(X, Ap)
+            exact = O.mttkrp(X, A, n)
+            ev.append(np.linalg.norm(O.pp_mttkrp(ops, Mp, A, dA, n, True) - exact))
+            e0.append(np.linalg.norm(O.pp_mttkrp(ops, Mp, A, dA, n, False) - exact))
+        sv = np.diff(np.log(ev)) / np.diff(np.log(ts))
+        s0 = np.diff(np.log(e0)) / np.diff(np.log(ts))
+        assert np.all(np.abs(sv - 3.0) < 0.15), sv
+        assert np.all(np.abs(s0 - 2.0) < 0.15), s0
+
+
+@pytest.mark.parametrize("dims", [(4, 5, 6), (3, 4, 3, 5)])
+def test_pp_operators_consistent(dims):
+    """T6: M_p^(n) = M_p^(i,n) x_i A_p^(i) for every i != n (Sec. 3.2.3)."""
+    _, X, Ap, ops, Mp = _pp_setup(dims, 2, 25)
+    N = len(dims)
+    for n in range(N):
+        for i in range(N):
+            if i == n:
+                continue
+            if i < n:
+                v = np.einsum("xyr,xr->yr", ops[(i, n)], Ap[i])
+            else:
+                v = np.einsum("yxr,xr->yr", ops[(n, i)], Ap[i])
+            np.testing.assert_allclose(v, Mp[n], rtol=1e-12, atol=1e-12)
+
+
+def test_pp_operator_matches_brute_force():
+    g = np.random.default_rng(26)
+    dims = (3, 2, 4, 2)
+    X = g.standard_normal(dims)
+    Ap = _rand_factors(dims, 2, 27)
+    ops, _ = O.pp_operators(X, Ap)
+    for (i, n), T in ops.items():
+        np.testing.assert_allclose(T, _brute_partial(X, Ap, [i, n]), rtol=1e-12, atol=1e-12)
+
+
+# --- T7: pairwise-update ALS (Algorithm 5) equals ALS (Algorithm 1) --------
+
+@pytest.mark.parametrize("dims", [(5, 6, 7), (3, 4, 3, 5)])
+def test_pairwise_update_als_equals_als(dims):
+    g = np.random.default_rng(28)
+    X = g.standard_normal(dims)
+    A0 = [g.random((s, 3)) for s in dims]
+    A1 = [a.copy() for a in A0]
+    S1 = [O.gram(a) for a in A1]
+    A2 = [a.copy() for a in A0]
+    S2 = [O.gram(a) for a in A2]
+    M = [O.mttkrp(X, A2, n) for n in range(len(dims))]
+    for _ in range(3):
+        O.als_sweep(X, A1, S1)
+        O.pairwise_update_als_sweep(X, A2, S2, M)
+    for a, b in zip(A1, A2):
+        np.testing.assert_allclose(a, b, rtol=1e-8, atol=1e-10)
+
+
+# --- Algorithm 3 controller special cases ------------------------------------
+
+def test_pp_als_eps_zero_is_als():
+    p = synth.scaled("normal", 8, 3, 3, seed=3, noise=1e-2, storage="f64")
+    X = p.X
+    A_als, tr_als = O.cp_als(X, p.A0, 12)
+    A_pp, tr = O.pp_cp_als(X, p.A0, 12, eps=0.0)
+    assert tr.kinds == ["als"] * 12
+    np.testing.assert_allclose(tr.fitness, tr_als, rtol=0, atol=1e-13)
+
+
+def test_pp_init_first_mode_equals_als():
+    """With eps > 1 the operators are built at once (dA = A initially); the
+    first PP sweep starts from dA = 0, so its first mode update is exactly
+    the ALS update."""
+    p = synth.scaled("normal", 7, 3, 2, seed=4, noise=1e-2, storage="f64")
+    A_pp, tr = O.pp_cp_als(p.X, p.A0, 1, eps=2.0)
+    assert tr.kinds == ["pp_init"]
+    A = [a.copy() for a in p.A0]
+    S = [O.gram(a) for a in A]
+    G = O.gamma(S, 0)
+    a0 = O.solve_normal(O.mttkrp(p.X, A, 0), G)
+    np.testing.assert_allclose(A_pp[0], a0, rtol=1e-11, atol=1e-12)
+
+
+def test_pp_als_converges_on_exact_tensor():
+    """On an exactly low-rank tensor the PP-ALS trajectory tracks ALS (the
+    PP error is second order in dA, Sec. 4.1) and reaches the exact fit."""
+    At = _rand_factors((9, 10, 11), 3, 29)
+    X = O.reconstruct(At)
+    g = np.random.default_rng(30)
+    A0 = [a + 5e-2 * g.standard_normal(a.shape) for a in At]
+    _, tr = O.pp_cp_als(X, A0, 80, eps=0.1)
+    _, ta = O.cp_als(X, A0, 80)
+    assert "pp_approx" in tr.kinds
+    assert max(abs(a - b) for a, b in zip(tr.fitness, ta)) < 1e-5
+    assert tr.fitness[-1] > 1.0 - 1e-7
+
+
+# --- Table 1 / Sec. 3.2.3 cost formulas ---------------------------------------
+
+@pytest.mark.parametrize("N", [3, 4, 5, 6])
+def test_operator_build_cost_expansion(N):
+    """2R sum_{l=2}^{N-1} C(l+1,2) s^{N-l+2} = 6 s^N R + 12 s^{N-1} R + O(s^{N-2})."""
+    R = 7
+    for s in (10, 100, 1000):
+        c = O.pp_operator_build_cost(s, N, R)
+        if N == 3:                       # a single level: three first-level contractions
+            assert c == 6 * s ** 3 * R
+            continue
+        lead = 6 * s ** N * R + 12 * s ** (N - 1) * R
+        rest = c - lead
+        assert rest >= 0
+        assert rest <= 2 * R * math.comb(N, 2) * N * s ** (N - 2)
+    assert O.table1_cp(10, N, R)["pp_init"] == 6 * 10 ** N * R
