@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark: time-to-fitness of PP-CP-ALS (Algorithm 3) on one GB300.
+
+One step = one decomposition of the 400x400x400 rank-100 workload (FP32
+storage, collinearity C ~ U[0.5,0.9), 1e-2 relative noise, U[0,1] init) by
+PP-ALS (eps = 0.1, with the second-order terms) through the whole hot path:
+first-level contractions on the tensor cores, multi-TTV, PP operator
+construction, PP corrections, float64 Gram/Cholesky/solve and fitness, and the
+eps controller.  The step stops at the first sweep whose exact fitness reaches
+f* - 1e-6, where f* is the fitness plain float64 GPU ALS reaches after 200
+sweeps (computed once, untimed).  value = seconds of that step (lower is
+better), timed with CUDA events, inputs resident in HBM, L2 flushed between
+steps.
+
+--impl reference times the FP64 CPU oracle (the baseline arm) on the host
+cores for the same workload and metric.
+Under torchrun (--gpus N > 1) every rank decomposes its own instance
+(replicas, no data-path collective); value is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-fitness (s) PP-ALS vs ALS on 1 GB300; MTTKRP TFLOP/s and HBM GB/s"
+SCHEDULE = os.path.join(ROOT, "tests", "golden", "order3_400_rank100_schedule.json")
+PROFILE = os.path.join(ROOT, "profiles", "umma_gemm_order3_400_rank100.json")
+UMMA_SRC = os.path.join(ROOT, "paper_1811_10573_gb300", "csrc", "umma.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="order3_400_rank100")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-als", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, seed):
+    from paper_1811_10573_gb300 import synth
+    table = {"order3_400_rank100": synth.order3_400_rank100,
+             "order4_120_rank64": synth.order4_120_rank64,
+             "order6_24_rank50": synth.order6_24_rank50,
+             "order3_60_rank10": synth.order3_60_rank10}
+    return table[name](seed=seed)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"], "src": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
+
+
+# ----------------------------------------------------------------- oracle timing
+def oracle_sample(p):
+    """Time one of each oracle step on the full workload (bounded sample)."""
+    import numpy as np
+    from oracle import cpals_oracle as O
+    X = p.X.astype(np.float64)
+    A = [a.copy() for a in p.A0]
+    S = [O.gram(a) for a in A]
+    t = time.perf_counter()
+    O.als_sweep(X, A, S)
+    t_als = time.perf_counter() - t
+    t = time.perf_counter()
+    ops, Mp = O.pp_operators(X, A)
+    t_build = time.perf_counter() - t
+    Ap = [a.copy() for a in A]
+    dA = [np.zeros_like(a) for a in A]
+    t = time.perf_counter()
+    O.pp_sweep(ops, Mp, A, Ap, dA, S, True)
+    t_pp = time.perf_counter() - t
+    t = time.perf_counter()
+    O.fitness(X, A)
+    t_fit = time.perf_counter() - t
+    return {"als": t_als, "build": t_build, "pp": t_pp, "fit": t_fit}
+
+
+def project(ts, counts):
+    """Oracle seconds for a sweep schedule: ALS sweeps, PP initialisation
+    sweeps (build + one PP pass), PP approximated sweeps, one exact check."""
+    return (counts.get("als", 0) * ts["als"] + counts.get("pp_init", 0) * (ts["build"] + ts["pp"])
+            + counts.get("pp_approx", 0) * ts["pp"] + ts["fit"])
+
+
+def oracle_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1811_10573_gb300 import build, cpals, harness
+
+    dist = harness.init()
+    torch.cuda.set_device(dist.local_rank)
+    build.build()
+    cpals.lib()
+    p = workload(args.workload, seed=dist.rank)
+    Xd = torch.from_numpy(np.ascontiguousarray(p.X)).cuda()
+
+    # f*: plain float64 GPU ALS after the workload's sweep budget (untimed)
+    with cpals.CPALS(p.dims, p.R, "fp64") as g64:
+        g64.set_tensor(Xd)
+        g64.init_factors(p.A0)
+        ref = g64.run(p.sweeps, 0.0, True, 0.0)
+        f_star = float(ref["fitness"][-1])
+    target = f_star - 1e-6
+    max_sweeps = 2 * p.sweeps
+
+    ctx = cpals.CPALS(p.dims, p.R, args.precision)
+    ctx.set_tensor(Xd)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    ctx.set_profiling(True)
+
+    def one(eps, timed=True):
+        ctx.init_factors(p.A0)
+        flush.zero_()
+        torch.cuda.synchronize()
+        dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = ctx.run(max_sweeps, eps, True, target)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, out
+
+    for _ in range(args.warmup):
+        one(p.eps)
+    ctx.reset_stats()
+    clocks = Clocks(dist.local_rank)
+    clocks.start()
+    times, outs = [], []
+    for _ in range(args.steps):
+        dt, out = one(p.eps)
+        times.append(dist.max(dt))
+        outs.append(out)
+    clk = clocks.stop()
+    fl = ctx.get_stats(0)
+    launches = ctx.get_stats(1)["launches"]
+
+    value = statistics.mean(times)
+    last = outs[-1]
+    kinds = last["kinds"]
+    counts = {k: kinds.count(k) for k in ("als", "pp_init", "pp_approx")}
+
+    # plain ALS in the same precision to the same target (the PP-ALS vs ALS comparison)
+    als_time = None
+    als_reached = None
+    if not args.no_als:
+        dt, out = one(0.0)
+        als_time = dist.max(dt)
+        als_reached = out["reached"]
+
+    # end to end through the C ABI from pinned host buffers
+    Xh = torch.from_numpy(np.ascontiguousarray(p.X)).pin_memory()
+    e2e_times = []
+    nsw = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.set_tensor(Xh)
+        ctx.init_factors(p.A0)
+        out = ctx.run(max_sweeps, p.eps, True, target)
+        A_host = ctx.get_factors()
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_times.append(dist.max(e0.elapsed_time(e1) / 1e3))
+        nsw.append(len(out["kinds"]))
+    fbytes = sum(a.nbytes for a in A_host)
+    h2d = int(Xh.numel() * Xh.element_size() + fbytes)
+    d2h = int(fbytes + statistics.mean(nsw) * (32 * 8 + 4 * 4))
+
+    # roofline of the first-level contraction (the dominant kernel)
+    pk = peaks()
+    ach = fl["bytes"] / (fl["total_ms"] / 1e3) / 1e9 if fl["total_ms"] > 0 else 0.0
+    tflops = fl["flops"] / (fl["total_ms"] / 1e3) / 1e12 if fl["total_ms"] > 0 else 0.0
+    traffic = None
+    if os.path.exists(PROFILE):
+        with open(PROFILE) as f:
+            prof = json.load(f)
+        h = hashlib.sha256(open(UMMA_SRC, "rb").read()).hexdigest()
+        if prof.get("source_sha256") == h and prof.get("precision") == args.precision:
+            traffic = prof.get("traffic_bytes_per_launch")
+    roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / pk["hbm_gbs"], 4), "traffic": traffic,
+                "kernel": "first-level contraction (tcgen05 bf16)" if args.precision == "mixed"
+                else "first-level contraction (SIMT)",
+                "launches": fl["launches"], "avg_launch_us": round(fl["total_ms"] * 1e3 / max(1, fl["launches"]), 2),
+                "algorithmic_bytes_per_launch": round(fl["bytes"] / max(1, fl["launches"])),
+                "tflops": round(tflops, 2), "peak_src": pk["src"] + " (copy bandwidth)"}
+
+    result = {
+        "metric": METRIC, "value": round(value, 6), "unit": "s", "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value * 1e3, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "bf16-tc/fp32/fp64", "fp32": "fp32/fp64", "fp64": "fp64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": p.name, "dims": p.dims, "R": p.R, "eps": p.eps,
+                   "max_sweeps": max_sweeps, "target_fitness": target, "f_star_fp64_als": f_star,
+                   "precision": args.precision, "use_V": True,
+                   "l2": "flushed between steps (256 MB write); X is 256 MB fp32",
+                   "parallelism": "replicas" if dist.world > 1 else "single GPU"},
+        "reached": all(o["reached"] for o in outs),
+        "sweeps_to_target": len(kinds), "sweep_counts": counts,
+        "final_fitness": float(last["fitness"][-1]),
+        "als_time_to_fitness_s": als_time, "als_reached": als_reached,
+        "pp_vs_als_speedup": (round(als_time / value, 3) if als_time else None),
+        "roofline": roofline,
+        "e2e": {"value": round(statistics.mean(e2e_times), 6), "unit": "s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches), "gpu_launches_per_step": round(launches / args.steps, 1),
+        "clocks": clk,
+    }
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        ts = oracle_sample(p)
+        result["cpu_baseline"] = {
+            "value": round(project(ts, counts), 3), "unit": "s", "cores": oracle_cores(),
+            "kind": "oracle",
+            "sample": ("float64 numpy oracle on the full workload: one ALS sweep "
+                       f"({ts['als']:.3f} s), one PP operator build ({ts['build']:.3f} s), one PP "
+                       f"sweep ({ts['pp']:.3f} s), one exact fitness ({ts['fit']:.3f} s); projected "
+                       f"onto this run's schedule {counts}")}
+    if dist.rank == 0:
+        print(json.dumps(result))
+    ctx.close()
+    dist.close()
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = workload(args.workload, seed=0)
+    counts = None
+    if args.workload == "order3_400_rank100" and os.path.exists(SCHEDULE):
+        with open(SCHEDULE) as f:
+            counts = json.load(f)["counts_to_target"]
+    vals = []
+    ts = None
+    for i in range(args.warmup + args.steps):
+        ts = oracle_sample(p)
+        if i >= args.warmup:
+            vals.append(project(ts, counts or {"als": p.sweeps}))
+    value = statistics.mean(vals)
+    sample = ("float64 numpy oracle on the full workload, each step one ALS sweep, one PP "
+              "operator build, one PP sweep and one exact fitness, projected onto the oracle's "
+              f"own schedule to the target {counts} (tests/golden/order3_400_rank100_schedule.json)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(value * 1e3, 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": p.name, "dims": p.dims, "R": p.R, "eps": p.eps},
+        "cpu_baseline": {"value": round(value, 4), "unit": "s", "cores": oracle_cores(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "last_sample_seconds": ts,
+    }))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

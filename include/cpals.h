@@ -1,0 +1,188 @@
+/*
+ * cpals.h -- C ABI of the GB300 pairwise-perturbation CP-ALS library.
+ *
+ * Source method: Ma & Solomonik, "Accelerating Alternating Least Squares for
+ * Tensor Decomposition by Pairwise Perturbation" (arXiv 1811.10573).
+ * The paper states the problem as: input a dense order-N tensor X
+ * (s_1 x ... x s_N), a rank R and a PP tolerance eps; output factors
+ * [[A^(1), ..., A^(N)]] (Algorithm 1 CP-ALS, Algorithm 3 PP-CP-ALS).
+ * These calls expose its steps one by one.
+ *
+ * Conventions for every call:
+ *   - Tensors are dense, row-major, last mode fastest.  Factors A^(n) are
+ *     s_n x R row-major (r fastest), always exchanged as float64.
+ *   - Modes are 0-based (the paper's mode n is index n-1).
+ *   - Every call returns a cpals_status; nothing throws across the ABI.
+ *     On failure, cpals_last_error(ctx) returns a message that stays valid
+ *     until the next call on the same context.
+ *   - The context owns all device memory it allocates; pointers passed in
+ *     stay owned by the caller and are only read (or written, for *_out
+ *     arguments) during the call.
+ *   - Work runs on the context's stream (see cpals_set_stream).  Calls that
+ *     return host data synchronise that stream before returning.
+ *   - One context = one decomposition; a context is not thread-safe.
+ */
+#ifndef CPALS_H
+#define CPALS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cpals_ctx cpals_ctx;
+
+typedef enum {
+  CPALS_OK = 0,
+  CPALS_E_INVALID = 1,     /* bad argument: N < 3, R < 1, dims <= 0, NULL pointer, bad mode */
+  CPALS_E_OOM = 2,         /* device allocation failed */
+  CPALS_E_CUDA = 3,        /* CUDA runtime/driver error (text in cpals_last_error) */
+  CPALS_E_STATE = 4,       /* call out of order (e.g. pp_sweep before pp_build_operators) */
+  CPALS_E_SINGULAR = 5,    /* Gamma not positive definite: the factor of that mode was left unchanged */
+  CPALS_E_NUMERIC = 6,     /* NaN/Inf detected in a result */
+  CPALS_E_TIMEOUT = 7,     /* a bounded device wait gave up */
+  CPALS_E_UNSUPPORTED = 8  /* configuration outside what this build implements */
+} cpals_status;
+
+/* Arithmetic of the contractions (the normal-equation solve, Grams and
+ * fitness are float64 in every mode). */
+typedef enum {
+  CPALS_FP64 = 0,        /* tensor, contractions and operators in float64 */
+  CPALS_FP32 = 1,        /* tensor, contractions and operators in float32 */
+  CPALS_MIXED_BF16 = 2   /* first-level contractions and operator construction on
+                            bf16 tensor cores (fp32 accumulate); lower levels,
+                            operators and PP corrections in float32 */
+} cpals_precision;
+
+/* Sweep kinds reported by cpals_run (Algorithm 3 and Table 2 of the paper). */
+enum { CPALS_SWEEP_ALS = 0, CPALS_SWEEP_PP_INIT = 1, CPALS_SWEEP_PP_APPROX = 2 };
+
+/* Create a context for an order-N tensor of size dims[0] x ... x dims[N-1]
+ * and CP rank R (Sec. 2.3).  3 <= N <= 8, 1 <= R <= 128.  Allocates the
+ * tensor storage and all workspaces of the dimension trees (Sec. 2.5,
+ * Sec. 3.2.3).  *out receives the context; NULL on failure. */
+cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpals_ctx** out);
+
+/* Free every device and host resource of the context.  NULL is ignored. */
+void cpals_destroy(cpals_ctx* ctx);
+
+/* Order the context's work after, and before, work already queued on a
+ * caller stream (a cudaStream_t passed as void*; NULL = the legacy default
+ * stream).  The library keeps its own stream and joins the caller stream at
+ * the start and end of every call. */
+cpals_status cpals_set_stream(cpals_ctx* ctx, void* cuda_stream);
+
+/* Copy the input tensor X (Sec. 2.3) into the context.  data: prod(dims)
+ * values, dtype 0 = float64, 1 = float32; on_device != 0 means data is a
+ * device pointer, else a host pointer (pinned or pageable).  In FP32 and
+ * MIXED_BF16 modes float64 input is rounded to float32; in MIXED_BF16 a bf16
+ * copy for the tensor cores is also made.  ||X||_F^2 is computed in float64
+ * from the stored values.  Clears any PP operators. */
+cpals_status cpals_set_tensor(cpals_ctx* ctx, const void* data, int dtype, int on_device);
+
+/* Set the factors A^(n) from N host float64 arrays of s_n x R (row-major);
+ * they are the random initial guess of Algorithm 1/3, line 2.  Resets the
+ * controller state as Algorithm 3 line 2 does: dA^(n) <- A^(n), so the next
+ * eps test fails, S^(n) <- A^(n)T A^(n); clears PP operators. */
+cpals_status cpals_init_factors(cpals_ctx* ctx, const double* const* factors);
+
+/* One regular ALS sweep (Algorithm 1, lines 4-11) over modes 0..N-1 with the
+ * binary dimension tree (Sec. 2.5): two first-level contractions of X per
+ * sweep.  Afterwards dA^(n) = A^(n)_new - A^(n)_old (Algorithm 3, line 20).
+ * fitness_out (nullable): exact fitness 1 - ||X - [[A]]||/||X|| (Sec. 5). */
+cpals_status cpals_als_sweep(cpals_ctx* ctx, double* fitness_out);
+
+/* Build the PP operators M_p^(i,n), i < n, and M_p^(n) at the current
+ * factors with the operator dimension tree (Sec. 3.2.3), then set
+ * A_p <- A, dA <- 0 (Algorithm 3, lines 5-8). */
+cpals_status cpals_pp_build_operators(cpals_ctx* ctx);
+
+/* One PP approximated sweep (Algorithm 3, lines 10-17): each right-hand side
+ * is Eq. 3's M~^(n); use_V != 0 adds the second-order terms V^(n,i,j).
+ * dA^(n) = A^(n)_new - A_p^(n).  fitness_out (nullable): fitness estimated
+ * from M~^(N) (not exact; see cpals_fitness).  CPALS_E_STATE if no operators. */
+cpals_status cpals_pp_sweep(cpals_ctx* ctx, int use_V, double* fitness_out);
+
+/* Exact fitness of the current factors: one exact MTTKRP of the last mode
+ * (a full pass over X) plus float64 Grams (Sec. 5). */
+cpals_status cpals_fitness(cpals_ctx* ctx, double* out);
+
+/* Copy the factors to N caller-owned host float64 arrays of s_n x R. */
+cpals_status cpals_get_factors(cpals_ctx* ctx, double* const* out);
+
+/* out_N[n] = ||dA^(n)||_F / ||A^(n)||_F (the quantities Algorithm 3 tests). */
+cpals_status cpals_get_dA_ratios(cpals_ctx* ctx, double* out_N);
+
+/* Run Algorithm 3 for at most max_sweeps sweeps with tolerance eps (eps <= 0
+ * gives plain ALS).  Each ALS sweep, PP initialisation sweep (build + one PP
+ * pass) and PP approximated sweep counts as one sweep.  If target > 0 the run
+ * stops after the first sweep whose exact fitness is >= target (for PP sweeps
+ * the estimate is checked first, then confirmed by cpals_fitness).
+ * Outputs (each nullable, length max_sweeps): fitness_trace (exact after ALS
+ * sweeps, estimate after PP sweeps), kind_trace (CPALS_SWEEP_*),
+ * time_trace (seconds since the start of the run, host clock after the
+ * sweep's stream synchronisation).  *n_done receives the number of sweeps
+ * run; *reached (nullable) 1 if the target was confirmed. */
+cpals_status cpals_run(cpals_ctx* ctx, int max_sweeps, double eps, int use_V, double target,
+                       double* fitness_trace, int* kind_trace, double* time_trace,
+                       int* n_done, int* reached);
+
+/* Message describing the last failure on this context ("" if none). */
+const char* cpals_last_error(const cpals_ctx* ctx);
+
+/* ---- inspection calls used by parity tests (same kernels as the sweeps) ---- */
+
+/* Exact MTTKRP M^(n) = X_(n) P^(n) (Sec. 2.3) at the current factors, through
+ * the same first-level and multi-TTV kernels as an ALS sweep; out: s_n x R
+ * float64 host buffer. */
+cpals_status cpals_mttkrp(cpals_ctx* ctx, int n, double* out);
+
+/* Copy the PP operator M_p^(i,n), i < n, (s_i x s_n x R, Sec. 3.2.1) or, for
+ * i == n, M_p^(n) (s_n x R) to a float64 host buffer.  CPALS_E_STATE if the
+ * operators have not been built. */
+cpals_status cpals_get_operator(cpals_ctx* ctx, int i, int n, double* out);
+
+/* Eq. 3's M~^(n) for the current A, A_p and dA, without updating anything;
+ * out: s_n x R float64 host buffer. */
+cpals_status cpals_pp_mttkrp(cpals_ctx* ctx, int n, int use_V, double* out);
+
+/* Copy A_p^(n) (which = 0) or dA^(n) (which = 1) to a host float64 buffer. */
+cpals_status cpals_get_state(cpals_ctx* ctx, int which, int n, double* out);
+
+/* ---- measurement ---- */
+
+/* enable != 0: record CUDA events around every first-level contraction on
+ * the context stream (also inside captured graphs); timings accumulate per
+ * kind until cpals_reset_stats. */
+cpals_status cpals_set_profiling(cpals_ctx* ctx, int enable);
+cpals_status cpals_reset_stats(cpals_ctx* ctx);
+
+/* Kernel statistics since the last reset.  kind 0 = first-level
+ * contraction (all launches), 1 = all kernels of the library (count only).
+ * *launches: number of launches; *total_ms: summed CUDA-event time (kind 0
+ * only, profiling on); *bytes, *flops: algorithmic bytes moved and flops of
+ * those launches (kind 0 only). */
+cpals_status cpals_get_stats(cpals_ctx* ctx, int kind, int64_t* launches, double* total_ms,
+                             double* bytes, double* flops);
+
+/* enable != 0 (default): capture each sweep kind in a CUDA graph on first use
+ * and replay it; 0 launches kernels directly. */
+cpals_status cpals_set_graphs(cpals_ctx* ctx, int enable);
+
+/* ---- host-only cost model (no GPU needed) ---- */
+
+/* Flop counts of the kernels this library launches for one step of the
+ * given kind (0 = ALS sweep, 1 = PP operator build, 2 = PP approximated
+ * sweep with V, 3 = PP operator build as the paper's formula
+ * 2R sum_{l=2}^{N-1} C(l+1,2) s^{N-l+2} for an equidimensional tensor)
+ * for dims[0..N-1] and rank R.  Contractions only (no solve), Sec. 3.2.3 and
+ * Table 1.  Returns CPALS_E_INVALID on bad sizes. */
+cpals_status cpals_cost_model(const int64_t* dims, int N, int R, int kind, double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPALS_H */

@@ -1,0 +1,326 @@
+"""Thin ctypes binding of libcpals (include/cpals.h).
+
+Argument marshalling only: every step of CP-ALS / PP-CP-ALS runs in the CUDA
+library.  The module-level functions carry the C ABI's names; ``CPALS`` wraps
+them for convenience.  Importing this module never falls back to anything:
+if the library is missing, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcpals.so")
+
+FP64, FP32, MIXED_BF16 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED_BF16, "mixed_bf16": MIXED_BF16}
+SWEEP_KINDS = {0: "als", 1: "pp_init", 2: "pp_approx"}
+STATUS = {0: "OK", 1: "E_INVALID", 2: "E_OOM", 3: "E_CUDA", 4: "E_STATE", 5: "E_SINGULAR",
+          6: "E_NUMERIC", 7: "E_TIMEOUT", 8: "E_UNSUPPORTED"}
+
+_lib = None
+_ctx_p = C.c_void_p
+_dp = C.POINTER(C.c_double)
+_i64p = C.POINTER(C.c_int64)
+_ip = C.POINTER(C.c_int)
+
+_SIGS = {
+    "cpals_create": (C.c_int, [_i64p, C.c_int, C.c_int, C.c_int, C.POINTER(_ctx_p)]),
+    "cpals_destroy": (None, [_ctx_p]),
+    "cpals_set_stream": (C.c_int, [_ctx_p, C.c_void_p]),
+    "cpals_set_tensor": (C.c_int, [_ctx_p, C.c_void_p, C.c_int, C.c_int]),
+    "cpals_init_factors": (C.c_int, [_ctx_p, C.POINTER(_dp)]),
+    "cpals_als_sweep": (C.c_int, [_ctx_p, _dp]),
+    "cpals_pp_build_operators": (C.c_int, [_ctx_p]),
+    "cpals_pp_sweep": (C.c_int, [_ctx_p, C.c_int, _dp]),
+    "cpals_fitness": (C.c_int, [_ctx_p, _dp]),
+    "cpals_get_factors": (C.c_int, [_ctx_p, C.POINTER(_dp)]),
+    "cpals_get_dA_ratios": (C.c_int, [_ctx_p, _dp]),
+    "cpals_run": (C.c_int, [_ctx_p, C.c_int, C.c_double, C.c_int, C.c_double, _dp, _ip, _dp,
+                            _ip, _ip]),
+    "cpals_last_error": (C.c_char_p, [_ctx_p]),
+    "cpals_mttkrp": (C.c_int, [_ctx_p, C.c_int, _dp]),
+    "cpals_get_operator": (C.c_int, [_ctx_p, C.c_int, C.c_int, _dp]),
+    "cpals_pp_mttkrp": (C.c_int, [_ctx_p, C.c_int, C.c_int, _dp]),
+    "cpals_get_state": (C.c_int, [_ctx_p, C.c_int, C.c_int, _dp]),
+    "cpals_set_profiling": (C.c_int, [_ctx_p, C.c_int]),
+    "cpals_reset_stats": (C.c_int, [_ctx_p]),
+    "cpals_get_stats": (C.c_int, [_ctx_p, C.c_int, _i64p, _dp, _dp, _dp]),
+    "cpals_set_graphs": (C.c_int, [_ctx_p, C.c_int]),
+    "cpals_cost_model": (C.c_int, [_i64p, C.c_int, C.c_int, C.c_int, _dp]),
+}
+
+
+def lib():
+    """Load libcpals.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_1811_10573_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class CPALSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+# ---------------------------------------------------------------- C names
+def cpals_create(dims, N, R, precision):
+    d = (C.c_int64 * N)(*[int(x) for x in dims])
+    out = _ctx_p()
+    st = lib().cpals_create(d, N, R, precision, C.byref(out))
+    return st, out
+
+
+def cpals_destroy(ctx):
+    lib().cpals_destroy(ctx)
+
+
+def cpals_last_error(ctx):
+    s = lib().cpals_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def cpals_set_stream(ctx, stream):
+    return lib().cpals_set_stream(ctx, C.c_void_p(int(stream)))
+
+
+def cpals_set_tensor(ctx, ptr, dtype, on_device):
+    return lib().cpals_set_tensor(ctx, C.c_void_p(int(ptr)), dtype, on_device)
+
+
+def cpals_init_factors(ctx, factors):
+    arr = (_dp * len(factors))(*[_dptr(f) for f in factors])
+    return lib().cpals_init_factors(ctx, arr)
+
+
+def cpals_als_sweep(ctx, fit):
+    return lib().cpals_als_sweep(ctx, fit)
+
+
+def cpals_pp_build_operators(ctx):
+    return lib().cpals_pp_build_operators(ctx)
+
+
+def cpals_pp_sweep(ctx, use_V, fit):
+    return lib().cpals_pp_sweep(ctx, use_V, fit)
+
+
+def cpals_fitness(ctx, out):
+    return lib().cpals_fitness(ctx, out)
+
+
+def cpals_get_factors(ctx, outs):
+    arr = (_dp * len(outs))(*[_dptr(o) for o in outs])
+    return lib().cpals_get_factors(ctx, arr)
+
+
+def cpals_get_dA_ratios(ctx, out):
+    return lib().cpals_get_dA_ratios(ctx, _dptr(out))
+
+
+def cpals_run(ctx, max_sweeps, eps, use_V, target, ftrace, ktrace, ttrace, n_done, reached):
+    return lib().cpals_run(ctx, max_sweeps, eps, use_V, target, ftrace, ktrace, ttrace, n_done,
+                           reached)
+
+
+def cpals_mttkrp(ctx, n, out):
+    return lib().cpals_mttkrp(ctx, n, _dptr(out))
+
+
+def cpals_get_operator(ctx, i, n, out):
+    return lib().cpals_get_operator(ctx, i, n, _dptr(out))
+
+
+def cpals_pp_mttkrp(ctx, n, use_V, out):
+    return lib().cpals_pp_mttkrp(ctx, n, use_V, _dptr(out))
+
+
+def cpals_get_state(ctx, which, n, out):
+    return lib().cpals_get_state(ctx, which, n, _dptr(out))
+
+
+def cpals_set_profiling(ctx, enable):
+    return lib().cpals_set_profiling(ctx, enable)
+
+
+def cpals_reset_stats(ctx):
+    return lib().cpals_reset_stats(ctx)
+
+
+def cpals_get_stats(ctx, kind):
+    n = C.c_int64()
+    ms, b, f = C.c_double(), C.c_double(), C.c_double()
+    st = lib().cpals_get_stats(ctx, kind, C.byref(n), C.byref(ms), C.byref(b), C.byref(f))
+    return st, n.value, ms.value, b.value, f.value
+
+
+def cpals_set_graphs(ctx, enable):
+    return lib().cpals_set_graphs(ctx, enable)
+
+
+def cpals_cost_model(dims, N, R, kind):
+    d = (C.c_int64 * N)(*[int(x) for x in dims])
+    out = C.c_double()
+    st = lib().cpals_cost_model(d, N, R, kind, C.byref(out))
+    if st != 0:
+        raise CPALSError(st, "cost model: bad sizes")
+    return out.value
+
+
+# ---------------------------------------------------------------- convenience wrapper
+class CPALS:
+    """One decomposition context (owns its device memory)."""
+
+    def __init__(self, dims, R, precision="fp64", stream=None):
+        self.dims = [int(d) for d in dims]
+        self.N = len(self.dims)
+        self.R = int(R)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        st, ctx = cpals_create(self.dims, self.N, self.R, prec)
+        if st != 0:
+            raise CPALSError(st, "cpals_create failed")
+        self.ctx = ctx
+        if stream is not None:
+            self._ck(cpals_set_stream(ctx, stream))
+
+    def _ck(self, st):
+        if st != 0:
+            raise CPALSError(st, cpals_last_error(self.ctx))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            cpals_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream):
+        self._ck(cpals_set_stream(self.ctx, stream))
+
+    def set_tensor(self, X):
+        """X: numpy array (host) or torch tensor (host or CUDA), float64/float32."""
+        if hasattr(X, "data_ptr"):          # torch tensor
+            import torch
+            assert X.is_contiguous()
+            dt = {torch.float64: 0, torch.float32: 1}[X.dtype]
+            self._ck(cpals_set_tensor(self.ctx, X.data_ptr(), dt, 1 if X.is_cuda else 0))
+            return
+        X = np.ascontiguousarray(X)
+        dt = {np.dtype(np.float64): 0, np.dtype(np.float32): 1}[X.dtype]
+        self._ck(cpals_set_tensor(self.ctx, X.ctypes.data, dt, 0))
+
+    def init_factors(self, factors):
+        fs = [_f64(f) for f in factors]
+        for f, s in zip(fs, self.dims):
+            assert f.shape == (s, self.R)
+        self._ck(cpals_init_factors(self.ctx, fs))
+
+    def als_sweep(self):
+        f = C.c_double()
+        self._ck(cpals_als_sweep(self.ctx, C.byref(f)))
+        return f.value
+
+    def pp_build_operators(self):
+        self._ck(cpals_pp_build_operators(self.ctx))
+
+    def pp_sweep(self, use_V=True):
+        f = C.c_double()
+        self._ck(cpals_pp_sweep(self.ctx, 1 if use_V else 0, C.byref(f)))
+        return f.value
+
+    def fitness(self):
+        f = C.c_double()
+        self._ck(cpals_fitness(self.ctx, C.byref(f)))
+        return f.value
+
+    def get_factors(self):
+        outs = [np.empty((s, self.R)) for s in self.dims]
+        self._ck(cpals_get_factors(self.ctx, outs))
+        return outs
+
+    def get_dA_ratios(self):
+        out = np.empty(self.N)
+        self._ck(cpals_get_dA_ratios(self.ctx, out))
+        return out
+
+    def run(self, max_sweeps, eps, use_V=True, target=0.0):
+        ft = np.zeros(max_sweeps)
+        kt = np.zeros(max_sweeps, dtype=np.int32)
+        tt = np.zeros(max_sweeps)
+        nd, rc = C.c_int(), C.c_int()
+        self._ck(cpals_run(self.ctx, max_sweeps, eps, 1 if use_V else 0, target, _dptr(ft),
+                           kt.ctypes.data_as(_ip), _dptr(tt), C.byref(nd), C.byref(rc)))
+        n = nd.value
+        return {"fitness": ft[:n], "kinds": [SWEEP_KINDS[int(k)] for k in kt[:n]],
+                "times": tt[:n], "reached": bool(rc.value)}
+
+    def mttkrp(self, n):
+        out = np.empty((self.dims[n], self.R))
+        self._ck(cpals_mttkrp(self.ctx, n, out))
+        return out
+
+    def get_operator(self, i, n):
+        shape = (self.dims[n], self.R) if i == n else (self.dims[i], self.dims[n], self.R)
+        out = np.empty(shape)
+        self._ck(cpals_get_operator(self.ctx, i, n, out))
+        return out
+
+    def pp_mttkrp(self, n, use_V=True):
+        out = np.empty((self.dims[n], self.R))
+        self._ck(cpals_pp_mttkrp(self.ctx, n, 1 if use_V else 0, out))
+        return out
+
+    def get_state(self, which, n):
+        out = np.empty((self.dims[n], self.R))
+        self._ck(cpals_get_state(self.ctx, {"Ap": 0, "dA": 1}[which], n, out))
+        return out
+
+    def set_profiling(self, enable):
+        self._ck(cpals_set_profiling(self.ctx, 1 if enable else 0))
+
+    def reset_stats(self):
+        self._ck(cpals_reset_stats(self.ctx))
+
+    def get_stats(self, kind=0):
+        st, n, ms, b, f = cpals_get_stats(self.ctx, kind)
+        self._ck(st)
+        return {"launches": n, "total_ms": ms, "bytes": b, "flops": f}
+
+    def set_graphs(self, enable):
+        self._ck(cpals_set_graphs(self.ctx, 1 if enable else 0))
+
+
+def cost_model(dims, R, kind):
+    """Host-only flop model (see cpals_cost_model)."""
+    return cpals_cost_model(dims, len(dims), R, kind)

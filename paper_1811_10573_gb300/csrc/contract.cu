@@ -1,0 +1,390 @@
+// SIMT contraction kernels: first-level contraction (float64/float32 CUDA
+// cores), multi-TTV of the dimension trees, PP first-order correction,
+// Khatri-Rao products and conversions.
+//
+// Paper: Sec. 2.5 (dimension tree: first level as a matrix product, lower
+// levels as batched matrix-vector products sharing r), Sec. 3.2.1 Eq. 3
+// (PP update), Sec. 3.2.3 (operator tree).
+#include <algorithm>
+
+#include "internal.h"
+
+namespace cpals {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------- first level
+// out_part[z][b][m][r] = sum_{k in chunk z} Xv(b,k,m) * B[k][r]
+// Thread (tm, tn) owns rows m = tm + i*THR_M and columns r = tn + j*THR_N
+// (strided, so shared-memory reads are conflict free and stores coalesce).
+template <typename TX, typename T, bool KMAJOR, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__(kThreads)
+gemm_simt_kernel(const TX* __restrict__ X, const T* __restrict__ B, T* __restrict__ out,
+                 int64_t batch, int64_t K, int64_t M, int R, int splits, int64_t kchunk,
+                 int64_t mtiles) {
+  constexpr int THR_N = BN / TN;
+  constexpr int THR_M = BM / TM;
+  static_assert(THR_N * THR_M == kThreads, "thread layout");
+  __shared__ T Xs[BK][BM + 1];
+  __shared__ T Bs[BK][BN];
+
+  const int tid = threadIdx.x;
+  const int tn = tid % THR_N;
+  const int tm = tid / THR_N;
+  const int64_t bid = blockIdx.x;
+  const int64_t mt = bid % mtiles;
+  const int64_t rest = bid / mtiles;
+  const int z = (int)(rest % splits);
+  const int64_t b = rest / splits;
+  const int64_t m0 = mt * BM;
+  const int64_t k0 = (int64_t)z * kchunk;
+  const int64_t k1 = min(K, k0 + kchunk);
+  const TX* Xb = X + b * K * M;
+
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; i++)
+#pragma unroll
+    for (int j = 0; j < TN; j++) acc[i][j] = T(0);
+
+  for (int64_t kk = k0; kk < k1; kk += BK) {
+    if (KMAJOR) {
+      for (int idx = tid; idx < BK * BM; idx += kThreads) {
+        const int k = idx % BK, m = idx / BK;
+        const int64_t gk = kk + k, gm = m0 + m;
+        Xs[k][m] = (gk < k1 && gm < M) ? T(Xb[gm * K + gk]) : T(0);
+      }
+    } else {
+      for (int idx = tid; idx < BK * BM; idx += kThreads) {
+        const int m = idx % BM, k = idx / BM;
+        const int64_t gk = kk + k, gm = m0 + m;
+        Xs[k][m] = (gk < k1 && gm < M) ? T(Xb[gk * M + gm]) : T(0);
+      }
+    }
+    for (int idx = tid; idx < BK * BN; idx += kThreads) {
+      const int r = idx % BN, k = idx / BN;
+      const int64_t gk = kk + k;
+      Bs[k][r] = (gk < k1 && r < R) ? B[gk * R + r] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; k++) {
+      T a[TM], bb[TN];
+#pragma unroll
+      for (int i = 0; i < TM; i++) a[i] = Xs[k][tm + i * THR_M];
+#pragma unroll
+      for (int j = 0; j < TN; j++) bb[j] = Bs[k][tn + j * THR_N];
+#pragma unroll
+      for (int i = 0; i < TM; i++)
+#pragma unroll
+        for (int j = 0; j < TN; j++) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  T* o = out + ((int64_t)z * batch + b) * M * R;
+#pragma unroll
+  for (int i = 0; i < TM; i++) {
+    const int64_t m = m0 + tm + i * THR_M;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; j++) {
+      const int r = tn + j * THR_N;
+      if (r < R) o[m * R + r] = acc[i][j];
+    }
+  }
+}
+
+template <typename T>
+__global__ void reduce_splits_kernel(const T* __restrict__ part, T* __restrict__ out, int64_t n,
+                                     int splits) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T acc = part[i];
+    for (int z = 1; z < splits; z++) acc += part[(int64_t)z * n + i];
+    out[i] = acc;
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  return (int)std::min<int64_t>(cdiv(n, threads), 152 * 16);
+}
+
+template <typename TX, typename T, bool KM, int BM, int BN, int TM, int TN>
+void gemm_launch(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K, int64_t M,
+                 int R, int splits, Launch L) {
+  constexpr int BK = 16;
+  int64_t mtiles = cdiv(M, BM);
+  int64_t kchunk = cdiv(cdiv(K, splits), BK) * BK;
+  splits = (int)cdiv(K, kchunk);
+  T* dst = splits > 1 ? partials : out;
+  int64_t blocks = mtiles * batch * splits;
+  gemm_simt_kernel<TX, T, KM, BM, BN, BK, TM, TN>
+      <<<(unsigned)blocks, kThreads, 0, L.stream>>>(X, B, dst, batch, K, M, R, splits, kchunk,
+                                                     mtiles);
+  (*L.counter)++;
+  if (splits > 1) {
+    int64_t n = batch * M * R;
+    reduce_splits_kernel<T><<<grid_for(n, 256), 256, 0, L.stream>>>(partials, out, n, splits);
+    (*L.counter)++;
+  }
+}
+
+// ---------------------------------------------------------------- multi-TTV
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+ttv_kernel(const T* __restrict__ in, const T* __restrict__ A, T* __restrict__ out, int sw,
+           int64_t QR, int R, int64_t chunks) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t o = blockIdx.x / chunks;
+  const int64_t c = blockIdx.x % chunks;
+  const int64_t f = c * 32 + lane;
+  T acc = T(0);
+  if (f < QR) {
+    const int r = (int)(f % R);
+    const T* base = in + o * sw * QR + f;
+#pragma unroll 4
+    for (int x = w; x < sw; x += 8) acc = fma(base[(int64_t)x * QR], A[(int64_t)x * R + r], acc);
+  }
+  __shared__ T red[8][33];
+  red[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && f < QR) {
+    T s = red[0][lane];
+#pragma unroll
+    for (int i = 1; i < 8; i++) s += red[i][lane];
+    out[o * QR + f] = s;
+  }
+}
+
+// ---------------------------------------------------------------- PP correction
+template <typename T>
+struct PPTermsArg {
+  PPTerm<T> t[kMaxModes];
+  int n;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+pp_correct_kernel(const T* __restrict__ Mp, PPTermsArg<T> terms, T* __restrict__ out,
+                  int64_t total, int R) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t f = (int64_t)blockIdx.x * 32 + lane;
+  T acc = T(0);
+  if (f < total) {
+    const int64_t y = f / R;
+    const int r = (int)(f % R);
+    for (int t = 0; t < terms.n; t++) {
+      const PPTerm<T> tt = terms.t[t];
+      const T* base = tt.op + y * tt.ystride + r;
+#pragma unroll 4
+      for (int x = w; x < tt.sx; x += 8)
+        acc = fma(base[(int64_t)x * tt.xstride], tt.dA[(int64_t)x * R + r], acc);
+    }
+  }
+  __shared__ T red[8][33];
+  red[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && f < total) {
+    T s = red[0][lane];
+#pragma unroll
+    for (int i = 1; i < 8; i++) s += red[i][lane];
+    out[f] = Mp[f] + s;
+  }
+}
+
+// ---------------------------------------------------------------- Khatri-Rao
+template <typename T>
+struct FactorList {
+  const T* A[kMaxModes];
+  int64_t dims[kMaxModes];
+  int n;
+};
+
+template <typename T>
+__global__ void khatri_rao_kernel(FactorList<T> fl, int R, T* __restrict__ out, int64_t rows) {
+  const int64_t n = rows * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i % R);
+    int64_t k = i / R;
+    T v = T(1);
+    for (int j = fl.n - 1; j >= 0; j--) {
+      const int64_t ij = k % fl.dims[j];
+      k /= fl.dims[j];
+      v *= fl.A[j][ij * R + r];
+    }
+    out[i] = v;
+  }
+}
+
+__global__ void khatri_rao_bf16_t_kernel(FactorList<float> fl, int R, int Rpad, int64_t K,
+                                         int64_t Kstride, __nv_bfloat16* __restrict__ outT) {
+  const int64_t n = (int64_t)Rpad * Kstride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / Kstride);
+    const int64_t kk = i % Kstride;
+    float v = 0.f;
+    if (r < R && kk < K) {
+      int64_t k = kk;
+      v = 1.f;
+      for (int j = fl.n - 1; j >= 0; j--) {
+        const int64_t ij = k % fl.dims[j];
+        k /= fl.dims[j];
+        v *= fl.A[j][ij * R + r];
+      }
+    }
+    outT[i] = __float2bfloat16_rn(v);
+  }
+}
+
+template <typename TS, typename TD>
+__global__ void convert_kernel(const TS* __restrict__ s, TD* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = (TD)s[i];
+}
+
+template <>
+__global__ void convert_kernel<float, __nv_bfloat16>(const float* __restrict__ s,
+                                                     __nv_bfloat16* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = __float2bfloat16_rn(s[i]);
+}
+
+template <typename TX>
+__global__ void sumsq_part_kernel(const TX* __restrict__ x, int64_t n, double* __restrict__ part) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)x[i];
+    acc = fma(v, v, acc);
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void sum_parts_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) acc += part[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host wrappers
+template <typename TX, typename T>
+void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K, int64_t M,
+               int R, bool kmajor, int splits, Launch L) {
+  if (splits < 1) splits = 1;
+  if (R <= 32) {
+    if (kmajor) gemm_launch<TX, T, true, 128, 32, 8, 2>(X, B, out, partials, batch, K, M, R, splits, L);
+    else gemm_launch<TX, T, false, 128, 32, 8, 2>(X, B, out, partials, batch, K, M, R, splits, L);
+  } else if (R <= 64) {
+    if (kmajor) gemm_launch<TX, T, true, 64, 64, 4, 4>(X, B, out, partials, batch, K, M, R, splits, L);
+    else gemm_launch<TX, T, false, 64, 64, 4, 4>(X, B, out, partials, batch, K, M, R, splits, L);
+  } else {
+    if (kmajor) gemm_launch<TX, T, true, 64, 128, 4, 8>(X, B, out, partials, batch, K, M, R, splits, L);
+    else gemm_launch<TX, T, false, 64, 128, 4, 8>(X, B, out, partials, batch, K, M, R, splits, L);
+  }
+}
+
+template <typename T>
+void ttv(const T* in, const T* A, T* out, int64_t outer, int sw, int64_t inner, int R, Launch L) {
+  const int64_t QR = inner * R;
+  const int64_t chunks = cdiv(QR, 32);
+  ttv_kernel<T><<<(unsigned)(outer * chunks), kThreads, 0, L.stream>>>(in, A, out, sw, QR, R, chunks);
+  (*L.counter)++;
+}
+
+template <typename T>
+void pp_correct(const T* Mp, const PPTerm<T>* terms, int nterms, T* out, int sy, int R, Launch L) {
+  PPTermsArg<T> a;
+  a.n = nterms;
+  for (int i = 0; i < nterms; i++) a.t[i] = terms[i];
+  const int64_t total = (int64_t)sy * R;
+  pp_correct_kernel<T><<<(unsigned)cdiv(total, 32), kThreads, 0, L.stream>>>(Mp, a, out, total, R);
+  (*L.counter)++;
+}
+
+template <typename T>
+void khatri_rao(const T* const* A, const int64_t* dims, int nm, int R, T* out, Launch L) {
+  FactorList<T> fl;
+  fl.n = nm;
+  int64_t rows = 1;
+  for (int i = 0; i < nm; i++) {
+    fl.A[i] = A[i];
+    fl.dims[i] = dims[i];
+    rows *= dims[i];
+  }
+  khatri_rao_kernel<T><<<grid_for(rows * R, 256), 256, 0, L.stream>>>(fl, R, out, rows);
+  (*L.counter)++;
+}
+
+void khatri_rao_bf16_t(const float* const* A, const int64_t* dims, int nm, int R, int Rpad,
+                       int64_t Kstride, __nv_bfloat16* outT, Launch L) {
+  FactorList<float> fl;
+  fl.n = nm;
+  int64_t K = 1;
+  for (int i = 0; i < nm; i++) {
+    fl.A[i] = A[i];
+    fl.dims[i] = dims[i];
+    K *= dims[i];
+  }
+  khatri_rao_bf16_t_kernel<<<grid_for((int64_t)Rpad * Kstride, 256), 256, 0, L.stream>>>(
+      fl, R, Rpad, K, Kstride, outT);
+  (*L.counter)++;
+}
+
+template <typename TS, typename TD>
+void convert(const TS* src, TD* dst, int64_t n, Launch L) {
+  convert_kernel<TS, TD><<<grid_for(n, 256), 256, 0, L.stream>>>(src, dst, n);
+  (*L.counter)++;
+}
+
+template <typename TX>
+void sumsq(const TX* x, int64_t n, double* partials, double* out, Launch L) {
+  const int blocks = 1024;
+  sumsq_part_kernel<TX><<<blocks, 256, 0, L.stream>>>(x, n, partials);
+  sum_parts_kernel<<<1, 256, 0, L.stream>>>(partials, blocks, out);
+  (*L.counter) += 2;
+}
+
+// ---------------------------------------------------------------- instantiations
+template void gemm_simt<double, double>(const double*, const double*, double*, double*, int64_t,
+                                        int64_t, int64_t, int, bool, int, Launch);
+template void gemm_simt<float, float>(const float*, const float*, float*, float*, int64_t, int64_t,
+                                      int64_t, int, bool, int, Launch);
+template void ttv<double>(const double*, const double*, double*, int64_t, int, int64_t, int, Launch);
+template void ttv<float>(const float*, const float*, float*, int64_t, int, int64_t, int, Launch);
+template void pp_correct<double>(const double*, const PPTerm<double>*, int, double*, int, int, Launch);
+template void pp_correct<float>(const float*, const PPTerm<float>*, int, float*, int, int, Launch);
+template void khatri_rao<double>(const double* const*, const int64_t*, int, int, double*, Launch);
+template void khatri_rao<float>(const float* const*, const int64_t*, int, int, float*, Launch);
+template void convert<double, float>(const double*, float*, int64_t, Launch);
+template void convert<float, double>(const float*, double*, int64_t, Launch);
+template void convert<double, double>(const double*, double*, int64_t, Launch);
+template void convert<float, float>(const float*, float*, int64_t, Launch);
+template void convert<float, __nv_bfloat16>(const float*, __nv_bfloat16*, int64_t, Launch);
+template void sumsq<double>(const double*, int64_t, double*, double*, Launch);
+template void sumsq<float>(const float*, int64_t, double*, double*, Launch);
+
+}  // namespace cpals

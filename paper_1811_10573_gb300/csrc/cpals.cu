@@ -1,0 +1,1087 @@
+// C ABI, context and the host-side plans of the dimension trees.
+//
+// Paper: Algorithm 1 (CP-ALS), Algorithm 3 (PP-CP-ALS), Sec. 2.5 (dimension
+// tree for ALS), Sec. 3.2.3 (dimension tree for the PP operators), Eq. 3 (PP
+// update), Sec. 5 (fitness).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cpals.h"
+#include "internal.h"
+
+using namespace cpals;
+
+namespace {
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+enum GraphSlot { G_ALS = 0, G_PP_V = 1, G_PP_NOV = 2, G_BUILD = 3, G_FIT = 4, G_SLOTS = 5 };
+constexpr int kEvPairs = 16;
+
+}  // namespace
+
+struct cpals_ctx {
+  // problem
+  int N = 0, R = 0, prec = 0;
+  int64_t dims[kMaxModes] = {0};
+  int64_t total = 0;
+  int h = 0;            // left half of the ALS tree: modes [0, h)
+  int64_t PL = 1, PR = 1;
+  int64_t smax = 0;
+  int Rpad = 0;         // R rounded up to the tensor-core N granularity
+  size_t esz = 0;       // bytes per compute-precision element
+
+  // streams and errors
+  cudaStream_t stream = nullptr;
+  cudaStream_t user = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::string err;
+
+  // tensor
+  void* X = nullptr;                 // float64 (FP64) or float32 (FP32, MIXED)
+  __nv_bfloat16* Xb = nullptr;       // MIXED: bf16 copy
+  double normX2 = 0.0;
+  bool have_tensor = false, have_factors = false;
+
+  // factors (float64 master copies) and compute-precision copies
+  double* A[kMaxModes] = {nullptr};
+  double* Ap[kMaxModes] = {nullptr};
+  double* dA[kMaxModes] = {nullptr};
+  void* Ac[kMaxModes] = {nullptr};
+  void* dAc[kMaxModes] = {nullptr};
+  double* S = nullptr;   // N*R*R
+  double* W = nullptr;   // N*R*R
+  double* Lf = nullptr;  // R*R
+  double* Z = nullptr;   // R*R
+
+  // workspaces (compute precision unless noted)
+  void* ML = nullptr;    // PL x R
+  void* MR = nullptr;    // PR x R
+  void* krp = nullptr;   // max(PL, PR) x R
+  void* tmp[2] = {nullptr, nullptr};
+  void* rhs = nullptr;   // smax x R
+  double* rhs2 = nullptr;  // smax x R float64
+  void* gpart = nullptr;   // split-K partials
+  size_t gpart_bytes = 0;
+  __nv_bfloat16* Bt = nullptr;   // MIXED: transposed bf16 B operand
+  size_t Bt_elems = 0;
+  double* rownorm = nullptr;     // 2*smax
+  double* dpart = nullptr;       // float64 partials (Grams, fitness, norms)
+  double* scal = nullptr;        // device scalars
+  double* scal_h = nullptr;      // pinned mirror
+  int* status = nullptr;         // device status words
+  int* status_h = nullptr;
+
+  // PP operators
+  bool pp_alloc = false, ops_built = false;
+  void* ops[kMaxModes][kMaxModes] = {{nullptr}};
+  void* Mp[kMaxModes] = {nullptr};
+  std::vector<void*> lvl_bufs;                 // intermediate levels (freed with ctx)
+  void* lvl[kMaxModes][kMaxModes][kMaxModes] = {{{nullptr}}};  // [l][i][j]
+
+  // graphs, stats
+  bool graphs = true;
+  cudaGraphExec_t gexec[G_SLOTS] = {nullptr};
+  int64_t gcount[G_SLOTS] = {0};
+  int gev[G_SLOTS] = {0};
+  bool profiling = false;
+  cudaEvent_t ev0[kEvPairs] = {nullptr}, ev1[kEvPairs] = {nullptr};
+  double ev_bytes[kEvPairs] = {0}, ev_flops[kEvPairs] = {0};
+  double gev_bytes[G_SLOTS][kEvPairs] = {{0}}, gev_flops[G_SLOTS][kEvPairs] = {{0}};
+  int ev_used = 0;
+  int64_t launches = 0;
+  int64_t fl_launches = 0;
+  double fl_ms = 0, fl_bytes = 0, fl_flops = 0;
+  int* umma_err = nullptr;
+
+  Launch L() { return Launch{stream, &launches}; }
+
+  cpals_status fail(cpals_status st, const std::string& msg) {
+    err = msg;
+    return st;
+  }
+  cpals_status cuda_fail(const char* what, cudaError_t e) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return CPALS_E_CUDA;
+  }
+};
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return c->cuda_fail(#call, e_);    \
+  } while (0)
+
+#define CKS(expr)                                \
+  do {                                           \
+    cpals_status s_ = (expr);                    \
+    if (s_ != CPALS_OK) return s_;               \
+  } while (0)
+
+namespace {
+
+template <typename T>
+T* P(void* p) {
+  return static_cast<T*>(p);
+}
+
+cpals_status dalloc(cpals_ctx* c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return c->fail(CPALS_E_OOM, std::string("cudaMalloc(") + std::to_string(bytes) +
+                                    "): " + cudaGetErrorString(e));
+  }
+  return CPALS_OK;
+}
+
+// ---------------------------------------------------------------- stream join
+struct Join {
+  cpals_ctx* c;
+  explicit Join(cpals_ctx* cc) : c(cc) {
+    cudaEventRecord(c->ev_in, c->user);
+    cudaStreamWaitEvent(c->stream, c->ev_in, 0);
+  }
+  ~Join() {
+    cudaEventRecord(c->ev_out, c->stream);
+    cudaStreamWaitEvent(c->user, c->ev_out, 0);
+  }
+};
+
+// ---------------------------------------------------------------- profiling
+void ev_begin(cpals_ctx* c, int idx) {
+  if (c->profiling && idx < kEvPairs)
+    cudaEventRecordWithFlags(c->ev0[idx], c->stream, cudaEventRecordExternal);
+}
+void ev_end(cpals_ctx* c, int idx, double bytes, double flops) {
+  if (c->profiling && idx < kEvPairs) {
+    cudaEventRecordWithFlags(c->ev1[idx], c->stream, cudaEventRecordExternal);
+    c->ev_bytes[idx] = bytes;
+    c->ev_flops[idx] = flops;
+  }
+}
+// after the stream is synchronised: accumulate the recorded pairs
+void ev_harvest(cpals_ctx* c) {
+  if (!c->profiling) {
+    c->ev_used = 0;
+    return;
+  }
+  for (int i = 0; i < c->ev_used && i < kEvPairs; i++) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev0[i], c->ev1[i]) == cudaSuccess) {
+      c->fl_ms += ms;
+      c->fl_launches++;
+      c->fl_bytes += c->ev_bytes[i];
+      c->fl_flops += c->ev_flops[i];
+    } else {
+      cudaGetLastError();
+    }
+  }
+  c->ev_used = 0;
+}
+
+// ---------------------------------------------------------------- first-level contraction
+// out = X contracted over the modes kmodes (contiguous block of modes) with
+// their factors' Khatri-Rao product (Sec. 2.5; Sec. 3.2.3 level 2).
+// kmajor: the contracted modes are the trailing ones (out is M x R, M = the rest);
+// else out[b][m][r] with b = modes before, m = modes after the contracted block.
+template <typename T>
+cpals_status contract_first(cpals_ctx* c, int k0, int nk, void* const* facs, T* out,
+                            int64_t batch, int64_t K, int64_t M, bool kmajor) {
+  const int R = c->R;
+  const bool tc = c->prec == CPALS_MIXED_BF16 && umma_supported(K, M, kmajor, R);
+  const size_t xsz = c->prec == CPALS_FP64 ? 8 : (tc ? 2 : 4);
+  // algorithmic bytes: read X once, read B once, write the output once
+  const double bytes = (double)batch * K * M * xsz + (double)batch * M * R * sizeof(T) +
+                       (double)K * R * (tc ? 2 : sizeof(T));
+  const double flops = 2.0 * batch * K * M * R;
+  const int idx = c->ev_used++;
+  // split K when the output alone does not fill the GPU
+  const int64_t mtiles = cdiv(M, 128) * batch;
+  int splits = 1;
+  if (mtiles < 2 * 152) splits = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(2 * 152, mtiles), cdiv(K, 256)));
+  while (splits > 1 && (size_t)splits * batch * M * R * sizeof(T) > c->gpart_bytes) splits--;
+
+  if (tc) {
+    const float* fl[kMaxModes];
+    for (int i = 0; i < nk; i++) fl[i] = P<const float>(facs[k0 + i]);
+    const int64_t Kstride = cdiv(K, 8) * 8;
+    khatri_rao_bf16_t(fl, c->dims + k0, nk, R, c->Rpad, Kstride, c->Bt, c->L());
+    ev_begin(c, idx);
+    CK(umma_gemm_bf16(c->Xb, c->Bt, P<float>(out), P<float>(c->gpart), batch, K, M, R, c->Rpad,
+                      Kstride, kmajor, splits, c->umma_err, c->L()));
+    ev_end(c, idx, bytes, flops);
+    return CPALS_OK;
+  }
+  const T* B;
+  if (nk == 1) {
+    B = P<const T>(facs[k0]);
+  } else {
+    const T* fl[kMaxModes];
+    for (int i = 0; i < nk; i++) fl[i] = P<const T>(facs[k0 + i]);
+    khatri_rao<T>(fl, c->dims + k0, nk, R, P<T>(c->krp), c->L());
+    B = P<const T>(c->krp);
+  }
+  ev_begin(c, idx);
+  gemm_simt<T, T>(P<const T>(c->X), B, out, P<T>(c->gpart), batch, K, M, R, kmajor, splits, c->L());
+  ev_end(c, idx, bytes, flops);
+  return CPALS_OK;
+}
+
+// Contract every mode of an intermediate except `keep` (multi-TTV chain,
+// Sec. 2.5 lower levels).  in has modes `modes` (ascending) then r.
+template <typename T>
+const T* contract_chain(cpals_ctx* c, const T* in, std::vector<int> modes, int keep,
+                        void* const* facs, T* final_out) {
+  const T* cur = in;
+  int ping = 0;
+  while (modes.size() > 1) {
+    int pos = (int)modes.size() - 1;
+    if (modes[pos] == keep) pos--;
+    const int w = modes[pos];
+    int64_t outer = 1, inner = 1;
+    for (int i = 0; i < pos; i++) outer *= c->dims[modes[i]];
+    for (int i = pos + 1; i < (int)modes.size(); i++) inner *= c->dims[modes[i]];
+    T* dst = modes.size() == 2 ? final_out : P<T>(c->tmp[ping]);
+    ttv<T>(cur, P<const T>(facs[w]), dst, outer, (int)c->dims[w], inner, c->R, c->L());
+    cur = dst;
+    ping ^= 1;
+    modes.erase(modes.begin() + pos);
+  }
+  return cur;
+}
+
+// Normal-equation update of mode n from right-hand side rhs (Algorithm 1
+// lines 5-10; Algorithm 3 lines 11-17 when pp).
+template <typename T>
+void update_mode(cpals_ctx* c, int n, const T* rhs, bool pp, bool useV) {
+  const int R = c->R;
+  const int s = (int)c->dims[n];
+  const bool v = pp && useV;
+  gamma_chol(c->S, c->W, c->N, n, R, c->Lf, c->Z, v, c->status, c->L());
+  if (v)
+    solve_rows_v<T>(rhs, c->A[n], c->Ap[n], c->dA[n], c->Lf, c->Z, c->rhs2, P<T>(c->Ac[n]),
+                    P<T>(c->dAc[n]), c->rownorm, s, R, n, c->status, c->L());
+  else
+    solve_rows<T>(rhs, c->A[n], pp ? c->Ap[n] : nullptr, c->dA[n], c->Lf, P<T>(c->Ac[n]),
+                  P<T>(c->dAc[n]), c->rownorm, s, R, n, c->status, c->L());
+  gram_update(c->A[n], c->dA[n], c->S + (int64_t)n * R * R, c->W + (int64_t)n * R * R, pp, s, R,
+              c->rownorm, c->scal + 8 + 2 * n, c->dpart, c->L());
+}
+
+// ---------------------------------------------------------------- ALS sweep
+template <typename T>
+cpals_status als_sweep_launch(cpals_ctx* c) {
+  const int N = c->N, h = c->h, R = c->R;
+  std::vector<int> Lm, Rm;
+  for (int k = 0; k < h; k++) Lm.push_back(k);
+  for (int k = h; k < N; k++) Rm.push_back(k);
+  // left half: M^(L) = X_(L) (A^(h) (.) ... (.) A^(N-1))
+  CKS(contract_first<T>(c, h, N - h, c->Ac, P<T>(c->ML), 1, c->PR, c->PL, true));
+  for (int n = 0; n < h; n++) {
+    const T* rhs = contract_chain<T>(c, P<const T>(c->ML), Lm, n, c->Ac, P<T>(c->rhs));
+    update_mode<T>(c, n, rhs, false, false);
+  }
+  // right half with the updated left factors: M^(Rt) = X_(L)^T (A^(0) (.) ... (.) A^(h-1))
+  CKS(contract_first<T>(c, 0, h, c->Ac, P<T>(c->MR), 1, c->PL, c->PR, false));
+  const T* last = nullptr;
+  for (int n = h; n < N; n++) {
+    last = contract_chain<T>(c, P<const T>(c->MR), Rm, n, c->Ac, P<T>(c->rhs));
+    update_mode<T>(c, n, last, false, false);
+  }
+  fitness<T>(last, c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->normX2, c->scal, c->dpart,
+             c->L());
+  return CPALS_OK;
+}
+
+// exact M^(n) at the current factors into a buffer; returns the pointer
+template <typename T>
+cpals_status mttkrp_launch(cpals_ctx* c, int n, const T** result) {
+  const int N = c->N, h = c->h;
+  std::vector<int> modes;
+  if (n < h) {
+    for (int k = 0; k < h; k++) modes.push_back(k);
+    CKS(contract_first<T>(c, h, N - h, c->Ac, P<T>(c->ML), 1, c->PR, c->PL, true));
+    *result = contract_chain<T>(c, P<const T>(c->ML), modes, n, c->Ac, P<T>(c->rhs));
+  } else {
+    for (int k = h; k < N; k++) modes.push_back(k);
+    CKS(contract_first<T>(c, 0, h, c->Ac, P<T>(c->MR), 1, c->PL, c->PR, false));
+    *result = contract_chain<T>(c, P<const T>(c->MR), modes, n, c->Ac, P<T>(c->rhs));
+  }
+  return CPALS_OK;
+}
+
+template <typename T>
+cpals_status fitness_launch(cpals_ctx* c) {
+  const T* last = nullptr;
+  CKS(mttkrp_launch<T>(c, c->N - 1, &last));
+  fitness<T>(last, c->A[c->N - 1], c->S, c->N, c->R, (int)c->dims[c->N - 1], c->normX2, c->scal,
+             c->dpart, c->L());
+  return CPALS_OK;
+}
+
+// ---------------------------------------------------------------- PP operators
+// Level-l tensors hold modes {i, j} U {l+1, ..., N-1} (0-based), i < j <= l
+// (Sec. 3.2.3).  Level 1 is X itself.
+std::vector<int> level_modes(int N, int l, int i, int j) {
+  std::vector<int> m = {i, j};
+  for (int k = l + 1; k < N; k++) m.push_back(k);
+  return m;
+}
+
+// parent of (i,j) at level l (a tensor at level l-1) and the mode contracted
+void tree_parent(int l, int i, int j, int* pi, int* pj, int* w) {
+  if (j <= l - 1) {
+    *pi = i; *pj = j; *w = l;
+  } else if (i < l - 1) {
+    *pi = i; *pj = l - 1; *w = l - 1;
+  } else {
+    *pi = l - 2; *pj = l - 1; *w = l - 2;
+  }
+}
+
+template <typename T>
+cpals_status pp_alloc(cpals_ctx* c) {
+  if (c->pp_alloc) return CPALS_OK;
+  const int N = c->N, R = c->R;
+  for (int i = 0; i < N; i++)
+    for (int n = i + 1; n < N; n++)
+      CKS(dalloc(c, &c->ops[i][n], (size_t)c->dims[i] * c->dims[n] * R * sizeof(T)));
+  for (int n = 0; n < N; n++) CKS(dalloc(c, &c->Mp[n], (size_t)c->dims[n] * R * sizeof(T)));
+  for (int l = 2; l <= N - 2; l++)
+    for (int i = 0; i <= l; i++)
+      for (int j = i + 1; j <= l; j++) {
+        int64_t sz = R;
+        for (int m : level_modes(N, l, i, j)) sz *= c->dims[m];
+        void* p = nullptr;
+        CKS(dalloc(c, &p, (size_t)sz * sizeof(T)));
+        c->lvl_bufs.push_back(p);
+        c->lvl[l][i][j] = p;
+      }
+  c->pp_alloc = true;
+  return CPALS_OK;
+}
+
+template <typename T>
+cpals_status pp_build_launch(cpals_ctx* c) {
+  const int N = c->N, R = c->R;
+  // level 2: three first-level contractions of X (modes 2, 1, 0)
+  for (int w = 2; w >= 0; w--) {
+    int i, j;
+    if (w == 2) { i = 0; j = 1; } else if (w == 1) { i = 0; j = 2; } else { i = 1; j = 2; }
+    T* dst = P<T>(N == 3 ? c->ops[i][j] : c->lvl[2][i][j]);
+    int64_t batch = 1, M = 1;
+    for (int k = 0; k < w; k++) batch *= c->dims[k];
+    for (int k = w + 1; k < N; k++) M *= c->dims[k];
+    const bool kmajor = (w == N - 1);
+    if (kmajor) { M = batch; batch = 1; }
+    CKS(contract_first<T>(c, w, 1, c->Ac, dst, batch, c->dims[w], M, kmajor));
+  }
+  // levels 3 .. N-1: one multi-TTV per child
+  for (int l = 3; l <= N - 1; l++) {
+    for (int i = 0; i <= l; i++)
+      for (int j = i + 1; j <= l; j++) {
+        int pi, pj, w;
+        tree_parent(l, i, j, &pi, &pj, &w);
+        const std::vector<int> pm = level_modes(N, l - 1, pi, pj);
+        int pos = 0;
+        while (pm[pos] != w) pos++;
+        int64_t outer = 1, inner = 1;
+        for (int k = 0; k < pos; k++) outer *= c->dims[pm[k]];
+        for (int k = pos + 1; k < (int)pm.size(); k++) inner *= c->dims[pm[k]];
+        const T* src = P<const T>(c->lvl[l - 1][pi][pj]);
+        T* dst = P<T>(l == N - 1 ? c->ops[i][j] : c->lvl[l][i][j]);
+        ttv<T>(src, P<const T>(c->Ac[w]), dst, outer, (int)c->dims[w], inner, R, c->L());
+      }
+  }
+  // M_p^(n) from a leaf (Sec. 3.2.3: contract M_p^(i,n) with A_p^(i))
+  for (int n = 0; n < N; n++) {
+    if (n == 0)
+      ttv<T>(P<const T>(c->ops[0][1]), P<const T>(c->Ac[1]), P<T>(c->Mp[0]), c->dims[0],
+             (int)c->dims[1], 1, R, c->L());
+    else
+      ttv<T>(P<const T>(c->ops[0][n]), P<const T>(c->Ac[0]), P<T>(c->Mp[n]), 1, (int)c->dims[0],
+             c->dims[n], R, c->L());
+  }
+  // A_p <- A, dA <- 0 (Algorithm 3, line 7)
+  for (int n = 0; n < N; n++) {
+    const size_t sR = (size_t)c->dims[n] * R;
+    CK(cudaMemcpyAsync(c->Ap[n], c->A[n], sR * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemsetAsync(c->dA[n], 0, sR * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(c->dAc[n], 0, sR * c->esz, c->stream));
+  }
+  CK(cudaMemsetAsync(c->W, 0, (size_t)N * R * R * sizeof(double), c->stream));
+  // ||dA^(n)||^2 <- 0; ||A^(n)||^2 is unchanged
+  for (int n = 0; n < N; n++)
+    CK(cudaMemsetAsync(c->scal + 8 + 2 * n, 0, sizeof(double), c->stream));
+  return CPALS_OK;
+}
+
+// ---------------------------------------------------------------- PP sweep
+template <typename T>
+void pp_terms(cpals_ctx* c, int n, PPTerm<T>* terms) {
+  const int N = c->N, R = c->R;
+  int t = 0;
+  for (int i = 0; i < N; i++) {
+    if (i == n) continue;
+    PPTerm<T> tt;
+    tt.dA = P<const T>(c->dAc[i]);
+    tt.sx = (int)c->dims[i];
+    if (i < n) {        // M_p^(i,n)(x, y, r)
+      tt.op = P<const T>(c->ops[i][n]);
+      tt.xstride = c->dims[n] * R;
+      tt.ystride = R;
+    } else {            // M_p^(n,i)(y, x, r)
+      tt.op = P<const T>(c->ops[n][i]);
+      tt.xstride = R;
+      tt.ystride = c->dims[i] * R;
+    }
+    terms[t++] = tt;
+  }
+}
+
+template <typename T>
+cpals_status pp_sweep_launch(cpals_ctx* c, bool useV) {
+  const int N = c->N, R = c->R;
+  PPTerm<T> terms[kMaxModes];
+  for (int n = 0; n < N; n++) {
+    pp_terms<T>(c, n, terms);
+    pp_correct<T>(P<const T>(c->Mp[n]), terms, N - 1, P<T>(c->rhs), (int)c->dims[n], R, c->L());
+    update_mode<T>(c, n, P<const T>(c->rhs), true, useV);
+  }
+  // fitness estimate from M~^(N) (the last right-hand side, updated factors)
+  fitness<T>(P<const T>(c->rhs), c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->normX2,
+             c->scal, c->dpart, c->L());
+  return CPALS_OK;
+}
+
+// ---------------------------------------------------------------- dispatch helpers
+template <typename F>
+cpals_status run_slot(cpals_ctx* c, int slot, F&& body) {
+  if (!c->graphs) {
+    c->ev_used = 0;
+    return body();
+  }
+  if (!c->gexec[slot]) {
+    cudaGraph_t g = nullptr;
+    const int64_t before = c->launches;
+    c->ev_used = 0;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cpals_status st = body();
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (st != CPALS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return c->cuda_fail("cudaStreamEndCapture", e);
+    e = cudaGraphInstantiate(&c->gexec[slot], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->gexec[slot] = nullptr;
+      return c->cuda_fail("cudaGraphInstantiate", e);
+    }
+    c->gcount[slot] = c->launches - before;
+    c->gev[slot] = c->ev_used;
+    for (int i = 0; i < kEvPairs; i++) {
+      c->gev_bytes[slot][i] = c->ev_bytes[i];
+      c->gev_flops[slot][i] = c->ev_flops[i];
+    }
+    c->launches = before;
+  }
+  CK(cudaGraphLaunch(c->gexec[slot], c->stream));
+  c->launches += c->gcount[slot];
+  c->ev_used = c->gev[slot];
+  for (int i = 0; i < kEvPairs; i++) {
+    c->ev_bytes[i] = c->gev_bytes[slot][i];
+    c->ev_flops[i] = c->gev_flops[slot][i];
+  }
+  return CPALS_OK;
+}
+
+void drop_graphs(cpals_ctx* c) {
+  for (int i = 0; i < G_SLOTS; i++)
+    if (c->gexec[i]) {
+      cudaGraphExecDestroy(c->gexec[i]);
+      c->gexec[i] = nullptr;
+    }
+}
+
+cpals_status sync_read(cpals_ctx* c) {
+  CK(cudaMemcpyAsync(c->scal_h, c->scal, sizeof(double) * 32, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->status_h, c->status, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  ev_harvest(c);
+  if (c->status_h[1])
+    return c->fail(CPALS_E_TIMEOUT, "tensor-core contraction: a bounded wait gave up (code " +
+                                        std::to_string(c->status_h[1]) + ")");
+  return CPALS_OK;
+}
+
+cpals_status check_status(cpals_ctx* c) {
+  if (c->status_h[0]) {
+    const int bits = c->status_h[0];
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->stream));
+    return c->fail(CPALS_E_SINGULAR, "Gamma not positive definite for mode mask " + std::to_string(bits) +
+                                         "; those factors were left unchanged");
+  }
+  for (int n = 0; n < c->N; n++)
+    if (!std::isfinite(c->scal_h[8 + 2 * n]) || !std::isfinite(c->scal_h[9 + 2 * n]))
+      return c->fail(CPALS_E_NUMERIC, "non-finite factor in mode " + std::to_string(n));
+  return CPALS_OK;
+}
+
+bool is64(const cpals_ctx* c) { return c->prec == CPALS_FP64; }
+
+cpals_status ready(cpals_ctx* c) {
+  if (!c) return CPALS_E_INVALID;
+  if (!c->have_tensor) return c->fail(CPALS_E_STATE, "no tensor: call cpals_set_tensor first");
+  if (!c->have_factors) return c->fail(CPALS_E_STATE, "no factors: call cpals_init_factors first");
+  return CPALS_OK;
+}
+
+template <typename T>
+cpals_status copy_out(cpals_ctx* c, const T* src, int64_t n, double* out) {
+  if (sizeof(T) == 8) {
+    CK(cudaMemcpyAsync(out, src, n * 8, cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    std::vector<float> tmp(n);
+    CK(cudaMemcpyAsync(tmp.data(), src, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int64_t i = 0; i < n; i++) out[i] = tmp[i];
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return CPALS_OK;
+}
+
+cpals_status do_als(cpals_ctx* c) {
+  return run_slot(c, G_ALS, [&]() { return is64(c) ? als_sweep_launch<double>(c) : als_sweep_launch<float>(c); });
+}
+cpals_status do_build(cpals_ctx* c) {
+  CKS(is64(c) ? pp_alloc<double>(c) : pp_alloc<float>(c));
+  return run_slot(c, G_BUILD, [&]() { return is64(c) ? pp_build_launch<double>(c) : pp_build_launch<float>(c); });
+}
+cpals_status do_pp(cpals_ctx* c, bool useV) {
+  return run_slot(c, useV ? G_PP_V : G_PP_NOV,
+                  [&]() { return is64(c) ? pp_sweep_launch<double>(c, useV) : pp_sweep_launch<float>(c, useV); });
+}
+cpals_status do_fit(cpals_ctx* c) {
+  return run_slot(c, G_FIT, [&]() { return is64(c) ? fitness_launch<double>(c) : fitness_launch<float>(c); });
+}
+
+bool all_small(const cpals_ctx* c, double eps) {
+  for (int n = 0; n < c->N; n++) {
+    const double d = std::sqrt(c->scal_h[8 + 2 * n]), a = std::sqrt(c->scal_h[9 + 2 * n]);
+    if (!(d < eps * a)) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpals_ctx** out) {
+  if (!out) return CPALS_E_INVALID;
+  *out = nullptr;
+  if (!dims || N < 3 || N > kMaxModes || R < 1 || R > kMaxRank) return CPALS_E_INVALID;
+  if (precision < CPALS_FP64 || precision > CPALS_MIXED_BF16) return CPALS_E_INVALID;
+  for (int i = 0; i < N; i++)
+    if (dims[i] < 1 || dims[i] > (1 << 30)) return CPALS_E_INVALID;
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return CPALS_E_CUDA;
+  }
+  if (!(prop.major == 10 && prop.minor == 3)) return CPALS_E_UNSUPPORTED;
+
+  cpals_ctx* c = new cpals_ctx();
+  c->N = N;
+  c->R = R;
+  c->prec = precision;
+  c->total = 1;
+  for (int i = 0; i < N; i++) {
+    c->dims[i] = dims[i];
+    c->total *= dims[i];
+    c->smax = std::max<int64_t>(c->smax, dims[i]);
+  }
+  c->h = (N + 1) / 2;
+  for (int i = 0; i < c->h; i++) c->PL *= dims[i];
+  for (int i = c->h; i < N; i++) c->PR *= dims[i];
+  c->Rpad = (int)cdiv(R, 16) * 16;
+  c->esz = precision == CPALS_FP64 ? 8 : 4;
+  const size_t esz = c->esz;
+
+  auto bail = [&](cpals_status st) {
+    cpals_destroy(c);
+    return st;
+  };
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return bail(CPALS_E_CUDA);
+  for (int i = 0; i < kEvPairs; i++)
+    if (cudaEventCreate(&c->ev0[i]) != cudaSuccess || cudaEventCreate(&c->ev1[i]) != cudaSuccess)
+      return bail(CPALS_E_CUDA);
+  if (setup_small_kernels() != cudaSuccess) return bail(CPALS_E_CUDA);
+  if (precision == CPALS_MIXED_BF16 && setup_umma_kernels() != cudaSuccess) return bail(CPALS_E_CUDA);
+
+  cpals_status st = CPALS_OK;
+#define AL(ptr, bytes)                                    \
+  do {                                                    \
+    void* p_ = nullptr;                                   \
+    st = dalloc(c, &p_, (bytes));                         \
+    if (st != CPALS_OK) return bail(st);                  \
+    ptr = decltype(ptr)(p_);                              \
+  } while (0)
+  AL(c->X, (size_t)c->total * (precision == CPALS_FP64 ? 8 : 4));
+  if (precision == CPALS_MIXED_BF16) AL(c->Xb, (size_t)c->total * 2);
+  for (int n = 0; n < N; n++) {
+    const size_t sR = (size_t)dims[n] * R;
+    AL(c->A[n], sR * 8);
+    AL(c->Ap[n], sR * 8);
+    AL(c->dA[n], sR * 8);
+    AL(c->Ac[n], sR * esz);
+    AL(c->dAc[n], sR * esz);
+  }
+  AL(c->S, (size_t)N * R * R * 8);
+  AL(c->W, (size_t)N * R * R * 8);
+  AL(c->Lf, (size_t)R * R * 8);
+  AL(c->Z, (size_t)R * R * 8);
+  const int64_t Pmax = std::max(c->PL, c->PR);
+  AL(c->ML, (size_t)c->PL * R * esz);
+  AL(c->MR, (size_t)c->PR * R * esz);
+  AL(c->krp, (size_t)Pmax * R * esz);
+  AL(c->tmp[0], (size_t)Pmax * R * esz);
+  AL(c->tmp[1], (size_t)Pmax * R * esz);
+  AL(c->rhs, (size_t)c->smax * R * esz);
+  AL(c->rhs2, (size_t)c->smax * R * 8);
+  // split-K partials: enough for 2*152 tiles' worth of outputs of 128 rows
+  c->gpart_bytes = std::max<size_t>((size_t)2 * 152 * 128 * R * esz, (size_t)4 * c->smax * R * esz);
+  c->gpart_bytes = std::max<size_t>(c->gpart_bytes, (size_t)8 * std::min(c->PL, c->PR) * R * esz);
+  AL(c->gpart, c->gpart_bytes);
+  if (precision == CPALS_MIXED_BF16) {
+    c->Bt_elems = (size_t)c->Rpad * (size_t)(cdiv(Pmax, 8) * 8);
+    AL(c->Bt, c->Bt_elems * 2);
+  }
+  AL(c->rownorm, (size_t)2 * c->smax * 8);
+  AL(c->dpart, (size_t)(2 * 152 + 64) * 1024 * 8);
+  AL(c->scal, 64 * 8);
+  AL(c->status, 4 * sizeof(int));
+  c->umma_err = c->status + 1;
+#undef AL
+  if (cudaMallocHost((void**)&c->scal_h, 64 * 8) != cudaSuccess ||
+      cudaMallocHost((void**)&c->status_h, 4 * sizeof(int)) != cudaSuccess)
+    return bail(CPALS_E_OOM);
+  if (cudaMemset(c->scal, 0, 64 * 8) != cudaSuccess || cudaMemset(c->status, 0, 16) != cudaSuccess ||
+      cudaMemset(c->W, 0, (size_t)N * R * R * 8) != cudaSuccess)
+    return bail(CPALS_E_CUDA);
+  memset(c->scal_h, 0, 64 * 8);
+  *out = c;
+  return CPALS_OK;
+}
+
+void cpals_destroy(cpals_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  auto F = [](void* p) {
+    if (p) cudaFree(p);
+  };
+  F(c->X);
+  F(c->Xb);
+  for (int n = 0; n < kMaxModes; n++) {
+    F(c->A[n]); F(c->Ap[n]); F(c->dA[n]); F(c->Ac[n]); F(c->dAc[n]); F(c->Mp[n]);
+    for (int m = 0; m < kMaxModes; m++) F(c->ops[n][m]);
+  }
+  for (void* p : c->lvl_bufs) F(p);
+  F(c->S); F(c->W); F(c->Lf); F(c->Z); F(c->ML); F(c->MR); F(c->krp); F(c->tmp[0]); F(c->tmp[1]);
+  F(c->rhs); F(c->rhs2); F(c->gpart); F(c->Bt); F(c->rownorm); F(c->dpart); F(c->scal);
+  F(c->status);
+  if (c->scal_h) cudaFreeHost(c->scal_h);
+  if (c->status_h) cudaFreeHost(c->status_h);
+  for (int i = 0; i < kEvPairs; i++) {
+    if (c->ev0[i]) cudaEventDestroy(c->ev0[i]);
+    if (c->ev1[i]) cudaEventDestroy(c->ev1[i]);
+  }
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+cpals_status cpals_set_stream(cpals_ctx* c, void* stream) {
+  if (!c) return CPALS_E_INVALID;
+  c->user = (cudaStream_t)stream;
+  return CPALS_OK;
+}
+
+const char* cpals_last_error(const cpals_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+cpals_status cpals_set_tensor(cpals_ctx* c, const void* data, int dtype, int on_device) {
+  if (!c || !data || (dtype != 0 && dtype != 1)) return c ? c->fail(CPALS_E_INVALID, "bad tensor argument") : CPALS_E_INVALID;
+  Join j(c);
+  const int64_t n = c->total;
+  const size_t insz = dtype == 0 ? 8 : 4;
+  const bool store64 = c->prec == CPALS_FP64;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if ((dtype == 0) == store64) {
+    CK(cudaMemcpyAsync(c->X, data, n * insz, kind, c->stream));
+  } else {
+    void* tmp = nullptr;
+    CKS(dalloc(c, &tmp, n * insz));
+    cudaError_t e = cudaMemcpyAsync(tmp, data, n * insz, kind, c->stream);
+    if (e == cudaSuccess) {
+      if (dtype == 0) convert<double, float>((const double*)tmp, (float*)c->X, n, c->L());
+      else convert<float, double>((const float*)tmp, (double*)c->X, n, c->L());
+      e = cudaStreamSynchronize(c->stream);
+    }
+    cudaFree(tmp);
+    if (e != cudaSuccess) return c->cuda_fail("set_tensor copy", e);
+  }
+  if (c->prec == CPALS_MIXED_BF16) convert<float, __nv_bfloat16>((const float*)c->X, c->Xb, n, c->L());
+  if (store64) sumsq<double>((const double*)c->X, n, c->dpart, c->scal + 40, c->L());
+  else sumsq<float>((const float*)c->X, n, c->dpart, c->scal + 40, c->L());
+  double nx = 0;
+  CK(cudaMemcpyAsync(&nx, c->scal + 40, 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  c->normX2 = nx;
+  c->have_tensor = true;
+  c->ops_built = false;
+  drop_graphs(c);   // normX2 is baked into the captured fitness kernels
+  return CPALS_OK;
+}
+
+cpals_status cpals_init_factors(cpals_ctx* c, const double* const* factors) {
+  if (!c || !factors) return c ? c->fail(CPALS_E_INVALID, "factors is NULL") : CPALS_E_INVALID;
+  for (int n = 0; n < c->N; n++)
+    if (!factors[n]) return c->fail(CPALS_E_INVALID, "factor pointer is NULL");
+  Join j(c);
+  const int R = c->R;
+  CK(cudaMemsetAsync(c->status, 0, 16, c->stream));
+  for (int n = 0; n < c->N; n++) {
+    const int64_t sR = c->dims[n] * R;
+    CK(cudaMemcpyAsync(c->A[n], factors[n], sR * 8, cudaMemcpyHostToDevice, c->stream));
+    // Algorithm 3 line 2: dA <- A, S <- A^T A
+    CK(cudaMemcpyAsync(c->dA[n], c->A[n], sR * 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (is64(c)) {
+      convert<double, double>(c->A[n], P<double>(c->Ac[n]), sR, c->L());
+      convert<double, double>(c->A[n], P<double>(c->dAc[n]), sR, c->L());
+    } else {
+      convert<double, float>(c->A[n], P<float>(c->Ac[n]), sR, c->L());
+      convert<double, float>(c->A[n], P<float>(c->dAc[n]), sR, c->L());
+    }
+    sumsq<double>(c->A[n], sR, c->dpart, c->scal + 8 + 2 * n, c->L());
+    CK(cudaMemcpyAsync(c->scal + 9 + 2 * n, c->scal + 8 + 2 * n, 8, cudaMemcpyDeviceToDevice, c->stream));
+    // rownorm is not needed: gram_update reduces it into a scratch slot
+    CK(cudaMemsetAsync(c->rownorm, 0, 2 * c->dims[n] * 8, c->stream));
+    gram_update(c->A[n], c->dA[n], c->S + (int64_t)n * R * R, c->W + (int64_t)n * R * R, false,
+                (int)c->dims[n], R, c->rownorm, c->scal + 48, c->dpart, c->L());
+  }
+  CK(cudaMemsetAsync(c->W, 0, (size_t)c->N * R * R * 8, c->stream));
+  CKS(sync_read(c));
+  c->have_factors = true;
+  c->ops_built = false;
+  return CPALS_OK;
+}
+
+cpals_status cpals_als_sweep(cpals_ctx* c, double* fitness_out) {
+  CKS(ready(c));
+  Join j(c);
+  CKS(do_als(c));
+  CKS(sync_read(c));
+  if (fitness_out) *fitness_out = c->scal_h[0];
+  return check_status(c);
+}
+
+cpals_status cpals_pp_build_operators(cpals_ctx* c) {
+  CKS(ready(c));
+  Join j(c);
+  CKS(do_build(c));
+  CKS(sync_read(c));
+  c->ops_built = true;
+  return CPALS_OK;
+}
+
+cpals_status cpals_pp_sweep(cpals_ctx* c, int use_V, double* fitness_out) {
+  CKS(ready(c));
+  if (!c->ops_built) return c->fail(CPALS_E_STATE, "PP operators not built: call cpals_pp_build_operators");
+  Join j(c);
+  CKS(do_pp(c, use_V != 0));
+  CKS(sync_read(c));
+  if (fitness_out) *fitness_out = c->scal_h[0];
+  return check_status(c);
+}
+
+cpals_status cpals_fitness(cpals_ctx* c, double* out) {
+  CKS(ready(c));
+  if (!out) return c->fail(CPALS_E_INVALID, "out is NULL");
+  Join j(c);
+  CKS(do_fit(c));
+  CKS(sync_read(c));
+  *out = c->scal_h[0];
+  return CPALS_OK;
+}
+
+cpals_status cpals_get_factors(cpals_ctx* c, double* const* out) {
+  CKS(ready(c));
+  if (!out) return c->fail(CPALS_E_INVALID, "out is NULL");
+  Join j(c);
+  for (int n = 0; n < c->N; n++) {
+    if (!out[n]) return c->fail(CPALS_E_INVALID, "out[n] is NULL");
+    CK(cudaMemcpyAsync(out[n], c->A[n], c->dims[n] * c->R * 8, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return CPALS_OK;
+}
+
+cpals_status cpals_get_dA_ratios(cpals_ctx* c, double* out) {
+  CKS(ready(c));
+  if (!out) return c->fail(CPALS_E_INVALID, "out is NULL");
+  Join j(c);
+  CKS(sync_read(c));
+  for (int n = 0; n < c->N; n++)
+    out[n] = std::sqrt(c->scal_h[8 + 2 * n]) / std::sqrt(c->scal_h[9 + 2 * n]);
+  return CPALS_OK;
+}
+
+cpals_status cpals_run(cpals_ctx* c, int max_sweeps, double eps, int use_V, double target,
+                       double* fitness_trace, int* kind_trace, double* time_trace, int* n_done,
+                       int* reached) {
+  CKS(ready(c));
+  if (max_sweeps < 0) return c->fail(CPALS_E_INVALID, "max_sweeps < 0");
+  Join j(c);
+  const auto t0 = std::chrono::steady_clock::now();
+  int t = 0;
+  int hit = 0;
+  auto record = [&](int kind, double f) {
+    if (fitness_trace) fitness_trace[t] = f;
+    if (kind_trace) kind_trace[t] = kind;
+    if (time_trace)
+      time_trace[t] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    t++;
+  };
+  cpals_status st = CPALS_OK;
+  // make sure the eps test sees current ratios
+  st = sync_read(c);
+  while (st == CPALS_OK && t < max_sweeps && !hit) {
+    if (eps > 0 && all_small(c, eps)) {
+      st = do_build(c);
+      if (st != CPALS_OK) break;
+      c->ops_built = true;
+      st = sync_read(c);
+      bool first = true;
+      while (st == CPALS_OK && t < max_sweeps && all_small(c, eps)) {
+        st = do_pp(c, use_V != 0);
+        if (st != CPALS_OK) break;
+        st = sync_read(c);
+        if (st != CPALS_OK) break;
+        st = check_status(c);
+        double f = c->scal_h[0];
+        if (target > 0 && f >= target) {
+          // confirm with the exact fitness (Sec. 5)
+          st = do_fit(c);
+          if (st == CPALS_OK) st = sync_read(c);
+          if (st == CPALS_OK && c->scal_h[0] >= target) {
+            f = c->scal_h[0];
+            hit = 1;
+          }
+        }
+        record(first ? CPALS_SWEEP_PP_INIT : CPALS_SWEEP_PP_APPROX, f);
+        first = false;
+        if (hit) break;
+      }
+      if (st != CPALS_OK || hit || t >= max_sweeps) break;
+    }
+    st = do_als(c);
+    if (st != CPALS_OK) break;
+    st = sync_read(c);
+    if (st != CPALS_OK) break;
+    st = check_status(c);
+    const double f = c->scal_h[0];
+    if (target > 0 && f >= target) hit = 1;
+    record(CPALS_SWEEP_ALS, f);
+  }
+  if (n_done) *n_done = t;
+  if (reached) *reached = hit;
+  return st;
+}
+
+cpals_status cpals_mttkrp(cpals_ctx* c, int n, double* out) {
+  CKS(ready(c));
+  if (n < 0 || n >= c->N || !out) return c->fail(CPALS_E_INVALID, "bad mode or NULL out");
+  Join j(c);
+  c->ev_used = 0;
+  const int64_t cnt = c->dims[n] * c->R;
+  if (is64(c)) {
+    const double* r = nullptr;
+    CKS(mttkrp_launch<double>(c, n, &r));
+    CKS(sync_read(c));
+    return copy_out<double>(c, r, cnt, out);
+  }
+  const float* r = nullptr;
+  CKS(mttkrp_launch<float>(c, n, &r));
+  CKS(sync_read(c));
+  return copy_out<float>(c, r, cnt, out);
+}
+
+cpals_status cpals_get_operator(cpals_ctx* c, int i, int n, double* out) {
+  CKS(ready(c));
+  if (!c->ops_built) return c->fail(CPALS_E_STATE, "PP operators not built");
+  if (i < 0 || n < 0 || i >= c->N || n >= c->N || i > n || !out)
+    return c->fail(CPALS_E_INVALID, "need 0 <= i <= n < N");
+  Join j(c);
+  const void* src = i == n ? c->Mp[n] : c->ops[i][n];
+  const int64_t cnt = (i == n ? 1 : c->dims[i]) * c->dims[n] * c->R;
+  if (is64(c)) return copy_out<double>(c, (const double*)src, cnt, out);
+  return copy_out<float>(c, (const float*)src, cnt, out);
+}
+
+cpals_status cpals_pp_mttkrp(cpals_ctx* c, int n, int use_V, double* out) {
+  CKS(ready(c));
+  if (!c->ops_built) return c->fail(CPALS_E_STATE, "PP operators not built");
+  if (n < 0 || n >= c->N || !out) return c->fail(CPALS_E_INVALID, "bad mode or NULL out");
+  Join j(c);
+  c->ev_used = 0;
+  const int R = c->R;
+  const int s = (int)c->dims[n];
+  const int64_t cnt = (int64_t)s * R;
+  auto go = [&](auto tag) -> cpals_status {
+    using T = decltype(tag);
+    PPTerm<T> terms[kMaxModes];
+    pp_terms<T>(c, n, terms);
+    pp_correct<T>(P<const T>(c->Mp[n]), terms, c->N - 1, P<T>(c->rhs), s, R, c->L());
+    const T* res = P<const T>(c->rhs);
+    if (use_V) {
+      gamma_chol(c->S, c->W, c->N, n, R, c->Lf, c->Z, true, c->status, c->L());
+      vterm<T>(P<const T>(c->rhs), c->A[n], c->Z, c->rhs2, s, R, c->L());
+      CKS(sync_read(c));
+      return copy_out<double>(c, c->rhs2, cnt, out);
+    }
+    CKS(sync_read(c));
+    return copy_out<T>(c, res, cnt, out);
+    return CPALS_OK;
+  };
+  return is64(c) ? go(double{}) : go(float{});
+}
+
+cpals_status cpals_get_state(cpals_ctx* c, int which, int n, double* out) {
+  CKS(ready(c));
+  if (n < 0 || n >= c->N || !out || which < 0 || which > 1) return c->fail(CPALS_E_INVALID, "bad argument");
+  Join j(c);
+  CK(cudaMemcpyAsync(out, which == 0 ? c->Ap[n] : c->dA[n], c->dims[n] * c->R * 8,
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return CPALS_OK;
+}
+
+cpals_status cpals_set_profiling(cpals_ctx* c, int enable) {
+  if (!c) return CPALS_E_INVALID;
+  if ((enable != 0) != c->profiling) drop_graphs(c);
+  c->profiling = enable != 0;
+  return CPALS_OK;
+}
+
+cpals_status cpals_reset_stats(cpals_ctx* c) {
+  if (!c) return CPALS_E_INVALID;
+  c->launches = 0;
+  c->fl_launches = 0;
+  c->fl_ms = c->fl_bytes = c->fl_flops = 0;
+  return CPALS_OK;
+}
+
+cpals_status cpals_get_stats(cpals_ctx* c, int kind, int64_t* launches, double* total_ms,
+                             double* bytes, double* flops) {
+  if (!c) return CPALS_E_INVALID;
+  if (kind == 0) {
+    if (launches) *launches = c->fl_launches;
+    if (total_ms) *total_ms = c->fl_ms;
+    if (bytes) *bytes = c->fl_bytes;
+    if (flops) *flops = c->fl_flops;
+  } else if (kind == 1) {
+    if (launches) *launches = c->launches;
+    if (total_ms) *total_ms = 0;
+    if (bytes) *bytes = 0;
+    if (flops) *flops = 0;
+  } else {
+    return c->fail(CPALS_E_INVALID, "kind must be 0 or 1");
+  }
+  return CPALS_OK;
+}
+
+cpals_status cpals_set_graphs(cpals_ctx* c, int enable) {
+  if (!c) return CPALS_E_INVALID;
+  if (!enable) drop_graphs(c);
+  c->graphs = enable != 0;
+  return CPALS_OK;
+}
+
+cpals_status cpals_cost_model(const int64_t* dims, int N, int R, int kind, double* flops) {
+  if (!dims || !flops || N < 3 || N > kMaxModes || R < 1) return CPALS_E_INVALID;
+  for (int i = 0; i < N; i++)
+    if (dims[i] < 1) return CPALS_E_INVALID;
+  double f = 0;
+  const int h = (N + 1) / 2;
+  auto chain_cost = [&](std::vector<int> modes, int keep) {
+    double cost = 0;
+    while (modes.size() > 1) {
+      int pos = (int)modes.size() - 1;
+      if (modes[pos] == keep) pos--;
+      double sz = R;
+      for (int m : modes) sz *= (double)dims[m];
+      cost += 2.0 * sz;
+      modes.erase(modes.begin() + pos);
+    }
+    return cost;
+  };
+  double total = 1;
+  for (int i = 0; i < N; i++) total *= (double)dims[i];
+  if (kind == 0) {
+    std::vector<int> Lm, Rm;
+    for (int k = 0; k < h; k++) Lm.push_back(k);
+    for (int k = h; k < N; k++) Rm.push_back(k);
+    f = 2 * 2.0 * total * R;
+    for (int n = 0; n < h; n++) f += chain_cost(Lm, n);
+    for (int n = h; n < N; n++) f += chain_cost(Rm, n);
+  } else if (kind == 1) {
+    f = 3 * 2.0 * total * R;
+    for (int l = 3; l <= N - 1; l++)
+      for (int i = 0; i <= l; i++)
+        for (int j = i + 1; j <= l; j++) {
+          int pi, pj, w;
+          tree_parent(l, i, j, &pi, &pj, &w);
+          double sz = R;
+          for (int m : level_modes(N, l - 1, pi, pj)) sz *= (double)dims[m];
+          f += 2.0 * sz;
+        }
+  } else if (kind == 2) {
+    for (int n = 0; n < N; n++) {
+      for (int i = 0; i < N; i++)
+        if (i != n) f += 2.0 * dims[i] * dims[n] * R;
+      f += 4.0 * dims[n] * R * R;
+    }
+  } else if (kind == 3) {
+    const double s = (double)dims[0];
+    for (int l = 2; l <= N - 1; l++) {
+      const double comb = (double)(l + 1) * l / 2.0;
+      f += comb * std::pow(s, N - l + 2);
+    }
+    f *= 2.0 * R;
+  } else {
+    return CPALS_E_INVALID;
+  }
+  *flops = f;
+  return CPALS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// Internal declarations shared by the translation units of libcpals.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+namespace cpals {
+
+// Where a launch goes and the counter of kernels launched.
+struct Launch {
+  cudaStream_t stream;
+  int64_t* counter;
+};
+
+constexpr int kMaxModes = 8;
+constexpr int kMaxRank = 128;
+
+// ---------------------------------------------------------------- contractions
+// First-level contraction of the tensor with a factor (or Khatri-Rao product)
+// B (K x R, r fastest), Sec. 2.5:
+//   kmajor:  out[m][r]    = sum_k X[m*K + k]          * B[k][r]   (batch must be 1)
+//   !kmajor: out[b][m][r] = sum_k X[(b*K + k)*M + m]  * B[k][r]
+// splits > 1 splits K; partials (splits*batch*M*R values) then holds the
+// partial sums and a deterministic reduction writes out.
+template <typename TX, typename T>
+void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K, int64_t M,
+               int R, bool kmajor, int splits, Launch L);
+
+// Multi-TTV (lower levels of the trees): out[o][q][r] = sum_x in[o][x][q][r] * A[x][r].
+template <typename T>
+void ttv(const T* in, const T* A, T* out, int64_t outer, int sw, int64_t inner, int R, Launch L);
+
+// One first-order term of Eq. 3: out[y][r] += sum_x op[y*ystride + x*xstride + r] * dA[x][r].
+template <typename T>
+struct PPTerm {
+  const T* op;
+  const T* dA;
+  int64_t xstride;
+  int64_t ystride;
+  int sx;
+};
+// out[y][r] = Mp[y][r] + sum over terms (Eq. 3, first two terms).
+template <typename T>
+void pp_correct(const T* Mp, const PPTerm<T>* terms, int nterms, T* out, int sy, int R, Launch L);
+
+// Row-major Khatri-Rao product of nm factors (last factor fastest): out is prod(dims) x R.
+template <typename T>
+void khatri_rao(const T* const* A, const int64_t* dims, int nm, int R, T* out, Launch L);
+
+// Same product written transposed, zero-padded and in bf16 for the tensor
+// cores: outT[r][k] for r < Rpad, k < Kstride (k >= K and r >= R are zero).
+void khatri_rao_bf16_t(const float* const* A, const int64_t* dims, int nm, int R, int Rpad,
+                       int64_t Kstride, __nv_bfloat16* outT, Launch L);
+
+// Element conversions.
+template <typename TS, typename TD>
+void convert(const TS* src, TD* dst, int64_t n, Launch L);
+
+// sum of squares of n values, accumulated in float64 (deterministic two-pass).
+template <typename TX>
+void sumsq(const TX* x, int64_t n, double* partials, double* out, Launch L);
+
+// ---------------------------------------------------------------- float64 small kernels
+// Gamma^(n) = *_{k != n} S^(k) (Algorithm 1 line 5), its Cholesky factor L,
+// and (useV) Z = sum_{i<j; i,j != n} W_i * W_j * (*_{k not in {i,j,n}} S_k)
+// so that sum_{i<j} V^(n,i,j) = A^(n) Z (Eq. 3).  status[0] |= 1<<n if not PD.
+void gamma_chol(const double* S, const double* W, int N, int n, int R, double* Lout, double* Z,
+                bool useV, int* status, Launch L);
+
+// Row-wise solve A_new = rhs Gamma^{-1} with the factor L; writes A (in place),
+// dA = A_new - (Aref ? Aref : A_old), compute-precision copies Ac, dAc and per-row
+// ||dA||^2, ||A_new||^2 into rownorm (2*s values).  Rows are left unchanged if
+// the factorisation failed for this mode (status bit set).
+template <typename T>
+void solve_rows(const T* rhs, double* A, const double* Aref, double* dA, const double* Lf, T* Ac,
+                T* dAc, double* rownorm, int s, int R, int n, const int* status, Launch L);
+// Same with the second-order PP terms: rhs2 = rhs + A_old Z (float64 scratch of
+// s*R values) is formed first.
+template <typename T>
+void solve_rows_v(const T* rhs, double* A, const double* Aref, double* dA, const double* Lf,
+                  const double* Z, double* rhs2, T* Ac, T* dAc, double* rownorm, int s, int R,
+                  int n, const int* status, Launch L);
+// out[y][r] = rhs[y][r] + sum_k A[y][k] Z[k][r] in float64 (second-order PP terms).
+template <typename T>
+void vterm(const T* rhs, const double* A, const double* Z, double* out, int s, int R, Launch L);
+// Raise the dynamic shared-memory limits of the float64 kernels (call once per device).
+cudaError_t setup_small_kernels();
+
+// S = A^T A and (withW) W = A^T dA in float64; also reduces rownorm into
+// scal[0] = ||dA||^2, scal[1] = ||A||^2.  partials: workspace.
+void gram_update(const double* A, const double* dA, double* S, double* W, bool withW, int s,
+                 int R, const double* rownorm, double* scal, double* partials, Launch L);
+
+// Fitness from the last mode's right-hand side (Sec. 5):
+// inner = sum rhs*A, model = sum_{r,r'} prod_k S_k, out[0] = fitness, out[1] = inner,
+// out[2] = model.  partials: workspace (>= 2*256 doubles).
+template <typename T>
+void fitness(const T* rhs, const double* A, const double* S, int N, int R, int s, double normX2,
+             double* out, double* partials, Launch L);
+
+// ---------------------------------------------------------------- tcgen05 (sm_103a)
+// bf16 tensor-core first-level contraction, fp32 accumulate in TMEM, TMA-fed:
+//   kmajor:  out[m][r]    = sum_k Xb[m*K + k]         * Bt[r][k]
+//   !kmajor: out[b][m][r] = sum_k Xb[(b*K + k)*M + m] * Bt[r][k]
+// Bt is R padded to Rpad (multiple of 16) rows of Kstride bf16 (zero padded).
+// splits > 1: fp32 partials + deterministic reduction into out.
+// Returns false if the shape is not supported (alignment), so the caller can
+// report CPALS_E_UNSUPPORTED.
+bool umma_supported(int64_t K, int64_t M, bool kmajor, int R);
+// Raise the dynamic shared-memory limit of the tensor-core kernels (once per device).
+cudaError_t setup_umma_kernels();
+cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, float* out,
+                           float* partials, int64_t batch, int64_t K, int64_t M, int R, int Rpad,
+                           int64_t Kstride, bool kmajor, int splits, int* err_flag, Launch L);
+
+}  // namespace cpals

@@ -1,0 +1,520 @@
+// tcgen05 (5th-generation tensor core) first-level contraction for sm_103a.
+//
+// The first level of both dimension trees (Sec. 2.5, Sec. 3.2.3) contracts the
+// input tensor X with one factor or with the Khatri-Rao product of a block of
+// factors: a matrix product whose long dimension streams X from HBM once.
+//   kmajor:  out[m][r]    = sum_k X[m*K + k]         * Bt[r][k]
+//   !kmajor: out[b][m][r] = sum_k X[(b*K + k)*M + m] * Bt[r][k]
+// X is bf16 (one-time copy of the input), Bt is the bf16 transposed B operand
+// (Rpad x Kstride, zero padded), accumulation is fp32 in tensor memory.
+//
+// Persistent warp-specialised kernel, one CTA per SM:
+//   warp 0      : TMA producer (A tile 128 x 64, B tile Rpad x 64 per stage,
+//                 128-byte swizzle, mbarrier complete_tx)
+//   warp 1      : TMEM allocation + single-thread tcgen05.mma issue (M = 128,
+//                 N = Rpad, K = 16 per instruction), tcgen05.commit to free
+//                 stages and to publish finished accumulators
+//   warps 2..5  : epilogue: tcgen05.ld 32x32b, fp32 stores of the rows < M
+// Two accumulators (2 x 128 TMEM columns) let the epilogue of one tile run
+// under the MMAs of the next.  Every wait is bounded: on timeout the kernel
+// records an error code, drains what it issued and returns.
+#include <cuda.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "internal.h"
+
+namespace cpals {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;                 // bf16 elements = 128 bytes = one swizzle row
+constexpr int kThreadsUmma = 192;      // 6 warps
+constexpr int A_STAGE_BYTES = BM * BK * 2;
+constexpr unsigned long long kTimeoutCycles = 4000000000ull;   // ~2 s at 2 GHz
+
+// error codes written to the error word
+enum { ERR_PRODUCER = 1, ERR_MMA_FULL = 2, ERR_MMA_ACC = 3, ERR_EPI = 4, ERR_DRAIN = 5 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; returns false on timeout or when another role aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          bool sleep) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = clock64();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kTimeoutCycles) return false;
+    if (sleep) __nanosleep(64);
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(map), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4 at [0,14), leading
+// byte offset >> 4 at [16,30), stride byte offset >> 4 at [32,46), fixed
+// 0b001 at [46,49), swizzle mode at [61,64) (2 = 128-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9 = 1, 10-12 = 1), A major at bit 15 (1 = MN-major), B K-major,
+// N >> 3 at [17,23), M >> 4 at [24,29).
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N, bool a_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+      " [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+struct UmmaParams {
+  int64_t batch, K, M;
+  int R, Rpad, splits, stages;
+  int64_t kchunk;       // multiple of BK
+  int64_t mtiles, units;
+  float* out;           // out or partials ([z][b][m][r])
+  int* err;
+};
+
+template <bool KMAJOR>
+__global__ void __launch_bounds__(kThreadsUmma, 1)
+umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                 UmmaParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[8], empty_bar[8], accf_bar[2], acce_bar[2], done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int S = p.stages;
+  const uint32_t b_stage_bytes = (uint32_t)p.Rpad * BK * 2;
+  const uint32_t stage_bytes = A_STAGE_BYTES + b_stage_bytes;
+
+  if (threadIdx.x == 0) {
+    abort_sh = 0;
+    for (int s = 0; s < S; s++) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      mbar_init(smem_u32(&accf_bar[b]), 1);
+      mbar_init(smem_u32(&acce_bar[b]), 4);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+                     smem_u32(&tmem_base_sh))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_base_sh;
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int issued[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+        const int64_t mt = u % p.mtiles;
+        const int64_t rest = u / p.mtiles;
+        const int z = (int)(rest % p.splits);
+        const int64_t b = rest / p.splits;
+        const int64_t k0 = (int64_t)z * p.kchunk;
+        const int64_t k1 = min(p.K, k0 + p.kchunk);
+        for (int64_t k = k0; k < k1; k += BK) {
+          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_sh, false)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full_bar[stage]);
+          const uint32_t sA = base + stage * stage_bytes;
+          const uint32_t sB = sA + A_STAGE_BYTES;
+          mbar_expect_tx(fb, stage_bytes);
+          if (KMAJOR) {
+            tma_load_2d(sA, &mapA, fb, (int)k, (int)(mt * BM));
+          } else {
+            tma_load_3d(sA, &mapA, fb, (int)(mt * BM), (int)k, (int)b);
+            tma_load_3d(sA + A_STAGE_BYTES / 2, &mapA, fb, (int)(mt * BM + 64), (int)k, (int)b);
+          }
+          tma_load_2d(sB, &mapB, fb, (int)k, 0);
+          issued[stage]++;
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+      if (!ok) {
+        atomicCAS(p.err, 0, ERR_PRODUCER);
+        abort_sh = 1;
+      }
+      // drain: every stage's last load has landed before the CTA may exit
+      for (int s = 0; s < S; s++) {
+        if (!issued[s]) continue;
+        const uint32_t par = (uint32_t)((issued[s] - 1) & 1);
+        const unsigned long long t0 = clock64();
+        while (!mbar_try(smem_u32(&full_bar[s]), par)) {
+          if (clock64() - t0 > kTimeoutCycles) {
+            atomicCAS(p.err, 0, ERR_DRAIN);
+            break;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(BM, p.Rpad, !KMAJOR);
+      int stage = 0;
+      uint32_t phase = 0;
+      int t = 0;
+      bool ok = true;
+      bool any = false;
+      for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x, t++) {
+        const int64_t rest = u / p.mtiles;
+        const int z = (int)(rest % p.splits);
+        const int64_t k0 = (int64_t)z * p.kchunk;
+        const int64_t k1 = min(p.K, k0 + p.kchunk);
+        const int buf = t & 1;
+        if (!mbar_wait(smem_u32(&acce_bar[buf]), ((t >> 1) & 1) ^ 1, &abort_sh, false)) {
+          atomicCAS(p.err, 0, ERR_MMA_ACC);
+          abort_sh = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 128);
+        uint32_t accum = 0;
+        for (int64_t k = k0; k < k1; k += BK) {
+          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_sh, false)) {
+            atomicCAS(p.err, 0, ERR_MMA_FULL);
+            abort_sh = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sA = base + stage * stage_bytes;
+          const uint32_t sB = sA + A_STAGE_BYTES;
+#pragma unroll
+          for (int ks = 0; ks < BK / 16; ks++) {
+            uint64_t adesc;
+            if (KMAJOR) adesc = smem_desc(sA + ks * 32, 16, 1024);
+            else adesc = smem_desc(sA + ks * 2048, A_STAGE_BYTES / 2, 1024);
+            const uint64_t bdesc = smem_desc(sB + ks * 32, 16, 1024);
+            umma_f16(d_tmem, adesc, bdesc, idesc, accum);
+            accum = 1;
+          }
+          umma_commit(smem_u32(&empty_bar[stage]));
+          any = true;
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        umma_commit(smem_u32(&accf_bar[buf]));
+      }
+      // all issued MMAs complete before TMEM is released
+      if (any) {
+        umma_commit(smem_u32(&done_bar));
+        const unsigned long long t0 = clock64();
+        while (!mbar_try(smem_u32(&done_bar), 0)) {
+          if (clock64() - t0 > kTimeoutCycles) {
+            atomicCAS(p.err, 0, ERR_DRAIN);
+            break;
+          }
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------ epilogue (warps 2..5)
+    const int q = warp & 3;                   // TMEM lane quarter this warp may access
+    const int row = q * 32 + lane;
+    int t = 0;
+    for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x, t++) {
+      const int64_t mt = u % p.mtiles;
+      const int64_t rest = u / p.mtiles;
+      const int z = (int)(rest % p.splits);
+      const int64_t b = rest / p.splits;
+      const int buf = t & 1;
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(smem_u32(&accf_bar[buf]), (t >> 1) & 1, &abort_sh, true) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) {
+          atomicCAS(p.err, 0, ERR_EPI);
+          abort_sh = 1;
+        }
+        break;
+      }
+      // the phase is complete for every lane once lane 0 has seen it
+      while (!mbar_try(smem_u32(&accf_bar[buf]), (t >> 1) & 1)) {
+      }
+      __syncwarp();
+      tc_fence_after();
+      const int64_t m = mt * BM + row;
+      float* orow = p.out + (((int64_t)z * p.batch + b) * p.M + m) * p.R;
+      const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 128);
+      for (int c = 0; c < p.Rpad; c += 16) {
+        float v[16];
+        tmem_ld16(taddr + c, v);
+        if (m < p.M) {
+#pragma unroll
+          for (int i = 0; i < 16; i++)
+            if (c + i < p.R) orow[c + i] = v[i];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acce_bar[buf]));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem_base)
+                 : "memory");
+  }
+}
+
+__global__ void reduce_splits_f32(const float* __restrict__ part, float* __restrict__ out,
+                                  int64_t n, int splits) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float acc = part[i];
+    for (int z = 1; z < splits; z++) acc += part[(int64_t)z * n + i];
+    out[i] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)f;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+cudaError_t setup_umma_kernels() {
+  const int smem = 200 * 1024 + 1024;
+  cudaError_t e = cudaFuncSetAttribute(umma_gemm_kernel<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(umma_gemm_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+bool umma_supported(int64_t K, int64_t M, bool kmajor, int R) {
+  if (R < 1 || R > 128) return false;
+  if (K >= (1ll << 31) || M >= (1ll << 31)) return false;
+  if (kmajor) return K % 8 == 0;
+  return M % 8 == 0;
+}
+
+cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, float* out,
+                           float* partials, int64_t batch, int64_t K, int64_t M, int R, int Rpad,
+                           int64_t Kstride, bool kmajor, int splits, int* err_flag, Launch L) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  if (!umma_supported(K, M, kmajor, R) || Rpad % 16 || Rpad > 128 || Rpad < R)
+    return cudaErrorInvalidValue;
+  if (kmajor && batch != 1) return cudaErrorInvalidValue;
+
+  CUtensorMap mapA, mapB;
+  CUresult cr;
+  if (kmajor) {
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)M};
+    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {BK, BM};
+    cuuint32_t es[2] = {1, 1};
+    cr = enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)Xb, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    cuuint64_t dims[3] = {(cuuint64_t)M, (cuuint64_t)K, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)M * 2, (cuuint64_t)M * K * 2};
+    cuuint32_t box[3] = {64, BK, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    cr = enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)Xb, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)Rpad};
+    cuuint64_t strides[1] = {(cuuint64_t)Kstride * 2};
+    cuuint32_t box[2] = {BK, (cuuint32_t)Rpad};
+    cuuint32_t es[2] = {1, 1};
+    cr = enc(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)Bt, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+
+  UmmaParams p;
+  p.batch = batch;
+  p.K = K;
+  p.M = M;
+  p.R = R;
+  p.Rpad = Rpad;
+  if (splits < 1) splits = 1;
+  p.kchunk = cdiv(cdiv(K, splits), BK) * BK;
+  p.splits = (int)cdiv(K, p.kchunk);
+  p.mtiles = cdiv(M, BM);
+  p.units = p.mtiles * batch * p.splits;
+  p.err = err_flag;
+  p.out = p.splits > 1 ? partials : out;
+  const int stage_bytes = A_STAGE_BYTES + Rpad * BK * 2;
+  p.stages = std::min(8, (200 * 1024) / stage_bytes);
+  const size_t smem = (size_t)p.stages * stage_bytes + 1024;
+  const int grid = (int)std::min<int64_t>(p.units, num_sms());
+
+  cudaError_t e;
+  if (kmajor)
+    umma_gemm_kernel<true><<<grid, kThreadsUmma, smem, L.stream>>>(mapA, mapB, p);
+  else
+    umma_gemm_kernel<false><<<grid, kThreadsUmma, smem, L.stream>>>(mapA, mapB, p);
+  (*L.counter)++;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (p.splits > 1) {
+    const int64_t n = batch * M * R;
+    const int blocks = (int)std::min<int64_t>(cdiv(n, 256), 152 * 16);
+    reduce_splits_f32<<<blocks, 256, 0, L.stream>>>(partials, out, n, p.splits);
+    (*L.counter)++;
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace cpals

@@ -1,0 +1,72 @@
+"""Host-only checks of the C-ABI library: it builds for sm_103a without a GPU,
+loads, exports every symbol include/cpals.h declares, rejects bad arguments
+before touching a device, and its flop model is the paper's (Table 1, Sec. 3.2.3).
+"""
+import os
+import re
+
+import pytest
+
+from oracle import cpals_oracle as O
+from paper_1811_10573_gb300 import build as B
+from paper_1811_10573_gb300 import cpals
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return cpals.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "cpals.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cpals_[a-z_A-Z0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding marshals each of them under the same name
+    for n in names:
+        assert n in cpals._SIGS, n
+        assert callable(getattr(cpals, n)), n
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    for dims, R, prec in [([4, 5], 2, 0), ([4, 5, 0], 2, 0), ([4, 5, 6], 0, 0),
+                          ([4, 5, 6], 200, 0), ([4, 5, 6], 3, 7), ([2] * 9, 2, 0)]:
+        st, ctx = cpals.cpals_create(dims, len(dims), R, prec)
+        assert st == 1 and not ctx, (dims, R, prec)
+
+
+@pytest.mark.parametrize("N", [3, 4, 5, 6])
+def test_operator_tree_cost_is_papers(lib, N):
+    """The operator dimension tree the library runs has exactly the paper's
+    cost 2R sum_{l=2}^{N-1} C(l+1,2) s^{N-l+2} (Sec. 3.2.3)."""
+    for s, R in [(7, 3), (24, 50), (40, 16)]:
+        mine = cpals.cost_model([s] * N, R, 1)
+        paper = cpals.cost_model([s] * N, R, 3)
+        assert mine == paper == O.pp_operator_build_cost(s, N, R)
+
+
+@pytest.mark.parametrize("N", [3, 4, 6])
+def test_als_and_pp_costs_table1(lib, N):
+    """ALS sweep 4 s^N R to leading order; PP approximated step within
+    2N^2(s^2R + sR^2) (Table 1)."""
+    R = 8
+    s = 400 if N == 3 else (120 if N == 4 else 24)
+    als = cpals.cost_model([s] * N, R, 0)
+    assert 1.0 <= als / (4 * s ** N * R) < 1.0 + 2.0 / s
+    pp = cpals.cost_model([s] * N, R, 2)
+    assert pp <= O.table1_cp(s, N, R)["pp_approx"]
+    assert pp >= 2 * N * (N - 1) * s * s * R
+
+
+def test_cost_model_rejects_bad_sizes(lib):
+    with pytest.raises(cpals.CPALSError):
+        cpals.cost_model([4, 0, 3], 2, 0)

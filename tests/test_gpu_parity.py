@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances:
+* FP64 mode: 1e-10 relative for factors, MTTKRP, operators; fitness within
+  1e-10 absolute (the spec bar is 1e-10 relative for factors and
+  fitness in FP64).
+* FP32 mode: relative error of a length-K float32 dot product with float32
+  inputs is below ~K * 2^-24 in the worst case and ~sqrt(K) * 2^-24 typically;
+  the tests allow 2e-5 (small K) relative to max|ref|.
+* MIXED_BF16 against the float64 oracle: X and the B operand are rounded to
+  bf16 (relative 2^-9 each), so a product carries up to ~2^-8 and a sum of
+  mixed-sign terms up to ~1e-2 relative to max|ref|; the tests allow 2e-2.
+  (tests/test_gpu_umma.py checks the tensor-core kernel itself at 2e-5 on
+  bf16-rounded inputs.)
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cpals_oracle as O
+from paper_1811_10573_gb300 import cpals, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 2e-5, "mixed": 2e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_1811_10573_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    cpals.lib()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+def X64(p):
+    return np.asarray(p.X, dtype=np.float64)
+
+
+SHAPES = [([70, 45, 33], 10), ([33, 70, 45], 17), ([13, 17, 11, 9], 7), ([7, 6, 5, 8, 9], 5),
+          ([9, 8, 7, 6, 5, 4], 3), ([130, 65, 40], 100), ([24, 24, 24], 1)]
+
+
+def _ctx(p, prec):
+    g = cpals.CPALS(p.dims, p.R, prec)
+    g.set_tensor(torch.from_numpy(np.ascontiguousarray(p.X)).cuda())
+    g.init_factors(p.A0)
+    return g
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("dims,R", SHAPES)
+def test_mttkrp(dims, R, prec):
+    storage = "f64" if prec == "fp64" else "f32"
+    p = synth.make_problem("normal", dims, R, seed=3, storage=storage)
+    with _ctx(p, prec) as g:
+        for n in range(len(dims)):
+            ref = O.mttkrp(X64(p), p.A0, n)
+            assert rel(g.mttkrp(n), ref) < TOL[prec], (n, prec)
+
+
+@pytest.mark.parametrize("dims,R", [([40, 33, 27], 9), ([11, 13, 9, 10], 6), ([6, 7, 5, 6, 4], 4)])
+def test_als_sweeps_fp64(dims, R):
+    p = synth.make_problem("normal", dims, R, seed=5, storage="f64")
+    A = [a.copy() for a in p.A0]
+    S = [O.gram(a) for a in A]
+    with _ctx(p, "fp64") as g:
+        for sweep in range(4):
+            f = g.als_sweep()
+            dA_ref, _ = O.als_sweep(p.X, A, S)
+            assert abs(f - O.fitness(p.X, A)) < 1e-10
+            for a, b in zip(g.get_factors(), A):
+                assert rel(a, b) < 1e-10, sweep
+            ratios = g.get_dA_ratios()
+            want = [np.linalg.norm(d) / np.linalg.norm(a) for d, a in zip(dA_ref, A)]
+            np.testing.assert_allclose(ratios, want, rtol=1e-9)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dims,R", [([40, 33, 27], 9), ([11, 13, 9, 10], 6), ([6, 7, 5, 6, 4], 4),
+                                    ([5, 6, 4, 5, 3, 4], 3)])
+def test_pp_operators(dims, R, prec):
+    storage = "f64" if prec == "fp64" else "f32"
+    p = synth.make_problem("normal", dims, R, seed=7, storage=storage)
+    with _ctx(p, prec) as g:
+        g.als_sweep()
+        A = g.get_factors()
+        g.pp_build_operators()
+        ops, Mp = O.pp_operators(X64(p), A)
+        N = len(dims)
+        for i in range(N):
+            for n in range(i + 1, N):
+                assert rel(g.get_operator(i, n), ops[(i, n)]) < TOL[prec], (i, n)
+            assert rel(g.get_operator(i, i), Mp[i]) < TOL[prec], i
+        for n in range(N):
+            np.testing.assert_array_equal(g.get_state("Ap", n), A[n])
+            assert not np.any(g.get_state("dA", n))
+
+
+@pytest.mark.parametrize("dims,R", [([40, 33, 27], 9), ([11, 13, 9, 10], 6), ([6, 7, 5, 6, 4], 4)])
+def test_pp_sweeps_fp64(dims, R):
+    """Algorithm 3's PP sweeps (with and without V) against the oracle, and the
+    approximated right-hand sides of Eq. 3 for the state the GPU holds."""
+    p = synth.make_problem("normal", dims, R, seed=9, storage="f64")
+    with _ctx(p, "fp64") as g:
+        for _ in range(2):
+            g.als_sweep()
+        A = g.get_factors()
+        S = [O.gram(a) for a in A]
+        g.pp_build_operators()
+        Ap = [a.copy() for a in A]
+        ops, Mp = O.pp_operators(p.X, Ap)
+        dA = [np.zeros_like(a) for a in A]
+        for sweep, useV in enumerate([True, False, True]):
+            g.pp_sweep(use_V=useV)
+            O.pp_sweep(ops, Mp, A, Ap, dA, S, useV)
+            for n, (a, b) in enumerate(zip(g.get_factors(), A)):
+                assert rel(a, b) < 1e-10, (sweep, n)
+                assert rel(g.get_state("dA", n), dA[n]) < 1e-9, (sweep, n)
+        A_g = g.get_factors()
+        dA_g = [g.get_state("dA", n) for n in range(len(dims))]
+        for n in range(len(dims)):
+            for useV in (False, True):
+                ref = O.pp_mttkrp(ops, Mp, A_g, dA_g, n, useV)
+                assert rel(g.pp_mttkrp(n, useV), ref) < 1e-10, (n, useV)
+
+
+def test_fitness_exact_fp64():
+    p = synth.make_problem("normal", [30, 20, 25], 5, seed=11, storage="f64")
+    with _ctx(p, "fp64") as g:
+        g.als_sweep()
+        g.pp_build_operators()
+        g.pp_sweep()
+        f = g.fitness()
+        A = g.get_factors()
+        assert abs(f - O.fitness_explicit(p.X, A)) < 1e-10
+
+
+def test_order3_60_rank10_run_fp64():
+    """The 60^3 rank-10 FP64 workload end to end (Algorithm 3, eps = 0.2,
+    50 sweeps): same sweep kinds as the oracle, fitness within 1e-10 for
+    every sweep, final factors within 1e-8 relative."""
+    p = synth.order3_60_rank10(seed=0)
+    A_ref, tr = O.pp_cp_als(p.X, p.A0, p.sweeps, p.eps, use_V=True)
+    with _ctx(p, "fp64") as g:
+        out = g.run(p.sweeps, p.eps, use_V=True)
+        assert out["kinds"] == tr.kinds
+        # the GPU reports the PP estimate after PP sweeps; compare exact ones
+        for k, (f, fr) in enumerate(zip(out["fitness"], tr.fitness)):
+            if out["kinds"][k] == "als":
+                assert abs(f - fr) < 1e-10, k
+        assert abs(g.fitness() - tr.fitness[-1]) < 1e-10
+        for a, b in zip(g.get_factors(), A_ref):
+            assert rel(a, b) < 1e-8
+
+
+def test_singular_gamma_reported():
+    """Identical columns in two factors make Gamma of the third mode singular:
+    CPALS_E_SINGULAR, and that factor is left unchanged."""
+    p = synth.make_problem("normal", [12, 10, 9], 3, seed=13, storage="f64")
+    A0 = [a.copy() for a in p.A0]
+    for n in (1, 2):
+        A0[n][:, 1] = A0[n][:, 0]
+    with cpals.CPALS(p.dims, p.R, "fp64") as g:
+        g.set_tensor(p.X)
+        g.init_factors(A0)
+        with pytest.raises(cpals.CPALSError) as e:
+            g.als_sweep()
+        assert e.value.status == 5
+        np.testing.assert_array_equal(g.get_factors()[0], A0[0])
+
+
+def test_call_order_errors():
+    with cpals.CPALS([5, 6, 7], 2, "fp64") as g:
+        with pytest.raises(cpals.CPALSError) as e:
+            g.als_sweep()
+        assert e.value.status == 4
+        g.set_tensor(np.ones((5, 6, 7)))
+        g.init_factors([np.ones((s, 2)) + np.arange(2) for s in (5, 6, 7)])
+        with pytest.raises(cpals.CPALSError) as e:
+            g.pp_sweep()
+        assert e.value.status == 4
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_full_size_order3_400_sampled(prec):
+    """400^3 rank 100 (FP32 storage), the launch configuration the benchmark
+    times: sampled MTTKRP rows of every mode against the oracle row by row,
+    then one ALS sweep's fitness against the oracle's formula."""
+    p = synth.order3_400_rank100(seed=0)
+    X = p.X
+    rng = np.random.default_rng(0)
+    with _ctx(p, prec) as g:
+        for n in range(3):
+            M = g.mttkrp(n)
+            for y in rng.choice(p.dims[n], 4, replace=False):
+                sub = np.take(X, [y], axis=n).astype(np.float64)
+                A = [a if k != n else a[y:y + 1] for k, a in enumerate(p.A0)]
+                ref = O.mttkrp(sub, A, n)[0]
+                assert rel(M[y], ref) < (1e-4 if prec == "fp32" else 1e-2), (n, y)
