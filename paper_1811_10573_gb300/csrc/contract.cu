@@ -98,14 +98,26 @@ gemm_simt_kernel(const TX* __restrict__ X, const T* __restrict__ B, T* __restric
   }
 }
 
+// out[i] = sum_z part[z][i]: 8 warps split the z range (z = w, w+8, ...), then
+// a fixed-order combine (deterministic).  32 outputs per CTA, coalesced.
 template <typename T>
-__global__ void reduce_splits_kernel(const T* __restrict__ part, T* __restrict__ out, int64_t n,
-                                     int splits) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    T acc = part[i];
-    for (int z = 1; z < splits; z++) acc += part[(int64_t)z * n + i];
-    out[i] = acc;
+__global__ void __launch_bounds__(256)
+reduce_splits_kernel(const T* __restrict__ part, T* __restrict__ out, int64_t n, int splits) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+  T acc = T(0);
+  if (i < n) {
+#pragma unroll 4
+    for (int z = w; z < splits; z += 8) acc += part[(int64_t)z * n + i];
+  }
+  __shared__ T red[8][33];
+  red[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && i < n) {
+    T sum = red[0][lane];
+#pragma unroll
+    for (int k = 1; k < 8; k++) sum += red[k][lane];
+    out[i] = sum;
   }
 }
 
@@ -126,11 +138,7 @@ void gemm_launch(const TX* X, const T* B, T* out, T* partials, int64_t batch, in
       <<<(unsigned)blocks, kThreads, 0, L.stream>>>(X, B, dst, batch, K, M, R, splits, kchunk,
                                                      mtiles);
   (*L.counter)++;
-  if (splits > 1) {
-    int64_t n = batch * M * R;
-    reduce_splits_kernel<T><<<grid_for(n, 256), 256, 0, L.stream>>>(partials, out, n, splits);
-    (*L.counter)++;
-  }
+  if (splits > 1) reduce_splits<T>(partials, out, batch * M * R, splits, L);
 }
 
 // ---------------------------------------------------------------- multi-TTV
@@ -157,6 +165,45 @@ ttv_kernel(const T* __restrict__ in, const T* __restrict__ A, T* __restrict__ ou
 #pragma unroll
     for (int i = 1; i < 8; i++) s += red[i][lane];
     out[o * QR + f] = s;
+  }
+}
+
+// float path with 4 outputs per lane (16-byte loads) when R % 4 == 0: a CTA
+// takes 128 consecutive (q, r) outputs of one o; 8 warps split x.
+__global__ void __launch_bounds__(kThreads)
+ttv4_kernel(const float* __restrict__ in, const float* __restrict__ A, float* __restrict__ out,
+            int sw, int64_t QR, int R, int64_t chunks) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t o = blockIdx.x / chunks;
+  const int64_t c = blockIdx.x % chunks;
+  const int64_t f = c * 128 + 4 * lane;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (f < QR) {
+    const int r = (int)(f % R);
+    const float* base = in + o * sw * QR + f;
+#pragma unroll 4
+    for (int x = w; x < sw; x += 8) {
+      const float4 v = *reinterpret_cast<const float4*>(base + (int64_t)x * QR);
+      const float4 a = __ldg(reinterpret_cast<const float4*>(A + (int64_t)x * R + r));
+      acc.x = fmaf(v.x, a.x, acc.x);
+      acc.y = fmaf(v.y, a.y, acc.y);
+      acc.z = fmaf(v.z, a.z, acc.z);
+      acc.w = fmaf(v.w, a.w, acc.w);
+    }
+  }
+  __shared__ float4 red[8][33];
+  red[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && f < QR) {
+    float4 s = red[0][lane];
+#pragma unroll
+    for (int i = 1; i < 8; i++) {
+      s.x += red[i][lane].x;
+      s.y += red[i][lane].y;
+      s.z += red[i][lane].z;
+      s.w += red[i][lane].w;
+    }
+    *reinterpret_cast<float4*>(out + o * QR + f) = s;
   }
 }
 
@@ -221,24 +268,57 @@ __global__ void khatri_rao_kernel(FactorList<T> fl, int R, T* __restrict__ out, 
   }
 }
 
-__global__ void khatri_rao_bf16_t_kernel(FactorList<float> fl, int R, int Rpad, int64_t K,
-                                         int64_t Kstride, __nv_bfloat16* __restrict__ outT) {
-  const int64_t n = (int64_t)Rpad * Kstride;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(i / Kstride);
-    const int64_t kk = i % Kstride;
-    float v = 0.f;
-    if (r < R && kk < K) {
-      int64_t k = kk;
-      v = 1.f;
-      for (int j = fl.n - 1; j >= 0; j--) {
-        const int64_t ij = k % fl.dims[j];
-        k /= fl.dims[j];
-        v *= fl.A[j][ij * R + r];
+// KRP^T in bf16: row r (blockIdx.y) of the transposed Khatri-Rao product.
+// Index k = p * s_last + i splits into a prefix p over the leading factors
+// and i over the last one.  A CTA takes a range of prefixes: the prefix
+// product pf = A_0[i_0][r] * ... * A_{nm-2}[i_{nm-2}][r] (float32, left to
+// right) is formed once per prefix, and v = pf * A_{nm-1}[i][r] is rounded to
+// bf16 (round to nearest even).  k >= K (padding up to Kstride) is zero.
+constexpr int kKrpSmem = 8192;   // floats of the staged last column
+
+__global__ void __launch_bounds__(256)
+khatri_rao_bf16_t_kernel(FactorList<float> fl, int R, int64_t K, int64_t Kstride, int64_t nprefix,
+                         int64_t pchunk, int64_t ichunk, __nv_bfloat16* __restrict__ outT) {
+  __shared__ float col[kKrpSmem];
+  const int r = blockIdx.y;
+  __nv_bfloat16* o = outT + (int64_t)r * Kstride;
+  const int last = fl.n - 1;
+  const int64_t sl = fl.dims[last];
+  const int64_t nib = (sl + ichunk - 1) / ichunk;      // i-blocks per prefix block
+  const int64_t pb = blockIdx.x / nib, ib = blockIdx.x % nib;
+  const int64_t p0 = pb * pchunk, p1 = min(nprefix, p0 + pchunk);
+  const int64_t i0 = ib * ichunk, i1 = min(sl, i0 + ichunk);
+  // zero padding k in [K, Kstride): taken by the first CTA of the row
+  if (blockIdx.x == 0)
+    for (int64_t k = K + threadIdx.x; k < Kstride; k += blockDim.x) o[k] = __float2bfloat16_rn(0.f);
+  if (r >= R) {
+    for (int64_t p = p0; p < p1; p++)
+      for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) o[p * sl + i] = __float2bfloat16_rn(0.f);
+    return;
+  }
+  const bool staged = (i1 - i0) <= kKrpSmem;
+  if (staged)
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) col[i - i0] = fl.A[last][i * R + r];
+  __syncthreads();
+  for (int64_t p = p0; p < p1; p++) {
+    float pf = 1.f;
+    if (last > 0) {
+      // decode p into the leading indices (last leading factor fastest)
+      uint32_t idx[kMaxModes];
+      uint32_t q = (uint32_t)p;
+      for (int j = last - 1; j >= 0; j--) {
+        const uint32_t d = (uint32_t)fl.dims[j];
+        idx[j] = q % d;
+        q /= d;
       }
+      pf = fl.A[0][(int64_t)idx[0] * R + r];
+      for (int j = 1; j < last; j++) pf *= fl.A[j][(int64_t)idx[j] * R + r];
     }
-    outT[i] = __float2bfloat16_rn(v);
+    __nv_bfloat16* op = o + p * sl;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const float a = staged ? col[i - i0] : fl.A[last][i * R + r];
+      op[i] = __float2bfloat16_rn(last > 0 ? pf * a : a);
+    }
   }
 }
 
@@ -291,6 +371,12 @@ __global__ void sum_parts_kernel(const double* __restrict__ part, int n, double*
 }  // namespace
 
 // ---------------------------------------------------------------- host wrappers
+template <typename T>
+void reduce_splits(const T* part, T* out, int64_t n, int splits, Launch L) {
+  reduce_splits_kernel<T><<<(unsigned)cdiv(n, 32), 256, 0, L.stream>>>(part, out, n, splits);
+  (*L.counter)++;
+}
+
 template <typename TX, typename T>
 void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K, int64_t M,
                int R, bool kmajor, int splits, Launch L) {
@@ -310,6 +396,13 @@ void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int6
 template <typename T>
 void ttv(const T* in, const T* A, T* out, int64_t outer, int sw, int64_t inner, int R, Launch L) {
   const int64_t QR = inner * R;
+  if (sizeof(T) == 4 && R % 4 == 0) {
+    const int64_t chunks = cdiv(QR, 128);
+    ttv4_kernel<<<(unsigned)(outer * chunks), kThreads, 0, L.stream>>>(
+        (const float*)in, (const float*)A, (float*)out, sw, QR, R, chunks);
+    (*L.counter)++;
+    return;
+  }
   const int64_t chunks = cdiv(QR, 32);
   ttv_kernel<T><<<(unsigned)(outer * chunks), kThreads, 0, L.stream>>>(in, A, out, sw, QR, R, chunks);
   (*L.counter)++;
@@ -349,8 +442,14 @@ void khatri_rao_bf16_t(const float* const* A, const int64_t* dims, int nm, int R
     fl.dims[i] = dims[i];
     K *= dims[i];
   }
-  khatri_rao_bf16_t_kernel<<<grid_for((int64_t)Rpad * Kstride, 256), 256, 0, L.stream>>>(
-      fl, R, Rpad, K, Kstride, outT);
+  const int64_t sl = dims[nm - 1];
+  const int64_t nprefix = K / sl;
+  const int64_t ichunk = std::min<int64_t>(sl, kKrpSmem);
+  const int64_t pchunk = std::max<int64_t>(1, 4096 / ichunk);
+  const int64_t blocks = cdiv(nprefix, pchunk) * cdiv(sl, ichunk);
+  dim3 grid((unsigned)blocks, (unsigned)Rpad);
+  khatri_rao_bf16_t_kernel<<<grid, 256, 0, L.stream>>>(fl, R, K, Kstride, nprefix, pchunk, ichunk,
+                                                      outT);
   (*L.counter)++;
 }
 
@@ -369,6 +468,8 @@ void sumsq(const TX* x, int64_t n, double* partials, double* out, Launch L) {
 }
 
 // ---------------------------------------------------------------- instantiations
+template void reduce_splits<float>(const float*, float*, int64_t, int, Launch);
+template void reduce_splits<double>(const double*, double*, int64_t, int, Launch);
 template void gemm_simt<double, double>(const double*, const double*, double*, double*, int64_t,
                                         int64_t, int64_t, int, bool, int, Launch);
 template void gemm_simt<float, float>(const float*, const float*, float*, float*, int64_t, int64_t,

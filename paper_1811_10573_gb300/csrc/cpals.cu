@@ -38,8 +38,9 @@ struct cpals_ctx {
 
   // streams and errors
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;       // Cholesky factorisations overlap the contractions
   cudaStream_t user = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
   std::string err;
 
   // tensor
@@ -65,7 +66,7 @@ struct cpals_ctx {
   void* krp = nullptr;   // max(PL, PR) x R
   void* tmp[2] = {nullptr, nullptr};
   void* rhs = nullptr;   // smax x R
-  double* rhs2 = nullptr;  // smax x R float64
+  void* rhs2 = nullptr;    // smax x R compute precision (allocated as float64)
   void* gpart = nullptr;   // split-K partials
   size_t gpart_bytes = 0;
   __nv_bfloat16* Bt = nullptr;   // MIXED: transposed bf16 B operand
@@ -75,6 +76,7 @@ struct cpals_ctx {
   double* scal = nullptr;        // device scalars
   double* scal_h = nullptr;      // pinned mirror
   int* status = nullptr;         // device status words
+  int* tickets = nullptr;        // per-tile completion tickets of the Gram kernel
   int* status_h = nullptr;
 
   // PP operators
@@ -100,6 +102,7 @@ struct cpals_ctx {
   int* umma_err = nullptr;
 
   Launch L() { return Launch{stream, &launches}; }
+  Launch Lside() { return Launch{side, &launches}; }
 
   cpals_status fail(cpals_status st, const std::string& msg) {
     err = msg;
@@ -258,22 +261,32 @@ const T* contract_chain(cpals_ctx* c, const T* in, std::vector<int> modes, int k
   return cur;
 }
 
-// Normal-equation update of mode n from right-hand side rhs (Algorithm 1
-// lines 5-10; Algorithm 3 lines 11-17 when pp).
+// Normal-equation update of mode n (Algorithm 1 lines 5-10; Algorithm 3 lines
+// 11-17 when pp), in two halves: factor_async factors Gamma^(n) on the side
+// stream (it needs only the Grams of the other modes), so it runs under the
+// contraction that forms the right-hand side; finish_mode joins and solves.
+void factor_async(cpals_ctx* c, int n, bool pp, bool useV) {
+  cudaEventRecord(c->ev_fork, c->stream);
+  cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+  gamma_chol(c->S, c->W, c->N, n, c->R, c->Lf, c->Z, pp && useV, c->status, c->Lside());
+  cudaEventRecord(c->ev_join, c->side);
+}
+
 template <typename T>
-void update_mode(cpals_ctx* c, int n, const T* rhs, bool pp, bool useV) {
+void finish_mode(cpals_ctx* c, int n, const T* rhs, bool pp, bool useV) {
   const int R = c->R;
   const int s = (int)c->dims[n];
   const bool v = pp && useV;
-  gamma_chol(c->S, c->W, c->N, n, R, c->Lf, c->Z, v, c->status, c->L());
+  cudaStreamWaitEvent(c->stream, c->ev_join, 0);
   if (v)
-    solve_rows_v<T>(rhs, c->A[n], c->Ap[n], c->dA[n], c->Lf, c->Z, c->rhs2, P<T>(c->Ac[n]),
+    solve_rows_v<T>(rhs, c->A[n], c->Ap[n], c->dA[n], c->Lf, c->Z, P<T>(c->rhs2), P<T>(c->Ac[n]),
                     P<T>(c->dAc[n]), c->rownorm, s, R, n, c->status, c->L());
   else
     solve_rows<T>(rhs, c->A[n], pp ? c->Ap[n] : nullptr, c->dA[n], c->Lf, P<T>(c->Ac[n]),
                   P<T>(c->dAc[n]), c->rownorm, s, R, n, c->status, c->L());
-  gram_update(c->A[n], c->dA[n], c->S + (int64_t)n * R * R, c->W + (int64_t)n * R * R, pp, s, R,
-              c->rownorm, c->scal + 8 + 2 * n, c->dpart, c->L());
+  gram_update<T>(c->A[n], P<const T>(c->Ac[n]), P<const T>(c->dAc[n]), c->S + (int64_t)n * R * R,
+                 c->W + (int64_t)n * R * R, pp, s, R, c->rownorm, c->scal + 8 + 2 * n, c->dpart,
+                 c->tickets, c->L());
 }
 
 // ---------------------------------------------------------------- ALS sweep
@@ -284,17 +297,21 @@ cpals_status als_sweep_launch(cpals_ctx* c) {
   for (int k = 0; k < h; k++) Lm.push_back(k);
   for (int k = h; k < N; k++) Rm.push_back(k);
   // left half: M^(L) = X_(L) (A^(h) (.) ... (.) A^(N-1))
+  factor_async(c, 0, false, false);
   CKS(contract_first<T>(c, h, N - h, c->Ac, P<T>(c->ML), 1, c->PR, c->PL, true));
   for (int n = 0; n < h; n++) {
+    if (n > 0) factor_async(c, n, false, false);
     const T* rhs = contract_chain<T>(c, P<const T>(c->ML), Lm, n, c->Ac, P<T>(c->rhs));
-    update_mode<T>(c, n, rhs, false, false);
+    finish_mode<T>(c, n, rhs, false, false);
   }
   // right half with the updated left factors: M^(Rt) = X_(L)^T (A^(0) (.) ... (.) A^(h-1))
+  factor_async(c, h, false, false);
   CKS(contract_first<T>(c, 0, h, c->Ac, P<T>(c->MR), 1, c->PL, c->PR, false));
   const T* last = nullptr;
   for (int n = h; n < N; n++) {
+    if (n > h) factor_async(c, n, false, false);
     last = contract_chain<T>(c, P<const T>(c->MR), Rm, n, c->Ac, P<T>(c->rhs));
-    update_mode<T>(c, n, last, false, false);
+    finish_mode<T>(c, n, last, false, false);
   }
   fitness<T>(last, c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->normX2, c->scal, c->dpart,
              c->L());
@@ -452,9 +469,10 @@ cpals_status pp_sweep_launch(cpals_ctx* c, bool useV) {
   const int N = c->N, R = c->R;
   PPTerm<T> terms[kMaxModes];
   for (int n = 0; n < N; n++) {
+    factor_async(c, n, true, useV);
     pp_terms<T>(c, n, terms);
     pp_correct<T>(P<const T>(c->Mp[n]), terms, N - 1, P<T>(c->rhs), (int)c->dims[n], R, c->L());
-    update_mode<T>(c, n, P<const T>(c->rhs), true, useV);
+    finish_mode<T>(c, n, P<const T>(c->rhs), true, useV);
   }
   // fitness estimate from M~^(N) (the last right-hand side, updated factors)
   fitness<T>(P<const T>(c->rhs), c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->normX2,
@@ -626,8 +644,11 @@ cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpal
     return st;
   };
   if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return bail(CPALS_E_CUDA);
   for (int i = 0; i < kEvPairs; i++)
     if (cudaEventCreate(&c->ev0[i]) != cudaSuccess || cudaEventCreate(&c->ev1[i]) != cudaSuccess)
@@ -674,15 +695,17 @@ cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpal
     AL(c->Bt, c->Bt_elems * 2);
   }
   AL(c->rownorm, (size_t)2 * c->smax * 8);
-  AL(c->dpart, (size_t)(2 * 152 + 64) * 1024 * 8);
+  AL(c->dpart, (size_t)std::max<int64_t>(2 * 152 + 64, cdiv(c->smax, 32) * 26 + 64) * 1024 * 8);
   AL(c->scal, 64 * 8);
   AL(c->status, 4 * sizeof(int));
+  AL(c->tickets, 64 * sizeof(int));
   c->umma_err = c->status + 1;
 #undef AL
   if (cudaMallocHost((void**)&c->scal_h, 64 * 8) != cudaSuccess ||
       cudaMallocHost((void**)&c->status_h, 4 * sizeof(int)) != cudaSuccess)
     return bail(CPALS_E_OOM);
   if (cudaMemset(c->scal, 0, 64 * 8) != cudaSuccess || cudaMemset(c->status, 0, 16) != cudaSuccess ||
+      cudaMemset(c->tickets, 0, 64 * sizeof(int)) != cudaSuccess ||
       cudaMemset(c->W, 0, (size_t)N * R * R * 8) != cudaSuccess)
     return bail(CPALS_E_CUDA);
   memset(c->scal_h, 0, 64 * 8);
@@ -693,6 +716,7 @@ cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpal
 void cpals_destroy(cpals_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->side) cudaStreamSynchronize(c->side);
   drop_graphs(c);
   auto F = [](void* p) {
     if (p) cudaFree(p);
@@ -706,7 +730,7 @@ void cpals_destroy(cpals_ctx* c) {
   for (void* p : c->lvl_bufs) F(p);
   F(c->S); F(c->W); F(c->Lf); F(c->Z); F(c->ML); F(c->MR); F(c->krp); F(c->tmp[0]); F(c->tmp[1]);
   F(c->rhs); F(c->rhs2); F(c->gpart); F(c->Bt); F(c->rownorm); F(c->dpart); F(c->scal);
-  F(c->status);
+  F(c->status); F(c->tickets);
   if (c->scal_h) cudaFreeHost(c->scal_h);
   if (c->status_h) cudaFreeHost(c->status_h);
   for (int i = 0; i < kEvPairs; i++) {
@@ -715,6 +739,9 @@ void cpals_destroy(cpals_ctx* c) {
   }
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -785,8 +812,14 @@ cpals_status cpals_init_factors(cpals_ctx* c, const double* const* factors) {
     CK(cudaMemcpyAsync(c->scal + 9 + 2 * n, c->scal + 8 + 2 * n, 8, cudaMemcpyDeviceToDevice, c->stream));
     // rownorm is not needed: gram_update reduces it into a scratch slot
     CK(cudaMemsetAsync(c->rownorm, 0, 2 * c->dims[n] * 8, c->stream));
-    gram_update(c->A[n], c->dA[n], c->S + (int64_t)n * R * R, c->W + (int64_t)n * R * R, false,
-                (int)c->dims[n], R, c->rownorm, c->scal + 48, c->dpart, c->L());
+    if (is64(c))
+      gram_update<double>(c->A[n], P<const double>(c->Ac[n]), P<const double>(c->dAc[n]),
+                          c->S + (int64_t)n * R * R, c->W + (int64_t)n * R * R, false,
+                          (int)c->dims[n], R, c->rownorm, c->scal + 48, c->dpart, c->tickets, c->L());
+    else
+      gram_update<float>(c->A[n], P<const float>(c->Ac[n]), P<const float>(c->dAc[n]),
+                         c->S + (int64_t)n * R * R, c->W + (int64_t)n * R * R, false,
+                         (int)c->dims[n], R, c->rownorm, c->scal + 48, c->dpart, c->tickets, c->L());
   }
   CK(cudaMemsetAsync(c->W, 0, (size_t)c->N * R * R * 8, c->stream));
   CKS(sync_read(c));
@@ -964,9 +997,9 @@ cpals_status cpals_pp_mttkrp(cpals_ctx* c, int n, int use_V, double* out) {
     const T* res = P<const T>(c->rhs);
     if (use_V) {
       gamma_chol(c->S, c->W, c->N, n, R, c->Lf, c->Z, true, c->status, c->L());
-      vterm<T>(P<const T>(c->rhs), c->A[n], c->Z, c->rhs2, s, R, c->L());
+      vterm<T>(P<const T>(c->rhs), P<const T>(c->Ac[n]), c->Z, P<T>(c->rhs2), s, R, c->L());
       CKS(sync_read(c));
-      return copy_out<double>(c, c->rhs2, cnt, out);
+      return copy_out<T>(c, P<const T>(c->rhs2), cnt, out);
     }
     CKS(sync_read(c));
     return copy_out<T>(c, res, cnt, out);

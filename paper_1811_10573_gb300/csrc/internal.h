@@ -27,6 +27,10 @@ template <typename TX, typename T>
 void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K, int64_t M,
                int R, bool kmajor, int splits, Launch L);
 
+// out[i] = sum_z part[z*n + i], deterministic order.
+template <typename T>
+void reduce_splits(const T* part, T* out, int64_t n, int splits, Launch L);
+
 // Multi-TTV (lower levels of the trees): out[o][q][r] = sum_x in[o][x][q][r] * A[x][r].
 template <typename T>
 void ttv(const T* in, const T* A, T* out, int64_t outer, int sw, int64_t inner, int R, Launch L);
@@ -75,22 +79,26 @@ void gamma_chol(const double* S, const double* W, int N, int n, int R, double* L
 template <typename T>
 void solve_rows(const T* rhs, double* A, const double* Aref, double* dA, const double* Lf, T* Ac,
                 T* dAc, double* rownorm, int s, int R, int n, const int* status, Launch L);
-// Same with the second-order PP terms: rhs2 = rhs + A_old Z (float64 scratch of
-// s*R values) is formed first.
+// Same with the second-order PP terms: rhs2 = rhs + A_old Z (compute precision,
+// s*R scratch values) is formed first from the compute copy Ac of A_old.
 template <typename T>
 void solve_rows_v(const T* rhs, double* A, const double* Aref, double* dA, const double* Lf,
-                  const double* Z, double* rhs2, T* Ac, T* dAc, double* rownorm, int s, int R,
-                  int n, const int* status, Launch L);
-// out[y][r] = rhs[y][r] + sum_k A[y][k] Z[k][r] in float64 (second-order PP terms).
+                  const double* Z, T* rhs2, T* Ac, T* dAc, double* rownorm, int s, int R, int n,
+                  const int* status, Launch L);
+// out[y][r] = rhs[y][r] + sum_k A[y][k] Z[k][r] in the compute precision.
 template <typename T>
-void vterm(const T* rhs, const double* A, const double* Z, double* out, int s, int R, Launch L);
+void vterm(const T* rhs, const T* A, const double* Z, T* out, int s, int R, Launch L);
 // Raise the dynamic shared-memory limits of the float64 kernels (call once per device).
 cudaError_t setup_small_kernels();
 
-// S = A^T A and (withW) W = A^T dA in float64; also reduces rownorm into
-// scal[0] = ||dA||^2, scal[1] = ||A||^2.  partials: workspace.
-void gram_update(const double* A, const double* dA, double* S, double* W, bool withW, int s,
-                 int R, const double* rownorm, double* scal, double* partials, Launch L);
+// S = A^T A in float64 and (withW) W = Ac^T dAc in the compute precision T;
+// also reduces rownorm into scal[0] = ||dA||^2, scal[1] = ||A||^2.
+// partials: ceil(s/32) * 26 * 1024 float64 scratch; tickets: 64 ints, zero
+// before the first launch (each launch leaves them zero).
+template <typename T>
+void gram_update(const double* A, const T* Ac, const T* dAc, double* S, double* W, bool withW,
+                 int s, int R, const double* rownorm, double* scal, double* partials, int* tickets,
+                 Launch L);
 
 // Fitness from the last mode's right-hand side (Sec. 5):
 // inner = sum rhs*A, model = sum_{r,r'} prod_k S_k, out[0] = fitness, out[1] = inner,

@@ -12,7 +12,8 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // ---------------------------------------------------------------- Gamma + Cholesky (+ Z)
 // One CTA: Gamma^(n) = Hadamard product of S^(k), k != n, then a right-looking
-// Cholesky Gamma = L L^T in shared memory.  With useV also
+// Cholesky Gamma = L L^T in shared memory (row stride RS = R|1, odd, so that
+// column accesses are free of bank conflicts).  With useV also
 // Z = sum_{i<j; i,j != n} W_i * W_j * (*_{k not in {i,j,n}} S_k) (Eq. 3's
 // V terms: sum V^(n,i,j) = A^(n) Z).
 __global__ void __launch_bounds__(512)
@@ -22,12 +23,14 @@ gamma_chol_kernel(const double* __restrict__ S, const double* __restrict__ W, in
   extern __shared__ double G[];
   __shared__ int bad;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int RR = R * R;
+  const int RS = R | 1;
   for (int idx = tid; idx < RR; idx += nt) {
     double g = 1.0;
     for (int k = 0; k < N; k++)
       if (k != n) g *= S[(int64_t)k * RR + idx];
-    G[idx] = g;
+    G[(idx / R) * RS + idx % R] = g;
     if (useV) {
       double z = 0.0;
       for (int i = 0; i < N; i++) {
@@ -43,24 +46,31 @@ gamma_chol_kernel(const double* __restrict__ S, const double* __restrict__ W, in
       Z[idx] = z;
     }
   }
+  __shared__ double il_sh;
   if (tid == 0) bad = 0;
   __syncthreads();
   for (int k = 0; k < R; k++) {
-    const double piv = G[k * R + k];
-    if (!(piv > 0.0) || !isfinite(piv)) {
-      if (tid == 0) bad = 1;
-      break;
+    // one thread takes the pivot's reciprocal square root (float64 division
+    // and square root are long sequences on the narrow FP64 pipe)
+    if (tid == 0) {
+      const double piv = G[k * RS + k];
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        bad = 1;
+      } else {
+        const double il = 1.0 / sqrt(piv);
+        il_sh = il;
+        G[k * RS + k] = piv * il;
+      }
     }
-    const double l = sqrt(piv);
-    const double il = 1.0 / l;
     __syncthreads();
-    if (tid == 0) G[k * R + k] = l;
-    for (int i = k + 1 + tid; i < R; i += nt) G[i * R + k] *= il;
+    if (bad) break;
+    const double il = il_sh;
+    for (int i = k + 1 + tid; i < R; i += nt) G[i * RS + k] *= il;
     __syncthreads();
-    const int m = R - k - 1;
-    for (int idx = tid; idx < m * m; idx += nt) {
-      const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-      if (j <= i) G[i * R + j] -= G[i * R + k] * G[j * R + k];
+    // trailing update of the lower triangle: one warp per row i, lanes over j
+    for (int i = k + 1 + warp; i < R; i += nw) {
+      const double lik = G[i * RS + k];
+      for (int j = k + 1 + lane; j <= i; j += 32) G[i * RS + j] = fma(-lik, G[j * RS + k], G[i * RS + j]);
     }
     __syncthreads();
   }
@@ -71,21 +81,28 @@ gamma_chol_kernel(const double* __restrict__ S, const double* __restrict__ W, in
   }
   for (int idx = tid; idx < RR; idx += nt) {
     const int i = idx / R, j = idx % R;
-    Lout[idx] = (j <= i) ? G[idx] : 0.0;
+    Lout[idx] = (j <= i) ? G[i * RS + j] : 0.0;
   }
 }
 
-// rhs2[y][r] = rhs[y][r] + sum_k A[y][k] Z[k][r]  (second-order PP terms)
+// rhs2[y][r] = rhs[y][r] + sum_k A[y][k] Z[k][r]  (second-order PP terms), in the
+// compute precision T (a second-order correction; float64 in FP64 mode).
 template <typename T>
-__global__ void vterm_kernel(const T* __restrict__ rhs, const double* __restrict__ A,
-                             const double* __restrict__ Z, double* __restrict__ out, int s, int R) {
+__global__ void __launch_bounds__(256)
+vterm_kernel(const T* __restrict__ rhs, const T* __restrict__ A, const double* __restrict__ Z,
+             T* __restrict__ out, int s, int R) {
+  extern __shared__ unsigned char zsm[];
+  T* Zs = reinterpret_cast<T*>(zsm);
+  for (int i = threadIdx.x; i < R * R; i += blockDim.x) Zs[i] = (T)Z[i];
+  __syncthreads();
   const int64_t n = (int64_t)s * R;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t y = i / R;
     const int r = (int)(i % R);
-    double acc = (double)rhs[i];
-    for (int k = 0; k < R; k++) acc = fma(A[y * R + k], Z[k * R + r], acc);
+    T acc = rhs[i];
+    const T* a = A + y * R;
+    for (int k = 0; k < R; k++) acc = fma(a[k], Zs[k * R + r], acc);
     out[i] = acc;
   }
 }
@@ -114,15 +131,16 @@ solve_rows_kernel(const TR* __restrict__ rhs, double* __restrict__ A,
                   const double* __restrict__ Aref, double* __restrict__ dA,
                   const double* __restrict__ Lg, T* __restrict__ Ac, T* __restrict__ dAc,
                   double* __restrict__ rownorm, int s, int R, int n, const int* __restrict__ status) {
-  extern __shared__ double Ls[];   // R*R lower factor, then R inverse diagonals
-  double* inv = Ls + R * R;
+  extern __shared__ double Ls[];   // R x RS lower factor (RS = R|1), then R inverse diagonals
+  const int RS = R | 1;
+  double* inv = Ls + R * RS;
   const bool failed = (status[0] >> n) & 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   if (!failed) {
-    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) Ls[idx] = Lg[idx];
+    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) Ls[(idx / R) * RS + idx % R] = Lg[idx];
     __syncthreads();
-    for (int i = threadIdx.x; i < R; i += blockDim.x) inv[i] = 1.0 / Ls[i * R + i];
+    for (int i = threadIdx.x; i < R; i += blockDim.x) inv[i] = 1.0 / Ls[i * RS + i];
     __syncthreads();
   }
   for (int y = blockIdx.x * nw + warp; y < s; y += gridDim.x * nw) {
@@ -143,8 +161,9 @@ solve_rows_kernel(const TR* __restrict__ rhs, double* __restrict__ A,
         if (lane == li) put(b, ci, zi);
 #pragma unroll
         for (int c = 0; c < kChunks; c++) {
+          if (32 * c + 31 <= i || 32 * c >= R) continue;     // warp-uniform: no lane of chunk c is updated
           const int r = lane + 32 * c;
-          if (r > i && r < R) b[c] = fma(-Ls[r * R + i], zi, b[c]);
+          if (r > i && r < R) b[c] = fma(-Ls[r * RS + i], zi, b[c]);
         }
       }
       for (int i = R - 1; i >= 0; i--) {
@@ -153,8 +172,9 @@ solve_rows_kernel(const TR* __restrict__ rhs, double* __restrict__ A,
         if (lane == li) put(b, ci, ai);
 #pragma unroll
         for (int c = 0; c < kChunks; c++) {
+          if (32 * c >= i) continue;                          // warp-uniform
           const int r = lane + 32 * c;
-          if (r < i) b[c] = fma(-Ls[i * R + r], ai, b[c]);
+          if (r < i) b[c] = fma(-Ls[i * RS + r], ai, b[c]);
         }
       }
     }
@@ -187,99 +207,126 @@ solve_rows_kernel(const TR* __restrict__ rhs, double* __restrict__ A,
 }
 
 // ---------------------------------------------------------------- Grams
-// partials[z][tile][32][32]: tile t < ntS is an upper block (ti <= tj) of A^T A,
-// the rest are blocks of A^T dA.  Rows [z*chunk, (z+1)*chunk).
+// One launch: CTA (z, t) forms the partial tile t over rows [z*chunk,
+// (z+1)*chunk) and the last CTA to finish a tile (per-tile ticket) sums that
+// tile's partials in split order (deterministic) and writes it.  Tile t < ntS
+// is an upper block (ti <= tj) of S = A^T A (float64); the others are blocks
+// of W = Aw^T dAw in the compute precision TW (W only feeds the second-order
+// PP terms).  The CTA that finishes last overall also reduces the per-row
+// norms.  Tickets are reset by their last CTA, ready for the next launch.
+template <typename TW>
 __global__ void __launch_bounds__(256)
-gram_part_kernel(const double* __restrict__ A, const double* __restrict__ dA, int s, int R,
-                 int nb, int ntS, int ntiles, int chunk, double* __restrict__ part) {
+gram_kernel(const double* __restrict__ A, const TW* __restrict__ Aw, const TW* __restrict__ dAw,
+            int s, int R, int nb, int ntS, int ntiles, int splits, int chunk,
+            double* __restrict__ part, int* __restrict__ tickets, double* __restrict__ S,
+            double* __restrict__ W, const double* __restrict__ rownorm, double* __restrict__ scal) {
   const int t = blockIdx.x % ntiles;
   const int z = blockIdx.x / ntiles;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int y0 = z * chunk, y1 = min(s, y0 + chunk);
+  double* p = part + ((int64_t)z * ntiles + t) * 1024;
   int ti, tj;
-  const double* Bm;
   if (t < ntS) {
     int tt = t;
     ti = 0;
     while (tt >= nb - ti) { tt -= nb - ti; ti++; }
     tj = ti + tt;
-    Bm = A;
-  } else {
-    ti = (t - ntS) / nb;
-    tj = (t - ntS) % nb;
-    Bm = dA;
-  }
-  __shared__ double As[32][33], Bs[32][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  const int y0 = z * chunk, y1 = min(s, y0 + chunk);
-  for (int yb = y0; yb < y1; yb += 32) {
-    for (int idx = threadIdx.x; idx < 32 * 32; idx += 256) {
-      const int yy = idx / 32, c = idx % 32;
-      const int y = yb + yy;
-      const int ci = ti * 32 + c, cj = tj * 32 + c;
-      As[yy][c] = (y < y1 && ci < R) ? A[(int64_t)y * R + ci] : 0.0;
-      Bs[yy][c] = (y < y1 && cj < R) ? Bm[(int64_t)y * R + cj] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int yy = 0; yy < 32; yy++) {
-      const double bj = Bs[yy][tx];
-#pragma unroll
-      for (int q = 0; q < 4; q++) acc[q] = fma(As[yy][ty + 8 * q], bj, acc[q]);
-    }
-    __syncthreads();
-  }
-  double* p = part + ((int64_t)z * ntiles + t) * 1024;
-#pragma unroll
-  for (int q = 0; q < 4; q++) p[(ty + 8 * q) * 32 + tx] = acc[q];
-}
-
-__global__ void gram_reduce_kernel(const double* __restrict__ part, int R, int nb, int ntS,
-                                   int ntiles, int splits, bool withW, double* __restrict__ S,
-                                   double* __restrict__ W, const double* __restrict__ rownorm,
-                                   int s, double* __restrict__ scal) {
-  const int nt_use = withW ? ntiles : ntS;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nt_use * 1024;
-       idx += gridDim.x * blockDim.x) {
-    const int t = idx / 1024, e = idx % 1024;
-    double acc = 0.0;
-    for (int z = 0; z < splits; z++) acc += part[((int64_t)z * ntiles + t) * 1024 + e];
-    const int li = e / 32, lj = e % 32;
-    if (t < ntS) {
-      int tt = t, ti = 0;
-      while (tt >= nb - ti) { tt -= nb - ti; ti++; }
-      const int tj = ti + tt;
-      const int i = ti * 32 + li, j = tj * 32 + lj;
-      if (i < R && j < R) {
-        S[i * R + j] = acc;
-        S[j * R + i] = acc;
+    __shared__ double As[32][33], Bs[32][33];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int yb = y0; yb < y1; yb += 32) {
+      for (int idx = threadIdx.x; idx < 32 * 32; idx += 256) {
+        const int yy = idx / 32, c = idx % 32;
+        const int y = yb + yy;
+        const int ci = ti * 32 + c, cj = tj * 32 + c;
+        As[yy][c] = (y < y1 && ci < R) ? A[(int64_t)y * R + ci] : 0.0;
+        Bs[yy][c] = (y < y1 && cj < R) ? A[(int64_t)y * R + cj] : 0.0;
       }
-    } else {
-      const int ti = (t - ntS) / nb, tj = (t - ntS) % nb;
-      const int i = ti * 32 + li, j = tj * 32 + lj;
-      if (i < R && j < R) W[i * R + j] = acc;
-    }
-  }
-  if (blockIdx.x == 0) {
-    __shared__ double rd[256], ra[256];
-    double a = 0.0, b = 0.0;
-    for (int y = threadIdx.x; y < s; y += blockDim.x) {
-      a += rownorm[2 * y];
-      b += rownorm[2 * y + 1];
-    }
-    rd[threadIdx.x] = a;
-    ra[threadIdx.x] = b;
-    __syncthreads();
-    for (int st = 128; st > 0; st >>= 1) {
-      if ((int)threadIdx.x < st) {
-        rd[threadIdx.x] += rd[threadIdx.x + st];
-        ra[threadIdx.x] += ra[threadIdx.x + st];
+      __syncthreads();
+#pragma unroll 8
+      for (int yy = 0; yy < 32; yy++) {
+        const double bj = Bs[yy][tx];
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[q] = fma(As[yy][ty + 8 * q], bj, acc[q]);
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) {
-      scal[0] = rd[0];
-      scal[1] = ra[0];
+#pragma unroll
+    for (int q = 0; q < 4; q++) p[(ty + 8 * q) * 32 + tx] = acc[q];
+  } else {
+    ti = (t - ntS) / nb;
+    tj = (t - ntS) % nb;
+    __shared__ TW Aws[32][33], Bws[32][33];
+    TW acc[4] = {TW(0), TW(0), TW(0), TW(0)};
+    for (int yb = y0; yb < y1; yb += 32) {
+      for (int idx = threadIdx.x; idx < 32 * 32; idx += 256) {
+        const int yy = idx / 32, c = idx % 32;
+        const int y = yb + yy;
+        const int ci = ti * 32 + c, cj = tj * 32 + c;
+        Aws[yy][c] = (y < y1 && ci < R) ? Aw[(int64_t)y * R + ci] : TW(0);
+        Bws[yy][c] = (y < y1 && cj < R) ? dAw[(int64_t)y * R + cj] : TW(0);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int yy = 0; yy < 32; yy++) {
+        const TW bj = Bws[yy][tx];
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[q] = fma(Aws[yy][ty + 8 * q], bj, acc[q]);
+      }
+      __syncthreads();
     }
+#pragma unroll
+    for (int q = 0; q < 4; q++) p[(ty + 8 * q) * 32 + tx] = (double)acc[q];
+  }
+  // ---- last CTA of this tile reduces it
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&tickets[t], 1) == splits - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int e = threadIdx.x; e < 1024; e += 256) {
+    double acc = 0.0;
+    for (int zz = 0; zz < splits; zz++) acc += __ldcg(part + ((int64_t)zz * ntiles + t) * 1024 + e);
+    const int i = ti * 32 + e / 32, j = tj * 32 + e % 32;
+    if (i < R && j < R) {
+      if (t < ntS) {
+        S[i * R + j] = acc;
+        S[j * R + i] = acc;
+      } else {
+        W[i * R + j] = acc;
+      }
+    }
+  }
+  __shared__ int lastall;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tickets[t] = 0;
+    lastall = (atomicAdd(&tickets[63], 1) == ntiles - 1);
+  }
+  __syncthreads();
+  if (!lastall) return;
+  // ---- the last tile to finish reduces the per-row norms
+  __shared__ double rd[256], ra[256];
+  double a = 0.0, bsum = 0.0;
+  for (int y = threadIdx.x; y < s; y += blockDim.x) {
+    a += __ldcg(rownorm + 2 * y);
+    bsum += __ldcg(rownorm + 2 * y + 1);
+  }
+  rd[threadIdx.x] = a;
+  ra[threadIdx.x] = bsum;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      rd[threadIdx.x] += rd[threadIdx.x + st];
+      ra[threadIdx.x] += ra[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    scal[0] = rd[0];
+    scal[1] = ra[0];
+    tickets[63] = 0;
   }
 }
 
@@ -318,12 +365,24 @@ __global__ void fitness_part_kernel(const T* __restrict__ rhs, const double* __r
 
 __global__ void fitness_final_kernel(const double* __restrict__ part, int nparts, double normX2,
                                      double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double inner = 0.0, model = 0.0;
-    for (int i = 0; i < nparts; i++) {
-      inner += part[2 * i];
-      model += part[2 * i + 1];
+  __shared__ double ra[256], rb[256];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
+  }
+  ra[threadIdx.x] = a;
+  rb[threadIdx.x] = b;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      ra[threadIdx.x] += ra[threadIdx.x + st];
+      rb[threadIdx.x] += rb[threadIdx.x + st];
     }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double inner = ra[0], model = rb[0];
     const double res2 = normX2 - 2.0 * inner + model;
     out[0] = 1.0 - sqrt(fmax(res2, 0.0)) / sqrt(normX2);
     out[1] = inner;
@@ -335,8 +394,10 @@ __global__ void fitness_final_kernel(const double* __restrict__ part, int nparts
 
 // ---------------------------------------------------------------- host wrappers
 cudaError_t setup_small_kernels() {
-  const int g = (int)(kMaxRank * kMaxRank * sizeof(double));
-  const int sv = (int)((kMaxRank * kMaxRank + kMaxRank) * sizeof(double));
+  const int RSmax = kMaxRank | 1;
+  const int g = (int)(kMaxRank * RSmax * sizeof(double));
+  const int sv = (int)((kMaxRank * RSmax + kMaxRank) * sizeof(double));
+  const int vz = (int)(kMaxRank * kMaxRank * sizeof(double));
   cudaError_t e = cudaFuncSetAttribute(gamma_chol_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, g);
   if (e == cudaSuccess)
@@ -346,26 +407,27 @@ cudaError_t setup_small_kernels() {
     e = cudaFuncSetAttribute(solve_rows_kernel<float, float>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sv);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(solve_rows_kernel<double, float>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, sv);
+    e = cudaFuncSetAttribute(vterm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, vz);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(vterm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, vz);
   return e;
 }
 
 void gamma_chol(const double* S, const double* W, int N, int n, int R, double* Lout, double* Z,
                 bool useV, int* status, Launch L) {
-  const size_t smem = (size_t)R * R * sizeof(double);
+  const size_t smem = (size_t)R * (R | 1) * sizeof(double);
   gamma_chol_kernel<<<1, 512, smem, L.stream>>>(S, W, N, n, R, Lout, Z, useV ? 1 : 0, status);
   (*L.counter)++;
 }
 
-template <typename TR, typename T>
-static void solve_launch(const TR* rhs, double* A, const double* Aref, double* dA, const double* Lf,
+template <typename T>
+static void solve_launch(const T* rhs, double* A, const double* Aref, double* dA, const double* Lf,
                          T* Ac, T* dAc, double* rownorm, int s, int R, int n, const int* status,
                          Launch L) {
-  const size_t smem = (size_t)(R * R + R) * sizeof(double);
-  const int rows_per_block = 4;
-  const int blocks = (int)std::min<int64_t>(cdiv(s, rows_per_block), 152 * 2);
-  solve_rows_kernel<TR, T><<<blocks, 32 * rows_per_block, smem, L.stream>>>(
+  const size_t smem = (size_t)(R * (R | 1) + R) * sizeof(double);
+  const int rows_per_block = 2;      // spread the rows over all SMs
+  const int blocks = (int)std::min<int64_t>(cdiv(s, rows_per_block), 152 * 4);
+  solve_rows_kernel<T, T><<<blocks, 32 * rows_per_block, smem, L.stream>>>(
       rhs, A, Aref, dA, Lf, Ac, dAc, rownorm, s, R, n, status);
   (*L.counter)++;
 }
@@ -373,41 +435,38 @@ static void solve_launch(const TR* rhs, double* A, const double* Aref, double* d
 template <typename T>
 void solve_rows(const T* rhs, double* A, const double* Aref, double* dA, const double* Lf, T* Ac,
                 T* dAc, double* rownorm, int s, int R, int n, const int* status, Launch L) {
-  solve_launch<T, T>(rhs, A, Aref, dA, Lf, Ac, dAc, rownorm, s, R, n, status, L);
+  solve_launch<T>(rhs, A, Aref, dA, Lf, Ac, dAc, rownorm, s, R, n, status, L);
+}
+
+template <typename T>
+void vterm(const T* rhs, const T* A, const double* Z, T* out, int s, int R, Launch L) {
+  const int64_t tot = (int64_t)s * R;
+  vterm_kernel<T><<<(int)std::min<int64_t>(cdiv(tot, 256), 152 * 2), 256,
+                    (size_t)R * R * sizeof(T), L.stream>>>(rhs, A, Z, out, s, R);
+  (*L.counter)++;
 }
 
 template <typename T>
 void solve_rows_v(const T* rhs, double* A, const double* Aref, double* dA, const double* Lf,
-                  const double* Z, double* rhs2, T* Ac, T* dAc, double* rownorm, int s, int R,
-                  int n, const int* status, Launch L) {
-  const int64_t tot = (int64_t)s * R;
-  vterm_kernel<T><<<(int)std::min<int64_t>(cdiv(tot, 256), 152 * 8), 256, 0, L.stream>>>(
-      rhs, A, Z, rhs2, s, R);
-  (*L.counter)++;
-  solve_launch<double, T>(rhs2, A, Aref, dA, Lf, Ac, dAc, rownorm, s, R, n, status, L);
+                  const double* Z, T* rhs2, T* Ac, T* dAc, double* rownorm, int s, int R, int n,
+                  const int* status, Launch L) {
+  vterm<T>(rhs, Ac, Z, rhs2, s, R, L);
+  solve_launch<T>(rhs2, A, Aref, dA, Lf, Ac, dAc, rownorm, s, R, n, status, L);
 }
 
 template <typename T>
-void vterm(const T* rhs, const double* A, const double* Z, double* out, int s, int R, Launch L) {
-  const int64_t tot = (int64_t)s * R;
-  vterm_kernel<T><<<(int)std::min<int64_t>(cdiv(tot, 256), 152 * 8), 256, 0, L.stream>>>(
-      rhs, A, Z, out, s, R);
-  (*L.counter)++;
-}
-
-void gram_update(const double* A, const double* dA, double* S, double* W, bool withW, int s,
-                 int R, const double* rownorm, double* scal, double* partials, Launch L) {
+void gram_update(const double* A, const T* Ac, const T* dAc, double* S, double* W, bool withW,
+                 int s, int R, const double* rownorm, double* scal, double* partials, int* tickets,
+                 Launch L) {
   const int nb = (R + 31) / 32;
   const int ntS = nb * (nb + 1) / 2;
   const int ntiles = withW ? ntS + nb * nb : ntS;
-  int splits = std::max(1, std::min((2 * 152) / ntiles, (s + 31) / 32));
-  const int chunk = (int)cdiv(cdiv(s, splits), 32) * 32;
-  splits = (int)cdiv(s, chunk);
-  gram_part_kernel<<<ntiles * splits, 256, 0, L.stream>>>(A, dA, s, R, nb, ntS, ntiles, chunk,
-                                                          partials);
-  gram_reduce_kernel<<<std::max(1, ntiles * 4), 256, 0, L.stream>>>(
-      partials, R, nb, ntS, ntiles, splits, withW, S, W, rownorm, s, scal);
-  (*L.counter) += 2;
+  const int chunk = 32;
+  const int splits = (int)cdiv(s, chunk);
+  gram_kernel<T><<<ntiles * splits, 256, 0, L.stream>>>(A, Ac, dAc, s, R, nb, ntS, ntiles, splits,
+                                                        chunk, partials, tickets, S, W, rownorm,
+                                                        scal);
+  (*L.counter) += 1;
 }
 
 template <typename T>
@@ -415,25 +474,23 @@ void fitness(const T* rhs, const double* A, const double* S, int N, int R, int s
              double* out, double* partials, Launch L) {
   const int blocks = 128;
   fitness_part_kernel<T><<<blocks, 256, 0, L.stream>>>(rhs, A, S, N, R, s, partials);
-  fitness_final_kernel<<<1, 32, 0, L.stream>>>(partials, blocks, normX2, out);
+  fitness_final_kernel<<<1, 128, 0, L.stream>>>(partials, blocks, normX2, out);
   (*L.counter) += 2;
 }
 
-template void solve_rows<double>(const double*, double*, const double*, double*, const double*,
-                                 double*, double*, double*, int, int, int, const int*, Launch);
-template void solve_rows<float>(const float*, double*, const double*, double*, const double*,
-                                float*, float*, double*, int, int, int, const int*, Launch);
-template void solve_rows_v<double>(const double*, double*, const double*, double*, const double*,
-                                   const double*, double*, double*, double*, double*, int, int,
-                                   int, const int*, Launch);
-template void solve_rows_v<float>(const float*, double*, const double*, double*, const double*,
-                                  const double*, double*, float*, float*, double*, int, int, int,
-                                  const int*, Launch);
-template void vterm<double>(const double*, const double*, const double*, double*, int, int, Launch);
-template void vterm<float>(const float*, const double*, const double*, double*, int, int, Launch);
-template void fitness<double>(const double*, const double*, const double*, int, int, int, double,
-                              double*, double*, Launch);
-template void fitness<float>(const float*, const double*, const double*, int, int, int, double,
-                             double*, double*, Launch);
+#define INST(T)                                                                                 \
+  template void solve_rows<T>(const T*, double*, const double*, double*, const double*, T*, T*, \
+                              double*, int, int, int, const int*, Launch);                      \
+  template void solve_rows_v<T>(const T*, double*, const double*, double*, const double*,       \
+                                const double*, T*, T*, T*, double*, int, int, int, const int*,  \
+                                Launch);                                                        \
+  template void vterm<T>(const T*, const T*, const double*, T*, int, int, Launch);              \
+  template void gram_update<T>(const double*, const T*, const T*, double*, double*, bool, int,  \
+                               int, const double*, double*, double*, int*, Launch);             \
+  template void fitness<T>(const T*, const double*, const double*, int, int, int, double,       \
+                           double*, double*, Launch);
+INST(double)
+INST(float)
+#undef INST
 
 }  // namespace cpals

@@ -157,6 +157,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 struct UmmaParams {
   int64_t batch, K, M;
   int R, Rpad, splits, stages;
+  int RS;               // row stride (floats) of the epilogue staging tile
   int64_t kchunk;       // multiple of BK
   int64_t mtiles, units;
   float* out;           // out or partials ([z][b][m][r])
@@ -325,8 +326,14 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     }
   } else {
     // ------------------------------------------------ epilogue (warps 2..5)
+    // TMEM -> registers -> shared staging tile (row stride RS, RS/4 odd: the
+    // 16-byte stores of 8 consecutive rows hit distinct banks) -> coalesced
+    // row copies to global (the 128 x R tile is contiguous there).
+    float* stg = reinterpret_cast<float*>(smem_raw + (base - smem_u32(smem_raw)) +
+                                          (size_t)S * stage_bytes);
     const int q = warp & 3;                   // TMEM lane quarter this warp may access
     const int row = q * 32 + lane;
+    const int ew = warp - 2;
     int t = 0;
     for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x, t++) {
       const int64_t mt = u % p.mtiles;
@@ -349,21 +356,30 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       }
       __syncwarp();
       tc_fence_after();
-      const int64_t m = mt * BM + row;
-      float* orow = p.out + (((int64_t)z * p.batch + b) * p.M + m) * p.R;
       const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 128);
+      float* srow = stg + row * p.RS;
       for (int c = 0; c < p.Rpad; c += 16) {
         float v[16];
         tmem_ld16(taddr + c, v);
-        if (m < p.M) {
 #pragma unroll
-          for (int i = 0; i < 16; i++)
-            if (c + i < p.R) orow[c + i] = v[i];
-        }
+        for (int g4 = 0; g4 < 4; g4++)
+          if (c + 4 * g4 < p.RS)
+            *reinterpret_cast<float4*>(srow + c + 4 * g4) =
+                make_float4(v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&acce_bar[buf]));
+      if (lane == 0) mbar_arrive(smem_u32(&acce_bar[buf]));   // accumulator free for the MMA warp
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      const int64_t m0 = mt * BM;
+      const int rows = (int)min((int64_t)BM, p.M - m0);
+      float* gout = p.out + (((int64_t)z * p.batch + b) * p.M + m0) * p.R;
+      for (int r2 = ew; r2 < rows; r2 += 4) {
+        const float* sr = stg + r2 * p.RS;
+        float* gr = gout + (int64_t)r2 * p.R;
+        for (int col = lane; col < p.R; col += 32) gr[col] = sr[col];
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
     }
   }
 
@@ -374,16 +390,6 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem_base)
                  : "memory");
-  }
-}
-
-__global__ void reduce_splits_f32(const float* __restrict__ part, float* __restrict__ out,
-                                  int64_t n, int splits) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float acc = part[i];
-    for (int z = 1; z < splits; z++) acc += part[(int64_t)z * n + i];
-    out[i] = acc;
   }
 }
 
@@ -425,7 +431,7 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 }  // namespace
 
 cudaError_t setup_umma_kernels() {
-  const int smem = 200 * 1024 + 1024;
+  const int smem = 227 * 1024 - 1024;
   cudaError_t e = cudaFuncSetAttribute(umma_gemm_kernel<true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
@@ -495,8 +501,14 @@ cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, flo
   p.err = err_flag;
   p.out = p.splits > 1 ? partials : out;
   const int stage_bytes = A_STAGE_BYTES + Rpad * BK * 2;
-  p.stages = std::min(8, (200 * 1024) / stage_bytes);
-  const size_t smem = (size_t)p.stages * stage_bytes + 1024;
+  int RS = (R + 3) / 4 * 4;
+  if (((RS / 4) & 1) == 0) RS += 4;
+  p.RS = RS;
+  const int staging = BM * RS * 4;
+  const int budget = 227 * 1024 - 2048;
+  p.stages = std::min(8, (budget - staging) / stage_bytes);
+  if (p.stages < 2) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)p.stages * stage_bytes + staging + 1024;
   const int grid = (int)std::min<int64_t>(p.units, num_sms());
 
   cudaError_t e;
@@ -508,10 +520,7 @@ cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, flo
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (p.splits > 1) {
-    const int64_t n = batch * M * R;
-    const int blocks = (int)std::min<int64_t>(cdiv(n, 256), 152 * 16);
-    reduce_splits_f32<<<blocks, 256, 0, L.stream>>>(partials, out, n, p.splits);
-    (*L.counter)++;
+    reduce_splits<float>(partials, out, batch * M * R, p.splits, L);
     e = cudaGetLastError();
   }
   return e;

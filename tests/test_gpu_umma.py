@@ -34,13 +34,13 @@ def bf16(a):
 
 
 def krp32(mats):
-    """Khatri-Rao product of float32 factors with the library's product order
-    (last factor first), in float32."""
+    """Khatri-Rao product of float32 factors in the library's order: the
+    leading factors multiplied left to right, then the last one, in float32."""
     R = mats[0].shape[1]
     rows = int(np.prod([m.shape[0] for m in mats]))
     idx = np.indices([m.shape[0] for m in mats]).reshape(len(mats), rows)
-    v = np.ones((rows, R), dtype=np.float32)
-    for j in range(len(mats) - 1, -1, -1):
+    v = mats[0].astype(np.float32)[idx[0]]
+    for j in range(1, len(mats)):
         v = (v * mats[j].astype(np.float32)[idx[j]]).astype(np.float32)
     return v
 
