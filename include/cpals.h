@@ -148,6 +148,12 @@ cpals_status cpals_get_operator(cpals_ctx* ctx, int i, int n, double* out);
  * out: s_n x R float64 host buffer. */
 cpals_status cpals_pp_mttkrp(cpals_ctx* ctx, int n, int use_V, double* out);
 
+/* Solve X Gamma^(n) = rhs (Sec. 2.3 normal equations) with the Grams the
+ * context currently holds, through the same factorisation and row-solve
+ * kernels as a sweep, without changing any state.  rhs, out: s_n x R float64
+ * host buffers.  CPALS_E_SINGULAR if Gamma^(n) is not positive definite. */
+cpals_status cpals_normal_solve(cpals_ctx* ctx, int n, const double* rhs, double* out);
+
 /* Copy A_p^(n) (which = 0) or dA^(n) (which = 1) to a host float64 buffer. */
 cpals_status cpals_get_state(cpals_ctx* ctx, int which, int n, double* out);
 

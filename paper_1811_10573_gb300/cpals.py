@@ -46,6 +46,7 @@ _SIGS = {
     "cpals_get_operator": (C.c_int, [_ctx_p, C.c_int, C.c_int, _dp]),
     "cpals_pp_mttkrp": (C.c_int, [_ctx_p, C.c_int, C.c_int, _dp]),
     "cpals_get_state": (C.c_int, [_ctx_p, C.c_int, C.c_int, _dp]),
+    "cpals_normal_solve": (C.c_int, [_ctx_p, C.c_int, _dp, _dp]),
     "cpals_set_profiling": (C.c_int, [_ctx_p, C.c_int]),
     "cpals_reset_stats": (C.c_int, [_ctx_p]),
     "cpals_get_stats": (C.c_int, [_ctx_p, C.c_int, _i64p, _dp, _dp, _dp]),
@@ -154,6 +155,10 @@ def cpals_get_operator(ctx, i, n, out):
 
 def cpals_pp_mttkrp(ctx, n, use_V, out):
     return lib().cpals_pp_mttkrp(ctx, n, use_V, _dptr(out))
+
+
+def cpals_normal_solve(ctx, n, rhs, out):
+    return lib().cpals_normal_solve(ctx, n, _dptr(rhs), _dptr(out))
 
 
 def cpals_get_state(ctx, which, n, out):
@@ -299,6 +304,12 @@ class CPALS:
     def pp_mttkrp(self, n, use_V=True):
         out = np.empty((self.dims[n], self.R))
         self._ck(cpals_pp_mttkrp(self.ctx, n, 1 if use_V else 0, out))
+        return out
+
+    def normal_solve(self, n, rhs):
+        rhs = _f64(rhs)
+        out = np.empty((self.dims[n], self.R))
+        self._ck(cpals_normal_solve(self.ctx, n, rhs, out))
         return out
 
     def get_state(self, which, n):

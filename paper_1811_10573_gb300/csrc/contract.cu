@@ -278,7 +278,8 @@ constexpr int kKrpSmem = 8192;   // floats of the staged last column
 
 __global__ void __launch_bounds__(256)
 khatri_rao_bf16_t_kernel(FactorList<float> fl, int R, int64_t K, int64_t Kstride, int64_t nprefix,
-                         int64_t pchunk, int64_t ichunk, __nv_bfloat16* __restrict__ outT) {
+                         int64_t pchunk, int64_t ichunk, int64_t lo_off,
+                         __nv_bfloat16* __restrict__ outT) {
   __shared__ float col[kKrpSmem];
   const int r = blockIdx.y;
   __nv_bfloat16* o = outT + (int64_t)r * Kstride;
@@ -290,10 +291,16 @@ khatri_rao_bf16_t_kernel(FactorList<float> fl, int R, int64_t K, int64_t Kstride
   const int64_t i0 = ib * ichunk, i1 = min(sl, i0 + ichunk);
   // zero padding k in [K, Kstride): taken by the first CTA of the row
   if (blockIdx.x == 0)
-    for (int64_t k = K + threadIdx.x; k < Kstride; k += blockDim.x) o[k] = __float2bfloat16_rn(0.f);
+    for (int64_t k = K + threadIdx.x; k < Kstride; k += blockDim.x) {
+      o[k] = __float2bfloat16_rn(0.f);
+      o[lo_off + k] = __float2bfloat16_rn(0.f);
+    }
   if (r >= R) {
     for (int64_t p = p0; p < p1; p++)
-      for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) o[p * sl + i] = __float2bfloat16_rn(0.f);
+      for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        o[p * sl + i] = __float2bfloat16_rn(0.f);
+        o[lo_off + p * sl + i] = __float2bfloat16_rn(0.f);
+      }
     return;
   }
   const bool staged = (i1 - i0) <= kKrpSmem;
@@ -315,9 +322,13 @@ khatri_rao_bf16_t_kernel(FactorList<float> fl, int R, int64_t K, int64_t Kstride
       for (int j = 1; j < last; j++) pf *= fl.A[j][(int64_t)idx[j] * R + r];
     }
     __nv_bfloat16* op = o + p * sl;
+    __nv_bfloat16* opl = op + lo_off;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       const float a = staged ? col[i - i0] : fl.A[last][i * R + r];
-      op[i] = __float2bfloat16_rn(last > 0 ? pf * a : a);
+      const float v = last > 0 ? pf * a : a;
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      op[i] = h;
+      opl[i] = __float2bfloat16_rn(v - __bfloat162float(h));
     }
   }
 }
@@ -449,7 +460,7 @@ void khatri_rao_bf16_t(const float* const* A, const int64_t* dims, int nm, int R
   const int64_t blocks = cdiv(nprefix, pchunk) * cdiv(sl, ichunk);
   dim3 grid((unsigned)blocks, (unsigned)Rpad);
   khatri_rao_bf16_t_kernel<<<grid, 256, 0, L.stream>>>(fl, R, K, Kstride, nprefix, pchunk, ichunk,
-                                                      outT);
+                                                      (int64_t)Rpad * Kstride, outT);
   (*L.counter)++;
 }
 

@@ -55,6 +55,16 @@ struct cpals_ctx {
   double* dA[kMaxModes] = {nullptr};
   void* Ac[kMaxModes] = {nullptr};
   void* dAc[kMaxModes] = {nullptr};
+  bool dfm = false;      // FP32/mixed: double-float normal-equation kernels
+  float* Alo[kMaxModes] = {nullptr};
+  float* Aphi[kMaxModes] = {nullptr};
+  float* Aplo[kMaxModes] = {nullptr};
+  float* Shi = nullptr;  // N*R*R
+  float* Slo = nullptr;
+  float* Wf = nullptr;   // N*R*R (float W for the df path)
+  float2* Ldf = nullptr; // R*R
+  float2* invd = nullptr;
+  float* Zf = nullptr;   // R*R
   double* S = nullptr;   // N*R*R
   double* W = nullptr;   // N*R*R
   double* Lf = nullptr;  // R*R
@@ -72,6 +82,7 @@ struct cpals_ctx {
   __nv_bfloat16* Bt = nullptr;   // MIXED: transposed bf16 B operand
   size_t Bt_elems = 0;
   double* rownorm = nullptr;     // 2*smax
+  double* dscr[2] = {nullptr, nullptr};   // smax x R float64 scratch (inspection solves)
   double* dpart = nullptr;       // float64 partials (Grams, fitness, norms)
   double* scal = nullptr;        // device scalars
   double* scal_h = nullptr;      // pinned mirror
@@ -268,7 +279,11 @@ const T* contract_chain(cpals_ctx* c, const T* in, std::vector<int> modes, int k
 void factor_async(cpals_ctx* c, int n, bool pp, bool useV) {
   cudaEventRecord(c->ev_fork, c->stream);
   cudaStreamWaitEvent(c->side, c->ev_fork, 0);
-  gamma_chol(c->S, c->W, c->N, n, c->R, c->Lf, c->Z, pp && useV, c->status, c->Lside());
+  if (c->dfm)
+    chol_df(c->Shi, c->Slo, c->Wf, c->N, n, c->R, c->Ldf, c->invd, c->Zf, pp && useV, c->status,
+            c->Lside());
+  else
+    gamma_chol(c->S, c->W, c->N, n, c->R, c->Lf, c->Z, pp && useV, c->status, c->Lside());
   cudaEventRecord(c->ev_join, c->side);
 }
 
@@ -277,16 +292,26 @@ void finish_mode(cpals_ctx* c, int n, const T* rhs, bool pp, bool useV) {
   const int R = c->R;
   const int s = (int)c->dims[n];
   const bool v = pp && useV;
+  const int64_t off = (int64_t)n * R * R;
   cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+  if (c->dfm) {
+    float* Ahi = P<float>(c->Ac[n]);
+    solve_df((const float*)rhs, c->A[n], Ahi, c->Alo[n], pp ? c->Aphi[n] : nullptr,
+             pp ? c->Aplo[n] : nullptr, c->dA[n], P<float>(c->dAc[n]), c->Ldf, c->invd,
+             v ? c->Zf : nullptr, (float2*)c->rownorm, s, R, n, c->status, c->L());
+    gram_df(Ahi, c->Alo[n], Ahi, P<const float>(c->dAc[n]), c->S + off, c->Shi + off,
+            c->Slo + off, c->Wf + off, pp, s, R, (const float2*)c->rownorm, c->scal + 8 + 2 * n,
+            (float2*)c->dpart, c->tickets, c->L());
+    return;
+  }
   if (v)
     solve_rows_v<T>(rhs, c->A[n], c->Ap[n], c->dA[n], c->Lf, c->Z, P<T>(c->rhs2), P<T>(c->Ac[n]),
                     P<T>(c->dAc[n]), c->rownorm, s, R, n, c->status, c->L());
   else
     solve_rows<T>(rhs, c->A[n], pp ? c->Ap[n] : nullptr, c->dA[n], c->Lf, P<T>(c->Ac[n]),
                   P<T>(c->dAc[n]), c->rownorm, s, R, n, c->status, c->L());
-  gram_update<T>(c->A[n], P<const T>(c->Ac[n]), P<const T>(c->dAc[n]), c->S + (int64_t)n * R * R,
-                 c->W + (int64_t)n * R * R, pp, s, R, c->rownorm, c->scal + 8 + 2 * n, c->dpart,
-                 c->tickets, c->L());
+  gram_update<T>(c->A[n], P<const T>(c->Ac[n]), P<const T>(c->dAc[n]), c->S + off, c->W + off,
+                 pp, s, R, c->rownorm, c->scal + 8 + 2 * n, c->dpart, c->tickets, c->L());
 }
 
 // ---------------------------------------------------------------- ALS sweep
@@ -435,6 +460,14 @@ cpals_status pp_build_launch(cpals_ctx* c) {
     CK(cudaMemsetAsync(c->dAc[n], 0, sR * c->esz, c->stream));
   }
   CK(cudaMemsetAsync(c->W, 0, (size_t)N * R * R * sizeof(double), c->stream));
+  if (c->dfm) {
+    CK(cudaMemsetAsync(c->Wf, 0, (size_t)N * R * R * sizeof(float), c->stream));
+    for (int n = 0; n < N; n++) {
+      const size_t sR = (size_t)c->dims[n] * R;
+      CK(cudaMemcpyAsync(c->Aphi[n], c->Ac[n], sR * 4, cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaMemcpyAsync(c->Aplo[n], c->Alo[n], sR * 4, cudaMemcpyDeviceToDevice, c->stream));
+    }
+  }
   // ||dA^(n)||^2 <- 0; ||A^(n)||^2 is unchanged
   for (int n = 0; n < N; n++)
     CK(cudaMemsetAsync(c->scal + 8 + 2 * n, 0, sizeof(double), c->stream));
@@ -540,6 +573,8 @@ cpals_status sync_read(cpals_ctx* c) {
   if (c->status_h[1])
     return c->fail(CPALS_E_TIMEOUT, "tensor-core contraction: a bounded wait gave up (code " +
                                         std::to_string(c->status_h[1]) + ")");
+  if (c->status_h[2])
+    return c->fail(CPALS_E_TIMEOUT, "row solve: the bulk copy of the factor did not complete");
   return CPALS_OK;
 }
 
@@ -654,6 +689,7 @@ cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpal
     if (cudaEventCreate(&c->ev0[i]) != cudaSuccess || cudaEventCreate(&c->ev1[i]) != cudaSuccess)
       return bail(CPALS_E_CUDA);
   if (setup_small_kernels() != cudaSuccess) return bail(CPALS_E_CUDA);
+  if (precision != CPALS_FP64 && setup_df_kernels() != cudaSuccess) return bail(CPALS_E_CUDA);
   if (precision == CPALS_MIXED_BF16 && setup_umma_kernels() != cudaSuccess) return bail(CPALS_E_CUDA);
 
   cpals_status st = CPALS_OK;
@@ -674,6 +710,22 @@ cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpal
     AL(c->Ac[n], sR * esz);
     AL(c->dAc[n], sR * esz);
   }
+  c->dfm = precision != CPALS_FP64;
+  if (c->dfm) {
+    for (int n = 0; n < N; n++) {
+      const size_t sR = (size_t)dims[n] * R;
+      AL(c->Alo[n], sR * 4);
+      AL(c->Aphi[n], sR * 4);
+      AL(c->Aplo[n], sR * 4);
+    }
+    AL(c->Shi, (size_t)N * R * R * 4);
+    AL(c->Slo, (size_t)N * R * R * 4);
+    AL(c->Wf, (size_t)N * R * R * 4);
+    // padded to 16-byte multiples: the row solve copies them with bulk transfers
+    AL(c->Ldf, (size_t)R * (R | 1) * 8 + 16);
+    AL(c->invd, (size_t)R * 8 + 16);
+    AL(c->Zf, (size_t)R * R * 4 + 16);
+  }
   AL(c->S, (size_t)N * R * R * 8);
   AL(c->W, (size_t)N * R * R * 8);
   AL(c->Lf, (size_t)R * R * 8);
@@ -691,10 +743,12 @@ cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpal
   c->gpart_bytes = std::max<size_t>(c->gpart_bytes, (size_t)8 * std::min(c->PL, c->PR) * R * esz);
   AL(c->gpart, c->gpart_bytes);
   if (precision == CPALS_MIXED_BF16) {
-    c->Bt_elems = (size_t)c->Rpad * (size_t)(cdiv(Pmax, 8) * 8);
+    c->Bt_elems = 2 * (size_t)c->Rpad * (size_t)(cdiv(Pmax, 8) * 8);
     AL(c->Bt, c->Bt_elems * 2);
   }
   AL(c->rownorm, (size_t)2 * c->smax * 8);
+  AL(c->dscr[0], (size_t)c->smax * R * 8);
+  AL(c->dscr[1], (size_t)c->smax * R * 8);
   AL(c->dpart, (size_t)std::max<int64_t>(2 * 152 + 64, cdiv(c->smax, 32) * 26 + 64) * 1024 * 8);
   AL(c->scal, 64 * 8);
   AL(c->status, 4 * sizeof(int));
@@ -726,11 +780,13 @@ void cpals_destroy(cpals_ctx* c) {
   for (int n = 0; n < kMaxModes; n++) {
     F(c->A[n]); F(c->Ap[n]); F(c->dA[n]); F(c->Ac[n]); F(c->dAc[n]); F(c->Mp[n]);
     for (int m = 0; m < kMaxModes; m++) F(c->ops[n][m]);
+    F(c->Alo[n]); F(c->Aphi[n]); F(c->Aplo[n]);
   }
   for (void* p : c->lvl_bufs) F(p);
+  F(c->Shi); F(c->Slo); F(c->Wf); F(c->Ldf); F(c->invd); F(c->Zf);
   F(c->S); F(c->W); F(c->Lf); F(c->Z); F(c->ML); F(c->MR); F(c->krp); F(c->tmp[0]); F(c->tmp[1]);
   F(c->rhs); F(c->rhs2); F(c->gpart); F(c->Bt); F(c->rownorm); F(c->dpart); F(c->scal);
-  F(c->status); F(c->tickets);
+  F(c->status); F(c->tickets); F(c->dscr[0]); F(c->dscr[1]);
   if (c->scal_h) cudaFreeHost(c->scal_h);
   if (c->status_h) cudaFreeHost(c->status_h);
   for (int i = 0; i < kEvPairs; i++) {
@@ -810,17 +866,22 @@ cpals_status cpals_init_factors(cpals_ctx* c, const double* const* factors) {
     }
     sumsq<double>(c->A[n], sR, c->dpart, c->scal + 8 + 2 * n, c->L());
     CK(cudaMemcpyAsync(c->scal + 9 + 2 * n, c->scal + 8 + 2 * n, 8, cudaMemcpyDeviceToDevice, c->stream));
-    // rownorm is not needed: gram_update reduces it into a scratch slot
+    // rownorm is not needed: the Gram kernel reduces it into a scratch slot
     CK(cudaMemsetAsync(c->rownorm, 0, 2 * c->dims[n] * 8, c->stream));
-    if (is64(c))
+    const int64_t off = (int64_t)n * R * R;
+    if (c->dfm) {
+      split_df(c->A[n], P<float>(c->Ac[n]), c->Alo[n], sR, c->L());
+      gram_df(P<const float>(c->Ac[n]), c->Alo[n], P<const float>(c->Ac[n]),
+              P<const float>(c->dAc[n]), c->S + off, c->Shi + off, c->Slo + off, c->Wf + off,
+              false, (int)c->dims[n], R, (const float2*)c->rownorm, c->scal + 48,
+              (float2*)c->dpart, c->tickets, c->L());
+    } else {
       gram_update<double>(c->A[n], P<const double>(c->Ac[n]), P<const double>(c->dAc[n]),
-                          c->S + (int64_t)n * R * R, c->W + (int64_t)n * R * R, false,
-                          (int)c->dims[n], R, c->rownorm, c->scal + 48, c->dpart, c->tickets, c->L());
-    else
-      gram_update<float>(c->A[n], P<const float>(c->Ac[n]), P<const float>(c->dAc[n]),
-                         c->S + (int64_t)n * R * R, c->W + (int64_t)n * R * R, false,
-                         (int)c->dims[n], R, c->rownorm, c->scal + 48, c->dpart, c->tickets, c->L());
+                          c->S + off, c->W + off, false, (int)c->dims[n], R, c->rownorm,
+                          c->scal + 48, c->dpart, c->tickets, c->L());
+    }
   }
+  if (c->dfm) CK(cudaMemsetAsync(c->Wf, 0, (size_t)c->N * R * R * 4, c->stream));
   CK(cudaMemsetAsync(c->W, 0, (size_t)c->N * R * R * 8, c->stream));
   CKS(sync_read(c));
   c->have_factors = true;
@@ -996,7 +1057,12 @@ cpals_status cpals_pp_mttkrp(cpals_ctx* c, int n, int use_V, double* out) {
     pp_correct<T>(P<const T>(c->Mp[n]), terms, c->N - 1, P<T>(c->rhs), s, R, c->L());
     const T* res = P<const T>(c->rhs);
     if (use_V) {
-      gamma_chol(c->S, c->W, c->N, n, R, c->Lf, c->Z, true, c->status, c->L());
+      if (c->dfm) {
+        chol_df(c->Shi, c->Slo, c->Wf, c->N, n, R, c->Ldf, c->invd, c->Zf, true, c->status, c->L());
+        convert<float, double>(c->Zf, c->Z, (int64_t)R * R, c->L());
+      } else {
+        gamma_chol(c->S, c->W, c->N, n, R, c->Lf, c->Z, true, c->status, c->L());
+      }
       vterm<T>(P<const T>(c->rhs), P<const T>(c->Ac[n]), c->Z, P<T>(c->rhs2), s, R, c->L());
       CKS(sync_read(c));
       return copy_out<T>(c, P<const T>(c->rhs2), cnt, out);
@@ -1006,6 +1072,42 @@ cpals_status cpals_pp_mttkrp(cpals_ctx* c, int n, int use_V, double* out) {
     return CPALS_OK;
   };
   return is64(c) ? go(double{}) : go(float{});
+}
+
+cpals_status cpals_normal_solve(cpals_ctx* c, int n, const double* rhs, double* out) {
+  CKS(ready(c));
+  if (n < 0 || n >= c->N || !rhs || !out) return c->fail(CPALS_E_INVALID, "bad mode or NULL buffer");
+  Join j(c);
+  const int R = c->R;
+  const int s = (int)c->dims[n];
+  const int64_t cnt = (int64_t)s * R;
+  CK(cudaMemsetAsync(c->status, 0, 16, c->stream));
+  CK(cudaMemcpyAsync(c->dscr[0], rhs, cnt * 8, cudaMemcpyHostToDevice, c->stream));
+  // scratch: dscr[1] <- A_new (float64); the other outputs of the row solve go to
+  // rhs2 (s*R*8 bytes), tmp[0] and dscr[0] (the rhs is consumed first)
+  if (c->dfm) {
+    float* frhs = P<float>(c->rhs);
+    convert<double, float>(c->dscr[0], frhs, cnt, c->L());
+    chol_df(c->Shi, c->Slo, c->Wf, c->N, n, R, c->Ldf, c->invd, c->Zf, false, c->status, c->L());
+    float* hi = P<float>(c->rhs2);
+    float* lo = hi + cnt;
+    CK(cudaMemsetAsync(hi, 0, cnt * 8, c->stream));
+    solve_df(frhs, c->dscr[1], hi, lo, nullptr, nullptr, c->dscr[0], P<float>(c->tmp[0]), c->Ldf,
+             c->invd, nullptr, (float2*)c->rownorm, s, R, n, c->status, c->L());
+  } else {
+    gamma_chol(c->S, c->W, c->N, n, R, c->Lf, c->Z, false, c->status, c->L());
+    CK(cudaMemsetAsync(c->dscr[1], 0, cnt * 8, c->stream));
+    solve_rows<double>(c->dscr[0], c->dscr[1], nullptr, P<double>(c->tmp[1]), c->Lf,
+                       P<double>(c->tmp[0]), P<double>(c->rhs2), c->rownorm, s, R, n, c->status,
+                       c->L());
+  }
+  CKS(sync_read(c));
+  CK(cudaMemcpy(out, c->dscr[1], cnt * 8, cudaMemcpyDeviceToHost));
+  if (c->status_h[0]) {
+    CK(cudaMemset(c->status, 0, 16));
+    return c->fail(CPALS_E_SINGULAR, "Gamma not positive definite");
+  }
+  return CPALS_OK;
 }
 
 cpals_status cpals_get_state(cpals_ctx* c, int which, int n, double* out) {

@@ -52,8 +52,9 @@ void pp_correct(const T* Mp, const PPTerm<T>* terms, int nterms, T* out, int sy,
 template <typename T>
 void khatri_rao(const T* const* A, const int64_t* dims, int nm, int R, T* out, Launch L);
 
-// Same product written transposed, zero-padded and in bf16 for the tensor
-// cores: outT[r][k] for r < Rpad, k < Kstride (k >= K and r >= R are zero).
+// Same product written transposed, zero-padded and split into two bf16 planes
+// for the tensor cores: outT[0][r][k] = hi = bf16(v), outT[1][r][k] =
+// bf16(v - hi), r < Rpad, k < Kstride (k >= K and r >= R are zero).
 void khatri_rao_bf16_t(const float* const* A, const int64_t* dims, int nm, int R, int Rpad,
                        int64_t Kstride, __nv_bfloat16* outT, Launch L);
 
@@ -107,11 +108,27 @@ template <typename T>
 void fitness(const T* rhs, const double* A, const double* S, int N, int R, int s, double normX2,
              double* out, double* partials, Launch L);
 
+// ---------------------------------------------------------------- double-float (FP32/mixed modes)
+// The same normal-equation steps in double-float arithmetic (hi + lo floats)
+// on the float32 pipes.  Factors are carried as Ahi (= the float compute copy)
+// and Alo; Grams as S (float64), Shi, Slo; W and Z in float.
+cudaError_t setup_df_kernels();
+void split_df(const double* A, float* hi, float* lo, int64_t n, Launch L);
+void gram_df(const float* Ahi, const float* Alo, const float* Aw, const float* dAw, double* S,
+             float* Shi, float* Slo, float* W, bool withW, int s, int R, const float2* rownorm,
+             double* scal, float2* partials, int* tickets, Launch L);
+void chol_df(const float* Shi, const float* Slo, const float* W, int N, int n, int R, float2* Lout,
+             float2* invd, float* Z, bool useV, int* status, Launch L);
+void solve_df(const float* rhs, double* A, float* Ahi, float* Alo, const float* Arefhi,
+              const float* Areflo, double* dA, float* dAc, const float2* Lf, const float2* invd,
+              const float* Z, float2* rownorm, int s, int R, int n, const int* status, Launch L);
+
 // ---------------------------------------------------------------- tcgen05 (sm_103a)
 // bf16 tensor-core first-level contraction, fp32 accumulate in TMEM, TMA-fed:
 //   kmajor:  out[m][r]    = sum_k Xb[m*K + k]         * Bt[r][k]
 //   !kmajor: out[b][m][r] = sum_k Xb[(b*K + k)*M + m] * Bt[r][k]
-// Bt is R padded to Rpad (multiple of 16) rows of Kstride bf16 (zero padded).
+// Bt holds two planes (hi, lo) of Rpad (multiple of 16) rows x Kstride bf16
+// (zero padded); the product uses hi + lo.
 // splits > 1: fp32 partials + deterministic reduction into out.
 // Returns false if the shape is not supported (alignment), so the caller can
 // report CPALS_E_UNSUPPORTED.

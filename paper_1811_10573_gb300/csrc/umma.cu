@@ -5,22 +5,30 @@
 // factors: a matrix product whose long dimension streams X from HBM once.
 //   kmajor:  out[m][r]    = sum_k X[m*K + k]         * Bt[r][k]
 //   !kmajor: out[b][m][r] = sum_k X[(b*K + k)*M + m] * Bt[r][k]
-// X is bf16 (one-time copy of the input), Bt is the bf16 transposed B operand
-// (Rpad x Kstride, zero padded), accumulation is fp32 in tensor memory.
+// X is bf16 (one-time copy of the input).  The B operand (a factor or a
+// Khatri-Rao product, float32) is carried as two bf16 planes, Bt = hi + lo with
+// hi = bf16(b) and lo = bf16(b - hi) (Rpad x Kstride each, zero padded): every
+// k-step issues two MMAs into the same fp32 TMEM accumulator, so the factor
+// enters with ~16 significant bits and only the one-time rounding of X
+// remains (the same for every contraction path, which keeps the PP and ALS
+// right-hand sides consistent).
 //
 // Persistent warp-specialised kernel, one CTA per SM:
-//   warp 0      : TMA producer (A tile 128 x 64, B tile Rpad x 64 per stage,
-//                 128-byte swizzle, mbarrier complete_tx)
+//   warp 0      : TMA producer (A tile 128 x 64, B tile 2 x Rpad x 64 per
+//                 stage, 128-byte swizzle, mbarrier complete_tx)
 //   warp 1      : TMEM allocation + single-thread tcgen05.mma issue (M = 128,
 //                 N = Rpad, K = 16 per instruction), tcgen05.commit to free
 //                 stages and to publish finished accumulators
-//   warps 2..5  : epilogue: tcgen05.ld 32x32b, fp32 stores of the rows < M
+//   warps 2..5  : epilogue: tcgen05.ld 32x32b into a 128-byte-swizzled shared
+//                 staging tile, then TMA tensor stores (R % 4 == 0) or
+//                 coalesced row copies (otherwise)
 // Two accumulators (2 x 128 TMEM columns) let the epilogue of one tile run
 // under the MMAs of the next.  Every wait is bounded: on timeout the kernel
 // records an error code, drains what it issued and returns.
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "internal.h"
@@ -97,6 +105,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t src, int c0, int c1,
+                                             int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(map),
+      "r"(src), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
 // Shared-memory matrix descriptor (tcgen05): start >> 4 at [0,14), leading
 // byte offset >> 4 at [16,30), stride byte offset >> 4 at [32,46), fixed
 // 0b001 at [46,49), swizzle mode at [61,64) (2 = 128-byte swizzle).
@@ -157,7 +173,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 struct UmmaParams {
   int64_t batch, K, M;
   int R, Rpad, splits, stages;
-  int RS;               // row stride (floats) of the epilogue staging tile
+  int RS;               // row stride (floats) of the padded staging tile (no TMA store)
+  int nbox;             // 32-column boxes of the swizzled staging tile (TMA store)
+  int tma_store;        // 1: epilogue through TMA tensor stores
   int64_t kchunk;       // multiple of BK
   int64_t mtiles, units;
   float* out;           // out or partials ([z][b][m][r])
@@ -167,7 +185,7 @@ struct UmmaParams {
 template <bool KMAJOR>
 __global__ void __launch_bounds__(kThreadsUmma, 1)
 umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                 UmmaParams p) {
+                 const __grid_constant__ CUtensorMap mapO, UmmaParams p) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[8], empty_bar[8], accf_bar[2], acce_bar[2], done_bar;
   __shared__ uint32_t tmem_base_sh;
@@ -176,7 +194,8 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int S = p.stages;
-  const uint32_t b_stage_bytes = (uint32_t)p.Rpad * BK * 2;
+  const uint32_t b_plane = (uint32_t)p.Rpad * BK * 2;
+  const uint32_t b_stage_bytes = 2 * b_plane;
   const uint32_t stage_bytes = A_STAGE_BYTES + b_stage_bytes;
 
   if (threadIdx.x == 0) {
@@ -193,6 +212,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
+    if (p.tma_store) asm volatile("prefetch.tensormap [%0];" ::"l"(&mapO) : "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
@@ -234,7 +254,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             tma_load_3d(sA, &mapA, fb, (int)(mt * BM), (int)k, (int)b);
             tma_load_3d(sA + A_STAGE_BYTES / 2, &mapA, fb, (int)(mt * BM + 64), (int)k, (int)b);
           }
-          tma_load_2d(sB, &mapB, fb, (int)k, 0);
+          tma_load_3d(sB, &mapB, fb, (int)k, 0, 0);       // hi and lo planes
           issued[stage]++;
           if (++stage == S) {
             stage = 0;
@@ -299,7 +319,9 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             if (KMAJOR) adesc = smem_desc(sA + ks * 32, 16, 1024);
             else adesc = smem_desc(sA + ks * 2048, A_STAGE_BYTES / 2, 1024);
             const uint64_t bdesc = smem_desc(sB + ks * 32, 16, 1024);
+            const uint64_t bdesc_lo = smem_desc(sB + b_plane + ks * 32, 16, 1024);
             umma_f16(d_tmem, adesc, bdesc, idesc, accum);
+            umma_f16(d_tmem, adesc, bdesc_lo, idesc, 1u);
             accum = 1;
           }
           umma_commit(smem_u32(&empty_bar[stage]));
@@ -326,14 +348,21 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     }
   } else {
     // ------------------------------------------------ epilogue (warps 2..5)
-    // TMEM -> registers -> shared staging tile (row stride RS, RS/4 odd: the
-    // 16-byte stores of 8 consecutive rows hit distinct banks) -> coalesced
-    // row copies to global (the 128 x R tile is contiguous there).
-    float* stg = reinterpret_cast<float*>(smem_raw + (base - smem_u32(smem_raw)) +
-                                          (size_t)S * stage_bytes);
+    // TMEM -> registers -> shared staging tile -> global.
+    //  * TMA store path (R % 4 == 0): the tile is staged as nbox boxes of
+    //    128 rows x 32 floats with the 128-byte swizzle (16-byte chunk c of
+    //    row r at chunk c ^ (r % 8): conflict-free writes), then one thread
+    //    issues one tensor store per box; the tensor map's M extent clips the
+    //    rows past the end of a batch and its R extent the padding columns.
+    //  * otherwise: padded staging (row stride RS, RS/4 odd) and coalesced
+    //    row copies.
+    uint8_t* stg_base = smem_raw + (base - smem_u32(smem_raw)) + (size_t)S * stage_bytes;
+    const uint32_t stg_u32 = base + S * stage_bytes;
+    float* stg = reinterpret_cast<float*>(stg_base);
     const int q = warp & 3;                   // TMEM lane quarter this warp may access
     const int row = q * 32 + lane;
     const int ew = warp - 2;
+    const bool leader = (ew == 0 && lane == 0);
     int t = 0;
     for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x, t++) {
       const int64_t mt = u % p.mtiles;
@@ -357,30 +386,58 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       __syncwarp();
       tc_fence_after();
       const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 128);
-      float* srow = stg + row * p.RS;
-      for (int c = 0; c < p.Rpad; c += 16) {
-        float v[16];
-        tmem_ld16(taddr + c, v);
+      if (p.tma_store) {
+        for (int c = 0; c < p.Rpad; c += 16) {
+          float v[16];
+          tmem_ld16(taddr + c, v);
+          uint8_t* boxp = stg_base + (size_t)(c >> 5) * (BM * 128) + row * 128;
 #pragma unroll
-        for (int g4 = 0; g4 < 4; g4++)
-          if (c + 4 * g4 < p.RS)
-            *reinterpret_cast<float4*>(srow + c + 4 * g4) =
+          for (int g4 = 0; g4 < 4; g4++) {
+            const int ch = ((c & 31) >> 2) + g4;
+            *reinterpret_cast<float4*>(boxp + ((ch ^ (row & 7)) << 4)) =
                 make_float4(v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
+          }
+        }
+      } else {
+        float* srow = stg + row * p.RS;
+        for (int c = 0; c < p.Rpad; c += 16) {
+          float v[16];
+          tmem_ld16(taddr + c, v);
+#pragma unroll
+          for (int g4 = 0; g4 < 4; g4++)
+            if (c + 4 * g4 < p.RS)
+              *reinterpret_cast<float4*>(srow + c + 4 * g4) =
+                  make_float4(v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
+        }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&acce_bar[buf]));   // accumulator free for the MMA warp
-      asm volatile("bar.sync 1, 128;" ::: "memory");
       const int64_t m0 = mt * BM;
-      const int rows = (int)min((int64_t)BM, p.M - m0);
-      float* gout = p.out + (((int64_t)z * p.batch + b) * p.M + m0) * p.R;
-      for (int r2 = ew; r2 < rows; r2 += 4) {
-        const float* sr = stg + r2 * p.RS;
-        float* gr = gout + (int64_t)r2 * p.R;
-        for (int col = lane; col < p.R; col += 32) gr[col] = sr[col];
+      if (p.tma_store) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (leader) {
+          const int zb = (int)((int64_t)z * p.batch + b);
+          for (int bx = 0; bx < p.nbox; bx++)
+            tma_store_3d(&mapO, stg_u32 + bx * (BM * 128), bx * 32, (int)m0, zb);
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+      } else {
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        const int rows = (int)min((int64_t)BM, p.M - m0);
+        float* gout = p.out + (((int64_t)z * p.batch + b) * p.M + m0) * p.R;
+        for (int r2 = ew; r2 < rows; r2 += 4) {
+          const float* sr = stg + r2 * p.RS;
+          float* gr = gout + (int64_t)r2 * p.R;
+          for (int col = lane; col < p.R; col += 32) gr[col] = sr[col];
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
     }
+    if (p.tma_store && leader) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
 
   tc_fence_before();
@@ -477,11 +534,12 @@ cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, flo
   }
   if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
   {
-    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)Rpad};
-    cuuint64_t strides[1] = {(cuuint64_t)Kstride * 2};
-    cuuint32_t box[2] = {BK, (cuuint32_t)Rpad};
-    cuuint32_t es[2] = {1, 1};
-    cr = enc(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)Bt, dims, strides, box, es,
+    // B: two planes (hi, lo) of Rpad rows x Kstride
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)Rpad, 2};
+    cuuint64_t strides[2] = {(cuuint64_t)Kstride * 2, (cuuint64_t)Kstride * Rpad * 2};
+    cuuint32_t box[3] = {BK, (cuuint32_t)Rpad, 2};
+    cuuint32_t es[3] = {1, 1, 1};
+    cr = enc(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)Bt, dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   }
@@ -500,11 +558,26 @@ cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, flo
   p.units = p.mtiles * batch * p.splits;
   p.err = err_flag;
   p.out = p.splits > 1 ? partials : out;
-  const int stage_bytes = A_STAGE_BYTES + Rpad * BK * 2;
+  const int stage_bytes = A_STAGE_BYTES + 2 * Rpad * BK * 2;
   int RS = (R + 3) / 4 * 4;
   if (((RS / 4) & 1) == 0) RS += 4;
   p.RS = RS;
-  const int staging = BM * RS * 4;
+  p.nbox = (Rpad + 31) / 32;
+  p.tma_store = (R % 4 == 0) ? 1 : 0;
+  CUtensorMap mapO;
+  memset(&mapO, 0, sizeof(mapO));
+  if (p.tma_store) {
+    // out viewed as [splits*batch][M][R] fp32; box 128 rows x 32 columns, swizzled
+    cuuint64_t dims[3] = {(cuuint64_t)R, (cuuint64_t)M, (cuuint64_t)(batch * p.splits)};
+    cuuint64_t strides[2] = {(cuuint64_t)R * 4, (cuuint64_t)M * R * 4};
+    cuuint32_t box[3] = {32, BM, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    cr = enc(&mapO, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)p.out, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  const int staging = p.tma_store ? p.nbox * BM * 128 : BM * RS * 4;
   const int budget = 227 * 1024 - 2048;
   p.stages = std::min(8, (budget - staging) / stage_bytes);
   if (p.stages < 2) return cudaErrorInvalidValue;
@@ -513,9 +586,9 @@ cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, flo
 
   cudaError_t e;
   if (kmajor)
-    umma_gemm_kernel<true><<<grid, kThreadsUmma, smem, L.stream>>>(mapA, mapB, p);
+    umma_gemm_kernel<true><<<grid, kThreadsUmma, smem, L.stream>>>(mapA, mapB, mapO, p);
   else
-    umma_gemm_kernel<false><<<grid, kThreadsUmma, smem, L.stream>>>(mapA, mapB, p);
+    umma_gemm_kernel<false><<<grid, kThreadsUmma, smem, L.stream>>>(mapA, mapB, mapO, p);
   (*L.counter)++;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -203,3 +203,29 @@ def test_full_size_order3_400_sampled(prec):
                 A = [a if k != n else a[y:y + 1] for k, a in enumerate(p.A0)]
                 ref = O.mttkrp(sub, A, n)[0]
                 assert rel(M[y], ref) < (1e-4 if prec == "fp32" else 1e-2), (n, y)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("dims,R", [([40, 33, 27], 9), ([130, 120, 110], 100), ([11, 13, 9, 10], 6)])
+def test_normal_solve(dims, R, prec):
+    """Grams, Gamma^(n), its Cholesky factor and the row solves (Sec. 2.3)
+    against the oracle's float64 solve for the Grams of the GPU's factors.
+    float64 mode: IEEE float64; FP32/mixed: double-float (48-bit) kernels,
+    which take the right-hand side in float (the contractions' precision),
+    so the oracle solves the float-rounded right-hand side.  Both within
+    1e-11 relative at these condition numbers."""
+    storage = "f64" if prec == "fp64" else "f32"
+    p = synth.make_problem("normal", dims, R, seed=31, storage=storage, init="normal")
+    g_ = np.random.default_rng(32)
+    with _ctx(p, prec) as g:
+        g.als_sweep()
+        A = g.get_factors()
+        S = [O.gram(a) for a in A]
+        for n in range(len(dims)):
+            G = O.gamma(S, n)
+            rhs = g_.standard_normal((dims[n], R)) @ G
+            if prec != "fp64":
+                rhs = rhs.astype(np.float32).astype(np.float64)
+            ref = O.solve_normal(rhs, G)
+            assert np.linalg.cond(G) < 1e6
+            assert rel(g.normal_solve(n, rhs), ref) < 1e-11, (n, prec)

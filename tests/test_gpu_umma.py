@@ -1,9 +1,10 @@
 """Sharp parity of the tcgen05 (bf16 tensor-core) first-level contraction.
 
-In MIXED_BF16 mode the library rounds X and the B operand (one factor, or the
-float32 Khatri-Rao product of several) to bf16 with round-to-nearest-even and
-accumulates in fp32.  These tests take that rounding decision on the host in
-the same precision (float32 products, then RNE to bf16), contract the
+In MIXED_BF16 mode the library rounds X to bf16 (round to nearest even) and
+carries the B operand (one factor, or the float32 Khatri-Rao product of
+several) as two bf16 planes hi = bf16(b), lo = bf16(b - hi); the tensor cores
+accumulate X (hi + lo) in fp32.  These tests take the same rounding decisions
+on the host (float32 products, then the two RNE roundings), contract the
 rounded values in float64, and compare: what remains is fp32 accumulation
 error only (~K 2^-24 worst case), so the bound is 2e-5 relative to max|ref|.
 A dropped k-step, a wrong swizzle or a transposed operand shows up as errors
@@ -31,6 +32,14 @@ def bf16(a):
     u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
     u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
     return u.view(np.float32).astype(np.float64)
+
+
+def bsplit(a):
+    """float32 B operand -> hi + lo as the library stores it (float64)."""
+    a32 = np.ascontiguousarray(a, dtype=np.float32)
+    hi = bf16(a32)
+    lo = bf16((a32 - hi.astype(np.float32)).astype(np.float32))
+    return hi + lo
 
 
 def krp32(mats):
@@ -68,11 +77,11 @@ def test_mttkrp_order3(dims, R):
     s0, s1, s2 = dims
     with _ctx(p) as g:
         # left half {0,1}: X_(01) times A^(2) (tensor cores), then one TTV in fp32
-        ML = (Xb.reshape(s0 * s1, s2) @ bf16(A32[2])).reshape(s0, s1, R)
+        ML = (Xb.reshape(s0 * s1, s2) @ bsplit(A32[2])).reshape(s0, s1, R)
         ref0 = np.einsum("ijr,jr->ir", ML, A32[1].astype(np.float64))
         ref1 = np.einsum("ijr,ir->jr", ML, A32[0].astype(np.float64))
-        # right half {2}: X_(01)^T times bf16(A^(0) (.) A^(1))
-        ref2 = Xb.reshape(s0 * s1, s2).T @ bf16(krp32([A32[0], A32[1]]))
+        # right half {2}: X_(01)^T times the split of A^(0) (.) A^(1)
+        ref2 = Xb.reshape(s0 * s1, s2).T @ bsplit(krp32([A32[0], A32[1]]))
         for n, ref in enumerate([ref0, ref1, ref2]):
             assert rel(g.mttkrp(n), ref) < TOL, n
 
@@ -84,8 +93,8 @@ def test_mttkrp_order4(dims, R):
     A32 = [a.astype(np.float32) for a in p.A0]
     A64 = [a.astype(np.float64) for a in A32]
     with _ctx(p) as g:
-        ML = (Xb @ bf16(krp32([A32[2], A32[3]]))).reshape(dims[0], dims[1], R)
-        MR = (Xb.T @ bf16(krp32([A32[0], A32[1]]))).reshape(dims[2], dims[3], R)
+        ML = (Xb @ bsplit(krp32([A32[2], A32[3]]))).reshape(dims[0], dims[1], R)
+        MR = (Xb.T @ bsplit(krp32([A32[0], A32[1]]))).reshape(dims[2], dims[3], R)
         refs = [np.einsum("ijr,jr->ir", ML, A64[1]), np.einsum("ijr,ir->jr", ML, A64[0]),
                 np.einsum("klr,lr->kr", MR, A64[3]), np.einsum("klr,kr->lr", MR, A64[2])]
         for n, ref in enumerate(refs):
@@ -101,7 +110,7 @@ def test_pp_operators_order3(dims, R):
     with _ctx(p) as g:
         g.pp_build_operators()
         A32 = [a.astype(np.float32) for a in p.A0]
-        B = [bf16(a) for a in A32]
+        B = [bsplit(a) for a in A32]
         refs = {(0, 1): np.einsum("ijk,kr->ijr", Xb, B[2]),
                 (0, 2): np.einsum("ijk,jr->ikr", Xb, B[1]),
                 (1, 2): np.einsum("ijk,ir->jkr", Xb, B[0])}
