@@ -69,6 +69,22 @@ __device__ __forceinline__ dfl df_recip(dfl a) {
   const dfl d = df_sub(dfl{1.f, 0.f}, df_mul(a, dfl{r, 0.f}));
   return fast_two_sum(r, __fmul_rn(d.hi, r));
 }
+// "sloppy" double-word addition (one TwoSum): error bounded relative to
+// |x| + |y| (a few units of 2^-48); used where that backward-error bound is
+// what matters (the Cholesky trailing update)
+__device__ __forceinline__ dfl df_add_fast(dfl x, dfl y) {
+  const dfl s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+// 1/sqrt(a): float reciprocal square root refined by one Newton step in
+// double-float, r = r0 + r0 (1 - a r0^2) / 2
+__device__ __forceinline__ dfl df_rsqrt(dfl a) {
+  const float r0 = rsqrtf(a.hi);
+  const dfl r2 = two_prod(r0, r0);
+  const dfl ar2 = df_mul(a, r2);
+  const dfl e = df_sub(dfl{1.f, 0.f}, ar2);
+  return fast_two_sum(r0, __fmul_rn(__fmul_rn(0.5f, r0), e.hi));
+}
 __device__ __forceinline__ dfl df_of(double x) {
   const float h = __double2float_rn(x);
   return {h, __double2float_rn(x - (double)h)};
@@ -229,26 +245,28 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
 
 // ---------------------------------------------------------------- Gamma + Cholesky
 // One CTA: Gamma^(n) = Hadamard product of S^(k), k != n (double-float), then
-// a blocked right-looking Cholesky (block 16) in shared memory, row stride
-// RS = R|1:
-//   1. warp 0 factors the 16 x 16 diagonal block in registers (lane = row,
-//      shuffles carry the pivot column);
-//   2. one thread per row below the block solves x L_kk^T = g (row TRSM);
-//   3. all threads apply the symmetric rank-16 update to the trailing lower
-//      triangle, each entry a 16-term double-float dot product.
+// a right-looking Cholesky in shared memory (row stride RS = R|1) with one
+// barrier per pivot.  The lower triangle is enumerated column-major,
+// e(i, j) = j R - j(j-1)/2 + (i - j); thread t owns the entries e = t mod nt.
+// At step k the entries still to update (columns > k) are the suffix
+// e >= e(k+1, k+1) and column k-1 is the range [e(k-1,k-1), e(k,k)), so a
+// thread only visits live entries.  Every thread takes 1/piv_k itself (no
+// broadcast) and updates G_ij -= G_ik G_jk / piv_k from the unscaled column k;
+// column k-1, which no thread reads at step k, is scaled to L then.
 // Writes L (row stride RS, the layout the row solve copies in one bulk
 // transfer) and the reciprocals of its diagonal.  With useV also the float
 // matrix Z of the second-order terms (Eq. 3).
-constexpr int kCB = 16;
+constexpr int kCholThreads = 1024;
 
-__global__ void __launch_bounds__(512)
+__device__ __forceinline__ int col_start(int j, int R) { return j * R - j * (j - 1) / 2; }
+
+__global__ void __launch_bounds__(kCholThreads, 1)
 chol_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
                const float* __restrict__ W, int N, int n, int R, float2* __restrict__ Lout,
                float2* __restrict__ invd, float* __restrict__ Z, int useV, int* __restrict__ status) {
   extern __shared__ float2 G[];
-  __shared__ int bad;
+  __shared__ int colstart[kMaxRank + 2];
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5;
   const int RR = R * R;
   const int RS = R | 1;
   for (int idx = tid; idx < RR; idx += nt) {
@@ -279,90 +297,54 @@ chol_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
       Z[idx] = zz;
     }
   }
-  if (tid == 0) bad = 0;
+  for (int j = tid; j <= R + 1; j += nt) colstart[j] = col_start(min(j, R), R);
   __syncthreads();
-  for (int kb = 0; kb < R; kb += kCB) {
-    const int nb = min(kCB, R - kb);
-    // ---- 1. diagonal block, warp 0: lane l < nb holds row kb+l
-    if (warp == 0) {
-      dfl d[kCB];
-#pragma unroll
-      for (int j = 0; j < kCB; j++)
-        d[j] = (lane < nb && j <= lane) ? upk(G[(kb + lane) * RS + kb + j]) : dfl{0.f, 0.f};
-      bool ok = true;
-#pragma unroll
-      for (int j = 0; j < kCB; j++) {
-        if (j < nb && ok) {
-          const dfl piv = {__shfl_sync(0xffffffffu, d[j].hi, j), __shfl_sync(0xffffffffu, d[j].lo, j)};
-          if (!(piv.hi > 0.f) || !isfinite(piv.hi)) {
-            ok = false;
-          } else {
-            const dfl l = df_sqrt(piv);
-            const dfl il = df_recip(l);
-            if (lane == j) {
-              d[j] = l;
-              invd[kb + j] = pk(il);
-            } else if (lane > j && lane < nb) {
-              d[j] = df_mul(d[j], il);
-            }
-#pragma unroll
-            for (int jp = j + 1; jp < kCB; jp++) {
-              const dfl ljp = {__shfl_sync(0xffffffffu, d[j].hi, jp), __shfl_sync(0xffffffffu, d[j].lo, jp)};
-              if (jp < nb && lane >= jp && lane < nb) d[jp] = df_sub(d[jp], df_mul(d[j], ljp));
-            }
-          }
-        }
+  const int E = colstart[R];
+  dfl ipiv_prev = {0.f, 0.f}, il_prev = {0.f, 0.f};
+  for (int k = 0; k <= R; k++) {
+    dfl il = {0.f, 0.f}, ipiv = {0.f, 0.f};
+    if (k < R) {
+      const dfl piv = upk(G[k * RS + k]);
+      if (!(piv.hi > 0.f) || !isfinite(piv.hi)) {
+        // every thread read the same pivot: the exit is uniform
+        if (tid == 0) atomicOr(status, 1 << n);
+        return;
       }
-      if (!ok) {
-        if (lane == 0) bad = 1;
-      } else {
-#pragma unroll
-        for (int j = 0; j < kCB; j++)
-          if (lane < nb && j <= lane) G[(kb + lane) * RS + kb + j] = pk(d[j]);
+      il = df_rsqrt(piv);
+      ipiv = df_mul(il, il);
+      if (tid == 0) invd[k] = pk(il);
+    }
+    // scale column k-1 to L: its entries are a contiguous range
+    if (k > 0) {
+      const int e0 = colstart[k - 1], e1 = colstart[k];
+      for (int e = e0 + tid; e < e1; e += nt) {
+        const int i = (k - 1) + (e - e0);
+        G[i * RS + (k - 1)] = pk(df_mul(upk(G[i * RS + (k - 1)]), il_prev));
       }
     }
-    __syncthreads();
-    if (bad) break;
-    // ---- 2. row TRSM below the block: x L_kk^T = g, one thread per row
-    for (int i = kb + nb + tid; i < R; i += nt) {
-      dfl x[kCB];
-#pragma unroll
-      for (int j = 0; j < kCB; j++) x[j] = j < nb ? upk(G[i * RS + kb + j]) : dfl{0.f, 0.f};
-#pragma unroll
-      for (int j = 0; j < kCB; j++) {
-        if (j < nb) {
-          x[j] = df_mul(x[j], upk(invd[kb + j]));
-#pragma unroll
-          for (int jp = j + 1; jp < kCB; jp++)
-            if (jp < nb) x[jp] = df_sub(x[jp], df_mul(x[j], upk(G[(kb + jp) * RS + kb + j])));
-        }
+    // trailing update of columns j > k
+    if (k < R - 1) {
+      const int es = colstart[k + 1];
+      // first owned entry >= es; the column of entry e is the largest j with
+      // colstart[j] <= e (root of j^2 - (2R+1) j + 2e, then exact fix-ups)
+      const float b2 = (float)(2 * R + 1);
+      for (int e = es + ((tid - es) % nt + nt) % nt; e < E; e += nt) {
+        int j = (int)((b2 - sqrtf(fmaxf(b2 * b2 - 8.f * (float)e, 0.f))) * 0.5f);
+        j = max(0, min(j, R - 1));
+        while (j > 0 && colstart[j] > e) j--;
+        while (colstart[j + 1] <= e) j++;
+        const int i = j + (e - colstart[j]);
+        const dfl gik = upk(G[i * RS + k]);
+        const dfl gjk = upk(G[j * RS + k]);
+        const dfl t = df_mul(df_mul(gik, gjk), ipiv);
+        G[i * RS + j] = pk(df_add_fast(upk(G[i * RS + j]), df_neg(t)));
       }
-#pragma unroll
-      for (int j = 0; j < kCB; j++)
-        if (j < nb) G[i * RS + kb + j] = pk(x[j]);
     }
-    __syncthreads();
-    // ---- 3. trailing update G[i][j] -= sum_t X[i][t] X[j][t], kb+nb <= j <= i < R
-    const int m = R - kb - nb;
-    const int pairs = m * (m + 1) / 2;
-    for (int e = tid; e < pairs; e += nt) {
-      int ii = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-      while (ii * (ii + 1) / 2 > e) ii--;
-      while ((ii + 1) * (ii + 2) / 2 <= e) ii++;
-      const int jj = e - ii * (ii + 1) / 2;
-      const int i = kb + nb + ii, j = kb + nb + jj;
-      dfl acc = upk(G[i * RS + j]);
-      for (int t = 0; t < nb; t++)
-        acc = df_sub(acc, df_mul(upk(G[i * RS + kb + t]), upk(G[j * RS + kb + t])));
-      G[i * RS + j] = pk(acc);
-    }
+    il_prev = il;
+    ipiv_prev = ipiv;
     __syncthreads();
   }
-  __syncthreads();
-  if (bad) {
-    if (tid == 0) atomicOr(status, 1 << n);
-    return;
-  }
+  (void)ipiv_prev;
   for (int idx = tid; idx < R * RS; idx += nt) {
     const int i = idx / RS, j = idx % RS;
     Lout[idx] = (j <= i && j < R) ? G[idx] : make_float2(0.f, 0.f);
@@ -446,87 +428,134 @@ solve_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float* __
     if (threadIdx.x == 0) atomicOr(const_cast<int*>(status) + 2, 1);
     return;
   }
-  for (int y = blockIdx.x * nwarp + warp; y < s; y += gridDim.x * nwarp) {
-    float oh[kChunks], ol[kChunks];
-    dfl b[kChunks];
+  // two rows per warp, interleaved: the two substitutions are independent
+  // instruction streams (latency hiding) and share every load of L
+  constexpr int RPW = 2;
+  for (int y0 = (blockIdx.x * nwarp + warp) * RPW; y0 < s; y0 += gridDim.x * nwarp * RPW) {
+    float oh[RPW][kChunks], ol[RPW][kChunks];
+    dfl b[RPW][kChunks];
 #pragma unroll
-    for (int c = 0; c < kChunks; c++) {
-      const int r = lane + 32 * c;
-      const bool v = r < R;
-      oh[c] = v ? Ahi[(int64_t)y * R + r] : 0.f;
-      ol[c] = v ? Alo[(int64_t)y * R + r] : 0.f;
-      b[c] = {v ? rhs[(int64_t)y * R + r] : 0.f, 0.f};
+    for (int w = 0; w < RPW; w++) {
+      const int y = min(y0 + w, s - 1);      // a missing second row repeats the first (not stored)
+#pragma unroll
+      for (int c = 0; c < kChunks; c++) {
+        const int r = lane + 32 * c;
+        const bool v = r < R;
+        oh[w][c] = v ? Ahi[(int64_t)y * R + r] : 0.f;
+        ol[w][c] = v ? Alo[(int64_t)y * R + r] : 0.f;
+        b[w][c] = {v ? rhs[(int64_t)y * R + r] : 0.f, 0.f};
+      }
     }
     if (failed) {
 #pragma unroll
-      for (int c = 0; c < kChunks; c++) b[c] = {oh[c], ol[c]};
+      for (int w = 0; w < RPW; w++)
+#pragma unroll
+        for (int c = 0; c < kChunks; c++) b[w][c] = {oh[w][c], ol[w][c]};
     } else {
       if (Zg) {
         // second-order PP terms: b += A_old Z (float)
-        float vz[kChunks] = {0.f, 0.f, 0.f, 0.f};
+        float vz[RPW][kChunks];
+#pragma unroll
+        for (int w = 0; w < RPW; w++)
+#pragma unroll
+          for (int c = 0; c < kChunks; c++) vz[w][c] = 0.f;
         for (int k = 0; k < R; k++) {
-          const float ak = __shfl_sync(0xffffffffu, pick(oh, k >> 5), k & 31);
+          float ak[RPW];
+#pragma unroll
+          for (int w = 0; w < RPW; w++) ak[w] = __shfl_sync(0xffffffffu, pick(oh[w], k >> 5), k & 31);
 #pragma unroll
           for (int c = 0; c < kChunks; c++) {
             const int r = lane + 32 * c;
-            if (32 * c < R && r < R) vz[c] = fmaf(ak, Zs[k * R + r], vz[c]);
+            if (32 * c < R && r < R) {
+              const float zz = Zs[k * R + r];
+#pragma unroll
+              for (int w = 0; w < RPW; w++) vz[w][c] = fmaf(ak[w], zz, vz[w][c]);
+            }
           }
         }
 #pragma unroll
-        for (int c = 0; c < kChunks; c++) b[c] = df_add(b[c], dfl{vz[c], 0.f});
+        for (int w = 0; w < RPW; w++)
+#pragma unroll
+          for (int c = 0; c < kChunks; c++) b[w][c] = df_add(b[w][c], dfl{vz[w][c], 0.f});
       }
+      // forward substitution L z = b (updates use the one-TwoSum addition:
+      // backward error of a few 2^-48 relative to the operands)
       for (int i = 0; i < R; i++) {
         const int ci = i >> 5, li = i & 31;
-        const dfl bi = pick(b, ci);
-        const dfl src = {__shfl_sync(0xffffffffu, bi.hi, li), __shfl_sync(0xffffffffu, bi.lo, li)};
-        const dfl zi = df_mul(src, upk(inv[i]));
-        if (lane == li) put(b, ci, zi);
+        const dfl inv_i = upk(inv[i]);
+        dfl zi[RPW];
+#pragma unroll
+        for (int w = 0; w < RPW; w++) {
+          const dfl bi = pick(b[w], ci);
+          const dfl src = {__shfl_sync(0xffffffffu, bi.hi, li), __shfl_sync(0xffffffffu, bi.lo, li)};
+          zi[w] = df_mul(src, inv_i);
+          if (lane == li) put(b[w], ci, zi[w]);
+        }
 #pragma unroll
         for (int c = 0; c < kChunks; c++) {
           if (32 * c + 31 <= i || 32 * c >= R) continue;
           const int r = lane + 32 * c;
-          if (r > i && r < R) b[c] = df_sub(b[c], df_mul(upk(Ls[r * RS + i]), zi));
+          if (r > i && r < R) {
+            const dfl l = upk(Ls[r * RS + i]);
+#pragma unroll
+            for (int w = 0; w < RPW; w++) b[w][c] = df_add_fast(b[w][c], df_neg(df_mul(l, zi[w])));
+          }
         }
       }
+      // back substitution L^T a = z
       for (int i = R - 1; i >= 0; i--) {
         const int ci = i >> 5, li = i & 31;
-        const dfl bi = pick(b, ci);
-        const dfl src = {__shfl_sync(0xffffffffu, bi.hi, li), __shfl_sync(0xffffffffu, bi.lo, li)};
-        const dfl ai = df_mul(src, upk(inv[i]));
-        if (lane == li) put(b, ci, ai);
+        const dfl inv_i = upk(inv[i]);
+        dfl ai[RPW];
+#pragma unroll
+        for (int w = 0; w < RPW; w++) {
+          const dfl bi = pick(b[w], ci);
+          const dfl src = {__shfl_sync(0xffffffffu, bi.hi, li), __shfl_sync(0xffffffffu, bi.lo, li)};
+          ai[w] = df_mul(src, inv_i);
+          if (lane == li) put(b[w], ci, ai[w]);
+        }
 #pragma unroll
         for (int c = 0; c < kChunks; c++) {
           if (32 * c >= i) continue;
           const int r = lane + 32 * c;
-          if (r < i) b[c] = df_sub(b[c], df_mul(upk(Ls[i * RS + r]), ai));
+          if (r < i) {
+            const dfl l = upk(Ls[i * RS + r]);
+#pragma unroll
+            for (int w = 0; w < RPW; w++) b[w][c] = df_add_fast(b[w][c], df_neg(df_mul(l, ai[w])));
+          }
         }
       }
     }
-    dfl nd = {0.f, 0.f}, na = {0.f, 0.f};
 #pragma unroll
-    for (int c = 0; c < kChunks; c++) {
-      const int r = lane + 32 * c;
-      if (r < R) {
-        const int64_t o = (int64_t)y * R + r;
-        const dfl ref = Arefhi ? dfl{Arefhi[o], Areflo[o]} : dfl{oh[c], ol[c]};
-        const dfl d = df_sub(b[c], ref);
-        A[o] = df_dbl(b[c]);
-        Ahi[o] = b[c].hi;
-        Alo[o] = b[c].lo;
-        dA[o] = df_dbl(d);
-        dAc[o] = d.hi;
-        nd = df_add(nd, df_mul(d, d));
-        na = df_add(na, df_mul(b[c], b[c]));
+    for (int w = 0; w < RPW; w++) {
+      const int y = y0 + w;
+      if (y >= s) break;
+      dfl nd = {0.f, 0.f}, na = {0.f, 0.f};
+#pragma unroll
+      for (int c = 0; c < kChunks; c++) {
+        const int r = lane + 32 * c;
+        if (r < R) {
+          const int64_t o = (int64_t)y * R + r;
+          const dfl ref = Arefhi ? dfl{Arefhi[o], Areflo[o]} : dfl{oh[w][c], ol[w][c]};
+          const dfl d = df_sub(b[w][c], ref);
+          A[o] = df_dbl(b[w][c]);
+          Ahi[o] = b[w][c].hi;
+          Alo[o] = b[w][c].lo;
+          dA[o] = df_dbl(d);
+          dAc[o] = d.hi;
+          nd = df_add(nd, df_mul(d, d));
+          na = df_add(na, df_mul(b[w][c], b[w][c]));
+        }
       }
-    }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      nd = df_add(nd, dfl{__shfl_xor_sync(0xffffffffu, nd.hi, off), __shfl_xor_sync(0xffffffffu, nd.lo, off)});
-      na = df_add(na, dfl{__shfl_xor_sync(0xffffffffu, na.hi, off), __shfl_xor_sync(0xffffffffu, na.lo, off)});
-    }
-    if (lane == 0) {
-      rownorm[2 * y] = pk(nd);
-      rownorm[2 * y + 1] = pk(na);
+      for (int off = 16; off > 0; off >>= 1) {
+        nd = df_add(nd, dfl{__shfl_xor_sync(0xffffffffu, nd.hi, off), __shfl_xor_sync(0xffffffffu, nd.lo, off)});
+        na = df_add(na, dfl{__shfl_xor_sync(0xffffffffu, na.hi, off), __shfl_xor_sync(0xffffffffu, na.lo, off)});
+      }
+      if (lane == 0) {
+        rownorm[2 * y] = pk(nd);
+        rownorm[2 * y + 1] = pk(na);
+      }
     }
   }
 }
@@ -569,8 +598,8 @@ void gram_df(const float* Ahi, const float* Alo, const float* Aw, const float* d
 void chol_df(const float* Shi, const float* Slo, const float* W, int N, int n, int R,
              float2* Lout, float2* invd, float* Z, bool useV, int* status, Launch L) {
   const size_t smem = (size_t)R * (R | 1) * sizeof(float2);
-  chol_df_kernel<<<1, 512, smem, L.stream>>>(Shi, Slo, W, N, n, R, Lout, invd, Z, useV ? 1 : 0,
-                                             status);
+  chol_df_kernel<<<1, kCholThreads, smem, L.stream>>>(Shi, Slo, W, N, n, R, Lout, invd, Z,
+                                                      useV ? 1 : 0, status);
   (*L.counter)++;
 }
 
@@ -580,9 +609,9 @@ void solve_df(const float* rhs, double* A, float* Ahi, float* Alo, const float* 
   const size_t lb = ((size_t)R * (R | 1) * sizeof(float2) + 15) / 16 * 16;
   const size_t ib = ((size_t)R * sizeof(float2) + 15) / 16 * 16;
   const size_t zb = Z ? ((size_t)R * R * sizeof(float) + 15) / 16 * 16 : 0;
-  const int rows_per_block = 4;
+  const int warps = 2, rows_per_block = 2 * warps;      // two rows per warp
   const int blocks = (int)std::min<int64_t>(cdiv(s, rows_per_block), 152 * 2);
-  solve_df_kernel<<<blocks, 32 * rows_per_block, lb + ib + zb, L.stream>>>(
+  solve_df_kernel<<<blocks, 32 * warps, lb + ib + zb, L.stream>>>(
       rhs, A, Ahi, Alo, Arefhi, Areflo, dA, dAc, Lf, invd, Z, rownorm, s, R, n, status);
   (*L.counter)++;
 }
