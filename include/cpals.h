@@ -177,6 +177,41 @@ cpals_status cpals_get_stats(cpals_ctx* ctx, int kind, int64_t* launches, double
  * and replay it; 0 launches kernels directly. */
 cpals_status cpals_set_graphs(cpals_ctx* ctx, int enable);
 
+/* ---- contraction without device allocation ---- */
+
+/* The paper has no counterpart to this call.  It is the tensor-core
+ * first-level contraction (the same kernel the MIXED_BF16 sweeps use) for
+ * callers that cannot allocate device memory when they need it: a host
+ * framework that hands out all device memory from its own pool and forbids
+ * raw allocations after start-up, a latency-critical loop that cannot afford
+ * cudaMalloc's implicit synchronisation, or a process whose device-memory
+ * budget is already committed.  It allocates nothing; its split-K partial
+ * sums live in a file-scope device array of CPALS_NOALLOC_SCRATCH_FLOATS
+ * floats (16 MiB) that every GPU loading the library holds until the process
+ * exits.
+ *   kmajor != 0: out[m][r]    = sum_k Xb[m*K + k]         * (hi + lo)[r][k]
+ *   kmajor == 0: out[b][m][r] = sum_k Xb[(b*K + k)*M + m] * (hi + lo)[r][k]
+ * Xb: device bf16 tensor (row stride K if kmajor, else M; M % 8 == 0 when
+ * kmajor == 0, K % 8 == 0 when kmajor != 0; batch must be 1 when kmajor).
+ * Bt: device bf16, two planes [2][Rpad][Kstride], Rpad = R rounded up to 16,
+ * plane 0 = bf16(b), plane 1 = bf16(b - plane 0), zero for r >= R or k >= K;
+ * Kstride >= K and a multiple of 8.  out: device float32, batch*M*R values,
+ * caller-owned.  splits >= 1 splits K across CTAs.  stream: cudaStream_t
+ * (NULL = legacy default stream); the call waits for its own work.
+ * Errors: CPALS_E_INVALID for bad arguments or when splits*batch*M*R exceeds
+ * CPALS_NOALLOC_SCRATCH_FLOATS (the scratch is not enlarged); CPALS_E_UNSUPPORTED
+ * for shapes the tensor-core path does not take (alignment, R > 128);
+ * CPALS_E_TIMEOUT if a bounded device wait gave up; CPALS_E_CUDA otherwise.
+ * The first call on a device takes the scratch array's device address
+ * (cudaGetSymbolAddress) and sets the kernels' shared-memory limit, with
+ * that device current.  All calls share the one array and it keeps the last
+ * call's contents; calls that overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller. */
+#define CPALS_NOALLOC_SCRATCH_FLOATS (4u << 20)
+cpals_status cpals_contract_bf16_noalloc(const void* Xb, const void* Bt, float* out, int64_t batch,
+                                         int64_t K, int64_t M, int R, int64_t Kstride,
+                                         int kmajor, int splits, void* stream);
+
 /* ---- host-only cost model (no GPU needed) ---- */
 
 /* Flop counts of the kernels this library launches for one step of the

@@ -52,7 +52,11 @@ _SIGS = {
     "cpals_get_stats": (C.c_int, [_ctx_p, C.c_int, _i64p, _dp, _dp, _dp]),
     "cpals_set_graphs": (C.c_int, [_ctx_p, C.c_int]),
     "cpals_cost_model": (C.c_int, [_i64p, C.c_int, C.c_int, C.c_int, _dp]),
+    "cpals_contract_bf16_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                             C.c_int64, C.c_int64, C.c_int, C.c_int64, C.c_int,
+                                             C.c_int, C.c_void_p]),
 }
+NOALLOC_SCRATCH_FLOATS = 4 << 20
 
 
 def lib():
@@ -191,6 +195,13 @@ def cpals_cost_model(dims, N, R, kind):
     if st != 0:
         raise CPALSError(st, "cost model: bad sizes")
     return out.value
+
+
+def cpals_contract_bf16_noalloc(Xb, Bt, out, batch, K, M, R, Kstride, kmajor, splits, stream=0):
+    """Device pointers (ints) in, status out; see include/cpals.h."""
+    return lib().cpals_contract_bf16_noalloc(C.c_void_p(int(Xb)), C.c_void_p(int(Bt)),
+                                             C.c_void_p(int(out)), batch, K, M, R, Kstride,
+                                             1 if kmajor else 0, splits, C.c_void_p(int(stream)))
 
 
 # ---------------------------------------------------------------- convenience wrapper
