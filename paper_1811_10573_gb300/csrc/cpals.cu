@@ -62,8 +62,7 @@ struct cpals_ctx {
   float* Shi = nullptr;  // N*R*R
   float* Slo = nullptr;
   float* Wf = nullptr;   // N*R*R (float W for the df path)
-  float2* Ldf = nullptr; // R*R
-  float2* invd = nullptr;
+  float2* Linv = nullptr; // W = L^-1 of Gamma^(n), double-float, R x (R|1)
   float* Zf = nullptr;   // R*R
   double* S = nullptr;   // N*R*R
   double* W = nullptr;   // N*R*R
@@ -280,7 +279,7 @@ void factor_async(cpals_ctx* c, int n, bool pp, bool useV) {
   cudaEventRecord(c->ev_fork, c->stream);
   cudaStreamWaitEvent(c->side, c->ev_fork, 0);
   if (c->dfm)
-    chol_df(c->Shi, c->Slo, c->Wf, c->N, n, c->R, c->Ldf, c->invd, c->Zf, pp && useV, c->status,
+    chol_df(c->Shi, c->Slo, c->Wf, c->N, n, c->R, c->Linv, c->Zf, pp && useV, c->status,
             c->Lside());
   else
     gamma_chol(c->S, c->W, c->N, n, c->R, c->Lf, c->Z, pp && useV, c->status, c->Lside());
@@ -297,7 +296,7 @@ void finish_mode(cpals_ctx* c, int n, const T* rhs, bool pp, bool useV) {
   if (c->dfm) {
     float* Ahi = P<float>(c->Ac[n]);
     solve_df((const float*)rhs, c->A[n], Ahi, c->Alo[n], pp ? c->Aphi[n] : nullptr,
-             pp ? c->Aplo[n] : nullptr, c->dA[n], P<float>(c->dAc[n]), c->Ldf, c->invd,
+             pp ? c->Aplo[n] : nullptr, c->dA[n], P<float>(c->dAc[n]), c->Linv,
              v ? c->Zf : nullptr, (float2*)c->rownorm, s, R, n, c->status, c->L());
     gram_df(Ahi, c->Alo[n], Ahi, P<const float>(c->dAc[n]), c->S + off, c->Shi + off,
             c->Slo + off, c->Wf + off, pp, s, R, (const float2*)c->rownorm, c->scal + 8 + 2 * n,
@@ -722,8 +721,7 @@ cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpal
     AL(c->Slo, (size_t)N * R * R * 4);
     AL(c->Wf, (size_t)N * R * R * 4);
     // padded to 16-byte multiples: the row solve copies them with bulk transfers
-    AL(c->Ldf, (size_t)R * (R | 1) * 8 + 16);
-    AL(c->invd, (size_t)R * 8 + 16);
+    AL(c->Linv, (size_t)R * (R | 1) * 8 + 16);
     AL(c->Zf, (size_t)R * R * 4 + 16);
   }
   AL(c->S, (size_t)N * R * R * 8);
@@ -783,7 +781,7 @@ void cpals_destroy(cpals_ctx* c) {
     F(c->Alo[n]); F(c->Aphi[n]); F(c->Aplo[n]);
   }
   for (void* p : c->lvl_bufs) F(p);
-  F(c->Shi); F(c->Slo); F(c->Wf); F(c->Ldf); F(c->invd); F(c->Zf);
+  F(c->Shi); F(c->Slo); F(c->Wf); F(c->Linv); F(c->Zf);
   F(c->S); F(c->W); F(c->Lf); F(c->Z); F(c->ML); F(c->MR); F(c->krp); F(c->tmp[0]); F(c->tmp[1]);
   F(c->rhs); F(c->rhs2); F(c->gpart); F(c->Bt); F(c->rownorm); F(c->dpart); F(c->scal);
   F(c->status); F(c->tickets); F(c->dscr[0]); F(c->dscr[1]);
@@ -1058,7 +1056,7 @@ cpals_status cpals_pp_mttkrp(cpals_ctx* c, int n, int use_V, double* out) {
     const T* res = P<const T>(c->rhs);
     if (use_V) {
       if (c->dfm) {
-        chol_df(c->Shi, c->Slo, c->Wf, c->N, n, R, c->Ldf, c->invd, c->Zf, true, c->status, c->L());
+        chol_df(c->Shi, c->Slo, c->Wf, c->N, n, R, c->Linv, c->Zf, true, c->status, c->L());
         convert<float, double>(c->Zf, c->Z, (int64_t)R * R, c->L());
       } else {
         gamma_chol(c->S, c->W, c->N, n, R, c->Lf, c->Z, true, c->status, c->L());
@@ -1088,12 +1086,12 @@ cpals_status cpals_normal_solve(cpals_ctx* c, int n, const double* rhs, double* 
   if (c->dfm) {
     float* frhs = P<float>(c->rhs);
     convert<double, float>(c->dscr[0], frhs, cnt, c->L());
-    chol_df(c->Shi, c->Slo, c->Wf, c->N, n, R, c->Ldf, c->invd, c->Zf, false, c->status, c->L());
+    chol_df(c->Shi, c->Slo, c->Wf, c->N, n, R, c->Linv, c->Zf, false, c->status, c->L());
     float* hi = P<float>(c->rhs2);
     float* lo = hi + cnt;
     CK(cudaMemsetAsync(hi, 0, cnt * 8, c->stream));
-    solve_df(frhs, c->dscr[1], hi, lo, nullptr, nullptr, c->dscr[0], P<float>(c->tmp[0]), c->Ldf,
-             c->invd, nullptr, (float2*)c->rownorm, s, R, n, c->status, c->L());
+    solve_df(frhs, c->dscr[1], hi, lo, nullptr, nullptr, c->dscr[0], P<float>(c->tmp[0]), c->Linv,
+             nullptr, (float2*)c->rownorm, s, R, n, c->status, c->L());
   } else {
     gamma_chol(c->S, c->W, c->N, n, R, c->Lf, c->Z, false, c->status, c->L());
     CK(cudaMemsetAsync(c->dscr[1], 0, cnt * 8, c->stream));

@@ -57,18 +57,6 @@ __device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
   const float t2 = __fmaf_rn(x.lo, y.hi, t1);
   return fast_two_sum(c.hi, __fadd_rn(c.lo, t2));
 }
-// sqrt by one Newton step from the float square root (doubles the precision)
-__device__ __forceinline__ dfl df_sqrt(dfl a) {
-  const float s = __fsqrt_rn(a.hi);
-  const dfl d = df_sub(a, two_prod(s, s));
-  return fast_two_sum(s, __fdiv_rn(d.hi, __fmul_rn(2.f, s)));
-}
-// reciprocal by one Newton step from the float reciprocal
-__device__ __forceinline__ dfl df_recip(dfl a) {
-  const float r = __frcp_rn(a.hi);
-  const dfl d = df_sub(dfl{1.f, 0.f}, df_mul(a, dfl{r, 0.f}));
-  return fast_two_sum(r, __fmul_rn(d.hi, r));
-}
 // "sloppy" double-word addition (one TwoSum): error bounded relative to
 // |x| + |y| (a few units of 2^-48); used where that backward-error bound is
 // what matters (the Cholesky trailing update)
@@ -243,52 +231,69 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
   }
 }
 
-// ---------------------------------------------------------------- Gamma + Cholesky
-// One CTA: Gamma^(n) = Hadamard product of S^(k), k != n (double-float), then
-// a right-looking Cholesky in shared memory (row stride RS = R|1) with one
-// barrier per pivot.  The lower triangle is enumerated column-major,
-// e(i, j) = j R - j(j-1)/2 + (i - j); thread t owns the entries e = t mod nt.
-// At step k the entries still to update (columns > k) are the suffix
-// e >= e(k+1, k+1) and column k-1 is the range [e(k-1,k-1), e(k,k)), so a
-// thread only visits live entries.  Every thread takes 1/piv_k itself (no
-// broadcast) and updates G_ij -= G_ik G_jk / piv_k from the unscaled column k;
-// column k-1, which no thread reads at step k, is scaled to L then.
-// Writes L (row stride RS, the layout the row solve copies in one bulk
-// transfer) and the reciprocals of its diagonal.  With useV also the float
-// matrix Z of the second-order terms (Eq. 3).
-constexpr int kCholThreads = 1024;
-
+// ---------------------------------------------------------------- Gamma, Cholesky, inverse
+// One CTA forms Gamma^(n) = Hadamard product of the Grams S^(k), k != n, in
+// double-float, factors it Gamma = L L^T and inverts the factor, W = L^-1, in
+// one right-looking loop that retires two pivots per barrier.  Shared memory:
+//   G   the lower triangle of Gamma, packed by columns: entry (i, j), i >= j,
+//       at cs(j) + i - j with cs(j) = j R - j (j - 1) / 2, so the trailing
+//       triangle right of a column is a contiguous suffix that all threads
+//       share evenly;
+//   crd the (row, column) of every packed index;
+//   B   the lower triangle of the inverse in progress, packed by rows
+//       (entry (i, c) at i (i + 1) / 2 + c), initially the identity;
+//   the current pair of columns of L, the same divided by their diagonal
+//   entries, both double-buffered, 1 / L_jj and L_{k+1,k} / L_kk.
+// Step k (pivots k and k+1 done; Golub & Van Loan Alg. 4.2.2 for the factor,
+// the column-oriented triangular inverse for W):
+//   (a) columns k+2 and k+3 of L from the unupdated G columns and columns k,
+//       k+1 (each thread recomputes the two pivots and L_{k+3,k+2} it needs);
+//   (b) G_ij -= L_ik L_jk + L_i,k+1 L_j,k+1 for the columns j >= k+4;
+//   (c) B_ic -= (L_ik / L_kk) B_kc + (L_i,k+1 / L_k+1,k+1) t_c for rows
+//       i >= k+2, c <= k+1, where t is row k+1 of B after pivot k (formed on
+//       the fly; row k+1 itself is updated at the end).
+// Row j of W is then the final row j of B divided by L_jj.  The work of (b)
+// falls and that of (c) rises with k, which keeps the steps evenly loaded.
+// Additions in the updates use the one-TwoSum double-word addition (backward
+// error a few units of 2^-48 relative to the operands).  Writes W (row
+// stride RS = R | 1, zeros above the diagonal and in the padding column)
+// and, with useV, the float matrix Z of the second-order PP terms (Eq. 3).
+#ifndef CPALS_CHOL_THREADS
+#define CPALS_CHOL_THREADS 512
+#endif
 __device__ __forceinline__ int col_start(int j, int R) { return j * R - j * (j - 1) / 2; }
+__device__ __forceinline__ dfl df_fms(dfl g, dfl a, dfl b) {   // g - a b
+  return df_add_fast(g, df_neg(df_mul(a, b)));
+}
+__device__ __forceinline__ bool bad_pivot(dfl p) { return !(p.hi > 0.f) || !isfinite(p.hi); }
 
-__global__ void __launch_bounds__(kCholThreads, 1)
-chol_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
-               const float* __restrict__ W, int N, int n, int R, float2* __restrict__ Lout,
-               float2* __restrict__ invd, float* __restrict__ Z, int useV, int* __restrict__ status) {
-  extern __shared__ float2 G[];
-  __shared__ int colstart[kMaxRank + 2];
+__global__ void __launch_bounds__(1024, 1)
+chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
+                   const float* __restrict__ Wg, int N, int n, int R, float2* __restrict__ Wout,
+                   float* __restrict__ Z, int useV, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  __shared__ int bad;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
   const int RR = R * R;
   const int RS = R | 1;
-  for (int idx = tid; idx < RR; idx += nt) {
-    const int i = idx / R, j = idx % R;
-    if (j <= i) {
-      dfl g = {1.f, 0.f};
-      bool first = true;
-      for (int k = 0; k < N; k++) {
-        if (k == n) continue;
-        const dfl sk = {Shi[(int64_t)k * RR + idx], Slo[(int64_t)k * RR + idx]};
-        g = first ? sk : df_mul(g, sk);
-        first = false;
-      }
-      G[i * RS + j] = pk(g);
-    }
-    if (useV) {
+  const int T = R * (R + 1) / 2;
+  const size_t tb = ((size_t)T * sizeof(float2) + 15) / 16 * 16;
+  float2* G = reinterpret_cast<float2*>(csm);
+  float2* B = reinterpret_cast<float2*>(csm + tb);
+  uint32_t* crd = reinterpret_cast<uint32_t*>(csm + 2 * tb);
+  float2* lb = reinterpret_cast<float2*>(csm + 2 * tb + ((size_t)T * 4 + 15) / 16 * 16);
+  float2* ls = lb + 4 * R;                       // [set][column][row], 2 x 2 x R
+  float2* id = ls + 4 * R;
+  float2* lsub = id + R;
+  if (useV) {
+    for (int idx = tid; idx < RR; idx += nt) {
       float zz = 0.f;
       for (int a = 0; a < N; a++) {
         if (a == n) continue;
         for (int b = a + 1; b < N; b++) {
           if (b == n) continue;
-          float h = W[(int64_t)a * RR + idx] * W[(int64_t)b * RR + idx];
+          float h = Wg[(int64_t)a * RR + idx] * Wg[(int64_t)b * RR + idx];
           for (int k = 0; k < N; k++)
             if (k != a && k != b && k != n) h *= Shi[(int64_t)k * RR + idx];
           zz += h;
@@ -297,115 +302,208 @@ chol_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
       Z[idx] = zz;
     }
   }
-  for (int j = tid; j <= R + 1; j += nt) colstart[j] = col_start(min(j, R), R);
+  if (tid == 0) bad = 0;
+  for (int j = warp; j < R; j += nwarp) {
+    const int e0 = col_start(j, R);
+    for (int i = j + lane; i < R; i += 32) {
+      const int idx = i * R + j;
+      dfl v = {0.f, 0.f};
+      bool first = true;
+      for (int k = 0; k < N; k++) {
+        if (k == n) continue;
+        const dfl sk = {Shi[(int64_t)k * RR + idx], Slo[(int64_t)k * RR + idx]};
+        v = first ? sk : df_mul(v, sk);
+        first = false;
+      }
+      G[e0 + i - j] = pk(v);
+      crd[e0 + i - j] = (uint32_t)i | ((uint32_t)j << 16);
+      B[i * (i + 1) / 2 + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+    }
+  }
+  for (int i = tid; i < 2 * R; i += nt) lb[2 * R + i] = make_float2(0.f, 0.f);   // no columns before 0
   __syncthreads();
-  const int E = colstart[R];
-  dfl ipiv_prev = {0.f, 0.f}, il_prev = {0.f, 0.f};
-  for (int k = 0; k <= R; k++) {
-    dfl il = {0.f, 0.f}, ipiv = {0.f, 0.f};
-    if (k < R) {
-      const dfl piv = upk(G[k * RS + k]);
-      if (!(piv.hi > 0.f) || !isfinite(piv.hi)) {
-        // every thread read the same pivot: the exit is uniform
-        if (tid == 0) atomicOr(status, 1 << n);
-        return;
+  // k = -2 is the prologue (columns 0 and 1 from zero columns); then pairs
+  for (int k = -2; k + 2 < R; k += 2) {
+    const int cur = (((k + 2) >> 1) & 1) ^ 1, nxt = cur ^ 1;   // the prologue reads set 1 (zeros)
+    const float2* c0 = lb + cur * 2 * R;
+    const float2* c1 = c0 + R;
+    const float2* s0 = ls + cur * 2 * R;
+    const float2* s1 = s0 + R;
+    float2* n0 = lb + nxt * 2 * R;
+    float2* n1 = n0 + R;
+    float2* m0 = ls + nxt * 2 * R;
+    float2* m1 = m0 + R;
+    // (a) columns p = k+2 and p+1 of L
+    {
+      const int p = k + 2;
+      const int ep = col_start(p, R);
+      const bool two = p + 1 < R;
+      const int ep1 = two ? col_start(p + 1, R) : 0;
+      for (int i = p + tid; i < R; i += nt) {
+        const dfl a2 = upk(c0[p]), b2 = upk(c1[p]);
+        const dfl piv2 = df_fms(df_fms(upk(G[ep]), a2, a2), b2, b2);
+        if (bad_pivot(piv2)) {
+          bad = 1;
+          break;
+        }
+        const dfl il2 = df_rsqrt(piv2);
+        const dfl ci0 = upk(c0[i]), ci1 = upk(c1[i]);
+        const dfl l2 = df_mul(df_fms(df_fms(upk(G[ep + i - p]), ci0, a2), ci1, b2), il2);
+        const dfl q2 = df_mul(l2, il2);
+        n0[i] = pk(l2);
+        m0[i] = pk(q2);
+        if (i == p) id[p] = pk(il2);
+        if (two && i > p) {
+          const dfl a3 = upk(c0[p + 1]), b3 = upk(c1[p + 1]);
+          const dfl c3 = df_mul(df_fms(df_fms(upk(G[ep + 1]), a3, a2), b3, b2), il2);
+          const dfl piv3 = df_fms(df_fms(df_fms(upk(G[ep1]), a3, a3), b3, b3), c3, c3);
+          if (bad_pivot(piv3)) {
+            bad = 1;
+            break;
+          }
+          const dfl il3 = df_rsqrt(piv3);
+          const dfl g3 = df_fms(df_fms(df_fms(upk(G[ep1 + i - p - 1]), ci0, a3), ci1, b3), l2, c3);
+          const dfl l3 = df_mul(g3, il3);
+          n1[i] = pk(l3);
+          m1[i] = pk(df_mul(l3, il3));
+          if (i == p + 1) {
+            id[p + 1] = pk(il3);
+            lsub[p + 1] = pk(q2);
+          }
+        }
       }
-      il = df_rsqrt(piv);
-      ipiv = df_mul(il, il);
-      if (tid == 0) invd[k] = pk(il);
     }
-    // scale column k-1 to L: its entries are a contiguous range
-    if (k > 0) {
-      const int e0 = colstart[k - 1], e1 = colstart[k];
-      for (int e = e0 + tid; e < e1; e += nt) {
-        const int i = (k - 1) + (e - e0);
-        G[i * RS + (k - 1)] = pk(df_mul(upk(G[i * RS + (k - 1)]), il_prev));
+    if (k >= 0) {
+      // (b) trailing update of the columns >= k+4 with the pivots k, k+1
+      if (k + 4 < R) {
+        for (int e = col_start(k + 4, R) + tid; e < T; e += nt) {
+          const uint32_t ij = crd[e];
+          const int i = ij & 0xffffu, j = ij >> 16;
+          dfl g = df_fms(upk(G[e]), upk(c0[i]), upk(c0[j]));
+          G[e] = pk(df_fms(g, upk(c1[i]), upk(c1[j])));
+        }
+      }
+      // (c) inverse update of rows >= k+2, columns <= k+1
+      {
+        const int cols = k + 2, tot = (R - k - 2) * cols;
+        if (tid < tot) {
+          const float rc = 1.f / (float)cols;
+          int q = (int)(((float)tid + 0.5f) * rc), c = tid - q * cols;
+          const int dq = (int)(((float)nt + 0.5f) * rc), dc = nt - dq * cols;
+          const float2* Bk = B + k * (k + 1) / 2;
+          const float2* Bk1 = B + (k + 1) * (k + 2) / 2;
+          const dfl sk1 = upk(s0[k + 1]);
+          for (int t = tid; t < tot; t += nt) {
+            const int i = k + 2 + q;
+            float2* bp = B + i * (i + 1) / 2 + c;
+            dfl b = upk(*bp);
+            if (c <= k) {
+              const dfl bk = upk(Bk[c]);
+              const dfl tc = df_fms(upk(Bk1[c]), sk1, bk);
+              b = df_fms(df_fms(b, upk(s0[i]), bk), upk(s1[i]), tc);
+            } else {
+              b = df_add_fast(b, df_neg(upk(s1[i])));
+            }
+            *bp = pk(b);
+            q += dq;
+            c += dc;
+            if (c >= cols) {
+              c -= cols;
+              q++;
+            }
+          }
+        }
       }
     }
-    // trailing update of columns j > k
-    if (k < R - 1) {
-      const int es = colstart[k + 1];
-      // first owned entry >= es; the column of entry e is the largest j with
-      // colstart[j] <= e (root of j^2 - (2R+1) j + 2e, then exact fix-ups)
-      const float b2 = (float)(2 * R + 1);
-      for (int e = es + ((tid - es) % nt + nt) % nt; e < E; e += nt) {
-        int j = (int)((b2 - sqrtf(fmaxf(b2 * b2 - 8.f * (float)e, 0.f))) * 0.5f);
-        j = max(0, min(j, R - 1));
-        while (j > 0 && colstart[j] > e) j--;
-        while (colstart[j + 1] <= e) j++;
-        const int i = j + (e - colstart[j]);
-        const dfl gik = upk(G[i * RS + k]);
-        const dfl gjk = upk(G[j * RS + k]);
-        const dfl t = df_mul(df_mul(gik, gjk), ipiv);
-        G[i * RS + j] = pk(df_add_fast(upk(G[i * RS + j]), df_neg(t)));
-      }
-    }
-    il_prev = il;
-    ipiv_prev = ipiv;
     __syncthreads();
+    if (bad) {
+      if (tid == 0) atomicOr(status, 1 << n);
+      return;
+    }
   }
-  (void)ipiv_prev;
-  for (int idx = tid; idx < R * RS; idx += nt) {
-    const int i = idx / RS, j = idx % RS;
-    Lout[idx] = (j <= i && j < R) ? G[idx] : make_float2(0.f, 0.f);
+  // W = diag(1 / L_ii) B; odd rows still lack pivot i-1: B_i. -= (L_i,i-1 / L_i-1,i-1) B_i-1.
+  for (int i = warp; i < R; i += nwarp) {
+    const dfl d = upk(id[i]);
+    const bool odd = i & 1;
+    const dfl f = odd ? upk(lsub[i]) : dfl{0.f, 0.f};
+    const float2* Bi = B + i * (i + 1) / 2;
+    const float2* Bp = B + (i - 1) * i / 2;
+    for (int c = lane; c < RS; c += 32) {
+      float2 w = make_float2(0.f, 0.f);
+      if (c < i) {
+        dfl b = upk(Bi[c]);
+        if (odd) b = df_fms(b, f, upk(Bp[c]));
+        w = pk(df_mul(b, d));
+      } else if (c == i) {
+        w = pk(d);
+      }
+      Wout[i * RS + c] = w;
+    }
   }
+}
+
+size_t chol_inv_smem(int R) {
+  const size_t T = (size_t)R * (R + 1) / 2;
+  return 2 * ((T * sizeof(float2) + 15) / 16 * 16) + (T * 4 + 15) / 16 * 16 +
+         10 * (size_t)R * sizeof(float2);
 }
 
 // ---------------------------------------------------------------- row solves
-constexpr int kChunks = kMaxRank / 32;
-
-template <typename V>
-__device__ __forceinline__ V pick(const V (&v)[kChunks], int c) {
-  V out = v[0];
-#pragma unroll
-  for (int i = 1; i < kChunks; i++)
-    if (c == i) out = v[i];
-  return out;
-}
-template <typename V>
-__device__ __forceinline__ void put(V (&v)[kChunks], int c, V x) {
-#pragma unroll
-  for (int i = 0; i < kChunks; i++)
-    if (c == i) v[i] = x;
+// Compensated dot-product accumulator (Dot2 of Ogita, Rump and Oishi, with
+// the double-float operands' cross terms added to the compensation):
+// s.hi is the running float sum, s.lo collects every rounding error.
+__device__ __forceinline__ void dot2_acc(dfl& s, dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const dfl t = two_sum(s.hi, p);
+  s.hi = t.hi;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, e));
 }
 
-// One warp per row y: b = rhs (+ A_old Z, float), forward substitution
-// L z = b, back substitution L^T a = z, all in double-float.  Writes the
-// float64 master A, the double-float copy (Ahi = the float compute copy, Alo),
-// dA = A_new - ref (ref = A_p, or A_old when Arefhi is null) as float64 and
-// float, and per-row ||dA||^2, ||A_new||^2 (double-float).
+// Row y of the normal equations, a Gamma = b (b = rhs, plus A_old Z for the
+// second-order PP terms), solved as a = W^T (W b) with W = L^-1 from the
+// factorisation kernel: two triangular products instead of two substitution
+// chains, so every output entry is an independent compensated dot product.
+// One CTA takes kRB rows at a time; thread r computes entry r of y and then
+// of a (W's zero upper triangle makes the loops warp-uniform).  Writes the
+// float64 master A, the double-float copy (Ahi = the float compute copy,
+// Alo), dA = A_new - ref (ref = A_p, or A_old when Arefhi is null) as
+// float64 and float, and per-row ||dA||^2, ||A_new||^2 (double-float).
+constexpr int kRB = 4;
+
 __global__ void __launch_bounds__(128)
-solve_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float* __restrict__ Ahi,
-                float* __restrict__ Alo, const float* __restrict__ Arefhi,
-                const float* __restrict__ Areflo, double* __restrict__ dA, float* __restrict__ dAc,
-                const float2* __restrict__ Lg, const float2* __restrict__ invg,
-                const float* __restrict__ Zg, float2* __restrict__ rownorm, int s, int R, int n,
-                const int* __restrict__ status) {
+solve_inv_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float* __restrict__ Ahi,
+                    float* __restrict__ Alo, const float* __restrict__ Arefhi,
+                    const float* __restrict__ Areflo, double* __restrict__ dA,
+                    float* __restrict__ dAc, const float2* __restrict__ Wg,
+                    const float* __restrict__ Zg, float2* __restrict__ rownorm, int s, int R, int n,
+                    const int* __restrict__ status) {
   extern __shared__ __align__(16) float2 smem[];
   const int RS = R | 1;
-  float2* Ls = smem;
-  const uint32_t lbytes = (uint32_t)(((size_t)R * RS * sizeof(float2) + 15) / 16 * 16);
-  const uint32_t ibytes = (uint32_t)(((size_t)R * sizeof(float2) + 15) / 16 * 16);
+  float2* Ws = smem;
+  const uint32_t wbytes = (uint32_t)(((size_t)R * RS * sizeof(float2) + 15) / 16 * 16);
   const uint32_t zbytes = Zg ? (uint32_t)(((size_t)R * R * sizeof(float) + 15) / 16 * 16) : 0u;
-  float2* inv = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem) + lbytes);
-  float* Zs = reinterpret_cast<float*>(reinterpret_cast<char*>(smem) + lbytes + ibytes);
+  float* Zs = reinterpret_cast<float*>(reinterpret_cast<char*>(smem) + wbytes);
   __shared__ __align__(8) uint64_t bar;
+  __shared__ float2 bs[kRB][kMaxRank], ys[kRB][kMaxRank];
+  __shared__ float as[kRB][kMaxRank];
+  __shared__ float2 red[kRB][2][kMaxRank / 32];
   const bool failed = (status[0] >> n) & 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarp = blockDim.x >> 5;
+  const int r = threadIdx.x, lane = r & 31, warp = r >> 5, nwarp = blockDim.x >> 5;
+  const bool act = r < R;
+  const int rr = act ? r : R - 1;               // padding threads read a valid row, store nothing
   bool loaded = true;
   if (!failed) {
-    // one bulk asynchronous copy per array (sizes are padded to 16 bytes in global memory)
     const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
     if (threadIdx.x == 0) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
-                   "r"(lbytes + ibytes + zbytes) : "memory");
+                   "r"(wbytes + zbytes) : "memory");
       asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                   ::"r"((uint32_t)__cvta_generic_to_shared(Ls)), "l"(Lg), "r"(lbytes), "r"(b) : "memory");
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                   ::"r"((uint32_t)__cvta_generic_to_shared(inv)), "l"(invg), "r"(ibytes), "r"(b) : "memory");
+                   ::"r"((uint32_t)__cvta_generic_to_shared(Ws)), "l"(Wg), "r"(wbytes), "r"(b) : "memory");
       if (Zg)
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                      ::"r"((uint32_t)__cvta_generic_to_shared(Zs)), "l"(Zg), "r"(zbytes), "r"(b) : "memory");
@@ -424,128 +522,88 @@ solve_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float* __
       }
     }
   }
-  if (!loaded) {
+  // every thread waited on the same barrier; a timeout anywhere reads as failure
+  if (__syncthreads_or(!loaded)) {
     if (threadIdx.x == 0) atomicOr(const_cast<int*>(status) + 2, 1);
     return;
   }
-  // two rows per warp, interleaved: the two substitutions are independent
-  // instruction streams (latency hiding) and share every load of L
-  constexpr int RPW = 2;
-  for (int y0 = (blockIdx.x * nwarp + warp) * RPW; y0 < s; y0 += gridDim.x * nwarp * RPW) {
-    float oh[RPW][kChunks], ol[RPW][kChunks];
-    dfl b[RPW][kChunks];
+  const int cend1 = min(R, 32 * warp + 32);     // W row r is zero beyond column r
+  const int cbeg2 = 32 * warp;                  // W column r is zero above row r
+  for (int y0 = blockIdx.x * kRB; y0 < s; y0 += gridDim.x * kRB) {
+    float oh[kRB], ol[kRB];
+    dfl a[kRB];
 #pragma unroll
-    for (int w = 0; w < RPW; w++) {
-      const int y = min(y0 + w, s - 1);      // a missing second row repeats the first (not stored)
-#pragma unroll
-      for (int c = 0; c < kChunks; c++) {
-        const int r = lane + 32 * c;
-        const bool v = r < R;
-        oh[w][c] = v ? Ahi[(int64_t)y * R + r] : 0.f;
-        ol[w][c] = v ? Alo[(int64_t)y * R + r] : 0.f;
-        b[w][c] = {v ? rhs[(int64_t)y * R + r] : 0.f, 0.f};
-      }
+    for (int w = 0; w < kRB; w++) {
+      const int y = min(y0 + w, s - 1);         // rows past the end repeat the last one (not stored)
+      const int64_t o = (int64_t)y * R + rr;
+      oh[w] = Ahi[o];
+      ol[w] = Alo[o];
+      a[w] = {rhs[o], 0.f};
+      as[w][rr] = oh[w];
     }
     if (failed) {
 #pragma unroll
-      for (int w = 0; w < RPW; w++)
-#pragma unroll
-        for (int c = 0; c < kChunks; c++) b[w][c] = {oh[w][c], ol[w][c]};
+      for (int w = 0; w < kRB; w++) a[w] = {oh[w], ol[w]};
     } else {
       if (Zg) {
+        __syncthreads();
         // second-order PP terms: b += A_old Z (float)
-        float vz[RPW][kChunks];
+        float vz[kRB];
 #pragma unroll
-        for (int w = 0; w < RPW; w++)
-#pragma unroll
-          for (int c = 0; c < kChunks; c++) vz[w][c] = 0.f;
+        for (int w = 0; w < kRB; w++) vz[w] = 0.f;
         for (int k = 0; k < R; k++) {
-          float ak[RPW];
+          const float zz = Zs[k * R + rr];
 #pragma unroll
-          for (int w = 0; w < RPW; w++) ak[w] = __shfl_sync(0xffffffffu, pick(oh[w], k >> 5), k & 31);
-#pragma unroll
-          for (int c = 0; c < kChunks; c++) {
-            const int r = lane + 32 * c;
-            if (32 * c < R && r < R) {
-              const float zz = Zs[k * R + r];
-#pragma unroll
-              for (int w = 0; w < RPW; w++) vz[w][c] = fmaf(ak[w], zz, vz[w][c]);
-            }
-          }
+          for (int w = 0; w < kRB; w++) vz[w] = fmaf(as[w][k], zz, vz[w]);
         }
 #pragma unroll
-        for (int w = 0; w < RPW; w++)
-#pragma unroll
-          for (int c = 0; c < kChunks; c++) b[w][c] = df_add(b[w][c], dfl{vz[w][c], 0.f});
+        for (int w = 0; w < kRB; w++) a[w] = df_add(a[w], dfl{vz[w], 0.f});
       }
-      // forward substitution L z = b (updates use the one-TwoSum addition:
-      // backward error of a few 2^-48 relative to the operands)
-      for (int i = 0; i < R; i++) {
-        const int ci = i >> 5, li = i & 31;
-        const dfl inv_i = upk(inv[i]);
-        dfl zi[RPW];
 #pragma unroll
-        for (int w = 0; w < RPW; w++) {
-          const dfl bi = pick(b[w], ci);
-          const dfl src = {__shfl_sync(0xffffffffu, bi.hi, li), __shfl_sync(0xffffffffu, bi.lo, li)};
-          zi[w] = df_mul(src, inv_i);
-          if (lane == li) put(b[w], ci, zi[w]);
-        }
+      for (int w = 0; w < kRB; w++) bs[w][rr] = pk(a[w]);
+      __syncthreads();
+      // y = W b
+      dfl acc[kRB];
 #pragma unroll
-        for (int c = 0; c < kChunks; c++) {
-          if (32 * c + 31 <= i || 32 * c >= R) continue;
-          const int r = lane + 32 * c;
-          if (r > i && r < R) {
-            const dfl l = upk(Ls[r * RS + i]);
+      for (int w = 0; w < kRB; w++) acc[w] = {0.f, 0.f};
+      const float2* wr = Ws + rr * RS;
+#pragma unroll 2
+      for (int c = 0; c < cend1; c++) {
+        const dfl wv = upk(wr[c]);
 #pragma unroll
-            for (int w = 0; w < RPW; w++) b[w][c] = df_add_fast(b[w][c], df_neg(df_mul(l, zi[w])));
-          }
-        }
+        for (int w = 0; w < kRB; w++) dot2_acc(acc[w], wv, upk(bs[w][c]));
       }
-      // back substitution L^T a = z
-      for (int i = R - 1; i >= 0; i--) {
-        const int ci = i >> 5, li = i & 31;
-        const dfl inv_i = upk(inv[i]);
-        dfl ai[RPW];
 #pragma unroll
-        for (int w = 0; w < RPW; w++) {
-          const dfl bi = pick(b[w], ci);
-          const dfl src = {__shfl_sync(0xffffffffu, bi.hi, li), __shfl_sync(0xffffffffu, bi.lo, li)};
-          ai[w] = df_mul(src, inv_i);
-          if (lane == li) put(b[w], ci, ai[w]);
-        }
+      for (int w = 0; w < kRB; w++) ys[w][rr] = pk(fast_two_sum(acc[w].hi, acc[w].lo));
+      __syncthreads();
+      // a = W^T y
 #pragma unroll
-        for (int c = 0; c < kChunks; c++) {
-          if (32 * c >= i) continue;
-          const int r = lane + 32 * c;
-          if (r < i) {
-            const dfl l = upk(Ls[i * RS + r]);
+      for (int w = 0; w < kRB; w++) acc[w] = {0.f, 0.f};
+#pragma unroll 2
+      for (int c = cbeg2; c < R; c++) {
+        const dfl wv = upk(Ws[c * RS + rr]);
 #pragma unroll
-            for (int w = 0; w < RPW; w++) b[w][c] = df_add_fast(b[w][c], df_neg(df_mul(l, ai[w])));
-          }
-        }
+        for (int w = 0; w < kRB; w++) dot2_acc(acc[w], wv, upk(ys[w][c]));
       }
+#pragma unroll
+      for (int w = 0; w < kRB; w++) a[w] = fast_two_sum(acc[w].hi, acc[w].lo);
     }
+    // outputs and per-row norms
 #pragma unroll
-    for (int w = 0; w < RPW; w++) {
+    for (int w = 0; w < kRB; w++) {
       const int y = y0 + w;
-      if (y >= s) break;
       dfl nd = {0.f, 0.f}, na = {0.f, 0.f};
-#pragma unroll
-      for (int c = 0; c < kChunks; c++) {
-        const int r = lane + 32 * c;
-        if (r < R) {
-          const int64_t o = (int64_t)y * R + r;
-          const dfl ref = Arefhi ? dfl{Arefhi[o], Areflo[o]} : dfl{oh[w][c], ol[w][c]};
-          const dfl d = df_sub(b[w][c], ref);
-          A[o] = df_dbl(b[w][c]);
-          Ahi[o] = b[w][c].hi;
-          Alo[o] = b[w][c].lo;
-          dA[o] = df_dbl(d);
-          dAc[o] = d.hi;
-          nd = df_add(nd, df_mul(d, d));
-          na = df_add(na, df_mul(b[w][c], b[w][c]));
-        }
+      if (act && y < s) {
+        const int64_t o = (int64_t)y * R + r;
+        const dfl ref = Arefhi ? dfl{Arefhi[o], Areflo[o]} : dfl{oh[w], ol[w]};
+        const dfl d = df_sub(a[w], ref);
+        A[o] = df_dbl(a[w]);
+        Ahi[o] = a[w].hi;
+        Alo[o] = a[w].lo;
+        dA[o] = df_dbl(d);
+        dAc[o] = d.hi;
+        nd = df_mul(d, d);
+        na = df_mul(a[w], a[w]);
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
@@ -553,10 +611,21 @@ solve_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float* __
         na = df_add(na, dfl{__shfl_xor_sync(0xffffffffu, na.hi, off), __shfl_xor_sync(0xffffffffu, na.lo, off)});
       }
       if (lane == 0) {
-        rownorm[2 * y] = pk(nd);
-        rownorm[2 * y + 1] = pk(na);
+        red[w][0][warp] = pk(nd);
+        red[w][1][warp] = pk(na);
       }
     }
+    __syncthreads();
+    if (r < kRB && y0 + r < s) {
+      dfl nd = upk(red[r][0][0]), na = upk(red[r][1][0]);
+      for (int q = 1; q < nwarp; q++) {
+        nd = df_add(nd, upk(red[r][0][q]));
+        na = df_add(na, upk(red[r][1][q]));
+      }
+      rownorm[2 * (y0 + r)] = pk(nd);
+      rownorm[2 * (y0 + r) + 1] = pk(na);
+    }
+    __syncthreads();                            // bs/ys/as/red are reused by the next rows
   }
 }
 
@@ -565,13 +634,12 @@ solve_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float* __
 // ---------------------------------------------------------------- host wrappers
 cudaError_t setup_df_kernels() {
   const int RSmax = kMaxRank | 1;
-  const int g = (int)(kMaxRank * RSmax * sizeof(float2));
-  const int sv = (int)(kMaxRank * RSmax * sizeof(float2) + 16 + kMaxRank * sizeof(float2) +
-                       kMaxRank * kMaxRank * sizeof(float));
-  cudaError_t e =
-      cudaFuncSetAttribute(chol_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, g);
+  const int sv = (int)(kMaxRank * RSmax * sizeof(float2) + 16 + kMaxRank * kMaxRank * sizeof(float));
+  cudaError_t e = cudaFuncSetAttribute(chol_inv_df_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)chol_inv_smem(kMaxRank));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(solve_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sv);
+    e = cudaFuncSetAttribute(solve_inv_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sv);
   return e;
 }
 
@@ -596,23 +664,25 @@ void gram_df(const float* Ahi, const float* Alo, const float* Aw, const float* d
 }
 
 void chol_df(const float* Shi, const float* Slo, const float* W, int N, int n, int R,
-             float2* Lout, float2* invd, float* Z, bool useV, int* status, Launch L) {
-  const size_t smem = (size_t)R * (R | 1) * sizeof(float2);
-  chol_df_kernel<<<1, kCholThreads, smem, L.stream>>>(Shi, Slo, W, N, n, R, Lout, invd, Z,
-                                                      useV ? 1 : 0, status);
+             float2* Winv, float* Z, bool useV, int* status, Launch L) {
+  // about eight packed entries per thread at the first step, 128..CPALS_CHOL_THREADS threads
+  const int T = R * (R + 1) / 2;
+  const int threads = std::min(CPALS_CHOL_THREADS, std::max(128, (T / 8 + 31) / 32 * 32));
+  chol_inv_df_kernel<<<1, threads, chol_inv_smem(R), L.stream>>>(Shi, Slo, W, N, n, R, Winv, Z,
+                                                                 useV ? 1 : 0, status);
   (*L.counter)++;
 }
 
 void solve_df(const float* rhs, double* A, float* Ahi, float* Alo, const float* Arefhi,
-              const float* Areflo, double* dA, float* dAc, const float2* Lf, const float2* invd,
-              const float* Z, float2* rownorm, int s, int R, int n, const int* status, Launch L) {
-  const size_t lb = ((size_t)R * (R | 1) * sizeof(float2) + 15) / 16 * 16;
-  const size_t ib = ((size_t)R * sizeof(float2) + 15) / 16 * 16;
+              const float* Areflo, double* dA, float* dAc, const float2* Winv, const float* Z,
+              float2* rownorm, int s, int R, int n, const int* status, Launch L) {
+  const size_t wb = ((size_t)R * (R | 1) * sizeof(float2) + 15) / 16 * 16;
   const size_t zb = Z ? ((size_t)R * R * sizeof(float) + 15) / 16 * 16 : 0;
-  const int warps = 2, rows_per_block = 2 * warps;      // two rows per warp
-  const int blocks = (int)std::min<int64_t>(cdiv(s, rows_per_block), 152 * 2);
-  solve_df_kernel<<<blocks, 32 * warps, lb + ib + zb, L.stream>>>(
-      rhs, A, Ahi, Alo, Arefhi, Areflo, dA, dAc, Lf, invd, Z, rownorm, s, R, n, status);
+  const int threads = (R + 31) / 32 * 32;
+  const int blocks = (int)std::min<int64_t>(cdiv(s, kRB), 152 * 2);
+  solve_inv_df_kernel<<<blocks, threads, wb + zb, L.stream>>>(rhs, A, Ahi, Alo, Arefhi, Areflo, dA,
+                                                              dAc, Winv, Z, rownorm, s, R, n,
+                                                              status);
   (*L.counter)++;
 }
 

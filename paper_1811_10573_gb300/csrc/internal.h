@@ -117,11 +117,13 @@ void split_df(const double* A, float* hi, float* lo, int64_t n, Launch L);
 void gram_df(const float* Ahi, const float* Alo, const float* Aw, const float* dAw, double* S,
              float* Shi, float* Slo, float* W, bool withW, int s, int R, const float2* rownorm,
              double* scal, float2* partials, int* tickets, Launch L);
-void chol_df(const float* Shi, const float* Slo, const float* W, int N, int n, int R, float2* Lout,
-             float2* invd, float* Z, bool useV, int* status, Launch L);
+// chol_df: Gamma^(n) = L L^T and Winv = L^-1 (row stride R|1, zero upper
+// triangle); solve_df: a = Winv^T Winv b per row.
+void chol_df(const float* Shi, const float* Slo, const float* W, int N, int n, int R, float2* Winv,
+             float* Z, bool useV, int* status, Launch L);
 void solve_df(const float* rhs, double* A, float* Ahi, float* Alo, const float* Arefhi,
-              const float* Areflo, double* dA, float* dAc, const float2* Lf, const float2* invd,
-              const float* Z, float2* rownorm, int s, int R, int n, const int* status, Launch L);
+              const float* Areflo, double* dA, float* dAc, const float2* Winv, const float* Z,
+              float2* rownorm, int s, int R, int n, const int* status, Launch L);
 
 // ---------------------------------------------------------------- tcgen05 (sm_103a)
 // bf16 tensor-core first-level contraction, fp32 accumulate in TMEM, TMA-fed:
