@@ -242,30 +242,52 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
 //   crd the (row, column) of every packed index;
 //   B   the lower triangle of the inverse in progress, packed by rows
 //       (entry (i, c) at i (i + 1) / 2 + c), initially the identity;
-//   the current pair of columns of L, the same divided by their diagonal
-//   entries, both double-buffered, 1 / L_jj and L_{k+1,k} / L_kk.
+//   per row, double-buffered: the current pair of columns (L_ik, L_i,k+1)
+//   and the pair of inverse-update coefficients (u_i, v_i) below; 1 / L_jj;
+//   L_{j,j-1} / L_{j-1,j-1} for odd j.
 // Step k (pivots k and k+1 done; Golub & Van Loan Alg. 4.2.2 for the factor,
 // the column-oriented triangular inverse for W):
 //   (a) columns k+2 and k+3 of L from the unupdated G columns and columns k,
-//       k+1 (each thread recomputes the two pivots and L_{k+3,k+2} it needs);
+//       k+1 (each thread recomputes the two pivots and L_{k+3,k+2}), and the
+//       coefficients of those two columns for the inverse;
 //   (b) G_ij -= L_ik L_jk + L_i,k+1 L_j,k+1 for the columns j >= k+4;
-//   (c) B_ic -= (L_ik / L_kk) B_kc + (L_i,k+1 / L_k+1,k+1) t_c for rows
-//       i >= k+2, c <= k+1, where t is row k+1 of B after pivot k (formed on
-//       the fly; row k+1 itself is updated at the end).
+//   (c) B_ic -= u_i B_kc + v_i B_k+1,c for rows i >= k+2, c <= k+1, where
+//       v_i = L_i,k+1 / L_k+1,k+1 and u_i = L_ik / L_kk - v_i L_k+1,k / L_kk:
+//       pivot k and pivot k+1 (which sees row k+1 after pivot k) in one pass.
+//       Row k+1 itself gets pivot k at the end.
 // Row j of W is then the final row j of B divided by L_jj.  The work of (b)
 // falls and that of (c) rises with k, which keeps the steps evenly loaded.
-// Additions in the updates use the one-TwoSum double-word addition (backward
-// error a few units of 2^-48 relative to the operands).  Writes W (row
-// stride RS = R | 1, zeros above the diagonal and in the padding column)
-// and, with useV, the float matrix Z of the second-order PP terms (Eq. 3).
+// Every update is one fused double-float g - a b - c d (exact leading
+// products and sums, one renormalisation: backward error a few units of
+// 2^-48 relative to the operands).  Writes W (row stride RS = R | 1, zeros
+// above the diagonal and in the padding column) and, with useV, the float
+// matrix Z of the second-order PP terms (Eq. 3).
 #ifndef CPALS_CHOL_THREADS
 #define CPALS_CHOL_THREADS 512
 #endif
 __device__ __forceinline__ int col_start(int j, int R) { return j * R - j * (j - 1) / 2; }
+// g - a b - c d
+__device__ __forceinline__ dfl df_fms2(dfl g, dfl a, dfl b, dfl c, dfl d) {
+  const float p1 = __fmul_rn(a.hi, b.hi);
+  float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+  e1 = __fmaf_rn(a.hi, b.lo, e1);
+  e1 = __fmaf_rn(a.lo, b.hi, e1);
+  const float p2 = __fmul_rn(c.hi, d.hi);
+  float e2 = __fmaf_rn(c.hi, d.hi, -p2);
+  e2 = __fmaf_rn(c.hi, d.lo, e2);
+  e2 = __fmaf_rn(c.lo, d.hi, e2);
+  const dfl s = two_sum(g.hi, -p1);
+  const dfl t = two_sum(s.hi, -p2);
+  const float lo = __fsub_rn(__fsub_rn(__fadd_rn(__fadd_rn(g.lo, s.lo), t.lo), e1), e2);
+  return fast_two_sum(t.hi, lo);
+}
 __device__ __forceinline__ dfl df_fms(dfl g, dfl a, dfl b) {   // g - a b
   return df_add_fast(g, df_neg(df_mul(a, b)));
 }
 __device__ __forceinline__ bool bad_pivot(dfl p) { return !(p.hi > 0.f) || !isfinite(p.hi); }
+__device__ __forceinline__ dfl lo2(float4 v) { return {v.x, v.y}; }
+__device__ __forceinline__ dfl hi2(float4 v) { return {v.z, v.w}; }
+__device__ __forceinline__ float4 pk2(dfl a, dfl b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
 
 __global__ void __launch_bounds__(1024, 1)
 chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
@@ -281,11 +303,11 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
   const size_t tb = ((size_t)T * sizeof(float2) + 15) / 16 * 16;
   float2* G = reinterpret_cast<float2*>(csm);
   float2* B = reinterpret_cast<float2*>(csm + tb);
-  uint32_t* crd = reinterpret_cast<uint32_t*>(csm + 2 * tb);
-  float2* lb = reinterpret_cast<float2*>(csm + 2 * tb + ((size_t)T * 4 + 15) / 16 * 16);
-  float2* ls = lb + 4 * R;                       // [set][column][row], 2 x 2 x R
-  float2* id = ls + 4 * R;
+  float4* lc = reinterpret_cast<float4*>(csm + 2 * tb);   // [set][row] (L_ik, L_i,k+1)
+  float4* uv = lc + 2 * R;                                 // [set][row] (u_i, v_i)
+  float2* id = reinterpret_cast<float2*>(uv + 2 * R);
   float2* lsub = id + R;
+  uint32_t* crd = reinterpret_cast<uint32_t*>(lsub + R);
   if (useV) {
     for (int idx = tid; idx < RR; idx += nt) {
       float zz = 0.f;
@@ -320,57 +342,55 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
       B[i * (i + 1) / 2 + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
     }
   }
-  for (int i = tid; i < 2 * R; i += nt) lb[2 * R + i] = make_float2(0.f, 0.f);   // no columns before 0
+  for (int i = tid; i < R; i += nt) lc[R + i] = make_float4(0.f, 0.f, 0.f, 0.f);  // no columns before 0
   __syncthreads();
   // k = -2 is the prologue (columns 0 and 1 from zero columns); then pairs
   for (int k = -2; k + 2 < R; k += 2) {
     const int cur = (((k + 2) >> 1) & 1) ^ 1, nxt = cur ^ 1;   // the prologue reads set 1 (zeros)
-    const float2* c0 = lb + cur * 2 * R;
-    const float2* c1 = c0 + R;
-    const float2* s0 = ls + cur * 2 * R;
-    const float2* s1 = s0 + R;
-    float2* n0 = lb + nxt * 2 * R;
-    float2* n1 = n0 + R;
-    float2* m0 = ls + nxt * 2 * R;
-    float2* m1 = m0 + R;
-    // (a) columns p = k+2 and p+1 of L
+    const float4* cc = lc + cur * R;
+    const float4* cu = uv + cur * R;
+    float4* nc = lc + nxt * R;
+    float4* nu = uv + nxt * R;
+    // (a) columns p = k+2 and p+1 of L and their inverse-update coefficients
     {
       const int p = k + 2;
       const int ep = col_start(p, R);
       const bool two = p + 1 < R;
       const int ep1 = two ? col_start(p + 1, R) : 0;
       for (int i = p + tid; i < R; i += nt) {
-        const dfl a2 = upk(c0[p]), b2 = upk(c1[p]);
-        const dfl piv2 = df_fms(df_fms(upk(G[ep]), a2, a2), b2, b2);
+        const float4 cp = cc[p];
+        const dfl a2 = lo2(cp), b2 = hi2(cp);
+        const dfl piv2 = df_fms2(upk(G[ep]), a2, a2, b2, b2);
         if (bad_pivot(piv2)) {
           bad = 1;
           break;
         }
         const dfl il2 = df_rsqrt(piv2);
-        const dfl ci0 = upk(c0[i]), ci1 = upk(c1[i]);
-        const dfl l2 = df_mul(df_fms(df_fms(upk(G[ep + i - p]), ci0, a2), ci1, b2), il2);
+        const float4 ci = cc[i];
+        const dfl l2 = df_mul(df_fms2(upk(G[ep + i - p]), lo2(ci), a2, hi2(ci), b2), il2);
         const dfl q2 = df_mul(l2, il2);
-        n0[i] = pk(l2);
-        m0[i] = pk(q2);
+        dfl l3 = {0.f, 0.f}, u = q2, v = {0.f, 0.f};
         if (i == p) id[p] = pk(il2);
         if (two && i > p) {
-          const dfl a3 = upk(c0[p + 1]), b3 = upk(c1[p + 1]);
-          const dfl c3 = df_mul(df_fms(df_fms(upk(G[ep + 1]), a3, a2), b3, b2), il2);
-          const dfl piv3 = df_fms(df_fms(df_fms(upk(G[ep1]), a3, a3), b3, b3), c3, c3);
+          const float4 cp1 = cc[p + 1];
+          const dfl a3 = lo2(cp1), b3 = hi2(cp1);
+          const dfl c3 = df_mul(df_fms2(upk(G[ep + 1]), a3, a2, b3, b2), il2);
+          const dfl piv3 = df_fms(df_fms2(upk(G[ep1]), a3, a3, b3, b3), c3, c3);
           if (bad_pivot(piv3)) {
             bad = 1;
             break;
           }
           const dfl il3 = df_rsqrt(piv3);
-          const dfl g3 = df_fms(df_fms(df_fms(upk(G[ep1 + i - p - 1]), ci0, a3), ci1, b3), l2, c3);
-          const dfl l3 = df_mul(g3, il3);
-          n1[i] = pk(l3);
-          m1[i] = pk(df_mul(l3, il3));
+          l3 = df_mul(df_fms(df_fms2(upk(G[ep1 + i - p - 1]), lo2(ci), a3, hi2(ci), b3), l2, c3), il3);
+          v = df_mul(l3, il3);
+          u = df_fms(q2, v, df_mul(c3, il2));
           if (i == p + 1) {
             id[p + 1] = pk(il3);
             lsub[p + 1] = pk(q2);
           }
         }
+        nc[i] = pk2(l2, l3);
+        nu[i] = pk2(u, v);
       }
     }
     if (k >= 0) {
@@ -378,9 +398,8 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
       if (k + 4 < R) {
         for (int e = col_start(k + 4, R) + tid; e < T; e += nt) {
           const uint32_t ij = crd[e];
-          const int i = ij & 0xffffu, j = ij >> 16;
-          dfl g = df_fms(upk(G[e]), upk(c0[i]), upk(c0[j]));
-          G[e] = pk(df_fms(g, upk(c1[i]), upk(c1[j])));
+          const float4 li = cc[ij & 0xffffu], lj = cc[ij >> 16];
+          G[e] = pk(df_fms2(upk(G[e]), lo2(li), lo2(lj), hi2(li), hi2(lj)));
         }
       }
       // (c) inverse update of rows >= k+2, columns <= k+1
@@ -392,19 +411,13 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
           const int dq = (int)(((float)nt + 0.5f) * rc), dc = nt - dq * cols;
           const float2* Bk = B + k * (k + 1) / 2;
           const float2* Bk1 = B + (k + 1) * (k + 2) / 2;
-          const dfl sk1 = upk(s0[k + 1]);
           for (int t = tid; t < tot; t += nt) {
             const int i = k + 2 + q;
             float2* bp = B + i * (i + 1) / 2 + c;
-            dfl b = upk(*bp);
-            if (c <= k) {
-              const dfl bk = upk(Bk[c]);
-              const dfl tc = df_fms(upk(Bk1[c]), sk1, bk);
-              b = df_fms(df_fms(b, upk(s0[i]), bk), upk(s1[i]), tc);
-            } else {
-              b = df_add_fast(b, df_neg(upk(s1[i])));
-            }
-            *bp = pk(b);
+            const float4 w = cu[i];
+            const dfl bk = c <= k ? upk(Bk[c]) : dfl{0.f, 0.f};
+            const dfl bk1 = c <= k ? upk(Bk1[c]) : dfl{1.f, 0.f};
+            *bp = pk(df_fms2(upk(*bp), lo2(w), bk, hi2(w), bk1));
             q += dq;
             c += dc;
             if (c >= cols) {
@@ -444,8 +457,8 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
 
 size_t chol_inv_smem(int R) {
   const size_t T = (size_t)R * (R + 1) / 2;
-  return 2 * ((T * sizeof(float2) + 15) / 16 * 16) + (T * 4 + 15) / 16 * 16 +
-         10 * (size_t)R * sizeof(float2);
+  return 2 * ((T * sizeof(float2) + 15) / 16 * 16) + 4 * (size_t)R * sizeof(float4) +
+         2 * (size_t)R * sizeof(float2) + T * 4;
 }
 
 // ---------------------------------------------------------------- row solves
