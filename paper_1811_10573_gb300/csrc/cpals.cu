@@ -300,7 +300,7 @@ void finish_mode(cpals_ctx* c, int n, const T* rhs, bool pp, bool useV) {
              v ? c->Zf : nullptr, (float2*)c->rownorm, s, R, n, c->status, c->L());
     gram_df(Ahi, c->Alo[n], Ahi, P<const float>(c->dAc[n]), c->S + off, c->Shi + off,
             c->Slo + off, c->Wf + off, pp, s, R, (const float2*)c->rownorm, c->scal + 8 + 2 * n,
-            (float2*)c->dpart, c->tickets, c->L());
+            c->L());
     return;
   }
   if (v)
@@ -872,7 +872,7 @@ cpals_status cpals_init_factors(cpals_ctx* c, const double* const* factors) {
       gram_df(P<const float>(c->Ac[n]), c->Alo[n], P<const float>(c->Ac[n]),
               P<const float>(c->dAc[n]), c->S + off, c->Shi + off, c->Slo + off, c->Wf + off,
               false, (int)c->dims[n], R, (const float2*)c->rownorm, c->scal + 48,
-              (float2*)c->dpart, c->tickets, c->L());
+              c->L());
     } else {
       gram_update<double>(c->A[n], P<const double>(c->Ac[n]), P<const double>(c->dAc[n]),
                           c->S + off, c->W + off, false, (int)c->dims[n], R, c->rownorm,

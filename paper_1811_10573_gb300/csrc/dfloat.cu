@@ -14,7 +14,11 @@
 // the IEEE float64 kernels of small.cu.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace cpals {
 
@@ -97,22 +101,27 @@ __global__ void split_kernel(const double* __restrict__ A, float* __restrict__ h
 // (TwoProd), sums are compensated (TwoSum, the Dot2 scheme of Ogita, Rump and
 // Oishi) and the cross terms hi*lo are added in float: the tile comes out as
 // if accumulated in twice the float precision.  W = Aw^T dAw (float; only the
-// second-order PP terms use it).  One launch; the last CTA of each tile
-// (ticket) reduces its split partials in split order with double-word adds.
+// second-order PP terms use it).  One thread-block cluster per 32 x 32 output
+// tile; its CTAs take consecutive row chunks, keep their partial tile in
+// shared memory and, after a cluster barrier, each CTA adds one slice of the
+// tile over all partials (distributed shared memory, split order) and writes
+// it: no global partials, fences or atomics.  CTA 0 of the grid also sums
+// the per-row ||dA||^2 and ||A||^2 of the row solve (written by the previous
+// kernel) in a fixed order.
 __global__ void __launch_bounds__(256)
 gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
                const float* __restrict__ Aw, const float* __restrict__ dAw, int s, int R, int nb,
-               int ntS, int ntiles, int splits, int chunk, float2* __restrict__ part,
-               int* __restrict__ tickets, double* __restrict__ S, float* __restrict__ Shi,
+               int ntS, int splits, int chunk, double* __restrict__ S, float* __restrict__ Shi,
                float* __restrict__ Slo, float* __restrict__ W, const float2* __restrict__ rownorm,
                double* __restrict__ scal) {
-  const int t = blockIdx.x % ntiles;
-  const int z = blockIdx.x / ntiles;
+  cg::cluster_group cl = cg::this_cluster();
+  const int z = (int)cl.block_rank();
+  const int t = blockIdx.x / splits;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int y0 = z * chunk, y1 = min(s, y0 + chunk);
-  float2* p = part + ((int64_t)z * ntiles + t) * 1024;
-  int ti, tj;
   __shared__ float Ah[32][33], Al[32][33], Bh[32][33], Bl[32][33];
+  __shared__ float2 part[1024];
+  int ti, tj;
   if (t < ntS) {
     int tt = t;
     ti = 0;
@@ -146,7 +155,7 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
       __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < 4; q++) p[(ty + 8 * q) * 32 + tx] = pk(fast_two_sum(sh[q], sl[q]));
+    for (int q = 0; q < 4; q++) part[(ty + 8 * q) * 32 + tx] = pk(fast_two_sum(sh[q], sl[q]));
   } else {
     ti = (t - ntS) / nb;
     tj = (t - ntS) % nb;
@@ -169,26 +178,27 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
       __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < 4; q++) p[(ty + 8 * q) * 32 + tx] = make_float2(acc[q], 0.f);
+    for (int q = 0; q < 4; q++) part[(ty + 8 * q) * 32 + tx] = make_float2(acc[q], 0.f);
   }
-  __shared__ int last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(&tickets[t], 1) == splits - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  const int RR = R * R;
-  for (int e = threadIdx.x; e < 1024; e += 256) {
-    dfl acc = upk(__ldcg(part + (int64_t)t * 1024 + e));
-    for (int zz = 1; zz < splits; zz++)
-      acc = df_add(acc, upk(__ldcg(part + ((int64_t)zz * ntiles + t) * 1024 + e)));
+  cl.sync();                                   // every partial tile is in its CTA's shared memory
+  // this CTA's slice of the tile, summed over the partials in split order
+  const int per = (1024 + splits - 1) / splits;
+  const int eend = min(1024, z * per + per);
+  for (int e = z * per + (int)threadIdx.x; e < eend; e += blockDim.x) {
+    float2 v[8];
+#pragma unroll
+    for (int zz = 0; zz < 8; zz++)
+      if (zz < splits) v[zz] = *cl.map_shared_rank(&part[e], zz);
+    dfl acc = upk(v[0]);
+#pragma unroll
+    for (int zz = 1; zz < 8; zz++)
+      if (zz < splits) acc = t < ntS ? df_add(acc, upk(v[zz])) : dfl{acc.hi + v[zz].x, 0.f};
     const int i = ti * 32 + e / 32, j = tj * 32 + e % 32;
     if (i < R && j < R) {
       if (t < ntS) {
-        const double v = df_dbl(acc);
-        S[i * R + j] = v;
-        S[j * R + i] = v;
+        const double d = df_dbl(acc);
+        S[i * R + j] = d;
+        S[j * R + i] = d;
         Shi[i * R + j] = acc.hi;
         Shi[j * R + i] = acc.hi;
         Slo[i * R + j] = acc.lo;
@@ -198,21 +208,14 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
       }
     }
   }
-  (void)RR;
-  __shared__ int lastall;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    tickets[t] = 0;
-    lastall = (atomicAdd(&tickets[63], 1) == ntiles - 1);
-  }
-  __syncthreads();
-  if (!lastall) return;
+  cl.sync();                                   // no CTA leaves while its partial is being read
+  if (blockIdx.x != 0) return;
   // per-row ||dA||^2 and ||A||^2 (double-float) reduced in a fixed order
   __shared__ float2 rd[256], ra[256];
   dfl a = {0.f, 0.f}, b = {0.f, 0.f};
   for (int y = threadIdx.x; y < s; y += blockDim.x) {
-    a = df_add(a, upk(__ldcg(rownorm + 2 * y)));
-    b = df_add(b, upk(__ldcg(rownorm + 2 * y + 1)));
+    a = df_add(a, upk(rownorm[2 * y]));
+    b = df_add(b, upk(rownorm[2 * y + 1]));
   }
   rd[threadIdx.x] = pk(a);
   ra[threadIdx.x] = pk(b);
@@ -227,7 +230,6 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
   if (threadIdx.x == 0) {
     scal[0] = df_dbl(upk(rd[0]));
     scal[1] = df_dbl(upk(ra[0]));
-    tickets[63] = 0;
   }
 }
 
@@ -263,7 +265,7 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
 // above the diagonal and in the padding column) and, with useV, the float
 // matrix Z of the second-order PP terms (Eq. 3).
 #ifndef CPALS_CHOL_THREADS
-#define CPALS_CHOL_THREADS 512
+#define CPALS_CHOL_THREADS 640
 #endif
 __device__ __forceinline__ int col_start(int j, int R) { return j * R - j * (j - 1) / 2; }
 // g - a b - c d
@@ -329,14 +331,15 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
     const int e0 = col_start(j, R);
     for (int i = j + lane; i < R; i += 32) {
       const int idx = i * R + j;
-      dfl v = {0.f, 0.f};
-      bool first = true;
-      for (int k = 0; k < N; k++) {
-        if (k == n) continue;
-        const dfl sk = {Shi[(int64_t)k * RR + idx], Slo[(int64_t)k * RR + idx]};
-        v = first ? sk : df_mul(v, sk);
-        first = false;
-      }
+      dfl sk[kMaxModes];                        // all loads first, then the products
+#pragma unroll
+      for (int k = 0; k < kMaxModes; k++)
+        sk[k] = (k < N && k != n) ? dfl{Shi[(int64_t)k * RR + idx], Slo[(int64_t)k * RR + idx]}
+                                  : dfl{1.f, 0.f};
+      dfl v = sk[0];
+#pragma unroll
+      for (int k = 1; k < kMaxModes; k++)
+        if (k < N) v = df_mul(v, sk[k]);
       G[e0 + i - j] = pk(v);
       crd[e0 + i - j] = (uint32_t)i | ((uint32_t)j << 16);
       B[i * (i + 1) / 2 + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
@@ -344,6 +347,12 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
   }
   for (int i = tid; i < R; i += nt) lc[R + i] = make_float4(0.f, 0.f, 0.f, 0.f);  // no columns before 0
   __syncthreads();
+  // The first 128 threads compute the next column pair (a); the others do
+  // the updates (b) and (c), so the long dependent chain of (a) is not
+  // followed by an update share on the same warps.  Small CTAs do both.
+  const int na = nt > 128 ? 128 : nt;
+  const int ub = nt > 128 ? 128 : 0;
+  const int ut = tid - ub, nu_t = nt - ub;
   // k = -2 is the prologue (columns 0 and 1 from zero columns); then pairs
   for (int k = -2; k + 2 < R; k += 2) {
     const int cur = (((k + 2) >> 1) & 1) ^ 1, nxt = cur ^ 1;   // the prologue reads set 1 (zeros)
@@ -357,7 +366,7 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
       const int ep = col_start(p, R);
       const bool two = p + 1 < R;
       const int ep1 = two ? col_start(p + 1, R) : 0;
-      for (int i = p + tid; i < R; i += nt) {
+      for (int i = p + tid; tid < na && i < R; i += na) {
         const float4 cp = cc[p];
         const dfl a2 = lo2(cp), b2 = hi2(cp);
         const dfl piv2 = df_fms2(upk(G[ep]), a2, a2, b2, b2);
@@ -393,10 +402,20 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
         nu[i] = pk2(u, v);
       }
     }
-    if (k >= 0) {
+    if (k >= 0 && ut >= 0) {
       // (b) trailing update of the columns >= k+4 with the pivots k, k+1
       if (k + 4 < R) {
-        for (int e = col_start(k + 4, R) + tid; e < T; e += nt) {
+        // two entries per iteration: independent double-float chains
+        int e = col_start(k + 4, R) + ut;
+        for (; e + nu_t < T; e += 2 * nu_t) {
+          const uint32_t ij0 = crd[e], ij1 = crd[e + nu_t];
+          const float4 li0 = cc[ij0 & 0xffffu], lj0 = cc[ij0 >> 16];
+          const float4 li1 = cc[ij1 & 0xffffu], lj1 = cc[ij1 >> 16];
+          const dfl g0 = upk(G[e]), g1 = upk(G[e + nu_t]);
+          G[e] = pk(df_fms2(g0, lo2(li0), lo2(lj0), hi2(li0), hi2(lj0)));
+          G[e + nu_t] = pk(df_fms2(g1, lo2(li1), lo2(lj1), hi2(li1), hi2(lj1)));
+        }
+        if (e < T) {
           const uint32_t ij = crd[e];
           const float4 li = cc[ij & 0xffffu], lj = cc[ij >> 16];
           G[e] = pk(df_fms2(upk(G[e]), lo2(li), lo2(lj), hi2(li), hi2(lj)));
@@ -405,25 +424,45 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
       // (c) inverse update of rows >= k+2, columns <= k+1
       {
         const int cols = k + 2, tot = (R - k - 2) * cols;
-        if (tid < tot) {
+        if (ut < tot) {
           const float rc = 1.f / (float)cols;
-          int q = (int)(((float)tid + 0.5f) * rc), c = tid - q * cols;
-          const int dq = (int)(((float)nt + 0.5f) * rc), dc = nt - dq * cols;
+          int q = (int)(((float)ut + 0.5f) * rc), c = ut - q * cols;
+          const int dq = (int)(((float)nu_t + 0.5f) * rc), dc = nu_t - dq * cols;
           const float2* Bk = B + k * (k + 1) / 2;
           const float2* Bk1 = B + (k + 1) * (k + 2) / 2;
-          for (int t = tid; t < tot; t += nt) {
+          // two entries per iteration (t and t + nt): independent chains
+          int t = ut;
+          for (; t + nu_t < tot; t += 2 * nu_t) {
+            int q1 = q + dq, c1 = c + dc;
+            if (c1 >= cols) {
+              c1 -= cols;
+              q1++;
+            }
+            const int i0 = k + 2 + q, i1 = k + 2 + q1;
+            float2* bp0 = B + i0 * (i0 + 1) / 2 + c;
+            float2* bp1 = B + i1 * (i1 + 1) / 2 + c1;
+            const float4 w0 = cu[i0], w1 = cu[i1];
+            const dfl bk0 = c <= k ? upk(Bk[c]) : dfl{0.f, 0.f};
+            const dfl bq0 = c <= k ? upk(Bk1[c]) : dfl{1.f, 0.f};
+            const dfl bk1 = c1 <= k ? upk(Bk[c1]) : dfl{0.f, 0.f};
+            const dfl bq1 = c1 <= k ? upk(Bk1[c1]) : dfl{1.f, 0.f};
+            const dfl x0 = upk(*bp0), x1 = upk(*bp1);
+            *bp0 = pk(df_fms2(x0, lo2(w0), bk0, hi2(w0), bq0));
+            *bp1 = pk(df_fms2(x1, lo2(w1), bk1, hi2(w1), bq1));
+            q = q1 + dq;
+            c = c1 + dc;
+            if (c >= cols) {
+              c -= cols;
+              q++;
+            }
+          }
+          if (t < tot) {
             const int i = k + 2 + q;
             float2* bp = B + i * (i + 1) / 2 + c;
             const float4 w = cu[i];
             const dfl bk = c <= k ? upk(Bk[c]) : dfl{0.f, 0.f};
             const dfl bk1 = c <= k ? upk(Bk1[c]) : dfl{1.f, 0.f};
             *bp = pk(df_fms2(upk(*bp), lo2(w), bk, hi2(w), bk1));
-            q += dq;
-            c += dc;
-            if (c >= cols) {
-              c -= cols;
-              q++;
-            }
           }
         }
       }
@@ -479,14 +518,19 @@ __device__ __forceinline__ void dot2_acc(dfl& s, dfl a, dfl b) {
 // second-order PP terms), solved as a = W^T (W b) with W = L^-1 from the
 // factorisation kernel: two triangular products instead of two substitution
 // chains, so every output entry is an independent compensated dot product.
-// One CTA takes kRB rows at a time; thread r computes entry r of y and then
-// of a (W's zero upper triangle makes the loops warp-uniform).  Writes the
-// float64 master A, the double-float copy (Ahi = the float compute copy,
-// Alo), dA = A_new - ref (ref = A_p, or A_old when Arefhi is null) as
-// float64 and float, and per-row ||dA||^2, ||A_new||^2 (double-float).
+// One CTA takes kRB rows at a time.  Two thread groups of Rp = R rounded up
+// to 32 threads share the work: thread (h, r) sums half h of the terms of
+// entry r (columns below / from the split point m), the halves are added in
+// shared memory; W's zero triangle makes the loop bounds warp-uniform.
+// Group 0 writes the float64 master A, the double-float copy (Ahi = the float
+// compute copy, Alo), dA = A_new - ref (ref = A_p, or A_old when Arefhi is
+// null) as float64 and float, and per-row ||dA||^2, ||A_new||^2
+// (double-float).
 constexpr int kRB = 4;
 
-__global__ void __launch_bounds__(128)
+__device__ __forceinline__ dfl dot2_val(dfl acc) { return fast_two_sum(acc.hi, acc.lo); }
+
+__global__ void __launch_bounds__(256)
 solve_inv_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float* __restrict__ Ahi,
                     float* __restrict__ Alo, const float* __restrict__ Arefhi,
                     const float* __restrict__ Areflo, double* __restrict__ dA,
@@ -500,13 +544,16 @@ solve_inv_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float
   const uint32_t zbytes = Zg ? (uint32_t)(((size_t)R * R * sizeof(float) + 15) / 16 * 16) : 0u;
   float* Zs = reinterpret_cast<float*>(reinterpret_cast<char*>(smem) + wbytes);
   __shared__ __align__(8) uint64_t bar;
-  __shared__ float2 bs[kRB][kMaxRank], ys[kRB][kMaxRank];
+  __shared__ float2 bs[kRB][kMaxRank], ys[kRB][kMaxRank], hp[kRB][kMaxRank];
   __shared__ float as[kRB][kMaxRank];
   __shared__ float2 red[kRB][2][kMaxRank / 32];
   const bool failed = (status[0] >> n) & 1;
-  const int r = threadIdx.x, lane = r & 31, warp = r >> 5, nwarp = blockDim.x >> 5;
+  const int Rp = (R + 31) / 32 * 32;
+  const int h = threadIdx.x >= Rp;              // half of the terms
+  const int r = threadIdx.x - h * Rp, lane = r & 31, warp = r >> 5, nwarp = Rp >> 5;
   const bool act = r < R;
   const int rr = act ? r : R - 1;               // padding threads read a valid row, store nothing
+  const int m = (R + 1) / 2;                    // split point of the terms
   bool loaded = true;
   if (!failed) {
     const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
@@ -540,8 +587,11 @@ solve_inv_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float
     if (threadIdx.x == 0) atomicOr(const_cast<int*>(status) + 2, 1);
     return;
   }
-  const int cend1 = min(R, 32 * warp + 32);     // W row r is zero beyond column r
-  const int cbeg2 = 32 * warp;                  // W column r is zero above row r
+  // y_r = sum_{c <= r} W_rc b_c: half 0 takes c < m, half 1 c >= m
+  const int wend = min(R, 32 * warp + 32);      // W row r is zero beyond column r
+  const int c1a = h ? m : 0, c1b = h ? wend : min(m, wend);
+  // a_r = sum_{c >= r} W_cr y_c: half 0 takes c < m, half 1 c >= m
+  const int c2a = h ? max(m, 32 * warp) : 32 * warp, c2b = h ? R : m;
   for (int y0 = blockIdx.x * kRB; y0 < s; y0 += gridDim.x * kRB) {
     float oh[kRB], ol[kRB];
     dfl a[kRB];
@@ -552,7 +602,7 @@ solve_inv_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float
       oh[w] = Ahi[o];
       ol[w] = Alo[o];
       a[w] = {rhs[o], 0.f};
-      as[w][rr] = oh[w];
+      if (!h) as[w][rr] = oh[w];
     }
     if (failed) {
 #pragma unroll
@@ -572,73 +622,84 @@ solve_inv_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float
 #pragma unroll
         for (int w = 0; w < kRB; w++) a[w] = df_add(a[w], dfl{vz[w], 0.f});
       }
+      if (!h)
 #pragma unroll
-      for (int w = 0; w < kRB; w++) bs[w][rr] = pk(a[w]);
+        for (int w = 0; w < kRB; w++) bs[w][rr] = pk(a[w]);
       __syncthreads();
-      // y = W b
       dfl acc[kRB];
 #pragma unroll
       for (int w = 0; w < kRB; w++) acc[w] = {0.f, 0.f};
       const float2* wr = Ws + rr * RS;
 #pragma unroll 2
-      for (int c = 0; c < cend1; c++) {
+      for (int c = c1a; c < c1b; c++) {
         const dfl wv = upk(wr[c]);
 #pragma unroll
         for (int w = 0; w < kRB; w++) dot2_acc(acc[w], wv, upk(bs[w][c]));
       }
+      if (h)
 #pragma unroll
-      for (int w = 0; w < kRB; w++) ys[w][rr] = pk(fast_two_sum(acc[w].hi, acc[w].lo));
+        for (int w = 0; w < kRB; w++) hp[w][rr] = pk(dot2_val(acc[w]));
       __syncthreads();
-      // a = W^T y
+      if (!h)
+#pragma unroll
+        for (int w = 0; w < kRB; w++) ys[w][rr] = pk(df_add(dot2_val(acc[w]), upk(hp[w][rr])));
+      __syncthreads();
 #pragma unroll
       for (int w = 0; w < kRB; w++) acc[w] = {0.f, 0.f};
 #pragma unroll 2
-      for (int c = cbeg2; c < R; c++) {
+      for (int c = c2a; c < c2b; c++) {
         const dfl wv = upk(Ws[c * RS + rr]);
 #pragma unroll
         for (int w = 0; w < kRB; w++) dot2_acc(acc[w], wv, upk(ys[w][c]));
       }
+      if (h)
 #pragma unroll
-      for (int w = 0; w < kRB; w++) a[w] = fast_two_sum(acc[w].hi, acc[w].lo);
+        for (int w = 0; w < kRB; w++) hp[w][rr] = pk(dot2_val(acc[w]));
+      __syncthreads();
+#pragma unroll
+      for (int w = 0; w < kRB; w++) a[w] = df_add(dot2_val(acc[w]), upk(hp[w][rr]));
     }
-    // outputs and per-row norms
+    // outputs and per-row norms (group 0)
+    if (!h) {
 #pragma unroll
-    for (int w = 0; w < kRB; w++) {
-      const int y = y0 + w;
-      dfl nd = {0.f, 0.f}, na = {0.f, 0.f};
-      if (act && y < s) {
-        const int64_t o = (int64_t)y * R + r;
-        const dfl ref = Arefhi ? dfl{Arefhi[o], Areflo[o]} : dfl{oh[w], ol[w]};
-        const dfl d = df_sub(a[w], ref);
-        A[o] = df_dbl(a[w]);
-        Ahi[o] = a[w].hi;
-        Alo[o] = a[w].lo;
-        dA[o] = df_dbl(d);
-        dAc[o] = d.hi;
-        nd = df_mul(d, d);
-        na = df_mul(a[w], a[w]);
-      }
+      for (int w = 0; w < kRB; w++) {
+        const int y = y0 + w;
+        dfl nd = {0.f, 0.f}, na = {0.f, 0.f};
+        if (act && y < s) {
+          const int64_t o = (int64_t)y * R + r;
+          const dfl ref = Arefhi ? dfl{Arefhi[o], Areflo[o]} : dfl{oh[w], ol[w]};
+          const dfl d = df_sub(a[w], ref);
+          A[o] = df_dbl(a[w]);
+          Ahi[o] = a[w].hi;
+          Alo[o] = a[w].lo;
+          dA[o] = df_dbl(d);
+          dAc[o] = d.hi;
+          nd = df_mul(d, d);
+          na = df_mul(a[w], a[w]);
+        }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        nd = df_add(nd, dfl{__shfl_xor_sync(0xffffffffu, nd.hi, off), __shfl_xor_sync(0xffffffffu, nd.lo, off)});
-        na = df_add(na, dfl{__shfl_xor_sync(0xffffffffu, na.hi, off), __shfl_xor_sync(0xffffffffu, na.lo, off)});
-      }
-      if (lane == 0) {
-        red[w][0][warp] = pk(nd);
-        red[w][1][warp] = pk(na);
+        for (int off = 16; off > 0; off >>= 1) {
+          nd = df_add(nd, dfl{__shfl_xor_sync(0xffffffffu, nd.hi, off), __shfl_xor_sync(0xffffffffu, nd.lo, off)});
+          na = df_add(na, dfl{__shfl_xor_sync(0xffffffffu, na.hi, off), __shfl_xor_sync(0xffffffffu, na.lo, off)});
+        }
+        if (lane == 0) {
+          red[w][0][warp] = pk(nd);
+          red[w][1][warp] = pk(na);
+        }
       }
     }
     __syncthreads();
-    if (r < kRB && y0 + r < s) {
-      dfl nd = upk(red[r][0][0]), na = upk(red[r][1][0]);
+    if (threadIdx.x < kRB && y0 + (int)threadIdx.x < s) {
+      const int w = threadIdx.x;
+      dfl nd = upk(red[w][0][0]), na = upk(red[w][1][0]);
       for (int q = 1; q < nwarp; q++) {
-        nd = df_add(nd, upk(red[r][0][q]));
-        na = df_add(na, upk(red[r][1][q]));
+        nd = df_add(nd, upk(red[w][0][q]));
+        na = df_add(na, upk(red[w][1][q]));
       }
-      rownorm[2 * (y0 + r)] = pk(nd);
-      rownorm[2 * (y0 + r) + 1] = pk(na);
+      rownorm[2 * (y0 + w)] = pk(nd);
+      rownorm[2 * (y0 + w) + 1] = pk(na);
     }
-    __syncthreads();                            // bs/ys/as/red are reused by the next rows
+    __syncthreads();                            // bs/ys/hp/as/red are reused by the next rows
   }
 }
 
@@ -664,23 +725,34 @@ void split_df(const double* A, float* hi, float* lo, int64_t n, Launch L) {
 
 void gram_df(const float* Ahi, const float* Alo, const float* Aw, const float* dAw, double* S,
              float* Shi, float* Slo, float* W, bool withW, int s, int R, const float2* rownorm,
-             double* scal, float2* partials, int* tickets, Launch L) {
+             double* scal, Launch L) {
   const int nb = (R + 31) / 32;
   const int ntS = nb * (nb + 1) / 2;
   const int ntiles = withW ? ntS + nb * nb : ntS;
-  const int chunk = 32;
-  const int splits = (int)cdiv(s, chunk);
-  gram_df_kernel<<<ntiles * splits, 256, 0, L.stream>>>(Ahi, Alo, Aw, dAw, s, R, nb, ntS, ntiles,
-                                                        splits, chunk, partials, tickets, S, Shi,
-                                                        Slo, W, rownorm, scal);
+  // up to 8 CTAs per tile (a portable cluster), at least 16 rows each
+  const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(8, cdiv(s, 16)));
+  const int chunk = (int)cdiv(s, splits);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ntiles * splits);
+  cfg.blockDim = dim3(256);
+  cfg.stream = L.stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = splits;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, gram_df_kernel, Ahi, Alo, Aw, dAw, s, R, nb, ntS, splits, chunk, S, Shi,
+                     Slo, W, rownorm, scal);
   (*L.counter)++;
 }
 
 void chol_df(const float* Shi, const float* Slo, const float* W, int N, int n, int R,
              float2* Winv, float* Z, bool useV, int* status, Launch L) {
-  // about eight packed entries per thread at the first step, 128..CPALS_CHOL_THREADS threads
+  // 128 column threads plus about one update thread per eight packed entries
   const int T = R * (R + 1) / 2;
-  const int threads = std::min(CPALS_CHOL_THREADS, std::max(128, (T / 8 + 31) / 32 * 32));
+  const int threads = std::min(CPALS_CHOL_THREADS, 128 + (T / 8 + 31) / 32 * 32);
   chol_inv_df_kernel<<<1, threads, chol_inv_smem(R), L.stream>>>(Shi, Slo, W, N, n, R, Winv, Z,
                                                                  useV ? 1 : 0, status);
   (*L.counter)++;
@@ -691,7 +763,7 @@ void solve_df(const float* rhs, double* A, float* Ahi, float* Alo, const float* 
               float2* rownorm, int s, int R, int n, const int* status, Launch L) {
   const size_t wb = ((size_t)R * (R | 1) * sizeof(float2) + 15) / 16 * 16;
   const size_t zb = Z ? ((size_t)R * R * sizeof(float) + 15) / 16 * 16 : 0;
-  const int threads = (R + 31) / 32 * 32;
+  const int threads = 2 * ((R + 31) / 32 * 32);
   const int blocks = (int)std::min<int64_t>(cdiv(s, kRB), 152 * 2);
   solve_inv_df_kernel<<<blocks, threads, wb + zb, L.stream>>>(rhs, A, Ahi, Alo, Arefhi, Areflo, dA,
                                                               dAc, Winv, Z, rownorm, s, R, n,

@@ -116,7 +116,7 @@ cudaError_t setup_df_kernels();
 void split_df(const double* A, float* hi, float* lo, int64_t n, Launch L);
 void gram_df(const float* Ahi, const float* Alo, const float* Aw, const float* dAw, double* S,
              float* Shi, float* Slo, float* W, bool withW, int s, int R, const float2* rownorm,
-             double* scal, float2* partials, int* tickets, Launch L);
+             double* scal, Launch L);
 // chol_df: Gamma^(n) = L L^T and Winv = L^-1 (row stride R|1, zero upper
 // triangle); solve_df: a = Winv^T Winv b per row.
 void chol_df(const float* Shi, const float* Slo, const float* W, int N, int n, int R, float2* Winv,
