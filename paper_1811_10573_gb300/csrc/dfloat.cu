@@ -234,36 +234,37 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
 }
 
 // ---------------------------------------------------------------- Gamma, Cholesky, inverse
-// One CTA forms Gamma^(n) = Hadamard product of the Grams S^(k), k != n, in
-// double-float, factors it Gamma = L L^T and inverts the factor, W = L^-1, in
-// one right-looking loop that retires two pivots per barrier.  Shared memory:
-//   G   the lower triangle of Gamma, packed by columns: entry (i, j), i >= j,
-//       at cs(j) + i - j with cs(j) = j R - j (j - 1) / 2, so the trailing
-//       triangle right of a column is a contiguous suffix that all threads
-//       share evenly;
-//   crd the (row, column) of every packed index;
-//   B   the lower triangle of the inverse in progress, packed by rows
-//       (entry (i, c) at i (i + 1) / 2 + c), initially the identity;
-//   per row, double-buffered: the current pair of columns (L_ik, L_i,k+1)
-//   and the pair of inverse-update coefficients (u_i, v_i) below; 1 / L_jj;
-//   L_{j,j-1} / L_{j-1,j-1} for odd j.
-// Step k (pivots k and k+1 done; Golub & Van Loan Alg. 4.2.2 for the factor,
-// the column-oriented triangular inverse for W):
+// A cluster of two CTAs forms Gamma^(n) = Hadamard product of the Grams
+// S^(k), k != n, in double-float, factors it Gamma = L L^T (CTA 0) and
+// inverts the factor, W = L^-1 (CTA 1), two pivots per step (right-looking;
+// Golub & Van Loan Alg. 4.2.2 for the factor, the column-oriented triangular
+// inverse for W).
+// CTA 0 holds the lower triangle of Gamma packed by columns (entry (i, j),
+// i >= j, at cs(j) + i - j with cs(j) = j R - j (j - 1) / 2, so the trailing
+// triangle right of a column is a contiguous suffix that all threads share
+// evenly), the (row, column) of every packed index and the current pair of
+// columns of L.  Its step k:
 //   (a) columns k+2 and k+3 of L from the unupdated G columns and columns k,
 //       k+1 (each thread recomputes the two pivots and L_{k+3,k+2}), and the
-//       coefficients of those two columns for the inverse;
-//   (b) G_ij -= L_ik L_jk + L_i,k+1 L_j,k+1 for the columns j >= k+4;
-//   (c) B_ic -= u_i B_kc + v_i B_k+1,c for rows i >= k+2, c <= k+1, where
-//       v_i = L_i,k+1 / L_k+1,k+1 and u_i = L_ik / L_kk - v_i L_k+1,k / L_kk:
+//       inverse-update coefficients of those two columns,
+//         v_i = L_i,k+3 / L_k+3,k+3,
+//         u_i = L_i,k+2 / L_k+2,k+2 - v_i L_k+3,k+2 / L_k+2,k+2,
+//       with 1 / L_jj and L_{k+3,k+2} / L_{k+2,k+2}, stored straight into
+//       CTA 1's shared memory, then a release flag for that pair;
+//   (b) G_ij -= L_ik L_jk + L_i,k+1 L_j,k+1 for the columns j >= k+4.
+// CTA 1 holds the lower triangle of the inverse in progress packed by rows
+// (entry (i, c) at i (i + 1) / 2 + c), initially the identity, and for each
+// pair k waits (bounded) for its flag and applies
+//   (c) B_ic -= u_i B_kc + v_i B_k+1,c for rows i >= k+2, c <= k+1:
 //       pivot k and pivot k+1 (which sees row k+1 after pivot k) in one pass.
-//       Row k+1 itself gets pivot k at the end.
-// Row j of W is then the final row j of B divided by L_jj.  The work of (b)
-// falls and that of (c) rises with k, which keeps the steps evenly loaded.
-// Every update is one fused double-float g - a b - c d (exact leading
+// Row k+1 gets pivot k at the end, and row j of W is the final row j of B
+// divided by L_jj.  CTA 0 never waits on CTA 1, so the two run at their own
+// pace.  Every update is one fused double-float g - a b - c d (exact leading
 // products and sums, one renormalisation: backward error a few units of
 // 2^-48 relative to the operands).  Writes W (row stride RS = R | 1, zeros
 // above the diagonal and in the padding column) and, with useV, the float
-// matrix Z of the second-order PP terms (Eq. 3).
+// matrix Z of the second-order PP terms (Eq. 3).  A non-positive pivot sets
+// bit n of status[0]; a wait that runs out sets status[2].
 #ifndef CPALS_CHOL_THREADS
 #define CPALS_CHOL_THREADS 640
 #endif
@@ -291,120 +292,195 @@ __device__ __forceinline__ dfl lo2(float4 v) { return {v.x, v.y}; }
 __device__ __forceinline__ dfl hi2(float4 v) { return {v.z, v.w}; }
 __device__ __forceinline__ float4 pk2(dfl a, dfl b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
 
-__global__ void __launch_bounds__(1024, 1)
+// Shared-memory layout of the two CTAs (byte offsets from the dynamic base).
+struct CholLayout {
+  size_t tb, crd, lc, end0;          // CTA 0: G, crd, column pairs
+  size_t uv, id, lsub, bars, flag, end1;   // CTA 1: B (at 0), coefficients, 1/L_jj,
+                                           // L_j,j-1/L_j-1,j-1, one mbarrier per pair, stop flag
+  __host__ __device__ CholLayout(int R) {
+    const size_t T = (size_t)R * (R + 1) / 2;
+    tb = (T * 8 + 15) / 16 * 16;
+    crd = tb;
+    lc = crd + (T * 4 + 15) / 16 * 16;
+    end0 = lc + 2 * (size_t)R * 16;
+    uv = tb;
+    id = uv + (size_t)(R / 2 + 1) * R * 16;
+    lsub = id + (size_t)R * 8;
+    bars = lsub + (size_t)R * 8;
+    flag = bars + (size_t)(R / 2 + 1) * 8;
+    end1 = flag + 16;
+  }
+  __host__ __device__ size_t bytes() const { return end0 > end1 ? end0 : end1; }
+};
+
+// Remote shared-memory stores that complete a transaction count on an
+// mbarrier of the receiving CTA (no fence on the sending side).
+__device__ __forceinline__ uint32_t cluster_addr(const void* local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_async16(uint32_t dst, float4 v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+               ::"r"(dst), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void st_async8(uint32_t dst, float2 v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
+               ::"r"(dst), "f"(v.x), "f"(v.y), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void st_release_cluster(int* p, int v) {
+  asm volatile("st.release.cluster.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_cluster(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cluster.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CPALS_CHOL_THREADS, 1)
 chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
                    const float* __restrict__ Wg, int N, int n, int R, float2* __restrict__ Wout,
                    float* __restrict__ Z, int useV, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char csm[];
   __shared__ int bad;
+  cg::cluster_group cl = cg::this_cluster();
+  const int role = (int)cl.block_rank();
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
   const int RR = R * R;
   const int RS = R | 1;
   const int T = R * (R + 1) / 2;
-  const size_t tb = ((size_t)T * sizeof(float2) + 15) / 16 * 16;
-  float2* G = reinterpret_cast<float2*>(csm);
-  float2* B = reinterpret_cast<float2*>(csm + tb);
-  float4* lc = reinterpret_cast<float4*>(csm + 2 * tb);   // [set][row] (L_ik, L_i,k+1)
-  float4* uv = lc + 2 * R;                                 // [set][row] (u_i, v_i)
-  float2* id = reinterpret_cast<float2*>(uv + 2 * R);
-  float2* lsub = id + R;
-  uint32_t* crd = reinterpret_cast<uint32_t*>(lsub + R);
-  if (useV) {
-    for (int idx = tid; idx < RR; idx += nt) {
-      float zz = 0.f;
-      for (int a = 0; a < N; a++) {
-        if (a == n) continue;
-        for (int b = a + 1; b < N; b++) {
-          if (b == n) continue;
-          float h = Wg[(int64_t)a * RR + idx] * Wg[(int64_t)b * RR + idx];
-          for (int k = 0; k < N; k++)
-            if (k != a && k != b && k != n) h *= Shi[(int64_t)k * RR + idx];
-          zz += h;
-        }
+  const CholLayout lay(R);
+  // CTA 1's arrays (CTA 0 writes them through the cluster window)
+  float4* UV = reinterpret_cast<float4*>(csm + lay.uv);
+  float2* id = reinterpret_cast<float2*>(csm + lay.id);
+  float2* lsub = reinterpret_cast<float2*>(csm + lay.lsub);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(csm + lay.bars);   // one per pair of columns
+  int* flag = reinterpret_cast<int*>(csm + lay.flag);             // [0] stop
+  const int npair = (R + 1) / 2;
+  if (role == 1) {
+    float2* B = reinterpret_cast<float2*>(csm);
+    if (tid == 0) {
+      flag[0] = 0;
+      // pair P brings 16 bytes per row i >= 2P, 1/L_jj of its columns and,
+      // when it has two, L_{2P+1,2P} / L_{2P,2P}
+      for (int P = 0; P < npair; P++) {
+        const uint32_t b = (uint32_t)__cvta_generic_to_shared(bars + P);
+        const uint32_t bytes = 16u * (uint32_t)(R - 2 * P) + (2 * P + 1 < R ? 24u : 8u);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
+                     : "memory");
       }
-      Z[idx] = zz;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    for (int i = warp; i < R; i += nwarp)
+      for (int j = lane; j <= i; j += 32) B[i * (i + 1) / 2 + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
   }
-  if (tid == 0) bad = 0;
-  for (int j = warp; j < R; j += nwarp) {
-    const int e0 = col_start(j, R);
-    for (int i = j + lane; i < R; i += 32) {
-      const int idx = i * R + j;
-      dfl sk[kMaxModes];                        // all loads first, then the products
+  cl.sync();                                   // CTA 1's barriers exist before CTA 0 writes
+  if (role == 0) {
+    float2* G = reinterpret_cast<float2*>(csm);
+    uint32_t* crd = reinterpret_cast<uint32_t*>(csm + lay.crd);
+    float4* lc = reinterpret_cast<float4*>(csm + lay.lc);  // [set][row] (L_ik, L_i,k+1)
+    const uint32_t UVr = cluster_addr(UV, 1), idr = cluster_addr(id, 1);
+    const uint32_t lsubr = cluster_addr(lsub, 1), barr = cluster_addr(bars, 1);
+    int* flagr = cl.map_shared_rank(flag, 1);
+    if (tid == 0) bad = 0;
+    // Gamma: entries in packed order, eight per thread in flight; each
+    // mode's loads are issued together before its products
+    for (int base = 0; base < T; base += 8 * nt) {
+      int gi[8];
+      dfl acc[8];
 #pragma unroll
-      for (int k = 0; k < kMaxModes; k++)
-        sk[k] = (k < N && k != n) ? dfl{Shi[(int64_t)k * RR + idx], Slo[(int64_t)k * RR + idx]}
-                                  : dfl{1.f, 0.f};
-      dfl v = sk[0];
-#pragma unroll
-      for (int k = 1; k < kMaxModes; k++)
-        if (k < N) v = df_mul(v, sk[k]);
-      G[e0 + i - j] = pk(v);
-      crd[e0 + i - j] = (uint32_t)i | ((uint32_t)j << 16);
-      B[i * (i + 1) / 2 + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
-    }
-  }
-  for (int i = tid; i < R; i += nt) lc[R + i] = make_float4(0.f, 0.f, 0.f, 0.f);  // no columns before 0
-  __syncthreads();
-  // The first 128 threads compute the next column pair (a); the others do
-  // the updates (b) and (c), so the long dependent chain of (a) is not
-  // followed by an update share on the same warps.  Small CTAs do both.
-  const int na = nt > 128 ? 128 : nt;
-  const int ub = nt > 128 ? 128 : 0;
-  const int ut = tid - ub, nu_t = nt - ub;
-  // k = -2 is the prologue (columns 0 and 1 from zero columns); then pairs
-  for (int k = -2; k + 2 < R; k += 2) {
-    const int cur = (((k + 2) >> 1) & 1) ^ 1, nxt = cur ^ 1;   // the prologue reads set 1 (zeros)
-    const float4* cc = lc + cur * R;
-    const float4* cu = uv + cur * R;
-    float4* nc = lc + nxt * R;
-    float4* nu = uv + nxt * R;
-    // (a) columns p = k+2 and p+1 of L and their inverse-update coefficients
-    {
-      const int p = k + 2;
-      const int ep = col_start(p, R);
-      const bool two = p + 1 < R;
-      const int ep1 = two ? col_start(p + 1, R) : 0;
-      for (int i = p + tid; tid < na && i < R; i += na) {
-        const float4 cp = cc[p];
-        const dfl a2 = lo2(cp), b2 = hi2(cp);
-        const dfl piv2 = df_fms2(upk(G[ep]), a2, a2, b2, b2);
-        if (bad_pivot(piv2)) {
-          bad = 1;
-          break;
+      for (int q = 0; q < 8; q++) {
+        const int e = base + q * nt + tid;
+        int j = 0, i = 0;
+        if (e < T) {
+          const float b2 = (float)(2 * R + 1);
+          j = (int)((b2 - sqrtf(b2 * b2 - 8.f * (float)e)) * 0.5f);
+          j = max(0, min(R - 1, j));
+          while (j + 1 < R && col_start(j + 1, R) <= e) j++;
+          while (col_start(j, R) > e) j--;
+          i = j + e - col_start(j, R);
+          crd[e] = (uint32_t)i | ((uint32_t)j << 16);
         }
-        const dfl il2 = df_rsqrt(piv2);
-        const float4 ci = cc[i];
-        const dfl l2 = df_mul(df_fms2(upk(G[ep + i - p]), lo2(ci), a2, hi2(ci), b2), il2);
-        const dfl q2 = df_mul(l2, il2);
-        dfl l3 = {0.f, 0.f}, u = q2, v = {0.f, 0.f};
-        if (i == p) id[p] = pk(il2);
-        if (two && i > p) {
-          const float4 cp1 = cc[p + 1];
-          const dfl a3 = lo2(cp1), b3 = hi2(cp1);
-          const dfl c3 = df_mul(df_fms2(upk(G[ep + 1]), a3, a2, b3, b2), il2);
-          const dfl piv3 = df_fms(df_fms2(upk(G[ep1]), a3, a3, b3, b3), c3, c3);
-          if (bad_pivot(piv3)) {
+        gi[q] = e < T ? i * R + j : -1;
+        acc[q] = {1.f, 0.f};
+      }
+      for (int k = 0; k < N; k++) {
+        if (k == n) continue;
+        float h[8], l[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          h[q] = gi[q] >= 0 ? Shi[(int64_t)k * RR + gi[q]] : 1.f;
+          l[q] = gi[q] >= 0 ? Slo[(int64_t)k * RR + gi[q]] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) acc[q] = df_mul(acc[q], dfl{h[q], l[q]});
+      }
+#pragma unroll
+      for (int q = 0; q < 8; q++)
+        if (gi[q] >= 0) G[base + q * nt + tid] = pk(acc[q]);
+    }
+    for (int i = tid; i < R; i += nt) lc[R + i] = make_float4(0.f, 0.f, 0.f, 0.f);  // no columns before 0
+    __syncthreads();
+    // The first 128 threads compute the next column pair (a); the others
+    // update (b).  Small CTAs do both.
+    const bool split = nt > 128;
+    const int na = split ? 128 : nt;
+    const int ut = tid - (split ? 128 : 0), nu_t = nt - (split ? 128 : 0);
+    // k = -2 is the prologue (columns 0 and 1 from zero columns); then pairs
+    for (int k = -2; k + 2 < R; k += 2) {
+      const int cur = (((k + 2) >> 1) & 1) ^ 1, nxt = cur ^ 1;   // the prologue reads set 1 (zeros)
+      const float4* cc = lc + cur * R;
+      float4* nc = lc + nxt * R;
+      const int p = k + 2;
+      if (tid < na) {
+        // (a) columns p and p+1 of L and their inverse-update coefficients,
+        // sent to CTA 1 as they are made
+        const int ep = col_start(p, R);
+        const bool two = p + 1 < R;
+        const int ep1 = two ? col_start(p + 1, R) : 0;
+        const uint32_t bar = barr + 8u * (uint32_t)(p >> 1);
+        const uint32_t uvp = UVr + 16u * (uint32_t)((p >> 1) * R);
+        for (int i = p + tid; i < R; i += na) {
+          const float4 cp = cc[p];
+          const dfl a2 = lo2(cp), b2 = hi2(cp);
+          const dfl piv2 = df_fms2(upk(G[ep]), a2, a2, b2, b2);
+          if (bad_pivot(piv2)) {
             bad = 1;
             break;
           }
-          const dfl il3 = df_rsqrt(piv3);
-          l3 = df_mul(df_fms(df_fms2(upk(G[ep1 + i - p - 1]), lo2(ci), a3, hi2(ci), b3), l2, c3), il3);
-          v = df_mul(l3, il3);
-          u = df_fms(q2, v, df_mul(c3, il2));
-          if (i == p + 1) {
-            id[p + 1] = pk(il3);
-            lsub[p + 1] = pk(q2);
+          const dfl il2 = df_rsqrt(piv2);
+          const float4 ci = cc[i];
+          const dfl l2 = df_mul(df_fms2(upk(G[ep + i - p]), lo2(ci), a2, hi2(ci), b2), il2);
+          const dfl q2 = df_mul(l2, il2);
+          dfl l3 = {0.f, 0.f}, u = q2, v = {0.f, 0.f};
+          if (i == p) st_async8(idr + 8u * p, pk(il2), bar);
+          if (two && i > p) {
+            const float4 cp1 = cc[p + 1];
+            const dfl a3 = lo2(cp1), b3 = hi2(cp1);
+            const dfl c3 = df_mul(df_fms2(upk(G[ep + 1]), a3, a2, b3, b2), il2);
+            const dfl piv3 = df_fms(df_fms2(upk(G[ep1]), a3, a3, b3, b3), c3, c3);
+            if (bad_pivot(piv3)) {
+              bad = 1;
+              break;
+            }
+            const dfl il3 = df_rsqrt(piv3);
+            l3 = df_mul(df_fms(df_fms2(upk(G[ep1 + i - p - 1]), lo2(ci), a3, hi2(ci), b3), l2, c3), il3);
+            v = df_mul(l3, il3);
+            u = df_fms(q2, v, df_mul(c3, il2));
+            if (i == p + 1) {
+              st_async8(idr + 8u * (p + 1), pk(il3), bar);
+              st_async8(lsubr + 8u * (p + 1), pk(q2), bar);
+            }
           }
+          nc[i] = pk2(l2, l3);
+          st_async16(uvp + 16u * i, pk2(u, v), bar);
         }
-        nc[i] = pk2(l2, l3);
-        nu[i] = pk2(u, v);
       }
-    }
-    if (k >= 0 && ut >= 0) {
       // (b) trailing update of the columns >= k+4 with the pivots k, k+1
-      if (k + 4 < R) {
+      if (k >= 0 && k + 4 < R && ut >= 0) {
         // two entries per iteration: independent double-float chains
         int e = col_start(k + 4, R) + ut;
         for (; e + nu_t < T; e += 2 * nu_t) {
@@ -421,84 +497,138 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
           G[e] = pk(df_fms2(upk(G[e]), lo2(li), lo2(lj), hi2(li), hi2(lj)));
         }
       }
+      __syncthreads();
+      if (bad) break;
+    }
+    if (bad && tid == 0) {
+      atomicOr(status, 1 << n);
+      st_release_cluster(flagr, 1);            // CTA 1 stops waiting
+    }
+  } else {
+    float2* B = reinterpret_cast<float2*>(csm);
+    if (useV) {
+      for (int idx = tid; idx < RR; idx += nt) {
+        float zz = 0.f;
+        for (int a = 0; a < N; a++) {
+          if (a == n) continue;
+          for (int b = a + 1; b < N; b++) {
+            if (b == n) continue;
+            float h = Wg[(int64_t)a * RR + idx] * Wg[(int64_t)b * RR + idx];
+            for (int k = 0; k < N; k++)
+              if (k != a && k != b && k != n) h *= Shi[(int64_t)k * RR + idx];
+            zz += h;
+          }
+        }
+        Z[idx] = zz;
+      }
+    }
+    // thread 0 waits (bounded) for pair P or a stop; 0 = ready, 1 = stopped,
+    // 2 = timed out; the caller's barrier publishes the state.  Two slots:
+    // a wait writes the slot the other threads are not reading.
+    __shared__ int state[2];
+    int slot = 0;
+    auto wait_pair = [&](int P, int sl) {
+      if (tid == 0) {
+        int st = 2;
+        const uint32_t b = (uint32_t)__cvta_generic_to_shared(bars + P);
+        const unsigned long long t0 = clock64();
+        while (clock64() - t0 < 4000000000ull) {
+          uint32_t done;
+          asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+                       " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(b) : "memory");
+          if (done) { st = 0; break; }
+          if (ld_acquire_cluster(flag)) { st = 1; break; }
+        }
+        state[sl] = st;
+      }
+    };
+    int st = 0;
+    if (R > 2) wait_pair(0, 0);
+    __syncthreads();
+    for (int k = 0; k + 2 < R; k += 2) {
+      st = state[slot];
+      if (st) break;
       // (c) inverse update of rows >= k+2, columns <= k+1
-      {
-        const int cols = k + 2, tot = (R - k - 2) * cols;
-        if (ut < tot) {
-          const float rc = 1.f / (float)cols;
-          int q = (int)(((float)ut + 0.5f) * rc), c = ut - q * cols;
-          const int dq = (int)(((float)nu_t + 0.5f) * rc), dc = nu_t - dq * cols;
-          const float2* Bk = B + k * (k + 1) / 2;
-          const float2* Bk1 = B + (k + 1) * (k + 2) / 2;
-          // two entries per iteration (t and t + nt): independent chains
-          int t = ut;
-          for (; t + nu_t < tot; t += 2 * nu_t) {
-            int q1 = q + dq, c1 = c + dc;
-            if (c1 >= cols) {
-              c1 -= cols;
-              q1++;
-            }
-            const int i0 = k + 2 + q, i1 = k + 2 + q1;
-            float2* bp0 = B + i0 * (i0 + 1) / 2 + c;
-            float2* bp1 = B + i1 * (i1 + 1) / 2 + c1;
-            const float4 w0 = cu[i0], w1 = cu[i1];
-            const dfl bk0 = c <= k ? upk(Bk[c]) : dfl{0.f, 0.f};
-            const dfl bq0 = c <= k ? upk(Bk1[c]) : dfl{1.f, 0.f};
-            const dfl bk1 = c1 <= k ? upk(Bk[c1]) : dfl{0.f, 0.f};
-            const dfl bq1 = c1 <= k ? upk(Bk1[c1]) : dfl{1.f, 0.f};
-            const dfl x0 = upk(*bp0), x1 = upk(*bp1);
-            *bp0 = pk(df_fms2(x0, lo2(w0), bk0, hi2(w0), bq0));
-            *bp1 = pk(df_fms2(x1, lo2(w1), bk1, hi2(w1), bq1));
-            q = q1 + dq;
-            c = c1 + dc;
-            if (c >= cols) {
-              c -= cols;
-              q++;
-            }
+      const float4* cu = UV + (size_t)(k >> 1) * R;
+      const int cols = k + 2, tot = (R - k - 2) * cols;
+      if (tid < tot) {
+        const float rc = 1.f / (float)cols;
+        int q = (int)(((float)tid + 0.5f) * rc), c = tid - q * cols;
+        const int dq = (int)(((float)nt + 0.5f) * rc), dc = nt - dq * cols;
+        const float2* Bk = B + k * (k + 1) / 2;
+        const float2* Bk1 = B + (k + 1) * (k + 2) / 2;
+        // two entries per iteration (t and t + nt): independent chains
+        int t = tid;
+        for (; t + nt < tot; t += 2 * nt) {
+          int q1 = q + dq, c1 = c + dc;
+          if (c1 >= cols) {
+            c1 -= cols;
+            q1++;
           }
-          if (t < tot) {
-            const int i = k + 2 + q;
-            float2* bp = B + i * (i + 1) / 2 + c;
-            const float4 w = cu[i];
-            const dfl bk = c <= k ? upk(Bk[c]) : dfl{0.f, 0.f};
-            const dfl bk1 = c <= k ? upk(Bk1[c]) : dfl{1.f, 0.f};
-            *bp = pk(df_fms2(upk(*bp), lo2(w), bk, hi2(w), bk1));
+          const int i0 = k + 2 + q, i1 = k + 2 + q1;
+          float2* bp0 = B + i0 * (i0 + 1) / 2 + c;
+          float2* bp1 = B + i1 * (i1 + 1) / 2 + c1;
+          const float4 w0 = cu[i0], w1 = cu[i1];
+          const dfl bk0 = c <= k ? upk(Bk[c]) : dfl{0.f, 0.f};
+          const dfl bq0 = c <= k ? upk(Bk1[c]) : dfl{1.f, 0.f};
+          const dfl bk1 = c1 <= k ? upk(Bk[c1]) : dfl{0.f, 0.f};
+          const dfl bq1 = c1 <= k ? upk(Bk1[c1]) : dfl{1.f, 0.f};
+          const dfl x0 = upk(*bp0), x1 = upk(*bp1);
+          *bp0 = pk(df_fms2(x0, lo2(w0), bk0, hi2(w0), bq0));
+          *bp1 = pk(df_fms2(x1, lo2(w1), bk1, hi2(w1), bq1));
+          q = q1 + dq;
+          c = c1 + dc;
+          if (c >= cols) {
+            c -= cols;
+            q++;
           }
+        }
+        if (t < tot) {
+          const int i = k + 2 + q;
+          float2* bp = B + i * (i + 1) / 2 + c;
+          const float4 w = cu[i];
+          const dfl bk = c <= k ? upk(Bk[c]) : dfl{0.f, 0.f};
+          const dfl bk1 = c <= k ? upk(Bk1[c]) : dfl{1.f, 0.f};
+          *bp = pk(df_fms2(upk(*bp), lo2(w), bk, hi2(w), bk1));
+        }
+      }
+      // the next pair (or, after the last step, the last one for 1 / L_jj)
+      slot ^= 1;
+      wait_pair(k + 4 < R ? (k + 2) >> 1 : npair - 1, slot);
+      __syncthreads();
+    }
+    if (R <= 2) {
+      wait_pair(npair - 1, slot);
+      __syncthreads();
+    }
+    if (!st) st = state[slot];
+    if (st == 2 && tid == 0) atomicOr(status + 2, 2);
+    if (!st) {
+      // W = diag(1 / L_ii) B; odd rows still lack pivot i-1: B_i. -= (L_i,i-1 / L_i-1,i-1) B_i-1.
+      for (int i = warp; i < R; i += nwarp) {
+        const dfl d = upk(id[i]);
+        const bool odd = i & 1;
+        const dfl f = odd ? upk(lsub[i]) : dfl{0.f, 0.f};
+        const float2* Bi = B + i * (i + 1) / 2;
+        const float2* Bp = B + (i - 1) * i / 2;
+        for (int c = lane; c < RS; c += 32) {
+          float2 w = make_float2(0.f, 0.f);
+          if (c < i) {
+            dfl b = upk(Bi[c]);
+            if (odd) b = df_fms(b, f, upk(Bp[c]));
+            w = pk(df_mul(b, d));
+          } else if (c == i) {
+            w = pk(d);
+          }
+          Wout[i * RS + c] = w;
         }
       }
     }
-    __syncthreads();
-    if (bad) {
-      if (tid == 0) atomicOr(status, 1 << n);
-      return;
-    }
   }
-  // W = diag(1 / L_ii) B; odd rows still lack pivot i-1: B_i. -= (L_i,i-1 / L_i-1,i-1) B_i-1.
-  for (int i = warp; i < R; i += nwarp) {
-    const dfl d = upk(id[i]);
-    const bool odd = i & 1;
-    const dfl f = odd ? upk(lsub[i]) : dfl{0.f, 0.f};
-    const float2* Bi = B + i * (i + 1) / 2;
-    const float2* Bp = B + (i - 1) * i / 2;
-    for (int c = lane; c < RS; c += 32) {
-      float2 w = make_float2(0.f, 0.f);
-      if (c < i) {
-        dfl b = upk(Bi[c]);
-        if (odd) b = df_fms(b, f, upk(Bp[c]));
-        w = pk(df_mul(b, d));
-      } else if (c == i) {
-        w = pk(d);
-      }
-      Wout[i * RS + c] = w;
-    }
-  }
+  cl.sync();                                   // CTA 0's last remote stores land before CTA 1 exits
 }
 
-size_t chol_inv_smem(int R) {
-  const size_t T = (size_t)R * (R + 1) / 2;
-  return 2 * ((T * sizeof(float2) + 15) / 16 * 16) + 4 * (size_t)R * sizeof(float4) +
-         2 * (size_t)R * sizeof(float2) + T * 4;
-}
+size_t chol_inv_smem(int R) { return CholLayout(R).bytes(); }
 
 // ---------------------------------------------------------------- row solves
 // Compensated dot-product accumulator (Dot2 of Ogita, Rump and Oishi, with
@@ -753,7 +883,7 @@ void chol_df(const float* Shi, const float* Slo, const float* W, int N, int n, i
   // 128 column threads plus about one update thread per eight packed entries
   const int T = R * (R + 1) / 2;
   const int threads = std::min(CPALS_CHOL_THREADS, 128 + (T / 8 + 31) / 32 * 32);
-  chol_inv_df_kernel<<<1, threads, chol_inv_smem(R), L.stream>>>(Shi, Slo, W, N, n, R, Winv, Z,
+  chol_inv_df_kernel<<<2, threads, chol_inv_smem(R), L.stream>>>(Shi, Slo, W, N, n, R, Winv, Z,
                                                                  useV ? 1 : 0, status);
   (*L.counter)++;
 }
