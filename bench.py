@@ -222,6 +222,21 @@ def run_ours(args):
         als_time = dist.max(dt)
         als_reached = out["reached"]
 
+    # the same PP-ALS with the normal-equation work in IEEE float64 instead of
+    # double-float (FP32/mixed contexts only)
+    ne64 = None
+    if args.precision != "fp64" and not args.no_als:
+        ctx.set_normal_arith("fp64")
+        one(p.eps)
+        ts, ok = [], True
+        for _ in range(min(2, args.steps)):
+            dt, out = one(p.eps)
+            ts.append(dist.max(dt))
+            ok = ok and out["reached"]
+        ne64 = {"value": round(statistics.mean(ts), 6), "unit": "s", "reached": ok,
+                "sweeps": len(out["kinds"])}
+        ctx.set_normal_arith("double_float")
+
     # end to end through the C ABI from pinned host buffers
     Xh = torch.from_numpy(np.ascontiguousarray(p.X)).pin_memory()
     e2e_times = []
@@ -267,11 +282,12 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 6), "unit": "s", "n_gpus": dist.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value * 1e3, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"mixed": "bf16-tc/fp32/fp64", "fp32": "fp32/fp64", "fp64": "fp64"}[args.precision],
+        "dtype": {"mixed": "bf16-tc/fp32/f32x2", "fp32": "fp32/f32x2", "fp64": "fp64"}[args.precision],
         "data": "synthetic",
         "config": {"workload": p.name, "dims": p.dims, "R": p.R, "eps": p.eps,
                    "max_sweeps": max_sweeps, "target_fitness": target, "f_star_fp64_als": f_star,
                    "precision": args.precision, "use_V": True,
+                   "normal_eq": "fp64" if args.precision == "fp64" else "double-float (f32 pair)",
                    "l2": "flushed between steps (256 MB write); X is 256 MB fp32",
                    "parallelism": "replicas" if dist.world > 1 else "single GPU"},
         "reached": all(o["reached"] for o in outs),
@@ -279,6 +295,7 @@ def run_ours(args):
         "final_fitness": float(last["fitness"][-1]),
         "als_time_to_fitness_s": als_time, "als_reached": als_reached,
         "pp_vs_als_speedup": (round(als_time / value, 3) if als_time else None),
+        "pp_fp64_normal_eq": ne64,
         "roofline": roofline,
         "e2e": {"value": round(statistics.mean(e2e_times), 6), "unit": "s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -46,8 +46,9 @@ typedef enum {
   CPALS_E_UNSUPPORTED = 8  /* configuration outside what this build implements */
 } cpals_status;
 
-/* Arithmetic of the contractions (the normal-equation solve, Grams and
- * fitness are float64 in every mode). */
+/* Arithmetic of the contractions.  The fitness is float64 in every mode;
+ * the normal-equation work (Grams, Gamma, its factorisation and the row
+ * solves) follows cpals_set_normal_arith. */
 typedef enum {
   CPALS_FP64 = 0,        /* tensor, contractions and operators in float64 */
   CPALS_FP32 = 1,        /* tensor, contractions and operators in float32 */
@@ -55,6 +56,17 @@ typedef enum {
                             bf16 tensor cores (fp32 accumulate); lower levels,
                             operators and PP corrections in float32 */
 } cpals_precision;
+
+/* Arithmetic of the normal-equation work of Algorithm 1 lines 5-10
+ * (Grams S^(n), Gamma^(n), its Cholesky factor, the row solves, the
+ * second-order terms' Z).  FP64 contexts always use IEEE float64.  FP32 and
+ * MIXED_BF16 contexts default to double-float (an unevaluated sum of two
+ * floats, 48-bit significand, built from error-free transformations on the
+ * float32 pipes); IEEE float64 is available to them as well. */
+typedef enum {
+  CPALS_NE_FP64 = 0,
+  CPALS_NE_DOUBLE_FLOAT = 1
+} cpals_normal_arith;
 
 /* Sweep kinds reported by cpals_run (Algorithm 3 and Table 2 of the paper). */
 enum { CPALS_SWEEP_ALS = 0, CPALS_SWEEP_PP_INIT = 1, CPALS_SWEEP_PP_APPROX = 2 };
@@ -67,6 +79,12 @@ cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpal
 
 /* Free every device and host resource of the context.  NULL is ignored. */
 void cpals_destroy(cpals_ctx* ctx);
+
+/* Select the normal-equation arithmetic (cpals_normal_arith).  Returns
+ * CPALS_E_UNSUPPORTED for CPALS_NE_DOUBLE_FLOAT on an FP64 context and
+ * CPALS_E_INVALID for an unknown value.  Drops the captured sweep graphs and
+ * the factors: call cpals_init_factors (again) afterwards. */
+cpals_status cpals_set_normal_arith(cpals_ctx* ctx, int arith);
 
 /* Order the context's work after, and before, work already queued on a
  * caller stream (a cudaStream_t passed as void*; NULL = the legacy default

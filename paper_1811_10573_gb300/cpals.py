@@ -51,6 +51,7 @@ _SIGS = {
     "cpals_reset_stats": (C.c_int, [_ctx_p]),
     "cpals_get_stats": (C.c_int, [_ctx_p, C.c_int, _i64p, _dp, _dp, _dp]),
     "cpals_set_graphs": (C.c_int, [_ctx_p, C.c_int]),
+    "cpals_set_normal_arith": (C.c_int, [_ctx_p, C.c_int]),
     "cpals_cost_model": (C.c_int, [_i64p, C.c_int, C.c_int, C.c_int, _dp]),
     "cpals_contract_bf16_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                              C.c_int64, C.c_int64, C.c_int, C.c_int64, C.c_int,
@@ -186,6 +187,13 @@ def cpals_get_stats(ctx, kind):
 
 def cpals_set_graphs(ctx, enable):
     return lib().cpals_set_graphs(ctx, enable)
+
+
+NORMAL_ARITH = {"fp64": 0, "double_float": 1}
+
+
+def cpals_set_normal_arith(ctx, arith):
+    return lib().cpals_set_normal_arith(ctx, arith)
 
 
 def cpals_cost_model(dims, N, R, kind):
@@ -341,6 +349,12 @@ class CPALS:
 
     def set_graphs(self, enable):
         self._ck(cpals_set_graphs(self.ctx, 1 if enable else 0))
+
+    def set_normal_arith(self, arith):
+        """'fp64' or 'double_float' (see cpals_set_normal_arith); the factors
+        must be set again afterwards."""
+        a = NORMAL_ARITH[arith] if isinstance(arith, str) else int(arith)
+        self._ck(cpals_set_normal_arith(self.ctx, a))
 
 
 def cost_model(dims, R, kind):

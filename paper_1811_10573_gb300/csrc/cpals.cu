@@ -63,6 +63,7 @@ struct cpals_ctx {
   float* Slo = nullptr;
   float* Wf = nullptr;   // N*R*R (float W for the df path)
   float2* Linv = nullptr; // W = L^-1 of Gamma^(n), double-float, R x (R|1)
+  float2* Gpk = nullptr;  // Gamma of the next mode, packed by columns (written by the Gram kernel)
   float* Zf = nullptr;   // R*R
   double* S = nullptr;   // N*R*R
   double* W = nullptr;   // N*R*R
@@ -279,7 +280,7 @@ void factor_async(cpals_ctx* c, int n, bool pp, bool useV) {
   cudaEventRecord(c->ev_fork, c->stream);
   cudaStreamWaitEvent(c->side, c->ev_fork, 0);
   if (c->dfm)
-    chol_df(c->Shi, c->Slo, c->Wf, c->N, n, c->R, c->Linv, c->Zf, pp && useV, c->status,
+    chol_df(c->Shi, c->Slo, c->Wf, c->Gpk, c->N, n, c->R, c->Linv, c->Zf, pp && useV, c->status,
             c->Lside());
   else
     gamma_chol(c->S, c->W, c->N, n, c->R, c->Lf, c->Z, pp && useV, c->status, c->Lside());
@@ -300,7 +301,7 @@ void finish_mode(cpals_ctx* c, int n, const T* rhs, bool pp, bool useV) {
              v ? c->Zf : nullptr, (float2*)c->rownorm, s, R, n, c->status, c->L());
     gram_df(Ahi, c->Alo[n], Ahi, P<const float>(c->dAc[n]), c->S + off, c->Shi + off,
             c->Slo + off, c->Wf + off, pp, s, R, (const float2*)c->rownorm, c->scal + 8 + 2 * n,
-            c->L());
+            c->Shi, c->Slo, c->N, n, (n + 1) % c->N, c->Gpk, c->L());
     return;
   }
   if (v)
@@ -722,6 +723,7 @@ cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpal
     AL(c->Wf, (size_t)N * R * R * 4);
     // padded to 16-byte multiples: the row solve copies them with bulk transfers
     AL(c->Linv, (size_t)R * (R | 1) * 8 + 16);
+    AL(c->Gpk, (size_t)R * (R + 1) / 2 * 8 + 16);
     AL(c->Zf, (size_t)R * R * 4 + 16);
   }
   AL(c->S, (size_t)N * R * R * 8);
@@ -781,7 +783,7 @@ void cpals_destroy(cpals_ctx* c) {
     F(c->Alo[n]); F(c->Aphi[n]); F(c->Aplo[n]);
   }
   for (void* p : c->lvl_bufs) F(p);
-  F(c->Shi); F(c->Slo); F(c->Wf); F(c->Linv); F(c->Zf);
+  F(c->Shi); F(c->Slo); F(c->Wf); F(c->Linv); F(c->Gpk); F(c->Zf);
   F(c->S); F(c->W); F(c->Lf); F(c->Z); F(c->ML); F(c->MR); F(c->krp); F(c->tmp[0]); F(c->tmp[1]);
   F(c->rhs); F(c->rhs2); F(c->gpart); F(c->Bt); F(c->rownorm); F(c->dpart); F(c->scal);
   F(c->status); F(c->tickets); F(c->dscr[0]); F(c->dscr[1]);
@@ -871,8 +873,8 @@ cpals_status cpals_init_factors(cpals_ctx* c, const double* const* factors) {
       split_df(c->A[n], P<float>(c->Ac[n]), c->Alo[n], sR, c->L());
       gram_df(P<const float>(c->Ac[n]), c->Alo[n], P<const float>(c->Ac[n]),
               P<const float>(c->dAc[n]), c->S + off, c->Shi + off, c->Slo + off, c->Wf + off,
-              false, (int)c->dims[n], R, (const float2*)c->rownorm, c->scal + 48,
-              c->L());
+              false, (int)c->dims[n], R, (const float2*)c->rownorm, c->scal + 48, c->Shi,
+              c->Slo, c->N, n, (n + 1) % c->N, c->Gpk, c->L());
     } else {
       gram_update<double>(c->A[n], P<const double>(c->Ac[n]), P<const double>(c->dAc[n]),
                           c->S + off, c->W + off, false, (int)c->dims[n], R, c->rownorm,
@@ -1056,7 +1058,7 @@ cpals_status cpals_pp_mttkrp(cpals_ctx* c, int n, int use_V, double* out) {
     const T* res = P<const T>(c->rhs);
     if (use_V) {
       if (c->dfm) {
-        chol_df(c->Shi, c->Slo, c->Wf, c->N, n, R, c->Linv, c->Zf, true, c->status, c->L());
+        chol_df(c->Shi, c->Slo, c->Wf, nullptr, c->N, n, R, c->Linv, c->Zf, true, c->status, c->L());
         convert<float, double>(c->Zf, c->Z, (int64_t)R * R, c->L());
       } else {
         gamma_chol(c->S, c->W, c->N, n, R, c->Lf, c->Z, true, c->status, c->L());
@@ -1086,7 +1088,7 @@ cpals_status cpals_normal_solve(cpals_ctx* c, int n, const double* rhs, double* 
   if (c->dfm) {
     float* frhs = P<float>(c->rhs);
     convert<double, float>(c->dscr[0], frhs, cnt, c->L());
-    chol_df(c->Shi, c->Slo, c->Wf, c->N, n, R, c->Linv, c->Zf, false, c->status, c->L());
+    chol_df(c->Shi, c->Slo, c->Wf, nullptr, c->N, n, R, c->Linv, c->Zf, false, c->status, c->L());
     float* hi = P<float>(c->rhs2);
     float* lo = hi + cnt;
     CK(cudaMemsetAsync(hi, 0, cnt * 8, c->stream));
@@ -1149,6 +1151,18 @@ cpals_status cpals_get_stats(cpals_ctx* c, int kind, int64_t* launches, double* 
   } else {
     return c->fail(CPALS_E_INVALID, "kind must be 0 or 1");
   }
+  return CPALS_OK;
+}
+
+cpals_status cpals_set_normal_arith(cpals_ctx* c, int arith) {
+  if (!c || (arith != CPALS_NE_FP64 && arith != CPALS_NE_DOUBLE_FLOAT)) return CPALS_E_INVALID;
+  if (arith == CPALS_NE_DOUBLE_FLOAT && is64(c))
+    return c->fail(CPALS_E_UNSUPPORTED, "double-float normal equations need an FP32 or MIXED_BF16 context");
+  CK(cudaStreamSynchronize(c->stream));     // no captured graph still running
+  drop_graphs(c);
+  c->dfm = arith == CPALS_NE_DOUBLE_FLOAT;
+  c->have_factors = false;
+  c->ops_built = false;
   return CPALS_OK;
 }
 

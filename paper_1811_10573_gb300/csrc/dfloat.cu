@@ -113,7 +113,8 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
                const float* __restrict__ Aw, const float* __restrict__ dAw, int s, int R, int nb,
                int ntS, int splits, int chunk, double* __restrict__ S, float* __restrict__ Shi,
                float* __restrict__ Slo, float* __restrict__ W, const float2* __restrict__ rownorm,
-               double* __restrict__ scal) {
+               double* __restrict__ scal, const float* __restrict__ ShiAll,
+               const float* __restrict__ SloAll, int N, int n, int nn, float2* __restrict__ Gpk) {
   cg::cluster_group cl = cg::this_cluster();
   const int z = (int)cl.block_rank();
   const int t = blockIdx.x / splits;
@@ -194,7 +195,10 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
     for (int zz = 1; zz < 8; zz++)
       if (zz < splits) acc = t < ntS ? df_add(acc, upk(v[zz])) : dfl{acc.hi + v[zz].x, 0.f};
     const int i = ti * 32 + e / 32, j = tj * 32 + e % 32;
-    if (i < R && j < R) {
+    // a diagonal tile holds both (i, j) and (j, i), summed in different
+    // orders: only i <= j writes the pair, so S is exactly symmetric and
+    // every run writes the same value
+    if (i < R && j < R && !(t < ntS && ti == tj && i > j)) {
       if (t < ntS) {
         const double d = df_dbl(acc);
         S[i * R + j] = d;
@@ -203,6 +207,19 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
         Shi[j * R + i] = acc.hi;
         Slo[i * R + j] = acc.lo;
         Slo[j * R + i] = acc.lo;
+        if (Gpk && i <= j) {
+          // Gamma^(nn)_ji = product over k != nn of S^(k)_ij, in mode order,
+          // packed by columns (entry (j, i), j >= i, at cs(i) + j - i)
+          dfl g = {1.f, 0.f};
+          const int RR = R * R;
+          for (int k = 0; k < N; k++) {
+            if (k == nn) continue;
+            const dfl sk = k == n ? acc : dfl{ShiAll[(int64_t)k * RR + i * R + j],
+                                              SloAll[(int64_t)k * RR + i * R + j]};
+            g = df_mul(g, sk);
+          }
+          Gpk[i * R - i * (i - 1) / 2 + (j - i)] = pk(g);
+        }
       } else {
         W[i * R + j] = acc.hi;
       }
@@ -294,7 +311,7 @@ __device__ __forceinline__ float4 pk2(dfl a, dfl b) { return make_float4(a.hi, a
 
 // Shared-memory layout of the two CTAs (byte offsets from the dynamic base).
 struct CholLayout {
-  size_t tb, crd, lc, end0;          // CTA 0: G, crd, column pairs
+  size_t tb, crd, lc, end0;          // CTA 0: G, crd, column pairs (3 sets + zeros)
   size_t uv, id, lsub, bars, flag, end1;   // CTA 1: B (at 0), coefficients, 1/L_jj,
                                            // L_j,j-1/L_j-1,j-1, one mbarrier per pair, stop flag
   __host__ __device__ CholLayout(int R) {
@@ -302,7 +319,7 @@ struct CholLayout {
     tb = (T * 8 + 15) / 16 * 16;
     crd = tb;
     lc = crd + (T * 4 + 15) / 16 * 16;
-    end0 = lc + 2 * (size_t)R * 16;
+    end0 = lc + 4 * (size_t)R * 16;
     uv = tb;
     id = uv + (size_t)(R / 2 + 1) * R * 16;
     lsub = id + (size_t)R * 8;
@@ -340,10 +357,12 @@ __device__ __forceinline__ int ld_acquire_cluster(const int* p) {
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CPALS_CHOL_THREADS, 1)
 chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
-                   const float* __restrict__ Wg, int N, int n, int R, float2* __restrict__ Wout,
-                   float* __restrict__ Z, int useV, int* __restrict__ status) {
+                   const float* __restrict__ Wg, const float2* __restrict__ Gpk, int N, int n,
+                   int R, float2* __restrict__ Wout, float* __restrict__ Z, int useV,
+                   int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char csm[];
   __shared__ int bad;
+  __shared__ __align__(8) uint64_t gbar;
   cg::cluster_group cl = cg::this_cluster();
   const int role = (int)cl.block_rank();
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -361,23 +380,21 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
   const int npair = (R + 1) / 2;
   if (role == 1) {
     float2* B = reinterpret_cast<float2*>(csm);
-    if (tid == 0) {
-      flag[0] = 0;
-      // pair P brings 16 bytes per row i >= 2P, 1/L_jj of its columns and,
-      // when it has two, L_{2P+1,2P} / L_{2P,2P}
-      for (int P = 0; P < npair; P++) {
-        const uint32_t b = (uint32_t)__cvta_generic_to_shared(bars + P);
-        const uint32_t bytes = 16u * (uint32_t)(R - 2 * P) + (2 * P + 1 < R ? 24u : 8u);
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
-                     : "memory");
-      }
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (tid == 0) flag[0] = 0;
+    // pair P brings 16 bytes per row i >= 2P, 1/L_jj of its columns and,
+    // when it has two, L_{2P+1,2P} / L_{2P,2P}
+    for (int P = tid; P < npair; P += nt) {
+      const uint32_t b = (uint32_t)__cvta_generic_to_shared(bars + P);
+      const uint32_t bytes = 16u * (uint32_t)(R - 2 * P) + (2 * P + 1 < R ? 24u : 8u);
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
+                   : "memory");
     }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int i = warp; i < R; i += nwarp)
       for (int j = lane; j <= i; j += 32) B[i * (i + 1) / 2 + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+    cl.sync();                                 // CTA 1's barriers exist before CTA 0 writes
   }
-  cl.sync();                                   // CTA 1's barriers exist before CTA 0 writes
   if (role == 0) {
     float2* G = reinterpret_cast<float2*>(csm);
     uint32_t* crd = reinterpret_cast<uint32_t*>(csm + lay.crd);
@@ -386,9 +403,27 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
     const uint32_t lsubr = cluster_addr(lsub, 1), barr = cluster_addr(bars, 1);
     int* flagr = cl.map_shared_rank(flag, 1);
     if (tid == 0) bad = 0;
-    // Gamma: entries in packed order, eight per thread in flight; each
-    // mode's loads are issued together before its products
-    for (int base = 0; base < T; base += 8 * nt) {
+    const uint32_t gb = (uint32_t)__cvta_generic_to_shared(&gbar);
+    const uint32_t gbytes = (uint32_t)((T * sizeof(float2) + 15) / 16 * 16);
+    if (Gpk) {
+      // Gamma arrives packed (formed by the Gram kernel of the previous mode)
+      if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(gb));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(gb), "r"(gbytes)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"((uint32_t)__cvta_generic_to_shared(G)), "l"(Gpk), "r"(gbytes), "r"(gb)
+                     : "memory");
+      }
+      for (int j = warp; j < R; j += nwarp) {
+        const int e0 = col_start(j, R);
+        for (int i = j + lane; i < R; i += 32) crd[e0 + i - j] = (uint32_t)i | ((uint32_t)j << 16);
+      }
+    }
+    // Gamma from the Grams otherwise: entries in packed order, eight per
+    // thread in flight; each mode's loads are issued together
+    for (int base = 0; !Gpk && base < T; base += 8 * nt) {
       int gi[8];
       dfl acc[8];
 #pragma unroll
@@ -422,84 +457,120 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
       for (int q = 0; q < 8; q++)
         if (gi[q] >= 0) G[base + q * nt + tid] = pk(acc[q]);
     }
-    for (int i = tid; i < R; i += nt) lc[R + i] = make_float4(0.f, 0.f, 0.f, 0.f);  // no columns before 0
+    for (int i = tid; i < R; i += nt) lc[3 * R + i] = make_float4(0.f, 0.f, 0.f, 0.f);  // no pair before 0
+    if (Gpk && tid == 0) {
+      // bounded wait for the packed Gamma
+      const unsigned long long t0 = clock64();
+      bool ok = false;
+      while (clock64() - t0 < 4000000000ull) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(gb) : "memory");
+        if (done) { ok = true; break; }
+      }
+      if (!ok) {
+        atomicOr(status + 2, 4);
+        bad = 1;
+      }
+    }
+    cl.sync();                                 // CTA 1's barriers exist before this CTA writes
     __syncthreads();
-    // The first 128 threads compute the next column pair (a); the others
-    // update (b).  Small CTAs do both.
-    const bool split = nt > 128;
-    const int na = split ? 128 : nt;
-    const int ut = tid - (split ? 128 : 0), nu_t = nt - (split ? 128 : 0);
-    // k = -2 is the prologue (columns 0 and 1 from zero columns); then pairs
-    for (int k = -2; k + 2 < R; k += 2) {
-      const int cur = (((k + 2) >> 1) & 1) ^ 1, nxt = cur ^ 1;   // the prologue reads set 1 (zeros)
-      const float4* cc = lc + cur * R;
-      float4* nc = lc + nxt * R;
-      const int p = k + 2;
-      if (tid < na) {
-        // (a) columns p and p+1 of L and their inverse-update coefficients,
-        // sent to CTA 1 as they are made
-        const int ep = col_start(p, R);
-        const bool two = p + 1 < R;
-        const int ep1 = two ? col_start(p + 1, R) : 0;
-        const uint32_t bar = barr + 8u * (uint32_t)(p >> 1);
-        const uint32_t uvp = UVr + 16u * (uint32_t)((p >> 1) * R);
-        for (int i = p + tid; i < R; i += na) {
-          const float4 cp = cc[p];
-          const dfl a2 = lo2(cp), b2 = hi2(cp);
-          const dfl piv2 = df_fms2(upk(G[ep]), a2, a2, b2, b2);
-          if (bad_pivot(piv2)) {
-            bad = 1;
-            break;
-          }
-          const dfl il2 = df_rsqrt(piv2);
-          const float4 ci = cc[i];
-          const dfl l2 = df_mul(df_fms2(upk(G[ep + i - p]), lo2(ci), a2, hi2(ci), b2), il2);
-          const dfl q2 = df_mul(l2, il2);
-          dfl l3 = {0.f, 0.f}, u = q2, v = {0.f, 0.f};
-          if (i == p) st_async8(idr + 8u * p, pk(il2), bar);
-          if (two && i > p) {
-            const float4 cp1 = cc[p + 1];
-            const dfl a3 = lo2(cp1), b3 = hi2(cp1);
-            const dfl c3 = df_mul(df_fms2(upk(G[ep + 1]), a3, a2, b3, b2), il2);
-            const dfl piv3 = df_fms(df_fms2(upk(G[ep1]), a3, a3, b3, b3), c3, c3);
-            if (bad_pivot(piv3)) {
+    // Two groups run as a pipeline over the column pairs P = (2P, 2P+1):
+    //   group A (threads 0..127) makes pair P (a) and stores it in set P % 3;
+    //   group B (the rest) applies pair P to the columns right of pair P+1
+    //   (b), first the two columns of pair P+2 (the only ones A needs next),
+    //   then the remainder while A is already working on later pairs.
+    // Named barriers, two of each kind so that consecutive pairs never share
+    // one: X[P % 2] (B arrives when pair P+2's columns are updated, A waits
+    // before making pair P+2), Y[P % 2] (A arrives when pair P is made, B
+    // waits before applying it); 5 orders A's first two pairs.
+    const int na = 128, nb = nt - na;
+    const bool inA = tid < na;
+    const int ut = tid - na;
+    for (int P = 0; P < npair; P++) {
+      const int p = 2 * P;
+      if (inA) {
+        if (P >= 2)
+          asm volatile("bar.sync %0, %1;" ::"r"(1 + (P & 1)), "r"(nt) : "memory");
+        else if (P == 1)
+          asm volatile("bar.sync 5, %0;" ::"r"(na) : "memory");
+        if (!bad) {
+          // (a) columns p and p+1 of L and their inverse-update coefficients,
+          // sent to CTA 1 as they are made
+          const float4* cc = lc + (P ? (P - 1) % 3 : 3) * R;
+          float4* nc = lc + (P % 3) * R;
+          const int ep = col_start(p, R);
+          const bool two = p + 1 < R;
+          const int ep1 = two ? col_start(p + 1, R) : 0;
+          const uint32_t bar = barr + 8u * (uint32_t)P;
+          const uint32_t uvp = UVr + 16u * (uint32_t)(P * R);
+          for (int i = p + tid; i < R; i += na) {
+            const float4 cp = cc[p];
+            const dfl a2 = lo2(cp), b2 = hi2(cp);
+            const dfl piv2 = df_fms2(upk(G[ep]), a2, a2, b2, b2);
+            if (bad_pivot(piv2)) {
               bad = 1;
               break;
             }
-            const dfl il3 = df_rsqrt(piv3);
-            l3 = df_mul(df_fms(df_fms2(upk(G[ep1 + i - p - 1]), lo2(ci), a3, hi2(ci), b3), l2, c3), il3);
-            v = df_mul(l3, il3);
-            u = df_fms(q2, v, df_mul(c3, il2));
-            if (i == p + 1) {
-              st_async8(idr + 8u * (p + 1), pk(il3), bar);
-              st_async8(lsubr + 8u * (p + 1), pk(q2), bar);
+            const dfl il2 = df_rsqrt(piv2);
+            const float4 ci = cc[i];
+            const dfl l2 = df_mul(df_fms2(upk(G[ep + i - p]), lo2(ci), a2, hi2(ci), b2), il2);
+            const dfl q2 = df_mul(l2, il2);
+            dfl l3 = {0.f, 0.f}, u = q2, v = {0.f, 0.f};
+            if (i == p) st_async8(idr + 8u * p, pk(il2), bar);
+            if (two && i > p) {
+              const float4 cp1 = cc[p + 1];
+              const dfl a3 = lo2(cp1), b3 = hi2(cp1);
+              const dfl c3 = df_mul(df_fms2(upk(G[ep + 1]), a3, a2, b3, b2), il2);
+              const dfl piv3 = df_fms(df_fms2(upk(G[ep1]), a3, a3, b3, b3), c3, c3);
+              if (bad_pivot(piv3)) {
+                bad = 1;
+                break;
+              }
+              const dfl il3 = df_rsqrt(piv3);
+              l3 = df_mul(df_fms(df_fms2(upk(G[ep1 + i - p - 1]), lo2(ci), a3, hi2(ci), b3), l2, c3), il3);
+              v = df_mul(l3, il3);
+              u = df_fms(q2, v, df_mul(c3, il2));
+              if (i == p + 1) {
+                st_async8(idr + 8u * (p + 1), pk(il3), bar);
+                st_async8(lsubr + 8u * (p + 1), pk(q2), bar);
+              }
             }
+            nc[i] = pk2(l2, l3);
+            st_async16(uvp + 16u * i, pk2(u, v), bar);
           }
-          nc[i] = pk2(l2, l3);
-          st_async16(uvp + 16u * i, pk2(u, v), bar);
         }
+        asm volatile("bar.arrive %0, %1;" ::"r"(3 + (P & 1)), "r"(nt) : "memory");
+      } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(3 + (P & 1)), "r"(nt) : "memory");
+        const float4* cc = lc + (P % 3) * R;
+        const bool work = !bad;
+        // (b) G_ij -= L_i,p L_j,p + L_i,p+1 L_j,p+1 on [e0, e1), two entries per
+        // iteration (independent double-float chains)
+        auto update = [&](int e0, int e1) {
+          int e = e0 + ut;
+          for (; e + nb < e1; e += 2 * nb) {
+            const uint32_t ij0 = crd[e], ij1 = crd[e + nb];
+            const float4 li0 = cc[ij0 & 0xffffu], lj0 = cc[ij0 >> 16];
+            const float4 li1 = cc[ij1 & 0xffffu], lj1 = cc[ij1 >> 16];
+            const dfl g0 = upk(G[e]), g1 = upk(G[e + nb]);
+            G[e] = pk(df_fms2(g0, lo2(li0), lo2(lj0), hi2(li0), hi2(lj0)));
+            G[e + nb] = pk(df_fms2(g1, lo2(li1), lo2(lj1), hi2(li1), hi2(lj1)));
+          }
+          if (e < e1) {
+            const uint32_t ij = crd[e];
+            const float4 li = cc[ij & 0xffffu], lj = cc[ij >> 16];
+            G[e] = pk(df_fms2(upk(G[e]), lo2(li), lo2(lj), hi2(li), hi2(lj)));
+          }
+        };
+        if (P + 2 < npair) {
+          if (work) update(col_start(p + 4, R), col_start(min(p + 6, R), R));
+          asm volatile("bar.arrive %0, %1;" ::"r"(1 + (P & 1)), "r"(nt) : "memory");
+        }
+        if (work && p + 6 < R) update(col_start(p + 6, R), T);
       }
-      // (b) trailing update of the columns >= k+4 with the pivots k, k+1
-      if (k >= 0 && k + 4 < R && ut >= 0) {
-        // two entries per iteration: independent double-float chains
-        int e = col_start(k + 4, R) + ut;
-        for (; e + nu_t < T; e += 2 * nu_t) {
-          const uint32_t ij0 = crd[e], ij1 = crd[e + nu_t];
-          const float4 li0 = cc[ij0 & 0xffffu], lj0 = cc[ij0 >> 16];
-          const float4 li1 = cc[ij1 & 0xffffu], lj1 = cc[ij1 >> 16];
-          const dfl g0 = upk(G[e]), g1 = upk(G[e + nu_t]);
-          G[e] = pk(df_fms2(g0, lo2(li0), lo2(lj0), hi2(li0), hi2(lj0)));
-          G[e + nu_t] = pk(df_fms2(g1, lo2(li1), lo2(lj1), hi2(li1), hi2(lj1)));
-        }
-        if (e < T) {
-          const uint32_t ij = crd[e];
-          const float4 li = cc[ij & 0xffffu], lj = cc[ij >> 16];
-          G[e] = pk(df_fms2(upk(G[e]), lo2(li), lo2(lj), hi2(li), hi2(lj)));
-        }
-      }
-      __syncthreads();
-      if (bad) break;
     }
+    __syncthreads();
     if (bad && tid == 0) {
       atomicOr(status, 1 << n);
       st_release_cluster(flagr, 1);            // CTA 1 stops waiting
@@ -855,7 +926,8 @@ void split_df(const double* A, float* hi, float* lo, int64_t n, Launch L) {
 
 void gram_df(const float* Ahi, const float* Alo, const float* Aw, const float* dAw, double* S,
              float* Shi, float* Slo, float* W, bool withW, int s, int R, const float2* rownorm,
-             double* scal, Launch L) {
+             double* scal, const float* ShiAll, const float* SloAll, int N, int n, int nn,
+             float2* Gpk, Launch L) {
   const int nb = (R + 31) / 32;
   const int ntS = nb * (nb + 1) / 2;
   const int ntiles = withW ? ntS + nb * nb : ntS;
@@ -874,17 +946,17 @@ void gram_df(const float* Ahi, const float* Alo, const float* Aw, const float* d
   cfg.attrs = at;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, gram_df_kernel, Ahi, Alo, Aw, dAw, s, R, nb, ntS, splits, chunk, S, Shi,
-                     Slo, W, rownorm, scal);
+                     Slo, W, rownorm, scal, ShiAll, SloAll, N, n, nn, nn >= 0 ? Gpk : nullptr);
   (*L.counter)++;
 }
 
-void chol_df(const float* Shi, const float* Slo, const float* W, int N, int n, int R,
-             float2* Winv, float* Z, bool useV, int* status, Launch L) {
+void chol_df(const float* Shi, const float* Slo, const float* W, const float2* Gpk, int N, int n,
+             int R, float2* Winv, float* Z, bool useV, int* status, Launch L) {
   // 128 column threads plus about one update thread per eight packed entries
   const int T = R * (R + 1) / 2;
-  const int threads = std::min(CPALS_CHOL_THREADS, 128 + (T / 8 + 31) / 32 * 32);
-  chol_inv_df_kernel<<<2, threads, chol_inv_smem(R), L.stream>>>(Shi, Slo, W, N, n, R, Winv, Z,
-                                                                 useV ? 1 : 0, status);
+  const int threads = std::min(CPALS_CHOL_THREADS, 128 + std::max(32, (T / 8 + 31) / 32 * 32));
+  chol_inv_df_kernel<<<2, threads, chol_inv_smem(R), L.stream>>>(Shi, Slo, W, Gpk, N, n, R, Winv,
+                                                                 Z, useV ? 1 : 0, status);
   (*L.counter)++;
 }
 

@@ -116,11 +116,14 @@ cudaError_t setup_df_kernels();
 void split_df(const double* A, float* hi, float* lo, int64_t n, Launch L);
 void gram_df(const float* Ahi, const float* Alo, const float* Aw, const float* dAw, double* S,
              float* Shi, float* Slo, float* W, bool withW, int s, int R, const float2* rownorm,
-             double* scal, Launch L);
-// chol_df: Gamma^(n) = L L^T and Winv = L^-1 (row stride R|1, zero upper
-// triangle); solve_df: a = Winv^T Winv b per row.
-void chol_df(const float* Shi, const float* Slo, const float* W, int N, int n, int R, float2* Winv,
-             float* Z, bool useV, int* status, Launch L);
+             double* scal, const float* ShiAll, const float* SloAll, int N, int n, int nn,
+             float2* Gpk, Launch L);
+// gram_df with nn >= 0 also writes Gamma^(nn) (the next mode's) packed by
+// columns into Gpk; chol_df: Gamma^(n) (from Gpk when not null, else from the
+// Grams) = L L^T and Winv = L^-1 (row stride R|1, zero upper triangle);
+// solve_df: a = Winv^T Winv b per row.
+void chol_df(const float* Shi, const float* Slo, const float* W, const float2* Gpk, int N, int n,
+             int R, float2* Winv, float* Z, bool useV, int* status, Launch L);
 void solve_df(const float* rhs, double* A, float* Ahi, float* Alo, const float* Arefhi,
               const float* Areflo, double* dA, float* dAc, const float2* Winv, const float* Z,
               float2* rownorm, int s, int R, int n, const int* status, Launch L);

@@ -229,3 +229,42 @@ def test_normal_solve(dims, R, prec):
             ref = O.solve_normal(rhs, G)
             assert np.linalg.cond(G) < 1e6
             assert rel(g.normal_solve(n, rhs), ref) < 1e-11, (n, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_normal_arith_fp64_and_double_float_agree(prec):
+    """FP32/mixed contexts run the normal-equation work (Sec. 2.3) in
+    double-float by default and in IEEE float64 on request.  The first mode
+    update sees identical inputs in both (the same float right-hand side and
+    Grams of the same factors), so the two agree within the double-float
+    rounding amplified by the conditioning (1e-10); later updates see
+    float compute copies that may differ in the last bit, so after ALS and
+    PP sweeps they agree within the contraction tolerance.  The float64
+    variant matches the float64 oracle sweep within that tolerance too.  An
+    FP64 context refuses double-float."""
+    p = synth.make_problem("normal", [40, 33, 27], 9, seed=5, storage="f32")
+    out = {}
+    for arith in ["double_float", "fp64"]:
+        with _ctx(p, prec) as g:
+            g.set_normal_arith(arith)
+            with pytest.raises(cpals.CPALSError):
+                g.als_sweep()                      # factors were dropped
+            g.init_factors(p.A0)
+            g.als_sweep()
+            first = g.get_factors()
+            for _ in range(2):
+                g.als_sweep()
+            g.pp_build_operators()
+            g.pp_sweep(True)
+            out[arith] = (first, g.get_factors())
+    assert rel(out["fp64"][0][0], out["double_float"][0][0]) < 1e-10
+    for a, b in zip(out["fp64"][1], out["double_float"][1]):
+        assert rel(a, b) < TOL[prec]
+    A = [a.copy() for a in p.A0]
+    S = [O.gram(a) for a in A]
+    O.als_sweep(X64(p), A, S)
+    for a, b in zip(out["fp64"][0], A):
+        assert rel(a, b) < 5 * TOL[prec]
+    with cpals.CPALS(p.dims, p.R, "fp64") as g:
+        with pytest.raises(cpals.CPALSError):
+            g.set_normal_arith("double_float")
