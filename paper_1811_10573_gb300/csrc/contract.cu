@@ -243,12 +243,18 @@ pp_correct_kernel(const T* __restrict__ Mp, PPTermsArg<T> terms, T* __restrict__
   }
 }
 
-// float path with 4 outputs per lane (16-byte loads) when R % 4 == 0.
+// float path when R % 4 == 0: a CTA owns 32 consecutive outputs (8 float4
+// units); lane l of every warp takes unit l % 8 and every 32nd x starting at
+// 4 * warp + l / 8, so one warp load touches four 128-byte runs of the
+// operator.  1,250 CTAs for a 400 x 100 mode keep eight CTAs per SM busy and
+// the waves even.  The 32 partial sums of each output are added in a fixed
+// order (deterministic).
 __global__ void __launch_bounds__(kThreads)
 pp_correct4_kernel(const float* __restrict__ Mp, PPTermsArg<float> terms, float* __restrict__ out,
                    int64_t total, int R) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t f = (int64_t)blockIdx.x * 128 + 4 * lane;
+  const int u = lane & 7, xg = 4 * w + (lane >> 3);          // unit, x offset (0..31)
+  const int64_t f = (int64_t)blockIdx.x * 32 + 4 * u;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   if (f < total) {
     const int64_t y = f / R;
@@ -256,9 +262,26 @@ pp_correct4_kernel(const float* __restrict__ Mp, PPTermsArg<float> terms, float*
     for (int t = 0; t < terms.n; t++) {
       const PPTerm<float> tt = terms.t[t];
       const float* base = tt.op + y * tt.ystride + r;
-#pragma unroll 4
-      for (int x = w; x < tt.sx; x += 8) {
-        const float4 v = *reinterpret_cast<const float4*>(base + (int64_t)x * tt.xstride);
+      // up to four 16-byte operator loads in flight per thread (the
+      // operators are streamed once per sweep: evict-first loads)
+      int x = xg;
+      for (; x + 96 < tt.sx; x += 128) {
+        float4 v[4], a[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          v[q] = __ldcs(reinterpret_cast<const float4*>(base + (int64_t)(x + 32 * q) * tt.xstride));
+          a[q] = __ldg(reinterpret_cast<const float4*>(tt.dA + (int64_t)(x + 32 * q) * R + r));
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          acc.x = fmaf(v[q].x, a[q].x, acc.x);
+          acc.y = fmaf(v[q].y, a[q].y, acc.y);
+          acc.z = fmaf(v[q].z, a[q].z, acc.z);
+          acc.w = fmaf(v[q].w, a[q].w, acc.w);
+        }
+      }
+      for (; x < tt.sx; x += 32) {
+        const float4 v = __ldcs(reinterpret_cast<const float4*>(base + (int64_t)x * tt.xstride));
         const float4 a = __ldg(reinterpret_cast<const float4*>(tt.dA + (int64_t)x * R + r));
         acc.x = fmaf(v.x, a.x, acc.x);
         acc.y = fmaf(v.y, a.y, acc.y);
@@ -267,20 +290,23 @@ pp_correct4_kernel(const float* __restrict__ Mp, PPTermsArg<float> terms, float*
       }
     }
   }
-  __shared__ float4 red[8][33];
-  red[w][lane] = acc;
+  __shared__ float4 red[32][9];
+  red[xg][u] = acc;
   __syncthreads();
-  if (w == 0 && f < total) {
-    float4 sum = red[0][lane];
-#pragma unroll
-    for (int i = 1; i < 8; i++) {
-      sum.x += red[i][lane].x;
-      sum.y += red[i][lane].y;
-      sum.z += red[i][lane].z;
-      sum.w += red[i][lane].w;
+  if (threadIdx.x < 8) {
+    const int uu = threadIdx.x;
+    const int64_t ff = (int64_t)blockIdx.x * 32 + 4 * uu;
+    if (ff < total) {
+      float4 sum = red[0][uu];
+      for (int i = 1; i < 32; i++) {
+        sum.x += red[i][uu].x;
+        sum.y += red[i][uu].y;
+        sum.z += red[i][uu].z;
+        sum.w += red[i][uu].w;
+      }
+      const float4 m = *reinterpret_cast<const float4*>(Mp + ff);
+      *reinterpret_cast<float4*>(out + ff) = make_float4(m.x + sum.x, m.y + sum.y, m.z + sum.z, m.w + sum.w);
     }
-    const float4 m = *reinterpret_cast<const float4*>(Mp + f);
-    *reinterpret_cast<float4*>(out + f) = make_float4(m.x + sum.x, m.y + sum.y, m.z + sum.z, m.w + sum.w);
   }
 }
 
@@ -467,7 +493,7 @@ void pp_correct(const T* Mp, const PPTerm<T>* terms, int nterms, T* out, int sy,
   for (int i = 0; i < nterms; i++) a.t[i] = terms[i];
   const int64_t total = (int64_t)sy * R;
   if (sizeof(T) == 4 && R % 4 == 0) {
-    pp_correct4_kernel<<<(unsigned)cdiv(total, 128), kThreads, 0, L.stream>>>(
+    pp_correct4_kernel<<<(unsigned)cdiv(total, 32), kThreads, 0, L.stream>>>(
         (const float*)Mp, *reinterpret_cast<PPTermsArg<float>*>(&a), (float*)out, total, R);
     (*L.counter)++;
     return;
