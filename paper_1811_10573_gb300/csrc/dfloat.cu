@@ -251,39 +251,44 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
 }
 
 // ---------------------------------------------------------------- Gamma, Cholesky, inverse
-// A cluster of two CTAs forms Gamma^(n) = Hadamard product of the Grams
-// S^(k), k != n, in double-float, factors it Gamma = L L^T (CTA 0) and
-// inverts the factor, W = L^-1 (CTA 1), two pivots per step (right-looking;
-// Golub & Van Loan Alg. 4.2.2 for the factor, the column-oriented triangular
-// inverse for W).
-// CTA 0 holds the lower triangle of Gamma packed by columns (entry (i, j),
-// i >= j, at cs(j) + i - j with cs(j) = j R - j (j - 1) / 2, so the trailing
-// triangle right of a column is a contiguous suffix that all threads share
-// evenly), the (row, column) of every packed index and the current pair of
-// columns of L.  Its step k:
-//   (a) columns k+2 and k+3 of L from the unupdated G columns and columns k,
-//       k+1 (each thread recomputes the two pivots and L_{k+3,k+2}), and the
-//       inverse-update coefficients of those two columns,
-//         v_i = L_i,k+3 / L_k+3,k+3,
-//         u_i = L_i,k+2 / L_k+2,k+2 - v_i L_k+3,k+2 / L_k+2,k+2,
-//       with 1 / L_jj and L_{k+3,k+2} / L_{k+2,k+2}, stored straight into
-//       CTA 1's shared memory, then a release flag for that pair;
-//   (b) G_ij -= L_ik L_jk + L_i,k+1 L_j,k+1 for the columns j >= k+4.
-// CTA 1 holds the lower triangle of the inverse in progress packed by rows
-// (entry (i, c) at i (i + 1) / 2 + c), initially the identity, and for each
-// pair k waits (bounded) for its flag and applies
-//   (c) B_ic -= u_i B_kc + v_i B_k+1,c for rows i >= k+2, c <= k+1:
-//       pivot k and pivot k+1 (which sees row k+1 after pivot k) in one pass.
-// Row k+1 gets pivot k at the end, and row j of W is the final row j of B
-// divided by L_jj.  CTA 0 never waits on CTA 1, so the two run at their own
-// pace.  Every update is one fused double-float g - a b - c d (exact leading
-// products and sums, one renormalisation: backward error a few units of
-// 2^-48 relative to the operands).  Writes W (row stride RS = R | 1, zeros
-// above the diagonal and in the padding column) and, with useV, the float
-// matrix Z of the second-order PP terms (Eq. 3).  A non-positive pivot sets
-// bit n of status[0]; a wait that runs out sets status[2].
+// A cluster of three CTAs forms Gamma^(n) = Hadamard product of the Grams
+// S^(k), k != n, in double-float, factors it Gamma = L L^T and inverts the
+// factor, W = L^-1, two pivots per step (right-looking; Golub & Van Loan
+// Alg. 4.2.2 for the factor, the column-oriented triangular inverse for W).
+//   CTA 2 (updates) holds the lower triangle of Gamma packed by columns
+//     (entry (i, j), i >= j, at cs(j) + i - j, cs(j) = j R - j (j - 1) / 2,
+//     so the trailing triangle right of a column is a contiguous suffix that
+//     all its threads share evenly).  For each column pair P = (p, p+1),
+//     p = 2P, it applies the pair to the columns right of pair P+1: first
+//     those of pair P+2, which it then sends to CTA 0, then the rest.
+//   CTA 0 (chain) makes the pairs.  A pivot warp factors the 2 x 2 pivot
+//     block (a, b; b, d) of pair P less pair P-1 (lanes 0..2 form a, b, d
+//     at once) as il2 = 1/sqrt(a), il3 = a il2 / sqrt(ad - b^2): two
+//     independent reciprocal square roots.  Row thread i keeps its row of
+//     pair P-1 in registers, forms the numerators of L_ip and L_i,p+1 before
+//     the pivots arrive, then L_ip, L_i,p+1 and the inverse-update
+//     coefficients v_i = L_i,p+1 / L_p+1,p+1, u_i = L_ip / L_pp - v_i
+//     L_p+1,p / L_pp.  Rows p+2 and p+3 release the next pivot block, so the
+//     chain from pair to pair is one pivot block and two short row steps on
+//     an SM that runs nothing else.
+//   CTA 1 (inverse) holds the lower triangle of the inverse in progress
+//     packed by rows (entry (i, c) at i (i + 1) / 2 + c), initially the
+//     identity, and applies B_ic -= u_i B_kc + v_i B_k+1,c for rows i >= k+2,
+//     c <= k+1 per pair k = 2P (pivot k and pivot k+1, which sees row k+1
+//     after pivot k).  Row k+1 gets pivot k at the end, and row j of W is
+//     the final row j of B divided by L_jj.
+// Data moves between the CTAs only as st.async stores into the receiver's
+// shared memory that complete a transaction count on one of its mbarriers
+// (one per pair and purpose), so no CTA reads another's shared memory and
+// no fence is needed; every wait is bounded.  Every update is one fused
+// double-float g - a b - c d (exact leading products and sums, one
+// renormalisation: backward error a few units of 2^-48 relative to the
+// operands).  Writes W (row stride RS = R | 1, zeros above the diagonal and
+// in the padding column) and, with useV, the float matrix Z of the
+// second-order PP terms (Eq. 3).  A non-positive pivot sets bit n of
+// status[0]; a wait that runs out sets a bit of status[2].
 #ifndef CPALS_CHOL_THREADS
-#define CPALS_CHOL_THREADS 640
+#define CPALS_CHOL_THREADS 512
 #endif
 __device__ __forceinline__ int col_start(int j, int R) { return j * R - j * (j - 1) / 2; }
 // g - a b - c d
@@ -309,16 +314,17 @@ __device__ __forceinline__ dfl lo2(float4 v) { return {v.x, v.y}; }
 __device__ __forceinline__ dfl hi2(float4 v) { return {v.z, v.w}; }
 __device__ __forceinline__ float4 pk2(dfl a, dfl b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
 
-// Shared-memory layout of the two CTAs (byte offsets from the dynamic base).
+// Shared-memory layout of the three CTAs (byte offsets from the dynamic base).
 struct CholLayout {
-  size_t tb, crd, lc, end0;          // CTA 0: G, crd, column pairs (3 sets + zeros)
-  size_t uv, id, lsub, bars, flag, end1;   // CTA 1: B (at 0), coefficients, 1/L_jj,
-                                           // L_j,j-1/L_j-1,j-1, one mbarrier per pair, stop flag
+  size_t gc, lc, end0;                      // CTA 0: pair columns of G (4 slots), pairs of L (4 sets)
+  size_t uv, id, lsub, bars, flag, end1;    // CTA 1: B (at 0), coefficients, 1/L_jj,
+                                            // L_j,j-1/L_j-1,j-1, one mbarrier per pair, stop flag
+  size_t crd, lc2, end2;                    // CTA 2: G (at 0), (row, column) of each entry, pairs of L
   __host__ __device__ CholLayout(int R) {
     const size_t T = (size_t)R * (R + 1) / 2;
-    tb = (T * 8 + 15) / 16 * 16;
-    crd = tb;
-    lc = crd + (T * 4 + 15) / 16 * 16;
+    const size_t tb = (T * 8 + 15) / 16 * 16;
+    gc = 0;
+    lc = gc + 8 * (size_t)R * 8;
     end0 = lc + 4 * (size_t)R * 16;
     uv = tb;
     id = uv + (size_t)(R / 2 + 1) * R * 16;
@@ -326,8 +332,14 @@ struct CholLayout {
     bars = lsub + (size_t)R * 8;
     flag = bars + (size_t)(R / 2 + 1) * 8;
     end1 = flag + 16;
+    crd = tb;
+    lc2 = crd + (T * 4 + 15) / 16 * 16;
+    end2 = lc2 + 4 * (size_t)R * 16;
   }
-  __host__ __device__ size_t bytes() const { return end0 > end1 ? end0 : end1; }
+  __host__ __device__ size_t bytes() const {
+    const size_t m = end0 > end1 ? end0 : end1;
+    return m > end2 ? m : end2;
+  }
 };
 
 // Remote shared-memory stores that complete a transaction count on an
@@ -355,7 +367,7 @@ __device__ __forceinline__ int ld_acquire_cluster(const int* p) {
   return v;
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CPALS_CHOL_THREADS, 1)
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(CPALS_CHOL_THREADS, 1)
 chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
                    const float* __restrict__ Wg, const float2* __restrict__ Gpk, int N, int n,
                    int R, float2* __restrict__ Wout, float* __restrict__ Z, int useV,
@@ -363,6 +375,12 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
   extern __shared__ __align__(16) unsigned char csm[];
   __shared__ int bad;
   __shared__ __align__(8) uint64_t gbar;
+  // CTA 0: mbX[P] (pair P's columns have arrived), mbR[P] (rows p, p+1 hold
+  // pair P-1), mbC[P] (pair P's pivot block is published); CTA 2: mbY[P]
+  // (every row of pair P has arrived)
+  __shared__ __align__(8) uint64_t mbX[kMaxRank / 2], mbR[kMaxRank / 2], mbC[kMaxRank / 2],
+      mbY[kMaxRank / 2];
+  __shared__ float2 piv[4][4];                 // per pair slot: il2, il3, c3 = L_p+1,p, c3 il2
   cg::cluster_group cl = cg::this_cluster();
   const int role = (int)cl.block_rank();
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -371,13 +389,63 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
   const int RS = R | 1;
   const int T = R * (R + 1) / 2;
   const CholLayout lay(R);
+  const int npair = (R + 1) / 2;
   // CTA 1's arrays (CTA 0 writes them through the cluster window)
   float4* UV = reinterpret_cast<float4*>(csm + lay.uv);
   float2* id = reinterpret_cast<float2*>(csm + lay.id);
   float2* lsub = reinterpret_cast<float2*>(csm + lay.lsub);
   uint64_t* bars = reinterpret_cast<uint64_t*>(csm + lay.bars);   // one per pair of columns
   int* flag = reinterpret_cast<int*>(csm + lay.flag);             // [0] stop
-  const int npair = (R + 1) / 2;
+  // CTA 0's and CTA 2's arrays
+  float2* gc = reinterpret_cast<float2*>(csm + lay.gc);           // [slot][column of the pair][row]
+  float4* lc = reinterpret_cast<float4*>(csm + lay.lc);           // [set][row] (L_ip, L_i,p+1)
+  float4* lc2 = reinterpret_cast<float4*>(csm + lay.lc2);
+  auto gc_bytes = [&](int P) {
+    const int p = 2 * P;
+    return (uint32_t)(8 * (p + 1 < R ? 2 * (R - p) - 1 : R - p));
+  };
+  auto mb_init = [](uint64_t* bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)),
+                 "r"(count));
+  };
+  auto mb_expect = [](uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(bytes) : "memory");
+  };
+  auto mwait = [&](uint64_t* bar, int code) {
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    const unsigned long long t0 = clock64();
+    while (true) {
+      uint32_t done;
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+                   " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(b) : "memory");
+      if (done) return;
+      if (clock64() - t0 > 4000000000ull) {
+        atomicOr(status + 2, code);
+        bad = 1;
+        return;
+      }
+    }
+  };
+  auto marrive = [](uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"((uint32_t)__cvta_generic_to_shared(bar))
+                 : "memory");
+  };
+  if (tid == 0) bad = 0;
+  if (role == 0) {
+    for (int P = tid; P < npair; P += nt) {
+      mb_init(mbX + P, 1);
+      mb_expect(mbX + P, gc_bytes(P));
+      mb_init(mbR + P, min(2, R - 2 * P));
+      mb_init(mbC + P, 1);
+    }
+  } else if (role == 2) {
+    for (int P = tid; P < npair; P += nt) {
+      mb_init(mbY + P, 1);
+      mb_expect(mbY + P, 16u * (uint32_t)(R - 2 * P));
+    }
+    if (tid == 0) mb_init(&gbar, 1);
+  }
   if (role == 1) {
     float2* B = reinterpret_cast<float2*>(csm);
     if (tid == 0) flag[0] = 0;
@@ -390,28 +458,22 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
                    : "memory");
     }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int i = warp; i < R; i += nwarp)
       for (int j = lane; j <= i; j += 32) B[i * (i + 1) / 2 + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
-    cl.sync();                                 // CTA 1's barriers exist before CTA 0 writes
   }
-  if (role == 0) {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  cl.sync();                                   // every CTA's barriers exist before anyone sends
+  if (role == 2) {
+    // ---------------------------------------------------------- updates
     float2* G = reinterpret_cast<float2*>(csm);
     uint32_t* crd = reinterpret_cast<uint32_t*>(csm + lay.crd);
-    float4* lc = reinterpret_cast<float4*>(csm + lay.lc);  // [set][row] (L_ik, L_i,k+1)
-    const uint32_t UVr = cluster_addr(UV, 1), idr = cluster_addr(id, 1);
-    const uint32_t lsubr = cluster_addr(lsub, 1), barr = cluster_addr(bars, 1);
-    int* flagr = cl.map_shared_rank(flag, 1);
-    if (tid == 0) bad = 0;
-    const uint32_t gb = (uint32_t)__cvta_generic_to_shared(&gbar);
+    const uint32_t gcr = cluster_addr(gc, 0), mbXr = cluster_addr(mbX, 0);
     const uint32_t gbytes = (uint32_t)((T * sizeof(float2) + 15) / 16 * 16);
     if (Gpk) {
       // Gamma arrives packed (formed by the Gram kernel of the previous mode)
       if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(gb));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(gb), "r"(gbytes)
-                     : "memory");
+        const uint32_t gb = (uint32_t)__cvta_generic_to_shared(&gbar);
+        mb_expect(&gbar, gbytes);
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                      ::"r"((uint32_t)__cvta_generic_to_shared(G)), "l"(Gpk), "r"(gbytes), "r"(gb)
                      : "memory");
@@ -420,6 +482,7 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
         const int e0 = col_start(j, R);
         for (int i = j + lane; i < R; i += 32) crd[e0 + i - j] = (uint32_t)i | ((uint32_t)j << 16);
       }
+      if (tid == 0) mwait(&gbar, 4);
     }
     // Gamma from the Grams otherwise: entries in packed order, eight per
     // thread in flight; each mode's loads are issued together
@@ -457,125 +520,140 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
       for (int q = 0; q < 8; q++)
         if (gi[q] >= 0) G[base + q * nt + tid] = pk(acc[q]);
     }
-    for (int i = tid; i < R; i += nt) lc[3 * R + i] = make_float4(0.f, 0.f, 0.f, 0.f);  // no pair before 0
-    if (Gpk && tid == 0) {
-      // bounded wait for the packed Gamma
-      const unsigned long long t0 = clock64();
-      bool ok = false;
-      while (clock64() - t0 < 4000000000ull) {
-        uint32_t done;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
-                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(gb) : "memory");
-        if (done) { ok = true; break; }
-      }
-      if (!ok) {
-        atomicOr(status + 2, 4);
-        bad = 1;
-      }
-    }
-    cl.sync();                                 // CTA 1's barriers exist before this CTA writes
     __syncthreads();
-    // Two groups run as a pipeline over the column pairs P = (2P, 2P+1):
-    //   group A (threads 0..127) makes pair P (a) and stores it in set P % 3;
-    //   group B (the rest) applies pair P to the columns right of pair P+1
-    //   (b), first the two columns of pair P+2 (the only ones A needs next),
-    //   then the remainder while A is already working on later pairs.
-    // Named barriers, two of each kind so that consecutive pairs never share
-    // one: X[P % 2] (B arrives when pair P+2's columns are updated, A waits
-    // before making pair P+2), Y[P % 2] (A arrives when pair P is made, B
-    // waits before applying it); 5 orders A's first two pairs.
-    const int na = 128, nb = nt - na;
-    const bool inA = tid < na;
-    const int ut = tid - na;
+    // send G entry e (row i, column j of pair P) to CTA 0's slot of pair P
+    auto send = [&](int e, dfl g) {
+      const uint32_t ij = crd[e];
+      const int i = ij & 0xffffu, j = ij >> 16, P = j >> 1;
+      const uint32_t dst = gcr + 8u * (uint32_t)((((P & 3) * 2 + (j & 1)) * R) + i);
+      st_async8(dst, pk(g), mbXr + 8u * (uint32_t)P);
+    };
+    // pairs 0 and 1 go out as they are
+    for (int e = tid; e < col_start(min(4, R), R); e += nt) send(e, upk(G[e]));
     for (int P = 0; P < npair; P++) {
       const int p = 2 * P;
-      if (inA) {
-        if (P >= 2)
-          asm volatile("bar.sync %0, %1;" ::"r"(1 + (P & 1)), "r"(nt) : "memory");
-        else if (P == 1)
-          asm volatile("bar.sync 5, %0;" ::"r"(na) : "memory");
-        if (!bad) {
-          // (a) columns p and p+1 of L and their inverse-update coefficients,
-          // sent to CTA 1 as they are made
-          const float4* cc = lc + (P ? (P - 1) % 3 : 3) * R;
-          float4* nc = lc + (P % 3) * R;
-          const int ep = col_start(p, R);
-          const bool two = p + 1 < R;
-          const int ep1 = two ? col_start(p + 1, R) : 0;
-          const uint32_t bar = barr + 8u * (uint32_t)P;
-          const uint32_t uvp = UVr + 16u * (uint32_t)(P * R);
-          for (int i = p + tid; i < R; i += na) {
-            const float4 cp = cc[p];
-            const dfl a2 = lo2(cp), b2 = hi2(cp);
-            const dfl piv2 = df_fms2(upk(G[ep]), a2, a2, b2, b2);
-            if (bad_pivot(piv2)) {
-              bad = 1;
-              break;
-            }
-            const dfl il2 = df_rsqrt(piv2);
-            const float4 ci = cc[i];
-            const dfl l2 = df_mul(df_fms2(upk(G[ep + i - p]), lo2(ci), a2, hi2(ci), b2), il2);
-            const dfl q2 = df_mul(l2, il2);
-            dfl l3 = {0.f, 0.f}, u = q2, v = {0.f, 0.f};
-            if (i == p) st_async8(idr + 8u * p, pk(il2), bar);
-            if (two && i > p) {
-              const float4 cp1 = cc[p + 1];
-              const dfl a3 = lo2(cp1), b3 = hi2(cp1);
-              const dfl c3 = df_mul(df_fms2(upk(G[ep + 1]), a3, a2, b3, b2), il2);
-              const dfl piv3 = df_fms(df_fms2(upk(G[ep1]), a3, a3, b3, b3), c3, c3);
-              if (bad_pivot(piv3)) {
-                bad = 1;
-                break;
-              }
-              const dfl il3 = df_rsqrt(piv3);
-              l3 = df_mul(df_fms(df_fms2(upk(G[ep1 + i - p - 1]), lo2(ci), a3, hi2(ci), b3), l2, c3), il3);
-              v = df_mul(l3, il3);
-              u = df_fms(q2, v, df_mul(c3, il2));
-              if (i == p + 1) {
-                st_async8(idr + 8u * (p + 1), pk(il3), bar);
-                st_async8(lsubr + 8u * (p + 1), pk(q2), bar);
-              }
-            }
-            nc[i] = pk2(l2, l3);
-            st_async16(uvp + 16u * i, pk2(u, v), bar);
+      if (tid == 0) mwait(mbY + P, 16);
+      __syncthreads();                         // pair P is here; the previous updates are done
+      const float4* cc = lc2 + (P & 3) * R;
+      // G_ij -= L_i,p L_j,p + L_i,p+1 L_j,p+1 on [e0, e1), two entries per
+      // iteration (independent double-float chains); out sends the result
+      auto update = [&](int e0, int e1, bool out) {
+        int e = e0 + tid;
+        for (; e + nt < e1; e += 2 * nt) {
+          const uint32_t ij0 = crd[e], ij1 = crd[e + nt];
+          const float4 li0 = cc[ij0 & 0xffffu], lj0 = cc[ij0 >> 16];
+          const float4 li1 = cc[ij1 & 0xffffu], lj1 = cc[ij1 >> 16];
+          const dfl g0 = df_fms2(upk(G[e]), lo2(li0), lo2(lj0), hi2(li0), hi2(lj0));
+          const dfl g1 = df_fms2(upk(G[e + nt]), lo2(li1), lo2(lj1), hi2(li1), hi2(lj1));
+          G[e] = pk(g0);
+          G[e + nt] = pk(g1);
+          if (out) {
+            send(e, g0);
+            send(e + nt, g1);
           }
         }
-        asm volatile("bar.arrive %0, %1;" ::"r"(3 + (P & 1)), "r"(nt) : "memory");
-      } else {
-        asm volatile("bar.sync %0, %1;" ::"r"(3 + (P & 1)), "r"(nt) : "memory");
-        const float4* cc = lc + (P % 3) * R;
-        const bool work = !bad;
-        // (b) G_ij -= L_i,p L_j,p + L_i,p+1 L_j,p+1 on [e0, e1), two entries per
-        // iteration (independent double-float chains)
-        auto update = [&](int e0, int e1) {
-          int e = e0 + ut;
-          for (; e + nb < e1; e += 2 * nb) {
-            const uint32_t ij0 = crd[e], ij1 = crd[e + nb];
-            const float4 li0 = cc[ij0 & 0xffffu], lj0 = cc[ij0 >> 16];
-            const float4 li1 = cc[ij1 & 0xffffu], lj1 = cc[ij1 >> 16];
-            const dfl g0 = upk(G[e]), g1 = upk(G[e + nb]);
-            G[e] = pk(df_fms2(g0, lo2(li0), lo2(lj0), hi2(li0), hi2(lj0)));
-            G[e + nb] = pk(df_fms2(g1, lo2(li1), lo2(lj1), hi2(li1), hi2(lj1)));
-          }
-          if (e < e1) {
-            const uint32_t ij = crd[e];
-            const float4 li = cc[ij & 0xffffu], lj = cc[ij >> 16];
-            G[e] = pk(df_fms2(upk(G[e]), lo2(li), lo2(lj), hi2(li), hi2(lj)));
-          }
-        };
-        if (P + 2 < npair) {
-          if (work) update(col_start(p + 4, R), col_start(min(p + 6, R), R));
-          asm volatile("bar.arrive %0, %1;" ::"r"(1 + (P & 1)), "r"(nt) : "memory");
+        if (e < e1) {
+          const uint32_t ij = crd[e];
+          const float4 li = cc[ij & 0xffffu], lj = cc[ij >> 16];
+          const dfl g = df_fms2(upk(G[e]), lo2(li), lo2(lj), hi2(li), hi2(lj));
+          G[e] = pk(g);
+          if (out) send(e, g);
         }
-        if (work && p + 6 < R) update(col_start(p + 6, R), T);
+      };
+      if (P + 2 < npair) update(col_start(p + 4, R), col_start(min(p + 6, R), R), true);
+      if (p + 6 < R) update(col_start(p + 6, R), T, false);
+    }
+  } else if (role == 0) {
+    // ---------------------------------------------------------- chain
+    const uint32_t UVr = cluster_addr(UV, 1), idr = cluster_addr(id, 1);
+    const uint32_t lsubr = cluster_addr(lsub, 1), barr = cluster_addr(bars, 1);
+    const uint32_t lc2r = cluster_addr(lc2, 2), mbYr = cluster_addr(mbY, 2);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    if (warp == 4) {
+      // pivot warp
+      for (int P = 0; P < npair; P++) {
+        const int p = 2 * P;
+        const bool two = p + 1 < R;
+        if (P >= 1) mwait(mbR + P, 8);
+        mwait(mbX + P, 8);
+        const float2* g = gc + (P & 3) * 2 * R;
+        // lane 0: a = G_pp, lane 1: b = G_p+1,p, lane 2: d = G_p+1,p+1, each
+        // less pair P-1
+        const int r1 = p + (lane >= 1 ? 1 : 0), r2 = p + (lane == 2 ? 1 : 0);
+        const float2 gv = lane == 2 ? g[R + p + 1] : g[p + (lane == 1 ? 1 : 0)];
+        dfl x = {1.f, 0.f};
+        if (lane < (two ? 3 : 1)) {
+          const float4 u1 = P >= 1 ? lc[((P - 1) & 3) * R + r1] : z4;
+          const float4 u2 = P >= 1 ? lc[((P - 1) & 3) * R + r2] : z4;
+          x = df_fms2(upk(gv), lo2(u1), lo2(u2), hi2(u1), hi2(u2));
+        }
+        const dfl a = {__shfl_sync(0xffffffffu, x.hi, 0), __shfl_sync(0xffffffffu, x.lo, 0)};
+        const dfl bb = {__shfl_sync(0xffffffffu, x.hi, 1), __shfl_sync(0xffffffffu, x.lo, 1)};
+        const dfl d = {__shfl_sync(0xffffffffu, x.hi, 2), __shfl_sync(0xffffffffu, x.lo, 2)};
+        // lane 0: 1/sqrt(ad - b^2); lane 1: 1/sqrt(a)
+        const dfl det = two ? df_fms(df_mul(a, d), bb, bb) : dfl{1.f, 0.f};
+        const dfl rin = df_rsqrt(lane == 0 ? det : a);
+        const dfl il2 = {__shfl_sync(0xffffffffu, rin.hi, 1), __shfl_sync(0xffffffffu, rin.lo, 1)};
+        const dfl rdet = {__shfl_sync(0xffffffffu, rin.hi, 0), __shfl_sync(0xffffffffu, rin.lo, 0)};
+        if (lane == 0) {
+          if (bad_pivot(a) || bad_pivot(det)) bad = 1;
+          const dfl il3 = two ? df_mul(df_mul(rdet, a), il2) : dfl{0.f, 0.f};
+          const dfl c3 = two ? df_mul(bb, il2) : dfl{0.f, 0.f};
+          piv[P & 3][0] = pk(il2);
+          piv[P & 3][1] = pk(il3);
+          piv[P & 3][2] = pk(c3);
+          piv[P & 3][3] = pk(df_mul(c3, il2));
+          marrive(mbC + P);
+        }
+        __syncwarp();
+      }
+    } else if (tid < 128) {
+      // row threads
+      const int i = tid;
+      dfl q1a = {0.f, 0.f}, q1b = {0.f, 0.f};   // row i of pair P-1
+      for (int P = 0; P < npair && 2 * P <= i && i < R; P++) {
+        const int p = 2 * P;
+        const bool two = p + 1 < R;
+        if (P >= 1) mwait(mbR + P, 8);
+        mwait(mbX + P, 8);
+        const float2* g = gc + (P & 3) * 2 * R;
+        const float4 L1p = P >= 1 ? lc[((P - 1) & 3) * R + p] : z4;
+        const float4 L1q = (two && P >= 1) ? lc[((P - 1) & 3) * R + p + 1] : z4;
+        const dfl gi = df_fms2(upk(g[i]), q1a, lo2(L1p), q1b, hi2(L1p));
+        dfl hi = {0.f, 0.f};
+        if (two && i > p) hi = df_fms2(upk(g[R + i]), q1a, lo2(L1q), q1b, hi2(L1q));
+        mwait(mbC + P, 8);
+        const dfl il2 = upk(piv[P & 3][0]), il3 = upk(piv[P & 3][1]);
+        const dfl c3 = upk(piv[P & 3][2]), m = upk(piv[P & 3][3]);
+        const dfl l2 = df_mul(gi, il2);
+        const dfl l3 = (two && i > p) ? df_mul(df_fms(hi, l2, c3), il3) : dfl{0.f, 0.f};
+        const float4 lv = pk2(l2, l3);
+        lc[(P & 3) * R + i] = lv;
+        if (P + 1 < npair && (i == p + 2 || i == p + 3)) marrive(mbR + P + 1);
+        st_async16(lc2r + 16u * (uint32_t)((P & 3) * R + i), lv, mbYr + 8u * (uint32_t)P);
+        // inverse-update coefficients to CTA 1
+        const dfl q2 = df_mul(l2, il2);
+        const dfl v = df_mul(l3, il3);
+        const dfl u = df_fms(q2, v, m);
+        const uint32_t bar = barr + 8u * (uint32_t)P;
+        st_async16(UVr + 16u * (uint32_t)(P * R + i), pk2(u, v), bar);
+        if (i == p) st_async8(idr + 8u * p, pk(il2), bar);
+        if (two && i == p + 1) {
+          st_async8(idr + 8u * (p + 1), pk(il3), bar);
+          st_async8(lsubr + 8u * (p + 1), pk(q2), bar);
+        }
+        q1a = l2;
+        q1b = l3;
       }
     }
     __syncthreads();
     if (bad && tid == 0) {
       atomicOr(status, 1 << n);
-      st_release_cluster(flagr, 1);            // CTA 1 stops waiting
+      st_release_cluster(cl.map_shared_rank(flag, 1), 1);   // CTA 1 stops waiting
     }
   } else {
+    // ---------------------------------------------------------- inverse
     float2* B = reinterpret_cast<float2*>(csm);
     if (useV) {
       for (int idx = tid; idx < RR; idx += nt) {
@@ -696,7 +774,7 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
       }
     }
   }
-  cl.sync();                                   // CTA 0's last remote stores land before CTA 1 exits
+  cl.sync();                                   // every remote store has landed before anyone exits
 }
 
 size_t chol_inv_smem(int R) { return CholLayout(R).bytes(); }
@@ -954,8 +1032,10 @@ void chol_df(const float* Shi, const float* Slo, const float* W, const float2* G
              int R, float2* Winv, float* Z, bool useV, int* status, Launch L) {
   // 128 column threads plus about one update thread per eight packed entries
   const int T = R * (R + 1) / 2;
-  const int threads = std::min(CPALS_CHOL_THREADS, 128 + std::max(32, (T / 8 + 31) / 32 * 32));
-  chol_inv_df_kernel<<<2, threads, chol_inv_smem(R), L.stream>>>(Shi, Slo, W, Gpk, N, n, R, Winv,
+  // the chain CTA needs 128 row threads and the pivot warp; the update and
+  // inverse CTAs use about one thread per eight packed entries
+  const int threads = std::min(CPALS_CHOL_THREADS, std::max(160, (T / 8 + 31) / 32 * 32));
+  chol_inv_df_kernel<<<3, threads, chol_inv_smem(R), L.stream>>>(Shi, Slo, W, Gpk, N, n, R, Winv,
                                                                  Z, useV ? 1 : 0, status);
   (*L.counter)++;
 }
