@@ -7,24 +7,32 @@
 //   !kmajor: out[b][m][r] = sum_k X[(b*K + k)*M + m] * Bt[r][k]
 // X is bf16 (one-time copy of the input).  The B operand (a factor or a
 // Khatri-Rao product, float32) is carried as two bf16 planes, Bt = hi + lo with
-// hi = bf16(b) and lo = bf16(b - hi) (Rpad x Kstride each, zero padded): every
-// k-step issues two MMAs into the same fp32 TMEM accumulator, so the factor
-// enters with ~16 significant bits and only the one-time rounding of X
-// remains (the same for every contraction path, which keeps the PP and ALS
-// right-hand sides consistent).
+// hi = bf16(b) and lo = bf16(b - hi) (Rpad x Kstride each, zero padded).  The
+// two planes sit one after the other in shared memory and enter one MMA as a
+// B operand of 2 Rpad rows: the accumulator holds the hi products in columns
+// [0, Rpad) and the lo products in [Rpad, 2 Rpad), which the epilogue adds.
+// The factor thus enters with ~16 significant bits and only the one-time
+// rounding of X remains (the same for every contraction path, which keeps
+// the PP and ALS right-hand sides consistent).
 //
-// Persistent warp-specialised kernel, one CTA per SM:
-//   warp 0      : TMA producer (A tile 128 x 64, B tile 2 x Rpad x 64 per
-//                 stage, 128-byte swizzle, mbarrier complete_tx)
+// Persistent warp-specialised kernel, one CTA per SM.  A work unit is one or
+// two 128-row output tiles (tpu) of one K chunk; the two tiles of a unit share
+// every stage of the B operand, which halves the B traffic per byte of X and
+// doubles the X bytes in flight:
+//   warp 0      : TMA producer (tpu A tiles 128 x 64 and the B tile 2 x Rpad x
+//                 64 per stage, 128-byte swizzle, mbarrier complete_tx)
 //   warp 1      : TMEM allocation + single-thread tcgen05.mma issue (M = 128,
-//                 N = Rpad, K = 16 per instruction), tcgen05.commit to free
+//                 N = 2 Rpad, K = 16 per instruction), tcgen05.commit to free
 //                 stages and to publish finished accumulators
-//   warps 2..5  : epilogue: tcgen05.ld 32x32b into a 128-byte-swizzled shared
-//                 staging tile, then TMA tensor stores (R % 4 == 0) or
-//                 coalesced row copies (otherwise)
-// Two accumulators (2 x 128 TMEM columns) let the epilogue of one tile run
-// under the MMAs of the next.  Every wait is bounded: on timeout the kernel
-// records an error code, drains what it issued and returns.
+//   warps 2..5  : epilogue: tcgen05.ld 32x32b into 128-byte-swizzled shared
+//                 boxes of 128 rows x 32 columns (two, alternating), each
+//                 written out by one TMA tensor store (R % 4 == 0), or a
+//                 padded staging tile and coalesced row copies (otherwise)
+// Each accumulator takes 256 TMEM columns (512 in all): with one tile per
+// unit two accumulators let the epilogue of one unit run under the MMAs of
+// the next; two tiles per unit are used only when every CTA has a single
+// unit.  Every wait is bounded: on timeout the kernel records an error code,
+// drains what it issued and returns.
 #include <cuda.h>
 
 #include <algorithm>
@@ -176,8 +184,9 @@ struct UmmaParams {
   int RS;               // row stride (floats) of the padded staging tile (no TMA store)
   int nbox;             // 32-column boxes of the swizzled staging tile (TMA store)
   int tma_store;        // 1: epilogue through TMA tensor stores
+  int tpu;              // output tiles per unit (1 or 2)
   int64_t kchunk;       // multiple of BK
-  int64_t mtiles, units;
+  int64_t mtiles, mgroups, units;
   float* out;           // out or partials ([z][b][m][r])
   int* err;
 };
@@ -194,9 +203,13 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int S = p.stages;
+  const int TPU = p.tpu;
   const uint32_t b_plane = (uint32_t)p.Rpad * BK * 2;
   const uint32_t b_stage_bytes = 2 * b_plane;
-  const uint32_t stage_bytes = A_STAGE_BYTES + b_stage_bytes;
+  const uint32_t a_bytes = (uint32_t)TPU * A_STAGE_BYTES;
+  const uint32_t stage_bytes = a_bytes + b_stage_bytes;
+  const uint32_t tmem_cols = 512;
+  const int NBUF = TPU == 1 ? 2 : 1;            // accumulator sets (256 columns per tile)
 
   if (threadIdx.x == 0) {
     abort_sh = 0;
@@ -215,8 +228,8 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     if (p.tma_store) asm volatile("prefetch.tensormap [%0];" ::"l"(&mapO) : "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
-                     smem_u32(&tmem_base_sh))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)), "r"(tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -233,10 +246,12 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       int issued[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       bool ok = true;
       for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
-        const int64_t mt = u % p.mtiles;
-        const int64_t rest = u / p.mtiles;
+        const int64_t mg = u % p.mgroups;
+        const int64_t rest = u / p.mgroups;
         const int z = (int)(rest % p.splits);
         const int64_t b = rest / p.splits;
+        const int64_t mt0 = mg * TPU;
+        const int nt = (int)min((int64_t)TPU, p.mtiles - mt0);   // tiles in this unit
         const int64_t k0 = (int64_t)z * p.kchunk;
         const int64_t k1 = min(p.K, k0 + p.kchunk);
         for (int64_t k = k0; k < k1; k += BK) {
@@ -246,13 +261,17 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           }
           const uint32_t fb = smem_u32(&full_bar[stage]);
           const uint32_t sA = base + stage * stage_bytes;
-          const uint32_t sB = sA + A_STAGE_BYTES;
-          mbar_expect_tx(fb, stage_bytes);
-          if (KMAJOR) {
-            tma_load_2d(sA, &mapA, fb, (int)k, (int)(mt * BM));
-          } else {
-            tma_load_3d(sA, &mapA, fb, (int)(mt * BM), (int)k, (int)b);
-            tma_load_3d(sA + A_STAGE_BYTES / 2, &mapA, fb, (int)(mt * BM + 64), (int)k, (int)b);
+          const uint32_t sB = sA + a_bytes;
+          mbar_expect_tx(fb, (uint32_t)nt * A_STAGE_BYTES + b_stage_bytes);
+          for (int t = 0; t < nt; t++) {
+            const uint32_t sAt = sA + t * A_STAGE_BYTES;
+            const int64_t mt = mt0 + t;
+            if (KMAJOR) {
+              tma_load_2d(sAt, &mapA, fb, (int)k, (int)(mt * BM));
+            } else {
+              tma_load_3d(sAt, &mapA, fb, (int)(mt * BM), (int)k, (int)b);
+              tma_load_3d(sAt + A_STAGE_BYTES / 2, &mapA, fb, (int)(mt * BM + 64), (int)k, (int)b);
+            }
           }
           tma_load_3d(sB, &mapB, fb, (int)k, 0, 0);       // hi and lo planes
           issued[stage]++;
@@ -282,26 +301,28 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(BM, p.Rpad, !KMAJOR);
+      const uint32_t idesc = make_idesc(BM, 2 * p.Rpad, !KMAJOR);
       int stage = 0;
       uint32_t phase = 0;
       int t = 0;
       bool ok = true;
       bool any = false;
       for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x, t++) {
-        const int64_t rest = u / p.mtiles;
+        const int64_t mg = u % p.mgroups;
+        const int64_t rest = u / p.mgroups;
         const int z = (int)(rest % p.splits);
+        const int nt = (int)min((int64_t)TPU, p.mtiles - mg * TPU);
         const int64_t k0 = (int64_t)z * p.kchunk;
         const int64_t k1 = min(p.K, k0 + p.kchunk);
-        const int buf = t & 1;
-        if (!mbar_wait(smem_u32(&acce_bar[buf]), ((t >> 1) & 1) ^ 1, &abort_sh, false)) {
+        const int buf = t % NBUF;
+        if (!mbar_wait(smem_u32(&acce_bar[buf]), ((t / NBUF) & 1) ^ 1, &abort_sh, false)) {
           atomicCAS(p.err, 0, ERR_MMA_ACC);
           abort_sh = 1;
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 128);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * TPU * 256);
         uint32_t accum = 0;
         for (int64_t k = k0; k < k1; k += BK) {
           if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_sh, false)) {
@@ -312,16 +333,18 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           }
           tc_fence_after();
           const uint32_t sA = base + stage * stage_bytes;
-          const uint32_t sB = sA + A_STAGE_BYTES;
+          const uint32_t sB = sA + a_bytes;
 #pragma unroll
           for (int ks = 0; ks < BK / 16; ks++) {
-            uint64_t adesc;
-            if (KMAJOR) adesc = smem_desc(sA + ks * 32, 16, 1024);
-            else adesc = smem_desc(sA + ks * 2048, A_STAGE_BYTES / 2, 1024);
+            // hi and lo planes: one B operand of 2 Rpad rows
             const uint64_t bdesc = smem_desc(sB + ks * 32, 16, 1024);
-            const uint64_t bdesc_lo = smem_desc(sB + b_plane + ks * 32, 16, 1024);
-            umma_f16(d_tmem, adesc, bdesc, idesc, accum);
-            umma_f16(d_tmem, adesc, bdesc_lo, idesc, 1u);
+            for (int tt = 0; tt < nt; tt++) {
+              const uint32_t sAt = sA + tt * A_STAGE_BYTES;
+              uint64_t adesc;
+              if (KMAJOR) adesc = smem_desc(sAt + ks * 32, 16, 1024);
+              else adesc = smem_desc(sAt + ks * 2048, A_STAGE_BYTES / 2, 1024);
+              umma_f16(d_tmem + (uint32_t)(tt * 256), adesc, bdesc, idesc, accum);
+            }
             accum = 1;
           }
           umma_commit(smem_u32(&empty_bar[stage]));
@@ -348,14 +371,15 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     }
   } else {
     // ------------------------------------------------ epilogue (warps 2..5)
-    // TMEM -> registers -> shared staging tile -> global.
-    //  * TMA store path (R % 4 == 0): the tile is staged as nbox boxes of
-    //    128 rows x 32 floats with the 128-byte swizzle (16-byte chunk c of
-    //    row r at chunk c ^ (r % 8): conflict-free writes), then one thread
-    //    issues one tensor store per box; the tensor map's M extent clips the
-    //    rows past the end of a batch and its R extent the padding columns.
-    //  * otherwise: padded staging (row stride RS, RS/4 odd) and coalesced
-    //    row copies.
+    // TMEM -> registers -> shared staging -> global.
+    //  * TMA store path (R % 4 == 0): each 128-row x 32-column box is staged
+    //    with the 128-byte swizzle (16-byte chunk c of row r at chunk
+    //    c ^ (r % 8): conflict-free writes) in one of two alternating
+    //    buffers and written by one tensor store; the tensor map's M extent
+    //    clips the rows past the end of a batch and its R extent the padding
+    //    columns.
+    //  * otherwise: padded staging of the tile (row stride RS, RS/4 odd) and
+    //    coalesced row copies.
     uint8_t* stg_base = smem_raw + (base - smem_u32(smem_raw)) + (size_t)S * stage_bytes;
     const uint32_t stg_u32 = base + S * stage_bytes;
     float* stg = reinterpret_cast<float*>(stg_base);
@@ -364,14 +388,17 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     const int ew = warp - 2;
     const bool leader = (ew == 0 && lane == 0);
     int t = 0;
+    int bc = 0;                               // boxes stored so far (alternating buffers)
     for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x, t++) {
-      const int64_t mt = u % p.mtiles;
-      const int64_t rest = u / p.mtiles;
+      const int64_t mg = u % p.mgroups;
+      const int64_t rest = u / p.mgroups;
       const int z = (int)(rest % p.splits);
       const int64_t b = rest / p.splits;
-      const int buf = t & 1;
+      const int nt = (int)min((int64_t)TPU, p.mtiles - mg * TPU);
+      const int buf = t % NBUF;
+      const uint32_t par = (uint32_t)((t / NBUF) & 1);
       int ok = 1;
-      if (lane == 0) ok = mbar_wait(smem_u32(&accf_bar[buf]), (t >> 1) & 1, &abort_sh, true) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait(smem_u32(&accf_bar[buf]), par, &abort_sh, true) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) {
         if (lane == 0) {
@@ -381,61 +408,75 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         break;
       }
       // the phase is complete for every lane once lane 0 has seen it
-      while (!mbar_try(smem_u32(&accf_bar[buf]), (t >> 1) & 1)) {
+      while (!mbar_try(smem_u32(&accf_bar[buf]), par)) {
       }
       __syncwarp();
       tc_fence_after();
-      const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 128);
-      if (p.tma_store) {
-        for (int c = 0; c < p.Rpad; c += 16) {
-          float v[16];
-          tmem_ld16(taddr + c, v);
-          uint8_t* boxp = stg_base + (size_t)(c >> 5) * (BM * 128) + row * 128;
+      const int zb = (int)((int64_t)z * p.batch + b);
+      for (int tt = 0; tt < nt; tt++) {
+        const int64_t m0 = (mg * TPU + tt) * BM;
+        const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)((buf * TPU + tt) * 256);
+        if (p.tma_store) {
+          for (int bx = 0; bx < p.nbox; bx++, bc++) {
+            const int sb = bc & 1;
+            if (bc >= 2) {
+              // the store that last used this buffer has finished reading it
+              if (leader) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+              asm volatile("bar.sync 1, 128;" ::: "memory");
+            }
+            uint8_t* boxp = stg_base + (size_t)sb * (BM * 128) + row * 128;
 #pragma unroll
-          for (int g4 = 0; g4 < 4; g4++) {
-            const int ch = ((c & 31) >> 2) + g4;
-            *reinterpret_cast<float4*>(boxp + ((ch ^ (row & 7)) << 4)) =
-                make_float4(v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
+            for (int h = 0; h < 2; h++) {
+              const int c = bx * 32 + h * 16;
+              if (c >= p.Rpad) break;
+              float v[16], w[16];
+              tmem_ld16(taddr + c, v);
+              tmem_ld16(taddr + p.Rpad + c, w);           // lo-plane products
+#pragma unroll
+              for (int e = 0; e < 16; e++) v[e] += w[e];
+#pragma unroll
+              for (int g4 = 0; g4 < 4; g4++) {
+                const int ch = h * 4 + g4;
+                *reinterpret_cast<float4*>(boxp + ((ch ^ (row & 7)) << 4)) =
+                    make_float4(v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
+              }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (leader) {
+              tma_store_3d(&mapO, stg_u32 + sb * (BM * 128), bx * 32, (int)m0, zb);
+              asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
           }
-        }
-      } else {
-        float* srow = stg + row * p.RS;
-        for (int c = 0; c < p.Rpad; c += 16) {
-          float v[16];
-          tmem_ld16(taddr + c, v);
+        } else {
+          float* srow = stg + row * p.RS;
+          for (int c = 0; c < p.Rpad; c += 16) {
+            float v[16], w[16];
+            tmem_ld16(taddr + c, v);
+            tmem_ld16(taddr + p.Rpad + c, w);             // lo-plane products
 #pragma unroll
-          for (int g4 = 0; g4 < 4; g4++)
-            if (c + 4 * g4 < p.RS)
-              *reinterpret_cast<float4*>(srow + c + 4 * g4) =
-                  make_float4(v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
+            for (int e = 0; e < 16; e++) v[e] += w[e];
+#pragma unroll
+            for (int g4 = 0; g4 < 4; g4++)
+              if (c + 4 * g4 < p.RS)
+                *reinterpret_cast<float4*>(srow + c + 4 * g4) =
+                    make_float4(v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
+          }
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+          const int rows = (int)min((int64_t)BM, p.M - m0);
+          float* gout = p.out + (((int64_t)z * p.batch + b) * p.M + m0) * p.R;
+          for (int r2 = ew; r2 < rows; r2 += 4) {
+            const float* sr = stg + r2 * p.RS;
+            float* gr = gout + (int64_t)r2 * p.R;
+            for (int col = lane; col < p.R; col += 32) gr[col] = sr[col];
+          }
+          asm volatile("bar.sync 1, 128;" ::: "memory");
         }
       }
+      // every TMEM load of this unit has completed: the accumulators are free
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&acce_bar[buf]));   // accumulator free for the MMA warp
-      const int64_t m0 = mt * BM;
-      if (p.tma_store) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (leader) {
-          const int zb = (int)((int64_t)z * p.batch + b);
-          for (int bx = 0; bx < p.nbox; bx++)
-            tma_store_3d(&mapO, stg_u32 + bx * (BM * 128), bx * 32, (int)m0, zb);
-          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-        }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-      } else {
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        const int rows = (int)min((int64_t)BM, p.M - m0);
-        float* gout = p.out + (((int64_t)z * p.batch + b) * p.M + m0) * p.R;
-        for (int r2 = ew; r2 < rows; r2 += 4) {
-          const float* sr = stg + r2 * p.RS;
-          float* gr = gout + (int64_t)r2 * p.R;
-          for (int col = lane; col < p.R; col += 32) gr[col] = sr[col];
-        }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-      }
+      if (lane == 0) mbar_arrive(smem_u32(&acce_bar[buf]));
     }
     if (p.tma_store && leader) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
@@ -445,7 +486,8 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
   tc_fence_after();
   if (warp == 1) {
     __syncwarp();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem_base)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(tmem_cols)
                  : "memory");
   }
 }
@@ -555,15 +597,25 @@ cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, flo
   p.kchunk = cdiv(cdiv(K, splits), BK) * BK;
   p.splits = (int)cdiv(K, p.kchunk);
   p.mtiles = cdiv(M, BM);
-  p.units = p.mtiles * batch * p.splits;
   p.err = err_flag;
   p.out = p.splits > 1 ? partials : out;
-  const int stage_bytes = A_STAGE_BYTES + 2 * Rpad * BK * 2;
   int RS = (R + 3) / 4 * 4;
   if (((RS / 4) & 1) == 0) RS += 4;
   p.RS = RS;
   p.nbox = (Rpad + 31) / 32;
   p.tma_store = (R % 4 == 0) ? 1 : 0;
+  const int staging = p.tma_store ? 2 * BM * 128 : BM * RS * 4;
+  const int budget = 227 * 1024 - 2048;
+  // two tiles per unit when there are two and three stages still fit
+  auto stages_for = [&](int tpu) {
+    return std::min(8, (budget - staging) / (tpu * A_STAGE_BYTES + 2 * Rpad * BK * 2));
+  };
+  // two tiles per unit (no double buffering then) only when every CTA gets
+  // a single unit and three stages still fit
+  p.tpu = (p.mtiles >= 2 && cdiv(p.mtiles, 2) * batch * p.splits <= num_sms() && stages_for(2) >= 3) ? 2 : 1;
+  p.mgroups = cdiv(p.mtiles, p.tpu);
+  p.units = p.mgroups * batch * p.splits;
+  const int stage_bytes = p.tpu * A_STAGE_BYTES + 2 * Rpad * BK * 2;
   CUtensorMap mapO;
   memset(&mapO, 0, sizeof(mapO));
   if (p.tma_store) {
@@ -577,9 +629,7 @@ cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, flo
              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
   }
-  const int staging = p.tma_store ? p.nbox * BM * 128 : BM * RS * 4;
-  const int budget = 227 * 1024 - 2048;
-  p.stages = std::min(8, (budget - staging) / stage_bytes);
+  p.stages = stages_for(p.tpu);
   if (p.stages < 2) return cudaErrorInvalidValue;
   const size_t smem = (size_t)p.stages * stage_bytes + staging + 1024;
   const int grid = (int)std::min<int64_t>(p.units, num_sms());
