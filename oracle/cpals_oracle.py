@@ -85,6 +85,26 @@ def partial_mttkrp(X: np.ndarray, A, modes) -> np.ndarray:
     return unfold(X, modes) @ khatri_rao(others)
 
 
+def partial_row(X: np.ndarray, A, fixed) -> np.ndarray:
+    """One length-R vector of Eq. 1: M^(I)(x_I, :) for the modes I of
+    ``fixed`` (a dict mode -> index), i.e. X with those modes fixed,
+    contracted with A^(k)(x_k, r) over every other mode k.  The modes are
+    contracted one at a time (last first), so a row of a large tensor costs
+    one pass over its slice; M^(n)[y] = partial_row(X, A, {n: y}) and
+    M_p^(i,n)[x_i, x_n] = partial_row(X, A_p, {i: x_i, n: x_n})."""
+    sub = X
+    for k in sorted(fixed, reverse=True):
+        sub = np.take(sub, fixed[k], axis=k)
+    others = [A[k] for k in range(X.ndim) if k not in fixed]
+    t = np.asarray(sub, dtype=np.float64)
+    if not others:
+        raise ValueError("at least one mode must be contracted")
+    t = t @ others[-1]                                   # (..., R)
+    for a in reversed(others[:-1]):
+        t = np.einsum("...ir,ir->...r", t, a)
+    return t
+
+
 # ---------------------------------------------------------------------------
 # Normal equations (Sec. 2.3)
 # ---------------------------------------------------------------------------

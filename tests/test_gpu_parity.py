@@ -268,3 +268,29 @@ def test_normal_arith_fp64_and_double_float_agree(prec):
     with cpals.CPALS(p.dims, p.R, "fp64") as g:
         with pytest.raises(cpals.CPALSError):
             g.set_normal_arith("double_float")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("name", ["order4_120_rank64", "order6_24_rank50"])
+def test_full_size_order4_order6_sampled(name, prec):
+    """The 120^4 rank-64 and 24^6 rank-50 workloads (FP32 storage) at full
+    size: sampled MTTKRP rows of every mode (Sec. 2.5 tree) and sampled
+    entries of PP operators (Sec. 3.2.3 tree), each against the oracle's
+    row-at-a-time contraction of the same slice."""
+    p = getattr(synth, name)(seed=0)
+    N = len(p.dims)
+    tol = 1e-4 if prec == "fp32" else 1e-2
+    rng = np.random.default_rng(2)
+    with _ctx(p, prec) as g:
+        for n in range(N):
+            M = g.mttkrp(n)
+            for y in rng.choice(p.dims[n], 2, replace=False):
+                ref = O.partial_row(p.X, p.A0, {n: int(y)})
+                assert rel(M[y], ref) < tol, (n, int(y))
+        g.pp_build_operators()
+        for i, n in [(0, 1), (0, N - 1), (N - 2, N - 1)]:
+            op = g.get_operator(i, n)
+            for _ in range(2):
+                xi, xn = int(rng.integers(p.dims[i])), int(rng.integers(p.dims[n]))
+                ref = O.partial_row(p.X, p.A0, {i: xi, n: xn})
+                assert rel(op[xi, xn], ref) < tol, (i, n, xi, xn)

@@ -400,3 +400,38 @@ def test_operator_build_cost_expansion(N):
         assert rest >= 0
         assert rest <= 2 * R * math.comb(N, 2) * N * s ** (N - 2)
     assert O.table1_cp(10, N, R)["pp_init"] == 6 * 10 ** N * R
+
+
+@pytest.mark.parametrize("dims", [[5, 6, 7], [4, 3, 5, 6], [3, 4, 2, 3, 4]])
+def test_partial_row_matches_definitions(dims):
+    """The row-at-a-time contraction used for full-size samples equals the
+    unfolded definitions: MTTKRP rows (Sec. 2.3) and PP operator entries
+    (Eq. 1 with two fixed modes), against a brute-force loop as well."""
+    rng = np.random.default_rng(11)
+    R = 3
+    X = rng.standard_normal(dims)
+    A = [rng.standard_normal((d, R)) for d in dims]
+    N = len(dims)
+    for n in range(N):
+        M = O.mttkrp(X, A, n)
+        for y in range(dims[n]):
+            assert np.allclose(O.partial_row(X, A, {n: y}), M[y], rtol=1e-12, atol=1e-12)
+    for i in range(N):
+        for n in range(i + 1, N):
+            P = O.partial_mttkrp(X, A, [i, n])
+            for xi in range(dims[i]):
+                for xn in range(dims[n]):
+                    assert np.allclose(O.partial_row(X, A, {i: xi, n: xn}), P[xi, xn], rtol=1e-12, atol=1e-12)
+    # brute force for one entry
+    idx = [rng.integers(d) for d in dims]
+    fixed = {0: idx[0], N - 1: idx[-1]}
+    brute = np.zeros(R)
+    for x in np.ndindex(*dims):
+        if x[0] != idx[0] or x[-1] != idx[-1]:
+            continue
+        w = X[x]
+        prod = np.ones(R)
+        for k in range(1, N - 1):
+            prod = prod * A[k][x[k]]
+        brute += w * prod
+    assert np.allclose(O.partial_row(X, A, fixed), brute, rtol=1e-12, atol=1e-12)
