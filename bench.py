@@ -237,6 +237,38 @@ def run_ours(args):
                 "sweeps": len(out["kinds"])}
         ctx.set_normal_arith("double_float")
 
+    # PP-ALS with the learned sweep-type controller (trained by
+    # paper_1811_10573_gb300/controller.py on self-generated logs), the eps
+    # rule standing in where the network is unsure
+    learned = None
+    if not args.no_als:
+        from paper_1811_10573_gb300 import controller as ctrl
+        params = ctrl.load()
+        if params is not None:
+            ctx.set_controller(params, 0.6)
+            ts, ok, frac = [], True, []
+            for i in range(1 + min(2, args.steps)):
+                ctx.init_factors(p.A0)
+                flush.zero_()
+                torch.cuda.synchronize()
+                dist.barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                out = ctx.run_controlled(max_sweeps, p.eps, True, target)
+                e1.record()
+                torch.cuda.synchronize()
+                if i == 0:
+                    continue                        # warm-up (graph capture)
+                ts.append(dist.max(e0.elapsed_time(e1) / 1e3))
+                ok = ok and out["reached"]
+                frac.append(float(np.mean(out["learned"])) if len(out["learned"]) else 0.0)
+            kinds = out["kinds"]
+            learned = {"value": round(statistics.mean(ts), 6), "unit": "s", "reached": ok,
+                       "sweeps": len(kinds),
+                       "sweep_counts": {k: kinds.count(k) for k in ("als", "pp_init", "pp_approx")},
+                       "network_decisions": round(statistics.mean(frac), 3)}
+            ctx.set_controller(None)
+
     # end to end through the C ABI from pinned host buffers
     Xh = torch.from_numpy(np.ascontiguousarray(p.X)).pin_memory()
     e2e_times = []
@@ -296,6 +328,7 @@ def run_ours(args):
         "als_time_to_fitness_s": als_time, "als_reached": als_reached,
         "pp_vs_als_speedup": (round(als_time / value, 3) if als_time else None),
         "pp_fp64_normal_eq": ne64,
+        "pp_learned_controller": learned,
         "roofline": roofline,
         "e2e": {"value": round(statistics.mean(e2e_times), 6), "unit": "s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -175,6 +175,68 @@ cpals_status cpals_normal_solve(cpals_ctx* ctx, int n, const double* rhs, double
 /* Copy A_p^(n) (which = 0) or dA^(n) (which = 1) to a host float64 buffer. */
 cpals_status cpals_get_state(cpals_ctx* ctx, int which, int n, double* out);
 
+/* ---- learned sweep-type controller ---- */
+
+/* The paper's Algorithm 3 chooses between PP sweeps, exact ALS sweeps and an
+ * operator rebuild with one threshold test (every ||dA^(n)|| < eps
+ * ||A^(n)||); its conclusion invites other switching schemes.  These calls
+ * add a learned alternative: a two-layer perceptron with
+ * CPALS_CTRL_FEATURES inputs, 32 ReLU hidden units and 3 outputs (0: PP
+ * approximated sweep, 1: exact ALS sweep, 2: rebuild the operators, then a
+ * PP sweep).  Its input, built after every sweep, holds the per-mode log10
+ * ||dA||/||A|| (8 slots), the largest of the two previous sweeps, log10 of
+ * the last three residual decreases, sweeps since the build, whether a PP
+ * sweep is possible, the last action (one-hot), log10 eps and log10 of the
+ * residual.  Parameters: W1[32][F], b1[32], W2[3][32], b2[3] as floats,
+ * CPALS_CTRL_PARAMS in all. */
+#define CPALS_CTRL_FEATURES 20
+#define CPALS_CTRL_PARAMS (32 * CPALS_CTRL_FEATURES + 32 + 3 * 32 + 3)
+
+/* Install (params != NULL, host array of nparams = CPALS_CTRL_PARAMS floats,
+ * copied) or remove (params == NULL) the controller of a context.  A
+ * decision is taken from the network only when its largest output
+ * probability is >= confidence and the action is possible; otherwise the
+ * eps rule decides. */
+cpals_status cpals_set_controller(cpals_ctx* ctx, const float* params, int nparams, double confidence);
+
+/* Like cpals_run, with each next sweep chosen by the installed controller
+ * (the eps rule where it stands in, or everywhere when none is installed).
+ * source_trace[t] (may be NULL) is 1 where the network decided, 0 where the
+ * rule did.  The reported fitness follows cpals_run (a PP estimate after PP
+ * sweeps, confirmed exactly when it reaches the target). */
+cpals_status cpals_run_controlled(cpals_ctx* ctx, int max_sweeps, double eps, int use_V,
+                                  double target, double* fitness_trace, int* kind_trace,
+                                  double* time_trace, int* source_trace, int* n_done,
+                                  int* reached);
+
+/* Training log generated by the method itself: from the current state, for
+ * up to `steps` decisions, the context saves its state, tries each possible
+ * action from it over four sweeps (PP sweeps against ALS sweeps when the
+ * operators are valid; otherwise rebuild + PP sweep, then PP sweeps,
+ * against ALS sweeps) timing them and
+ * taking the exact fitness afterwards, restores the state, labels the
+ * decision with the action of the larger exact-fitness gain per second, and
+ * continues with that action.  Outputs (caller-owned): features
+ * [steps][CPALS_CTRL_FEATURES], labels [steps], gains and costs (seconds)
+ * [steps][3] (NaN for actions not tried or that broke down); *n_out = decisions logged.  The
+ * saved state includes the operators when a rebuild is tried (device memory
+ * of about their size is kept by the context). */
+cpals_status cpals_controller_log(cpals_ctx* ctx, int steps, double eps, int use_V, float* features,
+                                  int* labels, double* gains, double* costs, int* n_out);
+
+/* Full-batch Adam training of the controller on n logged samples (host
+ * arrays: X [n][CPALS_CTRL_FEATURES], labels y in {0,1,2}, sample weights
+ * w >= 0), minimising the weighted cross-entropy plus decay/2 ||W||^2;
+ * params (CPALS_CTRL_PARAMS floats) hold the start and receive the result;
+ * *loss_out (may be NULL) the final weighted mean loss.  Runs on the
+ * current device; allocates and frees its own device memory. */
+cpals_status cpals_mlp_train(const float* X, const int* y, const float* w, int n, float* params,
+                             int nparams, int epochs, double lr, double decay, double* loss_out);
+
+/* Controller outputs (softmax probabilities, [n][3]) for n feature vectors
+ * (host arrays); runs on the current device. */
+cpals_status cpals_mlp_forward(const float* params, int nparams, const float* X, int n, float* probs);
+
 /* ---- measurement ---- */
 
 /* enable != 0: record CUDA events around every first-level contraction on

@@ -26,6 +26,7 @@ _ctx_p = C.c_void_p
 _dp = C.POINTER(C.c_double)
 _i64p = C.POINTER(C.c_int64)
 _ip = C.POINTER(C.c_int)
+_fp = C.POINTER(C.c_float)
 
 _SIGS = {
     "cpals_create": (C.c_int, [_i64p, C.c_int, C.c_int, C.c_int, C.POINTER(_ctx_p)]),
@@ -52,6 +53,14 @@ _SIGS = {
     "cpals_get_stats": (C.c_int, [_ctx_p, C.c_int, _i64p, _dp, _dp, _dp]),
     "cpals_set_graphs": (C.c_int, [_ctx_p, C.c_int]),
     "cpals_set_normal_arith": (C.c_int, [_ctx_p, C.c_int]),
+    "cpals_set_controller": (C.c_int, [_ctx_p, _fp, C.c_int, C.c_double]),
+    "cpals_run_controlled": (C.c_int, [_ctx_p, C.c_int, C.c_double, C.c_int, C.c_double, _dp,
+                                       _ip, _dp, _ip, _ip, _ip]),
+    "cpals_controller_log": (C.c_int, [_ctx_p, C.c_int, C.c_double, C.c_int, _fp, _ip, _dp, _dp,
+                                       _ip]),
+    "cpals_mlp_train": (C.c_int, [_fp, _ip, _fp, C.c_int, _fp, C.c_int, C.c_int, C.c_double,
+                                  C.c_double, _dp]),
+    "cpals_mlp_forward": (C.c_int, [_fp, C.c_int, _fp, C.c_int, _fp]),
     "cpals_cost_model": (C.c_int, [_i64p, C.c_int, C.c_int, C.c_int, _dp]),
     "cpals_contract_bf16_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                              C.c_int64, C.c_int64, C.c_int, C.c_int64, C.c_int,
@@ -148,6 +157,62 @@ def cpals_get_dA_ratios(ctx, out):
 def cpals_run(ctx, max_sweeps, eps, use_V, target, ftrace, ktrace, ttrace, n_done, reached):
     return lib().cpals_run(ctx, max_sweeps, eps, use_V, target, ftrace, ktrace, ttrace, n_done,
                            reached)
+
+
+CTRL_FEATURES = 20
+CTRL_PARAMS = 32 * CTRL_FEATURES + 32 + 3 * 32 + 3
+CTRL_ACTIONS = ["pp", "als", "rebuild"]
+
+
+def _fptr(a):
+    return a.ctypes.data_as(_fp)
+
+
+def cpals_set_controller(ctx, params, nparams, confidence):
+    return lib().cpals_set_controller(ctx, params, nparams, confidence)
+
+
+def cpals_run_controlled(ctx, max_sweeps, eps, use_V, target, ftrace, ktrace, ttrace, strace,
+                         n_done, reached):
+    return lib().cpals_run_controlled(ctx, max_sweeps, eps, use_V, target, ftrace, ktrace, ttrace,
+                                      strace, n_done, reached)
+
+
+def cpals_controller_log(ctx, steps, eps, use_V, features, labels, gains, costs, n_out):
+    return lib().cpals_controller_log(ctx, steps, eps, use_V, features, labels, gains, costs, n_out)
+
+
+def cpals_mlp_train(X, y, w, n, params, nparams, epochs, lr, decay, loss_out):
+    return lib().cpals_mlp_train(X, y, w, n, params, nparams, epochs, lr, decay, loss_out)
+
+
+def cpals_mlp_forward(params, nparams, X, n, probs):
+    return lib().cpals_mlp_forward(params, nparams, X, n, probs)
+
+
+def mlp_train(X, y, w, params, epochs=2000, lr=1e-2, decay=1e-4):
+    """Train the controller network (cpals_mlp_train); returns (params, loss)."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    p = np.ascontiguousarray(params, dtype=np.float32).copy()
+    loss = C.c_double()
+    st = cpals_mlp_train(_fptr(X), y.ctypes.data_as(_ip), _fptr(w), len(y), _fptr(p), p.size,
+                         epochs, lr, decay, C.byref(loss))
+    if st != 0:
+        raise CPALSError(st, "cpals_mlp_train")
+    return p, loss.value
+
+
+def mlp_forward(params, X):
+    """Controller probabilities for feature rows X (cpals_mlp_forward)."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    out = np.empty((X.shape[0], 3), dtype=np.float32)
+    st = cpals_mlp_forward(_fptr(p), p.size, _fptr(X), X.shape[0], _fptr(out))
+    if st != 0:
+        raise CPALSError(st, "cpals_mlp_forward")
+    return out
 
 
 def cpals_mttkrp(ctx, n, out):
@@ -308,6 +373,42 @@ class CPALS:
         n = nd.value
         return {"fitness": ft[:n], "kinds": [SWEEP_KINDS[int(k)] for k in kt[:n]],
                 "times": tt[:n], "reached": bool(rc.value)}
+
+    def set_controller(self, params, confidence=0.6):
+        """Install the learned sweep-type controller (None removes it)."""
+        if params is None:
+            self._ck(cpals_set_controller(self.ctx, None, 0, confidence))
+            return
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._ck(cpals_set_controller(self.ctx, _fptr(p), p.size, confidence))
+
+    def run_controlled(self, max_sweeps, eps, use_V=True, target=0.0):
+        ft = np.zeros(max_sweeps)
+        kt = np.zeros(max_sweeps, dtype=np.int32)
+        tt = np.zeros(max_sweeps)
+        st = np.zeros(max_sweeps, dtype=np.int32)
+        nd, rc = C.c_int(), C.c_int()
+        self._ck(cpals_run_controlled(self.ctx, max_sweeps, eps, 1 if use_V else 0, target,
+                                      _dptr(ft), kt.ctypes.data_as(_ip), _dptr(tt),
+                                      st.ctypes.data_as(_ip), C.byref(nd), C.byref(rc)))
+        n = nd.value
+        return {"fitness": ft[:n], "kinds": [SWEEP_KINDS[int(k)] for k in kt[:n]],
+                "times": tt[:n], "learned": st[:n].astype(bool), "reached": bool(rc.value)}
+
+    def controller_log(self, steps, eps, use_V=True):
+        """Self-generated training log (cpals_controller_log)."""
+        f = np.zeros((steps, CTRL_FEATURES), dtype=np.float32)
+        lab = np.zeros(steps, dtype=np.int32)
+        g = np.zeros((steps, 3))
+        c = np.zeros((steps, 3))
+        n = C.c_int()
+        st = cpals_controller_log(self.ctx, steps, eps, 1 if use_V else 0, _fptr(f),
+                                  lab.ctypes.data_as(_ip), _dptr(g), _dptr(c), C.byref(n))
+        if st not in (0, 5):          # a singular Gamma ends the log early; the rest stands
+            self._ck(st)
+        k = n.value
+        return {"features": f[:k], "labels": lab[:k], "gains": g[:k], "costs": c[:k],
+                "status": STATUS.get(st, st)}
 
     def mttkrp(self, n):
         out = np.empty((self.dims[n], self.R))

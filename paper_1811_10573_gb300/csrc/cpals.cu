@@ -111,6 +111,16 @@ struct cpals_ctx {
   int64_t fl_launches = 0;
   double fl_ms = 0, fl_bytes = 0, fl_flops = 0;
   int* umma_err = nullptr;
+  // learned controller
+  float* ctrl_params = nullptr;    // device, ctrl_param_count(kCtrlFeatures) floats
+  float* ctrl_io = nullptr;        // device: features (kCtrlFeatures) then probabilities
+  float* ctrl_io_h = nullptr;      // pinned host mirror
+  double ctrl_conf = 0.6;
+  bool ctrl_on = false;
+  // snapshot of the sweep state (controller logs)
+  std::vector<void*> snap_bufs;
+  bool snap_ops = false;
+  bool snap_built = false, snap_factors = false;
 
   Launch L() { return Launch{stream, &launches}; }
   Launch Lside() { return Launch{side, &launches}; }
@@ -637,6 +647,150 @@ bool all_small(const cpals_ctx* c, double eps) {
   return true;
 }
 
+// ---------------------------------------------------------------- snapshot
+// The state a sweep reads and writes: factors (float64 masters, compute and
+// double-float copies), A_p, dA, Grams, W, the next mode's packed Gamma and
+// the device scalars; with ops also the PP operators and M_p (a rebuild
+// overwrites them).  Buffers are allocated on first use and kept.
+struct Region {
+  void* p;
+  size_t bytes;
+};
+std::vector<Region> state_regions(cpals_ctx* c, bool ops) {
+  std::vector<Region> r;
+  const int N = c->N, R = c->R;
+  for (int n = 0; n < N; n++) {
+    const size_t sR = (size_t)c->dims[n] * R;
+    r.push_back({c->A[n], sR * 8});
+    r.push_back({c->Ap[n], sR * 8});
+    r.push_back({c->dA[n], sR * 8});
+    r.push_back({c->Ac[n], sR * c->esz});
+    r.push_back({c->dAc[n], sR * c->esz});
+    if (c->dfm || c->Alo[n]) {
+      if (c->Alo[n]) r.push_back({c->Alo[n], sR * 4});
+      if (c->Aphi[n]) r.push_back({c->Aphi[n], sR * 4});
+      if (c->Aplo[n]) r.push_back({c->Aplo[n], sR * 4});
+    }
+  }
+  r.push_back({c->S, (size_t)N * R * R * 8});
+  r.push_back({c->W, (size_t)N * R * R * 8});
+  if (c->Shi) r.push_back({c->Shi, (size_t)N * R * R * 4});
+  if (c->Slo) r.push_back({c->Slo, (size_t)N * R * R * 4});
+  if (c->Wf) r.push_back({c->Wf, (size_t)N * R * R * 4});
+  if (c->Gpk) r.push_back({c->Gpk, (size_t)R * (R + 1) / 2 * 8});
+  r.push_back({c->scal, 32 * 8});
+  if (ops && c->pp_alloc) {
+    for (int i = 0; i < N; i++)
+      for (int n = i + 1; n < N; n++) r.push_back({c->ops[i][n], (size_t)c->dims[i] * c->dims[n] * R * c->esz});
+    for (int n = 0; n < N; n++) r.push_back({c->Mp[n], (size_t)c->dims[n] * R * c->esz});
+  }
+  return r;
+}
+
+cpals_status snapshot_take(cpals_ctx* c, bool ops) {
+  const std::vector<Region> reg = state_regions(c, ops);
+  while (c->snap_bufs.size() < reg.size()) c->snap_bufs.push_back(nullptr);
+  for (size_t i = 0; i < reg.size(); i++) {
+    if (!c->snap_bufs[i]) CKS(dalloc(c, &c->snap_bufs[i], reg[i].bytes));
+    CK(cudaMemcpyAsync(c->snap_bufs[i], reg[i].p, reg[i].bytes, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  c->snap_ops = ops && c->pp_alloc;
+  c->snap_built = c->ops_built;
+  c->snap_factors = c->have_factors;
+  return CPALS_OK;
+}
+
+cpals_status snapshot_restore(cpals_ctx* c) {
+  const std::vector<Region> reg = state_regions(c, c->snap_ops);
+  for (size_t i = 0; i < reg.size() && i < c->snap_bufs.size(); i++)
+    CK(cudaMemcpyAsync(reg[i].p, c->snap_bufs[i], reg[i].bytes, cudaMemcpyDeviceToDevice, c->stream));
+  c->ops_built = c->snap_built;
+  c->have_factors = c->snap_factors;
+  return CPALS_OK;
+}
+
+// ---------------------------------------------------------------- controller features
+enum { ACT_PP = 0, ACT_ALS = 1, ACT_REBUILD = 2 };
+constexpr int kCtrlHorizon = 4;   // sweeps per trial in the controller log
+
+struct CtrlHist {
+  double maxlr[2] = {0, 0};        // largest log10 dA ratio of the last two sweeps
+  double res[4] = {-1, -1, -1, -1}; // residual 1 - f of the last four sweeps (newest first; -1: none)
+  int since_build = 0;
+  bool pp_ready = false;           // operators built and only PP sweeps since
+  int last = -1;
+  void push(cpals_ctx* c, int action, double fitness) {
+    double m = -12;
+    for (int n = 0; n < c->N; n++) {
+      const double d = std::sqrt(c->scal_h[8 + 2 * n]), a = std::sqrt(c->scal_h[9 + 2 * n]);
+      m = std::max(m, std::log10(std::max(d / std::max(a, 1e-300), 1e-12)));
+    }
+    maxlr[1] = maxlr[0];
+    maxlr[0] = m;
+    for (int k = 3; k > 0; k--) res[k] = res[k - 1];
+    res[0] = 1.0 - fitness;
+    last = action;
+    if (action == ACT_ALS) {
+      pp_ready = false;
+      since_build = 0;
+    } else if (action == ACT_REBUILD) {
+      pp_ready = true;
+      since_build = 1;
+    } else {
+      since_build++;
+    }
+  }
+};
+
+// The controller's input (kCtrlFeatures values, all O(1)): the per-mode log10
+// ||dA||/||A|| (padded to 8 modes), the largest one of the two previous
+// sweeps, log10 of the last three residual decreases, sweeps since the
+// operators were built, whether a PP sweep is possible, the last action
+// (one-hot), log10 eps and log10 of the current residual.
+void ctrl_features(cpals_ctx* c, const CtrlHist& h, double eps, float* x) {
+  for (int i = 0; i < kCtrlFeatures; i++) x[i] = 0.f;
+  for (int n = 0; n < c->N && n < 8; n++) {
+    const double d = std::sqrt(c->scal_h[8 + 2 * n]), a = std::sqrt(c->scal_h[9 + 2 * n]);
+    const double lr = std::log10(std::max(d / std::max(a, 1e-300), 1e-12));
+    x[n] = (float)(std::min(std::max(lr, -12.0), 2.0) / 4.0);
+  }
+  x[8] = (float)(h.maxlr[0] / 4.0);
+  x[9] = (float)(h.maxlr[1] / 4.0);
+  for (int k = 0; k < 3; k++) {
+    const bool have = h.res[k] >= 0 && h.res[k + 1] >= 0;
+    const double dec = have ? std::max(h.res[k + 1] - h.res[k], 1e-16) : 1e-16;
+    x[10 + k] = (float)(std::log10(dec) / 8.0);
+  }
+  x[13] = (float)(h.pp_ready ? std::min(h.since_build, 20) / 10.0 : 0.0);
+  x[14] = h.pp_ready ? 1.f : 0.f;
+  if (h.last >= 0) x[15 + h.last] = 1.f;
+  x[18] = (float)(std::log10(std::max(eps, 1e-12)) / 2.0);
+  x[19] = (float)(std::log10(std::max(h.res[0] >= 0 ? h.res[0] : 1.0, 1e-16)) / 8.0);
+}
+
+// one sweep of the given kind; leaves the scalars read back
+cpals_status do_action(cpals_ctx* c, int a, bool useV) {
+  if (a == ACT_REBUILD) {
+    CKS(do_build(c));
+    c->ops_built = true;
+    CKS(do_pp(c, useV));
+  } else if (a == ACT_PP) {
+    CKS(do_pp(c, useV));
+  } else {
+    CKS(do_als(c));
+  }
+  CKS(sync_read(c));
+  return check_status(c);
+}
+
+// exact fitness of the current factors (Sec. 5)
+cpals_status exact_fitness(cpals_ctx* c, double* f) {
+  CKS(do_fit(c));
+  CKS(sync_read(c));
+  *f = c->scal_h[0];
+  return CPALS_OK;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -787,6 +941,9 @@ void cpals_destroy(cpals_ctx* c) {
   F(c->S); F(c->W); F(c->Lf); F(c->Z); F(c->ML); F(c->MR); F(c->krp); F(c->tmp[0]); F(c->tmp[1]);
   F(c->rhs); F(c->rhs2); F(c->gpart); F(c->Bt); F(c->rownorm); F(c->dpart); F(c->scal);
   F(c->status); F(c->tickets); F(c->dscr[0]); F(c->dscr[1]);
+  F(c->ctrl_params); F(c->ctrl_io);
+  if (c->ctrl_io_h) cudaFreeHost(c->ctrl_io_h);
+  for (void* p : c->snap_bufs) F(p);
   if (c->scal_h) cudaFreeHost(c->scal_h);
   if (c->status_h) cudaFreeHost(c->status_h);
   for (int i = 0; i < kEvPairs; i++) {
@@ -1009,6 +1166,237 @@ cpals_status cpals_run(cpals_ctx* c, int max_sweeps, double eps, int use_V, doub
   if (n_done) *n_done = t;
   if (reached) *reached = hit;
   return st;
+}
+
+cpals_status cpals_set_controller(cpals_ctx* c, const float* params, int nparams, double confidence) {
+  if (!c) return CPALS_E_INVALID;
+  if (!params) {
+    c->ctrl_on = false;
+    return CPALS_OK;
+  }
+  if (nparams != ctrl_param_count(kCtrlFeatures) || !(confidence >= 0.0 && confidence <= 1.0))
+    return c->fail(CPALS_E_INVALID, "controller: need " + std::to_string(ctrl_param_count(kCtrlFeatures)) +
+                                        " parameters and 0 <= confidence <= 1");
+  if (!c->ctrl_params) CKS(dalloc(c, (void**)&c->ctrl_params, (size_t)nparams * 4));
+  if (!c->ctrl_io) CKS(dalloc(c, (void**)&c->ctrl_io, 64 * 4));
+  if (!c->ctrl_io_h) CK(cudaMallocHost(&c->ctrl_io_h, 64 * 4));
+  CK(cudaMemcpyAsync(c->ctrl_params, params, (size_t)nparams * 4, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->ctrl_conf = confidence;
+  c->ctrl_on = true;
+  return CPALS_OK;
+}
+
+cpals_status cpals_run_controlled(cpals_ctx* c, int max_sweeps, double eps, int use_V, double target,
+                                  double* fitness_trace, int* kind_trace, double* time_trace,
+                                  int* source_trace, int* n_done, int* reached) {
+  CKS(ready(c));
+  if (max_sweeps < 0 || !(eps > 0)) return c->fail(CPALS_E_INVALID, "max_sweeps < 0 or eps <= 0");
+  Join j(c);
+  const auto t0 = std::chrono::steady_clock::now();
+  CtrlHist h;
+  int t = 0, hit = 0;
+  cpals_status st = sync_read(c);
+  // the current state: after cpals_init_factors dA = A, so the first sweep is exact
+  h.res[0] = 1.0 - c->scal_h[0];
+  while (st == CPALS_OK && t < max_sweeps && !hit) {
+    // the paper's eps rule (Algorithm 3): stay in / enter the PP phase while
+    // every ||dA|| < eps ||A||
+    const bool small = all_small(c, eps);
+    const int rule = h.pp_ready ? (small ? ACT_PP : ACT_ALS) : (small ? ACT_REBUILD : ACT_ALS);
+    int act = rule, src = 0;
+    if (c->ctrl_on) {
+      ctrl_features(c, h, eps, c->ctrl_io_h);
+      CK(cudaMemcpyAsync(c->ctrl_io, c->ctrl_io_h, kCtrlFeatures * 4, cudaMemcpyHostToDevice, c->stream));
+      mlp_forward(c->ctrl_params, kCtrlFeatures, c->ctrl_io, 1, c->ctrl_io + 32, c->L());
+      CK(cudaMemcpyAsync(c->ctrl_io_h + 32, c->ctrl_io + 32, kCtrlClasses * 4, cudaMemcpyDeviceToHost,
+                         c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      const float* pr = c->ctrl_io_h + 32;
+      int best = 0;
+      for (int k = 1; k < kCtrlClasses; k++)
+        if (pr[k] > pr[best]) best = k;
+      // the rule stands in when the network is unsure or asks for a PP sweep
+      // without valid operators
+      if (pr[best] >= c->ctrl_conf && !(best == ACT_PP && !h.pp_ready)) {
+        act = best;
+        src = 1;
+      }
+    }
+    st = do_action(c, act, use_V != 0);
+    if (st != CPALS_OK) break;
+    double f = c->scal_h[0];
+    if (act != ACT_ALS && target > 0 && f >= target) {
+      // a PP estimate reached the target: confirm with the exact fitness (Sec. 5)
+      st = exact_fitness(c, &f);
+      if (st != CPALS_OK) break;
+    }
+    if (target > 0 && f >= target) hit = 1;
+    h.push(c, act, f);
+    if (fitness_trace) fitness_trace[t] = f;
+    if (kind_trace)
+      kind_trace[t] = act == ACT_ALS ? CPALS_SWEEP_ALS : act == ACT_REBUILD ? CPALS_SWEEP_PP_INIT : CPALS_SWEEP_PP_APPROX;
+    if (time_trace)
+      time_trace[t] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (source_trace) source_trace[t] = src;
+    t++;
+  }
+  if (n_done) *n_done = t;
+  if (reached) *reached = hit;
+  return st;
+}
+
+cpals_status cpals_controller_log(cpals_ctx* c, int steps, double eps, int use_V, float* features,
+                                  int* labels, double* gains, double* costs, int* n_out) {
+  CKS(ready(c));
+  if (steps < 0 || !(eps > 0) || !features || !labels || !gains || !costs || !n_out)
+    return c->fail(CPALS_E_INVALID, "bad argument");
+  Join j(c);
+  CtrlHist h;
+  cpals_status st = sync_read(c);
+  h.res[0] = 1.0 - c->scal_h[0];
+  int t = 0;
+  auto now = [] { return std::chrono::steady_clock::now(); };
+  while (st == CPALS_OK && t < steps) {
+    double f0 = 0;
+    st = exact_fitness(c, &f0);
+    if (st != CPALS_OK) break;
+    ctrl_features(c, h, eps, features + (size_t)t * kCtrlFeatures);
+    // candidates over kCtrlHorizon sweeps: PP sweeps against ALS sweeps when
+    // a PP sweep is possible, else rebuild + PP sweep then PP sweeps against
+    // ALS sweeps (a horizon of several sweeps lifts the gains above the
+    // rounding of the fitness)
+    const int cand[2] = {h.pp_ready ? ACT_PP : ACT_REBUILD, ACT_ALS};
+    const int depth = kCtrlHorizon;
+    double rate[3] = {-1e300, -1e300, -1e300};
+    for (int k = 0; k < 3; k++) {
+      gains[(size_t)t * 3 + k] = std::nan("");
+      costs[(size_t)t * 3 + k] = std::nan("");
+    }
+    st = snapshot_take(c, cand[0] == ACT_REBUILD);
+    for (int k = 0; k < 2 && st == CPALS_OK; k++) {
+      if (k > 0) st = snapshot_restore(c);
+      if (st != CPALS_OK) break;
+      CK(cudaStreamSynchronize(c->stream));
+      const auto ta = now();
+      for (int d = 0; d < depth && st == CPALS_OK; d++)
+        st = do_action(c, d == 0 ? cand[k] : (cand[k] == ACT_ALS ? ACT_ALS : ACT_PP), use_V != 0);
+      const double dt = std::chrono::duration<double>(now() - ta).count();
+      if (st == CPALS_E_SINGULAR) {
+        // a trial that breaks down (Gamma not positive definite) loses
+        st = CPALS_OK;
+        continue;
+      }
+      double f = 0;
+      if (st == CPALS_OK) st = exact_fitness(c, &f);
+      if (st != CPALS_OK) break;
+      gains[(size_t)t * 3 + cand[k]] = f - f0;
+      costs[(size_t)t * 3 + cand[k]] = dt;
+      rate[cand[k]] = (f - f0) / std::max(dt, 1e-9);
+    }
+    if (st != CPALS_OK) break;
+    // label: the larger fitness gain per second (ties and breakdowns of the
+    // PP candidate to the exact sweep)
+    const int label = rate[cand[0]] > rate[ACT_ALS] && gains[(size_t)t * 3 + cand[0]] > 0 ? cand[0] : ACT_ALS;
+    labels[t] = label;
+    // continue the trajectory with the labelled action
+    st = snapshot_restore(c);
+    if (st == CPALS_OK) st = do_action(c, label, use_V != 0);
+    if (st != CPALS_OK) break;
+    h.push(c, label, c->scal_h[0]);
+    t++;
+  }
+  *n_out = t;
+  return st;
+}
+
+cpals_status cpals_mlp_forward(const float* params, int nparams, const float* X, int n, float* probs) {
+  if (!params || !X || !probs || n < 0 || nparams != ctrl_param_count(kCtrlFeatures)) return CPALS_E_INVALID;
+  if (n == 0) return CPALS_OK;
+  float *dp = nullptr, *dx = nullptr, *dpr = nullptr;
+  int64_t cnt = 0;
+  auto done = [&](cpals_status s) {
+    cudaFree(dp);
+    cudaFree(dx);
+    cudaFree(dpr);
+    return s;
+  };
+  if (cudaMalloc(&dp, (size_t)nparams * 4) != cudaSuccess || cudaMalloc(&dx, (size_t)n * kCtrlFeatures * 4) != cudaSuccess ||
+      cudaMalloc(&dpr, (size_t)n * kCtrlClasses * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return done(CPALS_E_OOM);
+  }
+  if (cudaMemcpy(dp, params, (size_t)nparams * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dx, X, (size_t)n * kCtrlFeatures * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return done(CPALS_E_CUDA);
+  mlp_forward(dp, kCtrlFeatures, dx, n, dpr, Launch{0, &cnt});
+  if (cudaMemcpy(probs, dpr, (size_t)n * kCtrlClasses * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return done(CPALS_E_CUDA);
+  return done(CPALS_OK);
+}
+
+cpals_status cpals_mlp_train(const float* X, const int* y, const float* w, int n, float* params,
+                             int nparams, int epochs, double lr, double decay, double* loss_out) {
+  if (!X || !y || !w || !params || n < 1 || epochs < 0 || nparams != ctrl_param_count(kCtrlFeatures) ||
+      !(lr > 0))
+    return CPALS_E_INVALID;
+  for (int i = 0; i < n; i++)
+    if (y[i] < 0 || y[i] >= kCtrlClasses || !(w[i] >= 0)) return CPALS_E_INVALID;
+  double wsum = 0;
+  for (int i = 0; i < n; i++) wsum += w[i];
+  if (!(wsum > 0)) return CPALS_E_INVALID;
+  const int F = kCtrlFeatures;
+  std::vector<void*> bufs;
+  auto al = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    bufs.push_back(p);
+    return p;
+  };
+  auto done = [&](cpals_status s) {
+    for (void* p : bufs) cudaFree(p);
+    return s;
+  };
+  float* dp = (float*)al((size_t)nparams * 4);
+  float* dm = (float*)al((size_t)nparams * 4);
+  float* dv = (float*)al((size_t)nparams * 4);
+  float* dx = (float*)al((size_t)n * F * 4);
+  int* dy = (int*)al((size_t)n * 4);
+  float* dw = (float*)al((size_t)n * 4);
+  float* hs = (float*)al((size_t)n * kCtrlHidden * 4);
+  float* dz = (float*)al((size_t)n * kCtrlClasses * 4);
+  float* dh = (float*)al((size_t)n * kCtrlHidden * 4);
+  float* dl = (float*)al((size_t)n * 4);
+  if (!dp || !dm || !dv || !dx || !dy || !dw || !hs || !dz || !dh || !dl) return done(CPALS_E_OOM);
+  if (cudaMemcpy(dp, params, (size_t)nparams * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dx, X, (size_t)n * F * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dy, y, (size_t)n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dw, w, (size_t)n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(dm, 0, (size_t)nparams * 4) != cudaSuccess || cudaMemset(dv, 0, (size_t)nparams * 4) != cudaSuccess)
+    return done(CPALS_E_CUDA);
+  int64_t cnt = 0;
+  for (int e = 1; e <= epochs; e++)
+    mlp_train_epoch(dp, dm, dv, F, dx, dy, dw, n, (float)(1.0 / wsum), (float)lr, (float)decay, e, hs, dz,
+                    dh, dl, Launch{0, &cnt});
+  if (cudaMemcpy(params, dp, (size_t)nparams * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return done(CPALS_E_CUDA);
+  if (loss_out) {
+    // loss of the final parameters: one more forward/backward pass
+    if (epochs > 0) {
+      mlp_train_epoch(dp, dm, dv, F, dx, dy, dw, n, 0.f, 0.f, 0.f, epochs + 1, hs, dz, dh, dl, Launch{0, &cnt});
+    } else {
+      mlp_train_epoch(dp, dm, dv, F, dx, dy, dw, n, 0.f, 0.f, 0.f, 1, hs, dz, dh, dl, Launch{0, &cnt});
+    }
+    std::vector<float> hl(n);
+    if (cudaMemcpy(hl.data(), dl, (size_t)n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return done(CPALS_E_CUDA);
+    double sl = 0;
+    for (int i = 0; i < n; i++) sl += hl[i];
+    *loss_out = sl / wsum;
+  }
+  if (cudaGetLastError() != cudaSuccess) return done(CPALS_E_CUDA);
+  return done(CPALS_OK);
 }
 
 cpals_status cpals_mttkrp(cpals_ctx* c, int n, double* out) {

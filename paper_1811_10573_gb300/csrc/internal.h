@@ -128,6 +128,18 @@ void solve_df(const float* rhs, double* A, float* Ahi, float* Alo, const float* 
               const float* Areflo, double* dA, float* dAc, const float2* Winv, const float* Z,
               float2* rownorm, int s, int R, int n, const int* status, Launch L);
 
+// ---------------------------------------------------------------- learned controller
+// two-layer perceptron: kCtrlFeatures inputs, kCtrlHidden ReLU units,
+// kCtrlClasses outputs (PP sweep, ALS sweep, rebuild + PP sweep)
+constexpr int kCtrlFeatures = 20;
+constexpr int kCtrlHidden = 32;
+constexpr int kCtrlClasses = 3;
+int ctrl_param_count(int F);
+void mlp_forward(const float* params, int F, const float* X, int n, float* probs, Launch L);
+void mlp_train_epoch(float* params, float* m, float* v, int F, const float* X, const int* y,
+                     const float* w, int n, float inv_w, float lr, float decay, int t, float* hs,
+                     float* dz, float* dh, float* loss, Launch L);
+
 // ---------------------------------------------------------------- tcgen05 (sm_103a)
 // bf16 tensor-core first-level contraction, fp32 accumulate in TMEM, TMA-fed:
 //   kmajor:  out[m][r]    = sum_k Xb[m*K + k]         * Bt[r][k]
