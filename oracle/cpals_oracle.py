@@ -224,35 +224,77 @@ def fitness_explicit(X: np.ndarray, A) -> float:
 # ---------------------------------------------------------------------------
 
 
-def als_sweep(X: np.ndarray, A, S, info: SolveInfo | None = None):
+def _lam(lam, n: int) -> float:
+    """Step size of mode n: None means 1 (plain ALS), a scalar applies to
+    every mode, a sequence gives one value per mode."""
+    if lam is None:
+        return 1.0
+    if np.ndim(lam) == 0:
+        return float(lam)
+    return float(lam[n])
+
+
+def step(A_old: np.ndarray, A_ls: np.ndarray, lam: float) -> np.ndarray:
+    """ALS variant with an update step size (Sec. 5.3, chemistry tensor):
+    A_new = (1 - lambda) A^(n) + lambda M^(n) Gamma^(n)+, where A_ls is the
+    least-squares update M^(n) Gamma^(n)+ and A_old the current factor."""
+    if lam == 1.0:
+        return A_ls
+    return (1.0 - lam) * A_old + lam * A_ls
+
+
+def _tie_copy(A, S, dA, n: int, tie):
+    """Symmetry constraint (Sec. 5.3, X = [[A, B, B]]): every mode tied to
+    mode n takes mode n's new factor, Gram and change."""
+    if not tie:
+        return
+    for m2, m1 in tie.items():
+        if m1 == n:
+            A[m2] = A[n].copy()
+            S[m2] = S[n].copy()
+            dA[m2] = dA[n].copy()
+
+
+def als_sweep(X: np.ndarray, A, S, info: SolveInfo | None = None, lam=None, tie=None):
     """One sweep of Algorithm 1 (lines 4-11), Gauss-Seidel over the modes.
 
     ``A`` and ``S`` are lists updated in place.  Returns (dA, gnorm) where
     dA[n] = A^(n)_new - A^(n)_old (the per-sweep change used by Algorithm 3's
     regular sweep) and gnorm[n] = ||G^(n)||_F.
+
+    Variants of Sec. 5.3: ``lam`` is the update step size (see ``step``);
+    ``tie`` maps a mode m2 to a mode m1 < m2 whose factor it shares (the
+    symmetric decomposition [[A, B, B]] is tie = {2: 1}): mode m2 is not
+    solved for, it takes mode m1's factor as soon as that is updated.
     """
     N = X.ndim
     dA = [None] * N
     gnorm = [0.0] * N
     for n in range(N):
+        if tie and n in tie:
+            continue
         G = gamma(S, n)
         M = mttkrp(X, A, n)
-        Anew = solve_normal(M, G, info)
+        Anew = step(A[n], solve_normal(M, G, info), _lam(lam, n))
         dA[n] = Anew - A[n]
         gnorm[n] = float(np.linalg.norm((A[n] - Anew) @ G))
         A[n] = Anew
         S[n] = gram(Anew)
+        _tie_copy(A, S, dA, n, tie)
     return dA, gnorm
 
 
-def cp_als(X: np.ndarray, A0, n_sweeps: int):
-    """Algorithm 1 for a fixed number of sweeps; returns (A, fitness trace)."""
+def cp_als(X: np.ndarray, A0, n_sweeps: int, lam=None, tie=None):
+    """Algorithm 1 for a fixed number of sweeps; returns (A, fitness trace).
+    ``lam`` and ``tie`` select the variants of Sec. 5.3 (see ``als_sweep``)."""
     A = [a.copy() for a in A0]
+    for m2, m1 in (tie or {}).items():
+        A[m2] = A[m1].copy()              # tied factors start equal
     S = [gram(a) for a in A]
     normX = float(np.linalg.norm(X))
     trace = []
     for _ in range(n_sweeps):
-        als_sweep(X, A, S)
+        als_sweep(X, A, S, lam=lam, tie=tie)
         trace.append(fitness(X, A, normX))
     return A, trace
 
@@ -324,18 +366,25 @@ def pp_mttkrp(ops, Mp, A, dA, n: int, use_V: bool = True) -> np.ndarray:
     return out
 
 
-def pp_sweep(ops, Mp, A, Ap, dA, S, use_V: bool = True, info: SolveInfo | None = None):
-    """One PP approximated sweep (Algorithm 3, lines 10-17); lists updated in place."""
+def pp_sweep(ops, Mp, A, Ap, dA, S, use_V: bool = True, info: SolveInfo | None = None,
+             lam=None, tie=None):
+    """One PP approximated sweep (Algorithm 3, lines 10-17); lists updated in
+    place.  ``lam`` and ``tie`` as in ``als_sweep``: the step size blends the
+    current factor with the solution of the approximated normal equations, and
+    a tied mode takes its partner's factor, Gram and dA = A - A_p."""
     N = len(A)
     gnorm = [0.0] * N
     for n in range(N):
+        if tie and n in tie:
+            continue
         G = gamma(S, n)
         Mt = pp_mttkrp(ops, Mp, A, dA, n, use_V)
-        Anew = solve_normal(Mt, G, info)
+        Anew = step(A[n], solve_normal(Mt, G, info), _lam(lam, n))
         gnorm[n] = float(np.linalg.norm((A[n] - Anew) @ G))
         A[n] = Anew
         S[n] = gram(Anew)
         dA[n] = Anew - Ap[n]
+        _tie_copy(A, S, dA, n, tie)
     return gnorm
 
 
@@ -354,7 +403,7 @@ def _small(dA, A, eps: float) -> bool:
 
 
 def pp_cp_als(X: np.ndarray, A0, n_sweeps: int, eps: float, use_V: bool = True,
-              on_sweep=None):
+              on_sweep=None, lam=None, tie=None):
     """Algorithm 3 (PP-CP-ALS) for a budget of ``n_sweeps`` sweeps.
 
     Readings where the paper leaves room: the eps test is taken at the head
@@ -363,8 +412,12 @@ def pp_cp_als(X: np.ndarray, A0, n_sweeps: int, eps: float, use_V: bool = True,
     sweep and a regular ALS sweep each count as one sweep; the reported
     fitness is always the exact one; the gradient stopping test is not used
     (fixed budgets).  ``on_sweep(kind, A)`` is called after every sweep.
+    ``lam`` and ``tie`` select the ALS variants of Sec. 5.3 for both sweep
+    kinds (see ``als_sweep``).
     """
     A = [a.copy() for a in A0]
+    for m2, m1 in (tie or {}).items():
+        A[m2] = A[m1].copy()              # tied factors start equal
     N = len(A)
     S = [gram(a) for a in A]
     dA = [a.copy() for a in A]            # Algorithm 3 line 2: dA <- A
@@ -387,13 +440,13 @@ def pp_cp_als(X: np.ndarray, A0, n_sweeps: int, eps: float, use_V: bool = True,
             dA = [np.zeros_like(a) for a in A]
             first = True
             while t < n_sweeps and _small(dA, A, eps):
-                pp_sweep(ops, Mp, A, Ap, dA, S, use_V, info)
+                pp_sweep(ops, Mp, A, Ap, dA, S, use_V, info, lam=lam, tie=tie)
                 t += 1
                 log("pp_init" if first else "pp_approx")
                 first = False
             if t >= n_sweeps:
                 break
-        dA, _ = als_sweep(X, A, S, info)
+        dA, _ = als_sweep(X, A, S, info, lam=lam, tie=tie)
         t += 1
         log("als")
     tr.singular = int(info.singular)

@@ -435,3 +435,99 @@ def test_partial_row_matches_definitions(dims):
             prod = prod * A[k][x[k]]
         brute += w * prod
     assert np.allclose(O.partial_row(X, A, fixed), brute, rtol=1e-12, atol=1e-12)
+
+
+# --- Sec. 5.3 ALS variants: update step size and the symmetry constraint -------
+
+def _residual_sq(X, A):
+    return float(np.sum((X - O.reconstruct(A)) ** 2))
+
+
+@pytest.mark.parametrize("lam", [0.3, 0.7, 1.4])
+def test_step_size_residual_is_quadratic_in_lambda(lam):
+    """With the other factors fixed the residual is a convex quadratic in
+    A^(n) whose minimiser is the least-squares update, so along
+    A + lam (A_ls - A): r(lam) - r(1) = (1 - lam)^2 (r(0) - r(1)).  Only mode 0
+    moves (step size 0 leaves a factor exactly unchanged)."""
+    g = np.random.default_rng(11)
+    X = g.standard_normal((7, 6, 5))
+    A0 = _rand_factors((7, 6, 5), 3, 12)
+    def upd(l):
+        A = [a.copy() for a in A0]
+        S = [O.gram(a) for a in A]
+        O.als_sweep(X, A, S, lam=[l, 0.0, 0.0])
+        for k in (1, 2):
+            np.testing.assert_array_equal(A[k], A0[k])
+        return A
+    r0, r1, rl = (_residual_sq(X, upd(l)) for l in (0.0, 1.0, lam))
+    assert r0 > r1
+    np.testing.assert_allclose(rl - r1, (1 - lam) ** 2 * (r0 - r1), rtol=1e-9)
+
+
+def _lstsq_mode(X, A, n):
+    """min_B ||X_(n) - B K^T|| by numpy lstsq on the explicit unfolding, with
+    K[(x_other), r] = prod_{k != n} A^(k)(x_k, r) written out by einsum."""
+    N = X.ndim
+    other = [k for k in range(N) if k != n]
+    letters = "abcdefg"
+    spec = ",".join(letters[k] + "r" for k in other) + "->" + "".join(letters[k] for k in other) + "r"
+    R = A[other[0]].shape[1]
+    K = np.einsum(spec, *[A[k] for k in other]).reshape(-1, R)
+    Xn = np.moveaxis(X, n, 0).reshape(X.shape[n], -1)
+    return np.linalg.lstsq(K, Xn.T, rcond=None)[0].T
+
+
+def test_symmetric_sweep_matches_least_squares():
+    """[[A, B, B]] (Sec. 5.3): A takes the plain least-squares update with
+    (B, B); B the step-size-0.8 blend of its least-squares update with
+    (A_new, B_old) in the other two modes; mode 2 then carries B."""
+    g = np.random.default_rng(21)
+    At, Bt = g.standard_normal((9, 3)), g.standard_normal((6, 3))
+    X = O.reconstruct([At, Bt, Bt])
+    E = g.standard_normal(X.shape)
+    X = X + 1e-2 * (E + E.transpose(0, 2, 1))            # noise symmetric in modes 1, 2
+    A0 = _rand_factors((9, 6, 6), 3, 22)
+    A = [a.copy() for a in A0]
+    A[2] = A[1].copy()
+    S = [O.gram(a) for a in A]
+    O.als_sweep(X, A, S, lam=[1.0, 0.8, 1.0], tie={2: 1})
+    a_new = _lstsq_mode(X, [None, A0[1], A0[1]], 0)
+    b_ls = _lstsq_mode(X, [a_new, None, A0[1]], 1)
+    b_new = 0.2 * A0[1] + 0.8 * b_ls
+    np.testing.assert_allclose(A[0], a_new, rtol=1e-9, atol=1e-10)
+    np.testing.assert_allclose(A[1], b_new, rtol=1e-9, atol=1e-10)
+    np.testing.assert_array_equal(A[2], A[1])
+    np.testing.assert_allclose(S[2], b_new.T @ b_new, rtol=1e-9, atol=1e-10)
+
+
+def test_symmetric_als_and_pp_recover_exact_symmetric_tensor():
+    """An exactly symmetric rank-3 tensor [[A, B, B]] is approached from a
+    nearby start by the symmetric ALS (B step 0.8) and by symmetric PP-ALS;
+    the two trajectories agree to second order in dA."""
+    g = np.random.default_rng(31)
+    At, Bt = g.standard_normal((10, 3)), g.standard_normal((8, 3))
+    X = O.reconstruct([At, Bt, Bt])
+    A0 = [At + 3e-2 * g.standard_normal(At.shape), Bt + 3e-2 * g.standard_normal(Bt.shape), None]
+    A0[2] = A0[1].copy()
+    lam, tie = [1.0, 0.8, 1.0], {2: 1}
+    Aa, ta = O.cp_als(X, A0, 150, lam=lam, tie=tie)
+    Ap, tp = O.pp_cp_als(X, A0, 150, eps=0.1, lam=lam, tie=tie)
+    assert ta[-1] > 1 - 1e-5 and tp.fitness[-1] > 1 - 1e-5          # from 0.990 at sweep 1
+    assert "pp_approx" in tp.kinds
+    np.testing.assert_array_equal(Aa[2], Aa[1])
+    np.testing.assert_array_equal(Ap[2], Ap[1])
+    assert max(abs(a - b) for a, b in zip(tp.fitness, ta)) < 1e-6
+
+
+def test_pp_init_first_mode_equals_als_with_step_size():
+    """As test_pp_init_first_mode_equals_als, with step size 0.7: the first
+    PP mode update (all dA = 0) is the ALS update blended with the current
+    factor."""
+    p = synth.scaled("normal", 7, 3, 2, seed=4, noise=1e-2, storage="f64")
+    A_pp, tr = O.pp_cp_als(p.X, p.A0, 1, eps=2.0, lam=0.7)
+    A = [a.copy() for a in p.A0]
+    S = [O.gram(a) for a in A]
+    O.als_sweep(p.X, A, S, lam=[0.7, 0.0, 0.0])
+    np.testing.assert_allclose(A_pp[0], A[0], rtol=1e-11, atol=1e-12)
+    assert not np.allclose(A_pp[0], O.solve_normal(O.mttkrp(p.X, p.A0, 0),
+                                                   O.gamma([O.gram(a) for a in p.A0], 0)))
