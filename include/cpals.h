@@ -86,6 +86,27 @@ void cpals_destroy(cpals_ctx* ctx);
  * the factors: call cpals_init_factors (again) afterwards. */
 cpals_status cpals_set_normal_arith(cpals_ctx* ctx, int arith);
 
+/* ALS variants of Sec. 5.3 (chemistry-tensor experiment), for ALS and PP
+ * sweeps alike.
+ *
+ * Update step size: lam[n] (N host values in (0, 2]; NULL = all 1) makes
+ * the update of mode n A_new = (1 - lam[n]) A^(n) + lam[n] M^(n) Gamma^(n)^-1
+ * (M^(n) the exact or PP-approximated right-hand side, A^(n) the current
+ * factor).  dA is then taken from A_new as usual.  Drops the captured sweep
+ * graphs; the state is kept.  CPALS_E_INVALID for a value outside (0, 2].
+ *
+ * Symmetry constraint: modes m1 < m2 of equal size share one factor
+ * (X = [[A, B, B]] is m1 = 1, m2 = 2 of an order-3 tensor, with the tensor
+ * symmetric in those modes; that symmetry is the caller's to provide).  A
+ * sweep solves for mode m1 and gives mode m2 its factor, Gram and change at
+ * once; mode m2 is never solved for (its right-hand side is still formed
+ * when it is the last mode, for the fitness).  cpals_init_factors uses
+ * factors[m1] for both.  m1 = m2 = -1 removes every tie.  Drops the graphs
+ * and the factors (call cpals_init_factors afterwards).  CPALS_E_INVALID
+ * for modes out of range, of different sizes, or already tied. */
+cpals_status cpals_set_step_size(cpals_ctx* ctx, const double* lam);
+cpals_status cpals_set_symmetric(cpals_ctx* ctx, int m1, int m2);
+
 /* Order the context's work after, and before, work already queued on a
  * caller stream (a cudaStream_t passed as void*; NULL = the legacy default
  * stream).  The library keeps its own stream and joins the caller stream at

@@ -53,6 +53,8 @@ _SIGS = {
     "cpals_get_stats": (C.c_int, [_ctx_p, C.c_int, _i64p, _dp, _dp, _dp]),
     "cpals_set_graphs": (C.c_int, [_ctx_p, C.c_int]),
     "cpals_set_normal_arith": (C.c_int, [_ctx_p, C.c_int]),
+    "cpals_set_step_size": (C.c_int, [_ctx_p, _dp]),
+    "cpals_set_symmetric": (C.c_int, [_ctx_p, C.c_int, C.c_int]),
     "cpals_set_controller": (C.c_int, [_ctx_p, _fp, C.c_int, C.c_double]),
     "cpals_run_controlled": (C.c_int, [_ctx_p, C.c_int, C.c_double, C.c_int, C.c_double, _dp,
                                        _ip, _dp, _ip, _ip, _ip]),
@@ -261,6 +263,14 @@ def cpals_set_normal_arith(ctx, arith):
     return lib().cpals_set_normal_arith(ctx, arith)
 
 
+def cpals_set_step_size(ctx, lam):
+    return lib().cpals_set_step_size(ctx, lam)
+
+
+def cpals_set_symmetric(ctx, m1, m2):
+    return lib().cpals_set_symmetric(ctx, m1, m2)
+
+
 def cpals_cost_model(dims, N, R, kind):
     d = (C.c_int64 * N)(*[int(x) for x in dims])
     out = C.c_double()
@@ -456,6 +466,21 @@ class CPALS:
         must be set again afterwards."""
         a = NORMAL_ARITH[arith] if isinstance(arith, str) else int(arith)
         self._ck(cpals_set_normal_arith(self.ctx, a))
+
+    def set_step_size(self, lam):
+        """Update step size per mode (a scalar applies to all; None = 1),
+        see cpals_set_step_size."""
+        if lam is None:
+            self._ck(cpals_set_step_size(self.ctx, None))
+            return
+        v = np.full(len(self.dims), float(lam)) if np.ndim(lam) == 0 else np.asarray(lam, float)
+        self._lam = np.ascontiguousarray(v)
+        self._ck(cpals_set_step_size(self.ctx, _dptr(self._lam)))
+
+    def set_symmetric(self, m1, m2):
+        """Tie mode m2's factor to mode m1's (see cpals_set_symmetric);
+        (-1, -1) removes the ties.  The factors must be set again."""
+        self._ck(cpals_set_symmetric(self.ctx, int(m1), int(m2)))
 
 
 def cost_model(dims, R, kind):

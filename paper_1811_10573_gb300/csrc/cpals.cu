@@ -31,6 +31,11 @@ struct cpals_ctx {
   int64_t dims[kMaxModes] = {0};
   int64_t total = 0;
   int h = 0;            // left half of the ALS tree: modes [0, h)
+  // ALS variants (Sec. 5.3): update step size per mode (1 = plain ALS), and
+  // ties tie[m2] = m1 < m2 (mode m2 shares mode m1's factor; -1 = none)
+  double lam[kMaxModes] = {1, 1, 1, 1, 1, 1, 1, 1};
+  int tie[kMaxModes] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  bool tied_any = false;
   int64_t PL = 1, PR = 1;
   int64_t smax = 0;
   int Rpad = 0;         // R rounded up to the tensor-core N granularity
@@ -289,9 +294,10 @@ const T* contract_chain(cpals_ctx* c, const T* in, std::vector<int> modes, int k
 void factor_async(cpals_ctx* c, int n, bool pp, bool useV) {
   cudaEventRecord(c->ev_fork, c->stream);
   cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+  // with tied modes Gamma is formed from the Grams (the tied copies are in place)
   if (c->dfm)
-    chol_df(c->Shi, c->Slo, c->Wf, c->Gpk, c->N, n, c->R, c->Linv, c->Zf, pp && useV, c->status,
-            c->Lside());
+    chol_df(c->Shi, c->Slo, c->Wf, c->tied_any ? nullptr : c->Gpk, c->N, n, c->R, c->Linv, c->Zf,
+            pp && useV, c->status, c->Lside());
   else
     gamma_chol(c->S, c->W, c->N, n, c->R, c->Lf, c->Z, pp && useV, c->status, c->Lside());
   cudaEventRecord(c->ev_join, c->side);
@@ -308,20 +314,53 @@ void finish_mode(cpals_ctx* c, int n, const T* rhs, bool pp, bool useV) {
     float* Ahi = P<float>(c->Ac[n]);
     solve_df((const float*)rhs, c->A[n], Ahi, c->Alo[n], pp ? c->Aphi[n] : nullptr,
              pp ? c->Aplo[n] : nullptr, c->dA[n], P<float>(c->dAc[n]), c->Linv,
-             v ? c->Zf : nullptr, (float2*)c->rownorm, s, R, n, c->status, c->L());
+             v ? c->Zf : nullptr, (float2*)c->rownorm, s, R, n, c->lam[n], c->status, c->L());
     gram_df(Ahi, c->Alo[n], Ahi, P<const float>(c->dAc[n]), c->S + off, c->Shi + off,
             c->Slo + off, c->Wf + off, pp, s, R, (const float2*)c->rownorm, c->scal + 8 + 2 * n,
-            c->Shi, c->Slo, c->N, n, (n + 1) % c->N, c->Gpk, c->L());
+            c->Shi, c->Slo, c->N, n, c->tied_any ? -1 : (n + 1) % c->N, c->Gpk, c->L());
     return;
   }
   if (v)
     solve_rows_v<T>(rhs, c->A[n], c->Ap[n], c->dA[n], c->Lf, c->Z, P<T>(c->rhs2), P<T>(c->Ac[n]),
-                    P<T>(c->dAc[n]), c->rownorm, s, R, n, c->status, c->L());
+                    P<T>(c->dAc[n]), c->rownorm, s, R, n, c->lam[n], c->status, c->L());
   else
     solve_rows<T>(rhs, c->A[n], pp ? c->Ap[n] : nullptr, c->dA[n], c->Lf, P<T>(c->Ac[n]),
-                  P<T>(c->dAc[n]), c->rownorm, s, R, n, c->status, c->L());
+                  P<T>(c->dAc[n]), c->rownorm, s, R, n, c->lam[n], c->status, c->L());
   gram_update<T>(c->A[n], P<const T>(c->Ac[n]), P<const T>(c->dAc[n]), c->S + off, c->W + off,
                  pp, s, R, c->rownorm, c->scal + 8 + 2 * n, c->dpart, c->tickets, c->L());
+}
+
+// Symmetry constraint (Sec. 5.3, X = [[A, B, B]]): every mode tied to mode n
+// takes mode n's new factor and its derived state (compute copies, change,
+// Grams, W = A^T dA, norms) right after mode n's update; a tied mode is never
+// solved for.
+bool tied(const cpals_ctx* c, int n) { return c->tie[n] >= 0; }
+
+cpals_status tie_copy(cpals_ctx* c, int n) {
+  if (!c->tied_any) return CPALS_OK;
+  const int R = c->R;
+  auto cp = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  };
+  for (int m = 0; m < c->N; m++) {
+    if (c->tie[m] != n) continue;
+    const size_t sR = (size_t)c->dims[n] * R, RR = (size_t)R * R;
+    const int64_t om = (int64_t)m * R * R, on = (int64_t)n * R * R;
+    CK(cp(c->A[m], c->A[n], sR * 8));
+    CK(cp(c->dA[m], c->dA[n], sR * 8));
+    CK(cp(c->Ac[m], c->Ac[n], sR * c->esz));
+    CK(cp(c->dAc[m], c->dAc[n], sR * c->esz));
+    CK(cp(c->S + om, c->S + on, RR * 8));
+    CK(cp(c->W + om, c->W + on, RR * 8));
+    if (c->dfm) {
+      CK(cp(c->Alo[m], c->Alo[n], sR * 4));
+      CK(cp(c->Shi + om, c->Shi + on, RR * 4));
+      CK(cp(c->Slo + om, c->Slo + on, RR * 4));
+      CK(cp(c->Wf + om, c->Wf + on, RR * 4));
+    }
+    CK(cp(c->scal + 8 + 2 * m, c->scal + 8 + 2 * n, 2 * 8));
+  }
+  return CPALS_OK;
 }
 
 // ---------------------------------------------------------------- ALS sweep
@@ -332,21 +371,30 @@ cpals_status als_sweep_launch(cpals_ctx* c) {
   for (int k = 0; k < h; k++) Lm.push_back(k);
   for (int k = h; k < N; k++) Rm.push_back(k);
   // left half: M^(L) = X_(L) (A^(h) (.) ... (.) A^(N-1))
+  // (mode 0 is never tied; a tied mode is skipped, except that the last
+  // mode's right-hand side is still formed for the fitness)
   factor_async(c, 0, false, false);
   CKS(contract_first<T>(c, h, N - h, c->Ac, P<T>(c->ML), 1, c->PR, c->PL, true));
   for (int n = 0; n < h; n++) {
+    if (tied(c, n)) continue;
     if (n > 0) factor_async(c, n, false, false);
     const T* rhs = contract_chain<T>(c, P<const T>(c->ML), Lm, n, c->Ac, P<T>(c->rhs));
     finish_mode<T>(c, n, rhs, false, false);
+    CKS(tie_copy(c, n));
   }
   // right half with the updated left factors: M^(Rt) = X_(L)^T (A^(0) (.) ... (.) A^(h-1))
-  factor_async(c, h, false, false);
+  if (!tied(c, h)) factor_async(c, h, false, false);
   CKS(contract_first<T>(c, 0, h, c->Ac, P<T>(c->MR), 1, c->PL, c->PR, false));
   const T* last = nullptr;
   for (int n = h; n < N; n++) {
+    if (tied(c, n)) {
+      if (n == N - 1) last = contract_chain<T>(c, P<const T>(c->MR), Rm, n, c->Ac, P<T>(c->rhs));
+      continue;
+    }
     if (n > h) factor_async(c, n, false, false);
     last = contract_chain<T>(c, P<const T>(c->MR), Rm, n, c->Ac, P<T>(c->rhs));
     finish_mode<T>(c, n, last, false, false);
+    CKS(tie_copy(c, n));
   }
   fitness<T>(last, c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->normX2, c->scal, c->dpart,
              c->L());
@@ -512,10 +560,14 @@ cpals_status pp_sweep_launch(cpals_ctx* c, bool useV) {
   const int N = c->N, R = c->R;
   PPTerm<T> terms[kMaxModes];
   for (int n = 0; n < N; n++) {
-    factor_async(c, n, true, useV);
+    const bool skip = tied(c, n);
+    if (skip && n != N - 1) continue;
+    if (!skip) factor_async(c, n, true, useV);
     pp_terms<T>(c, n, terms);
     pp_correct<T>(P<const T>(c->Mp[n]), terms, N - 1, P<T>(c->rhs), (int)c->dims[n], R, c->L());
+    if (skip) continue;                 // a tied last mode: M~ only feeds the fitness estimate
     finish_mode<T>(c, n, P<const T>(c->rhs), true, useV);
+    CKS(tie_copy(c, n));
   }
   // fitness estimate from M~^(N) (the last right-hand side, updated factors)
   fitness<T>(P<const T>(c->rhs), c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->normX2,
@@ -1011,7 +1063,9 @@ cpals_status cpals_init_factors(cpals_ctx* c, const double* const* factors) {
   CK(cudaMemsetAsync(c->status, 0, 16, c->stream));
   for (int n = 0; n < c->N; n++) {
     const int64_t sR = c->dims[n] * R;
-    CK(cudaMemcpyAsync(c->A[n], factors[n], sR * 8, cudaMemcpyHostToDevice, c->stream));
+    // a tied mode starts from its partner's factor (Sec. 5.3)
+    const double* src = factors[tied(c, n) ? c->tie[n] : n];
+    CK(cudaMemcpyAsync(c->A[n], src, sR * 8, cudaMemcpyHostToDevice, c->stream));
     // Algorithm 3 line 2: dA <- A, S <- A^T A
     CK(cudaMemcpyAsync(c->dA[n], c->A[n], sR * 8, cudaMemcpyDeviceToDevice, c->stream));
     if (is64(c)) {
@@ -1481,12 +1535,12 @@ cpals_status cpals_normal_solve(cpals_ctx* c, int n, const double* rhs, double* 
     float* lo = hi + cnt;
     CK(cudaMemsetAsync(hi, 0, cnt * 8, c->stream));
     solve_df(frhs, c->dscr[1], hi, lo, nullptr, nullptr, c->dscr[0], P<float>(c->tmp[0]), c->Linv,
-             nullptr, (float2*)c->rownorm, s, R, n, c->status, c->L());
+             nullptr, (float2*)c->rownorm, s, R, n, 1.0, c->status, c->L());
   } else {
     gamma_chol(c->S, c->W, c->N, n, R, c->Lf, c->Z, false, c->status, c->L());
     CK(cudaMemsetAsync(c->dscr[1], 0, cnt * 8, c->stream));
     solve_rows<double>(c->dscr[0], c->dscr[1], nullptr, P<double>(c->tmp[1]), c->Lf,
-                       P<double>(c->tmp[0]), P<double>(c->rhs2), c->rownorm, s, R, n, c->status,
+                       P<double>(c->tmp[0]), P<double>(c->rhs2), c->rownorm, s, R, n, 1.0, c->status,
                        c->L());
   }
   CKS(sync_read(c));
@@ -1550,6 +1604,42 @@ cpals_status cpals_set_normal_arith(cpals_ctx* c, int arith) {
   drop_graphs(c);
   c->dfm = arith == CPALS_NE_DOUBLE_FLOAT;
   c->have_factors = false;
+  c->ops_built = false;
+  return CPALS_OK;
+}
+
+cpals_status cpals_set_step_size(cpals_ctx* c, const double* lam) {
+  if (!c) return CPALS_E_INVALID;
+  double v[kMaxModes];
+  for (int n = 0; n < c->N; n++) {
+    v[n] = lam ? lam[n] : 1.0;
+    if (!(v[n] > 0.0 && v[n] <= 2.0)) return c->fail(CPALS_E_INVALID, "step size outside (0, 2]");
+  }
+  CK(cudaStreamSynchronize(c->stream));     // no captured graph still running
+  drop_graphs(c);                           // the step sizes are kernel arguments
+  for (int n = 0; n < c->N; n++) c->lam[n] = v[n];
+  return CPALS_OK;
+}
+
+cpals_status cpals_set_symmetric(cpals_ctx* c, int m1, int m2) {
+  if (!c) return CPALS_E_INVALID;
+  const bool clear = m1 < 0 && m2 < 0;
+  if (!clear) {
+    if (m1 < 0 || m2 <= m1 || m2 >= c->N) return c->fail(CPALS_E_INVALID, "need 0 <= m1 < m2 < N");
+    if (c->dims[m1] != c->dims[m2]) return c->fail(CPALS_E_INVALID, "tied modes differ in size");
+    if (tied(c, m1)) return c->fail(CPALS_E_INVALID, "m1 is itself tied");
+    for (int k = 0; k < c->N; k++)
+      if (c->tie[k] == m2) return c->fail(CPALS_E_INVALID, "m2 already has a tied partner");
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  if (clear)
+    for (int k = 0; k < c->N; k++) c->tie[k] = -1;
+  else
+    c->tie[m2] = m1;
+  c->tied_any = false;
+  for (int k = 0; k < c->N; k++) c->tied_any = c->tied_any || tied(c, k);
+  c->have_factors = false;                  // cpals_init_factors applies the tie
   c->ops_built = false;
   return CPALS_OK;
 }

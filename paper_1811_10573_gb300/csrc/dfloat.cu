@@ -804,7 +804,8 @@ __device__ __forceinline__ void dot2_acc(dfl& s, dfl a, dfl b) {
 // Group 0 writes the float64 master A, the double-float copy (Ahi = the float
 // compute copy, Alo), dA = A_new - ref (ref = A_p, or A_old when Arefhi is
 // null) as float64 and float, and per-row ||dA||^2, ||A_new||^2
-// (double-float).
+// (double-float).  With an update step size lam != 1 (Sec. 5.3) the new row
+// is (1 - lam) A_old + lam a.
 constexpr int kRB = 4;
 
 __device__ __forceinline__ dfl dot2_val(dfl acc) { return fast_two_sum(acc.hi, acc.lo); }
@@ -815,7 +816,7 @@ solve_inv_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float
                     const float* __restrict__ Areflo, double* __restrict__ dA,
                     float* __restrict__ dAc, const float2* __restrict__ Wg,
                     const float* __restrict__ Zg, float2* __restrict__ rownorm, int s, int R, int n,
-                    const int* __restrict__ status) {
+                    double lam, const int* __restrict__ status) {
   extern __shared__ __align__(16) float2 smem[];
   const int RS = R | 1;
   float2* Ws = smem;
@@ -937,6 +938,12 @@ solve_inv_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float
       __syncthreads();
 #pragma unroll
       for (int w = 0; w < kRB; w++) a[w] = df_add(dot2_val(acc[w]), upk(hp[w][rr]));
+      if (lam != 1.0) {
+        // update step size (Sec. 5.3): (1 - lam) A_old + lam a
+        const dfl l1 = df_of(lam), l0 = df_of(1.0 - lam);
+#pragma unroll
+        for (int w = 0; w < kRB; w++) a[w] = df_add(df_mul(l1, a[w]), df_mul(l0, dfl{oh[w], ol[w]}));
+      }
     }
     // outputs and per-row norms (group 0)
     if (!h) {
@@ -1042,14 +1049,14 @@ void chol_df(const float* Shi, const float* Slo, const float* W, const float2* G
 
 void solve_df(const float* rhs, double* A, float* Ahi, float* Alo, const float* Arefhi,
               const float* Areflo, double* dA, float* dAc, const float2* Winv, const float* Z,
-              float2* rownorm, int s, int R, int n, const int* status, Launch L) {
+              float2* rownorm, int s, int R, int n, double lam, const int* status, Launch L) {
   const size_t wb = ((size_t)R * (R | 1) * sizeof(float2) + 15) / 16 * 16;
   const size_t zb = Z ? ((size_t)R * R * sizeof(float) + 15) / 16 * 16 : 0;
   const int threads = 2 * ((R + 31) / 32 * 32);
   const int blocks = (int)std::min<int64_t>(cdiv(s, kRB), 152 * 2);
   solve_inv_df_kernel<<<blocks, threads, wb + zb, L.stream>>>(rhs, A, Ahi, Alo, Arefhi, Areflo, dA,
                                                               dAc, Winv, Z, rownorm, s, R, n,
-                                                              status);
+                                                              lam, status);
   (*L.counter)++;
 }
 

@@ -76,16 +76,18 @@ void gamma_chol(const double* S, const double* W, int N, int n, int R, double* L
 // Row-wise solve A_new = rhs Gamma^{-1} with the factor L; writes A (in place),
 // dA = A_new - (Aref ? Aref : A_old), compute-precision copies Ac, dAc and per-row
 // ||dA||^2, ||A_new||^2 into rownorm (2*s values).  Rows are left unchanged if
-// the factorisation failed for this mode (status bit set).
+// the factorisation failed for this mode (status bit set).  lam is the update
+// step size (Sec. 5.3): A_new = (1 - lam) A_old + lam rhs Gamma^{-1}.
 template <typename T>
 void solve_rows(const T* rhs, double* A, const double* Aref, double* dA, const double* Lf, T* Ac,
-                T* dAc, double* rownorm, int s, int R, int n, const int* status, Launch L);
+                T* dAc, double* rownorm, int s, int R, int n, double lam, const int* status,
+                Launch L);
 // Same with the second-order PP terms: rhs2 = rhs + A_old Z (compute precision,
 // s*R scratch values) is formed first from the compute copy Ac of A_old.
 template <typename T>
 void solve_rows_v(const T* rhs, double* A, const double* Aref, double* dA, const double* Lf,
                   const double* Z, T* rhs2, T* Ac, T* dAc, double* rownorm, int s, int R, int n,
-                  const int* status, Launch L);
+                  double lam, const int* status, Launch L);
 // out[y][r] = rhs[y][r] + sum_k A[y][k] Z[k][r] in the compute precision.
 template <typename T>
 void vterm(const T* rhs, const T* A, const double* Z, T* out, int s, int R, Launch L);
@@ -121,12 +123,13 @@ void gram_df(const float* Ahi, const float* Alo, const float* Aw, const float* d
 // gram_df with nn >= 0 also writes Gamma^(nn) (the next mode's) packed by
 // columns into Gpk; chol_df: Gamma^(n) (from Gpk when not null, else from the
 // Grams) = L L^T and Winv = L^-1 (row stride R|1, zero upper triangle);
-// solve_df: a = Winv^T Winv b per row.
+// solve_df: a = Winv^T Winv b per row, blended with the old row when the
+// update step size lam != 1 (Sec. 5.3).
 void chol_df(const float* Shi, const float* Slo, const float* W, const float2* Gpk, int N, int n,
              int R, float2* Winv, float* Z, bool useV, int* status, Launch L);
 void solve_df(const float* rhs, double* A, float* Ahi, float* Alo, const float* Arefhi,
               const float* Areflo, double* dA, float* dAc, const float2* Winv, const float* Z,
-              float2* rownorm, int s, int R, int n, const int* status, Launch L);
+              float2* rownorm, int s, int R, int n, double lam, const int* status, Launch L);
 
 // ---------------------------------------------------------------- learned controller
 // two-layer perceptron: kCtrlFeatures inputs, kCtrlHidden ReLU units,

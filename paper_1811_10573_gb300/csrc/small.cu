@@ -124,13 +124,15 @@ __device__ __forceinline__ void put(double (&v)[kChunks], int c, double x) {
 }
 
 // One warp per row y: forward substitution L z = b, back substitution
-// L^T a = z, i.e. a = b Gamma^{-1} (two triangular solves per row).
+// L^T a = z, i.e. a = b Gamma^{-1} (two triangular solves per row); with an
+// update step size lam != 1 (Sec. 5.3) the new row is (1 - lam) A_old + lam a.
 template <typename TR, typename T>
 __global__ void __launch_bounds__(128)
 solve_rows_kernel(const TR* __restrict__ rhs, double* __restrict__ A,
                   const double* __restrict__ Aref, double* __restrict__ dA,
                   const double* __restrict__ Lg, T* __restrict__ Ac, T* __restrict__ dAc,
-                  double* __restrict__ rownorm, int s, int R, int n, const int* __restrict__ status) {
+                  double* __restrict__ rownorm, int s, int R, int n, double lam,
+                  const int* __restrict__ status) {
   extern __shared__ double Ls[];   // R x RS lower factor (RS = R|1), then R inverse diagonals
   const int RS = R | 1;
   double* inv = Ls + R * RS;
@@ -177,6 +179,9 @@ solve_rows_kernel(const TR* __restrict__ rhs, double* __restrict__ A,
           if (r < i) b[c] = fma(-Ls[i * RS + r], ai, b[c]);
         }
       }
+      if (lam != 1.0)   // update step size (Sec. 5.3): (1 - lam) A_old + lam a
+#pragma unroll
+        for (int c = 0; c < kChunks; c++) b[c] = (1.0 - lam) * old[c] + lam * b[c];
     }
     double nd = 0.0, na = 0.0;
 #pragma unroll
@@ -422,20 +427,21 @@ void gamma_chol(const double* S, const double* W, int N, int n, int R, double* L
 
 template <typename T>
 static void solve_launch(const T* rhs, double* A, const double* Aref, double* dA, const double* Lf,
-                         T* Ac, T* dAc, double* rownorm, int s, int R, int n, const int* status,
-                         Launch L) {
+                         T* Ac, T* dAc, double* rownorm, int s, int R, int n, double lam,
+                         const int* status, Launch L) {
   const size_t smem = (size_t)(R * (R | 1) + R) * sizeof(double);
   const int rows_per_block = 2;      // spread the rows over all SMs
   const int blocks = (int)std::min<int64_t>(cdiv(s, rows_per_block), 152 * 4);
   solve_rows_kernel<T, T><<<blocks, 32 * rows_per_block, smem, L.stream>>>(
-      rhs, A, Aref, dA, Lf, Ac, dAc, rownorm, s, R, n, status);
+      rhs, A, Aref, dA, Lf, Ac, dAc, rownorm, s, R, n, lam, status);
   (*L.counter)++;
 }
 
 template <typename T>
 void solve_rows(const T* rhs, double* A, const double* Aref, double* dA, const double* Lf, T* Ac,
-                T* dAc, double* rownorm, int s, int R, int n, const int* status, Launch L) {
-  solve_launch<T>(rhs, A, Aref, dA, Lf, Ac, dAc, rownorm, s, R, n, status, L);
+                T* dAc, double* rownorm, int s, int R, int n, double lam, const int* status,
+                Launch L) {
+  solve_launch<T>(rhs, A, Aref, dA, Lf, Ac, dAc, rownorm, s, R, n, lam, status, L);
 }
 
 template <typename T>
@@ -449,9 +455,9 @@ void vterm(const T* rhs, const T* A, const double* Z, T* out, int s, int R, Laun
 template <typename T>
 void solve_rows_v(const T* rhs, double* A, const double* Aref, double* dA, const double* Lf,
                   const double* Z, T* rhs2, T* Ac, T* dAc, double* rownorm, int s, int R, int n,
-                  const int* status, Launch L) {
+                  double lam, const int* status, Launch L) {
   vterm<T>(rhs, Ac, Z, rhs2, s, R, L);
-  solve_launch<T>(rhs2, A, Aref, dA, Lf, Ac, dAc, rownorm, s, R, n, status, L);
+  solve_launch<T>(rhs2, A, Aref, dA, Lf, Ac, dAc, rownorm, s, R, n, lam, status, L);
 }
 
 template <typename T>
@@ -480,10 +486,10 @@ void fitness(const T* rhs, const double* A, const double* S, int N, int R, int s
 
 #define INST(T)                                                                                 \
   template void solve_rows<T>(const T*, double*, const double*, double*, const double*, T*, T*, \
-                              double*, int, int, int, const int*, Launch);                      \
+                              double*, int, int, int, double, const int*, Launch);              \
   template void solve_rows_v<T>(const T*, double*, const double*, double*, const double*,       \
-                                const double*, T*, T*, T*, double*, int, int, int, const int*,  \
-                                Launch);                                                        \
+                                const double*, T*, T*, T*, double*, int, int, int, double,      \
+                                const int*, Launch);                                            \
   template void vterm<T>(const T*, const T*, const double*, T*, int, int, Launch);              \
   template void gram_update<T>(const double*, const T*, const T*, double*, double*, bool, int,  \
                                int, const double*, double*, double*, int*, Launch);             \

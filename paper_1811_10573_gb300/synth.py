@@ -166,6 +166,30 @@ def order6_24_rank50(seed=0) -> Problem:
                         eps=0.1, sweeps=300, name="order6_24_rank50_f32")
 
 
+def symmetric_order3(sa, sb, R, *, seed=0, noise=1e-2, collinearity=None, storage="f32",
+                     eps=0.1, sweeps=100, name=None) -> Problem:
+    """Order-3 tensor symmetric in modes 1 and 2, X = [[A, B, B]] + noise
+    (the structure of Sec. 5.3's symmetric decomposition), noise symmetrised
+    over modes 1 and 2 and scaled relative to ||X||.  True factors N(0,1), or
+    collinear with cosine C per factor when ``collinearity`` is given (C10
+    construction).  Initial factors U[0,1] with A0[2] = A0[1]."""
+    if collinearity is None:
+        At, Bt = factors_normal([sa, sb], R, seed)
+    else:
+        At, Bt = factors_collinear([sa, sb], R, float(collinearity), seed)
+    X = low_rank_tensor([At, Bt, Bt])
+    if noise:
+        E = _rng(seed, 4).standard_normal(X.shape)
+        E = E + E.transpose(0, 2, 1)
+        X = X + noise * (np.linalg.norm(X) / np.linalg.norm(E)) * E
+    A0 = factors_uniform([sa, sb], R, seed, stream=6)
+    A0 = [A0[0], A0[1], A0[1].copy()]
+    Xs = X.astype(np.float32) if storage == "f32" else X
+    meta = {} if collinearity is None else {"collinearity": float(collinearity)}
+    return Problem(name or f"symmetric_order3_{sa}x{sb}x{sb}_rank{R}", np.ascontiguousarray(Xs),
+                   A0, R, eps, sweeps, storage, meta)
+
+
 def batch_order3(count=256, seed=0, smin=32, smax=160, rmin=8, rmax=64):
     """Many small order-3 problems with per-mode sizes U{smin..smax} and ranks
     U{rmin..rmax}, FP32, 1e-2 relative noise, 100 sweeps each."""
