@@ -412,7 +412,7 @@ def run_variants(args, dist, p, Xd, flush, max_sweeps):
                     ok = ok and out["reached"]
                 kinds = out["kinds"]
                 res[kind] = {"value": round(float(np.mean(ts)), 6), "unit": "s", "reached": ok,
-                             "sweeps": len(kinds),
+                             "sweeps": len(kinds), "final_fitness": float(out["fitness"][-1]),
                              "sweep_counts": {k: kinds.count(k) for k in ("als", "pp_init", "pp_approx")}}
         res["pp_vs_als_speedup"] = round(res["als"]["value"] / res["pp"]["value"], 3)
         return res

@@ -116,6 +116,7 @@ struct cpals_ctx {
   int64_t fl_launches = 0;
   double fl_ms = 0, fl_bytes = 0, fl_flops = 0;
   int* umma_err = nullptr;
+  int* umma_sched = nullptr;       // work counter of the tensor-core kernel (launches on stream)
   // learned controller
   float* ctrl_params = nullptr;    // device, ctrl_param_count(kCtrlFeatures) floats
   float* ctrl_io = nullptr;        // device: features (kCtrlFeatures) then probabilities
@@ -245,7 +246,7 @@ cpals_status contract_first(cpals_ctx* c, int k0, int nk, void* const* facs, T* 
     khatri_rao_bf16_t(fl, c->dims + k0, nk, R, c->Rpad, Kstride, c->Bt, c->L());
     ev_begin(c, idx);
     CK(umma_gemm_bf16(c->Xb, c->Bt, P<float>(out), P<float>(c->gpart), batch, K, M, R, c->Rpad,
-                      Kstride, kmajor, splits, c->umma_err, c->L()));
+                      Kstride, kmajor, splits, c->umma_err, c->umma_sched, c->L()));
     ev_end(c, idx, bytes, flops);
     return CPALS_OK;
   }
@@ -959,6 +960,7 @@ cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpal
   AL(c->scal, 64 * 8);
   AL(c->status, 4 * sizeof(int));
   AL(c->tickets, 64 * sizeof(int));
+  AL(c->umma_sched, 2 * sizeof(int));
   c->umma_err = c->status + 1;
 #undef AL
   if (cudaMallocHost((void**)&c->scal_h, 64 * 8) != cudaSuccess ||
@@ -966,6 +968,7 @@ cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpal
     return bail(CPALS_E_OOM);
   if (cudaMemset(c->scal, 0, 64 * 8) != cudaSuccess || cudaMemset(c->status, 0, 16) != cudaSuccess ||
       cudaMemset(c->tickets, 0, 64 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->umma_sched, 0, 2 * sizeof(int)) != cudaSuccess ||
       cudaMemset(c->W, 0, (size_t)N * R * R * 8) != cudaSuccess)
     return bail(CPALS_E_CUDA);
   memset(c->scal_h, 0, 64 * 8);
@@ -992,7 +995,7 @@ void cpals_destroy(cpals_ctx* c) {
   F(c->Shi); F(c->Slo); F(c->Wf); F(c->Linv); F(c->Gpk); F(c->Zf);
   F(c->S); F(c->W); F(c->Lf); F(c->Z); F(c->ML); F(c->MR); F(c->krp); F(c->tmp[0]); F(c->tmp[1]);
   F(c->rhs); F(c->rhs2); F(c->gpart); F(c->Bt); F(c->rownorm); F(c->dpart); F(c->scal);
-  F(c->status); F(c->tickets); F(c->dscr[0]); F(c->dscr[1]);
+  F(c->status); F(c->tickets); F(c->umma_sched); F(c->dscr[0]); F(c->dscr[1]);
   F(c->ctrl_params); F(c->ctrl_io);
   if (c->ctrl_io_h) cudaFreeHost(c->ctrl_io_h);
   for (void* p : c->snap_bufs) F(p);

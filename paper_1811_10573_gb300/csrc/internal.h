@@ -150,6 +150,9 @@ void mlp_train_epoch(float* params, float* m, float* v, int F, const float* X, c
 // Bt holds two planes (hi, lo) of Rpad (multiple of 16) rows x Kstride bf16
 // (zero padded); the product uses hi + lo.
 // splits > 1: fp32 partials + deterministic reduction into out.
+// sched: two zeroed ints that launches on one stream may share (units are
+// handed out dynamically and the counter is reset by the kernel); null gives
+// a static round-robin assignment (safe for concurrent launches).
 // Returns false if the shape is not supported (alignment), so the caller can
 // report CPALS_E_UNSUPPORTED.
 bool umma_supported(int64_t K, int64_t M, bool kmajor, int R);
@@ -157,6 +160,7 @@ bool umma_supported(int64_t K, int64_t M, bool kmajor, int R);
 cudaError_t setup_umma_kernels();
 cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, float* out,
                            float* partials, int64_t batch, int64_t K, int64_t M, int R, int Rpad,
-                           int64_t Kstride, bool kmajor, int splits, int* err_flag, Launch L);
+                           int64_t Kstride, bool kmajor, int splits, int* err_flag, int* sched,
+                           Launch L);
 
 }  // namespace cpals

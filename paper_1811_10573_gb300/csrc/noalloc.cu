@@ -75,7 +75,8 @@ extern "C" cpals_status cpals_contract_bf16_noalloc(const void* Xb, const void* 
   cudaError_t e = cpals::umma_gemm_bf16(static_cast<const __nv_bfloat16*>(Xb),
                                         static_cast<const __nv_bfloat16*>(Bt), out,
                                         g_scratch_ptr[dev], batch, K, M, R, Rpad, Kstride,
-                                        kmajor != 0, splits, err, cpals::Launch{s, &launches});
+                                        kmajor != 0, splits, err, nullptr,
+                                        cpals::Launch{s, &launches});
   if (e != cudaSuccess) {
     cudaGetLastError();
     return e == cudaErrorInvalidValue ? CPALS_E_UNSUPPORTED : CPALS_E_CUDA;

@@ -18,7 +18,12 @@
 // Persistent warp-specialised kernel, one CTA per SM.  A work unit is one or
 // two 128-row output tiles (tpu) of one K chunk; the two tiles of a unit share
 // every stage of the B operand, which halves the B traffic per byte of X and
-// doubles the X bytes in flight:
+// doubles the X bytes in flight.  The producer takes units from a global
+// counter (atomicAdd) and passes each unit index to the MMA and epilogue
+// warps through a four-slot queue in shared memory, so a CTA that starts
+// late (its SM held by another kernel, e.g. the factorisation on the side
+// stream) takes fewer units instead of finishing last; the last CTA to exit
+// resets the counter for the next launch on the stream.
 //   warp 0      : TMA producer (tpu A tiles 128 x 64 and the B tile 2 x Rpad x
 //                 64 per stage, 128-byte swizzle, mbarrier complete_tx)
 //   warp 1      : TMEM allocation + single-thread tcgen05.mma issue (M = 128,
@@ -189,6 +194,7 @@ struct UmmaParams {
   int64_t mtiles, mgroups, units;
   float* out;           // out or partials ([z][b][m][r])
   int* err;
+  int* sched;           // [next unit, CTAs done], zero at launch; null: static round robin
 };
 
 template <bool KMAJOR>
@@ -197,6 +203,8 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                  const __grid_constant__ CUtensorMap mapO, UmmaParams p) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[8], empty_bar[8], accf_bar[2], acce_bar[2], done_bar;
+  __shared__ __align__(8) uint64_t uq_full[4], uq_empty[4];   // unit queue
+  __shared__ long long uq[4];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_sh;
 
@@ -222,6 +230,10 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       mbar_init(smem_u32(&acce_bar[b]), 4);
     }
     mbar_init(smem_u32(&done_bar), 1);
+    for (int q = 0; q < 4; q++) {
+      mbar_init(smem_u32(&uq_full[q]), 1);
+      mbar_init(smem_u32(&uq_empty[q]), 5);    // the MMA thread and the four epilogue warps
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
@@ -245,7 +257,18 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       uint32_t phase = 0;
       int issued[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       bool ok = true;
-      for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+      for (int t = 0;; t++) {
+        // next unit (-1 ends the queue); slot t % 4 is free once unit t-4 was read
+        const int64_t un = p.sched ? (int64_t)atomicAdd(p.sched, 1)
+                                   : (int64_t)blockIdx.x + (int64_t)t * gridDim.x;
+        const int64_t u = (ok && un < p.units) ? un : -1;
+        if (!mbar_wait(smem_u32(&uq_empty[t & 3]), ((t >> 2) & 1) ^ 1, &abort_sh, false)) {
+          ok = false;
+          break;
+        }
+        uq[t & 3] = u;
+        mbar_arrive(smem_u32(&uq_full[t & 3]));
+        if (u < 0) break;
         const int64_t mg = u % p.mgroups;
         const int64_t rest = u / p.mgroups;
         const int z = (int)(rest % p.splits);
@@ -263,9 +286,9 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
           const uint32_t sA = base + stage * stage_bytes;
           const uint32_t sB = sA + a_bytes;
           mbar_expect_tx(fb, (uint32_t)nt * A_STAGE_BYTES + b_stage_bytes);
-          for (int t = 0; t < nt; t++) {
-            const uint32_t sAt = sA + t * A_STAGE_BYTES;
-            const int64_t mt = mt0 + t;
+          for (int tt = 0; tt < nt; tt++) {
+            const uint32_t sAt = sA + tt * A_STAGE_BYTES;
+            const int64_t mt = mt0 + tt;
             if (KMAJOR) {
               tma_load_2d(sAt, &mapA, fb, (int)k, (int)(mt * BM));
             } else {
@@ -279,6 +302,12 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
             stage = 0;
             phase ^= 1;
           }
+        }
+        if (!ok) {
+          // the consumers may wait on this unit's stages: stop them
+          atomicCAS(p.err, 0, ERR_PRODUCER);
+          abort_sh = 1;
+          break;
         }
       }
       if (!ok) {
@@ -304,10 +333,17 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       const uint32_t idesc = make_idesc(BM, 2 * p.Rpad, !KMAJOR);
       int stage = 0;
       uint32_t phase = 0;
-      int t = 0;
       bool ok = true;
       bool any = false;
-      for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x, t++) {
+      for (int t = 0;; t++) {
+        if (!mbar_wait(smem_u32(&uq_full[t & 3]), (t >> 2) & 1, &abort_sh, false)) {
+          atomicCAS(p.err, 0, ERR_MMA_ACC);
+          abort_sh = 1;
+          break;
+        }
+        const int64_t u = uq[t & 3];
+        mbar_arrive(smem_u32(&uq_empty[t & 3]));
+        if (u < 0) break;
         const int64_t mg = u % p.mgroups;
         const int64_t rest = u / p.mgroups;
         const int z = (int)(rest % p.splits);
@@ -387,9 +423,27 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
     const int row = q * 32 + lane;
     const int ew = warp - 2;
     const bool leader = (ew == 0 && lane == 0);
-    int t = 0;
     int bc = 0;                               // boxes stored so far (alternating buffers)
-    for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x, t++) {
+    for (int t = 0;; t++) {
+      long long uu = 0;
+      int okq = 1;
+      if (lane == 0) {
+        okq = mbar_wait(smem_u32(&uq_full[t & 3]), (t >> 2) & 1, &abort_sh, true) ? 1 : 0;
+        if (okq) {
+          uu = uq[t & 3];
+          mbar_arrive(smem_u32(&uq_empty[t & 3]));
+        }
+      }
+      okq = __shfl_sync(0xffffffffu, okq, 0);
+      if (!okq) {
+        if (lane == 0) {
+          atomicCAS(p.err, 0, ERR_EPI);
+          abort_sh = 1;
+        }
+        break;
+      }
+      const int64_t u = (int64_t)__shfl_sync(0xffffffffu, uu, 0);
+      if (u < 0) break;
       const int64_t mg = u % p.mgroups;
       const int64_t rest = u / p.mgroups;
       const int z = (int)(rest % p.splits);
@@ -490,6 +544,14 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
                  "r"(tmem_cols)
                  : "memory");
   }
+  // every CTA has taken its last unit: the last one out resets the counter
+  if (threadIdx.x == 0 && p.sched) {
+    __threadfence();
+    if (atomicAdd(p.sched + 1, 1) == (int)gridDim.x - 1) {
+      atomicExch(p.sched, 0);
+      atomicExch(p.sched + 1, 0);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- host side
@@ -548,7 +610,8 @@ bool umma_supported(int64_t K, int64_t M, bool kmajor, int R) {
 
 cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, float* out,
                            float* partials, int64_t batch, int64_t K, int64_t M, int R, int Rpad,
-                           int64_t Kstride, bool kmajor, int splits, int* err_flag, Launch L) {
+                           int64_t Kstride, bool kmajor, int splits, int* err_flag, int* sched,
+                           Launch L) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   if (!umma_supported(K, M, kmajor, R) || Rpad % 16 || Rpad > 128 || Rpad < R)
@@ -598,6 +661,7 @@ cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, flo
   p.splits = (int)cdiv(K, p.kchunk);
   p.mtiles = cdiv(M, BM);
   p.err = err_flag;
+  p.sched = sched;
   p.out = p.splits > 1 ? partials : out;
   int RS = (R + 3) / 4 * 4;
   if (((RS / 4) & 1) == 0) RS += 4;
