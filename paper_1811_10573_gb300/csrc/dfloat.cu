@@ -68,14 +68,19 @@ __device__ __forceinline__ dfl df_add_fast(dfl x, dfl y) {
   const dfl s = two_sum(x.hi, y.hi);
   return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
 }
-// 1/sqrt(a): float reciprocal square root refined by one Newton step in
-// double-float, r = r0 + r0 (1 - a r0^2) / 2
+// 1/sqrt(a): float reciprocal square root refined by one Newton step,
+// r = r0 + r0 (1 - a r0^2) / 2.  The residual is formed with FMAs:
+// a.hi r0 = h + dh exactly, 1 - h r0 is exact before its one rounding (it is
+// ~2^-22), then the small terms dh r0 and a.lo r0^2 are taken off.
 __device__ __forceinline__ dfl df_rsqrt(dfl a) {
   const float r0 = rsqrtf(a.hi);
-  const dfl r2 = two_prod(r0, r0);
-  const dfl ar2 = df_mul(a, r2);
-  const dfl e = df_sub(dfl{1.f, 0.f}, ar2);
-  return fast_two_sum(r0, __fmul_rn(__fmul_rn(0.5f, r0), e.hi));
+  const float h = __fmul_rn(a.hi, r0);
+  const float dh = __fmaf_rn(a.hi, r0, -h);
+  const float r02 = __fmul_rn(r0, r0);
+  float e = __fmaf_rn(-h, r0, 1.f);
+  e = __fmaf_rn(-dh, r0, e);
+  e = __fmaf_rn(-a.lo, r02, e);
+  return fast_two_sum(r0, __fmul_rn(__fmul_rn(0.5f, r0), e));
 }
 __device__ __forceinline__ dfl df_of(double x) {
   const float h = __double2float_rn(x);
@@ -251,32 +256,32 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
 }
 
 // ---------------------------------------------------------------- Gamma, Cholesky, inverse
-// A cluster of three CTAs forms Gamma^(n) = Hadamard product of the Grams
+// A cluster of five CTAs forms Gamma^(n) = Hadamard product of the Grams
 // S^(k), k != n, in double-float, factors it Gamma = L L^T and inverts the
-// factor, W = L^-1, two pivots per step (right-looking; Golub & Van Loan
-// Alg. 4.2.2 for the factor, the column-oriented triangular inverse for W).
-//   CTA 2 (updates) holds the lower triangle of Gamma packed by columns
-//     (entry (i, j), i >= j, at cs(j) + i - j, cs(j) = j R - j (j - 1) / 2,
-//     so the trailing triangle right of a column is a contiguous suffix that
-//     all its threads share evenly).  For each column pair P = (p, p+1),
-//     p = 2P, it applies the pair to the columns right of pair P+1: first
-//     those of pair P+2, which it then sends to CTA 0, then the rest.
-//   CTA 0 (chain) makes the pairs.  A pivot warp factors the 2 x 2 pivot
-//     block (a, b; b, d) of pair P less pair P-1 (lanes 0..2 form a, b, d
-//     at once) as il2 = 1/sqrt(a), il3 = a il2 / sqrt(ad - b^2): two
-//     independent reciprocal square roots.  Row thread i keeps its row of
-//     pair P-1 in registers, forms the numerators of L_ip and L_i,p+1 before
-//     the pivots arrive, then L_ip, L_i,p+1 and the inverse-update
-//     coefficients v_i = L_i,p+1 / L_p+1,p+1, u_i = L_ip / L_pp - v_i
-//     L_p+1,p / L_pp.  Rows p+2 and p+3 release the next pivot block, so the
-//     chain from pair to pair is one pivot block and two short row steps on
-//     an SM that runs nothing else.
-//   CTA 1 (inverse) holds the lower triangle of the inverse in progress
-//     packed by rows (entry (i, c) at i (i + 1) / 2 + c), initially the
-//     identity, and applies B_ic -= u_i B_kc + v_i B_k+1,c for rows i >= k+2,
-//     c <= k+1 per pair k = 2P (pivot k and pivot k+1, which sees row k+1
-//     after pivot k).  Row k+1 gets pivot k at the end, and row j of W is
-//     the final row j of B divided by L_jj.
+// factor, W = L^-1, two pivots (one column pair P = (p, p+1), p = 2P) per
+// step (right-looking; Golub & Van Loan Alg. 4.2.2 for the factor, the
+// column-oriented triangular inverse for W).
+//   CTA 0 (chain) makes the pairs.  Its pivot warp factors the 2 x 2 pivot
+//     block (a, b; b, d) of pair P as il2 = 1/sqrt(a), il3 = a il2 /
+//     sqrt(ad - b^2) (two independent reciprocal square roots) and then forms
+//     rows p+2 and p+3 of the pair itself, so the next pivot block never
+//     waits for another warp.  Row thread i forms L_ip and L_i,p+1 and the
+//     inverse-update coefficients v_i = L_i,p+1 / L_p+1,p+1, u_i = L_ip / L_pp
+//     - v_i L_p+1,p / L_pp.
+//   CTAs 2 and 4 (trailing updates) hold the lower triangle of Gamma for the
+//     column pairs of their parity (pairs Q with Q % 2 = 0 on CTA 2, odd on
+//     CTA 4), packed by columns.  For each pair P they apply P to their
+//     columns of pairs >= P+3; the owner of pair P+3 does those columns first
+//     and sends them to CTA 0.  A column pair thus reaches CTA 0 three pairs
+//     ahead, with every pair up to Q-3 applied; CTA 0 applies pairs Q-2 and
+//     Q-1 (in that order) itself, so its chain never waits for a trailing
+//     update and the two halves of the trailing work run side by side.
+//   CTAs 1 and 3 (inverse) hold the columns of the inverse in progress of
+//     their parity (even columns on CTA 1, odd on CTA 3; row i at ro[i]),
+//     initially the identity, and apply B_ic -= u_i B_kc + v_i B_k+1,c for
+//     rows i >= k+2, columns c <= k+1 per pair k = 2P (pivot k and pivot k+1,
+//     which sees row k+1 after pivot k).  Row k+1 gets pivot k at the end,
+//     and row j of W is the final row j of B divided by L_jj.
 // Data moves between the CTAs only as st.async stores into the receiver's
 // shared memory that complete a transaction count on one of its mbarriers
 // (one per pair and purpose), so no CTA reads another's shared memory and
@@ -290,7 +295,8 @@ gram_df_kernel(const float* __restrict__ Ahi, const float* __restrict__ Alo,
 #ifndef CPALS_CHOL_THREADS
 #define CPALS_CHOL_THREADS 512
 #endif
-__device__ __forceinline__ int col_start(int j, int R) { return j * R - j * (j - 1) / 2; }
+constexpr int kLook = 3;        // pairs a column pair travels ahead of its use
+__host__ __device__ __forceinline__ int col_start(int j, int R) { return j * R - j * (j - 1) / 2; }
 // g - a b - c d
 __device__ __forceinline__ dfl df_fms2(dfl g, dfl a, dfl b, dfl c, dfl d) {
   const float p1 = __fmul_rn(a.hi, b.hi);
@@ -313,28 +319,74 @@ __device__ __forceinline__ bool bad_pivot(dfl p) { return !(p.hi > 0.f) || !isfi
 __device__ __forceinline__ dfl lo2(float4 v) { return {v.x, v.y}; }
 __device__ __forceinline__ dfl hi2(float4 v) { return {v.z, v.w}; }
 __device__ __forceinline__ float4 pk2(dfl a, dfl b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
+// g - (pair P-2 terms) - (pair P-1 terms): u2, v2 and u1, v1 hold the two
+// rows' (L_.,q, L_.,q+1) of those pairs.  Four exact leading products, one
+// chain of TwoSums on the high words, one renormalisation.
+__device__ __forceinline__ dfl df_fms4(dfl g, float4 u2, float4 v2, float4 u1, float4 v1) {
+  const dfl a[4] = {lo2(u2), hi2(u2), lo2(u1), hi2(u1)};
+  const dfl b[4] = {lo2(v2), hi2(v2), lo2(v1), hi2(v1)};
+  float p[4], e[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    p[k] = __fmul_rn(a[k].hi, b[k].hi);
+    e[k] = __fmaf_rn(a[k].hi, b[k].hi, -p[k]);
+    e[k] = __fmaf_rn(a[k].hi, b[k].lo, e[k]);
+    e[k] = __fmaf_rn(a[k].lo, b[k].hi, e[k]);
+  }
+  dfl s = two_sum(g.hi, -p[0]);
+  float lo = __fadd_rn(g.lo, s.lo);
+#pragma unroll
+  for (int k = 1; k < 4; k++) {
+    s = two_sum(s.hi, -p[k]);
+    lo = __fadd_rn(lo, s.lo);
+  }
+  lo = __fsub_rn(__fsub_rn(lo, __fadd_rn(e[0], e[1])), __fadd_rn(e[2], e[3]));
+  return fast_two_sum(s.hi, lo);
+}
 
-// Shared-memory layout of the three CTAs (byte offsets from the dynamic base).
+// Entries of the inverse held by the CTA of column parity h: row i keeps
+// columns c <= i with c % 2 == h, at ro(i) + c / 2.
+__host__ __device__ __forceinline__ int inv_tri(int x) { return x >= 1 ? ((x - 1) / 2) * (x / 2) : 0; }
+__host__ __device__ __forceinline__ int inv_ro(int i, int h) {
+  return h ? (i >= 1 ? (i - 1) + inv_tri(i - 1) : 0) : i + inv_tri(i);
+}
+// Packed entries of column pair Q (columns 2Q, 2Q+1, rows from the column down).
+__host__ __device__ __forceinline__ int pair_cnt(int Q, int R) {
+  const int p = 2 * Q;
+  return (R - p) + (p + 1 < R ? R - p - 1 : 0);
+}
+
+// Shared-memory layout (byte offsets from the dynamic base).  Arrays that
+// receive remote stores sit at the same offset in every CTA.
 struct CholLayout {
-  size_t gc, lc, end0;                      // CTA 0: pair columns of G (4 slots), pairs of L (4 sets)
-  size_t uv, id, lsub, bars, flag, end1;    // CTA 1: B (at 0), coefficients, 1/L_jj,
-                                            // L_j,j-1/L_j-1,j-1, one mbarrier per pair, stop flag
-  size_t crd, lc2, end2;                    // CTA 2: G (at 0), (row, column) of each entry, pairs of L
+  size_t gc, lc, end0;                        // CTA 0: pair columns (4 slots), L pairs (8 sets)
+  size_t B, ro, uv, id, lsub, bars, flag, end1;   // inverse CTAs
+  size_t G, crd, lcs, lc2, end2;              // trailing CTAs
   __host__ __device__ CholLayout(int R) {
-    const size_t T = (size_t)R * (R + 1) / 2;
-    const size_t tb = (T * 8 + 15) / 16 * 16;
+    const int npair = (R + 1) / 2;
+    auto al = [](size_t x) { return (x + 15) / 16 * 16; };
     gc = 0;
-    lc = gc + 8 * (size_t)R * 8;
-    end0 = lc + 4 * (size_t)R * 16;
-    uv = tb;
-    id = uv + (size_t)(R / 2 + 1) * R * 16;
-    lsub = id + (size_t)R * 8;
-    bars = lsub + (size_t)R * 8;
-    flag = bars + (size_t)(R / 2 + 1) * 8;
+    lc = gc + al(4 * 2 * (size_t)R * 8);
+    end0 = lc + 8 * (size_t)R * 16;
+    B = 0;
+    ro = al((size_t)inv_ro(R, 0) * 8);
+    uv = ro + al((size_t)R * 4);
+    id = uv + (size_t)npair * R * 16;
+    lsub = id + al((size_t)R * 8);
+    bars = lsub + al((size_t)R * 8);
+    flag = bars + (size_t)npair * 8;
     end1 = flag + 16;
-    crd = tb;
-    lc2 = crd + (T * 4 + 15) / 16 * 16;
-    end2 = lc2 + 4 * (size_t)R * 16;
+    int gmax = 0;
+    for (int h = 0; h < 2; h++) {
+      int c = 0;
+      for (int Q = h; Q < npair; Q += 2) c += pair_cnt(Q, R);
+      gmax = c > gmax ? c : gmax;
+    }
+    G = 0;
+    crd = al((size_t)gmax * 8);
+    lcs = crd + al((size_t)gmax * 4);
+    lc2 = lcs + al((size_t)(npair / 2 + 2) * 4);
+    end2 = lc2 + 8 * (size_t)R * 16;
   }
   __host__ __device__ size_t bytes() const {
     const size_t m = end0 > end1 ? end0 : end1;
@@ -367,19 +419,18 @@ __device__ __forceinline__ int ld_acquire_cluster(const int* p) {
   return v;
 }
 
-__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(CPALS_CHOL_THREADS, 1)
+__global__ void __cluster_dims__(5, 1, 1) __launch_bounds__(CPALS_CHOL_THREADS, 1)
 chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
                    const float* __restrict__ Wg, const float2* __restrict__ Gpk, int N, int n,
                    int R, float2* __restrict__ Wout, float* __restrict__ Z, int useV,
                    int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char csm[];
   __shared__ int bad;
-  __shared__ __align__(8) uint64_t gbar;
-  // CTA 0: mbX[P] (pair P's columns have arrived), mbR[P] (rows p, p+1 hold
-  // pair P-1), mbC[P] (pair P's pivot block is published); CTA 2: mbY[P]
-  // (every row of pair P has arrived)
-  __shared__ __align__(8) uint64_t mbX[kMaxRank / 2], mbR[kMaxRank / 2], mbC[kMaxRank / 2],
-      mbY[kMaxRank / 2];
+  // CTA 0: mbX[P] (pair P's columns are here), mbR[P] (rows p, p+1 hold pair
+  // P-1), mbR2[P] (rows p+2, p+3 hold pair P-1), mbC[P] (pair P's pivot block
+  // is published); trailing CTAs: mbY[P] (every row of pair P is here)
+  __shared__ __align__(8) uint64_t mbX[kMaxRank / 2], mbR[kMaxRank / 2], mbR2[kMaxRank / 2],
+      mbC[kMaxRank / 2], mbY[kMaxRank / 2];
   __shared__ float2 piv[4][4];                 // per pair slot: il2, il3, c3 = L_p+1,p, c3 il2
   cg::cluster_group cl = cg::this_cluster();
   const int role = (int)cl.block_rank();
@@ -387,23 +438,21 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
   const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
   const int RR = R * R;
   const int RS = R | 1;
-  const int T = R * (R + 1) / 2;
   const CholLayout lay(R);
   const int npair = (R + 1) / 2;
-  // CTA 1's arrays (CTA 0 writes them through the cluster window)
+  float2* gc = reinterpret_cast<float2*>(csm + lay.gc);           // [slot][column of the pair][row]
+  float4* lc = reinterpret_cast<float4*>(csm + lay.lc);           // [set][row] (L_ip, L_i,p+1)
+  float2* B = reinterpret_cast<float2*>(csm + lay.B);
+  int* ro = reinterpret_cast<int*>(csm + lay.ro);
   float4* UV = reinterpret_cast<float4*>(csm + lay.uv);
   float2* id = reinterpret_cast<float2*>(csm + lay.id);
   float2* lsub = reinterpret_cast<float2*>(csm + lay.lsub);
   uint64_t* bars = reinterpret_cast<uint64_t*>(csm + lay.bars);   // one per pair of columns
   int* flag = reinterpret_cast<int*>(csm + lay.flag);             // [0] stop
-  // CTA 0's and CTA 2's arrays
-  float2* gc = reinterpret_cast<float2*>(csm + lay.gc);           // [slot][column of the pair][row]
-  float4* lc = reinterpret_cast<float4*>(csm + lay.lc);           // [set][row] (L_ip, L_i,p+1)
+  float2* G = reinterpret_cast<float2*>(csm + lay.G);
+  uint32_t* crd = reinterpret_cast<uint32_t*>(csm + lay.crd);
+  int* lcs = reinterpret_cast<int*>(csm + lay.lcs);               // local start of owned pairs
   float4* lc2 = reinterpret_cast<float4*>(csm + lay.lc2);
-  auto gc_bytes = [&](int P) {
-    const int p = 2 * P;
-    return (uint32_t)(8 * (p + 1 < R ? 2 * (R - p) - 1 : R - p));
-  };
   auto mb_init = [](uint64_t* bar, int count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)),
                  "r"(count));
@@ -412,13 +461,31 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                  ::"r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(bytes) : "memory");
   };
-  auto mwait = [&](uint64_t* bar, int code) {
+  // hint: suspend-time hint in ns (0: poll); a waiting thread sleeps until the
+  // phase completes instead of spinning on the pipe the pivot warp uses
+  auto mwait = [&](uint64_t* bar, int code, uint32_t hint = 0) {
     const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
     const unsigned long long t0 = clock64();
     while (true) {
       uint32_t done;
-      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
-                   " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(b) : "memory");
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0, %2;\n"
+                   " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(b), "r"(hint) : "memory");
+      if (done) return;
+      if (clock64() - t0 > 4000000000ull) {
+        atomicOr(status + 2, code);
+        bad = 1;
+        return;
+      }
+    }
+  };
+  // barriers completed by this CTA's own threads need only CTA-scope acquire
+  auto mwait_cta = [&](uint64_t* bar, int code, uint32_t hint = 0) {
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    const unsigned long long t0 = clock64();
+    while (true) {
+      uint32_t done;
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, %2;\n"
+                   " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(b), "r"(hint) : "memory");
       if (done) return;
       if (clock64() - t0 > 4000000000ull) {
         atomicOr(status + 2, code);
@@ -431,23 +498,31 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"((uint32_t)__cvta_generic_to_shared(bar))
                  : "memory");
   };
+  const bool inv = role == 1 || role == 3, trl = role == 2 || role == 4;
+  const int par = inv ? (role - 1) / 2 : trl ? (role - 2) / 2 : 0;   // column (pair) parity
   if (tid == 0) bad = 0;
   if (role == 0) {
     for (int P = tid; P < npair; P += nt) {
       mb_init(mbX + P, 1);
-      mb_expect(mbX + P, gc_bytes(P));
+      if (P >= kLook) mb_expect(mbX + P, 8u * (uint32_t)pair_cnt(P, R));   // the first ones: formed here
       mb_init(mbR + P, min(2, R - 2 * P));
+      mb_init(mbR2 + P, max(1, min(2, R - 2 * P - 2)));   // waited only when the rows exist
       mb_init(mbC + P, 1);
     }
-  } else if (role == 2) {
+  } else if (trl) {
     for (int P = tid; P < npair; P += nt) {
       mb_init(mbY + P, 1);
       mb_expect(mbY + P, 16u * (uint32_t)(R - 2 * P));
     }
-    if (tid == 0) mb_init(&gbar, 1);
-  }
-  if (role == 1) {
-    float2* B = reinterpret_cast<float2*>(csm);
+    if (tid == 0) {
+      int c = 0;
+      for (int Q = par, k = 0; Q < npair; Q += 2, k++) {
+        lcs[k] = c;
+        c += pair_cnt(Q, R);
+      }
+      lcs[(npair - par + 1) / 2] = c;                // end of the owned entries
+    }
+  } else {
     if (tid == 0) flag[0] = 0;
     // pair P brings 16 bytes per row i >= 2P, 1/L_jj of its columns and,
     // when it has two, L_{2P+1,2P} / L_{2P,2P}
@@ -458,86 +533,47 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
                    : "memory");
     }
-    for (int i = warp; i < R; i += nwarp)
-      for (int j = lane; j <= i; j += 32) B[i * (i + 1) / 2 + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+    for (int i = tid; i < R; i += nt) ro[i] = inv_ro(i, par);
+    // identity (columns of this parity)
+    for (int i = warp; i < R; i += nwarp) {
+      const int o = inv_ro(i, par);
+      for (int c = 2 * lane + par; c <= i; c += 64) B[o + (c >> 1)] = make_float2(c == i ? 1.f : 0.f, 0.f);
+    }
   }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   cl.sync();                                   // every CTA's barriers exist before anyone sends
-  if (role == 2) {
-    // ---------------------------------------------------------- updates
-    float2* G = reinterpret_cast<float2*>(csm);
-    uint32_t* crd = reinterpret_cast<uint32_t*>(csm + lay.crd);
+  if (trl) {
+    // ---------------------------------------------------------- trailing updates
     const uint32_t gcr = cluster_addr(gc, 0), mbXr = cluster_addr(mbX, 0);
-    const uint32_t gbytes = (uint32_t)((T * sizeof(float2) + 15) / 16 * 16);
-    if (Gpk) {
-      // Gamma arrives packed (formed by the Gram kernel of the previous mode)
-      if (tid == 0) {
-        const uint32_t gb = (uint32_t)__cvta_generic_to_shared(&gbar);
-        mb_expect(&gbar, gbytes);
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"((uint32_t)__cvta_generic_to_shared(G)), "l"(Gpk), "r"(gbytes), "r"(gb)
-                     : "memory");
+    const int nown = (npair - par + 1) / 2;
+    const int gtot = lcs[nown];
+    // (row, column) of every owned entry, and Gamma there
+    for (int e = tid; e < gtot; e += nt) {
+      int k = 0;
+      while (k + 1 < nown && lcs[k + 1] <= e) k++;
+      const int Q = par + 2 * k, p = 2 * Q;
+      const int r = e - lcs[k];
+      const int j = r < R - p ? p : p + 1;
+      const int i = j == p ? p + r : p + 1 + (r - (R - p));
+      crd[e] = (uint32_t)i | ((uint32_t)j << 16);
+      dfl g = {1.f, 0.f};
+      if (Gpk) {
+        g = upk(Gpk[col_start(j, R) + i - j]);
+      } else {
+        for (int k2 = 0; k2 < N; k2++)
+          if (k2 != n) g = df_mul(g, dfl{Shi[(int64_t)k2 * RR + i * R + j], Slo[(int64_t)k2 * RR + i * R + j]});
       }
-      for (int j = warp; j < R; j += nwarp) {
-        const int e0 = col_start(j, R);
-        for (int i = j + lane; i < R; i += 32) crd[e0 + i - j] = (uint32_t)i | ((uint32_t)j << 16);
-      }
-      if (tid == 0) mwait(&gbar, 4);
-    }
-    // Gamma from the Grams otherwise: entries in packed order, eight per
-    // thread in flight; each mode's loads are issued together
-    for (int base = 0; !Gpk && base < T; base += 8 * nt) {
-      int gi[8];
-      dfl acc[8];
-#pragma unroll
-      for (int q = 0; q < 8; q++) {
-        const int e = base + q * nt + tid;
-        int j = 0, i = 0;
-        if (e < T) {
-          const float b2 = (float)(2 * R + 1);
-          j = (int)((b2 - sqrtf(b2 * b2 - 8.f * (float)e)) * 0.5f);
-          j = max(0, min(R - 1, j));
-          while (j + 1 < R && col_start(j + 1, R) <= e) j++;
-          while (col_start(j, R) > e) j--;
-          i = j + e - col_start(j, R);
-          crd[e] = (uint32_t)i | ((uint32_t)j << 16);
-        }
-        gi[q] = e < T ? i * R + j : -1;
-        acc[q] = {1.f, 0.f};
-      }
-      for (int k = 0; k < N; k++) {
-        if (k == n) continue;
-        float h[8], l[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-          h[q] = gi[q] >= 0 ? Shi[(int64_t)k * RR + gi[q]] : 1.f;
-          l[q] = gi[q] >= 0 ? Slo[(int64_t)k * RR + gi[q]] : 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; q++) acc[q] = df_mul(acc[q], dfl{h[q], l[q]});
-      }
-#pragma unroll
-      for (int q = 0; q < 8; q++)
-        if (gi[q] >= 0) G[base + q * nt + tid] = pk(acc[q]);
+      G[e] = pk(g);
     }
     __syncthreads();
-    // send G entry e (row i, column j of pair P) to CTA 0's slot of pair P
-    auto send = [&](int e, dfl g) {
-      const uint32_t ij = crd[e];
-      const int i = ij & 0xffffu, j = ij >> 16, P = j >> 1;
-      const uint32_t dst = gcr + 8u * (uint32_t)((((P & 3) * 2 + (j & 1)) * R) + i);
-      st_async8(dst, pk(g), mbXr + 8u * (uint32_t)P);
-    };
-    // pairs 0 and 1 go out as they are
-    for (int e = tid; e < col_start(min(4, R), R); e += nt) send(e, upk(G[e]));
     for (int P = 0; P < npair; P++) {
-      const int p = 2 * P;
-      if (tid == 0) mwait(mbY + P, 16);
+      if (tid == 0) mwait(mbY + P, 16, 2000);
       __syncthreads();                         // pair P is here; the previous updates are done
-      const float4* cc = lc2 + (P & 3) * R;
+      const float4* cc = lc2 + (P & 7) * R;
       // G_ij -= L_i,p L_j,p + L_i,p+1 L_j,p+1 on [e0, e1), two entries per
       // iteration (independent double-float chains); out sends the result
-      auto update = [&](int e0, int e1, bool out) {
+      // to CTA 0's slot of pair Qs
+      auto update = [&](int e0, int e1, int Qs) {
         int e = e0 + tid;
         for (; e + nt < e1; e += 2 * nt) {
           const uint32_t ij0 = crd[e], ij1 = crd[e + nt];
@@ -547,9 +583,10 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
           const dfl g1 = df_fms2(upk(G[e + nt]), lo2(li1), lo2(lj1), hi2(li1), hi2(lj1));
           G[e] = pk(g0);
           G[e + nt] = pk(g1);
-          if (out) {
-            send(e, g0);
-            send(e + nt, g1);
+          if (Qs >= 0) {
+            const int i0 = ij0 & 0xffffu, j0 = ij0 >> 16, i1 = ij1 & 0xffffu, j1 = ij1 >> 16;
+            st_async8(gcr + 8u * (uint32_t)((((Qs & 3) * 2 + (j0 & 1)) * R) + i0), pk(g0), mbXr + 8u * (uint32_t)Qs);
+            st_async8(gcr + 8u * (uint32_t)((((Qs & 3) * 2 + (j1 & 1)) * R) + i1), pk(g1), mbXr + 8u * (uint32_t)Qs);
           }
         }
         if (e < e1) {
@@ -557,36 +594,83 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
           const float4 li = cc[ij & 0xffffu], lj = cc[ij >> 16];
           const dfl g = df_fms2(upk(G[e]), lo2(li), lo2(lj), hi2(li), hi2(lj));
           G[e] = pk(g);
-          if (out) send(e, g);
+          if (Qs >= 0)
+            st_async8(gcr + 8u * (uint32_t)((((Qs & 3) * 2 + ((ij >> 16) & 1)) * R) + (ij & 0xffffu)), pk(g),
+                      mbXr + 8u * (uint32_t)Qs);
         }
       };
-      if (P + 2 < npair) update(col_start(p + 4, R), col_start(min(p + 6, R), R), true);
-      if (p + 6 < R) update(col_start(p + 6, R), T, false);
+      const int Qn = P + kLook;                // goes to CTA 0 once pair P is in
+      if (Qn < npair && (Qn & 1) == par) update(lcs[(Qn - par) >> 1], lcs[((Qn - par) >> 1) + 1], Qn);
+      int Qr = P + kLook + 1;                  // the rest: owned pairs >= P+4
+      Qr += (Qr - par) & 1;
+      if (Qr < npair) update(lcs[(Qr - par) >> 1], gtot, -1);
     }
   } else if (role == 0) {
     // ---------------------------------------------------------- chain
-    const uint32_t UVr = cluster_addr(UV, 1), idr = cluster_addr(id, 1);
-    const uint32_t lsubr = cluster_addr(lsub, 1), barr = cluster_addr(bars, 1);
-    const uint32_t lc2r = cluster_addr(lc2, 2), mbYr = cluster_addr(mbY, 2);
+    uint32_t UVr[2], idr[2], lsubr[2], barr[2], lc2r[2], mbYr[2];
+    for (int h = 0; h < 2; h++) {
+      UVr[h] = cluster_addr(UV, 1 + 2 * h);
+      idr[h] = cluster_addr(id, 1 + 2 * h);
+      lsubr[h] = cluster_addr(lsub, 1 + 2 * h);
+      barr[h] = cluster_addr(bars, 1 + 2 * h);
+      lc2r[h] = cluster_addr(lc2, 2 + 2 * h);
+      mbYr[h] = cluster_addr(mbY, 2 + 2 * h);
+    }
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // the first kLook column pairs straight from Gamma (no pair applies to
+    // them yet); same product order as the trailing CTAs and the Gram kernel
+    const int cf = min(2 * kLook, R);
+    for (int e = tid; e < col_start(cf, R); e += nt) {
+      int j = 0;
+      while (j + 1 < cf && col_start(j + 1, R) <= e) j++;
+      const int i = j + e - col_start(j, R);
+      dfl g = {1.f, 0.f};
+      if (Gpk) {
+        g = upk(Gpk[e]);
+      } else {
+        for (int k = 0; k < N; k++)
+          if (k != n) g = df_mul(g, dfl{Shi[(int64_t)k * RR + i * R + j], Slo[(int64_t)k * RR + i * R + j]});
+      }
+      gc[(((j >> 1) & 3) * 2 + (j & 1)) * R + i] = pk(g);
+    }
     __syncthreads();
+    if (tid == 0)
+      for (int P = 0; P < min(kLook, npair); P++) marrive(mbX + P);
     if (warp == 4) {
-      // pivot warp
+      // pivot warp.  It keeps rows p and p+1 of the two previous pairs in
+      // registers (Lp1, Lq1: pair P-1; Lp2, Lq2: pair P-2; each (L_.,q,
+      // L_.,q+1)) and, once it has published a pivot block, forms rows p+2
+      // and p+3 of the pair itself (the row threads' operations in the same
+      // order, so the values are identical).
+      float4 Lp1 = z4, Lq1 = z4, Lp2 = z4, Lq2 = z4;
       for (int P = 0; P < npair; P++) {
         const int p = 2 * P;
         const bool two = p + 1 < R;
-        if (P >= 1) mwait(mbR + P, 8);
+        const bool more = p + 2 < R;           // rows p+2 (and p+3) exist
+        if (more && P >= 1) mwait_cta(mbR2 + P, 8);
         mwait(mbX + P, 8);
         const float2* g = gc + (P & 3) * 2 * R;
-        // lane 0: a = G_pp, lane 1: b = G_p+1,p, lane 2: d = G_p+1,p+1, each
-        // less pair P-1
-        const int r1 = p + (lane >= 1 ? 1 : 0), r2 = p + (lane == 2 ? 1 : 0);
-        const float2 gv = lane == 2 ? g[R + p + 1] : g[p + (lane == 1 ? 1 : 0)];
+        // lane 0: a = G_pp, lane 1: b = G_p+1,p, lane 2: d = G_p+1,p+1;
+        // lanes 3, 4: column p of rows p+2, p+3; lanes 5, 6: column p+1 of
+        // rows p+2, p+3; each less pairs P-2 and P-1 (rows p+2, p+3 of those
+        // pairs come from the row threads)
+        const int ii = p + 2 + ((lane - 3) & 1);
+        const bool rowl = lane >= 3 && lane < 7 && ii < R && two;
+        float4 q1 = z4, q2 = z4;
+        float2 gv = make_float2(0.f, 0.f);
+        if (lane < 3) {
+          gv = lane == 2 ? g[R + p + 1] : g[p + (lane == 1 ? 1 : 0)];
+        } else if (rowl) {
+          if (P >= 1) q1 = lc[((P - 1) & 7) * R + ii];
+          if (P >= 2) q2 = lc[((P - 2) & 7) * R + ii];
+          gv = lane < 5 ? g[ii] : g[R + ii];
+        }
         dfl x = {1.f, 0.f};
-        if (lane < (two ? 3 : 1)) {
-          const float4 u1 = P >= 1 ? lc[((P - 1) & 3) * R + r1] : z4;
-          const float4 u2 = P >= 1 ? lc[((P - 1) & 3) * R + r2] : z4;
-          x = df_fms2(upk(gv), lo2(u1), lo2(u2), hi2(u1), hi2(u2));
+        if (lane < (two ? 3 : 1) || rowl) {
+          const float4 u1 = lane < 3 ? (lane >= 1 ? Lq1 : Lp1) : q1;
+          const float4 u2 = lane < 3 ? (lane >= 1 ? Lq2 : Lp2) : q2;
+          const bool vq = lane == 2 || lane >= 5;
+          x = df_fms4(upk(gv), u2, vq ? Lq2 : Lp2, u1, vq ? Lq1 : Lp1);
         }
         const dfl a = {__shfl_sync(0xffffffffu, x.hi, 0), __shfl_sync(0xffffffffu, x.lo, 0)};
         const dfl bb = {__shfl_sync(0xffffffffu, x.hi, 1), __shfl_sync(0xffffffffu, x.lo, 1)};
@@ -596,67 +680,92 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
         const dfl rin = df_rsqrt(lane == 0 ? det : a);
         const dfl il2 = {__shfl_sync(0xffffffffu, rin.hi, 1), __shfl_sync(0xffffffffu, rin.lo, 1)};
         const dfl rdet = {__shfl_sync(0xffffffffu, rin.hi, 0), __shfl_sync(0xffffffffu, rin.lo, 0)};
+        const dfl il3 = two ? df_mul(df_mul(rdet, a), il2) : dfl{0.f, 0.f};
+        const dfl c3 = two ? df_mul(bb, il2) : dfl{0.f, 0.f};
         if (lane == 0) {
           if (bad_pivot(a) || bad_pivot(det)) bad = 1;
-          const dfl il3 = two ? df_mul(df_mul(rdet, a), il2) : dfl{0.f, 0.f};
-          const dfl c3 = two ? df_mul(bb, il2) : dfl{0.f, 0.f};
           piv[P & 3][0] = pk(il2);
           piv[P & 3][1] = pk(il3);
           piv[P & 3][2] = pk(c3);
           piv[P & 3][3] = pk(df_mul(c3, il2));
           marrive(mbC + P);
         }
+        if (more) {
+          // rows p+2 and p+3 of this pair: L_ip on lanes 3, 4, then L_i,p+1
+          // on lanes 5, 6 (row threads' operations, same order)
+          const dfl l2 = df_mul(x, il2);
+          const int src = lane >= 5 ? lane - 2 : lane;
+          const dfl l2s = {__shfl_sync(0xffffffffu, l2.hi, src), __shfl_sync(0xffffffffu, l2.lo, src)};
+          const dfl l3 = two ? df_mul(df_fms(x, l2s, c3), il3) : dfl{0.f, 0.f};
+          // the next pair's pivot rows p+2, p+3: this pair from l2, l3; pair
+          // P-1 from what the row threads stored
+          Lp2 = make_float4(__shfl_sync(0xffffffffu, q1.x, 3), __shfl_sync(0xffffffffu, q1.y, 3),
+                            __shfl_sync(0xffffffffu, q1.z, 3), __shfl_sync(0xffffffffu, q1.w, 3));
+          Lq2 = make_float4(__shfl_sync(0xffffffffu, q1.x, 4), __shfl_sync(0xffffffffu, q1.y, 4),
+                            __shfl_sync(0xffffffffu, q1.z, 4), __shfl_sync(0xffffffffu, q1.w, 4));
+          Lp1 = make_float4(__shfl_sync(0xffffffffu, l2.hi, 3), __shfl_sync(0xffffffffu, l2.lo, 3),
+                            __shfl_sync(0xffffffffu, l3.hi, 5), __shfl_sync(0xffffffffu, l3.lo, 5));
+          Lq1 = make_float4(__shfl_sync(0xffffffffu, l2.hi, 4), __shfl_sync(0xffffffffu, l2.lo, 4),
+                            __shfl_sync(0xffffffffu, l3.hi, 6), __shfl_sync(0xffffffffu, l3.lo, 6));
+        }
         __syncwarp();
       }
-    } else if (tid < 128) {
-      // row threads
-      const int i = tid;
-      dfl q1a = {0.f, 0.f}, q1b = {0.f, 0.f};   // row i of pair P-1
+    } else if ((warp >= 1 && warp <= 3) || warp == 5) {
+      // row threads (warps 1-3 and 5: the pivot warp, warp 4, has its
+      // scheduler partition to itself, warps 0, 8 and 12 idle)
+      const int i = warp == 5 ? 96 + lane : tid - 32;
+      float4 q1 = z4, q2 = z4;                  // row i of pairs P-1 and P-2
       for (int P = 0; P < npair && 2 * P <= i && i < R; P++) {
         const int p = 2 * P;
         const bool two = p + 1 < R;
-        if (P >= 1) mwait(mbR + P, 8);
-        mwait(mbX + P, 8);
+        if (P >= 1) mwait_cta(mbR + P, 8, 2000);
+        mwait(mbX + P, 8, 2000);
         const float2* g = gc + (P & 3) * 2 * R;
-        const float4 L1p = P >= 1 ? lc[((P - 1) & 3) * R + p] : z4;
-        const float4 L1q = (two && P >= 1) ? lc[((P - 1) & 3) * R + p + 1] : z4;
-        const dfl gi = df_fms2(upk(g[i]), q1a, lo2(L1p), q1b, hi2(L1p));
+        const float4 L1p = P >= 1 ? lc[((P - 1) & 7) * R + p] : z4;
+        const float4 L1q = (two && P >= 1) ? lc[((P - 1) & 7) * R + p + 1] : z4;
+        const float4 L2p = P >= 2 ? lc[((P - 2) & 7) * R + p] : z4;
+        const float4 L2q = (two && P >= 2) ? lc[((P - 2) & 7) * R + p + 1] : z4;
+        const dfl gi = df_fms4(upk(g[i]), q2, L2p, q1, L1p);
         dfl hi = {0.f, 0.f};
-        if (two && i > p) hi = df_fms2(upk(g[R + i]), q1a, lo2(L1q), q1b, hi2(L1q));
-        mwait(mbC + P, 8);
+        if (two && i > p) hi = df_fms4(upk(g[R + i]), q2, L2q, q1, L1q);
+        mwait_cta(mbC + P, 8, 2000);
         const dfl il2 = upk(piv[P & 3][0]), il3 = upk(piv[P & 3][1]);
         const dfl c3 = upk(piv[P & 3][2]), m = upk(piv[P & 3][3]);
         const dfl l2 = df_mul(gi, il2);
         const dfl l3 = (two && i > p) ? df_mul(df_fms(hi, l2, c3), il3) : dfl{0.f, 0.f};
         const float4 lv = pk2(l2, l3);
-        lc[(P & 3) * R + i] = lv;
+        lc[(P & 7) * R + i] = lv;
         if (P + 1 < npair && (i == p + 2 || i == p + 3)) marrive(mbR + P + 1);
-        st_async16(lc2r + 16u * (uint32_t)((P & 3) * R + i), lv, mbYr + 8u * (uint32_t)P);
-        // inverse-update coefficients to CTA 1
-        const dfl q2 = df_mul(l2, il2);
+        if (i == p + 4 || i == p + 5) marrive(mbR2 + P + 1);   // for the pivot warp
+        for (int h = 0; h < 2; h++)
+          st_async16(lc2r[h] + 16u * (uint32_t)((P & 7) * R + i), lv, mbYr[h] + 8u * (uint32_t)P);
+        // inverse-update coefficients to both inverse CTAs
+        const dfl q2v = df_mul(l2, il2);
         const dfl v = df_mul(l3, il3);
-        const dfl u = df_fms(q2, v, m);
-        const uint32_t bar = barr + 8u * (uint32_t)P;
-        st_async16(UVr + 16u * (uint32_t)(P * R + i), pk2(u, v), bar);
-        if (i == p) st_async8(idr + 8u * p, pk(il2), bar);
-        if (two && i == p + 1) {
-          st_async8(idr + 8u * (p + 1), pk(il3), bar);
-          st_async8(lsubr + 8u * (p + 1), pk(q2), bar);
+        const dfl u = df_fms(q2v, v, m);
+        for (int h = 0; h < 2; h++) {
+          const uint32_t bar = barr[h] + 8u * (uint32_t)P;
+          st_async16(UVr[h] + 16u * (uint32_t)(P * R + i), pk2(u, v), bar);
+          if (i == p) st_async8(idr[h] + 8u * p, pk(il2), bar);
+          if (two && i == p + 1) {
+            st_async8(idr[h] + 8u * (p + 1), pk(il3), bar);
+            st_async8(lsubr[h] + 8u * (p + 1), pk(q2v), bar);
+          }
         }
-        q1a = l2;
-        q1b = l3;
+        q2 = q1;
+        q1 = lv;
       }
     }
     __syncthreads();
     if (bad && tid == 0) {
       atomicOr(status, 1 << n);
-      st_release_cluster(cl.map_shared_rank(flag, 1), 1);   // CTA 1 stops waiting
+      for (int h = 0; h < 2; h++) st_release_cluster(cl.map_shared_rank(flag, 1 + 2 * h), 1);   // stop the inverse CTAs
     }
   } else {
-    // ---------------------------------------------------------- inverse
-    float2* B = reinterpret_cast<float2*>(csm);
+    // ---------------------------------------------------------- inverse (columns of parity par)
     if (useV) {
-      for (int idx = tid; idx < RR; idx += nt) {
+      // Z (second-order PP terms), entries split between the two inverse CTAs
+      for (int idx = 2 * tid + par; idx < RR; idx += 2 * nt) {
         float zz = 0.f;
         for (int a = 0; a < N; a++) {
           if (a == n) continue;
@@ -691,21 +800,43 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
         state[sl] = st;
       }
     };
+    // row i of W = (final row i of B) / L_ii; odd rows still lack pivot
+    // i-1: B_i. -= (L_i,i-1 / L_i-1,i-1) B_i-1.  One warp per row, this
+    // CTA's columns.
+    auto write_row = [&](int i) {
+      const dfl d = upk(id[i]);
+      const bool odd = i & 1;
+      const dfl f = odd ? upk(lsub[i]) : dfl{0.f, 0.f};
+      const float2* Bi = B + ro[i];
+      const float2* Bp = i >= 1 ? B + ro[i - 1] : B;
+      for (int c = 2 * lane + par; c < RS; c += 64) {
+        float2 w = make_float2(0.f, 0.f);
+        if (c < i) {
+          dfl b = upk(Bi[c >> 1]);
+          if (odd) b = df_fms(b, f, upk(Bp[c >> 1]));
+          w = pk(df_mul(b, d));
+        } else if (c == i) {
+          w = pk(d);
+        }
+        Wout[i * RS + c] = w;
+      }
+    };
     int st = 0;
     if (R > 2) wait_pair(0, 0);
     __syncthreads();
     for (int k = 0; k + 2 < R; k += 2) {
       st = state[slot];
       if (st) break;
-      // (c) inverse update of rows >= k+2, columns <= k+1
+      // (c) inverse update of rows >= k+2, this CTA's columns <= k+1
       const float4* cu = UV + (size_t)(k >> 1) * R;
-      const int cols = k + 2, tot = (R - k - 2) * cols;
+      const int cols = (k + 2) >> 1, tot = (R - k - 2) * cols;
       if (tid < tot) {
         const float rc = 1.f / (float)cols;
         int q = (int)(((float)tid + 0.5f) * rc), c = tid - q * cols;
         const int dq = (int)(((float)nt + 0.5f) * rc), dc = nt - dq * cols;
-        const float2* Bk = B + k * (k + 1) / 2;
-        const float2* Bk1 = B + (k + 1) * (k + 2) / 2;
+        const float2* Bk = B + ro[k];
+        const float2* Bk1 = B + ro[k + 1];
+        const int ck = par ? (k >> 1) : (k >> 1) + 1;   // local columns <= k in row k
         // two entries per iteration (t and t + nt): independent chains
         int t = tid;
         for (; t + nt < tot; t += 2 * nt) {
@@ -715,16 +846,14 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
             q1++;
           }
           const int i0 = k + 2 + q, i1 = k + 2 + q1;
-          float2* bp0 = B + i0 * (i0 + 1) / 2 + c;
-          float2* bp1 = B + i1 * (i1 + 1) / 2 + c1;
+          float2* bp0 = B + ro[i0] + c;
+          float2* bp1 = B + ro[i1] + c1;
           const float4 w0 = cu[i0], w1 = cu[i1];
-          const dfl bk0 = c <= k ? upk(Bk[c]) : dfl{0.f, 0.f};
-          const dfl bq0 = c <= k ? upk(Bk1[c]) : dfl{1.f, 0.f};
-          const dfl bk1 = c1 <= k ? upk(Bk[c1]) : dfl{0.f, 0.f};
-          const dfl bq1 = c1 <= k ? upk(Bk1[c1]) : dfl{1.f, 0.f};
+          const dfl bk0 = c < ck ? upk(Bk[c]) : dfl{0.f, 0.f};
+          const dfl bk1 = c1 < ck ? upk(Bk[c1]) : dfl{0.f, 0.f};
           const dfl x0 = upk(*bp0), x1 = upk(*bp1);
-          *bp0 = pk(df_fms2(x0, lo2(w0), bk0, hi2(w0), bq0));
-          *bp1 = pk(df_fms2(x1, lo2(w1), bk1, hi2(w1), bq1));
+          *bp0 = pk(df_fms2(x0, lo2(w0), bk0, hi2(w0), upk(Bk1[c])));
+          *bp1 = pk(df_fms2(x1, lo2(w1), bk1, hi2(w1), upk(Bk1[c1])));
           q = q1 + dq;
           c = c1 + dc;
           if (c >= cols) {
@@ -734,11 +863,10 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
         }
         if (t < tot) {
           const int i = k + 2 + q;
-          float2* bp = B + i * (i + 1) / 2 + c;
+          float2* bp = B + ro[i] + c;
           const float4 w = cu[i];
-          const dfl bk = c <= k ? upk(Bk[c]) : dfl{0.f, 0.f};
-          const dfl bk1 = c <= k ? upk(Bk1[c]) : dfl{1.f, 0.f};
-          *bp = pk(df_fms2(upk(*bp), lo2(w), bk, hi2(w), bk1));
+          const dfl bk = c < ck ? upk(Bk[c]) : dfl{0.f, 0.f};
+          *bp = pk(df_fms2(upk(*bp), lo2(w), bk, hi2(w), upk(Bk1[c])));
         }
       }
       // the next pair (or, after the last step, the last one for 1 / L_jj)
@@ -752,29 +880,26 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
     }
     if (!st) st = state[slot];
     if (st == 2 && tid == 0) atomicOr(status + 2, 2);
-    if (!st) {
-      // W = diag(1 / L_ii) B; odd rows still lack pivot i-1: B_i. -= (L_i,i-1 / L_i-1,i-1) B_i-1.
-      for (int i = warp; i < R; i += nwarp) {
-        const dfl d = upk(id[i]);
-        const bool odd = i & 1;
-        const dfl f = odd ? upk(lsub[i]) : dfl{0.f, 0.f};
-        const float2* Bi = B + i * (i + 1) / 2;
-        const float2* Bp = B + (i - 1) * i / 2;
-        for (int c = lane; c < RS; c += 32) {
-          float2 w = make_float2(0.f, 0.f);
-          if (c < i) {
-            dfl b = upk(Bi[c]);
-            if (odd) b = df_fms(b, f, upk(Bp[c]));
-            w = pk(df_mul(b, d));
-          } else if (c == i) {
-            w = pk(d);
-          }
-          Wout[i * RS + c] = w;
+    if (!st)
+      for (int i = warp; i < R; i += nwarp) write_row(i);
+    if (st == 1 && tid == 0) {
+      // stopped after a bad pivot: CTA 0 still sends every pair, so let them
+      // all land (bounded) before this CTA may exit
+      const unsigned long long t0 = clock64();
+      for (int P = 0; P < npair; P++) {
+        const uint32_t b = (uint32_t)__cvta_generic_to_shared(bars + P);
+        while (clock64() - t0 < 4000000000ull) {
+          uint32_t done;
+          asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+                       " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(b) : "memory");
+          if (done) break;
         }
       }
     }
   }
-  cl.sync();                                   // every remote store has landed before anyone exits
+  // no CTA exits while another may still store into its shared memory (every
+  // expected store was waited for on an mbarrier, so no ordering is needed)
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
 }
 
 size_t chol_inv_smem(int R) { return CholLayout(R).bytes(); }
@@ -1037,12 +1162,11 @@ void gram_df(const float* Ahi, const float* Alo, const float* Aw, const float* d
 
 void chol_df(const float* Shi, const float* Slo, const float* W, const float2* Gpk, int N, int n,
              int R, float2* Winv, float* Z, bool useV, int* status, Launch L) {
-  // 128 column threads plus about one update thread per eight packed entries
   const int T = R * (R + 1) / 2;
-  // the chain CTA needs 128 row threads and the pivot warp; the update and
-  // inverse CTAs use about one thread per eight packed entries
-  const int threads = std::min(CPALS_CHOL_THREADS, std::max(160, (T / 8 + 31) / 32 * 32));
-  chol_inv_df_kernel<<<3, threads, chol_inv_smem(R), L.stream>>>(Shi, Slo, W, Gpk, N, n, R, Winv,
+  // the chain CTA needs six warps (row threads in warps 1-3 and 5, the pivot
+  // warp 4); the other CTAs use about one thread per eight packed entries
+  const int threads = std::min(CPALS_CHOL_THREADS, std::max(192, (T / 8 + 31) / 32 * 32));
+  chol_inv_df_kernel<<<5, threads, chol_inv_smem(R), L.stream>>>(Shi, Slo, W, Gpk, N, n, R, Winv,
                                                                  Z, useV ? 1 : 0, status);
   (*L.counter)++;
 }
