@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-als", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -276,10 +277,10 @@ def run_ours(args):
                 ts.append(dist.max(e0.elapsed_time(e1) / 1e3))
                 ok = ok and out["reached"]
                 frac.append(float(np.mean(out["learned"])) if len(out["learned"]) else 0.0)
-            kinds = out["kinds"]
+            lk = out["kinds"]
             learned = {"value": round(statistics.mean(ts), 6), "unit": "s", "reached": ok,
-                       "sweeps": len(kinds),
-                       "sweep_counts": {k: kinds.count(k) for k in ("als", "pp_init", "pp_approx")},
+                       "sweeps": len(lk),
+                       "sweep_counts": {k: lk.count(k) for k in ("als", "pp_init", "pp_approx")},
                        "network_decisions": round(statistics.mean(frac), 3)}
             ctx.set_controller(None)
 
@@ -289,6 +290,11 @@ def run_ours(args):
     variants = None
     if not args.no_als and not args.no_variants and args.workload == "order3_400_rank100":
         variants = run_variants(args, dist, p, Xd, flush, max_sweeps)
+
+    # 256 small uneven tensors decomposed at once (cpals_run_batch)
+    batch = None
+    if not args.no_als and not args.no_batch and args.workload == "order3_400_rank100":
+        batch = run_batch_bench(args, dist, flush)
 
     # end to end through the C ABI from pinned host buffers
     Xh = torch.from_numpy(np.ascontiguousarray(p.X)).pin_memory()
@@ -352,6 +358,7 @@ def run_ours(args):
         "als_fp64_time_to_fitness": als64,
         "pp_learned_controller": learned,
         "variants": variants,
+        "batch": batch,
         "roofline": roofline,
         "e2e": {"value": round(statistics.mean(e2e_times), 6), "unit": "s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -371,6 +378,49 @@ def run_ours(args):
         print(json.dumps(result))
     ctx.close()
     dist.close()
+
+
+def run_batch_bench(args, dist, flush, workers=16):
+    import numpy as np
+    import torch
+
+    from paper_1811_10573_gb300 import cpals, synth
+
+    probs = synth.batch_order3(count=256, seed=dist.rank)
+    ctxs = []
+    try:
+        for q in probs:
+            g = cpals.CPALS(q.dims, q.R, args.precision)
+            g.set_tensor(torch.from_numpy(np.ascontiguousarray(q.X)).cuda())
+            ctxs.append(g)
+
+        def timed(w):
+            for g, q in zip(ctxs, probs):
+                g.init_factors(q.A0)
+            flush.zero_()
+            torch.cuda.synchronize()
+            dist.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fit, sw, st = cpals.run_batch(ctxs, workers=w, max_sweeps=probs[0].sweeps, eps=probs[0].eps)
+            e1.record()
+            torch.cuda.synchronize()
+            return dist.max(e0.elapsed_time(e1) / 1e3), fit, sw, st
+
+        timed(workers)                          # warm-up: every context captures its graphs
+        t_w, fit, sw, st = timed(workers)
+        t_1, fit1, sw1, st1 = timed(1)
+        same = bool(np.array_equal(fit, fit1) and np.array_equal(sw, sw1))
+        return {"workload": "batch_order3: 256 order-3 tensors, s_n ~ U{32..160}, R ~ U{8..64}, "
+                            "1e-2 relative noise, eps 0.1, 100 sweeps each (Algorithm 3 per tensor)",
+                "value": round(t_w, 4), "unit": "s", "workers": workers,
+                "decompositions_per_s": round(len(probs) / t_w, 1),
+                "sweeps_total": int(np.sum(sw)), "failed": int(np.sum(st != 0)),
+                "one_at_a_time_s": round(t_1, 4), "speedup_vs_one_at_a_time": round(t_1 / t_w, 2),
+                "same_results_as_one_at_a_time": same}
+    finally:
+        for g in ctxs:
+            g.close()
 
 
 def run_variants(args, dist, p, Xd, flush, max_sweeps):

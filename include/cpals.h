@@ -168,6 +168,23 @@ cpals_status cpals_run(cpals_ctx* ctx, int max_sweeps, double eps, int use_V, do
                        double* fitness_trace, int* kind_trace, double* time_trace,
                        int* n_done, int* reached);
 
+/* Many independent decompositions at once (tensors of different shapes, one
+ * context each, already given their tensor and factors): `workers` host
+ * threads take the contexts one after the other from a shared counter and
+ * run cpals_run(ctx, max_sweeps, eps, use_V, targets ? targets[i] : 0, ...)
+ * on each, on the contexts' own streams, so up to `workers` decompositions
+ * are in flight on the GPU and uneven ones balance themselves.  Every
+ * context keeps its own controller (Algorithm 3) and gets the result a lone
+ * cpals_run would give it.  Per instance (each output nullable, length n):
+ * fitness_out = the last fitness of its trace, sweeps_out = sweeps run,
+ * status_out = its cpals_status.  The contexts must all live on devices the
+ * calling process can use; none may be used by another thread meanwhile.
+ * Returns CPALS_E_INVALID for bad arguments, else CPALS_OK (per-instance
+ * failures are in status_out). */
+cpals_status cpals_run_batch(cpals_ctx* const* ctxs, int n, int workers, int max_sweeps, double eps,
+                             int use_V, const double* targets, double* fitness_out,
+                             int* sweeps_out, int* status_out);
+
 /* Message describing the last failure on this context ("" if none). */
 const char* cpals_last_error(const cpals_ctx* ctx);
 

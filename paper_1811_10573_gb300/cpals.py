@@ -40,6 +40,8 @@ _SIGS = {
     "cpals_fitness": (C.c_int, [_ctx_p, _dp]),
     "cpals_get_factors": (C.c_int, [_ctx_p, C.POINTER(_dp)]),
     "cpals_get_dA_ratios": (C.c_int, [_ctx_p, _dp]),
+    "cpals_run_batch": (C.c_int, [C.POINTER(_ctx_p), C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
+                                  _dp, _dp, _ip, _ip]),
     "cpals_run": (C.c_int, [_ctx_p, C.c_int, C.c_double, C.c_int, C.c_double, _dp, _ip, _dp,
                             _ip, _ip]),
     "cpals_last_error": (C.c_char_p, [_ctx_p]),
@@ -159,6 +161,30 @@ def cpals_get_dA_ratios(ctx, out):
 def cpals_run(ctx, max_sweeps, eps, use_V, target, ftrace, ktrace, ttrace, n_done, reached):
     return lib().cpals_run(ctx, max_sweeps, eps, use_V, target, ftrace, ktrace, ttrace, n_done,
                            reached)
+
+
+def cpals_run_batch(ctxs, n, workers, max_sweeps, eps, use_V, targets, fit, sweeps, status):
+    return lib().cpals_run_batch(ctxs, n, workers, max_sweeps, eps, use_V, targets, fit, sweeps,
+                                 status)
+
+
+def run_batch(contexts, workers, max_sweeps, eps, use_V=True, targets=None):
+    """Run Algorithm 3 on many contexts at once (cpals_run_batch).  Returns
+    per-instance final fitness, sweeps run and status (numpy arrays)."""
+    n = len(contexts)
+    arr = (_ctx_p * max(n, 1))(*[c.ctx for c in contexts])
+    fit = np.zeros(max(n, 1))
+    sw = np.zeros(max(n, 1), dtype=np.int32)
+    st = np.zeros(max(n, 1), dtype=np.int32)
+    tg = None
+    if targets is not None:
+        tg = np.ascontiguousarray(targets, dtype=np.float64)
+    rc = cpals_run_batch(arr, n, int(workers), int(max_sweeps), float(eps), 1 if use_V else 0,
+                         _dptr(tg) if tg is not None else None, _dptr(fit),
+                         sw.ctypes.data_as(_ip), st.ctypes.data_as(_ip))
+    if rc != 0:
+        raise CPALSError(rc, "cpals_run_batch: bad arguments")
+    return fit[:n], sw[:n], st[:n]
 
 
 CTRL_FEATURES = 20

@@ -4,11 +4,13 @@
 // tree for ALS), Sec. 3.2.3 (dimension tree for the PP operators), Eq. 3 (PP
 // update), Sec. 5 (fitness).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/cpals.h"
@@ -28,6 +30,7 @@ constexpr int kEvPairs = 16;
 struct cpals_ctx {
   // problem
   int N = 0, R = 0, prec = 0;
+  int dev = 0;          // device the context lives on
   int64_t dims[kMaxModes] = {0};
   int64_t total = 0;
   int h = 0;            // left half of the ALS tree: modes [0, h)
@@ -865,6 +868,7 @@ cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpal
   if (!(prop.major == 10 && prop.minor == 3)) return CPALS_E_UNSUPPORTED;
 
   cpals_ctx* c = new cpals_ctx();
+  c->dev = dev;
   c->N = N;
   c->R = R;
   c->prec = precision;
@@ -1017,6 +1021,47 @@ void cpals_destroy(cpals_ctx* c) {
 cpals_status cpals_set_stream(cpals_ctx* c, void* stream) {
   if (!c) return CPALS_E_INVALID;
   c->user = (cudaStream_t)stream;
+  return CPALS_OK;
+}
+
+// Many independent decompositions (tensors of different shapes, each with its
+// own context): worker threads take the next context from a shared counter
+// and run Algorithm 3 on it (cpals_run, on the context's own streams), so up
+// to `workers` decompositions are in flight on the GPU at once while each
+// keeps its own controller.  Uneven instances balance themselves; the result
+// of every instance is the one cpals_run gives it alone.
+cpals_status cpals_run_batch(cpals_ctx* const* ctxs, int n, int workers, int max_sweeps, double eps,
+                             int use_V, const double* targets, double* fitness_out,
+                             int* sweeps_out, int* status_out) {
+  if (!ctxs || n < 0 || workers < 1 || max_sweeps < 1) return CPALS_E_INVALID;
+  for (int i = 0; i < n; i++)
+    if (!ctxs[i]) return CPALS_E_INVALID;
+  // operator buffers before any worker captures a graph
+  for (int i = 0; i < n; i++) {
+    cpals_ctx* c = ctxs[i];
+    if (cudaSetDevice(c->dev) != cudaSuccess) return c->cuda_fail("cudaSetDevice", cudaGetLastError());
+    CKS(is64(c) ? pp_alloc<double>(c) : pp_alloc<float>(c));
+  }
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    std::vector<double> ft((size_t)max_sweeps);
+    while (true) {
+      const int i = next.fetch_add(1);
+      if (i >= n) break;
+      cpals_ctx* c = ctxs[i];
+      int nd = 0, rc = 0;
+      cpals_status st = cudaSetDevice(c->dev) == cudaSuccess ? CPALS_OK : CPALS_E_CUDA;
+      if (st == CPALS_OK)
+        st = cpals_run(c, max_sweeps, eps, use_V, targets ? targets[i] : 0.0, ft.data(), nullptr,
+                       nullptr, &nd, &rc);
+      if (fitness_out) fitness_out[i] = nd > 0 ? ft[nd - 1] : std::nan("");
+      if (sweeps_out) sweeps_out[i] = nd;
+      if (status_out) status_out[i] = (int)st;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 0; w < std::min(workers, n); w++) pool.emplace_back(work);
+  for (auto& t : pool) t.join();
   return CPALS_OK;
 }
 
