@@ -465,6 +465,12 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
   // phase completes instead of spinning on the pipe the pivot warp uses
   auto mwait = [&](uint64_t* bar, int code, uint32_t hint = 0) {
     const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    {
+      uint32_t done;   // fast path: already complete, no clock read
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+                   " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(b) : "memory");
+      if (done) return;
+    }
     const unsigned long long t0 = clock64();
     while (true) {
       uint32_t done;
@@ -481,6 +487,12 @@ chol_inv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
   // barriers completed by this CTA's own threads need only CTA-scope acquire
   auto mwait_cta = [&](uint64_t* bar, int code, uint32_t hint = 0) {
     const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    {
+      uint32_t done;
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+                   " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(b) : "memory");
+      if (done) return;
+    }
     const unsigned long long t0 = clock64();
     while (true) {
       uint32_t done;
