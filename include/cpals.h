@@ -284,10 +284,11 @@ cpals_status cpals_set_profiling(cpals_ctx* ctx, int enable);
 cpals_status cpals_reset_stats(cpals_ctx* ctx);
 
 /* Kernel statistics since the last reset.  kind 0 = first-level
- * contraction (all launches), 1 = all kernels of the library (count only).
- * *launches: number of launches; *total_ms: summed CUDA-event time (kind 0
- * only, profiling on); *bytes, *flops: algorithmic bytes moved and flops of
- * those launches (kind 0 only). */
+ * contraction (all launches), 1 = all kernels of the library (count only),
+ * 2 = PP correction kernels (Eq. 3 first-order terms).
+ * *launches: number of launches; *total_ms: summed CUDA-event time (kinds 0
+ * and 2, profiling on); *bytes, *flops: algorithmic bytes moved and flops of
+ * those launches (kinds 0 and 2; flops kind 0 only). */
 cpals_status cpals_get_stats(cpals_ctx* ctx, int kind, int64_t* launches, double* total_ms,
                              double* bytes, double* flops);
 

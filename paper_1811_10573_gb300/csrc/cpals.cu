@@ -113,11 +113,15 @@ struct cpals_ctx {
   bool profiling = false;
   cudaEvent_t ev0[kEvPairs] = {nullptr}, ev1[kEvPairs] = {nullptr};
   double ev_bytes[kEvPairs] = {0}, ev_flops[kEvPairs] = {0};
+  int ev_kind[kEvPairs] = {0};     // 0: first-level contraction, 2: PP correction
   double gev_bytes[G_SLOTS][kEvPairs] = {{0}}, gev_flops[G_SLOTS][kEvPairs] = {{0}};
+  int gev_kind[G_SLOTS][kEvPairs] = {{0}};
   int ev_used = 0;
   int64_t launches = 0;
   int64_t fl_launches = 0;
   double fl_ms = 0, fl_bytes = 0, fl_flops = 0;
+  int64_t pc_launches = 0;         // PP correction launches timed with events
+  double pc_ms = 0, pc_bytes = 0;
   int* umma_err = nullptr;
   int* umma_sched = nullptr;       // work counter of the tensor-core kernel (launches on stream)
   // learned controller
@@ -193,11 +197,12 @@ void ev_begin(cpals_ctx* c, int idx) {
   if (c->profiling && idx < kEvPairs)
     cudaEventRecordWithFlags(c->ev0[idx], c->stream, cudaEventRecordExternal);
 }
-void ev_end(cpals_ctx* c, int idx, double bytes, double flops) {
+void ev_end(cpals_ctx* c, int idx, double bytes, double flops, int kind = 0) {
   if (c->profiling && idx < kEvPairs) {
     cudaEventRecordWithFlags(c->ev1[idx], c->stream, cudaEventRecordExternal);
     c->ev_bytes[idx] = bytes;
     c->ev_flops[idx] = flops;
+    c->ev_kind[idx] = kind;
   }
 }
 // after the stream is synchronised: accumulate the recorded pairs
@@ -209,10 +214,16 @@ void ev_harvest(cpals_ctx* c) {
   for (int i = 0; i < c->ev_used && i < kEvPairs; i++) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->ev0[i], c->ev1[i]) == cudaSuccess) {
-      c->fl_ms += ms;
-      c->fl_launches++;
-      c->fl_bytes += c->ev_bytes[i];
-      c->fl_flops += c->ev_flops[i];
+      if (c->ev_kind[i] == 2) {
+        c->pc_ms += ms;
+        c->pc_launches++;
+        c->pc_bytes += c->ev_bytes[i];
+      } else {
+        c->fl_ms += ms;
+        c->fl_launches++;
+        c->fl_bytes += c->ev_bytes[i];
+        c->fl_flops += c->ev_flops[i];
+      }
     } else {
       cudaGetLastError();
     }
@@ -401,7 +412,7 @@ cpals_status als_sweep_launch(cpals_ctx* c) {
     CKS(tie_copy(c, n));
   }
   fitness<T>(last, c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->normX2, c->scal, c->dpart,
-             c->L());
+             c->tickets + 62, c->L());
   return CPALS_OK;
 }
 
@@ -427,7 +438,7 @@ cpals_status fitness_launch(cpals_ctx* c) {
   const T* last = nullptr;
   CKS(mttkrp_launch<T>(c, c->N - 1, &last));
   fitness<T>(last, c->A[c->N - 1], c->S, c->N, c->R, (int)c->dims[c->N - 1], c->normX2, c->scal,
-             c->dpart, c->L());
+             c->dpart, c->tickets + 62, c->L());
   return CPALS_OK;
 }
 
@@ -568,14 +579,21 @@ cpals_status pp_sweep_launch(cpals_ctx* c, bool useV) {
     if (skip && n != N - 1) continue;
     if (!skip) factor_async(c, n, true, useV);
     pp_terms<T>(c, n, terms);
+    // algorithmic bytes: every operator and dA^(i) once, M_p^(n) once, the result once
+    double pcb = 2.0 * (double)c->dims[n] * R * sizeof(T);
+    for (int i = 0; i < N; i++)
+      if (i != n) pcb += ((double)c->dims[i] * c->dims[n] * R + (double)c->dims[i] * R) * sizeof(T);
+    const int idx = c->ev_used++;
+    ev_begin(c, idx);
     pp_correct<T>(P<const T>(c->Mp[n]), terms, N - 1, P<T>(c->rhs), (int)c->dims[n], R, c->L());
+    ev_end(c, idx, pcb, 0.0, 2);
     if (skip) continue;                 // a tied last mode: M~ only feeds the fitness estimate
     finish_mode<T>(c, n, P<const T>(c->rhs), true, useV);
     CKS(tie_copy(c, n));
   }
   // fitness estimate from M~^(N) (the last right-hand side, updated factors)
   fitness<T>(P<const T>(c->rhs), c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->normX2,
-             c->scal, c->dpart, c->L());
+             c->scal, c->dpart, c->tickets + 62, c->L());
   return CPALS_OK;
 }
 
@@ -609,6 +627,7 @@ cpals_status run_slot(cpals_ctx* c, int slot, F&& body) {
     for (int i = 0; i < kEvPairs; i++) {
       c->gev_bytes[slot][i] = c->ev_bytes[i];
       c->gev_flops[slot][i] = c->ev_flops[i];
+      c->gev_kind[slot][i] = c->ev_kind[i];
     }
     c->launches = before;
   }
@@ -618,6 +637,7 @@ cpals_status run_slot(cpals_ctx* c, int slot, F&& body) {
   for (int i = 0; i < kEvPairs; i++) {
     c->ev_bytes[i] = c->gev_bytes[slot][i];
     c->ev_flops[i] = c->gev_flops[slot][i];
+    c->ev_kind[i] = c->gev_kind[slot][i];
   }
   return CPALS_OK;
 }
@@ -1622,6 +1642,8 @@ cpals_status cpals_reset_stats(cpals_ctx* c) {
   c->launches = 0;
   c->fl_launches = 0;
   c->fl_ms = c->fl_bytes = c->fl_flops = 0;
+  c->pc_launches = 0;
+  c->pc_ms = c->pc_bytes = 0;
   return CPALS_OK;
 }
 
@@ -1638,8 +1660,13 @@ cpals_status cpals_get_stats(cpals_ctx* c, int kind, int64_t* launches, double* 
     if (total_ms) *total_ms = 0;
     if (bytes) *bytes = 0;
     if (flops) *flops = 0;
+  } else if (kind == 2) {
+    if (launches) *launches = c->pc_launches;
+    if (total_ms) *total_ms = c->pc_ms;
+    if (bytes) *bytes = c->pc_bytes;
+    if (flops) *flops = 0;
   } else {
-    return c->fail(CPALS_E_INVALID, "kind must be 0 or 1");
+    return c->fail(CPALS_E_INVALID, "kind must be 0, 1 or 2");
   }
   return CPALS_OK;
 }

@@ -105,10 +105,11 @@ void gram_update(const double* A, const T* Ac, const T* dAc, double* S, double* 
 
 // Fitness from the last mode's right-hand side (Sec. 5):
 // inner = sum rhs*A, model = sum_{r,r'} prod_k S_k, out[0] = fitness, out[1] = inner,
-// out[2] = model.  partials: workspace (>= 2*256 doubles).
+// out[2] = model.  partials: workspace (>= 2*256 doubles); ticket: one zeroed
+// int (the last block resets it), shared only by launches on one stream.
 template <typename T>
 void fitness(const T* rhs, const double* A, const double* S, int N, int R, int s, double normX2,
-             double* out, double* partials, Launch L);
+             double* out, double* partials, int* ticket, Launch L);
 
 // ---------------------------------------------------------------- double-float (FP32/mixed modes)
 // The same normal-equation steps in double-float arithmetic (hi + lo floats)

@@ -337,9 +337,11 @@ gram_kernel(const double* __restrict__ A, const TW* __restrict__ Aw, const TW* _
 
 // ---------------------------------------------------------------- fitness
 template <typename T>
-__global__ void fitness_part_kernel(const T* __restrict__ rhs, const double* __restrict__ A,
-                                    const double* __restrict__ S, int N, int R, int s,
-                                    double* __restrict__ part) {
+__global__ void fitness_kernel(const T* __restrict__ rhs, const double* __restrict__ A,
+                               const double* __restrict__ S, int N, int R, int s,
+                               double* __restrict__ part, double normX2, double* __restrict__ out,
+                               int* __restrict__ ticket) {
+  // per block: <M^(N), A^(N)> and sum of the Hadamard product of the Grams
   const int64_t n1 = (int64_t)s * R;
   const int RR = R * R;
   double a = 0.0, b = 0.0;
@@ -352,6 +354,7 @@ __global__ void fitness_part_kernel(const T* __restrict__ rhs, const double* __r
     b += h;
   }
   __shared__ double ra[256], rb[256];
+  __shared__ int last;
   ra[threadIdx.x] = a;
   rb[threadIdx.x] = b;
   __syncthreads();
@@ -365,21 +368,24 @@ __global__ void fitness_part_kernel(const T* __restrict__ rhs, const double* __r
   if (threadIdx.x == 0) {
     part[2 * blockIdx.x] = ra[0];
     part[2 * blockIdx.x + 1] = rb[0];
+    __threadfence();
+    last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
   }
-}
-
-__global__ void fitness_final_kernel(const double* __restrict__ part, int nparts, double normX2,
-                                     double* __restrict__ out) {
-  __shared__ double ra[256], rb[256];
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+  __syncthreads();
+  if (!last) return;
+  // the last block sums the partials in block order (deterministic) and
+  // resets the ticket for the next launch
+  __threadfence();
+  a = 0.0;
+  b = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
     a += part[2 * i];
     b += part[2 * i + 1];
   }
   ra[threadIdx.x] = a;
   rb[threadIdx.x] = b;
   __syncthreads();
-  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+  for (int st = 128; st > 0; st >>= 1) {
     if ((int)threadIdx.x < st) {
       ra[threadIdx.x] += ra[threadIdx.x + st];
       rb[threadIdx.x] += rb[threadIdx.x + st];
@@ -392,6 +398,7 @@ __global__ void fitness_final_kernel(const double* __restrict__ part, int nparts
     out[0] = 1.0 - sqrt(fmax(res2, 0.0)) / sqrt(normX2);
     out[1] = inner;
     out[2] = model;
+    *ticket = 0;
   }
 }
 
@@ -477,11 +484,9 @@ void gram_update(const double* A, const T* Ac, const T* dAc, double* S, double* 
 
 template <typename T>
 void fitness(const T* rhs, const double* A, const double* S, int N, int R, int s, double normX2,
-             double* out, double* partials, Launch L) {
-  const int blocks = 128;
-  fitness_part_kernel<T><<<blocks, 256, 0, L.stream>>>(rhs, A, S, N, R, s, partials);
-  fitness_final_kernel<<<1, 128, 0, L.stream>>>(partials, blocks, normX2, out);
-  (*L.counter) += 2;
+             double* out, double* partials, int* ticket, Launch L) {
+  fitness_kernel<T><<<128, 256, 0, L.stream>>>(rhs, A, S, N, R, s, partials, normX2, out, ticket);
+  (*L.counter) += 1;
 }
 
 #define INST(T)                                                                                 \
@@ -494,7 +499,7 @@ void fitness(const T* rhs, const double* A, const double* S, int N, int R, int s
   template void gram_update<T>(const double*, const T*, const T*, double*, double*, bool, int,  \
                                int, const double*, double*, double*, int*, Launch);             \
   template void fitness<T>(const T*, const double*, const double*, int, int, int, double,       \
-                           double*, double*, Launch);
+                           double*, double*, int*, Launch);
 INST(double)
 INST(float)
 #undef INST
