@@ -190,6 +190,32 @@ def symmetric_order3(sa, sb, R, *, seed=0, noise=1e-2, collinearity=None, storag
                    A0, R, eps, sweeps, storage, meta)
 
 
+def orthonormal(s, R, seed, stream):
+    """An s x R matrix with orthonormal columns (QR of a Gaussian matrix)."""
+    Q, _ = np.linalg.qr(_rng(seed, stream).standard_normal((s, R)))
+    return Q
+
+
+def tucker_problem(dims, ranks, *, seed=0, noise=1e-2, storage="f64", eps=0.3, sweeps=20,
+                   name=None) -> Problem:
+    """X = [[G; A^(1), ..., A^(N)]] + noise (Sec. 2.4): core G N(0,1), factors
+    with orthonormal columns, noise relative to ||X||.  A0: random
+    orthonormal factors (the paper starts from HOSVD, which the tests compute
+    with the oracle).  Problem.R holds the ranks."""
+    dims = [int(d) for d in dims]
+    G = _rng(seed, 8).standard_normal(tuple(int(r) for r in ranks))
+    At = [orthonormal(s, r, seed, 20 + k) for k, (s, r) in enumerate(zip(dims, ranks))]
+    X = G
+    for k, A in enumerate(At):
+        X = np.moveaxis(np.tensordot(X, A, axes=([k], [1])), -1, k)
+    if noise:
+        X = add_noise(X, noise, seed)
+    A0 = [orthonormal(s, r, seed, 40 + k) for k, (s, r) in enumerate(zip(dims, ranks))]
+    Xs = X.astype(np.float32) if storage == "f32" else X
+    return Problem(name or "tucker", np.ascontiguousarray(Xs), A0, list(ranks), eps, sweeps, storage,
+                   {"ranks": list(ranks)})
+
+
 def batch_order3(count=256, seed=0, smin=32, smax=160, rmin=8, rmax=64):
     """Many small order-3 problems with per-mode sizes U{smin..smax} and ranks
     U{rmin..rmax}, FP32, 1e-2 relative noise, 100 sweeps each."""

@@ -531,3 +531,98 @@ def test_pp_init_first_mode_equals_als_with_step_size():
     np.testing.assert_allclose(A_pp[0], A[0], rtol=1e-11, atol=1e-12)
     assert not np.allclose(A_pp[0], O.solve_normal(O.mttkrp(p.X, p.A0, 0),
                                                    O.gamma([O.gram(a) for a in p.A0], 0)))
+
+
+# --- Tucker-ALS and PP-Tucker-ALS (Sec. 2.4, Sec. 3.1.2, Sec. 3.2.2) ----------
+
+from oracle import tucker_oracle as TO  # noqa: E402
+
+
+def test_tucker_ttmc_brute_force():
+    g = np.random.default_rng(61)
+    X = g.standard_normal((3, 4, 5))
+    A = [g.standard_normal((3, 2)), g.standard_normal((4, 2)), g.standard_normal((5, 3))]
+    for n in range(3):
+        Y = TO.ttmc(X, A, n)
+        ref = np.zeros(Y.shape)
+        for idx in itertools.product(*[range(s) for s in X.shape]):
+            for out in itertools.product(*[range(d) for d in Y.shape]):
+                if out[n] != idx[n]:
+                    continue
+                w = X[idx]
+                for k in range(3):
+                    if k != n:
+                        w *= A[k][idx[k], out[k]]
+                ref[out] += w
+        np.testing.assert_allclose(Y, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_tucker_hosvd_recovers_exact_multilinear_rank():
+    p = synth.tucker_problem([12, 10, 9], [3, 4, 2], seed=3, noise=0.0)
+    A = TO.hosvd(p.X, p.R)
+    G = TO.core(p.X, A)
+    normX = float(np.linalg.norm(p.X))
+    assert TO.fitness(normX, G) > 1 - 1e-7
+    np.testing.assert_allclose(TO.reconstruct(G, A), p.X, rtol=0, atol=1e-10 * normX)
+    for a in A:
+        np.testing.assert_allclose(a.T @ a, np.eye(a.shape[1]), atol=1e-12)
+
+
+def test_tucker_hooi_core_norm_nondecreasing_and_fitness_identity():
+    """HOOI never decreases ||G|| (Sec. 4.2), and with orthonormal factors the
+    fitness from ||G|| equals the explicit residual."""
+    p = synth.tucker_problem([14, 12, 10], [3, 3, 2], seed=4, noise=0.3)
+    A = [a.copy() for a in p.A0]
+    normX = float(np.linalg.norm(p.X))
+    last = -1.0
+    for _ in range(6):
+        _, G = TO.als_sweep(p.X, A)
+        gn = float(np.linalg.norm(G))
+        assert gn >= last - 1e-12
+        last = gn
+        explicit = 1 - np.linalg.norm(p.X - TO.reconstruct(G, A)) / normX
+        assert abs(TO.fitness(normX, G) - explicit) < 1e-12
+
+
+def test_tucker_gram_eigvecs_span_the_svd_subspace():
+    g = np.random.default_rng(62)
+    Y = g.standard_normal((15, 40))
+    V = TO.leading_eigvecs(Y @ Y.T, 4)
+    U = np.linalg.svd(Y, full_matrices=False)[0][:, :4]
+    np.testing.assert_allclose(V @ V.T, U @ U.T, atol=1e-12)
+    np.testing.assert_allclose(np.abs(V.T @ U), np.eye(4), atol=1e-10)
+
+
+def test_pp_tucker_exact_at_zero_and_second_order():
+    """Order 3: Y^(n)(A_p + dA) = Y~^(n) + X x_i dA^(i)T x_j dA^(j)T exactly
+    (the expansion of Sec. 3.1.2 has four terms), so Y~ is exact at dA = 0
+    and its error is the product term."""
+    g = np.random.default_rng(63)
+    X = g.standard_normal((7, 6, 5))
+    Ap = [np.linalg.qr(g.standard_normal((s, r)))[0] for s, r in zip(X.shape, (3, 2, 2))]
+    ops, Mp = TO.pp_operators(X, Ap)
+    D = [g.standard_normal(a.shape) for a in Ap]
+    for n in range(3):
+        zero = [np.zeros_like(a) for a in Ap]
+        np.testing.assert_allclose(TO.pp_ttmc(ops, Mp, zero, n), TO.ttmc(X, Ap, n), atol=1e-12)
+        for t in (1e-2, 0.3):
+            dA = [t * d for d in D]
+            A = [a + d for a, d in zip(Ap, dA)]
+            i, j = [k for k in range(3) if k != n]
+            product = TO.ttm(TO.ttm(X, dA[i], i), dA[j], j)
+            np.testing.assert_allclose(TO.ttmc(X, A, n) - TO.pp_ttmc(ops, Mp, dA, n), product,
+                                       rtol=1e-10, atol=1e-12)
+
+
+def test_pp_tucker_als_tracks_hooi():
+    p = synth.tucker_problem([16, 14, 12], [3, 3, 2], seed=5, noise=0.05)
+    A0 = TO.hosvd(p.X, p.R)
+    _, kinds, fit = TO.pp_tucker_als(p.X, A0, 20, eps=0.3)
+    A = [a.copy() for a in A0]
+    normX = float(np.linalg.norm(p.X))
+    als = []
+    for _ in range(20):
+        _, G = TO.als_sweep(p.X, A)
+        als.append(TO.fitness(normX, G))
+    assert "pp_approx" in kinds
+    assert max(abs(a - b) for a, b in zip(fit, als)) < 1e-6
