@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-als", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-tucker", action="store_true")
     return ap.parse_args()
 
 
@@ -297,6 +298,11 @@ def run_ours(args):
     if not args.no_als and not args.no_batch and args.workload == "order3_400_rank100":
         batch = run_batch_bench(args, dist, flush)
 
+    # PP-Tucker-ALS (Algorithm 4) vs Tucker-ALS on a 400^3 float64 tensor
+    tucker = None
+    if not args.no_als and not args.no_tucker and args.workload == "order3_400_rank100":
+        tucker = run_tucker_bench(args, dist, flush)
+
     # end to end through the C ABI from pinned host buffers
     Xh = torch.from_numpy(np.ascontiguousarray(p.X)).pin_memory()
     e2e_times = []
@@ -369,6 +375,7 @@ def run_ours(args):
         "pp_learned_controller": learned,
         "variants": variants,
         "batch": batch,
+        "tucker": tucker,
         "roofline": roofline,
         "roofline_pp_correct": roofline_pp,
         "e2e": {"value": round(statistics.mean(e2e_times), 6), "unit": "s",
@@ -432,6 +439,56 @@ def run_batch_bench(args, dist, flush, workers=16):
     finally:
         for g in ctxs:
             g.close()
+
+
+def run_tucker_bench(args, dist, flush, s=400, R=20, sweeps=20, eps=0.3):
+    """Tucker rank R = 0.05 s on an order-3 s^3 tensor (the paper's Tucker
+    sweep-time setting), float64: mean time of each sweep kind, and a budget
+    of sweeps with PP (eps 0.3, the paper's Tucker tolerance) and without."""
+    import numpy as np
+    import torch
+
+    from paper_1811_10573_gb300 import cpals, synth
+
+    p = synth.tucker_problem([s] * 3, [R] * 3, seed=dist.rank, noise=0.3)
+    Xd = torch.from_numpy(np.ascontiguousarray(p.X)).cuda()
+
+    def ev_time(fn):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, out
+
+    with cpals.Tucker([s] * 3, [R] * 3) as t:
+        t.set_tensor(Xd)
+        t.init_factors(p.A0)
+        for _ in range(3):
+            t.als_sweep()
+        als = [ev_time(t.als_sweep)[0] for _ in range(5)]
+        build = [ev_time(t.pp_build_operators)[0] for _ in range(3)]
+        pps = [ev_time(t.pp_sweep)[0] for _ in range(5)]
+        runs = {}
+        for name, e in (("pp", eps), ("als", 0.0)):
+            t.init_factors(p.A0)
+            t.run(2, e)                                  # warm-up
+            t.init_factors(p.A0)
+            torch.cuda.synchronize()
+            dist.barrier()
+            dt, out = ev_time(lambda: t.run(sweeps, e))
+            runs[name] = {"value": round(dist.max(dt), 6), "unit": "s", "sweeps": len(out["kinds"]),
+                          "sweep_counts": {k: out["kinds"].count(k) for k in ("als", "pp_init", "pp_approx")},
+                          "final_fitness": t.fitness()}
+    ms = lambda v: round(statistics.mean(v) * 1e3, 3)
+    return {"workload": f"tucker_order3_{s}_rank{R}: X = [[G; A1, A2, A3]] + 0.3 relative noise, "
+                        f"float64, random orthonormal start, {sweeps} sweeps",
+            "sweep_ms": {"als": ms(als), "pp_build": ms(build), "pp_approx": ms(pps)},
+            "pp_approx_vs_als_sweep": round(statistics.mean(als) / statistics.mean(pps), 2),
+            "pp": runs["pp"], "als": runs["als"],
+            "pp_vs_als_speedup": round(runs["als"]["value"] / runs["pp"]["value"], 3)}
 
 
 def run_variants(args, dist, p, Xd, flush, max_sweeps):

@@ -185,6 +185,43 @@ cpals_status cpals_run_batch(cpals_ctx* const* ctxs, int n, int workers, int max
                              int use_V, const double* targets, double* fitness_out,
                              int* sweeps_out, int* status_out);
 
+/* ---- Tucker-ALS and PP-Tucker-ALS (Sec. 2.4, Sec. 3.1.2, Algorithm 4) ----
+ * Order-3 tensors, IEEE float64, Tucker ranks 1 <= R_n <= min(48, s_n),
+ * s_n <= 4096.  Factors are s_n x R_n float64 row-major with orthonormal
+ * columns; the core is R_1 x R_2 x R_3 row-major.  Each factor update takes
+ * the R_n leading eigenvectors of W = Y_(n) Y_(n)^T (Y^(n) the TTMc) in
+ * decreasing eigenvalue order, each column signed to a non-negative inner
+ * product with the column it replaces; the eigenvectors come from subspace
+ * iteration started at the current factor (cpals_tucker_set_iterations,
+ * default 8) and a Rayleigh-Ritz step, so a factor is exact once the
+ * iteration has converged (a spectral gap after R_n).  Fitness: 1 -
+ * sqrt(||X||^2 - ||G||^2) / ||X||.  Errors as for the CP context;
+ * CPALS_E_SINGULAR if an orthonormalisation met a non-positive pivot. */
+typedef struct cpals_tucker cpals_tucker;
+cpals_status cpals_tucker_create(const int64_t* dims, int N, const int* ranks, cpals_tucker** out);
+void cpals_tucker_destroy(cpals_tucker* t);
+cpals_status cpals_tucker_set_iterations(cpals_tucker* t, int iters);
+/* data: row-major, last mode fastest; dtype 0 = float64, 1 = float32 (copied) */
+cpals_status cpals_tucker_set_tensor(cpals_tucker* t, const void* data, int dtype, int on_device);
+/* three host arrays (orthonormal columns; e.g. the HOSVD); dA <- A (Algorithm 4 line 2) */
+cpals_status cpals_tucker_init_factors(cpals_tucker* t, const double* const* factors);
+/* one HOOI sweep (Algorithm 2); *fitness (nullable) exact */
+cpals_status cpals_tucker_als_sweep(cpals_tucker* t, double* fitness);
+/* Y_p^(i,n) and Y_p^(n) at the current factors; A_p <- A, dA <- 0 */
+cpals_status cpals_tucker_pp_build_operators(cpals_tucker* t);
+/* one PP approximated sweep; *fitness (nullable) the estimate from Y~^(3) */
+cpals_status cpals_tucker_pp_sweep(cpals_tucker* t, double* fitness);
+/* Algorithm 4 for max_sweeps sweeps (eps as in cpals_run); traces nullable,
+ * length max_sweeps; kinds CPALS_SWEEP_* */
+cpals_status cpals_tucker_run(cpals_tucker* t, int max_sweeps, double eps, double* fitness_trace,
+                              int* kind_trace, int* n_done);
+/* exact fitness at the current factors (also refreshes the core) */
+cpals_status cpals_tucker_fitness(cpals_tucker* t, double* out);
+cpals_status cpals_tucker_get_factors(cpals_tucker* t, double* const* out);
+/* the core of the last sweep or fitness call */
+cpals_status cpals_tucker_get_core(cpals_tucker* t, double* out);
+const char* cpals_tucker_last_error(const cpals_tucker* t);
+
 /* Message describing the last failure on this context ("" if none). */
 const char* cpals_last_error(const cpals_ctx* ctx);
 

@@ -58,6 +58,19 @@ _SIGS = {
     "cpals_set_step_size": (C.c_int, [_ctx_p, _dp]),
     "cpals_set_symmetric": (C.c_int, [_ctx_p, C.c_int, C.c_int]),
     "cpals_set_controller": (C.c_int, [_ctx_p, _fp, C.c_int, C.c_double]),
+    "cpals_tucker_create": (C.c_int, [_i64p, C.c_int, _ip, C.POINTER(_ctx_p)]),
+    "cpals_tucker_destroy": (None, [_ctx_p]),
+    "cpals_tucker_set_iterations": (C.c_int, [_ctx_p, C.c_int]),
+    "cpals_tucker_set_tensor": (C.c_int, [_ctx_p, C.c_void_p, C.c_int, C.c_int]),
+    "cpals_tucker_init_factors": (C.c_int, [_ctx_p, C.POINTER(_dp)]),
+    "cpals_tucker_als_sweep": (C.c_int, [_ctx_p, _dp]),
+    "cpals_tucker_pp_build_operators": (C.c_int, [_ctx_p]),
+    "cpals_tucker_pp_sweep": (C.c_int, [_ctx_p, _dp]),
+    "cpals_tucker_run": (C.c_int, [_ctx_p, C.c_int, C.c_double, _dp, _ip, _ip]),
+    "cpals_tucker_fitness": (C.c_int, [_ctx_p, _dp]),
+    "cpals_tucker_get_factors": (C.c_int, [_ctx_p, C.POINTER(_dp)]),
+    "cpals_tucker_get_core": (C.c_int, [_ctx_p, _dp]),
+    "cpals_tucker_last_error": (C.c_char_p, [_ctx_p]),
     "cpals_run_controlled": (C.c_int, [_ctx_p, C.c_int, C.c_double, C.c_int, C.c_double, _dp,
                                        _ip, _dp, _ip, _ip, _ip]),
     "cpals_controller_log": (C.c_int, [_ctx_p, C.c_int, C.c_double, C.c_int, _fp, _ip, _dp, _dp,
@@ -512,3 +525,153 @@ class CPALS:
 def cost_model(dims, R, kind):
     """Host-only flop model (see cpals_cost_model)."""
     return cpals_cost_model(dims, len(dims), R, kind)
+
+
+# ---------------------------------------------------------------- Tucker (order 3, float64)
+def cpals_tucker_create(dims, ranks):
+    d = (C.c_int64 * 3)(*[int(x) for x in dims])
+    r = (C.c_int * 3)(*[int(x) for x in ranks])
+    out = _ctx_p()
+    st = lib().cpals_tucker_create(d, 3, r, C.byref(out))
+    return st, out
+
+
+def cpals_tucker_destroy(t):
+    lib().cpals_tucker_destroy(t)
+
+
+def cpals_tucker_set_iterations(t, iters):
+    return lib().cpals_tucker_set_iterations(t, iters)
+
+
+def cpals_tucker_set_tensor(t, ptr, dtype, on_device):
+    return lib().cpals_tucker_set_tensor(t, C.c_void_p(int(ptr)), dtype, on_device)
+
+
+def cpals_tucker_init_factors(t, factors):
+    arr = (_dp * 3)(*[_dptr(f) for f in factors])
+    return lib().cpals_tucker_init_factors(t, arr)
+
+
+def cpals_tucker_als_sweep(t, fit):
+    return lib().cpals_tucker_als_sweep(t, fit)
+
+
+def cpals_tucker_pp_build_operators(t):
+    return lib().cpals_tucker_pp_build_operators(t)
+
+
+def cpals_tucker_pp_sweep(t, fit):
+    return lib().cpals_tucker_pp_sweep(t, fit)
+
+
+def cpals_tucker_run(t, max_sweeps, eps, ftrace, ktrace, n_done):
+    return lib().cpals_tucker_run(t, max_sweeps, eps, ftrace, ktrace, n_done)
+
+
+def cpals_tucker_fitness(t, out):
+    return lib().cpals_tucker_fitness(t, out)
+
+
+def cpals_tucker_get_factors(t, out):
+    return lib().cpals_tucker_get_factors(t, out)
+
+
+def cpals_tucker_get_core(t, out):
+    return lib().cpals_tucker_get_core(t, out)
+
+
+def cpals_tucker_last_error(t):
+    s = lib().cpals_tucker_last_error(t)
+    return s.decode() if s else ""
+
+
+class Tucker:
+    """Order-3 Tucker-ALS / PP-Tucker-ALS context in float64 (owns its device memory)."""
+
+    def __init__(self, dims, ranks):
+        self.dims = [int(d) for d in dims]
+        self.ranks = [int(r) for r in ranks]
+        st, t = cpals_tucker_create(self.dims, self.ranks)
+        if st != 0:
+            raise CPALSError(st, "cpals_tucker_create failed")
+        self.t = t
+
+    def _ck(self, st):
+        if st != 0:
+            raise CPALSError(st, cpals_tucker_last_error(self.t))
+
+    def close(self):
+        if self.t:
+            cpals_tucker_destroy(self.t)
+            self.t = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_iterations(self, iters):
+        self._ck(cpals_tucker_set_iterations(self.t, int(iters)))
+
+    def set_tensor(self, X):
+        if hasattr(X, "data_ptr"):
+            import torch
+            assert X.is_contiguous()
+            dt = {torch.float64: 0, torch.float32: 1}[X.dtype]
+            self._ck(cpals_tucker_set_tensor(self.t, X.data_ptr(), dt, 1 if X.is_cuda else 0))
+            return
+        X = np.ascontiguousarray(X)
+        dt = {np.dtype(np.float64): 0, np.dtype(np.float32): 1}[X.dtype]
+        self._ck(cpals_tucker_set_tensor(self.t, X.ctypes.data, dt, 0))
+
+    def init_factors(self, factors):
+        fs = [_f64(f) for f in factors]
+        for f, s, r in zip(fs, self.dims, self.ranks):
+            assert f.shape == (s, r)
+        self._ck(cpals_tucker_init_factors(self.t, fs))
+
+    def als_sweep(self):
+        f = C.c_double()
+        self._ck(cpals_tucker_als_sweep(self.t, C.byref(f)))
+        return f.value
+
+    def pp_build_operators(self):
+        self._ck(cpals_tucker_pp_build_operators(self.t))
+
+    def pp_sweep(self):
+        f = C.c_double()
+        self._ck(cpals_tucker_pp_sweep(self.t, C.byref(f)))
+        return f.value
+
+    def run(self, max_sweeps, eps):
+        ft = np.zeros(max(max_sweeps, 1))
+        kt = np.zeros(max(max_sweeps, 1), dtype=np.int32)
+        nd = C.c_int()
+        self._ck(cpals_tucker_run(self.t, int(max_sweeps), float(eps), _dptr(ft),
+                                  kt.ctypes.data_as(_ip), C.byref(nd)))
+        n = nd.value
+        return {"fitness": ft[:n], "kinds": [SWEEP_KINDS[int(k)] for k in kt[:n]]}
+
+    def fitness(self):
+        f = C.c_double()
+        self._ck(cpals_tucker_fitness(self.t, C.byref(f)))
+        return f.value
+
+    def get_factors(self):
+        out = [np.empty((s, r)) for s, r in zip(self.dims, self.ranks)]
+        arr = (_dp * 3)(*[_dptr(o) for o in out])
+        self._ck(cpals_tucker_get_factors(self.t, arr))
+        return out
+
+    def get_core(self):
+        out = np.empty(tuple(self.ranks))
+        self._ck(cpals_tucker_get_core(self.t, _dptr(out)))
+        return out

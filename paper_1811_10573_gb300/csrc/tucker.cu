@@ -1,0 +1,751 @@
+// Tucker-ALS (HOOI, Algorithm 2) and pairwise-perturbation Tucker-ALS
+// (Algorithm 4) for order-3 tensors in IEEE float64.
+//
+// Per sweep (Sec. 2.4 with the dimension tree of Sec. 2.5):
+//   T  = X x_3 A3        [x1][x2][r3]   first level for modes 1 and 2
+//   Y1 = T x_2 A2        [x1][r3][r2]
+//   Y2 = T x_1 A1        [x2][r3][r1]   (A1 already updated)
+//   U  = X x_1 A1        [x2][x3][r1]   first level for mode 3
+//   Y3 = U x_2 A2        [x3][r1][r2]
+//   G  = Y3 x_3 A3       [r1][r2][r3]
+// (x_n A: contraction of mode n with the rows of A; 1-based in this comment.)
+// Each factor update takes the R_n leading eigenvectors of the Gram matrix
+// W = Y_(n) Y_(n)^T (the paper's reading of the leading left singular
+// vectors) by subspace iteration started from the current factor (the
+// W-products orthonormalised by Cholesky QR), then a Rayleigh-Ritz step
+// whose R_n x R_n eigenproblem is solved by parallel cyclic Jacobi on one
+// CTA; eigenvectors in decreasing eigenvalue order, each column signed to
+// a non-negative inner product with the column it replaces.
+//
+// PP (Sec. 3.1.2): operators Y_p^(i,n) = X x_k A_p^(k) (k the third mode)
+// and Y_p^(n); a PP sweep forms Y~^(n) = Y_p^(n) + sum_i Y_p^(i,n) x_i dA^(i)
+// in the layouts above and updates as in ALS.  Fitness: 1 - sqrt(||X||^2 -
+// ||G||^2) / ||X|| (orthonormal factors).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cpals.h"
+#include "internal.h"
+
+namespace cpals {
+namespace {
+
+inline int64_t cdivt(int64_t a, int64_t b) { return (a + b - 1) / b; }
+constexpr int kTuckerMaxRank = 48;
+
+// W[i][j] = sum_k Y[i K + k] Y[j K + k], 32 x 32 output tiles, K in chunks of 32
+__global__ void __launch_bounds__(256) syrk_kernel(const double* __restrict__ Y, int s, int K,
+                                                   double* __restrict__ W) {
+  __shared__ double a[32][33], b[32][33];
+  const int ti = blockIdx.y * 32, tj = blockIdx.x * 32;
+  if (tj < ti) return;                       // upper tiles; mirrored below
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 rows of threads
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      const int i = ti + r, j = tj + r, k = k0 + tx;
+      a[r][tx] = (i < s && k < K) ? Y[(int64_t)i * K + k] : 0.0;
+      b[r][tx] = (j < s && k < K) ? Y[(int64_t)j * K + k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; k++)
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[q] = fma(a[ty + 8 * q][k], b[tx][k], acc[q]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int i = ti + ty + 8 * q, j = tj + tx;
+    if (i < s && j < s) {
+      W[(int64_t)i * s + j] = acc[q];
+      W[(int64_t)j * s + i] = acc[q];
+    }
+  }
+}
+
+// C[a][b] = sum_i P[i R + a] Q[i R + b]  (R x R, one thread per entry)
+__global__ void atb_kernel(const double* __restrict__ P, const double* __restrict__ Q, int s, int R,
+                           double* __restrict__ C) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= R * R) return;
+  const int a = e / R, b = e % R;
+  double acc = 0.0;
+  for (int i = 0; i < s; i++) acc = fma(P[(int64_t)i * R + a], Q[(int64_t)i * R + b], acc);
+  C[e] = acc;
+}
+
+// Cholesky C = L L^T of an R x R SPD matrix (one CTA); L (lower) to Lout.
+// A non-positive pivot sets bit 0 of *status.
+__global__ void chol_small_kernel(const double* __restrict__ C, int R, double* __restrict__ Lout,
+                                  int* __restrict__ status) {
+  __shared__ double L[kTuckerMaxRank][kTuckerMaxRank + 1];
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) L[e / R][e % R] = C[e];
+  __syncthreads();
+  for (int k = 0; k < R; k++) {
+    if (threadIdx.x == 0) {
+      const double d = L[k][k];
+      if (!(d > 0.0)) atomicOr(status, 1);
+      L[k][k] = sqrt(fmax(d, 1e-300));
+    }
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < R; i += blockDim.x) L[i][k] /= L[k][k];
+    __syncthreads();
+    for (int e = threadIdx.x; e < (R - k - 1) * (R - k - 1); e += blockDim.x) {
+      const int i = k + 1 + e / (R - k - 1), j = k + 1 + e % (R - k - 1);
+      if (j <= i) L[i][j] = fma(-L[i][k], L[j][k], L[i][j]);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    const int i = e / R, j = e % R;
+    Lout[e] = j <= i ? L[i][j] : 0.0;
+  }
+}
+
+// Q = Z L^-T row by row: q L^T = z (forward substitution), one warp per row
+__global__ void rowsolve_lt_kernel(const double* __restrict__ Z, const double* __restrict__ Lg, int s,
+                                   int R, double* __restrict__ Q) {
+  __shared__ double L[kTuckerMaxRank][kTuckerMaxRank + 1];
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) L[e / R][e % R] = Lg[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = blockIdx.x * nw + warp; i < s; i += gridDim.x * nw) {
+    double z0 = lane < R ? Z[(int64_t)i * R + lane] : 0.0;
+    double z1 = lane + 32 < R ? Z[(int64_t)i * R + lane + 32] : 0.0;
+    for (int k = 0; k < R; k++) {
+      const double zk = __shfl_sync(0xffffffffu, k < 32 ? z0 : z1, k & 31) / L[k][k];
+      if (k < 32) { if (lane == k) z0 = zk; } else { if (lane == k - 32) z1 = zk; }
+      if (lane > k && lane < R) z0 = fma(-L[lane][k], zk, z0);
+      if (lane + 32 > k && lane + 32 < R) z1 = fma(-L[lane + 32][k], zk, z1);
+    }
+    if (lane < R) Q[(int64_t)i * R + lane] = z0;
+    if (lane + 32 < R) Q[(int64_t)i * R + lane + 32] = z1;
+  }
+}
+
+// Eigen-decomposition of the symmetric R x R matrix H (one CTA): parallel
+// cyclic Jacobi (round-robin pairing, R/2 disjoint rotations per step,
+// fixed 12 sweeps), then V's columns sorted by decreasing eigenvalue.
+__global__ void jacobi_kernel(const double* __restrict__ Hg, int R, double* __restrict__ Vout,
+                              double* __restrict__ lam_out) {
+  __shared__ double A[kTuckerMaxRank][kTuckerMaxRank + 1], V[kTuckerMaxRank][kTuckerMaxRank + 1];
+  __shared__ double cs[kTuckerMaxRank / 2][2];
+  __shared__ int pp[kTuckerMaxRank / 2][2];
+  __shared__ int perm[kTuckerMaxRank + 1];
+  __shared__ double lam[kTuckerMaxRank];
+  const int Re = R + (R & 1);                // even number of slots (a dummy when R is odd)
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+    A[e / R][e % R] = Hg[e];
+    V[e / R][e % R] = (e / R == e % R) ? 1.0 : 0.0;
+  }
+  for (int i = threadIdx.x; i < Re; i += blockDim.x) perm[i] = i;
+  __syncthreads();
+  for (int sweep = 0; sweep < 12; sweep++) {
+    for (int step = 0; step < Re - 1; step++) {
+      // pairs of this step: (perm[k], perm[Re-1-k])
+      for (int k = threadIdx.x; k < Re / 2; k += blockDim.x) {
+        int p = perm[k], q = perm[Re - 1 - k];
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, sn = 0.0;
+        if (q < R) {
+          const double apq = A[p][q];
+          if (apq != 0.0) {
+            const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+        }
+        pp[k][0] = p;
+        pp[k][1] = q;
+        cs[k][0] = c;
+        cs[k][1] = sn;
+      }
+      __syncthreads();
+      // rows: A <- J^T A (each pair's two rows, all columns)
+      for (int e = threadIdx.x; e < (Re / 2) * R; e += blockDim.x) {
+        const int k = e / R, j = e % R, p = pp[k][0], q = pp[k][1];
+        if (q >= R) continue;
+        const double c = cs[k][0], sn = cs[k][1];
+        const double ap = A[p][j], aq = A[q][j];
+        A[p][j] = c * ap - sn * aq;
+        A[q][j] = sn * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int e = threadIdx.x; e < (Re / 2) * R; e += blockDim.x) {
+        const int k = e / R, i = e % R, p = pp[k][0], q = pp[k][1];
+        if (q >= R) continue;
+        const double c = cs[k][0], sn = cs[k][1];
+        const double ap = A[i][p], aq = A[i][q];
+        A[i][p] = c * ap - sn * aq;
+        A[i][q] = sn * ap + c * aq;
+        const double vp = V[i][p], vq = V[i][q];
+        V[i][p] = c * vp - sn * vq;
+        V[i][q] = sn * vp + c * vq;
+      }
+      __syncthreads();
+      // next round-robin arrangement: slot 0 fixed, the others rotate
+      if (threadIdx.x == 0) {
+        const int last = perm[Re - 1];
+        for (int i = Re - 1; i > 1; i--) perm[i] = perm[i - 1];
+        perm[1] = last;
+      }
+      __syncthreads();
+    }
+  }
+  // sort by decreasing eigenvalue (selection by rank; ties keep index order)
+  for (int i = threadIdx.x; i < R; i += blockDim.x) lam[i] = A[i][i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < R; i += blockDim.x) {
+    int rank = 0;
+    for (int j = 0; j < R; j++)
+      if (lam[j] > lam[i] || (lam[j] == lam[i] && j < i)) rank++;
+    lam_out[rank] = lam[i];
+    for (int r = 0; r < R; r++) Vout[r * R + rank] = V[r][i];
+  }
+}
+
+// A_new[:, r] = Q V[:, r], signed to a non-negative inner product with
+// A_old[:, r]; one CTA per column.  dA = A_new - A_ref (ref = A_old, or A_p
+// in PP sweeps); per-column ||dA||^2 and ||A_new||^2 into part[2 r], [2 r + 1].
+__global__ void __launch_bounds__(256) qv_sign_kernel(const double* __restrict__ Q,
+                                                      const double* __restrict__ V, int s, int R,
+                                                      double* __restrict__ A,
+                                                      const double* __restrict__ Aref,
+                                                      double* __restrict__ dA,
+                                                      double* __restrict__ part) {
+  const int r = blockIdx.x;
+  __shared__ double red[256];
+  __shared__ double sgn;
+  double dot = 0.0;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    double a = 0.0;
+    for (int k = 0; k < R; k++) a = fma(Q[(int64_t)i * R + k], V[k * R + r], a);
+    dot = fma(a, A[(int64_t)i * R + r], dot);
+  }
+  red[threadIdx.x] = dot;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sgn = red[0] < 0.0 ? -1.0 : 1.0;
+  __syncthreads();
+  double nd = 0.0, na = 0.0;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    double a = 0.0;
+    for (int k = 0; k < R; k++) a = fma(Q[(int64_t)i * R + k], V[k * R + r], a);
+    a *= sgn;
+    const double d = a - (Aref ? Aref[(int64_t)i * R + r] : A[(int64_t)i * R + r]);
+    dA[(int64_t)i * R + r] = d;
+    A[(int64_t)i * R + r] = a;
+    nd = fma(d, d, nd);
+    na = fma(a, a, na);
+  }
+  __syncthreads();
+  red[threadIdx.x] = nd;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[2 * r] = red[0];
+  __syncthreads();
+  red[threadIdx.x] = na;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[2 * r + 1] = red[0];
+}
+
+// out[i] = in[i] (copy) or out[i] += in[i]
+__global__ void axpy_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t n,
+                            int add) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = add ? out[i] + in[i] : in[i];
+}
+
+// out[b][i][j] += in[b][j][i]  (i < P, j < Qd)
+__global__ void add_transposed_kernel(const double* __restrict__ in, double* __restrict__ out,
+                                      int64_t B, int P, int Qd) {
+  const int64_t n = B * P * Qd;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / ((int64_t)P * Qd);
+    const int rem = (int)(e % ((int64_t)P * Qd));
+    const int i = rem / Qd, j = rem % Qd;
+    out[e] += in[b * P * Qd + (int64_t)j * P + i];
+  }
+}
+
+// scal[0] = fitness, scal[1] = ||G||^2, scal[2 + 2n] = ||dA^(n)||^2,
+// scal[3 + 2n] = ||A^(n)||^2 (sums of the per-column parts)
+__global__ void tucker_scalars_kernel(const double* __restrict__ G, int64_t ng, double normX2,
+                                      const double* __restrict__ part, int R0, int R1, int R2,
+                                      double* __restrict__ scal) {
+  __shared__ double red[256];
+  double g = 0.0;
+  for (int64_t i = threadIdx.x; i < ng; i += blockDim.x) g = fma(G[i], G[i], g);
+  red[threadIdx.x] = g;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double gn = red[0];
+    scal[0] = 1.0 - sqrt(fmax(normX2 - gn, 0.0)) / sqrt(normX2);
+    scal[1] = gn;
+    const int Rs[3] = {R0, R1, R2};
+    for (int n = 0; n < 3; n++) {
+      double nd = 0.0, na = 0.0;
+      for (int r = 0; r < Rs[n]; r++) {
+        nd += part[2 * (kTuckerMaxRank * n + r)];
+        na += part[2 * (kTuckerMaxRank * n + r) + 1];
+      }
+      scal[2 + 2 * n] = nd;
+      scal[3 + 2 * n] = na;
+    }
+  }
+}
+
+__global__ void sumsq64_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+  __shared__ double red[256];
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a = fma(x[i], x[i], a);
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+}  // namespace
+}  // namespace cpals
+
+using namespace cpals;
+
+struct cpals_tucker {
+  int64_t s[3] = {0, 0, 0};
+  int R[3] = {0, 0, 0};
+  int iters = 8;                       // subspace iterations per factor update
+  cudaStream_t stream = nullptr;
+  int64_t launches = 0;
+  std::string err;
+  double* X = nullptr;
+  double normX2 = 0.0;
+  bool have_tensor = false, have_factors = false, ops_built = false;
+  double* A[3] = {nullptr, nullptr, nullptr};
+  double* Ap[3] = {nullptr, nullptr, nullptr};
+  double* dA[3] = {nullptr, nullptr, nullptr};
+  double *T = nullptr, *U = nullptr, *Y = nullptr, *Yt = nullptr, *G = nullptr;
+  double *W = nullptr, *Z = nullptr, *Q = nullptr, *C = nullptr, *Lc = nullptr, *V = nullptr, *lam = nullptr;
+  double* part = nullptr;              // 3 * kTuckerMaxRank * 2 column norms
+  double* ops[3] = {nullptr, nullptr, nullptr};   // (1,2), (1,3), (2,3) in 1-based mode pairs
+  double* Mp[3] = {nullptr, nullptr, nullptr};
+  double* scal = nullptr;
+  double* scal_h = nullptr;
+  int* status = nullptr;
+  int status_h = 0;
+  Launch L() { return Launch{stream, &launches}; }
+  cpals_status fail(cpals_status st, const std::string& m) {
+    err = m;
+    return st;
+  }
+};
+
+namespace {
+
+#define TK(x)                                                                  \
+  do {                                                                         \
+    cudaError_t e_ = (x);                                                      \
+    if (e_ != cudaSuccess) return t->fail(CPALS_E_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define TKS(x)                                                                 \
+  do {                                                                         \
+    cpals_status s_ = (x);                                                     \
+    if (s_ != CPALS_OK) return s_;                                             \
+  } while (0)
+
+// out = in x_mode B for the layouts of the file comment (gemm_simt: K-major
+// contracts the trailing index, MN-major a leading or middle one)
+void gemm(cpals_tucker* t, const double* in, const double* B, double* out, int64_t batch, int64_t K,
+          int64_t M, int R, bool kmajor) {
+  gemm_simt<double, double>(in, B, out, nullptr, batch, K, M, R, kmajor, 1, t->L());
+}
+
+// Leading R_n eigenvectors of W = Y_(n) Y_(n)^T into A[n] (Y: s_n rows of K)
+cpals_status eig_update(cpals_tucker* t, int n, const double* Yn, int64_t K, const double* Aref) {
+  const int s = (int)t->s[n], R = t->R[n];
+  const int64_t tiles = cdivt(s, 32);
+  syrk_kernel<<<dim3((unsigned)tiles, (unsigned)tiles), 256, 0, t->stream>>>(Yn, s, (int)K, t->W);
+  t->launches++;
+  // subspace iteration from the current factor
+  const double* src = t->A[n];
+  const unsigned rows_grid = (unsigned)std::min<int64_t>(cdivt(s, 8), 304);
+  for (int it = 0; it < t->iters; it++) {
+    gemm(t, t->W, src, t->Z, 1, s, s, R, true);                 // Z = W Q
+    // Cholesky QR twice: Q = Z L^-T with Z^T Z = L L^T, then once more on Q
+    for (int pass = 0; pass < 2; pass++) {
+      const double* in = pass == 0 ? t->Z : t->Q;
+      atb_kernel<<<(unsigned)cdivt((int64_t)R * R, 256), 256, 0, t->stream>>>(in, in, s, R, t->C);
+      chol_small_kernel<<<1, 256, 0, t->stream>>>(t->C, R, t->Lc, t->status);
+      rowsolve_lt_kernel<<<rows_grid, 256, 0, t->stream>>>(in, t->Lc, s, R, t->Q);
+      t->launches += 3;
+    }
+    src = t->Q;
+  }
+  // Rayleigh-Ritz: H = Q^T W Q, its eigenvectors V, A = Q V
+  gemm(t, t->W, t->Q, t->Z, 1, s, s, R, true);
+  atb_kernel<<<(unsigned)cdivt((int64_t)R * R, 256), 256, 0, t->stream>>>(t->Q, t->Z, s, R, t->C);
+  jacobi_kernel<<<1, 256, 0, t->stream>>>(t->C, R, t->V, t->lam);
+  qv_sign_kernel<<<(unsigned)R, 256, 0, t->stream>>>(t->Q, t->V, s, R, t->A[n], Aref, t->dA[n],
+                                                    t->part + 2 * kTuckerMaxRank * n);
+  t->launches += 3;
+  return CPALS_OK;
+}
+
+cpals_status finish_sweep(cpals_tucker* t, const double* Y3) {
+  // G = Y3 x_3 A3: out[m = (r1, r2)][r3] = sum_x3 Y3[x3][m] A3[x3][r3]
+  gemm(t, Y3, t->A[2], t->G, 1, t->s[2], (int64_t)t->R[0] * t->R[1], t->R[2], false);
+  tucker_scalars_kernel<<<1, 256, 0, t->stream>>>(t->G, (int64_t)t->R[0] * t->R[1] * t->R[2], t->normX2,
+                                                  t->part, t->R[0], t->R[1], t->R[2], t->scal);
+  t->launches += 1;
+  TK(cudaMemcpyAsync(t->scal_h, t->scal, 8 * 8, cudaMemcpyDeviceToHost, t->stream));
+  TK(cudaMemcpyAsync(&t->status_h, t->status, 4, cudaMemcpyDeviceToHost, t->stream));
+  TK(cudaStreamSynchronize(t->stream));
+  TK(cudaGetLastError());
+  if (t->status_h) {
+    TK(cudaMemset(t->status, 0, 4));
+    return t->fail(CPALS_E_SINGULAR, "Cholesky QR met a non-positive pivot");
+  }
+  return CPALS_OK;
+}
+
+cpals_status tucker_als(cpals_tucker* t) {
+  const int64_t s1 = t->s[0], s2 = t->s[1], s3 = t->s[2];
+  const int R1 = t->R[0], R2 = t->R[1], R3 = t->R[2];
+  // T = X x_3 A3 [x1][x2][r3]
+  gemm(t, t->X, t->A[2], t->T, 1, s3, s1 * s2, R3, true);
+  // Y1 = T x_2 A2 [x1][r3][r2]
+  gemm(t, t->T, t->A[1], t->Y, s1, s2, R3, R2, false);
+  TKS(eig_update(t, 0, t->Y, (int64_t)R3 * R2, nullptr));
+  // Y2 = T x_1 A1 [x2][r3][r1]
+  gemm(t, t->T, t->A[0], t->Y, 1, s1, s2 * R3, R1, false);
+  TKS(eig_update(t, 1, t->Y, (int64_t)R3 * R1, nullptr));
+  // U = X x_1 A1 [x2][x3][r1]; Y3 = U x_2 A2 [x3][r1][r2]
+  gemm(t, t->X, t->A[0], t->U, 1, s1, s2 * s3, R1, false);
+  gemm(t, t->U, t->A[1], t->Y, 1, s2, s3 * R1, R2, false);
+  TKS(eig_update(t, 2, t->Y, (int64_t)R1 * R2, nullptr));
+  return finish_sweep(t, t->Y);
+}
+
+cpals_status tucker_build(cpals_tucker* t) {
+  const int64_t s1 = t->s[0], s2 = t->s[1], s3 = t->s[2];
+  const int R1 = t->R[0], R2 = t->R[1], R3 = t->R[2];
+  for (int n = 0; n < 3; n++)
+    TK(cudaMemcpyAsync(t->Ap[n], t->A[n], t->s[n] * t->R[n] * 8, cudaMemcpyDeviceToDevice, t->stream));
+  // Y_p^(1,2) = X x_3 A3 [x1][x2][r3]; Y_p^(1,3) = X x_2 A2 [x1][x3][r2]; Y_p^(2,3) = X x_1 A1 [x2][x3][r1]
+  gemm(t, t->X, t->Ap[2], t->ops[0], 1, s3, s1 * s2, R3, true);
+  gemm(t, t->X, t->Ap[1], t->ops[1], s1, s2, s3, R2, false);
+  gemm(t, t->X, t->Ap[0], t->ops[2], 1, s1, s2 * s3, R1, false);
+  // Y_p^(1) [x1][r3][r2], Y_p^(2) [x2][r3][r1], Y_p^(3) [x3][r1][r2]
+  gemm(t, t->ops[0], t->Ap[1], t->Mp[0], s1, s2, R3, R2, false);
+  gemm(t, t->ops[0], t->Ap[0], t->Mp[1], 1, s1, s2 * R3, R1, false);
+  gemm(t, t->ops[2], t->Ap[1], t->Mp[2], 1, s2, s3 * R1, R2, false);
+  for (int n = 0; n < 3; n++) TK(cudaMemsetAsync(t->dA[n], 0, t->s[n] * t->R[n] * 8, t->stream));
+  t->ops_built = true;
+  return CPALS_OK;
+}
+
+cpals_status tucker_pp(cpals_tucker* t) {
+  const int64_t s1 = t->s[0], s2 = t->s[1], s3 = t->s[2];
+  const int R1 = t->R[0], R2 = t->R[1], R3 = t->R[2];
+  auto copy = [&](const double* in, double* out, int64_t n) {
+    axpy_kernel<<<(unsigned)std::min<int64_t>(cdivt(n, 256), 1216), 256, 0, t->stream>>>(in, out, n, 0);
+    t->launches++;
+  };
+  auto add = [&](const double* in, double* out, int64_t n) {
+    axpy_kernel<<<(unsigned)std::min<int64_t>(cdivt(n, 256), 1216), 256, 0, t->stream>>>(in, out, n, 1);
+    t->launches++;
+  };
+  auto addT = [&](const double* in, double* out, int64_t B, int P, int Qd) {
+    add_transposed_kernel<<<(unsigned)std::min<int64_t>(cdivt(B * P * Qd, 256), 1216), 256, 0, t->stream>>>(
+        in, out, B, P, Qd);
+    t->launches++;
+  };
+  // mode 1: Y~1 [x1][r3][r2] = Mp1 + Y_p^(1,2) x_2 dA2 + Y_p^(1,3) x_3 dA3
+  copy(t->Mp[0], t->Y, s1 * R3 * R2);
+  gemm(t, t->ops[0], t->dA[1], t->Yt, s1, s2, R3, R2, false);            // [x1][r3][r2]
+  add(t->Yt, t->Y, s1 * R3 * R2);
+  gemm(t, t->ops[1], t->dA[2], t->Yt, s1, s3, R2, R3, false);            // [x1][r2][r3]
+  addT(t->Yt, t->Y, s1, R3, R2);
+  TKS(eig_update(t, 0, t->Y, (int64_t)R3 * R2, t->Ap[0]));
+  // mode 2: Y~2 [x2][r3][r1] = Mp2 + Y_p^(1,2) x_1 dA1 + Y_p^(2,3) x_3 dA3
+  copy(t->Mp[1], t->Y, s2 * R3 * R1);
+  gemm(t, t->ops[0], t->dA[0], t->Yt, 1, s1, s2 * R3, R1, false);        // [x2][r3][r1]
+  add(t->Yt, t->Y, s2 * R3 * R1);
+  gemm(t, t->ops[2], t->dA[2], t->Yt, s2, s3, R1, R3, false);            // [x2][r1][r3]
+  addT(t->Yt, t->Y, s2, R3, R1);
+  TKS(eig_update(t, 1, t->Y, (int64_t)R3 * R1, t->Ap[1]));
+  // mode 3: Y~3 [x3][r1][r2] = Mp3 + Y_p^(1,3) x_1 dA1 + Y_p^(2,3) x_2 dA2
+  copy(t->Mp[2], t->Y, s3 * R1 * R2);
+  gemm(t, t->ops[1], t->dA[0], t->Yt, 1, s1, s3 * R2, R1, false);        // [x3][r2][r1]
+  addT(t->Yt, t->Y, s3, R1, R2);
+  gemm(t, t->ops[2], t->dA[1], t->Yt, 1, s2, s3 * R1, R2, false);        // [x3][r1][r2]
+  add(t->Yt, t->Y, s3 * R1 * R2);
+  TKS(eig_update(t, 2, t->Y, (int64_t)R1 * R2, t->Ap[2]));
+  return finish_sweep(t, t->Y);
+}
+
+cpals_status tk_ready(cpals_tucker* t) {
+  if (!t) return CPALS_E_INVALID;
+  if (!t->have_tensor) return t->fail(CPALS_E_STATE, "no tensor");
+  if (!t->have_factors) return t->fail(CPALS_E_STATE, "no factors");
+  return CPALS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cpals_status cpals_tucker_create(const int64_t* dims, int N, const int* ranks, cpals_tucker** out) {
+  if (!out) return CPALS_E_INVALID;
+  *out = nullptr;
+  if (!dims || !ranks || N != 3) return CPALS_E_INVALID;
+  for (int n = 0; n < 3; n++)
+    if (dims[n] < 1 || dims[n] > 4096 || ranks[n] < 1 || ranks[n] > kTuckerMaxRank || ranks[n] > dims[n])
+      return CPALS_E_INVALID;
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return CPALS_E_CUDA;
+  }
+  if (!(prop.major == 10 && prop.minor == 3)) return CPALS_E_UNSUPPORTED;
+  cpals_tucker* t = new cpals_tucker();
+  for (int n = 0; n < 3; n++) {
+    t->s[n] = dims[n];
+    t->R[n] = ranks[n];
+  }
+  const int64_t s1 = dims[0], s2 = dims[1], s3 = dims[2];
+  const int64_t smax = std::max(s1, std::max(s2, s3));
+  const int R1 = ranks[0], R2 = ranks[1], R3 = ranks[2];
+  const int64_t Ymax = std::max(s1 * R2 * R3, std::max(s2 * R1 * R3, s3 * R1 * R2));
+  bool ok = cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking) == cudaSuccess;
+  auto al = [&](double** p, int64_t n) {
+    if (ok) ok = cudaMalloc((void**)p, (size_t)std::max<int64_t>(n, 1) * 8) == cudaSuccess;
+  };
+  al(&t->X, s1 * s2 * s3);
+  for (int n = 0; n < 3; n++) {
+    al(&t->A[n], dims[n] * ranks[n]);
+    al(&t->Ap[n], dims[n] * ranks[n]);
+    al(&t->dA[n], dims[n] * ranks[n]);
+  }
+  al(&t->T, s1 * s2 * R3);
+  al(&t->U, s2 * s3 * R1);
+  al(&t->Y, Ymax);
+  al(&t->Yt, Ymax);
+  al(&t->G, (int64_t)R1 * R2 * R3);
+  al(&t->W, smax * smax);
+  al(&t->Z, smax * kTuckerMaxRank);
+  al(&t->Q, smax * kTuckerMaxRank);
+  al(&t->C, kTuckerMaxRank * kTuckerMaxRank);
+  al(&t->Lc, kTuckerMaxRank * kTuckerMaxRank);
+  al(&t->V, kTuckerMaxRank * kTuckerMaxRank);
+  al(&t->lam, kTuckerMaxRank);
+  al(&t->part, 3 * 2 * kTuckerMaxRank);
+  al(&t->ops[0], s1 * s2 * R3);
+  al(&t->ops[1], s1 * s3 * R2);
+  al(&t->ops[2], s2 * s3 * R1);
+  al(&t->Mp[0], s1 * R3 * R2);
+  al(&t->Mp[1], s2 * R3 * R1);
+  al(&t->Mp[2], s3 * R1 * R2);
+  al(&t->scal, 16);
+  if (ok) ok = cudaMalloc((void**)&t->status, 16) == cudaSuccess && cudaMemset(t->status, 0, 16) == cudaSuccess;
+  if (ok) ok = cudaMallocHost((void**)&t->scal_h, 16 * 8) == cudaSuccess;
+  if (ok) ok = cudaMemset(t->part, 0, 3 * 2 * kTuckerMaxRank * 8) == cudaSuccess;
+  if (ok) ok = setup_small_kernels() == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    cpals_tucker_destroy(t);
+    return CPALS_E_OOM;
+  }
+  *out = t;
+  return CPALS_OK;
+}
+
+void cpals_tucker_destroy(cpals_tucker* t) {
+  if (!t) return;
+  if (t->stream) cudaStreamSynchronize(t->stream);
+  auto F = [](void* p) {
+    if (p) cudaFree(p);
+  };
+  F(t->X);
+  for (int n = 0; n < 3; n++) {
+    F(t->A[n]); F(t->Ap[n]); F(t->dA[n]); F(t->ops[n]); F(t->Mp[n]);
+  }
+  F(t->T); F(t->U); F(t->Y); F(t->Yt); F(t->G); F(t->W); F(t->Z); F(t->Q); F(t->C); F(t->Lc);
+  F(t->V); F(t->lam); F(t->part); F(t->scal); F(t->status);
+  if (t->scal_h) cudaFreeHost(t->scal_h);
+  if (t->stream) cudaStreamDestroy(t->stream);
+  cudaGetLastError();
+  delete t;
+}
+
+cpals_status cpals_tucker_set_iterations(cpals_tucker* t, int iters) {
+  if (!t || iters < 1 || iters > 1000) return CPALS_E_INVALID;
+  t->iters = iters;
+  return CPALS_OK;
+}
+
+cpals_status cpals_tucker_set_tensor(cpals_tucker* t, const void* data, int dtype, int on_device) {
+  if (!t || !data || (dtype != 0 && dtype != 1)) return t ? t->fail(CPALS_E_INVALID, "bad tensor") : CPALS_E_INVALID;
+  const int64_t n = t->s[0] * t->s[1] * t->s[2];
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (dtype == 0) {
+    TK(cudaMemcpyAsync(t->X, data, n * 8, kind, t->stream));
+  } else {
+    float* tmp = nullptr;
+    TK(cudaMalloc((void**)&tmp, n * 4));
+    cudaError_t e = cudaMemcpyAsync(tmp, data, n * 4, kind, t->stream);
+    if (e == cudaSuccess) {
+      convert<float, double>(tmp, t->X, n, t->L());
+      e = cudaStreamSynchronize(t->stream);
+    }
+    cudaFree(tmp);
+    TK(e);
+  }
+  sumsq64_kernel<<<1, 256, 0, t->stream>>>(t->X, n, t->scal + 15);
+  TK(cudaMemcpyAsync(t->scal_h + 15, t->scal + 15, 8, cudaMemcpyDeviceToHost, t->stream));
+  TK(cudaStreamSynchronize(t->stream));
+  TK(cudaGetLastError());
+  t->normX2 = t->scal_h[15];
+  t->have_tensor = true;
+  t->ops_built = false;
+  return CPALS_OK;
+}
+
+cpals_status cpals_tucker_init_factors(cpals_tucker* t, const double* const* factors) {
+  if (!t || !factors) return t ? t->fail(CPALS_E_INVALID, "factors is NULL") : CPALS_E_INVALID;
+  for (int n = 0; n < 3; n++) {
+    if (!factors[n]) return t->fail(CPALS_E_INVALID, "factor pointer is NULL");
+    TK(cudaMemcpyAsync(t->A[n], factors[n], t->s[n] * t->R[n] * 8, cudaMemcpyHostToDevice, t->stream));
+    // Algorithm 4 line 2: dA <- A
+    TK(cudaMemcpyAsync(t->dA[n], t->A[n], t->s[n] * t->R[n] * 8, cudaMemcpyDeviceToDevice, t->stream));
+  }
+  TK(cudaStreamSynchronize(t->stream));
+  for (int n = 0; n < 3; n++) {
+    t->scal_h[2 + 2 * n] = t->R[n];       // ||dA||^2 = ||A||^2 = R for orthonormal columns
+    t->scal_h[3 + 2 * n] = t->R[n];
+  }
+  t->have_factors = true;
+  t->ops_built = false;
+  return CPALS_OK;
+}
+
+cpals_status cpals_tucker_als_sweep(cpals_tucker* t, double* fitness) {
+  TKS(tk_ready(t));
+  TKS(tucker_als(t));
+  if (fitness) *fitness = t->scal_h[0];
+  return CPALS_OK;
+}
+
+cpals_status cpals_tucker_pp_build_operators(cpals_tucker* t) {
+  TKS(tk_ready(t));
+  TKS(tucker_build(t));
+  TK(cudaStreamSynchronize(t->stream));
+  TK(cudaGetLastError());
+  return CPALS_OK;
+}
+
+cpals_status cpals_tucker_pp_sweep(cpals_tucker* t, double* fitness) {
+  TKS(tk_ready(t));
+  if (!t->ops_built) return t->fail(CPALS_E_STATE, "PP operators not built");
+  TKS(tucker_pp(t));
+  if (fitness) *fitness = t->scal_h[0];
+  return CPALS_OK;
+}
+
+cpals_status cpals_tucker_run(cpals_tucker* t, int max_sweeps, double eps, double* fitness_trace,
+                              int* kind_trace, int* n_done) {
+  TKS(tk_ready(t));
+  if (max_sweeps < 0) return t->fail(CPALS_E_INVALID, "max_sweeps < 0");
+  auto small = [&]() {
+    for (int n = 0; n < 3; n++)
+      if (!(t->scal_h[2 + 2 * n] < eps * eps * t->scal_h[3 + 2 * n])) return false;
+    return true;
+  };
+  int k = 0;
+  cpals_status st = CPALS_OK;
+  auto record = [&](int kind) {
+    if (fitness_trace) fitness_trace[k] = t->scal_h[0];
+    if (kind_trace) kind_trace[k] = kind;
+    k++;
+  };
+  while (st == CPALS_OK && k < max_sweeps) {
+    if (eps > 0 && small()) {
+      st = tucker_build(t);
+      if (st != CPALS_OK) break;
+      // dA <- 0 (Algorithm 4 line 7)
+      for (int n = 0; n < 3; n++) t->scal_h[2 + 2 * n] = 0.0;
+      bool first = true;
+      while (st == CPALS_OK && k < max_sweeps && small()) {
+        st = tucker_pp(t);
+        if (st != CPALS_OK) break;
+        record(first ? CPALS_SWEEP_PP_INIT : CPALS_SWEEP_PP_APPROX);
+        first = false;
+      }
+      if (st != CPALS_OK || k >= max_sweeps) break;
+    }
+    st = tucker_als(t);
+    if (st != CPALS_OK) break;
+    record(CPALS_SWEEP_ALS);
+  }
+  if (n_done) *n_done = k;
+  return st;
+}
+
+cpals_status cpals_tucker_fitness(cpals_tucker* t, double* out) {
+  TKS(tk_ready(t));
+  if (!out) return t->fail(CPALS_E_INVALID, "out is NULL");
+  // exact: Y3 and the core at the current factors
+  const int64_t s1 = t->s[0], s2 = t->s[1], s3 = t->s[2];
+  gemm(t, t->X, t->A[0], t->U, 1, s1, s2 * s3, t->R[0], false);
+  gemm(t, t->U, t->A[1], t->Yt, 1, s2, s3 * t->R[0], t->R[1], false);
+  TKS(finish_sweep(t, t->Yt));
+  *out = t->scal_h[0];
+  return CPALS_OK;
+}
+
+cpals_status cpals_tucker_get_factors(cpals_tucker* t, double* const* out) {
+  if (!t || !out) return CPALS_E_INVALID;
+  for (int n = 0; n < 3; n++) {
+    if (!out[n]) return t->fail(CPALS_E_INVALID, "NULL buffer");
+    TK(cudaMemcpyAsync(out[n], t->A[n], t->s[n] * t->R[n] * 8, cudaMemcpyDeviceToHost, t->stream));
+  }
+  TK(cudaStreamSynchronize(t->stream));
+  return CPALS_OK;
+}
+
+cpals_status cpals_tucker_get_core(cpals_tucker* t, double* out) {
+  if (!t || !out) return CPALS_E_INVALID;
+  TK(cudaMemcpyAsync(out, t->G, (size_t)t->R[0] * t->R[1] * t->R[2] * 8, cudaMemcpyDeviceToHost, t->stream));
+  TK(cudaStreamSynchronize(t->stream));
+  return CPALS_OK;
+}
+
+const char* cpals_tucker_last_error(const cpals_tucker* t) { return t ? t->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+"""GPU parity of Tucker-ALS (HOOI) and PP-Tucker-ALS (Algorithm 4), order 3,
+float64, against the oracle fed with the same state; tolerance 1e-10 (the
+subspace iteration converges to rounding on these spectrally separated
+problems)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import tucker_oracle as TO
+from paper_1811_10573_gb300 import cpals, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_1811_10573_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    cpals.lib()
+
+
+def _setup(dims, ranks, seed, noise=0.05, init="hosvd"):
+    p = synth.tucker_problem(dims, ranks, seed=seed, noise=noise)
+    A0 = TO.hosvd(p.X, ranks) if init == "hosvd" else p.A0
+    t = cpals.Tucker(dims, ranks)
+    if init != "hosvd":
+        t.set_iterations(100)                            # converged from a random start
+    t.set_tensor(torch.from_numpy(np.ascontiguousarray(p.X)).cuda())
+    t.init_factors(A0)
+    return p, A0, t
+
+
+@pytest.mark.parametrize("dims,ranks,init", [([40, 36, 32], [4, 3, 5], "hosvd"),
+                                             ([30, 50, 24], [6, 2, 3], "hosvd"),
+                                             ([33, 29, 40], [5, 4, 3], "random")])
+def test_tucker_als_sweeps(dims, ranks, init):
+    p, A0, t = _setup(dims, ranks, seed=7, noise=0.05 if init == "hosvd" else 0.3, init=init)
+    with t:
+        normX = float(np.linalg.norm(p.X))
+        for sweep in range(3):
+            A = t.get_factors()
+            f = t.als_sweep()
+            _, G = TO.als_sweep(p.X, A)
+            for n, (a, b) in enumerate(zip(t.get_factors(), A)):
+                assert np.max(np.abs(a - b)) < 1e-10, (sweep, n, np.max(np.abs(a - b)))
+            np.testing.assert_allclose(t.get_core(), G, rtol=0, atol=1e-9 * np.max(np.abs(G)))
+            assert abs(f - TO.fitness(normX, G)) < 1e-10
+        assert abs(t.fitness() - TO.fitness(normX, TO.core(p.X, t.get_factors()))) < 1e-10
+
+
+def test_tucker_pp_sweeps():
+    p, A0, t = _setup([36, 32, 28], [4, 4, 3], seed=8)
+    with t:
+        for _ in range(2):
+            t.als_sweep()
+        t.pp_build_operators()
+        Ap = t.get_factors()
+        ops, Mp = TO.pp_operators(p.X, Ap)
+        A = [a.copy() for a in Ap]
+        dA = [np.zeros_like(a) for a in Ap]
+        normX = float(np.linalg.norm(p.X))
+        for sweep in range(3):
+            f = t.pp_sweep()
+            G = TO.pp_sweep(ops, Mp, A, Ap, dA)
+            for n, (a, b) in enumerate(zip(t.get_factors(), A)):
+                assert np.max(np.abs(a - b)) < 1e-10, (sweep, n, np.max(np.abs(a - b)))
+            assert abs(f - TO.fitness(normX, G)) < 1e-10
+
+
+def test_tucker_run_matches_oracle():
+    # random orthonormal start, 0.3 relative noise: ALS sweeps until every
+    # ||dA|| < 0.3 ||A||, then PP-init and PP-approx sweeps (Algorithm 4)
+    p = synth.tucker_problem([32, 30, 28], [3, 3, 2], seed=9, noise=0.3)
+    A_ref, kinds, fit = TO.pp_tucker_als(p.X, p.A0, 16, eps=0.3)
+    assert kinds[0] == "als" and "pp_init" in kinds and "pp_approx" in kinds
+    with cpals.Tucker([32, 30, 28], [3, 3, 2]) as t:
+        t.set_iterations(100)                            # eigen ratio up to 0.65 in sweep 1
+        t.set_tensor(np.ascontiguousarray(p.X))
+        t.init_factors(p.A0)
+        out = t.run(16, 0.3)
+        assert out["kinds"] == kinds
+        for k, (f, fr) in enumerate(zip(out["fitness"], fit)):
+            if kinds[k] == "als":
+                assert abs(f - fr) < 1e-10, k
+        for a, b in zip(t.get_factors(), A_ref):
+            assert np.max(np.abs(a - b)) < 1e-9
+        assert abs(t.fitness() - fit[-1]) < 1e-10
+
+
+def test_tucker_errors():
+    with pytest.raises(cpals.CPALSError):
+        cpals.Tucker([10, 10, 10], [11, 2, 2])          # rank above the size
+    with pytest.raises(cpals.CPALSError):
+        cpals.Tucker([10, 10, 10], [2, 2, 49])          # rank above the cap
+    p, A0, t = _setup([12, 10, 9], [2, 2, 2], seed=1)
+    with t:
+        with pytest.raises(cpals.CPALSError):
+            t.pp_sweep()                                 # operators not built
+        t.als_sweep()
+        t.pp_build_operators()
+        t.pp_sweep()
