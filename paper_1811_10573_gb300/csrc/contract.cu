@@ -455,11 +455,38 @@ void reduce_splits(const T* part, T* out, int64_t n, int splits, Launch L) {
   (*L.counter)++;
 }
 
+// Rows per tile of the configuration gemm_simt picks for (M, R, kmajor).
+static int64_t gemm_simt_bm(int64_t M, int R, bool kmajor) {
+  if (!kmajor && M <= 32 && R <= 64) return 32;
+  return R <= 32 ? 128 : 64;
+}
+
+int gemm_simt_splits(int64_t batch, int64_t K, int64_t M, int R, bool kmajor, int64_t cap,
+                     int min_blocks) {
+  const int64_t base = cdiv(M, gemm_simt_bm(M, R, kmajor)) * batch;
+  if (base >= min_blocks) return 1;
+  int64_t sp = cdiv(min_blocks, base);
+  sp = std::min<int64_t>(sp, std::max<int64_t>(1, K / 64));      // at least 64 k per split
+  sp = std::min<int64_t>(sp, cap / std::max<int64_t>(1, batch * M * R));
+  return (int)std::max<int64_t>(sp, 1);
+}
+
 template <typename TX, typename T>
 void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K, int64_t M,
                int R, bool kmajor, int splits, Launch L) {
   if (splits < 1) splits = 1;
-  if (R <= 32) {
+  if (gemm_simt_bm(M, R, kmajor) == 32) {
+    // few rows per batch (batched lower-level contractions): 32-row tiles
+    if (R <= 32) gemm_launch<TX, T, false, 32, 32, 2, 2>(X, B, out, partials, batch, K, M, R, splits, L);
+    else gemm_launch<TX, T, false, 32, 64, 2, 4>(X, B, out, partials, batch, K, M, R, splits, L);
+  } else if (R <= 16) {
+    // narrower column tiles for small R (no padded FMAs on the FP64 pipe)
+    if (kmajor) gemm_launch<TX, T, true, 128, 16, 8, 1>(X, B, out, partials, batch, K, M, R, splits, L);
+    else gemm_launch<TX, T, false, 128, 16, 8, 1>(X, B, out, partials, batch, K, M, R, splits, L);
+  } else if (R <= 24) {
+    if (kmajor) gemm_launch<TX, T, true, 128, 24, 4, 3>(X, B, out, partials, batch, K, M, R, splits, L);
+    else gemm_launch<TX, T, false, 128, 24, 4, 3>(X, B, out, partials, batch, K, M, R, splits, L);
+  } else if (R <= 32) {
     if (kmajor) gemm_launch<TX, T, true, 128, 32, 8, 2>(X, B, out, partials, batch, K, M, R, splits, L);
     else gemm_launch<TX, T, false, 128, 32, 8, 2>(X, B, out, partials, batch, K, M, R, splits, L);
   } else if (R <= 64) {

@@ -27,6 +27,11 @@ template <typename TX, typename T>
 void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K, int64_t M,
                int R, bool kmajor, int splits, Launch L);
 
+// K splits for gemm_simt so that its grid has at least min_blocks CTAs
+// (at least 64 k per split; splits * batch * M * R must fit in cap values).
+int gemm_simt_splits(int64_t batch, int64_t K, int64_t M, int R, bool kmajor, int64_t cap,
+                     int min_blocks);
+
 // out[i] = sum_z part[z*n + i], deterministic order.
 template <typename T>
 void reduce_splits(const T* part, T* out, int64_t n, int splits, Launch L);

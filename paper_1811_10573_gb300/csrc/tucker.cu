@@ -37,88 +37,163 @@ namespace {
 inline int64_t cdivt(int64_t a, int64_t b) { return (a + b - 1) / b; }
 constexpr int kTuckerMaxRank = 48;
 
-// W[i][j] = sum_k Y[i K + k] Y[j K + k], 32 x 32 output tiles, K in chunks of 32
+// W[i][j] = sum_k Y[i K + k] Y[j K + k], 16 x 16 output tiles (one output per
+// thread), K in chunks of 16; upper tiles only, mirrored on store.
 __global__ void __launch_bounds__(256) syrk_kernel(const double* __restrict__ Y, int s, int K,
                                                    double* __restrict__ W) {
-  __shared__ double a[32][33], b[32][33];
-  const int ti = blockIdx.y * 32, tj = blockIdx.x * 32;
-  if (tj < ti) return;                       // upper tiles; mirrored below
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 rows of threads
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int k0 = 0; k0 < K; k0 += 32) {
-    for (int r = ty; r < 32; r += 8) {
-      const int i = ti + r, j = tj + r, k = k0 + tx;
-      a[r][tx] = (i < s && k < K) ? Y[(int64_t)i * K + k] : 0.0;
-      b[r][tx] = (j < s && k < K) ? Y[(int64_t)j * K + k] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < 32; k++)
-#pragma unroll
-      for (int q = 0; q < 4; q++) acc[q] = fma(a[ty + 8 * q][k], b[tx][k], acc[q]);
-    __syncthreads();
-  }
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    const int i = ti + ty + 8 * q, j = tj + tx;
-    if (i < s && j < s) {
-      W[(int64_t)i * s + j] = acc[q];
-      W[(int64_t)j * s + i] = acc[q];
-    }
-  }
-}
-
-// C[a][b] = sum_i P[i R + a] Q[i R + b]  (R x R, one thread per entry)
-__global__ void atb_kernel(const double* __restrict__ P, const double* __restrict__ Q, int s, int R,
-                           double* __restrict__ C) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= R * R) return;
-  const int a = e / R, b = e % R;
+  __shared__ double a[16][17], b[16][17];
+  const int ti = blockIdx.y * 16, tj = blockIdx.x * 16;
+  if (tj < ti) return;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   double acc = 0.0;
-  for (int i = 0; i < s; i++) acc = fma(P[(int64_t)i * R + a], Q[(int64_t)i * R + b], acc);
-  C[e] = acc;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    const int k = k0 + tx;
+    a[ty][tx] = (ti + ty < s && k < K) ? Y[(int64_t)(ti + ty) * K + k] : 0.0;
+    b[ty][tx] = (tj + ty < s && k < K) ? Y[(int64_t)(tj + ty) * K + k] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; q++) acc = fma(a[ty][q], b[tx][q], acc);
+    __syncthreads();
+  }
+  const int i = ti + ty, j = tj + tx;
+  if (i < s && j < s) {
+    W[(int64_t)i * s + j] = acc;
+    W[(int64_t)j * s + i] = acc;
+  }
 }
 
-// Cholesky C = L L^T of an R x R SPD matrix (one CTA); L (lower) to Lout.
-// A non-positive pivot sets bit 0 of *status.
-__global__ void chol_small_kernel(const double* __restrict__ C, int R, double* __restrict__ Lout,
-                                  int* __restrict__ status) {
+// out[i][c] = sum_k P[i K + k] B[k R + c] for R <= 48 columns, one CTA per
+// row: warp w takes the 32-wide k chunks w, w + 8, ..., lanes own columns c
+// and c + 32 with two accumulation chains each (the FP64 pipe has a long
+// latency, so the row is spread over 8 warps); the warps' sums are added in
+// warp order.
+__global__ void __launch_bounds__(256) rowmm_kernel(const double* __restrict__ P,
+                                                    const double* __restrict__ B, int K, int R,
+                                                    double* __restrict__ out) {
+  __shared__ double red[8][64];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = blockIdx.x;
+  const bool c0 = lane < R, c1 = lane + 32 < R;
+  double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+  for (int k0 = w * 32; k0 < K; k0 += 256) {
+    const int n = min(32, K - k0);
+    const double pv = lane < n ? P[i * K + k0 + lane] : 0.0;
+    const double* Bk = B + (int64_t)k0 * R;
+    if (n == 32) {
+#pragma unroll
+      for (int j = 0; j < 32; j += 2) {
+        const double p0 = __shfl_sync(0xffffffffu, pv, j), p1 = __shfl_sync(0xffffffffu, pv, j + 1);
+        if (c0) {
+          a0 = fma(p0, __ldg(Bk + j * R + lane), a0);
+          b0 = fma(p1, __ldg(Bk + (j + 1) * R + lane), b0);
+        }
+        if (c1) {
+          a1 = fma(p0, __ldg(Bk + j * R + lane + 32), a1);
+          b1 = fma(p1, __ldg(Bk + (j + 1) * R + lane + 32), b1);
+        }
+      }
+    } else {
+      for (int j = 0; j < n; j++) {
+        const double p0 = __shfl_sync(0xffffffffu, pv, j);
+        if (c0) a0 = fma(p0, __ldg(Bk + j * R + lane), a0);
+        if (c1) a1 = fma(p0, __ldg(Bk + j * R + lane + 32), a1);
+      }
+    }
+  }
+  red[w][lane] = a0 + b0;
+  red[w][lane + 32] = a1 + b1;
+  __syncthreads();
+  if (w == 0) {
+    double v0 = 0.0, v1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      v0 += red[q][lane];
+      v1 += red[q][lane + 32];
+    }
+    if (c0) out[i * R + lane] = v0;
+    if (c1) out[i * R + lane + 32] = v1;
+  }
+}
+
+// part[blk][a][c] = sum over the block's rows i of P[i R + a] Q[i R + c]
+// (rows_per_block consecutive rows; 32 rows staged in shared memory at a time)
+__global__ void __launch_bounds__(256) atb_part_kernel(const double* __restrict__ P,
+                                                       const double* __restrict__ Q, int s, int R,
+                                                       int rows_per_block, double* __restrict__ part) {
+  __shared__ double ps[32][kTuckerMaxRank + 1], qs[32][kTuckerMaxRank + 1];
+  const int r0 = blockIdx.x * rows_per_block, r1 = min(s, r0 + rows_per_block);
+  const int RR = R * R;
+  double acc[(kTuckerMaxRank * kTuckerMaxRank + 255) / 256];
+#pragma unroll
+  for (int q = 0; q < (kTuckerMaxRank * kTuckerMaxRank + 255) / 256; q++) acc[q] = 0.0;
+  for (int i0 = r0; i0 < r1; i0 += 32) {
+    const int n = min(32, r1 - i0);
+    for (int e = threadIdx.x; e < 32 * R; e += blockDim.x) {
+      const int i = e / R, c = e % R;
+      ps[i][c] = i < n ? P[(int64_t)(i0 + i) * R + c] : 0.0;
+      qs[i][c] = i < n ? Q[(int64_t)(i0 + i) * R + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < (kTuckerMaxRank * kTuckerMaxRank + 255) / 256; q++) {
+      const int e = threadIdx.x + 256 * q;
+      if (e < RR) {
+        const int a = e / R, c = e % R;
+        double v = acc[q];
+        for (int i = 0; i < n; i++) v = fma(ps[i][a], qs[i][c], v);
+        acc[q] = v;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < (kTuckerMaxRank * kTuckerMaxRank + 255) / 256; q++) {
+    const int e = threadIdx.x + 256 * q;
+    if (e < RR) part[(int64_t)blockIdx.x * RR + e] = acc[q];
+  }
+}
+
+// Cholesky QR step Q = Z L^-T with Z^T Z = L L^T: every CTA sums the nb
+// partial Grams in block order, factors the R x R matrix in shared memory
+// (redundantly; CTA 0 reports a non-positive pivot in bit 0 of *status),
+// then solves q L^T = z for its rows (one warp per row).  Z and Q may alias.
+__global__ void __launch_bounds__(256) cholqr_kernel(const double* __restrict__ part, int nb,
+                                                     const double* Z, int s, int R, double* Q,
+                                                     int* __restrict__ status) {
   __shared__ double L[kTuckerMaxRank][kTuckerMaxRank + 1];
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) L[e / R][e % R] = C[e];
+  __shared__ double dinv[kTuckerMaxRank];
+  const int RR = R * R;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    double v = 0.0;
+    for (int b = 0; b < nb; b++) v += part[(int64_t)b * RR + e];
+    L[e / R][e % R] = v;
+  }
   __syncthreads();
   for (int k = 0; k < R; k++) {
     if (threadIdx.x == 0) {
       const double d = L[k][k];
-      if (!(d > 0.0)) atomicOr(status, 1);
-      L[k][k] = sqrt(fmax(d, 1e-300));
+      if (!(d > 0.0) && blockIdx.x == 0) atomicOr(status, 1);
+      const double ri = rsqrt(fmax(d, 1e-300));
+      L[k][k] = fmax(d, 1e-300) * ri;        // sqrt(d) = d / sqrt(d)
+      dinv[k] = ri;
     }
     __syncthreads();
-    for (int i = k + 1 + threadIdx.x; i < R; i += blockDim.x) L[i][k] /= L[k][k];
+    const double di = dinv[k];
+    for (int i = k + 1 + threadIdx.x; i < R; i += blockDim.x) L[i][k] *= di;
     __syncthreads();
-    for (int e = threadIdx.x; e < (R - k - 1) * (R - k - 1); e += blockDim.x) {
-      const int i = k + 1 + e / (R - k - 1), j = k + 1 + e % (R - k - 1);
+    const int w = R - k - 1;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int i = k + 1 + e / w, j = k + 1 + e % w;
       if (j <= i) L[i][j] = fma(-L[i][k], L[j][k], L[i][j]);
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-    const int i = e / R, j = e % R;
-    Lout[e] = j <= i ? L[i][j] : 0.0;
-  }
-}
-
-// Q = Z L^-T row by row: q L^T = z (forward substitution), one warp per row
-__global__ void rowsolve_lt_kernel(const double* __restrict__ Z, const double* __restrict__ Lg, int s,
-                                   int R, double* __restrict__ Q) {
-  __shared__ double L[kTuckerMaxRank][kTuckerMaxRank + 1];
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) L[e / R][e % R] = Lg[e];
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = blockIdx.x * nw + warp; i < s; i += gridDim.x * nw) {
     double z0 = lane < R ? Z[(int64_t)i * R + lane] : 0.0;
     double z1 = lane + 32 < R ? Z[(int64_t)i * R + lane + 32] : 0.0;
     for (int k = 0; k < R; k++) {
-      const double zk = __shfl_sync(0xffffffffu, k < 32 ? z0 : z1, k & 31) / L[k][k];
+      const double zk = __shfl_sync(0xffffffffu, k < 32 ? z0 : z1, k & 31) * dinv[k];
       if (k < 32) { if (lane == k) z0 = zk; } else { if (lane == k - 32) z1 = zk; }
       if (lane > k && lane < R) z0 = fma(-L[lane][k], zk, z0);
       if (lane + 32 > k && lane + 32 < R) z1 = fma(-L[lane + 32][k], zk, z1);
@@ -128,24 +203,52 @@ __global__ void rowsolve_lt_kernel(const double* __restrict__ Z, const double* _
   }
 }
 
-// Eigen-decomposition of the symmetric R x R matrix H (one CTA): parallel
-// cyclic Jacobi (round-robin pairing, R/2 disjoint rotations per step,
-// fixed 12 sweeps), then V's columns sorted by decreasing eigenvalue.
-__global__ void jacobi_kernel(const double* __restrict__ Hg, int R, double* __restrict__ Vout,
-                              double* __restrict__ lam_out) {
+// Eigen-decomposition of the symmetric R x R matrix H = sum of nb partials
+// (one CTA): parallel cyclic Jacobi (round-robin pairing, R/2 disjoint
+// rotations per step) until the off-diagonal sum of squares is below 1e-30
+// of the diagonal one (at most 16 sweeps), then V's columns sorted by
+// decreasing eigenvalue.
+__global__ void __launch_bounds__(256) jacobi_kernel(const double* __restrict__ part, int nb, int R,
+                                                     double* __restrict__ Vout,
+                                                     double* __restrict__ lam_out) {
   __shared__ double A[kTuckerMaxRank][kTuckerMaxRank + 1], V[kTuckerMaxRank][kTuckerMaxRank + 1];
   __shared__ double cs[kTuckerMaxRank / 2][2];
   __shared__ int pp[kTuckerMaxRank / 2][2];
   __shared__ int perm[kTuckerMaxRank + 1];
   __shared__ double lam[kTuckerMaxRank];
   const int Re = R + (R & 1);                // even number of slots (a dummy when R is odd)
+  __shared__ double red[2][8];
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-    A[e / R][e % R] = Hg[e];
+    double h = 0.0;
+    for (int b = 0; b < nb; b++) h += part[(int64_t)b * R * R + e];
+    A[e / R][e % R] = h;
     V[e / R][e % R] = (e / R == e % R) ? 1.0 : 0.0;
   }
   for (int i = threadIdx.x; i < Re; i += blockDim.x) perm[i] = i;
   __syncthreads();
-  for (int sweep = 0; sweep < 12; sweep++) {
+  for (int sweep = 0; sweep < 16; sweep++) {
+    double off = 0.0, dg = 0.0;
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+      const double v = A[e / R][e % R];
+      if (e / R == e % R) dg = fma(v, v, dg);
+      else off = fma(v, v, off);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dg += __shfl_xor_sync(0xffffffffu, dg, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = off;
+      red[1][threadIdx.x >> 5] = dg;
+    }
+    __syncthreads();
+    double to = 0.0, td = 0.0;
+    for (int w = 0; w < 8; w++) {
+      to += red[0][w];
+      td += red[1][w];
+    }
+    __syncthreads();
+    if (to <= 1e-30 * td) break;
     for (int step = 0; step < Re - 1; step++) {
       // pairs of this step: (perm[k], perm[Re-1-k])
       for (int k = threadIdx.x; k < Re / 2; k += blockDim.x) {
@@ -155,9 +258,16 @@ __global__ void jacobi_kernel(const double* __restrict__ Hg, int R, double* __re
         if (q < R) {
           const double apq = A[p][q];
           if (apq != 0.0) {
+            // tan of the rotation angle: the smaller root of t^2 + 2 tau t - 1 = 0
             const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
+            double t;
+            if (fabs(tau) > 1e100) {
+              t = 0.5 / tau;
+            } else {
+              const double u = fma(tau, tau, 1.0);
+              t = copysign(1.0, tau) / fma(u, rsqrt(u), fabs(tau));   // sqrt(u) = u / sqrt(u)
+            }
+            c = rsqrt(fma(t, t, 1.0));
             sn = t * c;
           }
         }
@@ -318,19 +428,6 @@ __global__ void tucker_scalars_kernel(const double* __restrict__ G, int64_t ng, 
   }
 }
 
-__global__ void sumsq64_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
-  __shared__ double red[256];
-  double a = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a = fma(x[i], x[i], a);
-  red[threadIdx.x] = a;
-  __syncthreads();
-  for (int st = 128; st > 0; st >>= 1) {
-    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = red[0];
-}
-
 }  // namespace
 }  // namespace cpals
 
@@ -350,8 +447,10 @@ struct cpals_tucker {
   double* Ap[3] = {nullptr, nullptr, nullptr};
   double* dA[3] = {nullptr, nullptr, nullptr};
   double *T = nullptr, *U = nullptr, *Y = nullptr, *Yt = nullptr, *G = nullptr;
-  double *W = nullptr, *Z = nullptr, *Q = nullptr, *C = nullptr, *Lc = nullptr, *V = nullptr, *lam = nullptr;
+  double *W = nullptr, *Z = nullptr, *Q = nullptr, *C = nullptr, *V = nullptr, *lam = nullptr;
   double* part = nullptr;              // 3 * kTuckerMaxRank * 2 column norms
+  double* gpart = nullptr;             // K-split partial sums of the contractions
+  int64_t gpart_cap = 0;
   double* ops[3] = {nullptr, nullptr, nullptr};   // (1,2), (1,3), (2,3) in 1-based mode pairs
   double* Mp[3] = {nullptr, nullptr, nullptr};
   double* scal = nullptr;
@@ -379,40 +478,53 @@ namespace {
   } while (0)
 
 // out = in x_mode B for the layouts of the file comment (gemm_simt: K-major
-// contracts the trailing index, MN-major a leading or middle one)
+// contracts the trailing index, MN-major a leading or middle one); K is split
+// so that the grid covers the SMs at least twice
 void gemm(cpals_tucker* t, const double* in, const double* B, double* out, int64_t batch, int64_t K,
           int64_t M, int R, bool kmajor) {
-  gemm_simt<double, double>(in, B, out, nullptr, batch, K, M, R, kmajor, 1, t->L());
+  const int sp = gemm_simt_splits(batch, K, M, R, kmajor, t->gpart_cap, 2 * 152);
+  gemm_simt<double, double>(in, B, out, t->gpart, batch, K, M, R, kmajor, sp, t->L());
+}
+
+// nb partial Grams of P^T Q (s rows of R) into t->C
+int atb_parts(cpals_tucker* t, const double* P, const double* Q, int s, int R) {
+  const int rpb = (int)std::max<int64_t>(32, cdivt(cdivt(s, 128), 32) * 32);
+  const int nb = (int)cdivt(s, rpb);
+  atb_part_kernel<<<(unsigned)nb, 256, 0, t->stream>>>(P, Q, s, R, rpb, t->C);
+  t->launches++;
+  return nb;
 }
 
 // Leading R_n eigenvectors of W = Y_(n) Y_(n)^T into A[n] (Y: s_n rows of K)
 cpals_status eig_update(cpals_tucker* t, int n, const double* Yn, int64_t K, const double* Aref) {
   const int s = (int)t->s[n], R = t->R[n];
-  const int64_t tiles = cdivt(s, 32);
-  syrk_kernel<<<dim3((unsigned)tiles, (unsigned)tiles), 256, 0, t->stream>>>(Yn, s, (int)K, t->W);
+  const unsigned tiles = (unsigned)cdivt(s, 16);
+  syrk_kernel<<<dim3(tiles, tiles), 256, 0, t->stream>>>(Yn, s, (int)K, t->W);
   t->launches++;
-  // subspace iteration from the current factor
+  const unsigned rows_grid = (unsigned)std::min<int64_t>(cdivt(s, 8), 152);
+  auto cholqr = [&](const double* in) {
+    const int nb = atb_parts(t, in, in, s, R);
+    cholqr_kernel<<<rows_grid, 256, 0, t->stream>>>(t->C, nb, in, s, R, t->Q, t->status);
+    t->launches++;
+  };
+  // subspace iteration from the current factor: Z = W Q, orthonormalised by
+  // Cholesky QR (once; twice on the last iteration)
   const double* src = t->A[n];
-  const unsigned rows_grid = (unsigned)std::min<int64_t>(cdivt(s, 8), 304);
   for (int it = 0; it < t->iters; it++) {
-    gemm(t, t->W, src, t->Z, 1, s, s, R, true);                 // Z = W Q
-    // Cholesky QR twice: Q = Z L^-T with Z^T Z = L L^T, then once more on Q
-    for (int pass = 0; pass < 2; pass++) {
-      const double* in = pass == 0 ? t->Z : t->Q;
-      atb_kernel<<<(unsigned)cdivt((int64_t)R * R, 256), 256, 0, t->stream>>>(in, in, s, R, t->C);
-      chol_small_kernel<<<1, 256, 0, t->stream>>>(t->C, R, t->Lc, t->status);
-      rowsolve_lt_kernel<<<rows_grid, 256, 0, t->stream>>>(in, t->Lc, s, R, t->Q);
-      t->launches += 3;
-    }
+    rowmm_kernel<<<(unsigned)s, 256, 0, t->stream>>>(t->W, src, s, R, t->Z);
+    t->launches++;
+    cholqr(t->Z);
+    if (it == t->iters - 1) cholqr(t->Q);
     src = t->Q;
   }
   // Rayleigh-Ritz: H = Q^T W Q, its eigenvectors V, A = Q V
-  gemm(t, t->W, t->Q, t->Z, 1, s, s, R, true);
-  atb_kernel<<<(unsigned)cdivt((int64_t)R * R, 256), 256, 0, t->stream>>>(t->Q, t->Z, s, R, t->C);
-  jacobi_kernel<<<1, 256, 0, t->stream>>>(t->C, R, t->V, t->lam);
+  rowmm_kernel<<<(unsigned)s, 256, 0, t->stream>>>(t->W, t->Q, s, R, t->Z);
+  t->launches++;
+  const int nb = atb_parts(t, t->Q, t->Z, s, R);
+  jacobi_kernel<<<1, 256, 0, t->stream>>>(t->C, nb, R, t->V, t->lam);
   qv_sign_kernel<<<(unsigned)R, 256, 0, t->stream>>>(t->Q, t->V, s, R, t->A[n], Aref, t->dA[n],
                                                     t->part + 2 * kTuckerMaxRank * n);
-  t->launches += 3;
+  t->launches += 2;
   return CPALS_OK;
 }
 
@@ -561,8 +673,9 @@ cpals_status cpals_tucker_create(const int64_t* dims, int N, const int* ranks, c
   al(&t->W, smax * smax);
   al(&t->Z, smax * kTuckerMaxRank);
   al(&t->Q, smax * kTuckerMaxRank);
-  al(&t->C, kTuckerMaxRank * kTuckerMaxRank);
-  al(&t->Lc, kTuckerMaxRank * kTuckerMaxRank);
+  al(&t->C, 128 * kTuckerMaxRank * kTuckerMaxRank);   // up to 128 partial Grams
+  t->gpart_cap = std::max<int64_t>(1 << 20, 4 * Ymax);
+  al(&t->gpart, t->gpart_cap);
   al(&t->V, kTuckerMaxRank * kTuckerMaxRank);
   al(&t->lam, kTuckerMaxRank);
   al(&t->part, 3 * 2 * kTuckerMaxRank);
@@ -596,8 +709,8 @@ void cpals_tucker_destroy(cpals_tucker* t) {
   for (int n = 0; n < 3; n++) {
     F(t->A[n]); F(t->Ap[n]); F(t->dA[n]); F(t->ops[n]); F(t->Mp[n]);
   }
-  F(t->T); F(t->U); F(t->Y); F(t->Yt); F(t->G); F(t->W); F(t->Z); F(t->Q); F(t->C); F(t->Lc);
-  F(t->V); F(t->lam); F(t->part); F(t->scal); F(t->status);
+  F(t->T); F(t->U); F(t->Y); F(t->Yt); F(t->G); F(t->W); F(t->Z); F(t->Q); F(t->C);
+  F(t->V); F(t->lam); F(t->part); F(t->gpart); F(t->scal); F(t->status);
   if (t->scal_h) cudaFreeHost(t->scal_h);
   if (t->stream) cudaStreamDestroy(t->stream);
   cudaGetLastError();
@@ -627,7 +740,7 @@ cpals_status cpals_tucker_set_tensor(cpals_tucker* t, const void* data, int dtyp
     cudaFree(tmp);
     TK(e);
   }
-  sumsq64_kernel<<<1, 256, 0, t->stream>>>(t->X, n, t->scal + 15);
+  sumsq<double>(t->X, n, t->gpart, t->scal + 15, t->L());
   TK(cudaMemcpyAsync(t->scal_h + 15, t->scal + 15, 8, cudaMemcpyDeviceToHost, t->stream));
   TK(cudaStreamSynchronize(t->stream));
   TK(cudaGetLastError());
