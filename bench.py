@@ -443,8 +443,9 @@ def run_batch_bench(args, dist, flush, workers=16):
 
 def run_tucker_bench(args, dist, flush, s=400, R=20, sweeps=20, eps=0.3):
     """Tucker rank R = 0.05 s on an order-3 s^3 tensor (the paper's Tucker
-    sweep-time setting), float64: mean time of each sweep kind, and a budget
-    of sweeps with PP (eps 0.3, the paper's Tucker tolerance) and without."""
+    sweep-time setting), float64 and with tensor-core first-level TTMs: mean
+    time of each sweep kind, and a budget of sweeps with PP (eps 0.3, the
+    paper's Tucker tolerance) and without."""
     import numpy as np
     import torch
 
@@ -463,32 +464,38 @@ def run_tucker_bench(args, dist, flush, s=400, R=20, sweeps=20, eps=0.3):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3, out
 
-    with cpals.Tucker([s] * 3, [R] * 3) as t:
-        t.set_tensor(Xd)
-        t.init_factors(p.A0)
-        for _ in range(3):
-            t.als_sweep()
-        als = [ev_time(t.als_sweep)[0] for _ in range(5)]
-        build = [ev_time(t.pp_build_operators)[0] for _ in range(3)]
-        pps = [ev_time(t.pp_sweep)[0] for _ in range(5)]
-        runs = {}
-        for name, e in (("pp", eps), ("als", 0.0)):
+    def one(precision):
+        with cpals.Tucker([s] * 3, [R] * 3, precision) as t:
+            t.set_tensor(Xd)
             t.init_factors(p.A0)
-            t.run(2, e)                                  # warm-up
-            t.init_factors(p.A0)
-            torch.cuda.synchronize()
-            dist.barrier()
-            dt, out = ev_time(lambda: t.run(sweeps, e))
-            runs[name] = {"value": round(dist.max(dt), 6), "unit": "s", "sweeps": len(out["kinds"]),
-                          "sweep_counts": {k: out["kinds"].count(k) for k in ("als", "pp_init", "pp_approx")},
-                          "final_fitness": t.fitness()}
-    ms = lambda v: round(statistics.mean(v) * 1e3, 3)
-    return {"workload": f"tucker_order3_{s}_rank{R}: X = [[G; A1, A2, A3]] + 0.3 relative noise, "
-                        f"float64, random orthonormal start, {sweeps} sweeps",
-            "sweep_ms": {"als": ms(als), "pp_build": ms(build), "pp_approx": ms(pps)},
-            "pp_approx_vs_als_sweep": round(statistics.mean(als) / statistics.mean(pps), 2),
-            "pp": runs["pp"], "als": runs["als"],
-            "pp_vs_als_speedup": round(runs["als"]["value"] / runs["pp"]["value"], 3)}
+            for _ in range(3):
+                t.als_sweep()
+            als = [ev_time(t.als_sweep)[0] for _ in range(5)]
+            build = [ev_time(t.pp_build_operators)[0] for _ in range(3)]
+            pps = [ev_time(t.pp_sweep)[0] for _ in range(5)]
+            runs = {}
+            for name, e in (("pp", eps), ("als", 0.0)):
+                t.init_factors(p.A0)
+                t.run(2, e)                              # warm-up
+                t.init_factors(p.A0)
+                torch.cuda.synchronize()
+                dist.barrier()
+                dt, out = ev_time(lambda: t.run(sweeps, e))
+                runs[name] = {"value": round(dist.max(dt), 6), "unit": "s", "sweeps": len(out["kinds"]),
+                              "sweep_counts": {k: out["kinds"].count(k) for k in ("als", "pp_init", "pp_approx")},
+                              "final_fitness": t.fitness()}
+        ms = lambda v: round(statistics.mean(v) * 1e3, 3)
+        return {"sweep_ms": {"als": ms(als), "pp_build": ms(build), "pp_approx": ms(pps)},
+                "pp_approx_vs_als_sweep": round(statistics.mean(als) / statistics.mean(pps), 2),
+                "pp": runs["pp"], "als": runs["als"],
+                "pp_vs_als_speedup": round(runs["als"]["value"] / runs["pp"]["value"], 3)}
+
+    out = {"workload": f"tucker_order3_{s}_rank{R}: X = [[G; A1, A2, A3]] + 0.3 relative noise, "
+                       f"random orthonormal start, {sweeps} sweeps",
+           "fp64": one("fp64")}
+    out["mixed"] = one("mixed")
+    out["mixed"]["note"] = "first-level TTMs on the tensor cores (X bf16, factor hi + lo), the rest float64"
+    return out
 
 
 def run_variants(args, dist, p, Xd, flush, max_sweeps):

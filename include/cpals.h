@@ -186,7 +186,8 @@ cpals_status cpals_run_batch(cpals_ctx* const* ctxs, int n, int workers, int max
                              int* sweeps_out, int* status_out);
 
 /* ---- Tucker-ALS and PP-Tucker-ALS (Sec. 2.4, Sec. 3.1.2, Algorithm 4) ----
- * Order-3 tensors, IEEE float64, Tucker ranks 1 <= R_n <= min(48, s_n),
+ * Order-3 tensors, IEEE float64 (first-level TTMs optionally on the tensor
+ * cores, cpals_tucker_set_precision), Tucker ranks 1 <= R_n <= min(48, s_n),
  * s_n <= 4096.  Factors are s_n x R_n float64 row-major with orthonormal
  * columns; the core is R_1 x R_2 x R_3 row-major.  Each factor update takes
  * the R_n leading eigenvectors of W = Y_(n) Y_(n)^T (Y^(n) the TTMc) in
@@ -201,6 +202,15 @@ typedef struct cpals_tucker cpals_tucker;
 cpals_status cpals_tucker_create(const int64_t* dims, int N, const int* ranks, cpals_tucker** out);
 void cpals_tucker_destroy(cpals_tucker* t);
 cpals_status cpals_tucker_set_iterations(cpals_tucker* t, int iters);
+/* CPALS_FP64 (default) or CPALS_MIXED_BF16: the first-level TTMs (X x_3 A3,
+ * X x_1 A1, and the three PP operators X x_k A_p) run on the tensor cores
+ * with X rounded to bf16 and the factor as hi + lo bf16 planes, fp32
+ * accumulation, converted to float64 for the rest of the sweep (relative
+ * error about 1e-3 against float64).  CPALS_E_UNSUPPORTED if a contraction
+ * shape is not aligned for the tensor-core kernel (s_3 and s_2 s_3 and s_3
+ * multiples of 8), CPALS_E_INVALID for another value.  May be called before
+ * or after cpals_tucker_set_tensor. */
+cpals_status cpals_tucker_set_precision(cpals_tucker* t, int precision);
 /* data: row-major, last mode fastest; dtype 0 = float64, 1 = float32 (copied) */
 cpals_status cpals_tucker_set_tensor(cpals_tucker* t, const void* data, int dtype, int on_device);
 /* three host arrays (orthonormal columns; e.g. the HOSVD); dA <- A (Algorithm 4 line 2) */

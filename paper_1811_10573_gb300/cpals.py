@@ -61,6 +61,7 @@ _SIGS = {
     "cpals_tucker_create": (C.c_int, [_i64p, C.c_int, _ip, C.POINTER(_ctx_p)]),
     "cpals_tucker_destroy": (None, [_ctx_p]),
     "cpals_tucker_set_iterations": (C.c_int, [_ctx_p, C.c_int]),
+    "cpals_tucker_set_precision": (C.c_int, [_ctx_p, C.c_int]),
     "cpals_tucker_set_tensor": (C.c_int, [_ctx_p, C.c_void_p, C.c_int, C.c_int]),
     "cpals_tucker_init_factors": (C.c_int, [_ctx_p, C.POINTER(_dp)]),
     "cpals_tucker_als_sweep": (C.c_int, [_ctx_p, _dp]),
@@ -544,6 +545,10 @@ def cpals_tucker_set_iterations(t, iters):
     return lib().cpals_tucker_set_iterations(t, iters)
 
 
+def cpals_tucker_set_precision(t, precision):
+    return lib().cpals_tucker_set_precision(t, precision)
+
+
 def cpals_tucker_set_tensor(t, ptr, dtype, on_device):
     return lib().cpals_tucker_set_tensor(t, C.c_void_p(int(ptr)), dtype, on_device)
 
@@ -587,15 +592,22 @@ def cpals_tucker_last_error(t):
 
 
 class Tucker:
-    """Order-3 Tucker-ALS / PP-Tucker-ALS context in float64 (owns its device memory)."""
+    """Order-3 Tucker-ALS / PP-Tucker-ALS context in float64 (owns its device
+    memory); precision "mixed" puts the first-level TTMs on the tensor cores."""
 
-    def __init__(self, dims, ranks):
+    def __init__(self, dims, ranks, precision="fp64"):
         self.dims = [int(d) for d in dims]
         self.ranks = [int(r) for r in ranks]
         st, t = cpals_tucker_create(self.dims, self.ranks)
         if st != 0:
             raise CPALSError(st, "cpals_tucker_create failed")
         self.t = t
+        if precision != "fp64":
+            try:
+                self._ck(cpals_tucker_set_precision(self.t, PRECISIONS[precision]))
+            except Exception:
+                self.close()
+                raise
 
     def _ck(self, st):
         if st != 0:

@@ -397,6 +397,30 @@ __global__ void add_transposed_kernel(const double* __restrict__ in, double* __r
   }
 }
 
+// Xb[i] = bf16(X[i]) (through float, round to nearest)
+__global__ void to_bf16_kernel(const double* __restrict__ X, __nv_bfloat16* __restrict__ Xb, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    Xb[i] = __float2bfloat16_rn((float)X[i]);
+}
+
+// Tensor-core B operand of a factor A (K x R, row-major): two planes of Rpad
+// rows x Kstride, Bt[r][k] = hi(A[k][r]) and Bt[Rpad Kstride + r Kstride + k]
+// = lo = bf16(a - hi) with a = float(A[k][r]); zero padding.
+__global__ void factor_bt_kernel(const double* __restrict__ A, int64_t K, int R, int Rpad,
+                                 int64_t Kstride, __nv_bfloat16* __restrict__ Bt) {
+  const int64_t n = (int64_t)Rpad * Kstride;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / Kstride);
+    const int64_t k = e % Kstride;
+    const float a = (r < R && k < K) ? (float)A[k * R + r] : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(a);
+    Bt[e] = hi;
+    Bt[n + e] = __float2bfloat16_rn(a - __bfloat162float(hi));
+  }
+}
+
 // scal[0] = fitness, scal[1] = ||G||^2, scal[2 + 2n] = ||dA^(n)||^2,
 // scal[3 + 2n] = ||A^(n)||^2 (sums of the per-column parts)
 __global__ void tucker_scalars_kernel(const double* __restrict__ G, int64_t ng, double normX2,
@@ -455,8 +479,16 @@ struct cpals_tucker {
   double* Mp[3] = {nullptr, nullptr, nullptr};
   double* scal = nullptr;
   double* scal_h = nullptr;
+  // tensor-core first level (CPALS_MIXED_BF16)
+  bool mixed = false;
+  __nv_bfloat16* Xb = nullptr;
+  __nv_bfloat16* Bt = nullptr;
+  float* outf = nullptr;
+  float* gpartf = nullptr;
+  int64_t gpartf_cap = 0;
+  int* umma_sched = nullptr;
   int* status = nullptr;
-  int status_h = 0;
+  int status_h[2] = {0, 0};             // Cholesky-QR pivot bits, tensor-core kernel error
   Launch L() { return Launch{stream, &launches}; }
   cpals_status fail(cpals_status st, const std::string& m) {
     err = m;
@@ -484,6 +516,30 @@ void gemm(cpals_tucker* t, const double* in, const double* B, double* out, int64
           int64_t M, int R, bool kmajor) {
   const int sp = gemm_simt_splits(batch, K, M, R, kmajor, t->gpart_cap, 2 * 152);
   gemm_simt<double, double>(in, B, out, t->gpart, batch, K, M, R, kmajor, sp, t->L());
+}
+
+// First-level TTM of X with factor A (K x R): out = X x_mode A in the layouts
+// of gemm_simt; on the tensor cores in mixed precision.
+cpals_status first_level(cpals_tucker* t, const double* A, double* out, int64_t batch, int64_t K,
+                         int64_t M, int R, bool kmajor) {
+  if (!t->mixed) {
+    gemm(t, t->X, A, out, batch, K, M, R, kmajor);
+    return CPALS_OK;
+  }
+  const int Rpad = (int)cdivt(R, 16) * 16;
+  const int64_t Kstride = cdivt(K, 8) * 8;
+  factor_bt_kernel<<<(unsigned)std::min<int64_t>(cdivt((int64_t)Rpad * Kstride, 256), 1216), 256, 0,
+                     t->stream>>>(A, K, R, Rpad, Kstride, t->Bt);
+  t->launches++;
+  const int64_t mtiles = cdivt(M, 128) * batch;
+  int splits = 1;
+  if (mtiles < 2 * 152)
+    splits = (int)std::max<int64_t>(1, std::min<int64_t>(cdivt(2 * 152, mtiles), cdivt(K, 256)));
+  while (splits > 1 && (int64_t)splits * batch * M * R > t->gpartf_cap) splits--;
+  TK(umma_gemm_bf16(t->Xb, t->Bt, t->outf, t->gpartf, batch, K, M, R, Rpad, Kstride, kmajor, splits,
+                    t->status + 1, t->umma_sched, t->L()));
+  convert<float, double>(t->outf, out, batch * M * R, t->L());
+  return CPALS_OK;
 }
 
 // nb partial Grams of P^T Q (s rows of R) into t->C
@@ -535,11 +591,16 @@ cpals_status finish_sweep(cpals_tucker* t, const double* Y3) {
                                                   t->part, t->R[0], t->R[1], t->R[2], t->scal);
   t->launches += 1;
   TK(cudaMemcpyAsync(t->scal_h, t->scal, 8 * 8, cudaMemcpyDeviceToHost, t->stream));
-  TK(cudaMemcpyAsync(&t->status_h, t->status, 4, cudaMemcpyDeviceToHost, t->stream));
+  TK(cudaMemcpyAsync(t->status_h, t->status, 8, cudaMemcpyDeviceToHost, t->stream));
   TK(cudaStreamSynchronize(t->stream));
   TK(cudaGetLastError());
-  if (t->status_h) {
-    TK(cudaMemset(t->status, 0, 4));
+  if (t->status_h[1]) {
+    TK(cudaMemset(t->status, 0, 8));
+    return t->fail(CPALS_E_TIMEOUT, "tensor-core contraction gave up waiting (code " +
+                                        std::to_string(t->status_h[1]) + ")");
+  }
+  if (t->status_h[0]) {
+    TK(cudaMemset(t->status, 0, 8));
     return t->fail(CPALS_E_SINGULAR, "Cholesky QR met a non-positive pivot");
   }
   return CPALS_OK;
@@ -549,7 +610,7 @@ cpals_status tucker_als(cpals_tucker* t) {
   const int64_t s1 = t->s[0], s2 = t->s[1], s3 = t->s[2];
   const int R1 = t->R[0], R2 = t->R[1], R3 = t->R[2];
   // T = X x_3 A3 [x1][x2][r3]
-  gemm(t, t->X, t->A[2], t->T, 1, s3, s1 * s2, R3, true);
+  TKS(first_level(t, t->A[2], t->T, 1, s3, s1 * s2, R3, true));
   // Y1 = T x_2 A2 [x1][r3][r2]
   gemm(t, t->T, t->A[1], t->Y, s1, s2, R3, R2, false);
   TKS(eig_update(t, 0, t->Y, (int64_t)R3 * R2, nullptr));
@@ -557,7 +618,7 @@ cpals_status tucker_als(cpals_tucker* t) {
   gemm(t, t->T, t->A[0], t->Y, 1, s1, s2 * R3, R1, false);
   TKS(eig_update(t, 1, t->Y, (int64_t)R3 * R1, nullptr));
   // U = X x_1 A1 [x2][x3][r1]; Y3 = U x_2 A2 [x3][r1][r2]
-  gemm(t, t->X, t->A[0], t->U, 1, s1, s2 * s3, R1, false);
+  TKS(first_level(t, t->A[0], t->U, 1, s1, s2 * s3, R1, false));
   gemm(t, t->U, t->A[1], t->Y, 1, s2, s3 * R1, R2, false);
   TKS(eig_update(t, 2, t->Y, (int64_t)R1 * R2, nullptr));
   return finish_sweep(t, t->Y);
@@ -569,9 +630,9 @@ cpals_status tucker_build(cpals_tucker* t) {
   for (int n = 0; n < 3; n++)
     TK(cudaMemcpyAsync(t->Ap[n], t->A[n], t->s[n] * t->R[n] * 8, cudaMemcpyDeviceToDevice, t->stream));
   // Y_p^(1,2) = X x_3 A3 [x1][x2][r3]; Y_p^(1,3) = X x_2 A2 [x1][x3][r2]; Y_p^(2,3) = X x_1 A1 [x2][x3][r1]
-  gemm(t, t->X, t->Ap[2], t->ops[0], 1, s3, s1 * s2, R3, true);
-  gemm(t, t->X, t->Ap[1], t->ops[1], s1, s2, s3, R2, false);
-  gemm(t, t->X, t->Ap[0], t->ops[2], 1, s1, s2 * s3, R1, false);
+  TKS(first_level(t, t->Ap[2], t->ops[0], 1, s3, s1 * s2, R3, true));
+  TKS(first_level(t, t->Ap[1], t->ops[1], s1, s2, s3, R2, false));
+  TKS(first_level(t, t->Ap[0], t->ops[2], 1, s1, s2 * s3, R1, false));
   // Y_p^(1) [x1][r3][r2], Y_p^(2) [x2][r3][r1], Y_p^(3) [x3][r1][r2]
   gemm(t, t->ops[0], t->Ap[1], t->Mp[0], s1, s2, R3, R2, false);
   gemm(t, t->ops[0], t->Ap[0], t->Mp[1], 1, s1, s2 * R3, R1, false);
@@ -711,6 +772,7 @@ void cpals_tucker_destroy(cpals_tucker* t) {
   }
   F(t->T); F(t->U); F(t->Y); F(t->Yt); F(t->G); F(t->W); F(t->Z); F(t->Q); F(t->C);
   F(t->V); F(t->lam); F(t->part); F(t->gpart); F(t->scal); F(t->status);
+  F(t->Xb); F(t->Bt); F(t->outf); F(t->gpartf); F(t->umma_sched);
   if (t->scal_h) cudaFreeHost(t->scal_h);
   if (t->stream) cudaStreamDestroy(t->stream);
   cudaGetLastError();
@@ -720,6 +782,48 @@ void cpals_tucker_destroy(cpals_tucker* t) {
 cpals_status cpals_tucker_set_iterations(cpals_tucker* t, int iters) {
   if (!t || iters < 1 || iters > 1000) return CPALS_E_INVALID;
   t->iters = iters;
+  return CPALS_OK;
+}
+
+cpals_status cpals_tucker_set_precision(cpals_tucker* t, int precision) {
+  if (!t) return CPALS_E_INVALID;
+  if (precision == CPALS_FP64) {
+    t->mixed = false;
+    return CPALS_OK;
+  }
+  if (precision != CPALS_MIXED_BF16) return t->fail(CPALS_E_INVALID, "precision must be FP64 or MIXED_BF16");
+  const int64_t s1 = t->s[0], s2 = t->s[1], s3 = t->s[2];
+  if (!umma_supported(s3, s1 * s2, true, t->R[2]) || !umma_supported(s1, s2 * s3, false, t->R[0]) ||
+      !umma_supported(s2, s3, false, t->R[1]))
+    return t->fail(CPALS_E_UNSUPPORTED, "tensor-core TTM needs s_3 and s_2 s_3 multiples of 8");
+  if (!t->Xb) {
+    const int64_t n = s1 * s2 * s3;
+    const int64_t kmax = cdivt(std::max(s1, std::max(s2, s3)), 8) * 8;
+    const int64_t omax = std::max(s1 * s2 * t->R[2], std::max(s2 * s3 * t->R[0], s1 * s3 * t->R[1]));
+    t->gpartf_cap = std::max<int64_t>(1 << 22, 2 * omax);
+    bool ok = cudaMalloc((void**)&t->Xb, n * 2) == cudaSuccess &&
+              cudaMalloc((void**)&t->Bt, 2 * 64 * kmax * 2) == cudaSuccess &&
+              cudaMalloc((void**)&t->outf, omax * 4) == cudaSuccess &&
+              cudaMalloc((void**)&t->gpartf, t->gpartf_cap * 4) == cudaSuccess &&
+              cudaMalloc((void**)&t->umma_sched, 2 * sizeof(int)) == cudaSuccess &&
+              cudaMemset(t->umma_sched, 0, 2 * sizeof(int)) == cudaSuccess &&
+              setup_umma_kernels() == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      auto F = [](void* p) { if (p) cudaFree(p); };
+      F(t->Xb); F(t->Bt); F(t->outf); F(t->gpartf); F(t->umma_sched);
+      t->Xb = nullptr; t->Bt = nullptr; t->outf = nullptr; t->gpartf = nullptr; t->umma_sched = nullptr;
+      return t->fail(CPALS_E_OOM, "tensor-core buffers");
+    }
+  }
+  t->mixed = true;
+  if (t->have_tensor) {
+    to_bf16_kernel<<<1216, 256, 0, t->stream>>>(t->X, t->Xb, t->s[0] * t->s[1] * t->s[2]);
+    t->launches++;
+    TK(cudaStreamSynchronize(t->stream));
+    TK(cudaGetLastError());
+  }
+  t->ops_built = false;
   return CPALS_OK;
 }
 
@@ -745,6 +849,12 @@ cpals_status cpals_tucker_set_tensor(cpals_tucker* t, const void* data, int dtyp
   TK(cudaStreamSynchronize(t->stream));
   TK(cudaGetLastError());
   t->normX2 = t->scal_h[15];
+  if (t->mixed) {
+    to_bf16_kernel<<<1216, 256, 0, t->stream>>>(t->X, t->Xb, n);
+    t->launches++;
+    TK(cudaStreamSynchronize(t->stream));
+    TK(cudaGetLastError());
+  }
   t->have_tensor = true;
   t->ops_built = false;
   return CPALS_OK;
@@ -835,7 +945,7 @@ cpals_status cpals_tucker_fitness(cpals_tucker* t, double* out) {
   if (!out) return t->fail(CPALS_E_INVALID, "out is NULL");
   // exact: Y3 and the core at the current factors
   const int64_t s1 = t->s[0], s2 = t->s[1], s3 = t->s[2];
-  gemm(t, t->X, t->A[0], t->U, 1, s1, s2 * s3, t->R[0], false);
+  TKS(first_level(t, t->A[0], t->U, 1, s1, s2 * s3, t->R[0], false));
   gemm(t, t->U, t->A[1], t->Yt, 1, s2, s3 * t->R[0], t->R[1], false);
   TKS(finish_sweep(t, t->Yt));
   *out = t->scal_h[0];

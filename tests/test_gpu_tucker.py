@@ -100,3 +100,69 @@ def test_tucker_errors():
         t.als_sweep()
         t.pp_build_operators()
         t.pp_sweep()
+
+
+def test_tucker_full_size_sweeps():
+    # the bench's tensor (400^3, ranks 20 = 0.05 s, 0.3 relative noise) from
+    # the oracle's HOSVD, default subspace-iteration count: two ALS sweeps,
+    # then an operator build and a PP sweep, against the oracle
+    dims, ranks = [400] * 3, [20] * 3
+    p = synth.tucker_problem(dims, ranks, seed=0, noise=0.3)
+    A0 = TO.hosvd(p.X, ranks)
+    normX = float(np.linalg.norm(p.X))
+    A = [a.copy() for a in A0]
+    with cpals.Tucker(dims, ranks) as t:
+        t.set_tensor(torch.from_numpy(np.ascontiguousarray(p.X)).cuda())
+        t.init_factors(A0)
+        for _ in range(2):
+            f = t.als_sweep()
+            _, G = TO.als_sweep(p.X, A)
+            assert abs(f - TO.fitness(normX, G)) < 1e-10
+        for a, b in zip(t.get_factors(), A):
+            assert np.max(np.abs(a - b)) < 1e-9
+        t.pp_build_operators()
+        ops, Mp = TO.pp_operators(p.X, A)
+        Ap = [a.copy() for a in A]
+        dA = [np.zeros_like(a) for a in A]
+        f = t.pp_sweep()
+        G = TO.pp_sweep(ops, Mp, A, Ap, dA)
+        assert abs(f - TO.fitness(normX, G)) < 1e-10
+        for a, b in zip(t.get_factors(), A):
+            assert np.max(np.abs(a - b)) < 1e-9
+
+
+@pytest.mark.parametrize("dims,ranks", [([40, 32, 48], [4, 3, 5]), ([64, 56, 40], [6, 5, 4])])
+def test_tucker_mixed_precision(dims, ranks):
+    # first-level TTMs on the tensor cores (X in bf16, factor hi + lo): ALS
+    # sweeps, the operators and a PP sweep against the float64 oracle at the
+    # bf16 tolerance of the CP path (2e-2 on factors), fitness to 5e-3
+    p = synth.tucker_problem(dims, ranks, seed=11, noise=0.05)
+    A0 = TO.hosvd(p.X, ranks)
+    normX = float(np.linalg.norm(p.X))
+    with cpals.Tucker(dims, ranks, "mixed") as t:
+        t.set_tensor(np.ascontiguousarray(p.X))
+        t.init_factors(A0)
+        A = [a.copy() for a in A0]
+        for _ in range(2):
+            f = t.als_sweep()
+            _, G = TO.als_sweep(p.X, A)
+            assert abs(f - TO.fitness(normX, G)) < 5e-3
+        for a, b in zip(t.get_factors(), A):
+            assert np.max(np.abs(a - b)) < 2e-2 * np.max(np.abs(b))
+        t.pp_build_operators()
+        A = t.get_factors()
+        ops, Mp = TO.pp_operators(p.X, A)
+        Ap = [a.copy() for a in A]
+        dA = [np.zeros_like(a) for a in A]
+        f = t.pp_sweep()
+        G = TO.pp_sweep(ops, Mp, A, Ap, dA)
+        assert abs(f - TO.fitness(normX, G)) < 5e-3
+        for a, b in zip(t.get_factors(), A):
+            assert np.max(np.abs(a - b)) < 2e-2 * np.max(np.abs(b))
+        assert abs(t.fitness() - TO.fitness(normX, TO.core(p.X, t.get_factors()))) < 5e-3
+
+
+def test_tucker_mixed_unsupported_shape():
+    with pytest.raises(cpals.CPALSError) as e:
+        cpals.Tucker([12, 10, 9], [2, 2, 2], "mixed")    # s_3 = 9 is not a multiple of 8
+    assert e.value.status == 8
