@@ -243,17 +243,19 @@ pp_correct_kernel(const T* __restrict__ Mp, PPTermsArg<T> terms, T* __restrict__
   }
 }
 
-// float path when R % 4 == 0: a CTA owns 32 consecutive outputs (8 float4
-// units); lane l of every warp takes unit l % 8 and every 32nd x starting at
-// 4 * warp + l / 8, so one warp load touches four 128-byte runs of the
-// operator.  1,250 CTAs for a 400 x 100 mode keep eight CTAs per SM busy and
-// the waves even.  The 32 partial sums of each output are added in a fixed
-// order (deterministic).
-__global__ void __launch_bounds__(kThreads)
+// float path when R % 4 == 0: a CTA of 512 threads owns 32 consecutive
+// outputs (8 float4 units); lane l of every warp takes unit l % 8 and every
+// 64th x starting at 4 * warp + l / 8, so one warp load touches four
+// 128-byte runs of the operator.  At 40 registers three CTAs fit on an SM
+// (1,250 CTAs for a 400 x 100 mode, 2.7 waves); 256-thread CTAs (1.4 waves)
+// measured the same, 31-32 us cold for the 128.6 MB of a mode.  The 64
+// partial sums of each output are added in a fixed order (deterministic).
+constexpr int kPPThreads = 512;
+__global__ void __launch_bounds__(kPPThreads)
 pp_correct4_kernel(const float* __restrict__ Mp, PPTermsArg<float> terms, float* __restrict__ out,
                    int64_t total, int R) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int u = lane & 7, xg = 4 * w + (lane >> 3);          // unit, x offset (0..31)
+  const int u = lane & 7, xg = 4 * w + (lane >> 3);          // unit, x offset (0..63)
   const int64_t f = (int64_t)blockIdx.x * 32 + 4 * u;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   if (f < total) {
@@ -265,12 +267,12 @@ pp_correct4_kernel(const float* __restrict__ Mp, PPTermsArg<float> terms, float*
       // up to four 16-byte operator loads in flight per thread (the
       // operators are streamed once per sweep: evict-first loads)
       int x = xg;
-      for (; x + 96 < tt.sx; x += 128) {
+      for (; x + 192 < tt.sx; x += 256) {
         float4 v[4], a[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-          v[q] = __ldcs(reinterpret_cast<const float4*>(base + (int64_t)(x + 32 * q) * tt.xstride));
-          a[q] = __ldg(reinterpret_cast<const float4*>(tt.dA + (int64_t)(x + 32 * q) * R + r));
+          v[q] = __ldcs(reinterpret_cast<const float4*>(base + (int64_t)(x + 64 * q) * tt.xstride));
+          a[q] = __ldg(reinterpret_cast<const float4*>(tt.dA + (int64_t)(x + 64 * q) * R + r));
         }
 #pragma unroll
         for (int q = 0; q < 4; q++) {
@@ -280,7 +282,7 @@ pp_correct4_kernel(const float* __restrict__ Mp, PPTermsArg<float> terms, float*
           acc.w = fmaf(v[q].w, a[q].w, acc.w);
         }
       }
-      for (; x < tt.sx; x += 32) {
+      for (; x < tt.sx; x += 64) {
         const float4 v = __ldcs(reinterpret_cast<const float4*>(base + (int64_t)x * tt.xstride));
         const float4 a = __ldg(reinterpret_cast<const float4*>(tt.dA + (int64_t)x * R + r));
         acc.x = fmaf(v.x, a.x, acc.x);
@@ -290,7 +292,7 @@ pp_correct4_kernel(const float* __restrict__ Mp, PPTermsArg<float> terms, float*
       }
     }
   }
-  __shared__ float4 red[32][9];
+  __shared__ float4 red[64][9];
   red[xg][u] = acc;
   __syncthreads();
   if (threadIdx.x < 8) {
@@ -298,7 +300,7 @@ pp_correct4_kernel(const float* __restrict__ Mp, PPTermsArg<float> terms, float*
     const int64_t ff = (int64_t)blockIdx.x * 32 + 4 * uu;
     if (ff < total) {
       float4 sum = red[0][uu];
-      for (int i = 1; i < 32; i++) {
+      for (int i = 1; i < 64; i++) {
         sum.x += red[i][uu].x;
         sum.y += red[i][uu].y;
         sum.z += red[i][uu].z;
@@ -520,7 +522,7 @@ void pp_correct(const T* Mp, const PPTerm<T>* terms, int nterms, T* out, int sy,
   for (int i = 0; i < nterms; i++) a.t[i] = terms[i];
   const int64_t total = (int64_t)sy * R;
   if (sizeof(T) == 4 && R % 4 == 0) {
-    pp_correct4_kernel<<<(unsigned)cdiv(total, 32), kThreads, 0, L.stream>>>(
+    pp_correct4_kernel<<<(unsigned)cdiv(total, 32), kPPThreads, 0, L.stream>>>(
         (const float*)Mp, *reinterpret_cast<PPTermsArg<float>*>(&a), (float*)out, total, R);
     (*L.counter)++;
     return;
