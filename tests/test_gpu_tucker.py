@@ -166,3 +166,39 @@ def test_tucker_mixed_unsupported_shape():
     with pytest.raises(cpals.CPALSError) as e:
         cpals.Tucker([12, 10, 9], [2, 2, 2], "mixed")    # s_3 = 9 is not a multiple of 8
     assert e.value.status == 8
+
+
+def test_tucker_full_rank_is_exact():
+    # R_n = s_n: the factors are orthogonal matrices, the core holds all of X
+    # (||G|| = ||X||) and [[G; A]] reproduces X; which basis is returned is
+    # not unique (noise-level eigenvalues may be close), so compare invariants
+    dims = [8, 9, 10]
+    p = synth.tucker_problem(dims, [3, 3, 3], seed=4, noise=0.05)
+    A0 = TO.hosvd(p.X, dims)
+    with cpals.Tucker(dims, dims) as t:
+        t.set_tensor(np.ascontiguousarray(p.X))
+        t.init_factors(A0)
+        f = t.als_sweep()
+        A = t.get_factors()
+        G = t.get_core()
+    assert f > 1.0 - 1e-6
+    for a in A:
+        assert np.max(np.abs(a.T @ a - np.eye(a.shape[1]))) < 1e-12
+    Xr = TO.reconstruct(G, A)
+    assert np.max(np.abs(Xr - p.X)) < 1e-10 * np.max(np.abs(p.X))
+
+
+@pytest.mark.parametrize("dims,ranks", [([16, 24, 8], [1, 1, 1]), ([56, 48, 64], [48, 40, 48])])
+def test_tucker_rank_extremes(dims, ranks):
+    # rank 1 (one Jacobi slot and a dummy) and the largest supported rank
+    p, A0, t = _setup(dims, ranks, seed=5)
+    with t:
+        normX = float(np.linalg.norm(p.X))
+        A = [a.copy() for a in A0]
+        for _ in range(2):
+            f = t.als_sweep()
+            _, G = TO.als_sweep(p.X, A)
+            assert abs(f - TO.fitness(normX, G)) < 1e-10
+        for a, b in zip(t.get_factors(), A):
+            assert np.max(np.abs(a - b)) < 1e-9
+        np.testing.assert_allclose(t.get_core(), G, rtol=0, atol=1e-9 * np.max(np.abs(G)))
