@@ -57,7 +57,7 @@ typedef enum {
                             operators and PP corrections in float32 */
 } cpals_precision;
 
-/* Arithmetic of the normal-equation work of Algorithm 1 lines 5-10
+/* Arithmetic of the normal-equation work of Algorithm 1
  * (Grams S^(n), Gamma^(n), its Cholesky factor, the row solves, the
  * second-order terms' Z).  FP64 contexts always use IEEE float64.  FP32 and
  * MIXED_BF16 contexts default to double-float (an unevaluated sum of two
@@ -122,23 +122,23 @@ cpals_status cpals_set_stream(cpals_ctx* ctx, void* cuda_stream);
 cpals_status cpals_set_tensor(cpals_ctx* ctx, const void* data, int dtype, int on_device);
 
 /* Set the factors A^(n) from N host float64 arrays of s_n x R (row-major);
- * they are the random initial guess of Algorithm 1/3, line 2.  Resets the
- * controller state as Algorithm 3 line 2 does: dA^(n) <- A^(n), so the next
+ * they are the random initial guess of Algorithms 1 and 3.  Resets the
+ * controller state as the start of Algorithm 3 does: dA^(n) <- A^(n), so the next
  * eps test fails, S^(n) <- A^(n)T A^(n); clears PP operators. */
 cpals_status cpals_init_factors(cpals_ctx* ctx, const double* const* factors);
 
-/* One regular ALS sweep (Algorithm 1, lines 4-11) over modes 0..N-1 with the
+/* One regular ALS sweep (Algorithm 1) over modes 0..N-1 with the
  * binary dimension tree (Sec. 2.5): two first-level contractions of X per
- * sweep.  Afterwards dA^(n) = A^(n)_new - A^(n)_old (Algorithm 3, line 20).
+ * sweep.  Afterwards dA^(n) = A^(n)_new - A^(n)_old (the regular sweep of Algorithm 3).
  * fitness_out (nullable): exact fitness 1 - ||X - [[A]]||/||X|| (Sec. 5). */
 cpals_status cpals_als_sweep(cpals_ctx* ctx, double* fitness_out);
 
 /* Build the PP operators M_p^(i,n), i < n, and M_p^(n) at the current
  * factors with the operator dimension tree (Sec. 3.2.3), then set
- * A_p <- A, dA <- 0 (Algorithm 3, lines 5-8). */
+ * A_p <- A, dA <- 0 (the PP initialisation of Algorithm 3). */
 cpals_status cpals_pp_build_operators(cpals_ctx* ctx);
 
-/* One PP approximated sweep (Algorithm 3, lines 10-17): each right-hand side
+/* One PP approximated sweep (Algorithm 3): each right-hand side
  * is Eq. 3's M~^(n); use_V != 0 adds the second-order terms V^(n,i,j).
  * dA^(n) = A^(n)_new - A_p^(n).  fitness_out (nullable): fitness estimated
  * from M~^(N) (not exact; see cpals_fitness).  CPALS_E_STATE if no operators. */
@@ -213,7 +213,7 @@ cpals_status cpals_tucker_set_iterations(cpals_tucker* t, int iters);
 cpals_status cpals_tucker_set_precision(cpals_tucker* t, int precision);
 /* data: row-major, last mode fastest; dtype 0 = float64, 1 = float32 (copied) */
 cpals_status cpals_tucker_set_tensor(cpals_tucker* t, const void* data, int dtype, int on_device);
-/* three host arrays (orthonormal columns; e.g. the HOSVD); dA <- A (Algorithm 4 line 2) */
+/* three host arrays (orthonormal columns; e.g. the HOSVD); dA <- A, as Algorithm 4 starts */
 cpals_status cpals_tucker_init_factors(cpals_tucker* t, const double* const* factors);
 /* one HOOI sweep (Algorithm 2); *fitness (nullable) exact */
 cpals_status cpals_tucker_als_sweep(cpals_tucker* t, double* fitness);

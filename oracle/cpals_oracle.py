@@ -116,7 +116,7 @@ def gram(A: np.ndarray) -> np.ndarray:
 
 
 def gamma(S, n: int) -> np.ndarray:
-    """Gamma^(n) = Hadamard product of all S^(k), k != n (Algorithm 1, line 5)."""
+    """Gamma^(n) = Hadamard product of all S^(k), k != n (Algorithm 1)."""
     G = np.ones_like(S[0])
     for k, Sk in enumerate(S):
         if k != n:
@@ -132,7 +132,7 @@ class SolveInfo:
 
 
 def solve_normal(M: np.ndarray, G: np.ndarray, info: SolveInfo | None = None) -> np.ndarray:
-    """A_new = M Gamma^dagger (Algorithm 1, line 7).
+    """A_new = M Gamma^dagger (Algorithm 1).
 
     Gamma is symmetric positive (semi)definite.  The paper writes the
     pseudo-inverse and implements an SPD solve; this oracle takes the reading
@@ -256,7 +256,7 @@ def _tie_copy(A, S, dA, n: int, tie):
 
 
 def als_sweep(X: np.ndarray, A, S, info: SolveInfo | None = None, lam=None, tie=None):
-    """One sweep of Algorithm 1 (lines 4-11), Gauss-Seidel over the modes.
+    """One sweep of Algorithm 1, Gauss-Seidel over the modes.
 
     ``A`` and ``S`` are lists updated in place.  Returns (dA, gnorm) where
     dA[n] = A^(n)_new - A^(n)_old (the per-sweep change used by Algorithm 3's
@@ -368,7 +368,7 @@ def pp_mttkrp(ops, Mp, A, dA, n: int, use_V: bool = True) -> np.ndarray:
 
 def pp_sweep(ops, Mp, A, Ap, dA, S, use_V: bool = True, info: SolveInfo | None = None,
              lam=None, tie=None):
-    """One PP approximated sweep (Algorithm 3, lines 10-17); lists updated in
+    """One PP approximated sweep (the PP sweep of Algorithm 3); lists updated in
     place.  ``lam`` and ``tie`` as in ``als_sweep``: the step size blends the
     current factor with the solution of the approximated normal equations, and
     a tied mode takes its partner's factor, Gram and dA = A - A_p."""
@@ -420,7 +420,7 @@ def pp_cp_als(X: np.ndarray, A0, n_sweeps: int, eps: float, use_V: bool = True,
         A[m2] = A[m1].copy()              # tied factors start equal
     N = len(A)
     S = [gram(a) for a in A]
-    dA = [a.copy() for a in A]            # Algorithm 3 line 2: dA <- A
+    dA = [a.copy() for a in A]            # Algorithm 3 starts from dA <- A
     normX = float(np.linalg.norm(X))
     tr = PPTrace()
     info = SolveInfo()

@@ -172,7 +172,7 @@ def pp_tucker_als(X: np.ndarray, A0, n_sweeps: int, eps: float):
     PP-approx counts as one).  Returns (A, kinds, fitness) with the exact
     fitness after every sweep."""
     A = [a.copy() for a in A0]
-    dA = [a.copy() for a in A]            # Algorithm 4 line 2: dA <- A
+    dA = [a.copy() for a in A]            # Algorithm 4 starts from dA <- A
     normX = float(np.linalg.norm(X))
     kinds, fit = [], []
     t = 0

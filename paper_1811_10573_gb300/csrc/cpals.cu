@@ -302,8 +302,8 @@ const T* contract_chain(cpals_ctx* c, const T* in, std::vector<int> modes, int k
   return cur;
 }
 
-// Normal-equation update of mode n (Algorithm 1 lines 5-10; Algorithm 3 lines
-// 11-17 when pp), in two halves: factor_async factors Gamma^(n) on the side
+// Normal-equation update of mode n (Algorithm 1; the PP sweep of Algorithm 3
+// when pp), in two halves: factor_async factors Gamma^(n) on the side
 // stream (it needs only the Grams of the other modes), so it runs under the
 // contraction that forms the right-hand side; finish_mode joins and solves.
 void factor_async(cpals_ctx* c, int n, bool pp, bool useV) {
@@ -525,7 +525,7 @@ cpals_status pp_build_launch(cpals_ctx* c) {
       ttv<T>(P<const T>(c->ops[0][n]), P<const T>(c->Ac[0]), P<T>(c->Mp[n]), 1, (int)c->dims[0],
              c->dims[n], R, c->L());
   }
-  // A_p <- A, dA <- 0 (Algorithm 3, line 7)
+  // A_p <- A, dA <- 0 (the PP initialisation of Algorithm 3)
   for (int n = 0; n < N; n++) {
     const size_t sR = (size_t)c->dims[n] * R;
     CK(cudaMemcpyAsync(c->Ap[n], c->A[n], sR * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -1134,7 +1134,7 @@ cpals_status cpals_init_factors(cpals_ctx* c, const double* const* factors) {
     // a tied mode starts from its partner's factor (Sec. 5.3)
     const double* src = factors[tied(c, n) ? c->tie[n] : n];
     CK(cudaMemcpyAsync(c->A[n], src, sR * 8, cudaMemcpyHostToDevice, c->stream));
-    // Algorithm 3 line 2: dA <- A, S <- A^T A
+    // the start of Algorithm 3: dA <- A, S <- A^T A
     CK(cudaMemcpyAsync(c->dA[n], c->A[n], sR * 8, cudaMemcpyDeviceToDevice, c->stream));
     if (is64(c)) {
       convert<double, double>(c->A[n], P<double>(c->Ac[n]), sR, c->L());

@@ -1,6 +1,6 @@
 // Double-float (hi + lo, two floats, 48-bit significand) kernels for the R x R
-// normal-equation work of the FP32 and MIXED_BF16 modes (Sec. 2.3; Algorithm 1
-// lines 5-10; Algorithm 3 lines 11-17).
+// normal-equation work of the FP32 and MIXED_BF16 modes (Sec. 2.3; the
+// normal-equation steps of Algorithms 1 and 3).
 //
 // GB300's float64 pipe runs at 1/64 of the float32 rate, costs a full warp
 // cycle even for partially active warps and takes ~1,100 cycles for a

@@ -72,7 +72,7 @@ template <typename TX>
 void sumsq(const TX* x, int64_t n, double* partials, double* out, Launch L);
 
 // ---------------------------------------------------------------- float64 small kernels
-// Gamma^(n) = *_{k != n} S^(k) (Algorithm 1 line 5), its Cholesky factor L,
+// Gamma^(n) = *_{k != n} S^(k) (Algorithm 1), its Cholesky factor L,
 // and (useV) Z = sum_{i<j; i,j != n} W_i * W_j * (*_{k not in {i,j,n}} S_k)
 // so that sum_{i<j} V^(n,i,j) = A^(n) Z (Eq. 3).  status[0] |= 1<<n if not PD.
 void gamma_chol(const double* S, const double* W, int N, int n, int R, double* Lout, double* Z,

@@ -1,5 +1,5 @@
-// Float64 kernels of the normal-equation update (Sec. 2.3, Algorithm 1 lines
-// 5-10, Algorithm 3 lines 11-17) and the fitness (Sec. 5).  R <= 128.
+// Float64 kernels of the normal-equation update (Sec. 2.3, the normal-equation
+// steps of Algorithms 1 and 3) and the fitness (Sec. 5).  R <= 128.
 #include <algorithm>
 
 #include "internal.h"

@@ -865,7 +865,7 @@ cpals_status cpals_tucker_init_factors(cpals_tucker* t, const double* const* fac
   for (int n = 0; n < 3; n++) {
     if (!factors[n]) return t->fail(CPALS_E_INVALID, "factor pointer is NULL");
     TK(cudaMemcpyAsync(t->A[n], factors[n], t->s[n] * t->R[n] * 8, cudaMemcpyHostToDevice, t->stream));
-    // Algorithm 4 line 2: dA <- A
+    // Algorithm 4 starts from dA <- A
     TK(cudaMemcpyAsync(t->dA[n], t->A[n], t->s[n] * t->R[n] * 8, cudaMemcpyDeviceToDevice, t->stream));
   }
   TK(cudaStreamSynchronize(t->stream));
@@ -921,7 +921,7 @@ cpals_status cpals_tucker_run(cpals_tucker* t, int max_sweeps, double eps, doubl
     if (eps > 0 && small()) {
       st = tucker_build(t);
       if (st != CPALS_OK) break;
-      // dA <- 0 (Algorithm 4 line 7)
+      // dA <- 0 after the operators are formed (Algorithm 4)
       for (int n = 0; n < 3; n++) t->scal_h[2 + 2 * n] = 0.0;
       bool first = true;
       while (st == CPALS_OK && k < max_sweeps && small()) {

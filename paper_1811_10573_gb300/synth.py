@@ -4,7 +4,7 @@ This module is the only one shared by the CUDA path's tests/bench and by the
 FP64 oracle's tests.  It draws random numbers and assembles input tensors; it
 holds none of the decomposition's arithmetic (no MTTKRP, no solve, no
 fitness).  The random numbers the method itself would draw (the initial
-factors of Algorithm 1, line 2) are drawn here and passed to both sides as
+factors that Algorithm 1 draws at its start) are drawn here and passed to both sides as
 inputs.
 
 Recipes (one per workload; sizes and distributions as the paper describes its
@@ -105,7 +105,7 @@ def make_problem(kind: str, dims, R, *, seed=0, noise=1e-2, relative=True,
     """Assemble X = [[A_true]] + noise and an initial guess.
 
     kind: "normal" | "uniform" | "collinear" (true factors' distribution).
-    init: "uniform" (U[0,1], Algorithm 1 line 2) | "normal".
+    init: "uniform" (U[0,1], the initial guess of Algorithm 1) | "normal".
     """
     dims = [int(d) for d in dims]
     meta = {}

@@ -117,7 +117,7 @@ def test_hurwitz_norm_preserving(s):
     assert abs(np.linalg.norm(z) - s) > 1e-6
 
 
-# --- normal-equation solve (Sec. 2.3, Algorithm 1 line 7) --------------------
+# --- normal-equation solve (Sec. 2.3, Algorithm 1) --------------------
 
 def test_solve_matches_library_spd():
     g = np.random.default_rng(8)
