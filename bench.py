@@ -286,7 +286,7 @@ def run_ours(args):
                        "network_decisions": round(statistics.mean(frac), 3)}
             ctx.set_controller(None)
 
-    # ALS variants of Sec. 5.3 (update step size 0.7; symmetric [[A, B, B]]
+    # ALS variants of Sec. 5.1 (update step size 0.7; symmetric [[A, B, B]]
     # with the B step 0.8 on a symmetric tensor of the same size), PP-ALS vs
     # ALS to their own float64-ALS targets
     variants = None

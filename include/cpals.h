@@ -86,7 +86,7 @@ void cpals_destroy(cpals_ctx* ctx);
  * the factors: call cpals_init_factors (again) afterwards. */
 cpals_status cpals_set_normal_arith(cpals_ctx* ctx, int arith);
 
-/* ALS variants of Sec. 5.3 (chemistry-tensor experiment), for ALS and PP
+/* ALS variants of Sec. 5.1 (chemistry-tensor experiment), for ALS and PP
  * sweeps alike.
  *
  * Update step size: lam[n] (N host values in (0, 2]; NULL = all 1) makes

@@ -235,7 +235,7 @@ def _lam(lam, n: int) -> float:
 
 
 def step(A_old: np.ndarray, A_ls: np.ndarray, lam: float) -> np.ndarray:
-    """ALS variant with an update step size (Sec. 5.3, chemistry tensor):
+    """ALS variant with an update step size (Sec. 5.1, chemistry tensor):
     A_new = (1 - lambda) A^(n) + lambda M^(n) Gamma^(n)+, where A_ls is the
     least-squares update M^(n) Gamma^(n)+ and A_old the current factor."""
     if lam == 1.0:
@@ -244,7 +244,7 @@ def step(A_old: np.ndarray, A_ls: np.ndarray, lam: float) -> np.ndarray:
 
 
 def _tie_copy(A, S, dA, n: int, tie):
-    """Symmetry constraint (Sec. 5.3, X = [[A, B, B]]): every mode tied to
+    """Symmetry constraint (Sec. 5.1, X = [[A, B, B]]): every mode tied to
     mode n takes mode n's new factor, Gram and change."""
     if not tie:
         return
@@ -262,7 +262,7 @@ def als_sweep(X: np.ndarray, A, S, info: SolveInfo | None = None, lam=None, tie=
     dA[n] = A^(n)_new - A^(n)_old (the per-sweep change used by Algorithm 3's
     regular sweep) and gnorm[n] = ||G^(n)||_F.
 
-    Variants of Sec. 5.3: ``lam`` is the update step size (see ``step``);
+    Variants of Sec. 5.1: ``lam`` is the update step size (see ``step``);
     ``tie`` maps a mode m2 to a mode m1 < m2 whose factor it shares (the
     symmetric decomposition [[A, B, B]] is tie = {2: 1}): mode m2 is not
     solved for, it takes mode m1's factor as soon as that is updated.
@@ -286,7 +286,7 @@ def als_sweep(X: np.ndarray, A, S, info: SolveInfo | None = None, lam=None, tie=
 
 def cp_als(X: np.ndarray, A0, n_sweeps: int, lam=None, tie=None):
     """Algorithm 1 for a fixed number of sweeps; returns (A, fitness trace).
-    ``lam`` and ``tie`` select the variants of Sec. 5.3 (see ``als_sweep``)."""
+    ``lam`` and ``tie`` select the variants of Sec. 5.1 (see ``als_sweep``)."""
     A = [a.copy() for a in A0]
     for m2, m1 in (tie or {}).items():
         A[m2] = A[m1].copy()              # tied factors start equal
@@ -412,7 +412,7 @@ def pp_cp_als(X: np.ndarray, A0, n_sweeps: int, eps: float, use_V: bool = True,
     sweep and a regular ALS sweep each count as one sweep; the reported
     fitness is always the exact one; the gradient stopping test is not used
     (fixed budgets).  ``on_sweep(kind, A)`` is called after every sweep.
-    ``lam`` and ``tie`` select the ALS variants of Sec. 5.3 for both sweep
+    ``lam`` and ``tie`` select the ALS variants of Sec. 5.1 for both sweep
     kinds (see ``als_sweep``).
     """
     A = [a.copy() for a in A0]

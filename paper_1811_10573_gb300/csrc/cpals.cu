@@ -34,7 +34,7 @@ struct cpals_ctx {
   int64_t dims[kMaxModes] = {0};
   int64_t total = 0;
   int h = 0;            // left half of the ALS tree: modes [0, h)
-  // ALS variants (Sec. 5.3): update step size per mode (1 = plain ALS), and
+  // ALS variants (Sec. 5.1): update step size per mode (1 = plain ALS), and
   // ties tie[m2] = m1 < m2 (mode m2 shares mode m1's factor; -1 = none)
   double lam[kMaxModes] = {1, 1, 1, 1, 1, 1, 1, 1};
   int tie[kMaxModes] = {-1, -1, -1, -1, -1, -1, -1, -1};
@@ -345,7 +345,7 @@ void finish_mode(cpals_ctx* c, int n, const T* rhs, bool pp, bool useV) {
                  pp, s, R, c->rownorm, c->scal + 8 + 2 * n, c->dpart, c->tickets, c->L());
 }
 
-// Symmetry constraint (Sec. 5.3, X = [[A, B, B]]): every mode tied to mode n
+// Symmetry constraint (Sec. 5.1, X = [[A, B, B]]): every mode tied to mode n
 // takes mode n's new factor and its derived state (compute copies, change,
 // Grams, W = A^T dA, norms) right after mode n's update; a tied mode is never
 // solved for.
@@ -1131,7 +1131,7 @@ cpals_status cpals_init_factors(cpals_ctx* c, const double* const* factors) {
   CK(cudaMemsetAsync(c->status, 0, 16, c->stream));
   for (int n = 0; n < c->N; n++) {
     const int64_t sR = c->dims[n] * R;
-    // a tied mode starts from its partner's factor (Sec. 5.3)
+    // a tied mode starts from its partner's factor (Sec. 5.1)
     const double* src = factors[tied(c, n) ? c->tie[n] : n];
     CK(cudaMemcpyAsync(c->A[n], src, sR * 8, cudaMemcpyHostToDevice, c->stream));
     // the start of Algorithm 3: dA <- A, S <- A^T A

@@ -941,7 +941,7 @@ __device__ __forceinline__ void dot2_acc(dfl& s, dfl a, dfl b) {
 // Group 0 writes the float64 master A, the double-float copy (Ahi = the float
 // compute copy, Alo), dA = A_new - ref (ref = A_p, or A_old when Arefhi is
 // null) as float64 and float, and per-row ||dA||^2, ||A_new||^2
-// (double-float).  With an update step size lam != 1 (Sec. 5.3) the new row
+// (double-float).  With an update step size lam != 1 (Sec. 5.1) the new row
 // is (1 - lam) A_old + lam a.
 constexpr int kRB = 4;
 
@@ -1076,7 +1076,7 @@ solve_inv_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float
 #pragma unroll
       for (int w = 0; w < kRB; w++) a[w] = df_add(dot2_val(acc[w]), upk(hp[w][rr]));
       if (lam != 1.0) {
-        // update step size (Sec. 5.3): (1 - lam) A_old + lam a
+        // update step size (Sec. 5.1): (1 - lam) A_old + lam a
         const dfl l1 = df_of(lam), l0 = df_of(1.0 - lam);
 #pragma unroll
         for (int w = 0; w < kRB; w++) a[w] = df_add(df_mul(l1, a[w]), df_mul(l0, dfl{oh[w], ol[w]}));

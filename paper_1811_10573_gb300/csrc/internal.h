@@ -82,7 +82,7 @@ void gamma_chol(const double* S, const double* W, int N, int n, int R, double* L
 // dA = A_new - (Aref ? Aref : A_old), compute-precision copies Ac, dAc and per-row
 // ||dA||^2, ||A_new||^2 into rownorm (2*s values).  Rows are left unchanged if
 // the factorisation failed for this mode (status bit set).  lam is the update
-// step size (Sec. 5.3): A_new = (1 - lam) A_old + lam rhs Gamma^{-1}.
+// step size (Sec. 5.1): A_new = (1 - lam) A_old + lam rhs Gamma^{-1}.
 template <typename T>
 void solve_rows(const T* rhs, double* A, const double* Aref, double* dA, const double* Lf, T* Ac,
                 T* dAc, double* rownorm, int s, int R, int n, double lam, const int* status,
@@ -130,7 +130,7 @@ void gram_df(const float* Ahi, const float* Alo, const float* Aw, const float* d
 // columns into Gpk; chol_df: Gamma^(n) (from Gpk when not null, else from the
 // Grams) = L L^T and Winv = L^-1 (row stride R|1, zero upper triangle);
 // solve_df: a = Winv^T Winv b per row, blended with the old row when the
-// update step size lam != 1 (Sec. 5.3).
+// update step size lam != 1 (Sec. 5.1).
 void chol_df(const float* Shi, const float* Slo, const float* W, const float2* Gpk, int N, int n,
              int R, float2* Winv, float* Z, bool useV, int* status, Launch L);
 void solve_df(const float* rhs, double* A, float* Ahi, float* Alo, const float* Arefhi,

@@ -125,7 +125,7 @@ __device__ __forceinline__ void put(double (&v)[kChunks], int c, double x) {
 
 // One warp per row y: forward substitution L z = b, back substitution
 // L^T a = z, i.e. a = b Gamma^{-1} (two triangular solves per row); with an
-// update step size lam != 1 (Sec. 5.3) the new row is (1 - lam) A_old + lam a.
+// update step size lam != 1 (Sec. 5.1) the new row is (1 - lam) A_old + lam a.
 template <typename TR, typename T>
 __global__ void __launch_bounds__(128)
 solve_rows_kernel(const TR* __restrict__ rhs, double* __restrict__ A,
@@ -179,7 +179,7 @@ solve_rows_kernel(const TR* __restrict__ rhs, double* __restrict__ A,
           if (r < i) b[c] = fma(-Ls[i * RS + r], ai, b[c]);
         }
       }
-      if (lam != 1.0)   // update step size (Sec. 5.3): (1 - lam) A_old + lam a
+      if (lam != 1.0)   // update step size (Sec. 5.1): (1 - lam) A_old + lam a
 #pragma unroll
         for (int c = 0; c < kChunks; c++) b[c] = (1.0 - lam) * old[c] + lam * b[c];
     }

@@ -169,7 +169,7 @@ def order6_24_rank50(seed=0) -> Problem:
 def symmetric_order3(sa, sb, R, *, seed=0, noise=1e-2, collinearity=None, storage="f32",
                      eps=0.1, sweeps=100, name=None) -> Problem:
     """Order-3 tensor symmetric in modes 1 and 2, X = [[A, B, B]] + noise
-    (the structure of Sec. 5.3's symmetric decomposition), noise symmetrised
+    (the structure of Sec. 5.1's symmetric decomposition), noise symmetrised
     over modes 1 and 2 and scaled relative to ||X||.  True factors N(0,1), or
     collinear with cosine C per factor when ``collinearity`` is given (C10
     construction).  Initial factors U[0,1] with A0[2] = A0[1]."""

@@ -1,4 +1,4 @@
-"""GPU parity of the ALS variants of Sec. 5.3 (update step size; symmetric
+"""GPU parity of the ALS variants of Sec. 5.1 (update step size; symmetric
 decomposition [[A, B, B]] with the B step 0.8) against the FP64 oracle, for
 ALS sweeps, PP sweeps and whole Algorithm 3 runs, in every precision.
 Tolerances as in test_gpu_parity.py."""

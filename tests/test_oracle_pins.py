@@ -437,7 +437,7 @@ def test_partial_row_matches_definitions(dims):
     assert np.allclose(O.partial_row(X, A, fixed), brute, rtol=1e-12, atol=1e-12)
 
 
-# --- Sec. 5.3 ALS variants: update step size and the symmetry constraint -------
+# --- Sec. 5.1 ALS variants: update step size and the symmetry constraint -------
 
 def _residual_sq(X, A):
     return float(np.sum((X - O.reconstruct(A)) ** 2))
@@ -478,7 +478,7 @@ def _lstsq_mode(X, A, n):
 
 
 def test_symmetric_sweep_matches_least_squares():
-    """[[A, B, B]] (Sec. 5.3): A takes the plain least-squares update with
+    """[[A, B, B]] (Sec. 5.1): A takes the plain least-squares update with
     (B, B); B the step-size-0.8 blend of its least-squares update with
     (A_new, B_old) in the other two modes; mode 2 then carries B."""
     g = np.random.default_rng(21)
