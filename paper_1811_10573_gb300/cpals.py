@@ -530,10 +530,11 @@ def cost_model(dims, R, kind):
 
 # ---------------------------------------------------------------- Tucker (order 3, float64)
 def cpals_tucker_create(dims, ranks):
-    d = (C.c_int64 * 3)(*[int(x) for x in dims])
-    r = (C.c_int * 3)(*[int(x) for x in ranks])
+    n = len(dims)
+    d = (C.c_int64 * n)(*[int(x) for x in dims])
+    r = (C.c_int * len(ranks))(*[int(x) for x in ranks])
     out = _ctx_p()
-    st = lib().cpals_tucker_create(d, 3, r, C.byref(out))
+    st = lib().cpals_tucker_create(d, n, r, C.byref(out))
     return st, out
 
 

@@ -44,6 +44,16 @@ def test_invalid_arguments_rejected_on_host(lib):
         assert st == 1 and not ctx, (dims, R, prec)
 
 
+def test_tucker_invalid_arguments_rejected_on_host(lib):
+    # order other than 3, an empty mode, a rank above its mode size or above
+    # 48, a mode above 4096: rejected before any device call
+    for dims, ranks in [([4, 5], [2, 2]), ([4, 5, 6, 7], [2, 2, 2, 2]), ([4, 0, 6], [2, 1, 2]),
+                        ([4, 5, 6], [5, 2, 2]), ([60, 60, 60], [49, 2, 2]), ([4, 5, 6], [2, 0, 2]),
+                        ([5000, 5, 6], [2, 2, 2])]:
+        st, t = cpals.cpals_tucker_create(dims, ranks)
+        assert st == 1 and not t, (dims, ranks)
+
+
 @pytest.mark.parametrize("N", [3, 4, 5, 6])
 def test_operator_tree_cost_is_papers(lib, N):
     """The operator dimension tree the library runs has exactly the paper's

@@ -64,7 +64,11 @@ def test_mttkrp(dims, R, prec):
             assert rel(g.mttkrp(n), ref) < TOL[prec], (n, prec)
 
 
-@pytest.mark.parametrize("dims,R", [([40, 33, 27], 9), ([11, 13, 9, 10], 6), ([6, 7, 5, 6, 4], 4)])
+# the largest order (8), order 7, and modes of size 1 (degenerate unfoldings)
+EDGE = [([3, 2, 4, 2, 3, 2, 2], 3), ([2, 3, 2, 2, 3, 2, 2, 3], 2), ([1, 9, 7], 4), ([8, 1, 6, 5], 3)]
+
+
+@pytest.mark.parametrize("dims,R", [([40, 33, 27], 9), ([11, 13, 9, 10], 6), ([6, 7, 5, 6, 4], 4)] + EDGE)
 def test_als_sweeps_fp64(dims, R):
     p = synth.make_problem("normal", dims, R, seed=5, storage="f64")
     A = [a.copy() for a in p.A0]
@@ -78,7 +82,9 @@ def test_als_sweeps_fp64(dims, R):
                 assert rel(a, b) < 1e-10, sweep
             ratios = g.get_dA_ratios()
             want = [np.linalg.norm(d) / np.linalg.norm(a) for d, a in zip(dA_ref, A)]
-            np.testing.assert_allclose(ratios, want, rtol=1e-9)
+            # a mode of size 1 settles after one sweep: its ratio is then
+            # rounding noise (~1e-16), compared absolutely
+            np.testing.assert_allclose(ratios, want, rtol=1e-9, atol=1e-13)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -102,6 +108,12 @@ def test_pp_operators(dims, R, prec):
             assert not np.any(g.get_state("dA", n))
 
 
+def _dA_close(got, want, A):
+    """dA agrees to 1e-9 relative, or to rounding (1e-13 of the factor) when
+    the reference itself is rounding noise (a settled mode)."""
+    return rel(got, want) < 1e-9 or np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(A))
+
+
 @pytest.mark.parametrize("dims,R", [([40, 33, 27], 9), ([11, 13, 9, 10], 6), ([6, 7, 5, 6, 4], 4)])
 def test_pp_sweeps_fp64(dims, R):
     """Algorithm 3's PP sweeps (with and without V) against the oracle, and the
@@ -121,7 +133,38 @@ def test_pp_sweeps_fp64(dims, R):
             O.pp_sweep(ops, Mp, A, Ap, dA, S, useV)
             for n, (a, b) in enumerate(zip(g.get_factors(), A)):
                 assert rel(a, b) < 1e-10, (sweep, n)
-                assert rel(g.get_state("dA", n), dA[n]) < 1e-9, (sweep, n)
+                assert _dA_close(g.get_state("dA", n), dA[n], A[n]), (sweep, n)
+        A_g = g.get_factors()
+        dA_g = [g.get_state("dA", n) for n in range(len(dims))]
+        for n in range(len(dims)):
+            for useV in (False, True):
+                ref = O.pp_mttkrp(ops, Mp, A_g, dA_g, n, useV)
+                assert rel(g.pp_mttkrp(n, useV), ref) < 1e-10, (n, useV)
+
+
+@pytest.mark.parametrize("dims,R", EDGE)
+def test_pp_sweep_edge_shapes_fp64(dims, R):
+    """Orders 7 and 8 and modes of size 1: one PP sweep against the oracle,
+    then the approximated right-hand sides (Eq. 3, with and without V) on the
+    state the GPU holds.  Only one sweep: on these tiny tensors the PP
+    iteration itself amplifies a 1e-15 perturbation of the factors to 1e-8
+    within two sweeps (measured in the oracle), so later sweeps compare
+    rounding paths, not the method."""
+    p = synth.make_problem("normal", dims, R, seed=9, storage="f64")
+    with _ctx(p, "fp64") as g:
+        for _ in range(2):
+            g.als_sweep()
+        A = g.get_factors()
+        S = [O.gram(a) for a in A]
+        g.pp_build_operators()
+        Ap = [a.copy() for a in A]
+        ops, Mp = O.pp_operators(p.X, Ap)
+        dA = [np.zeros_like(a) for a in A]
+        g.pp_sweep(use_V=True)
+        O.pp_sweep(ops, Mp, A, Ap, dA, S, True)
+        for n, (a, b) in enumerate(zip(g.get_factors(), A)):
+            assert rel(a, b) < 1e-10, n
+            assert _dA_close(g.get_state("dA", n), dA[n], A[n]), n
         A_g = g.get_factors()
         dA_g = [g.get_state("dA", n) for n in range(len(dims))]
         for n in range(len(dims)):
