@@ -193,9 +193,11 @@ cpals_status cpals_run_batch(cpals_ctx* const* ctxs, int n, int workers, int max
  * the R_n leading eigenvectors of W = Y_(n) Y_(n)^T (Y^(n) the TTMc) in
  * decreasing eigenvalue order, each column signed to a non-negative inner
  * product with the column it replaces; the eigenvectors come from subspace
- * iteration started at the current factor (cpals_tucker_set_iterations,
- * default 8) and a Rayleigh-Ritz step, so a factor is exact once the
- * iteration has converged (a spectral gap after R_n).  Fitness: 1 -
+ * iteration started at the current factor (at most
+ * cpals_tucker_set_iterations steps, default 8; it stops once the invariance
+ * residual ||W Q - Q Q^T W Q|| / ||W Q|| is below 1e-13) and a Rayleigh-Ritz
+ * step, so a factor is exact once the iteration has converged (a spectral
+ * gap after R_n).  Fitness: 1 -
  * sqrt(||X||^2 - ||G||^2) / ||X||.  Errors as for the CP context;
  * CPALS_E_SINGULAR if an orthonormalisation met a non-positive pivot. */
 typedef struct cpals_tucker cpals_tucker;

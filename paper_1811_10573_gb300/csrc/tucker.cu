@@ -69,7 +69,9 @@ __global__ void __launch_bounds__(256) syrk_kernel(const double* __restrict__ Y,
 // warp order.
 __global__ void __launch_bounds__(256) rowmm_kernel(const double* __restrict__ P,
                                                     const double* __restrict__ B, int K, int R,
-                                                    double* __restrict__ out) {
+                                                    double* __restrict__ out,
+                                                    const int* __restrict__ skip) {
+  if (skip && *skip) return;                 // the subspace iteration has converged
   __shared__ double red[8][64];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t i = blockIdx.x;
@@ -119,7 +121,9 @@ __global__ void __launch_bounds__(256) rowmm_kernel(const double* __restrict__ P
 // (rows_per_block consecutive rows; 32 rows staged in shared memory at a time)
 __global__ void __launch_bounds__(256) atb_part_kernel(const double* __restrict__ P,
                                                        const double* __restrict__ Q, int s, int R,
-                                                       int rows_per_block, double* __restrict__ part) {
+                                                       int rows_per_block, double* __restrict__ part,
+                                                       const int* __restrict__ skip) {
+  if (skip && *skip) return;
   __shared__ double ps[32][kTuckerMaxRank + 1], qs[32][kTuckerMaxRank + 1];
   const int r0 = blockIdx.x * rows_per_block, r1 = min(s, r0 + rows_per_block);
   const int RR = R * R;
@@ -159,7 +163,9 @@ __global__ void __launch_bounds__(256) atb_part_kernel(const double* __restrict_
 // then solves q L^T = z for its rows (one warp per row).  Z and Q may alias.
 __global__ void __launch_bounds__(256) cholqr_kernel(const double* __restrict__ part, int nb,
                                                      const double* Z, int s, int R, double* Q,
-                                                     int* __restrict__ status) {
+                                                     int* __restrict__ status,
+                                                     const int* __restrict__ skip) {
+  if (skip && *skip) return;
   __shared__ double L[kTuckerMaxRank][kTuckerMaxRank + 1];
   __shared__ double dinv[kTuckerMaxRank];
   const int RR = R * R;
@@ -200,6 +206,78 @@ __global__ void __launch_bounds__(256) cholqr_kernel(const double* __restrict__ 
     }
     if (lane < R) Q[(int64_t)i * R + lane] = z0;
     if (lane + 32 < R) Q[(int64_t)i * R + lane + 32] = z1;
+  }
+}
+
+// Convergence test of the subspace iteration: with Z = W Q and H = Q^T Z
+// (the sum of nb partials), the invariance residual ||Z - Q H||_F^2 against
+// ||Z||_F^2.  Every CTA sums the partials in block order and takes rows (one
+// warp per row); the last CTA to finish adds the CTAs' sums in block order and
+// sets *done when residual^2 <= tol2 * ||Z||^2, then re-arms the ticket.
+__global__ void __launch_bounds__(256) resid_kernel(const double* __restrict__ part, int nb,
+                                                    const double* __restrict__ Q,
+                                                    const double* __restrict__ Z, int s, int R,
+                                                    double tol2, double* __restrict__ rpart,
+                                                    int* __restrict__ ticket, int* __restrict__ done) {
+  if (*done) return;
+  __shared__ double H[kTuckerMaxRank][kTuckerMaxRank + 1];
+  __shared__ double red[2][8];
+  __shared__ bool last;
+  const int RR = R * R;
+  for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    double v = 0.0;
+    for (int b = 0; b < nb; b++) v += part[(int64_t)b * RR + e];
+    H[e / R][e % R] = v;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double r2 = 0.0, z2 = 0.0;
+  for (int i = blockIdx.x * nw + warp; i < s; i += gridDim.x * nw) {
+    const double q0 = lane < R ? Q[(int64_t)i * R + lane] : 0.0;
+    const double q1 = lane + 32 < R ? Q[(int64_t)i * R + lane + 32] : 0.0;
+    const double z0 = lane < R ? Z[(int64_t)i * R + lane] : 0.0;
+    const double z1 = lane + 32 < R ? Z[(int64_t)i * R + lane + 32] : 0.0;
+    double a0 = 0.0, a1 = 0.0;
+    for (int k = 0; k < R; k++) {
+      const double qk = __shfl_sync(0xffffffffu, k < 32 ? q0 : q1, k & 31);
+      if (lane < R) a0 = fma(qk, H[k][lane], a0);
+      if (lane + 32 < R) a1 = fma(qk, H[k][lane + 32], a1);
+    }
+    const double d0 = z0 - a0, d1 = z1 - a1;
+    r2 = fma(d0, d0, fma(d1, d1, r2));
+    z2 = fma(z0, z0, fma(z1, z1, z2));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    z2 += __shfl_xor_sync(0xffffffffu, z2, o);
+  }
+  if (lane == 0) {
+    red[0][warp] = r2;
+    red[1][warp] = z2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < nw; w++) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    rpart[2 * blockIdx.x] = a;
+    rpart[2 * blockIdx.x + 1] = b;
+    __threadfence();
+    last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const volatile double* vp = rpart;
+    double a = 0.0, b = 0.0;
+    for (int blk = 0; blk < (int)gridDim.x; blk++) {
+      a += vp[2 * blk];
+      b += vp[2 * blk + 1];
+    }
+    if (a <= tol2 * b) *done = 1;
+    *ticket = 0;
   }
 }
 
@@ -473,6 +551,8 @@ struct cpals_tucker {
   double *T = nullptr, *U = nullptr, *Y = nullptr, *Yt = nullptr, *G = nullptr;
   double *W = nullptr, *Z = nullptr, *Q = nullptr, *C = nullptr, *V = nullptr, *lam = nullptr;
   double* part = nullptr;              // 3 * kTuckerMaxRank * 2 column norms
+  double* C2 = nullptr;                // partial Grams of the convergence test
+  double* rpart = nullptr;             // per-CTA residual sums
   double* gpart = nullptr;             // K-split partial sums of the contractions
   int64_t gpart_cap = 0;
   double* ops[3] = {nullptr, nullptr, nullptr};   // (1,2), (1,3), (2,3) in 1-based mode pairs
@@ -542,11 +622,12 @@ cpals_status first_level(cpals_tucker* t, const double* A, double* out, int64_t 
   return CPALS_OK;
 }
 
-// nb partial Grams of P^T Q (s rows of R) into t->C
-int atb_parts(cpals_tucker* t, const double* P, const double* Q, int s, int R) {
+// nb partial Grams of P^T Q (s rows of R) into dst (skipped once *skip is set)
+int atb_parts(cpals_tucker* t, const double* P, const double* Q, int s, int R, double* dst,
+              const int* skip) {
   const int rpb = (int)std::max<int64_t>(32, cdivt(cdivt(s, 128), 32) * 32);
   const int nb = (int)cdivt(s, rpb);
-  atb_part_kernel<<<(unsigned)nb, 256, 0, t->stream>>>(P, Q, s, R, rpb, t->C);
+  atb_part_kernel<<<(unsigned)nb, 256, 0, t->stream>>>(P, Q, s, R, rpb, dst, skip);
   t->launches++;
   return nb;
 }
@@ -558,25 +639,36 @@ cpals_status eig_update(cpals_tucker* t, int n, const double* Yn, int64_t K, con
   syrk_kernel<<<dim3(tiles, tiles), 256, 0, t->stream>>>(Yn, s, (int)K, t->W);
   t->launches++;
   const unsigned rows_grid = (unsigned)std::min<int64_t>(cdivt(s, 8), 152);
-  auto cholqr = [&](const double* in) {
-    const int nb = atb_parts(t, in, in, s, R);
-    cholqr_kernel<<<rows_grid, 256, 0, t->stream>>>(t->C, nb, in, s, R, t->Q, t->status);
+  int* done = t->status + 2;
+  TK(cudaMemsetAsync(done, 0, sizeof(int), t->stream));
+  auto cholqr = [&](const double* in, const int* skip) {
+    const int nb = atb_parts(t, in, in, s, R, t->C, skip);
+    cholqr_kernel<<<rows_grid, 256, 0, t->stream>>>(t->C, nb, in, s, R, t->Q, t->status, skip);
     t->launches++;
   };
   // subspace iteration from the current factor: Z = W Q, orthonormalised by
-  // Cholesky QR (once; twice on the last iteration)
+  // Cholesky QR.  From the second step on, the invariance residual of the
+  // current basis is tested first; once it is below 1e-13 the remaining steps
+  // return at entry (no host round trip).  A last Cholesky QR pass always runs.
   const double* src = t->A[n];
   for (int it = 0; it < t->iters; it++) {
-    rowmm_kernel<<<(unsigned)s, 256, 0, t->stream>>>(t->W, src, s, R, t->Z);
+    const int* skip = it ? done : nullptr;
+    rowmm_kernel<<<(unsigned)s, 256, 0, t->stream>>>(t->W, src, s, R, t->Z, skip);
     t->launches++;
-    cholqr(t->Z);
-    if (it == t->iters - 1) cholqr(t->Q);
+    if (it) {
+      const int nb2 = atb_parts(t, src, t->Z, s, R, t->C2, skip);
+      resid_kernel<<<rows_grid, 256, 0, t->stream>>>(t->C2, nb2, src, t->Z, s, R, 1e-26, t->rpart,
+                                                     t->status + 3, done);
+      t->launches++;
+    }
+    cholqr(t->Z, skip);
     src = t->Q;
   }
+  cholqr(t->Q, nullptr);
   // Rayleigh-Ritz: H = Q^T W Q, its eigenvectors V, A = Q V
-  rowmm_kernel<<<(unsigned)s, 256, 0, t->stream>>>(t->W, t->Q, s, R, t->Z);
+  rowmm_kernel<<<(unsigned)s, 256, 0, t->stream>>>(t->W, t->Q, s, R, t->Z, nullptr);
   t->launches++;
-  const int nb = atb_parts(t, t->Q, t->Z, s, R);
+  const int nb = atb_parts(t, t->Q, t->Z, s, R, t->C, nullptr);
   jacobi_kernel<<<1, 256, 0, t->stream>>>(t->C, nb, R, t->V, t->lam);
   qv_sign_kernel<<<(unsigned)R, 256, 0, t->stream>>>(t->Q, t->V, s, R, t->A[n], Aref, t->dA[n],
                                                     t->part + 2 * kTuckerMaxRank * n);
@@ -735,6 +827,8 @@ cpals_status cpals_tucker_create(const int64_t* dims, int N, const int* ranks, c
   al(&t->Z, smax * kTuckerMaxRank);
   al(&t->Q, smax * kTuckerMaxRank);
   al(&t->C, 128 * kTuckerMaxRank * kTuckerMaxRank);   // up to 128 partial Grams
+  al(&t->C2, 128 * kTuckerMaxRank * kTuckerMaxRank);
+  al(&t->rpart, 2 * 152);
   t->gpart_cap = std::max<int64_t>(1 << 20, 4 * Ymax);
   al(&t->gpart, t->gpart_cap);
   al(&t->V, kTuckerMaxRank * kTuckerMaxRank);
@@ -770,7 +864,7 @@ void cpals_tucker_destroy(cpals_tucker* t) {
   for (int n = 0; n < 3; n++) {
     F(t->A[n]); F(t->Ap[n]); F(t->dA[n]); F(t->ops[n]); F(t->Mp[n]);
   }
-  F(t->T); F(t->U); F(t->Y); F(t->Yt); F(t->G); F(t->W); F(t->Z); F(t->Q); F(t->C);
+  F(t->T); F(t->U); F(t->Y); F(t->Yt); F(t->G); F(t->W); F(t->Z); F(t->Q); F(t->C); F(t->C2); F(t->rpart);
   F(t->V); F(t->lam); F(t->part); F(t->gpart); F(t->scal); F(t->status);
   F(t->Xb); F(t->Bt); F(t->outf); F(t->gpartf); F(t->umma_sched);
   if (t->scal_h) cudaFreeHost(t->scal_h);
