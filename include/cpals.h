@@ -390,6 +390,14 @@ cpals_status cpals_contract_bf16_noalloc(const void* Xb, const void* Bt, float* 
  * Table 1.  Returns CPALS_E_INVALID on bad sizes. */
 cpals_status cpals_cost_model(const int64_t* dims, int N, int R, int kind, double* flops);
 
+/* Flop counts of the contractions the order-3 Tucker context launches for
+ * one step (0 = Tucker-ALS sweep TTMc, 1 = PP operator build, 2 = PP
+ * approximated sweep, 3 = the paper's operator-construction sum
+ * 2 sum_{l=2}^{N-1} C(l+1,2) s^{N-l+2} R^{l-1} for equal sizes and ranks)
+ * for dims[0..2] and ranks[0..2]; eigen-updates not counted.  Sec. 3.2.2,
+ * Table 1.  CPALS_E_INVALID on bad sizes or kind. */
+cpals_status cpals_tucker_cost_model(const int64_t* dims, const int* ranks, int kind, double* flops);
+
 #ifdef __cplusplus
 }
 #endif

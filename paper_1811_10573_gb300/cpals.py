@@ -72,6 +72,7 @@ _SIGS = {
     "cpals_tucker_get_factors": (C.c_int, [_ctx_p, C.POINTER(_dp)]),
     "cpals_tucker_get_core": (C.c_int, [_ctx_p, _dp]),
     "cpals_tucker_last_error": (C.c_char_p, [_ctx_p]),
+    "cpals_tucker_cost_model": (C.c_int, [_i64p, _ip, C.c_int, _dp]),
     "cpals_run_controlled": (C.c_int, [_ctx_p, C.c_int, C.c_double, C.c_int, C.c_double, _dp,
                                        _ip, _dp, _ip, _ip, _ip]),
     "cpals_controller_log": (C.c_int, [_ctx_p, C.c_int, C.c_double, C.c_int, _fp, _ip, _dp, _dp,
@@ -544,6 +545,14 @@ def cpals_tucker_destroy(t):
 
 def cpals_tucker_set_iterations(t, iters):
     return lib().cpals_tucker_set_iterations(t, iters)
+
+
+def cpals_tucker_cost_model(dims, ranks, kind):
+    d = (C.c_int64 * 3)(*[int(x) for x in dims])
+    r = (C.c_int * 3)(*[int(x) for x in ranks])
+    f = C.c_double()
+    st = lib().cpals_tucker_cost_model(d, r, int(kind), C.byref(f))
+    return st, f.value
 
 
 def cpals_tucker_set_precision(t, precision):

@@ -1065,4 +1065,38 @@ cpals_status cpals_tucker_get_core(cpals_tucker* t, double* out) {
 
 const char* cpals_tucker_last_error(const cpals_tucker* t) { return t ? t->err.c_str() : "null context"; }
 
+cpals_status cpals_tucker_cost_model(const int64_t* dims, const int* ranks, int kind, double* flops) {
+  if (!dims || !ranks || !flops) return CPALS_E_INVALID;
+  for (int n = 0; n < 3; n++)
+    if (dims[n] < 1 || ranks[n] < 1) return CPALS_E_INVALID;
+  const double s1 = (double)dims[0], s2 = (double)dims[1], s3 = (double)dims[2];
+  const double R1 = ranks[0], R2 = ranks[1], R3 = ranks[2];
+  const double X = s1 * s2 * s3;
+  double f = 0.0;
+  if (kind == 0) {
+    // T = X x3 A3, Y1 = T x2 A2, Y2 = T x1 A1, U = X x1 A1, Y3 = U x2 A2, G = Y3 x3 A3
+    f = 2 * X * R3 + 2 * s1 * s2 * R3 * R2 + 2 * s1 * s2 * R3 * R1 + 2 * X * R1 +
+        2 * s2 * s3 * R1 * R2 + 2 * s3 * R1 * R2 * R3;
+  } else if (kind == 1) {
+    // three first-level operators, then Y_p^(1), Y_p^(2), Y_p^(3)
+    f = 2 * X * (R1 + R2 + R3) + 2 * s1 * s2 * R3 * R2 + 2 * s1 * s2 * R3 * R1 +
+        2 * s2 * s3 * R1 * R2;
+  } else if (kind == 2) {
+    // two first-order corrections per mode, then the core estimate
+    f = 2 * s1 * s2 * R3 * R2 + 2 * s1 * s3 * R2 * R3 + 2 * s1 * s2 * R3 * R1 +
+        2 * s2 * s3 * R1 * R3 + 2 * s1 * s3 * R2 * R1 + 2 * s2 * s3 * R1 * R2 +
+        2 * s3 * R1 * R2 * R3;
+  } else if (kind == 3) {
+    // the paper's operator-construction sum for N = 3 (one level, l = 2):
+    // 2 C(3,2) s^3 R, equidimensional
+    if (dims[0] != dims[1] || dims[1] != dims[2] || ranks[0] != ranks[1] || ranks[1] != ranks[2])
+      return CPALS_E_INVALID;
+    f = 2.0 * 3.0 * X * R1;
+  } else {
+    return CPALS_E_INVALID;
+  }
+  *flops = f;
+  return CPALS_OK;
+}
+
 }  // extern "C"

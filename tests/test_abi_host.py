@@ -54,6 +54,30 @@ def test_tucker_invalid_arguments_rejected_on_host(lib):
         assert st == 1 and not t, (dims, ranks)
 
 
+@pytest.mark.parametrize("s,R", [(400, 20), (2000, 10), (120, 12)])
+def test_tucker_costs_table1(lib, s, R):
+    """The order-3 Tucker context's contraction counts against Table 1's
+    Tucker row (DT-ALS 4 s^N R, PP operators 6 s^N R, approximated step at
+    most 2 N^2 s^2 R^{N-1}) and the paper's operator-construction sum."""
+    def cost(kind, dims=(s, s, s), ranks=(R, R, R)):
+        st, f = cpals.cpals_tucker_cost_model(dims, ranks, kind)
+        assert st == 0, kind
+        return f
+    als, build, pp, paper = cost(0), cost(1), cost(2), cost(3)
+    assert paper == 6 * s**3 * R                               # 2 C(3,2) s^3 R
+    assert 4 * s**3 * R < als <= 4 * s**3 * R * (1 + 3 * R / s)
+    assert paper < build <= paper * (1 + 2 * R / s)           # + the Y_p^(n)
+    # N(N-1) first-order corrections of 2 s^2 R^2 each, plus the core estimate
+    assert 12 * s**2 * R**2 < pp <= 2 * 9 * s**2 * R**2 + 2 * s * R**3
+    # uneven sizes and ranks: every term scales with its own modes
+    f0 = cost(0, (30, 40, 50), (2, 3, 4))
+    assert f0 == 2 * 60000 * 4 + 2 * 1200 * 12 + 2 * 1200 * 8 + 2 * 60000 * 2 + 2 * 2000 * 6 + 2 * 50 * 24
+    for kind, dims, ranks in [(3, (30, 40, 50), (2, 2, 2)), (4, (8, 8, 8), (2, 2, 2)),
+                              (0, (8, 0, 8), (2, 2, 2)), (0, (8, 8, 8), (2, 0, 2))]:
+        st, _ = cpals.cpals_tucker_cost_model(dims, ranks, kind)
+        assert st == 1, (kind, dims, ranks)
+
+
 @pytest.mark.parametrize("N", [3, 4, 5, 6])
 def test_operator_tree_cost_is_papers(lib, N):
     """The operator dimension tree the library runs has exactly the paper's
