@@ -334,7 +334,10 @@ def run_ours(args):
         with open(PROFILE) as f:
             prof = json.load(f)
         h = hashlib.sha256(open(UMMA_SRC, "rb").read()).hexdigest()
-        if prof.get("source_sha256") == h and prof.get("precision") == args.precision:
+        # DRAM bytes from the committed ncu capture, valid only for the workload
+        # and precision it was taken on and while the kernel source is unchanged
+        if (prof.get("source_sha256") == h and prof.get("precision") == args.precision
+                and str(prof.get("workload", "")).startswith(args.workload)):
             traffic = prof.get("traffic_bytes_per_launch")
     roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(ach / pk["hbm_gbs"], 4), "traffic": traffic,
