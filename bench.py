@@ -580,9 +580,13 @@ def run_reference(args):
         if i >= args.warmup:
             vals.append(project(ts, counts or {"als": p.sweeps}))
     value = statistics.mean(vals)
+    if counts:
+        sched = (f"the oracle's own schedule to the target {counts} "
+                 "(tests/golden/order3_400_rank100_schedule.json)")
+    else:
+        sched = f"the workload's sweep budget ({p.sweeps} ALS sweeps)"
     sample = ("float64 numpy oracle on the full workload, each step one ALS sweep, one PP "
-              "operator build, one PP sweep and one exact fitness, projected onto the oracle's "
-              f"own schedule to the target {counts} (tests/golden/order3_400_rank100_schedule.json)")
+              "operator build, one PP sweep and one exact fitness, projected onto " + sched)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "s",
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
