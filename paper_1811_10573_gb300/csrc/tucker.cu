@@ -117,6 +117,51 @@ __global__ void __launch_bounds__(256) rowmm_kernel(const double* __restrict__ P
   }
 }
 
+// Batched small contraction out[b][m][r] = sum_k in[(b K + k) M + m] B[k R + r]
+// for M, R <= 48 (the second-level TTMs and PP terms whose kept mode is a
+// rank): one CTA per b owns its M x R outputs exactly (no padded FMAs on the
+// FP64 pipe); 16 k at a time staged in shared memory, each output summed in
+// k order.
+__global__ void __launch_bounds__(256) bsmall_kernel(const double* __restrict__ in,
+                                                     const double* __restrict__ B, int K, int M,
+                                                     int R, double* __restrict__ out) {
+  constexpr int kQ = (kTuckerMaxRank * kTuckerMaxRank + 255) / 256;
+  __shared__ double is[16][kTuckerMaxRank], bs[16][kTuckerMaxRank];
+  const double* inb = in + (int64_t)blockIdx.x * K * M;
+  const int MR = M * R;
+  double acc[kQ];
+#pragma unroll
+  for (int q = 0; q < kQ; q++) acc[q] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    const int n = min(16, K - k0);
+    for (int e = threadIdx.x; e < 16 * M; e += blockDim.x) {
+      const int kk = e / M, m = e % M;
+      is[kk][m] = kk < n ? inb[(int64_t)(k0 + kk) * M + m] : 0.0;
+    }
+    for (int e = threadIdx.x; e < 16 * R; e += blockDim.x) {
+      const int kk = e / R, r = e % R;
+      bs[kk][r] = kk < n ? B[(int64_t)(k0 + kk) * R + r] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+      const int e = threadIdx.x + 256 * q;
+      if (e < MR) {
+        const int m = e / R, r = e % R;
+        double v = acc[q];
+        for (int kk = 0; kk < n; kk++) v = fma(is[kk][m], bs[kk][r], v);
+        acc[q] = v;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < kQ; q++) {
+    const int e = threadIdx.x + 256 * q;
+    if (e < MR) out[(int64_t)blockIdx.x * MR + e] = acc[q];
+  }
+}
+
 // part[blk][a][c] = sum over the block's rows i of P[i R + a] Q[i R + c]
 // (rows_per_block consecutive rows; 32 rows staged in shared memory at a time)
 __global__ void __launch_bounds__(256) atb_part_kernel(const double* __restrict__ P,
@@ -594,6 +639,11 @@ namespace {
 // so that the grid covers the SMs at least twice
 void gemm(cpals_tucker* t, const double* in, const double* B, double* out, int64_t batch, int64_t K,
           int64_t M, int R, bool kmajor) {
+  if (!kmajor && batch > 1 && M <= kTuckerMaxRank && R <= kTuckerMaxRank && batch < (1ll << 31)) {
+    bsmall_kernel<<<(unsigned)batch, 256, 0, t->stream>>>(in, B, (int)K, (int)M, R, out);
+    t->launches++;
+    return;
+  }
   const int sp = gemm_simt_splits(batch, K, M, R, kmajor, t->gpart_cap, 2 * 152);
   gemm_simt<double, double>(in, B, out, t->gpart, batch, K, M, R, kmajor, sp, t->L());
 }
