@@ -3,7 +3,6 @@ rank, only timings cross ranks) on CPU with the gloo backend, world size 2."""
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 
