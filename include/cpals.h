@@ -197,12 +197,21 @@ cpals_status cpals_run_batch(cpals_ctx* const* ctxs, int n, int workers, int max
  * cpals_tucker_set_iterations steps, default 8; it stops once the invariance
  * residual ||W Q - Q Q^T W Q|| / ||W Q|| is below 1e-13) and a Rayleigh-Ritz
  * step, so a factor is exact once the iteration has converged (a spectral
- * gap after R_n).  Fitness: 1 -
- * sqrt(||X||^2 - ||G||^2) / ||X||.  Errors as for the CP context;
- * CPALS_E_SINGULAR if an orthonormalisation met a non-positive pivot. */
+ * gap after R_n).  Fitness: 1 - sqrt(||X||^2 - ||G||^2) / ||X||.
+ * The context owns all device memory and one stream; every call returns
+ * after its work has finished.  Errors as for the CP context; E_STATE for a
+ * sweep before set_tensor and init_factors, or a PP sweep before
+ * pp_build_operators; CPALS_E_SINGULAR if an orthonormalisation met a
+ * non-positive pivot; CPALS_E_TIMEOUT if the tensor-core kernel gave up
+ * waiting (mixed precision). */
 typedef struct cpals_tucker cpals_tucker;
+/* dims[0..2], ranks[0..2] (host, read only), N must be 3; *out receives the
+ * context or NULL.  E_INVALID for bad sizes, E_UNSUPPORTED off sm_103,
+ * E_OOM if the buffers do not fit. */
 cpals_status cpals_tucker_create(const int64_t* dims, int N, const int* ranks, cpals_tucker** out);
+/* frees everything the context owns; NULL is a no-op */
 void cpals_tucker_destroy(cpals_tucker* t);
+/* maximum subspace-iteration steps per factor update, 1..1000 (E_INVALID otherwise) */
 cpals_status cpals_tucker_set_iterations(cpals_tucker* t, int iters);
 /* CPALS_FP64 (default) or CPALS_MIXED_BF16: the first-level TTMs (X x_3 A3,
  * X x_1 A1, and the three PP operators X x_k A_p) run on the tensor cores
@@ -213,9 +222,14 @@ cpals_status cpals_tucker_set_iterations(cpals_tucker* t, int iters);
  * multiples of 8), CPALS_E_INVALID for another value.  May be called before
  * or after cpals_tucker_set_tensor. */
 cpals_status cpals_tucker_set_precision(cpals_tucker* t, int precision);
-/* data: row-major, last mode fastest; dtype 0 = float64, 1 = float32 (copied) */
+/* data: row-major, last mode fastest, s_1 s_2 s_3 values; dtype 0 = float64,
+ * 1 = float32 (widened); on_device selects a device or a host pointer.  The
+ * tensor is copied (the caller keeps ownership) and ||X||^2 is formed in
+ * float64.  Invalidates the PP operators.  E_INVALID for a NULL pointer or
+ * another dtype. */
 cpals_status cpals_tucker_set_tensor(cpals_tucker* t, const void* data, int dtype, int on_device);
-/* three host arrays (orthonormal columns; e.g. the HOSVD); dA <- A, as Algorithm 4 starts */
+/* three host arrays s_n x R_n (orthonormal columns; e.g. the HOSVD), copied;
+ * dA <- A, as Algorithm 4 starts.  E_INVALID for a NULL pointer. */
 cpals_status cpals_tucker_init_factors(cpals_tucker* t, const double* const* factors);
 /* one HOOI sweep (Algorithm 2); *fitness (nullable) exact */
 cpals_status cpals_tucker_als_sweep(cpals_tucker* t, double* fitness);
@@ -229,9 +243,13 @@ cpals_status cpals_tucker_run(cpals_tucker* t, int max_sweeps, double eps, doubl
                               int* kind_trace, int* n_done);
 /* exact fitness at the current factors (also refreshes the core) */
 cpals_status cpals_tucker_fitness(cpals_tucker* t, double* out);
+/* copies the factors into three caller-owned host buffers of s_n x R_n */
 cpals_status cpals_tucker_get_factors(cpals_tucker* t, double* const* out);
-/* the core of the last sweep or fitness call */
+/* the core of the last sweep or fitness call into a caller-owned host
+ * buffer of R_1 R_2 R_3 values (in PP sweeps the estimate from Y~^(3)) */
 cpals_status cpals_tucker_get_core(cpals_tucker* t, double* out);
+/* message of the last failure on this context (owned by the context, valid
+ * until its next call; "" if none) */
 const char* cpals_tucker_last_error(const cpals_tucker* t);
 
 /* Message describing the last failure on this context ("" if none). */
