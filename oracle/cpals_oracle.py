@@ -22,7 +22,9 @@ with no blocking, fusion or reordering beyond those definitions.
 
 Pinned by the tests in ``tests/test_oracle_pins.py`` (brute-force MTTKRP,
 closed forms, invariants, Hurwitz unit-condition tensors from the appendix,
-exact low-rank recovery, the t^2 scaling of the PP error).  Parity unpinned:
+exact low-rank recovery, the t^2 scaling of the PP error, and the sweep
+sequence of ``pp_cp_als`` against eps crossings fixed by a plain ALS trace and
+the Algorithm 3 rule re-derived from the factor history).  Parity unpinned:
 the long-run fitness trajectory of ``pp_cp_als`` against the paper's own
 experiments (its figures are not recoverable and its seeds are unknown); only
 its parts are pinned.

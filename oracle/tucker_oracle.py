@@ -27,7 +27,8 @@ Readings (where the paper leaves room):
 Pinned by ``tests/test_oracle_pins.py`` (brute-force TTMc, exact recovery
 of a tensor of exact multilinear rank, the non-decreasing core norm of HOOI,
 agreement of the Gram eigenvectors with the SVD, exactness of PP at dA = 0
-and its second-order error).
+and its second-order error, and the core estimate a PP sweep returns against
+the exact core minus the order-3 product term of Sec. 3.1.2's expansion).
 """
 from __future__ import annotations
 

@@ -626,3 +626,144 @@ def test_pp_tucker_als_tracks_hooi():
         als.append(TO.fitness(normX, G))
     assert "pp_approx" in kinds
     assert max(abs(a - b) for a, b in zip(fit, als)) < 1e-6
+
+
+# --- Algorithm 3 sequencing (the PP-CP-ALS algorithm, Sec. 3.2) -----------------
+
+def _max_ratio(new, old):
+    return max(float(np.linalg.norm(a - b) / np.linalg.norm(a)) for a, b in zip(new, old))
+
+
+def test_pp_cp_als_schedule_follows_eps_crossings(monkeypatch):
+    """Algorithm 3's control flow, checked against a schedule the test derives
+    on its own.
+
+    (i) eps is placed between two ratios of a plain ALS trace (als_sweep
+    alone), so the first operator build must come right after the first ALS
+    sweep whose ratio falls below eps.  (ii) From the factors after every
+    sweep, the test recomputes ||dA^(i)|| / ||A^(i)|| by the paper's
+    definitions (A_new - A_old after an ALS sweep, A_new - A_p after a PP
+    sweep, A_p = the factors at the head of the PP initialisation sweep) and
+    checks that each sweep's kind follows the rule taken at the head of that
+    sweep: after an ALS sweep a build and PP initialisation sweep iff every
+    ratio is below eps; inside a PP run another PP approximated sweep iff
+    every ratio is below eps, and otherwise exactly one ALS sweep.  (iii) The
+    eps test is evaluated only between sweeps, once per sweep head (twice at
+    a build: the outer test and the PP loop's own test with dA = 0)."""
+    p = synth.make_problem("collinear", [14, 13, 12], 4, seed=11, noise=1e-2, collinearity=0.8,
+                           storage="f64")
+    X = p.X
+    A = [a.copy() for a in p.A0]
+    S = [O.gram(a) for a in A]
+    hist = [[a.copy() for a in A]]
+    ratios = []
+    for _ in range(20):
+        O.als_sweep(X, A, S)
+        hist.append([a.copy() for a in A])
+        ratios.append(_max_ratio(hist[-1], hist[-2]))
+    # first sweep t0 >= 3 whose ratio is below every earlier one
+    t0 = next(t for t in range(3, 20) if ratios[t] < min(ratios[:t]))
+    eps = float(np.sqrt(ratios[t0] * min(ratios[:t0])))
+
+    state = {"done": 0, "inside": False}
+    calls = []
+    real_small, real_als, real_pp = O._small, O.als_sweep, O.pp_sweep
+
+    def spy_small(dA, A, e):
+        assert not state["inside"], "eps test taken inside a sweep"
+        res = real_small(dA, A, e)
+        calls.append((state["done"], res))
+        return res
+
+    def wrap(fn):
+        def inner(*a, **k):
+            state["inside"] = True
+            try:
+                return fn(*a, **k)
+            finally:
+                state["inside"] = False
+        return inner
+
+    monkeypatch.setattr(O, "_small", spy_small)
+    monkeypatch.setattr(O, "als_sweep", wrap(real_als))
+    monkeypatch.setattr(O, "pp_sweep", wrap(real_pp))
+    after = []
+
+    def on_sweep(kind, A):
+        state["done"] += 1
+        after.append([a.copy() for a in A])
+
+    n = 45
+    _, tr = O.pp_cp_als(X, p.A0, n, eps, use_V=True, on_sweep=on_sweep)
+    kinds = tr.kinds
+    assert len(kinds) == n
+    # (i) the crossing fixed by the ALS-only trace
+    assert kinds[: t0 + 2] == ["als"] * (t0 + 1) + ["pp_init"]
+    for t in range(t0 + 1):
+        for a, b in zip(after[t], hist[t + 1]):
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+    # (ii) every later kind follows the rule at its head
+    prev_f = [a.copy() for a in p.A0]
+    Ap = None
+    r = []
+    for t, k in enumerate(kinds):
+        if k == "pp_init":
+            Ap = prev_f
+        r.append(_max_ratio(after[t], Ap if k != "als" else prev_f))
+        prev_f = after[t]
+    assert kinds[0] == "als"
+    for t in range(1, n):
+        small = r[t - 1] < eps
+        if kinds[t - 1] == "als":
+            assert kinds[t] == ("pp_init" if small else "als"), t
+        else:
+            assert kinds[t] == ("pp_approx" if small else "als"), t
+    assert "pp_approx" in kinds and any(
+        kinds[t - 1] in ("pp_init", "pp_approx") and kinds[t] == "als" for t in range(1, n)), kinds
+    # the oracle's own ratio log agrees with the definitions
+    np.testing.assert_allclose([max(x) for x in tr.ratios], r, rtol=1e-12, atol=0)
+    # (iii) one test per sweep head, two at a build head, none at the budget's end
+    per_head = {}
+    for head, _ in calls:
+        per_head[head] = per_head.get(head, 0) + 1
+    for t in range(n):
+        assert per_head.get(t, 0) == (2 if kinds[t] == "pp_init" else 1), (t, kinds[t], per_head.get(t))
+    assert n not in per_head
+
+
+def test_pp_tucker_core_estimate():
+    """The core estimate a PP-Tucker sweep returns (Algorithm 4) is Y~^(3)
+    contracted with the new A^(3).  Order 3 has the exact four-term expansion
+    of Sec. 3.1.2, Y^(3)(A_p + dA) = Y~^(3) + X x_1 dA^(1)T x_2 dA^(2)T, so the
+    exact core at the new factors minus the estimate must be
+    X x_1 dA^(1)T x_2 dA^(2)T x_3 A^(3)T with the sweep's final changes
+    dA = A - A_p (loop sums here, not the oracle's contractions); at dA = 0
+    the two cores coincide."""
+    def core_loops(X, U, V, W):
+        return np.einsum("abc,ai,bj,ck->ijk", X, U, V, W, optimize=False)
+
+    g = np.random.default_rng(64)
+    X = g.standard_normal((9, 8, 7))
+    ranks = (3, 2, 4)
+    Ap = [np.linalg.qr(g.standard_normal((s, r)))[0] for s, r in zip(X.shape, ranks)]
+    ops, Mp = TO.pp_operators(X, Ap)
+    A = [a.copy() for a in Ap]
+    dA = [np.zeros_like(a) for a in Ap]
+    est = TO.pp_sweep(ops, Mp, A, Ap, dA)
+    assert est.shape == ranks
+    assert max(float(np.linalg.norm(d)) for d in dA) > 1e-3        # the sweep moved the factors
+    for n in range(3):
+        np.testing.assert_allclose(dA[n], A[n] - Ap[n], atol=1e-15)
+    exact = core_loops(X, A[0], A[1], A[2])
+    product = core_loops(X, dA[0], dA[1], A[2])
+    np.testing.assert_allclose(exact - est, product, rtol=1e-10, atol=1e-12)
+    # dA = 0: an exact multilinear-rank tensor at its HOSVD factors is a fixed point
+    q = synth.tucker_problem([10, 9, 8], [3, 2, 4], seed=6, noise=0.0)
+    H = TO.hosvd(q.X, q.R)
+    ops, Mp = TO.pp_operators(q.X, H)
+    A = [a.copy() for a in H]
+    dA = [np.zeros_like(a) for a in H]
+    est = TO.pp_sweep(ops, Mp, A, H, dA)
+    assert max(float(np.max(np.abs(d))) for d in dA) < 1e-10
+    exact = core_loops(q.X, A[0], A[1], A[2])
+    np.testing.assert_allclose(est, exact, rtol=0, atol=1e-10 * float(np.linalg.norm(q.X)))
