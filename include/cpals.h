@@ -359,6 +359,18 @@ cpals_status cpals_reset_stats(cpals_ctx* ctx);
 cpals_status cpals_get_stats(cpals_ctx* ctx, int kind, int64_t* launches, double* total_ms,
                              double* bytes, double* flops);
 
+/* Bound, in SM clock cycles, of the tensor-core contraction kernel's waits
+ * on its own pipeline (a stage's loads, an accumulator, the unit queue);
+ * 0 restores the default (4e9 cycles, about 2 s).  When a wait runs out the
+ * kernel records an error code, lets the loads and tensor-core operations it
+ * already issued complete, frees its tensor memory and returns; the call
+ * that ran it returns CPALS_E_TIMEOUT (as does every later call that reads
+ * the context's status) until cpals_init_factors clears the status.  The
+ * output of that contraction is then undefined.  A short bound exists to
+ * test this path; the default never expires in normal operation.  Drops the
+ * captured sweep graphs; the state is kept. */
+cpals_status cpals_set_wait_limit(cpals_ctx* ctx, uint64_t cycles);
+
 /* enable != 0 (default): capture each sweep kind in a CUDA graph on first use
  * and replay it; 0 launches kernels directly. */
 cpals_status cpals_set_graphs(cpals_ctx* ctx, int enable);
@@ -384,13 +396,19 @@ cpals_status cpals_set_graphs(cpals_ctx* ctx, int enable);
  * Kstride >= K and a multiple of 8.  out: device float32, batch*M*R values,
  * caller-owned.  splits >= 1 splits K across CTAs.  stream: cudaStream_t
  * (NULL = legacy default stream); the call waits for its own work.
- * Errors: CPALS_E_INVALID for bad arguments or when splits*batch*M*R exceeds
- * CPALS_NOALLOC_SCRATCH_FLOATS (the scratch is not enlarged); CPALS_E_UNSUPPORTED
+ * Errors: CPALS_E_INVALID for bad arguments or when the partial sums,
+ * used*batch*M*R floats, exceed CPALS_NOALLOC_SCRATCH_FLOATS (the scratch is
+ * not enlarged); `used` is the number of K chunks the kernel runs, K split
+ * into chunks of ceil(K/splits) rounded up to a multiple of 64, which can be
+ * fewer than `splits`; used == 1 writes out directly and needs no scratch.
+ * CPALS_E_UNSUPPORTED
  * for shapes the tensor-core path does not take (alignment, R > 128);
  * CPALS_E_TIMEOUT if a bounded device wait gave up; CPALS_E_CUDA otherwise.
  * The first call on a device takes the scratch array's device address
  * (cudaGetSymbolAddress) and sets the kernels' shared-memory limit, with
- * that device current.  All calls share the one array and it keeps the last
+ * that device current; host threads making their first calls at the same
+ * time do this once (it runs under a lock).  Make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last
  * call's contents; calls that overlap on the GPU (other streams, other host
  * threads) race on it and must be serialised by the caller. */
 #define CPALS_NOALLOC_SCRATCH_FLOATS (4u << 20)

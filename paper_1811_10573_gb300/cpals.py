@@ -54,6 +54,7 @@ _SIGS = {
     "cpals_reset_stats": (C.c_int, [_ctx_p]),
     "cpals_get_stats": (C.c_int, [_ctx_p, C.c_int, _i64p, _dp, _dp, _dp]),
     "cpals_set_graphs": (C.c_int, [_ctx_p, C.c_int]),
+    "cpals_set_wait_limit": (C.c_int, [_ctx_p, C.c_uint64]),
     "cpals_set_normal_arith": (C.c_int, [_ctx_p, C.c_int]),
     "cpals_set_step_size": (C.c_int, [_ctx_p, _dp]),
     "cpals_set_symmetric": (C.c_int, [_ctx_p, C.c_int, C.c_int]),
@@ -300,6 +301,10 @@ def cpals_set_graphs(ctx, enable):
 NORMAL_ARITH = {"fp64": 0, "double_float": 1}
 
 
+def cpals_set_wait_limit(ctx, cycles):
+    return lib().cpals_set_wait_limit(ctx, int(cycles))
+
+
 def cpals_set_normal_arith(ctx, arith):
     return lib().cpals_set_normal_arith(ctx, arith)
 
@@ -501,6 +506,10 @@ class CPALS:
 
     def set_graphs(self, enable):
         self._ck(cpals_set_graphs(self.ctx, 1 if enable else 0))
+
+    def set_wait_limit(self, cycles):
+        """Bound of the tensor-core kernel's waits in SM cycles (0 = default)."""
+        self._ck(cpals_set_wait_limit(self.ctx, cycles))
 
     def set_normal_arith(self, arith):
         """'fp64' or 'double_float' (see cpals_set_normal_arith); the factors

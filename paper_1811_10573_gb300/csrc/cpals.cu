@@ -123,6 +123,7 @@ struct cpals_ctx {
   int64_t pc_launches = 0;         // PP correction launches timed with events
   double pc_ms = 0, pc_bytes = 0;
   int* umma_err = nullptr;
+  uint64_t wait_limit = 0;         // bound of the tensor-core kernel's waits (cycles; 0 = default)
   int* umma_sched = nullptr;       // work counter of the tensor-core kernel (launches on stream)
   // learned controller
   float* ctrl_params = nullptr;    // device, ctrl_param_count(kCtrlFeatures) floats
@@ -260,7 +261,7 @@ cpals_status contract_first(cpals_ctx* c, int k0, int nk, void* const* facs, T* 
     khatri_rao_bf16_t(fl, c->dims + k0, nk, R, c->Rpad, Kstride, c->Bt, c->L());
     ev_begin(c, idx);
     CK(umma_gemm_bf16(c->Xb, c->Bt, P<float>(out), P<float>(c->gpart), batch, K, M, R, c->Rpad,
-                      Kstride, kmajor, splits, c->umma_err, c->umma_sched, c->L()));
+                      Kstride, kmajor, splits, c->umma_err, c->umma_sched, c->L(), c->wait_limit));
     ev_end(c, idx, bytes, flops);
     return CPALS_OK;
   }
@@ -411,7 +412,7 @@ cpals_status als_sweep_launch(cpals_ctx* c) {
     finish_mode<T>(c, n, last, false, false);
     CKS(tie_copy(c, n));
   }
-  fitness<T>(last, c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->normX2, c->scal, c->dpart,
+  fitness<T>(last, c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->scal + 40, c->scal, c->dpart,
              c->tickets + 62, c->L());
   return CPALS_OK;
 }
@@ -437,7 +438,7 @@ template <typename T>
 cpals_status fitness_launch(cpals_ctx* c) {
   const T* last = nullptr;
   CKS(mttkrp_launch<T>(c, c->N - 1, &last));
-  fitness<T>(last, c->A[c->N - 1], c->S, c->N, c->R, (int)c->dims[c->N - 1], c->normX2, c->scal,
+  fitness<T>(last, c->A[c->N - 1], c->S, c->N, c->R, (int)c->dims[c->N - 1], c->scal + 40, c->scal,
              c->dpart, c->tickets + 62, c->L());
   return CPALS_OK;
 }
@@ -592,7 +593,7 @@ cpals_status pp_sweep_launch(cpals_ctx* c, bool useV) {
     CKS(tie_copy(c, n));
   }
   // fitness estimate from M~^(N) (the last right-hand side, updated factors)
-  fitness<T>(P<const T>(c->rhs), c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->normX2,
+  fitness<T>(P<const T>(c->rhs), c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->scal + 40,
              c->scal, c->dpart, c->tickets + 62, c->L());
   return CPALS_OK;
 }
@@ -665,15 +666,19 @@ cpals_status sync_read(cpals_ctx* c) {
 }
 
 cpals_status check_status(cpals_ctx* c) {
+  // a non-finite value (e.g. from a NaN or Inf in the input) is reported
+  // before a failed factorisation it may have caused
+  for (int n = 0; n < c->N; n++)
+    if (!std::isfinite(c->scal_h[8 + 2 * n]) || !std::isfinite(c->scal_h[9 + 2 * n]))
+      return c->fail(CPALS_E_NUMERIC, "non-finite factor in mode " + std::to_string(n));
+  if (!std::isfinite(c->scal_h[0]))
+    return c->fail(CPALS_E_NUMERIC, "non-finite fitness");
   if (c->status_h[0]) {
     const int bits = c->status_h[0];
     CK(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->stream));
     return c->fail(CPALS_E_SINGULAR, "Gamma not positive definite for mode mask " + std::to_string(bits) +
                                          "; those factors were left unchanged");
   }
-  for (int n = 0; n < c->N; n++)
-    if (!std::isfinite(c->scal_h[8 + 2 * n]) || !std::isfinite(c->scal_h[9 + 2 * n]))
-      return c->fail(CPALS_E_NUMERIC, "non-finite factor in mode " + std::to_string(n));
   return CPALS_OK;
 }
 
@@ -1118,7 +1123,8 @@ cpals_status cpals_set_tensor(cpals_ctx* c, const void* data, int dtype, int on_
   c->normX2 = nx;
   c->have_tensor = true;
   c->ops_built = false;
-  drop_graphs(c);   // normX2 is baked into the captured fitness kernels
+  // the captured graphs stay valid: the fitness kernels read ||X||^2 from
+  // device memory (scal[40]) when they run
   return CPALS_OK;
 }
 
@@ -1716,6 +1722,13 @@ cpals_status cpals_set_symmetric(cpals_ctx* c, int m1, int m2) {
   for (int k = 0; k < c->N; k++) c->tied_any = c->tied_any || tied(c, k);
   c->have_factors = false;                  // cpals_init_factors applies the tie
   c->ops_built = false;
+  return CPALS_OK;
+}
+
+cpals_status cpals_set_wait_limit(cpals_ctx* c, uint64_t cycles) {
+  if (!c) return CPALS_E_INVALID;
+  c->wait_limit = cycles;
+  drop_graphs(c);   // the bound is a launch parameter of the captured kernels
   return CPALS_OK;
 }
 

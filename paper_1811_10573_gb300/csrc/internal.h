@@ -108,13 +108,14 @@ void gram_update(const double* A, const T* Ac, const T* dAc, double* S, double* 
                  int s, int R, const double* rownorm, double* scal, double* partials, int* tickets,
                  Launch L);
 
-// Fitness from the last mode's right-hand side (Sec. 5):
+// Fitness from the last mode's right-hand side (Sec. 5), with ||X||^2 read
+// from device memory at run time (normX2):
 // inner = sum rhs*A, model = sum_{r,r'} prod_k S_k, out[0] = fitness, out[1] = inner,
 // out[2] = model.  partials: workspace (>= 2*256 doubles); ticket: one zeroed
 // int (the last block resets it), shared only by launches on one stream.
 template <typename T>
-void fitness(const T* rhs, const double* A, const double* S, int N, int R, int s, double normX2,
-             double* out, double* partials, int* ticket, Launch L);
+void fitness(const T* rhs, const double* A, const double* S, int N, int R, int s,
+             const double* normX2, double* out, double* partials, int* ticket, Launch L);
 
 // ---------------------------------------------------------------- double-float (FP32/mixed modes)
 // The same normal-equation steps in double-float arithmetic (hi + lo floats)
@@ -159,6 +160,9 @@ void mlp_train_epoch(float* params, float* m, float* v, int F, const float* X, c
 // sched: two zeroed ints that launches on one stream may share (units are
 // handed out dynamically and the counter is reset by the kernel); null gives
 // a static round-robin assignment (safe for concurrent launches).
+// wait_limit: bound of the kernel's waits on work in SM clock cycles (0 = the
+// default, about 2 s); on expiry the kernel writes a nonzero code to *err_flag,
+// lets what it already issued land and returns.
 // Returns false if the shape is not supported (alignment), so the caller can
 // report CPALS_E_UNSUPPORTED.
 bool umma_supported(int64_t K, int64_t M, bool kmajor, int R);
@@ -167,6 +171,6 @@ cudaError_t setup_umma_kernels();
 cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, float* out,
                            float* partials, int64_t batch, int64_t K, int64_t M, int R, int Rpad,
                            int64_t Kstride, bool kmajor, int splits, int* err_flag, int* sched,
-                           Launch L);
+                           Launch L, uint64_t wait_limit = 0);
 
 }  // namespace cpals

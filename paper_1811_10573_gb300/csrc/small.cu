@@ -339,8 +339,8 @@ gram_kernel(const double* __restrict__ A, const TW* __restrict__ Aw, const TW* _
 template <typename T>
 __global__ void fitness_kernel(const T* __restrict__ rhs, const double* __restrict__ A,
                                const double* __restrict__ S, int N, int R, int s,
-                               double* __restrict__ part, double normX2, double* __restrict__ out,
-                               int* __restrict__ ticket) {
+                               double* __restrict__ part, const double* __restrict__ normX2p,
+                               double* __restrict__ out, int* __restrict__ ticket) {
   // per block: <M^(N), A^(N)> and sum of the Hadamard product of the Grams
   const int64_t n1 = (int64_t)s * R;
   const int RR = R * R;
@@ -394,6 +394,7 @@ __global__ void fitness_kernel(const T* __restrict__ rhs, const double* __restri
   }
   if (threadIdx.x == 0) {
     const double inner = ra[0], model = rb[0];
+    const double normX2 = *normX2p;
     const double res2 = normX2 - 2.0 * inner + model;
     out[0] = 1.0 - sqrt(fmax(res2, 0.0)) / sqrt(normX2);
     out[1] = inner;
@@ -483,8 +484,8 @@ void gram_update(const double* A, const T* Ac, const T* dAc, double* S, double* 
 }
 
 template <typename T>
-void fitness(const T* rhs, const double* A, const double* S, int N, int R, int s, double normX2,
-             double* out, double* partials, int* ticket, Launch L) {
+void fitness(const T* rhs, const double* A, const double* S, int N, int R, int s,
+             const double* normX2, double* out, double* partials, int* ticket, Launch L) {
   fitness_kernel<T><<<128, 256, 0, L.stream>>>(rhs, A, S, N, R, s, partials, normX2, out, ticket);
   (*L.counter) += 1;
 }
@@ -498,8 +499,8 @@ void fitness(const T* rhs, const double* A, const double* S, int N, int R, int s
   template void vterm<T>(const T*, const T*, const double*, T*, int, int, Launch);              \
   template void gram_update<T>(const double*, const T*, const T*, double*, double*, bool, int,  \
                                int, const double*, double*, double*, int*, Launch);             \
-  template void fitness<T>(const T*, const double*, const double*, int, int, int, double,       \
-                           double*, double*, int*, Launch);
+  template void fitness<T>(const T*, const double*, const double*, int, int, int,               \
+                           const double*, double*, double*, int*, Launch);
 INST(double)
 INST(float)
 #undef INST

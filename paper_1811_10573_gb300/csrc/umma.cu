@@ -54,7 +54,11 @@ constexpr int BM = 128;
 constexpr int BK = 64;                 // bf16 elements = 128 bytes = one swizzle row
 constexpr int kThreadsUmma = 192;      // 6 warps
 constexpr int A_STAGE_BYTES = BM * BK * 2;
-constexpr unsigned long long kTimeoutCycles = 4000000000ull;   // ~2 s at 2 GHz
+// Default bound of the waits on work (a stage, an accumulator, the unit
+// queue), ~2 s at 2 GHz; a launch may pass a shorter one (UmmaParams.wait_limit).
+// The drain waits at exit (loads and MMAs already issued must land before the
+// CTA releases shared memory and TMEM) always use this bound.
+constexpr unsigned long long kTimeoutCycles = 4000000000ull;
 
 // error codes written to the error word
 enum { ERR_PRODUCER = 1, ERR_MMA_FULL = 2, ERR_MMA_ACC = 3, ERR_EPI = 4, ERR_DRAIN = 5 };
@@ -87,15 +91,16 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait; returns false on timeout or when another role aborted
+// bounded wait (limit in SM clock cycles); returns false on timeout or when
+// another role aborted
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          bool sleep) {
+                                          bool sleep, unsigned long long limit) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = clock64();
   while (true) {
     if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (clock64() - t0 > kTimeoutCycles) return false;
+    if (clock64() - t0 > limit) return false;
     if (sleep) __nanosleep(64);
   }
 }
@@ -195,6 +200,7 @@ struct UmmaParams {
   float* out;           // out or partials ([z][b][m][r])
   int* err;
   int* sched;           // [next unit, CTAs done], zero at launch; null: static round robin
+  unsigned long long wait_limit;   // bound of the waits on work, SM clock cycles
 };
 
 template <bool KMAJOR>
@@ -262,7 +268,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         const int64_t un = p.sched ? (int64_t)atomicAdd(p.sched, 1)
                                    : (int64_t)blockIdx.x + (int64_t)t * gridDim.x;
         const int64_t u = (ok && un < p.units) ? un : -1;
-        if (!mbar_wait(smem_u32(&uq_empty[t & 3]), ((t >> 2) & 1) ^ 1, &abort_sh, false)) {
+        if (!mbar_wait(smem_u32(&uq_empty[t & 3]), ((t >> 2) & 1) ^ 1, &abort_sh, false, p.wait_limit)) {
           ok = false;
           break;
         }
@@ -278,7 +284,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         const int64_t k0 = (int64_t)z * p.kchunk;
         const int64_t k1 = min(p.K, k0 + p.kchunk);
         for (int64_t k = k0; k < k1; k += BK) {
-          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_sh, false)) {
+          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_sh, false, p.wait_limit)) {
             ok = false;
             break;
           }
@@ -336,7 +342,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       bool ok = true;
       bool any = false;
       for (int t = 0;; t++) {
-        if (!mbar_wait(smem_u32(&uq_full[t & 3]), (t >> 2) & 1, &abort_sh, false)) {
+        if (!mbar_wait(smem_u32(&uq_full[t & 3]), (t >> 2) & 1, &abort_sh, false, p.wait_limit)) {
           atomicCAS(p.err, 0, ERR_MMA_ACC);
           abort_sh = 1;
           break;
@@ -351,7 +357,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         const int64_t k0 = (int64_t)z * p.kchunk;
         const int64_t k1 = min(p.K, k0 + p.kchunk);
         const int buf = t % NBUF;
-        if (!mbar_wait(smem_u32(&acce_bar[buf]), ((t / NBUF) & 1) ^ 1, &abort_sh, false)) {
+        if (!mbar_wait(smem_u32(&acce_bar[buf]), ((t / NBUF) & 1) ^ 1, &abort_sh, false, p.wait_limit)) {
           atomicCAS(p.err, 0, ERR_MMA_ACC);
           abort_sh = 1;
           ok = false;
@@ -361,7 +367,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
         const uint32_t d_tmem = tmem_base + (uint32_t)(buf * TPU * 256);
         uint32_t accum = 0;
         for (int64_t k = k0; k < k1; k += BK) {
-          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_sh, false)) {
+          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_sh, false, p.wait_limit)) {
             atomicCAS(p.err, 0, ERR_MMA_FULL);
             abort_sh = 1;
             ok = false;
@@ -428,7 +434,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       long long uu = 0;
       int okq = 1;
       if (lane == 0) {
-        okq = mbar_wait(smem_u32(&uq_full[t & 3]), (t >> 2) & 1, &abort_sh, true) ? 1 : 0;
+        okq = mbar_wait(smem_u32(&uq_full[t & 3]), (t >> 2) & 1, &abort_sh, true, p.wait_limit) ? 1 : 0;
         if (okq) {
           uu = uq[t & 3];
           mbar_arrive(smem_u32(&uq_empty[t & 3]));
@@ -452,7 +458,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant
       const int buf = t % NBUF;
       const uint32_t par = (uint32_t)((t / NBUF) & 1);
       int ok = 1;
-      if (lane == 0) ok = mbar_wait(smem_u32(&accf_bar[buf]), par, &abort_sh, true) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait(smem_u32(&accf_bar[buf]), par, &abort_sh, true, p.wait_limit) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) {
         if (lane == 0) {
@@ -611,7 +617,7 @@ bool umma_supported(int64_t K, int64_t M, bool kmajor, int R) {
 cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, float* out,
                            float* partials, int64_t batch, int64_t K, int64_t M, int R, int Rpad,
                            int64_t Kstride, bool kmajor, int splits, int* err_flag, int* sched,
-                           Launch L) {
+                           Launch L, uint64_t wait_limit) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   if (!umma_supported(K, M, kmajor, R) || Rpad % 16 || Rpad > 128 || Rpad < R)
@@ -662,6 +668,7 @@ cudaError_t umma_gemm_bf16(const __nv_bfloat16* Xb, const __nv_bfloat16* Bt, flo
   p.mtiles = cdiv(M, BM);
   p.err = err_flag;
   p.sched = sched;
+  p.wait_limit = wait_limit ? (unsigned long long)wait_limit : kTimeoutCycles;
   p.out = p.splits > 1 ? partials : out;
   int RS = (R + 3) / 4 * 4;
   if (((RS / 4) & 1) == 0) RS += 4;
