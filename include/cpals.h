@@ -140,8 +140,10 @@ cpals_status cpals_pp_build_operators(cpals_ctx* ctx);
 
 /* One PP approximated sweep (Algorithm 3): each right-hand side
  * is Eq. 3's M~^(n); use_V != 0 adds the second-order terms V^(n,i,j).
- * dA^(n) = A^(n)_new - A_p^(n).  fitness_out (nullable): fitness estimated
- * from M~^(N) (not exact; see cpals_fitness).  CPALS_E_STATE if no operators. */
+ * dA^(n) = A^(n)_new - A_p^(n).  fitness_out (nullable): the fitness
+ * estimated from the first-order part of M~^(N),
+ * M_p^(N) + sum_i M_p^(i,N) x_i dA^(i), and the new factors (not exact; see
+ * cpals_fitness).  CPALS_E_STATE if no operators. */
 cpals_status cpals_pp_sweep(cpals_ctx* ctx, int use_V, double* fitness_out);
 
 /* Exact fitness of the current factors: one exact MTTKRP of the last mode
@@ -161,9 +163,18 @@ cpals_status cpals_get_dA_ratios(cpals_ctx* ctx, double* out_N);
  * the estimate is checked first, then confirmed by cpals_fitness).
  * Outputs (each nullable, length max_sweeps): fitness_trace (exact after ALS
  * sweeps, estimate after PP sweeps), kind_trace (CPALS_SWEEP_*),
- * time_trace (seconds since the start of the run, host clock after the
- * sweep's stream synchronisation).  *n_done receives the number of sweeps
- * run; *reached (nullable) 1 if the target was confirmed. */
+ * time_trace (seconds since the start of the run at the end of each sweep).
+ * *n_done receives the number of sweeps run; *reached (nullable) 1 if the
+ * target was confirmed.
+ * With captured graphs on, profiling off and the device loop enabled (the
+ * default, cpals_set_device_loop), every decision of the algorithm is taken
+ * on the GPU: one CUDA graph holds a while loop around a switch over the
+ * sweep kinds and a one-thread kernel that applies the eps and target tests
+ * to the device scalars, so the run synchronises with the host once, at its
+ * end; time_trace then comes from the GPU's global timer.  Otherwise the
+ * decisions are taken on the host after each sweep's stream
+ * synchronisation (host clock).  Both take the same decisions on the same
+ * values, and the sweeps run the same kernels. */
 cpals_status cpals_run(cpals_ctx* ctx, int max_sweeps, double eps, int use_V, double target,
                        double* fitness_trace, int* kind_trace, double* time_trace,
                        int* n_done, int* reached);
@@ -358,6 +369,29 @@ cpals_status cpals_reset_stats(cpals_ctx* ctx);
  * those launches (kinds 0 and 2; flops kind 0 only). */
 cpals_status cpals_get_stats(cpals_ctx* ctx, int kind, int64_t* launches, double* total_ms,
                              double* bytes, double* flops);
+
+/* Algorithm 3's stopping test inside the PP loop (its while condition on
+ * Delta), in the form the paper's experiments use (Sec. 5.1: the fitness
+ * difference between two neighbouring sweeps): with tol > 0, at the head of
+ * every PP sweep after the first of a PP run, cpals_run goes on with the
+ * run only if the last sweep raised the fitness it reports (exact after ALS
+ * sweeps, the estimate after PP sweeps) by at least tol; otherwise the
+ * regular ALS sweep follows, as when the eps test fails.  This ends PP runs
+ * that stall at a fixed point of the approximated update.  tol = 0 (the
+ * default) leaves the test out.  CPALS_E_INVALID for tol < 0 or NaN.  Used
+ * by cpals_run and cpals_run_batch. */
+cpals_status cpals_set_pp_stop_tol(cpals_ctx* ctx, double tol);
+
+/* enable != 0 (default): cpals_run takes Algorithm 3's decisions on the
+ * device (see cpals_run); 0: on the host after every sweep.  The device loop
+ * needs captured graphs (cpals_set_graphs) and profiling off. */
+cpals_status cpals_set_device_loop(cpals_ctx* ctx, int enable);
+
+/* 1 if the next cpals_run of this context runs its decisions on the device,
+ * 0 if it will use the host loop (device loop disabled, graphs off,
+ * profiling on, or a driver that could not build the loop graph, whose
+ * error cpals_last_error reported once). */
+int cpals_device_loop_active(const cpals_ctx* ctx);
 
 /* Bound, in SM clock cycles, of the tensor-core contraction kernel's waits
  * on its own pipeline (a stage's loads, an accumulator, the unit queue);

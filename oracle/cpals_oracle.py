@@ -390,12 +390,27 @@ def pp_sweep(ops, Mp, A, Ap, dA, S, use_V: bool = True, info: SolveInfo | None =
     return gnorm
 
 
+def pp_fitness_estimate(ops, Mp, A, dA, normX: float) -> float:
+    """The fitness a PP sweep reports without touching X: the fitness formula
+    of Sec. 5 with the inner product <X, [[A]]> taken from the first-order
+    right-hand side of the last mode, M_p^(N) + sum_i M_p^(i,N) x_i dA^(i)
+    (Eq. 3 without its second-order terms), and the factors after the sweep."""
+    N = len(A)
+    Mt = pp_first_order(ops, Mp, dA, N - 1)
+    inner = float(np.sum(Mt * A[N - 1]))
+    res2 = normX * normX - 2.0 * inner + norm_model_sq(A)
+    return 1.0 - math.sqrt(max(res2, 0.0)) / normX
+
+
 @dataclass
 class PPTrace:
-    """Per-sweep log of Algorithm 3: type, exact fitness, dA ratios."""
+    """Per-sweep log of Algorithm 3: type, exact fitness, dA ratios, and the
+    fitness the algorithm itself sees (exact after ALS sweeps, the estimate
+    of ``pp_fitness_estimate`` after PP sweeps)."""
     kinds: list = field(default_factory=list)      # "als" | "pp_init" | "pp_approx"
     fitness: list = field(default_factory=list)
     ratios: list = field(default_factory=list)     # ||dA^(i)|| / ||A^(i)|| after the sweep
+    seen: list = field(default_factory=list)
     singular: int = 0
 
 
@@ -405,17 +420,23 @@ def _small(dA, A, eps: float) -> bool:
 
 
 def pp_cp_als(X: np.ndarray, A0, n_sweeps: int, eps: float, use_V: bool = True,
-              on_sweep=None, lam=None, tie=None):
+              on_sweep=None, lam=None, tie=None, pp_stop_tol: float = 0.0):
     """Algorithm 3 (PP-CP-ALS) for a budget of ``n_sweeps`` sweeps.
 
     Readings where the paper leaves room: the eps test is taken at the head
     of each PP sweep (whole-matrix Frobenius norms, as written); a PP
     initialisation sweep (operator build plus one PP pass), a PP approximated
     sweep and a regular ALS sweep each count as one sweep; the reported
-    fitness is always the exact one; the gradient stopping test is not used
-    (fixed budgets).  ``on_sweep(kind, A)`` is called after every sweep.
-    ``lam`` and ``tie`` select the ALS variants of Sec. 5.1 for both sweep
-    kinds (see ``als_sweep``).
+    fitness is always the exact one.  The stopping test Delta of Algorithm 3
+    is not used to end the run (fixed budgets); with ``pp_stop_tol`` > 0 it
+    is taken inside the PP loop in the form of the paper's experiments
+    (Sec. 5.1: the fitness difference of two neighbouring sweeps): at the
+    head of every PP sweep after the first of a run, the run goes on only if
+    the last sweep raised the fitness the algorithm sees (``PPTrace.seen``)
+    by at least ``pp_stop_tol``; otherwise the regular ALS sweep follows, as
+    when the eps test fails.  ``on_sweep(kind, A)`` is called after every
+    sweep.  ``lam`` and ``tie`` select the ALS variants of Sec. 5.1 for both
+    sweep kinds (see ``als_sweep``).
     """
     A = [a.copy() for a in A0]
     for m2, m1 in (tie or {}).items():
@@ -427,12 +448,19 @@ def pp_cp_als(X: np.ndarray, A0, n_sweeps: int, eps: float, use_V: bool = True,
     tr = PPTrace()
     info = SolveInfo()
 
-    def log(kind):
+    def log(kind, seen):
         tr.kinds.append(kind)
         tr.fitness.append(fitness(X, A, normX))
         tr.ratios.append([float(np.linalg.norm(d) / np.linalg.norm(a)) for d, a in zip(dA, A)])
+        tr.seen.append(seen)
         if on_sweep is not None:
             on_sweep(kind, A)
+
+    def gained():
+        if pp_stop_tol <= 0.0:
+            return True
+        prev = tr.seen[-2] if len(tr.seen) >= 2 else -math.inf
+        return tr.seen[-1] - prev >= pp_stop_tol
 
     t = 0
     while t < n_sweeps:
@@ -441,16 +469,17 @@ def pp_cp_als(X: np.ndarray, A0, n_sweeps: int, eps: float, use_V: bool = True,
             ops, Mp = pp_operators(X, Ap)
             dA = [np.zeros_like(a) for a in A]
             first = True
-            while t < n_sweeps and _small(dA, A, eps):
+            while t < n_sweeps and _small(dA, A, eps) and (first or gained()):
                 pp_sweep(ops, Mp, A, Ap, dA, S, use_V, info, lam=lam, tie=tie)
                 t += 1
-                log("pp_init" if first else "pp_approx")
+                log("pp_init" if first else "pp_approx", pp_fitness_estimate(ops, Mp, A, dA, normX))
                 first = False
             if t >= n_sweeps:
                 break
         dA, _ = als_sweep(X, A, S, info, lam=lam, tie=tie)
         t += 1
-        log("als")
+        log("als", None)
+        tr.seen[-1] = tr.fitness[-1]
     tr.singular = int(info.singular)
     return A, tr
 

@@ -55,6 +55,9 @@ _SIGS = {
     "cpals_get_stats": (C.c_int, [_ctx_p, C.c_int, _i64p, _dp, _dp, _dp]),
     "cpals_set_graphs": (C.c_int, [_ctx_p, C.c_int]),
     "cpals_set_wait_limit": (C.c_int, [_ctx_p, C.c_uint64]),
+    "cpals_set_device_loop": (C.c_int, [_ctx_p, C.c_int]),
+    "cpals_set_pp_stop_tol": (C.c_int, [_ctx_p, C.c_double]),
+    "cpals_device_loop_active": (C.c_int, [_ctx_p]),
     "cpals_set_normal_arith": (C.c_int, [_ctx_p, C.c_int]),
     "cpals_set_step_size": (C.c_int, [_ctx_p, _dp]),
     "cpals_set_symmetric": (C.c_int, [_ctx_p, C.c_int, C.c_int]),
@@ -301,6 +304,18 @@ def cpals_set_graphs(ctx, enable):
 NORMAL_ARITH = {"fp64": 0, "double_float": 1}
 
 
+def cpals_set_pp_stop_tol(ctx, tol):
+    return lib().cpals_set_pp_stop_tol(ctx, float(tol))
+
+
+def cpals_set_device_loop(ctx, enable):
+    return lib().cpals_set_device_loop(ctx, enable)
+
+
+def cpals_device_loop_active(ctx):
+    return lib().cpals_device_loop_active(ctx)
+
+
 def cpals_set_wait_limit(ctx, cycles):
     return lib().cpals_set_wait_limit(ctx, int(cycles))
 
@@ -506,6 +521,17 @@ class CPALS:
 
     def set_graphs(self, enable):
         self._ck(cpals_set_graphs(self.ctx, 1 if enable else 0))
+
+    def set_pp_stop_tol(self, tol):
+        """Fitness gain a PP sweep must make for its PP run to go on (0 = no test)."""
+        self._ck(cpals_set_pp_stop_tol(self.ctx, tol))
+
+    def set_device_loop(self, enable):
+        """Algorithm 3's decisions on the device (True, default) or the host."""
+        self._ck(cpals_set_device_loop(self.ctx, 1 if enable else 0))
+
+    def device_loop_active(self):
+        return bool(cpals_device_loop_active(self.ctx))
 
     def set_wait_limit(self, cycles):
         """Bound of the tensor-core kernel's waits in SM cycles (0 = default)."""

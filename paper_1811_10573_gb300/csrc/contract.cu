@@ -473,10 +473,41 @@ int gemm_simt_splits(int64_t batch, int64_t K, int64_t M, int R, bool kmajor, in
   return (int)std::max<int64_t>(sp, 1);
 }
 
+// float64 contractions with R > 32: 64-row tiles whose column tile is R
+// rounded up to a multiple of 8 (8 thread columns of TN = ceil(R/8) each), so
+// the FP64 pipe, the bound of these kernels, runs almost no padded FMAs
+// (R = 100: 104 columns instead of 128).  Each output's k order is the same
+// as with any other tile, so the results are unchanged bit for bit.
+template <typename TX, typename T, bool KM>
+void gemm_exact_cols(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K,
+                     int64_t M, int R, int splits, Launch L) {
+  switch ((R + 7) / 8) {
+    case 5: gemm_launch<TX, T, KM, 64, 40, 2, 5>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 6: gemm_launch<TX, T, KM, 64, 48, 2, 6>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 7: gemm_launch<TX, T, KM, 64, 56, 2, 7>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 8: gemm_launch<TX, T, KM, 64, 64, 2, 8>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 9: gemm_launch<TX, T, KM, 64, 72, 2, 9>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 10: gemm_launch<TX, T, KM, 64, 80, 2, 10>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 11: gemm_launch<TX, T, KM, 64, 88, 2, 11>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 12: gemm_launch<TX, T, KM, 64, 96, 2, 12>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 13: gemm_launch<TX, T, KM, 64, 104, 2, 13>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 14: gemm_launch<TX, T, KM, 64, 112, 2, 14>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 15: gemm_launch<TX, T, KM, 64, 120, 2, 15>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    default: gemm_launch<TX, T, KM, 64, 128, 2, 16>(X, B, out, partials, batch, K, M, R, splits, L); break;
+  }
+}
+
 template <typename TX, typename T>
 void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K, int64_t M,
                int R, bool kmajor, int splits, Launch L) {
   if (splits < 1) splits = 1;
+  if constexpr (sizeof(T) == 8) {
+    if (R > 32 && gemm_simt_bm(M, R, kmajor) == 64) {
+      if (kmajor) gemm_exact_cols<TX, T, true>(X, B, out, partials, batch, K, M, R, splits, L);
+      else gemm_exact_cols<TX, T, false>(X, B, out, partials, batch, K, M, R, splits, L);
+      return;
+    }
+  }
   if (gemm_simt_bm(M, R, kmajor) == 32) {
     // few rows per batch (batched lower-level contractions): 32-row tiles
     if (R <= 32) gemm_launch<TX, T, false, 32, 32, 2, 2>(X, B, out, partials, batch, K, M, R, splits, L);

@@ -131,6 +131,20 @@ struct cpals_ctx {
   float* ctrl_io_h = nullptr;      // pinned host mirror
   double ctrl_conf = 0.6;
   bool ctrl_on = false;
+  // Algorithm 3 on device flags (cpals_run without a host round trip per
+  // sweep): one graph per use_V value, a while loop around a switch over
+  // the sweep kinds, its state and traces in device memory
+  bool device_loop = true;
+  double pp_stop_tol = 0.0;                // Algorithm 3's stopping test inside PP runs (0: off)
+  cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};
+  int64_t loop_count[2][4] = {{0}};        // kernels per branch (launch accounting)
+  void* loop_state = nullptr;              // LoopState (device)
+  void* loop_state_h = nullptr;            // pinned mirror
+  double* loop_fit = nullptr;              // traces (device), loop_cap entries each
+  double* loop_time = nullptr;
+  int* loop_kind = nullptr;
+  int loop_cap = 0;
+  std::string loop_note;                   // why the device loop is unavailable ("" if it is)
   // snapshot of the sweep state (controller logs)
   std::vector<void*> snap_bufs;
   bool snap_ops = false;
@@ -649,6 +663,11 @@ void drop_graphs(cpals_ctx* c) {
       cudaGraphExecDestroy(c->gexec[i]);
       c->gexec[i] = nullptr;
     }
+  for (int i = 0; i < 2; i++)
+    if (c->loop_exec[i]) {
+      cudaGraphExecDestroy(c->loop_exec[i]);
+      c->loop_exec[i] = nullptr;
+    }
 }
 
 cpals_status sync_read(cpals_ctx* c) {
@@ -872,6 +891,285 @@ cpals_status exact_fitness(cpals_ctx* c, double* f) {
   return CPALS_OK;
 }
 
+// ---------------------------------------------------------------- Algorithm 3 on the device
+// The eps test of Algorithm 3 and the target test taken on the GPU: one CUDA
+// graph per run holds a while loop (handle hw) whose body selects the next
+// step with a switch (handle hs) over four captured bodies -- 0: ALS sweep,
+// 1: operator build + PP sweep (the PP initialisation sweep), 2: PP sweep,
+// 3: exact fitness (confirms a PP estimate that reached the target) -- and
+// then decides the following step from the device scalars.  The decisions
+// are those of the host loop of cpals_run: after an ALS sweep the operators
+// are built iff every ||dA^(n)|| < eps ||A^(n)||; after a PP sweep another PP
+// sweep follows iff that still holds, else one ALS sweep.  The loop ends at
+// the sweep budget, at a confirmed target or at an error.
+struct LoopState {
+  int t;            // sweeps done
+  int next;         // branch of the next iteration
+  int hit;          // target confirmed
+  int err;          // 0; 1 non-finite value; 2 Gamma not positive definite; 3 a bounded wait gave up
+  int pending;      // kind of the PP sweep whose estimate awaits the exact fitness
+  int confirms;     // exact-fitness branches run
+  int max_sweeps;
+  int N;
+  double eps, target, pending_f;
+  double tol;       // PP runs end when a sweep gains less fitness than this (0: off)
+  double f_last, f_prev;   // fitness the algorithm saw after the last two sweeps
+  unsigned long long t0;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool loop_all_small(const LoopState* s, const double* scal) {
+  if (!(s->eps > 0.0)) return false;
+  for (int n = 0; n < s->N; n++)
+    if (!(sqrt(scal[8 + 2 * n]) < s->eps * sqrt(scal[9 + 2 * n]))) return false;
+  return true;
+}
+
+__global__ void loop_init_kernel(LoopState* s, const double* scal, cudaGraphConditionalHandle hw) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  s->t = 0;
+  s->hit = 0;
+  s->err = 0;
+  s->confirms = 0;
+  s->f_last = s->f_prev = -1e300;
+  s->next = loop_all_small(s, scal) ? 1 : 0;   // the test at the head of the first sweep
+  s->t0 = global_ns();
+  cudaGraphSetConditional(hw, s->max_sweeps > 0 ? 1u : 0u);
+}
+
+__global__ void loop_select_kernel(const LoopState* s, cudaGraphConditionalHandle hs) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(hs, (unsigned)s->next);
+}
+
+__global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* status, double* ftr,
+                                   int* ktr, double* ttr, cudaGraphConditionalHandle hw) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int ran = s->next;
+  const double f = scal[0];
+  auto record = [&](int kind, double fv) {
+    const int t = s->t;
+    ftr[t] = fv;
+    ktr[t] = kind;
+    ttr[t] = (double)(global_ns() - s->t0) * 1e-9;
+    s->t = t + 1;
+    s->f_prev = s->f_last;
+    s->f_last = fv;
+  };
+  bool stop = false;
+  if (ran == 3) {
+    // the exact fitness of the factors a PP sweep left
+    s->confirms++;
+    if (f >= s->target) {
+      s->hit = 1;
+      record(s->pending, f);
+    } else {
+      record(s->pending, s->pending_f);
+    }
+    ran = s->pending;
+  } else {
+    if (status[1] || status[2]) {
+      s->err = 3;                   // not recorded, as the host loop does
+      stop = true;
+    } else {
+      bool finite = isfinite(f);
+      for (int n = 0; n < s->N; n++)
+        finite = finite && isfinite(scal[8 + 2 * n]) && isfinite(scal[9 + 2 * n]);
+      if (!finite || status[0]) {
+        s->err = finite ? 2 : 1;
+        record(ran, f);
+        stop = true;
+      } else if (ran != 0 && s->target > 0.0 && f >= s->target) {
+        // a PP estimate at the target: confirm with the exact fitness first
+        s->pending = ran;
+        s->pending_f = f;
+        s->next = 3;
+        cudaGraphSetConditional(hw, 1u);
+        return;
+      } else {
+        if (ran == 0 && s->target > 0.0 && f >= s->target) s->hit = 1;
+        record(ran, f);
+      }
+    }
+  }
+  if (stop || s->hit || s->t >= s->max_sweeps) {
+    cudaGraphSetConditional(hw, 0u);
+    return;
+  }
+  const bool small = loop_all_small(s, scal);
+  // inside a PP run the stopping test also asks for a fitness gain of tol
+  const bool gain = !(s->tol > 0.0) || s->f_last - s->f_prev >= s->tol;
+  s->next = ran != 0 ? ((small && gain) ? 2 : 0) : (small ? 1 : 0);
+  cudaGraphSetConditional(hw, 1u);
+}
+
+cudaError_t add_kernel_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                            void* func, void** args) {
+  cudaKernelNodeParams kp = {};
+  kp.func = func;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(32);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
+}
+
+// Capture one branch body into the conditional node's graph; counts its kernels.
+template <typename F>
+cpals_status capture_into(cpals_ctx* c, cudaGraph_t body, int64_t* count, F&& fn) {
+  const int64_t before = c->launches;
+  c->ev_used = 0;
+  CK(cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cpals_status st = fn();
+  cudaGraph_t out = body;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &out);
+  *count = c->launches - before;
+  c->launches = before;
+  if (st != CPALS_OK) return st;
+  if (e != cudaSuccess) return c->cuda_fail("cudaStreamEndCapture (loop body)", e);
+  return CPALS_OK;
+}
+
+cpals_status loop_build(cpals_ctx* c, int slot, bool useV) {
+  const bool d = is64(c);
+  CKS(d ? pp_alloc<double>(c) : pp_alloc<float>(c));
+  cudaGraph_t G = nullptr;
+  CK(cudaGraphCreate(&G, 0));
+  struct Guard {
+    cudaGraph_t g;
+    ~Guard() { cudaGraphDestroy(g); }
+  } guard{G};
+  cudaGraphConditionalHandle hw, hs;
+  CK(cudaGraphConditionalHandleCreate(&hw, G, 1, cudaGraphCondAssignDefault));
+  LoopState* st = static_cast<LoopState*>(c->loop_state);
+  const double* scal = c->scal;
+  const int* status = c->status;
+  cudaGraphNode_t n_init, n_while, n_sel, n_sw, n_dec;
+  {
+    void* args[] = {&st, &scal, &hw};
+    CK(add_kernel_node(&n_init, G, nullptr, 0, (void*)loop_init_kernel, args));
+  }
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  CK(cudaGraphAddNode(&n_while, G, &n_init, nullptr, 1, &wp));
+  cudaGraph_t B = wp.conditional.phGraph_out[0];
+  CK(cudaGraphConditionalHandleCreate(&hs, B, 0, 0));
+  {
+    void* args[] = {&st, &hs};
+    CK(add_kernel_node(&n_sel, B, nullptr, 0, (void*)loop_select_kernel, args));
+  }
+  cudaGraphNodeParams sp = {};
+  sp.type = cudaGraphNodeTypeConditional;
+  sp.conditional.handle = hs;
+  sp.conditional.type = cudaGraphCondTypeSwitch;
+  sp.conditional.size = 4;
+  CK(cudaGraphAddNode(&n_sw, B, &n_sel, nullptr, 1, &sp));
+  {
+    double* ftr = c->loop_fit;
+    int* ktr = c->loop_kind;
+    double* ttr = c->loop_time;
+    void* args[] = {&st, &scal, &status, &ftr, &ktr, &ttr, &hw};
+    CK(add_kernel_node(&n_dec, B, &n_sw, 1, (void*)loop_decide_kernel, args));
+  }
+  int64_t* cnt = c->loop_count[slot];
+  CKS(capture_into(c, sp.conditional.phGraph_out[0], &cnt[0],
+                   [&]() { return d ? als_sweep_launch<double>(c) : als_sweep_launch<float>(c); }));
+  CKS(capture_into(c, sp.conditional.phGraph_out[1], &cnt[1], [&]() {
+    CKS(d ? pp_build_launch<double>(c) : pp_build_launch<float>(c));
+    return d ? pp_sweep_launch<double>(c, useV) : pp_sweep_launch<float>(c, useV);
+  }));
+  CKS(capture_into(c, sp.conditional.phGraph_out[2], &cnt[2],
+                   [&]() { return d ? pp_sweep_launch<double>(c, useV) : pp_sweep_launch<float>(c, useV); }));
+  CKS(capture_into(c, sp.conditional.phGraph_out[3], &cnt[3],
+                   [&]() { return d ? fitness_launch<double>(c) : fitness_launch<float>(c); }));
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ex, G, 0);
+  if (e != cudaSuccess) return c->cuda_fail("cudaGraphInstantiate (device loop)", e);
+  c->loop_exec[slot] = ex;
+  return CPALS_OK;
+}
+
+// Algorithm 3 with every decision on the device; one synchronisation at the end.
+cpals_status run_device_loop(cpals_ctx* c, int max_sweeps, double eps, bool useV, double target,
+                             double* fitness_trace, int* kind_trace, double* time_trace, int* n_done,
+                             int* reached) {
+  if (max_sweeps > c->loop_cap) {
+    // larger traces: the graphs hold the trace pointers
+    for (int i = 0; i < 2; i++)
+      if (c->loop_exec[i]) {
+        cudaGraphExecDestroy(c->loop_exec[i]);
+        c->loop_exec[i] = nullptr;
+      }
+    if (c->loop_fit) cudaFree(c->loop_fit);
+    if (c->loop_time) cudaFree(c->loop_time);
+    if (c->loop_kind) cudaFree(c->loop_kind);
+    c->loop_fit = c->loop_time = nullptr;
+    c->loop_kind = nullptr;
+    c->loop_cap = 0;
+    const int cap = std::max(1024, max_sweeps);
+    CKS(dalloc(c, (void**)&c->loop_fit, (size_t)cap * 8));
+    CKS(dalloc(c, (void**)&c->loop_time, (size_t)cap * 8));
+    CKS(dalloc(c, (void**)&c->loop_kind, (size_t)cap * 4));
+    c->loop_cap = cap;
+  }
+  if (!c->loop_state) {
+    CKS(dalloc(c, &c->loop_state, sizeof(LoopState)));
+    if (cudaMallocHost(&c->loop_state_h, sizeof(LoopState)) != cudaSuccess) {
+      cudaGetLastError();
+      c->loop_state_h = nullptr;
+      return c->fail(CPALS_E_OOM, "cudaMallocHost (loop state)");
+    }
+  }
+  const int slot = useV ? 0 : 1;
+  if (!c->loop_exec[slot]) CKS(loop_build(c, slot, useV));
+  LoopState* h = static_cast<LoopState*>(c->loop_state_h);
+  memset(h, 0, sizeof(LoopState));
+  h->max_sweeps = max_sweeps;
+  h->N = c->N;
+  h->eps = eps;
+  h->target = target;
+  h->tol = c->pp_stop_tol;
+  CK(cudaMemcpyAsync(c->loop_state, h, sizeof(LoopState), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaGraphLaunch(c->loop_exec[slot], c->stream));
+  CK(cudaMemcpyAsync(h, c->loop_state, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
+  const cpals_status sst = sync_read(c);      // also waits for the copy of the state
+  if (sst != CPALS_OK && sst != CPALS_E_TIMEOUT) return sst;
+  const int t = std::min(h->t, max_sweeps);
+  std::vector<double> ft(t), tt(t);
+  std::vector<int> kt(t);
+  if (t > 0) {
+    CK(cudaMemcpyAsync(ft.data(), c->loop_fit, (size_t)t * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(tt.data(), c->loop_time, (size_t)t * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(kt.data(), c->loop_kind, (size_t)t * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  int64_t l = 1 + 2 * ((int64_t)t + h->confirms) + h->confirms * c->loop_count[slot][3];
+  for (int i = 0; i < t; i++) {
+    l += c->loop_count[slot][kt[i] == CPALS_SWEEP_ALS ? 0 : (kt[i] == CPALS_SWEEP_PP_INIT ? 1 : 2)];
+    if (kt[i] == CPALS_SWEEP_PP_INIT) c->ops_built = true;
+    if (fitness_trace) fitness_trace[i] = ft[i];
+    if (kind_trace) kind_trace[i] = kt[i];
+    if (time_trace) time_trace[i] = tt[i];
+  }
+  c->launches += l;
+  if (n_done) *n_done = t;
+  if (reached) *reached = h->hit;
+  if (sst != CPALS_OK) return sst;
+  if (h->err == 3)
+    return c->fail(CPALS_E_TIMEOUT, "a bounded device wait gave up during the run");
+  if (h->err == 1) return c->fail(CPALS_E_NUMERIC, "non-finite value in a sweep");
+  if (h->err == 2) return check_status(c);
+  return CPALS_OK;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -1028,6 +1326,8 @@ void cpals_destroy(cpals_ctx* c) {
   F(c->ctrl_params); F(c->ctrl_io);
   if (c->ctrl_io_h) cudaFreeHost(c->ctrl_io_h);
   for (void* p : c->snap_bufs) F(p);
+  F(c->loop_state); F(c->loop_fit); F(c->loop_time); F(c->loop_kind);
+  if (c->loop_state_h) cudaFreeHost(c->loop_state_h);
   if (c->scal_h) cudaFreeHost(c->scal_h);
   if (c->status_h) cudaFreeHost(c->status_h);
   for (int i = 0; i < kEvPairs; i++) {
@@ -1240,16 +1540,34 @@ cpals_status cpals_run(cpals_ctx* c, int max_sweeps, double eps, int use_V, doub
   CKS(ready(c));
   if (max_sweeps < 0) return c->fail(CPALS_E_INVALID, "max_sweeps < 0");
   Join j(c);
+  if (c->device_loop && c->graphs && !c->profiling && max_sweeps > 0) {
+    if (c->loop_note.empty()) {
+      const std::string saved = c->err;
+      cpals_status st = run_device_loop(c, max_sweeps, eps, use_V != 0, target, fitness_trace,
+                                        kind_trace, time_trace, n_done, reached);
+      // a graph this driver cannot build or run with conditional nodes: the
+      // host loop below takes over (the reason stays in loop_note)
+      if (st != CPALS_E_CUDA || c->loop_exec[use_V ? 0 : 1]) return st;
+      c->loop_note = c->err;
+      c->err = saved;
+      cudaGetLastError();
+    }
+  }
   const auto t0 = std::chrono::steady_clock::now();
   int t = 0;
   int hit = 0;
+  double f_last = -1e300, f_prev = -1e300;   // fitness seen after the last two sweeps
   auto record = [&](int kind, double f) {
     if (fitness_trace) fitness_trace[t] = f;
     if (kind_trace) kind_trace[t] = kind;
     if (time_trace)
       time_trace[t] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     t++;
+    f_prev = f_last;
+    f_last = f;
   };
+  const double tol = c->pp_stop_tol;
+  auto gained = [&]() { return !(tol > 0.0) || f_last - f_prev >= tol; };
   cpals_status st = CPALS_OK;
   // make sure the eps test sees current ratios
   st = sync_read(c);
@@ -1260,7 +1578,7 @@ cpals_status cpals_run(cpals_ctx* c, int max_sweeps, double eps, int use_V, doub
       c->ops_built = true;
       st = sync_read(c);
       bool first = true;
-      while (st == CPALS_OK && t < max_sweeps && all_small(c, eps)) {
+      while (st == CPALS_OK && t < max_sweeps && all_small(c, eps) && (first || gained())) {
         st = do_pp(c, use_V != 0);
         if (st != CPALS_OK) break;
         st = sync_read(c);
@@ -1730,6 +2048,23 @@ cpals_status cpals_set_wait_limit(cpals_ctx* c, uint64_t cycles) {
   c->wait_limit = cycles;
   drop_graphs(c);   // the bound is a launch parameter of the captured kernels
   return CPALS_OK;
+}
+
+cpals_status cpals_set_pp_stop_tol(cpals_ctx* c, double tol) {
+  if (!c) return CPALS_E_INVALID;
+  if (!(tol >= 0.0)) return c->fail(CPALS_E_INVALID, "pp stop tolerance must be >= 0");
+  c->pp_stop_tol = tol;
+  return CPALS_OK;
+}
+
+cpals_status cpals_set_device_loop(cpals_ctx* c, int enable) {
+  if (!c) return CPALS_E_INVALID;
+  c->device_loop = enable != 0;
+  return CPALS_OK;
+}
+
+int cpals_device_loop_active(const cpals_ctx* c) {
+  return (c && c->device_loop && c->graphs && !c->profiling && c->loop_note.empty()) ? 1 : 0;
 }
 
 cpals_status cpals_set_graphs(cpals_ctx* c, int enable) {

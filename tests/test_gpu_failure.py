@@ -73,3 +73,23 @@ def test_nan_in_tensor_reports_numeric(prec):
         g.init_factors(p.A0)
         f = g.als_sweep()
         assert np.isfinite(f) and 0.0 < f <= 1.0
+
+
+def test_wait_limit_timeout_in_device_loop():
+    """The same bounded wait running out inside cpals_run's device loop: the
+    loop stops at that sweep, the run reports CPALS_E_TIMEOUT, and the
+    context runs normally once the bound is restored and the status cleared."""
+    p = synth.make_problem("normal", [64, 72, 80], 16, seed=23, storage="f32")
+    X = torch.from_numpy(np.ascontiguousarray(p.X)).cuda()
+    with cpals.CPALS(p.dims, p.R, "mixed") as g:
+        g.set_tensor(X)
+        g.init_factors(p.A0)
+        assert g.device_loop_active()
+        g.set_wait_limit(1)
+        with pytest.raises(cpals.CPALSError) as ei:
+            g.run(10, 0.2, True, 0.0)
+        assert ei.value.status == E_TIMEOUT, ei.value
+        g.set_wait_limit(0)
+        g.init_factors(p.A0)
+        out = g.run(10, 0.2, True, 0.0)
+        assert len(out["kinds"]) == 10 and np.all(np.isfinite(out["fitness"]))

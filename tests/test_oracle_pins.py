@@ -767,3 +767,79 @@ def test_pp_tucker_core_estimate():
     assert max(float(np.max(np.abs(d))) for d in dA) < 1e-10
     exact = core_loops(q.X, A[0], A[1], A[2])
     np.testing.assert_allclose(est, exact, rtol=0, atol=1e-10 * float(np.linalg.norm(q.X)))
+
+
+def test_pp_fitness_estimate_is_the_order3_expansion_minus_its_product_term():
+    """The fitness a PP sweep reports uses the first-order right-hand side of
+    the last mode.  For order 3 the expansion of Sec. 3.1.1 has exactly one
+    term beyond first order, X contracted with dA^(1) and dA^(2), so the
+    estimate's inner product is the exact <X, [[A]]> minus that term (both
+    summed here straight from X), and at dA = 0 the estimate is the exact
+    fitness of A_p."""
+    g = np.random.default_rng(71)
+    X = g.standard_normal((7, 6, 5))
+    Ap = [g.standard_normal((s, 3)) for s in X.shape]
+    ops, Mp = O.pp_operators(X, Ap)
+    normX = float(np.linalg.norm(X))
+    zero = [np.zeros_like(a) for a in Ap]
+    assert abs(O.pp_fitness_estimate(ops, Mp, Ap, zero, normX) - O.fitness(X, Ap)) < 1e-13
+    dA = [0.05 * g.standard_normal(a.shape) for a in Ap]
+    A = [a + d for a, d in zip(Ap, dA)]
+    inner = float(np.einsum("abc,ar,br,cr->", X, A[0], A[1], A[2], optimize=False))
+    second = float(np.einsum("abc,ar,br,cr->", X, dA[0], dA[1], A[2], optimize=False))
+    model = float(np.sum(reduce_hadamard([a.T @ a for a in A])))
+    want = 1.0 - np.sqrt(max(normX ** 2 - 2.0 * (inner - second) + model, 0.0)) / normX
+    got = O.pp_fitness_estimate(ops, Mp, A, dA, normX)
+    assert abs(got - want) < 1e-12, (got, want)
+    assert abs(got - O.fitness(X, A)) > 1e-8          # the product term matters here
+
+
+def reduce_hadamard(mats):
+    out = np.ones_like(mats[0])
+    for m in mats:
+        out = out * m
+    return out
+
+
+def test_pp_stop_tolerance_sequence():
+    """Algorithm 3's stopping test inside the PP loop, in the fitness-difference
+    form of Sec. 5.1 (pp_stop_tol): a PP run goes on at the head of each of
+    its sweeps after the first only if the last sweep raised the fitness the
+    algorithm sees by at least the tolerance and the eps test holds;
+    otherwise an ALS sweep follows.  Checked from the trace's own values and
+    ratios recomputed from the factor history; a tolerance no sweep can meet
+    ends every PP run after its initialisation sweep; a zero tolerance is the
+    run without the test."""
+    p = synth.make_problem("collinear", [14, 13, 12], 4, seed=11, noise=1e-2, collinearity=0.8,
+                           storage="f64")
+    eps = 0.0993
+    hist = []
+    _, tr = O.pp_cp_als(p.X, p.A0, 45, eps, on_sweep=lambda k, A: hist.append([a.copy() for a in A]))
+    _, tr0 = O.pp_cp_als(p.X, p.A0, 45, eps, pp_stop_tol=0.0)
+    assert tr0.kinds == tr.kinds
+    _, big = O.pp_cp_als(p.X, p.A0, 45, eps, pp_stop_tol=1.0)
+    for t, k in enumerate(big.kinds[:-1]):
+        if k == "pp_init":
+            assert big.kinds[t + 1] == "als"
+    assert "pp_init" in big.kinds and "pp_approx" not in big.kinds
+    tol = 2e-6
+    after = []
+    _, tt = O.pp_cp_als(p.X, p.A0, 45, eps, pp_stop_tol=tol,
+                        on_sweep=lambda k, A: after.append([a.copy() for a in A]))
+    kinds, seen = tt.kinds, tt.seen
+    prev_f = [a.copy() for a in p.A0]
+    Ap, r = None, []
+    for t, k in enumerate(kinds):
+        if k == "pp_init":
+            Ap = prev_f
+        r.append(_max_ratio(after[t], Ap if k != "als" else prev_f))
+        prev_f = after[t]
+    stops = 0
+    for t in range(1, len(kinds)):
+        if kinds[t - 1] in ("pp_init", "pp_approx"):
+            gain = seen[t - 1] - (seen[t - 2] if t >= 2 else -np.inf)
+            go = r[t - 1] < eps and gain >= tol
+            assert kinds[t] == ("pp_approx" if go else "als"), t
+            stops += r[t - 1] < eps and gain < tol
+    assert stops >= 1, "no PP run ended on the stopping test"
+    assert kinds != tr.kinds
