@@ -45,6 +45,9 @@ CSRC = os.path.join(ROOT, "paper_1811_10573_gb300", "csrc")
 # FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2070 MHz
 # (the 1.25 TFLOP/s FP64 figure of the part at its maximum SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# Algorithm 3's stopping test inside PP runs (fitness-difference form): a PP
+# run goes on only while each sweep gains at least the target's own margin
+PP_STOP_TOL = 1e-6
 
 
 def log(*a):
@@ -329,6 +332,7 @@ def run_ours(args):
     dims, R, sweeps, eps = p0.dims, p0.R, p0.sweeps, p0.eps
     max_sweeps = 2 * sweeps
     ctx = {"fp64": cpals.CPALS(dims, R, "fp64")}
+    ctx["fp64"].set_pp_stop_tol(PP_STOP_TOL)
 
     def load(s):
         if s not in probs:
@@ -356,6 +360,7 @@ def run_ours(args):
     # ---- headline: PP-ALS in the headline precision (float64 by default)
     if hp not in ctx:
         ctx[hp] = cpals.CPALS(dims, R, hp)
+        ctx[hp].set_pp_stop_tol(PP_STOP_TOL)
     gh = ctx[hp]
     gh.set_profiling(True)
     gh.set_tensor(Xd[seeds[0]])
@@ -378,6 +383,19 @@ def run_ours(args):
     fl, pc = gh.get_stats(0), gh.get_stats(2)
     launches = gh.get_stats(1)["launches"]
     gh.set_profiling(False)
+    # the same runs with Algorithm 3's decisions on the device (the default
+    # of cpals_run; the timed steps above keep the host loop because their
+    # CUDA events, which time the contraction for the roofline, cannot sit
+    # inside the device loop's conditional graph)
+    loop_check = {}
+    for s in seeds[: min(3, nseed)]:
+        gh.set_tensor(Xd[s])
+        runner.run(gh, probs[s].A0, max_sweeps, eps, target[s])    # device-loop graph capture
+        dd, od = runner.run(gh, probs[s].A0, max_sweeps, eps, target[s])
+        hs = [x for x in steps if x["seed"] == s]
+        loop_check[str(s)] = {"device_loop_s": round(dd, 6), "host_loop_s": hs[0]["s"] if hs else None,
+                              "same_kinds": (counts_of(od["kinds"]) == hs[0]["counts"]) if hs else None,
+                              "reached": bool(od["reached"])}
     value = statistics.mean(x["s"] for x in steps)
     pp_by_seed = {}
     for x in steps:
@@ -488,12 +506,13 @@ def run_ours(args):
         "dtype": {"mixed": "bf16-tc/fp32/f32x2", "fp32": "fp32/f32x2", "fp64": "f64"}[hp],
         "data": "synthetic",
         "config": {"workload": p0.name, "dims": dims, "R": R, "eps": eps, "max_sweeps": max_sweeps,
+                   "pp_stop_tol": PP_STOP_TOL,
                    "seeds": seeds, "precision": hp, "use_V": True,
                    "target": "f* - 1e-6, f* = float64 GPU ALS fitness after 200 sweeps, per seed",
                    "normal_eq": "fp64" if hp == "fp64" else "double-float (f32 pair)",
                    "l2": "flushed between steps (256 MB write); X is 256 MB fp32 (512 MB as float64)",
                    "parallelism": "replicas" if dist.world > 1 else "single GPU"},
-        "reached": reached, "steps_detail": steps,
+        "reached": reached, "steps_detail": steps, "device_loop_check": loop_check,
         "f_star_per_seed": {str(s): f_star[s] for s in seeds},
         "als_fp64_per_seed": {str(s): als64[s] for s in seeds},
         "reduced_precision": reduced or None,
@@ -559,16 +578,16 @@ def precision_block(prec, ctx, dims, R, seeds, probs, Xd, target, f_star, runner
 
     if prec not in ctx:
         ctx[prec] = cpals.CPALS(dims, R, prec)
+        ctx[prec].set_pp_stop_tol(PP_STOP_TOL)
     g = ctx[prec]
     params = ctrl.load() if learned else None
     per = {}
-    g.set_profiling(prec == "mixed")
     for i, s in enumerate(seeds):
         p = probs[s]
         g.set_tensor(Xd[s])
         if i == 0:
             runner.run(g, p.A0, max_sweeps, eps, target[s])        # graph capture
-            g.reset_stats()
+            runner.run(g, p.A0, max_sweeps, 0.0, target[s])
         dpp, opp = runner.run(g, p.A0, max_sweeps, eps, target[s])
         dals, oals = runner.run(g, p.A0, max_sweeps, 0.0, target[s])
         e = {"pp_s": round(dpp, 6), "pp_reached": bool(opp["reached"]), "pp_sweeps": len(opp["kinds"]),
@@ -579,6 +598,13 @@ def precision_block(prec, ctx, dims, R, seeds, probs, Xd, target, f_star, runner
              "als_final_minus_f_star": float(f"{oals['fitness'][-1] - f_star[s]:.3e}")}
         e["speedup"] = round(dals / dpp, 3) if (oals["reached"] and opp["reached"]) else None
         per[str(s)] = e
+    # the tensor-core roofline: CUDA events around every first-level
+    # contraction of one more PP-ALS run of the first seed (host loop)
+    g.set_profiling(prec == "mixed")
+    g.set_tensor(Xd[seeds[0]])
+    runner.run(g, probs[seeds[0]].A0, max_sweeps, eps, target[seeds[0]])
+    g.reset_stats()
+    runner.run(g, probs[seeds[0]].A0, max_sweeps, eps, target[seeds[0]])
     st = g.get_stats(0)
     g.set_profiling(False)
     if params is not None:
@@ -610,7 +636,7 @@ def precision_block(prec, ctx, dims, R, seeds, probs, Xd, target, f_star, runner
         ach = st["bytes"] / (st["total_ms"] / 1e3) / 1e9
         out["roofline_tc"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"],
                               "unit": "GB/s", "frac": round(ach / pk["hbm_gbs"], 4),
-                              "kernel": "first-level contraction (tcgen05 bf16), PP-ALS runs",
+                              "kernel": "first-level contraction (tcgen05 bf16), one PP-ALS run of the first seed",
                               "launches": st["launches"],
                               "avg_launch_us": round(st["total_ms"] * 1e3 / max(1, st["launches"]), 2),
                               "algorithmic_bytes_per_launch": round(st["bytes"] / max(1, st["launches"])),
@@ -639,6 +665,7 @@ def run_config(cname, dist, runner):
     for prec in ("fp64", "mixed"):
         with cpals.CPALS(p.dims, p.R, prec) as g:
             g.set_tensor(X)
+            g.set_pp_stop_tol(PP_STOP_TOL)
             runner.run(g, p.A0, 2, 0.0, 0.0)                      # graph capture
             if prec == "fp64":
                 dt, out = runner.run(g, p.A0, p.sweeps, 0.0, 0.0)
@@ -659,11 +686,20 @@ def run_config(cname, dist, runner):
                  "pp_counts": counts_of(opp["kinds"]),
                  "pp_per_sweep_us": round(dpp / max(1, len(opp["kinds"])) * 1e6, 1), **als}
             e["speedup"] = round(e["als_s"] / dpp, 3) if (e["als_s"] and opp["reached"]) else None
+            if cname == "order3_60_rank10":
+                # the same PP-ALS run with a host round trip per sweep
+                g.set_device_loop(False)
+                runner.run(g, p.A0, 2 * p.sweeps, p.eps, target)
+                dh, oh = runner.run(g, p.A0, 2 * p.sweeps, p.eps, target)
+                g.set_device_loop(True)
+                e["host_loop_pp_s"] = round(dh, 6)
+                e["host_loop_pp_per_sweep_us"] = round(dh / max(1, len(oh["kinds"])) * 1e6, 1)
             res[prec] = e
             summ[prec] = {"pp_s": e["pp_s"], "als_s": e["als_s"], "speedup": e["speedup"]}
     if cname == "order3_60_rank10":
         res["graph_replay_floor_us"] = round(graph_replay_floor_us(), 1)
         summ["fp64_pp_per_sweep_us"] = res["fp64"]["pp_per_sweep_us"]
+        summ["fp64_host_loop_pp_per_sweep_us"] = res["fp64"].get("host_loop_pp_per_sweep_us")
         summ["graph_replay_floor_us"] = res["graph_replay_floor_us"]
     res["summary"] = summ
     return res
@@ -680,6 +716,7 @@ def run_batch_bench(args, dist, flush, prec, workers=16):
     try:
         for q in probs:
             g = cpals.CPALS(q.dims, q.R, prec)
+            g.set_pp_stop_tol(PP_STOP_TOL)
             g.set_tensor(torch.from_numpy(np.ascontiguousarray(q.X)).cuda())
             ctxs.append(g)
 
@@ -797,6 +834,7 @@ def run_variants(args, dist, p, Xd, flush, max_sweeps, prec):
         res = {"note": note, "target_fitness": target}
         with cpals.CPALS(q.dims, q.R, prec) as g:
             g.set_tensor(X)
+            g.set_pp_stop_tol(PP_STOP_TOL)
             setup(g)
             for kind, eps in (("pp", q.eps), ("als", 0.0)):
                 ts, ok = [], True
