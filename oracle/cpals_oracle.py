@@ -369,18 +369,24 @@ def pp_mttkrp(ops, Mp, A, dA, n: int, use_V: bool = True) -> np.ndarray:
 
 
 def pp_sweep(ops, Mp, A, Ap, dA, S, use_V: bool = True, info: SolveInfo | None = None,
-             lam=None, tie=None):
+             lam=None, tie=None, last_rhs=None):
     """One PP approximated sweep (the PP sweep of Algorithm 3); lists updated in
     place.  ``lam`` and ``tie`` as in ``als_sweep``: the step size blends the
     current factor with the solution of the approximated normal equations, and
-    a tied mode takes its partner's factor, Gram and dA = A - A_p."""
+    a tied mode takes its partner's factor, Gram and dA = A - A_p.  A list
+    passed as ``last_rhs`` receives the last mode's M~^(N) (Eq. 3; for a
+    tied last mode, which is not solved for, its first-order part)."""
     N = len(A)
     gnorm = [0.0] * N
     for n in range(N):
         if tie and n in tie:
+            if last_rhs is not None and n == N - 1:
+                last_rhs.append(pp_first_order(ops, Mp, dA, n))
             continue
         G = gamma(S, n)
         Mt = pp_mttkrp(ops, Mp, A, dA, n, use_V)
+        if last_rhs is not None and n == N - 1:
+            last_rhs.append(Mt)
         Anew = step(A[n], solve_normal(Mt, G, info), _lam(lam, n))
         gnorm[n] = float(np.linalg.norm((A[n] - Anew) @ G))
         A[n] = Anew
@@ -390,13 +396,12 @@ def pp_sweep(ops, Mp, A, Ap, dA, S, use_V: bool = True, info: SolveInfo | None =
     return gnorm
 
 
-def pp_fitness_estimate(ops, Mp, A, dA, normX: float) -> float:
+def pp_fitness_estimate(Mt, A, normX: float) -> float:
     """The fitness a PP sweep reports without touching X: the fitness formula
-    of Sec. 5 with the inner product <X, [[A]]> taken from the first-order
-    right-hand side of the last mode, M_p^(N) + sum_i M_p^(i,N) x_i dA^(i)
-    (Eq. 3 without its second-order terms), and the factors after the sweep."""
+    of Sec. 5 with the inner product <X, [[A]]> taken from the last mode's
+    approximated right-hand side Mt = M~^(N) of that sweep (Eq. 3, formed
+    before the last mode's update) and the factors after the sweep."""
     N = len(A)
-    Mt = pp_first_order(ops, Mp, dA, N - 1)
     inner = float(np.sum(Mt * A[N - 1]))
     res2 = normX * normX - 2.0 * inner + norm_model_sq(A)
     return 1.0 - math.sqrt(max(res2, 0.0)) / normX
@@ -430,11 +435,15 @@ def pp_cp_als(X: np.ndarray, A0, n_sweeps: int, eps: float, use_V: bool = True,
     fitness is always the exact one.  The stopping test Delta of Algorithm 3
     is not used to end the run (fixed budgets); with ``pp_stop_tol`` > 0 it
     is taken inside the PP loop in the form of the paper's experiments
-    (Sec. 5.1: the fitness difference of two neighbouring sweeps): at the
-    head of every PP sweep after the first of a run, the run goes on only if
-    the last sweep raised the fitness the algorithm sees (``PPTrace.seen``)
-    by at least ``pp_stop_tol``; otherwise the regular ALS sweep follows, as
-    when the eps test fails.  ``on_sweep(kind, A)`` is called after every
+    (Sec. 5.1: the fitness difference of two neighbouring sweeps), between
+    the two last sweeps of the PP run: at the head of every PP sweep after
+    the second of a run, the run goes on only if the last PP sweep raised
+    the fitness estimate (``pp_fitness_estimate``, ``PPTrace.seen``) over
+    the one before it by at least ``pp_stop_tol``; otherwise the regular ALS
+    sweep follows, as when the eps test fails.  (Both values are estimates
+    from the same operators, so their difference follows the run's progress;
+    the estimate against the exact fitness of the ALS sweep before the run
+    would carry the estimate's own second-order error.)  ``on_sweep(kind, A)`` is called after every
     sweep.  ``lam`` and ``tie`` select the ALS variants of Sec. 5.1 for both
     sweep kinds (see ``als_sweep``).
     """
@@ -456,11 +465,10 @@ def pp_cp_als(X: np.ndarray, A0, n_sweeps: int, eps: float, use_V: bool = True,
         if on_sweep is not None:
             on_sweep(kind, A)
 
-    def gained():
-        if pp_stop_tol <= 0.0:
+    def gained(run):
+        if pp_stop_tol <= 0.0 or run < 2:
             return True
-        prev = tr.seen[-2] if len(tr.seen) >= 2 else -math.inf
-        return tr.seen[-1] - prev >= pp_stop_tol
+        return tr.seen[-1] - tr.seen[-2] >= pp_stop_tol
 
     t = 0
     while t < n_sweeps:
@@ -469,10 +477,13 @@ def pp_cp_als(X: np.ndarray, A0, n_sweeps: int, eps: float, use_V: bool = True,
             ops, Mp = pp_operators(X, Ap)
             dA = [np.zeros_like(a) for a in A]
             first = True
-            while t < n_sweeps and _small(dA, A, eps) and (first or gained()):
-                pp_sweep(ops, Mp, A, Ap, dA, S, use_V, info, lam=lam, tie=tie)
+            run = 0                       # PP sweeps of this run so far
+            while t < n_sweeps and _small(dA, A, eps) and gained(run):
+                last = []
+                pp_sweep(ops, Mp, A, Ap, dA, S, use_V, info, lam=lam, tie=tie, last_rhs=last)
                 t += 1
-                log("pp_init" if first else "pp_approx", pp_fitness_estimate(ops, Mp, A, dA, normX))
+                run += 1
+                log("pp_init" if first else "pp_approx", pp_fitness_estimate(last[0], A, normX))
                 first = False
             if t >= n_sweeps:
                 break

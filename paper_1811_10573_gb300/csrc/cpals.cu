@@ -342,6 +342,9 @@ void finish_mode(cpals_ctx* c, int n, const T* rhs, bool pp, bool useV) {
   cudaStreamWaitEvent(c->stream, c->ev_join, 0);
   if (c->dfm) {
     float* Ahi = P<float>(c->Ac[n]);
+    // the last mode's full M~ (with the second-order terms) for the PP
+    // fitness estimate; the solve forms its own double-float sum
+    if (v && n == c->N - 1) vterm_fz((const float*)rhs, Ahi, c->Zf, P<float>(c->rhs2), s, R, c->L());
     solve_df((const float*)rhs, c->A[n], Ahi, c->Alo[n], pp ? c->Aphi[n] : nullptr,
              pp ? c->Aplo[n] : nullptr, c->dA[n], P<float>(c->dAc[n]), c->Linv,
              v ? c->Zf : nullptr, (float2*)c->rownorm, s, R, n, c->lam[n], c->status, c->L());
@@ -606,8 +609,11 @@ cpals_status pp_sweep_launch(cpals_ctx* c, bool useV) {
     finish_mode<T>(c, n, P<const T>(c->rhs), true, useV);
     CKS(tie_copy(c, n));
   }
-  // fitness estimate from M~^(N) (the last right-hand side, updated factors)
-  fitness<T>(P<const T>(c->rhs), c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->scal + 40,
+  // fitness estimate from M~^(N) (the last mode's right-hand side with the
+  // second-order terms when they are on; the updated factors); a tied last
+  // mode, which is not solved for, has only the first-order part
+  const bool full = useV && !tied(c, N - 1);
+  fitness<T>(P<const T>(full ? c->rhs2 : c->rhs), c->A[N - 1], c->S, N, R, (int)c->dims[N - 1], c->scal + 40,
              c->scal, c->dpart, c->tickets + 62, c->L());
   return CPALS_OK;
 }
@@ -914,6 +920,7 @@ struct LoopState {
   double eps, target, pending_f;
   double tol;       // PP runs end when a sweep gains less fitness than this (0: off)
   double f_last, f_prev;   // fitness the algorithm saw after the last two sweeps
+  int in_run;       // PP sweeps of the current PP run up to the last sweep (0 after ALS)
   unsigned long long t0;
 };
 
@@ -937,6 +944,7 @@ __global__ void loop_init_kernel(LoopState* s, const double* scal, cudaGraphCond
   s->err = 0;
   s->confirms = 0;
   s->f_last = s->f_prev = -1e300;
+  s->in_run = 0;
   s->next = loop_all_small(s, scal) ? 1 : 0;   // the test at the head of the first sweep
   s->t0 = global_ns();
   cudaGraphSetConditional(hw, s->max_sweeps > 0 ? 1u : 0u);
@@ -959,6 +967,7 @@ __global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* 
     s->t = t + 1;
     s->f_prev = s->f_last;
     s->f_last = fv;
+    s->in_run = kind == 0 ? 0 : (kind == 1 ? 1 : s->in_run + 1);
   };
   bool stop = false;
   if (ran == 3) {
@@ -1001,8 +1010,9 @@ __global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* 
     return;
   }
   const bool small = loop_all_small(s, scal);
-  // inside a PP run the stopping test also asks for a fitness gain of tol
-  const bool gain = !(s->tol > 0.0) || s->f_last - s->f_prev >= s->tol;
+  // from the third sweep of a PP run on, the stopping test also asks the
+  // last PP sweep for a gain of tol over the one before it
+  const bool gain = !(s->tol > 0.0) || s->in_run < 2 || s->f_last - s->f_prev >= s->tol;
   s->next = ran != 0 ? ((small && gain) ? 2 : 0) : (small ? 1 : 0);
   cudaGraphSetConditional(hw, 1u);
 }
@@ -1557,6 +1567,7 @@ cpals_status cpals_run(cpals_ctx* c, int max_sweeps, double eps, int use_V, doub
   int t = 0;
   int hit = 0;
   double f_last = -1e300, f_prev = -1e300;   // fitness seen after the last two sweeps
+  int in_run = 0;                              // PP sweeps of the current PP run
   auto record = [&](int kind, double f) {
     if (fitness_trace) fitness_trace[t] = f;
     if (kind_trace) kind_trace[t] = kind;
@@ -1565,9 +1576,10 @@ cpals_status cpals_run(cpals_ctx* c, int max_sweeps, double eps, int use_V, doub
     t++;
     f_prev = f_last;
     f_last = f;
+    in_run = kind == CPALS_SWEEP_ALS ? 0 : (kind == CPALS_SWEEP_PP_INIT ? 1 : in_run + 1);
   };
   const double tol = c->pp_stop_tol;
-  auto gained = [&]() { return !(tol > 0.0) || f_last - f_prev >= tol; };
+  auto gained = [&]() { return !(tol > 0.0) || in_run < 2 || f_last - f_prev >= tol; };
   cpals_status st = CPALS_OK;
   // make sure the eps test sees current ratios
   st = sync_read(c);

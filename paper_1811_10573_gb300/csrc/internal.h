@@ -96,6 +96,8 @@ void solve_rows_v(const T* rhs, double* A, const double* Aref, double* dA, const
 // out[y][r] = rhs[y][r] + sum_k A[y][k] Z[k][r] in the compute precision.
 template <typename T>
 void vterm(const T* rhs, const T* A, const double* Z, T* out, int s, int R, Launch L);
+// The same with a float Z (the double-float path's second-order terms).
+void vterm_fz(const float* rhs, const float* A, const float* Z, float* out, int s, int R, Launch L);
 // Raise the dynamic shared-memory limits of the float64 kernels (call once per device).
 cudaError_t setup_small_kernels();
 

@@ -87,9 +87,9 @@ gamma_chol_kernel(const double* __restrict__ S, const double* __restrict__ W, in
 
 // rhs2[y][r] = rhs[y][r] + sum_k A[y][k] Z[k][r]  (second-order PP terms), in the
 // compute precision T (a second-order correction; float64 in FP64 mode).
-template <typename T>
+template <typename T, typename TZ>
 __global__ void __launch_bounds__(256)
-vterm_kernel(const T* __restrict__ rhs, const T* __restrict__ A, const double* __restrict__ Z,
+vterm_kernel(const T* __restrict__ rhs, const T* __restrict__ A, const TZ* __restrict__ Z,
              T* __restrict__ out, int s, int R) {
   extern __shared__ unsigned char zsm[];
   T* Zs = reinterpret_cast<T*>(zsm);
@@ -420,9 +420,11 @@ cudaError_t setup_small_kernels() {
     e = cudaFuncSetAttribute(solve_rows_kernel<float, float>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sv);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(vterm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, vz);
+    e = cudaFuncSetAttribute(vterm_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, vz);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(vterm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, vz);
+    e = cudaFuncSetAttribute(vterm_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, vz);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(vterm_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, vz);
   return e;
 }
 
@@ -455,8 +457,15 @@ void solve_rows(const T* rhs, double* A, const double* Aref, double* dA, const d
 template <typename T>
 void vterm(const T* rhs, const T* A, const double* Z, T* out, int s, int R, Launch L) {
   const int64_t tot = (int64_t)s * R;
-  vterm_kernel<T><<<(int)std::min<int64_t>(cdiv(tot, 256), 152 * 2), 256,
-                    (size_t)R * R * sizeof(T), L.stream>>>(rhs, A, Z, out, s, R);
+  vterm_kernel<T, double><<<(int)std::min<int64_t>(cdiv(tot, 256), 152 * 2), 256,
+                            (size_t)R * R * sizeof(T), L.stream>>>(rhs, A, Z, out, s, R);
+  (*L.counter)++;
+}
+
+void vterm_fz(const float* rhs, const float* A, const float* Z, float* out, int s, int R, Launch L) {
+  const int64_t tot = (int64_t)s * R;
+  vterm_kernel<float, float><<<(int)std::min<int64_t>(cdiv(tot, 256), 152 * 2), 256,
+                               (size_t)R * R * sizeof(float), L.stream>>>(rhs, A, Z, out, s, R);
   (*L.counter)++;
 }
 
