@@ -48,6 +48,15 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # Algorithm 3's stopping test inside PP runs (fitness-difference form): a PP
 # run goes on only while each sweep gains at least the target's own margin
 PP_STOP_TOL = 1e-6
+HOST_LOOP = False      # --host-loop: decisions on the host (for profilers)
+
+
+def prep(g):
+    """Settings every decomposition context of the benchmark gets."""
+    g.set_pp_stop_tol(PP_STOP_TOL)
+    if HOST_LOOP:
+        g.set_device_loop(False)
+    return g
 
 
 def log(*a):
@@ -70,6 +79,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tucker", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline and FP32/mixed only")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="Algorithm 3's decisions on the host in every run (for profilers)")
     return ap.parse_args()
 
 
@@ -332,7 +343,7 @@ def run_ours(args):
     dims, R, sweeps, eps = p0.dims, p0.R, p0.sweeps, p0.eps
     max_sweeps = 2 * sweeps
     ctx = {"fp64": cpals.CPALS(dims, R, "fp64")}
-    ctx["fp64"].set_pp_stop_tol(PP_STOP_TOL)
+    prep(ctx["fp64"])
 
     def load(s):
         if s not in probs:
@@ -360,7 +371,7 @@ def run_ours(args):
     # ---- headline: PP-ALS in the headline precision (float64 by default)
     if hp not in ctx:
         ctx[hp] = cpals.CPALS(dims, R, hp)
-        ctx[hp].set_pp_stop_tol(PP_STOP_TOL)
+        prep(ctx[hp])
     gh = ctx[hp]
     gh.set_profiling(True)
     gh.set_tensor(Xd[seeds[0]])
@@ -388,7 +399,7 @@ def run_ours(args):
     # CUDA events, which time the contraction for the roofline, cannot sit
     # inside the device loop's conditional graph)
     loop_check = {}
-    for s in seeds[: min(3, nseed)]:
+    for s in ([] if HOST_LOOP else seeds[: min(3, nseed)]):
         gh.set_tensor(Xd[s])
         runner.run(gh, probs[s].A0, max_sweeps, eps, target[s])    # device-loop graph capture
         dd, od = runner.run(gh, probs[s].A0, max_sweeps, eps, target[s])
@@ -578,7 +589,7 @@ def precision_block(prec, ctx, dims, R, seeds, probs, Xd, target, f_star, runner
 
     if prec not in ctx:
         ctx[prec] = cpals.CPALS(dims, R, prec)
-        ctx[prec].set_pp_stop_tol(PP_STOP_TOL)
+        prep(ctx[prec])
     g = ctx[prec]
     params = ctrl.load() if learned else None
     per = {}
@@ -665,7 +676,7 @@ def run_config(cname, dist, runner):
     for prec in ("fp64", "mixed"):
         with cpals.CPALS(p.dims, p.R, prec) as g:
             g.set_tensor(X)
-            g.set_pp_stop_tol(PP_STOP_TOL)
+            prep(g)
             runner.run(g, p.A0, 2, 0.0, 0.0)                      # graph capture
             if prec == "fp64":
                 dt, out = runner.run(g, p.A0, p.sweeps, 0.0, 0.0)
@@ -716,7 +727,7 @@ def run_batch_bench(args, dist, flush, prec, workers=16):
     try:
         for q in probs:
             g = cpals.CPALS(q.dims, q.R, prec)
-            g.set_pp_stop_tol(PP_STOP_TOL)
+            prep(g)
             g.set_tensor(torch.from_numpy(np.ascontiguousarray(q.X)).cuda())
             ctxs.append(g)
 
@@ -826,6 +837,7 @@ def run_variants(args, dist, p, Xd, flush, max_sweeps, prec):
 
     def one_variant(q, X, setup, note):
         with cpals.CPALS(q.dims, q.R, "fp64") as g64:
+            prep(g64)
             g64.set_tensor(X)
             setup(g64)
             g64.init_factors(q.A0)
@@ -834,7 +846,7 @@ def run_variants(args, dist, p, Xd, flush, max_sweeps, prec):
         res = {"note": note, "target_fitness": target}
         with cpals.CPALS(q.dims, q.R, prec) as g:
             g.set_tensor(X)
-            g.set_pp_stop_tol(PP_STOP_TOL)
+            prep(g)
             setup(g)
             for kind, eps in (("pp", q.eps), ("als", 0.0)):
                 ts, ok = [], True
@@ -907,6 +919,7 @@ def run_reference(args):
 
 if __name__ == "__main__":
     a = parse()
+    HOST_LOOP = a.host_loop
     if a.impl == "reference":
         run_reference(a)
     else:
