@@ -85,3 +85,22 @@ def test_order3_400_fp64_pp_als_schedule(ctx, gold):
     err = np.abs(fit - ref)
     assert err.max() < 1e-6, (int(err.argmax()), float(err.max()))
     assert fit[-1] >= gold["target"] - 1e-9
+
+
+def test_order3_400_fp64_pp_als_schedule_with_stop_test(ctx, gold):
+    """The benchmark's setting: Algorithm 3's stopping test inside PP runs
+    (tolerance 1e-6, cpals_set_pp_stop_tol) in the library's device loop
+    against the oracle's run with the same test: the same sweep kinds up to
+    the target and the fitness the algorithm sees (exact after ALS sweeps,
+    the M~ estimate after PP sweeps) within 1e-6."""
+    g, p = ctx
+    n = gold["pp_tol_hit_index"] + 1
+    g.set_pp_stop_tol(gold["pp_stop_tol"])
+    try:
+        g.init_factors(p.A0)
+        out = g.run(n, gold["eps"], True, 0.0)
+    finally:
+        g.set_pp_stop_tol(0.0)
+    assert out["kinds"] == gold["pp_tol_kinds"][:n]
+    err = np.abs(np.asarray(out["fitness"]) - np.asarray(gold["pp_tol_seen"][:n]))
+    assert err.max() < 1e-6, (int(err.argmax()), float(err.max()))
