@@ -497,6 +497,42 @@ void gemm_exact_cols(const TX* X, const T* B, T* out, T* partials, int64_t batch
   }
 }
 
+// Resident CTAs per SM of the float64 configuration gemm_exact_cols launches
+// for R (queried once per configuration).
+template <typename TX, bool KM, int BN, int TN>
+int exact_cols_occ() {
+  static int occ = 0;
+  if (occ == 0) {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &o, gemm_simt_kernel<TX, double, KM, 64, BN, 16, 2, TN>, kThreads, 0) != cudaSuccess ||
+        o < 1) {
+      cudaGetLastError();
+      o = 1;
+    }
+    occ = o;
+  }
+  return occ;
+}
+
+template <typename TX, bool KM>
+int exact_cols_occ_for(int R) {
+  switch ((R + 7) / 8) {
+    case 5: return exact_cols_occ<TX, KM, 40, 5>();
+    case 6: return exact_cols_occ<TX, KM, 48, 6>();
+    case 7: return exact_cols_occ<TX, KM, 56, 7>();
+    case 8: return exact_cols_occ<TX, KM, 64, 8>();
+    case 9: return exact_cols_occ<TX, KM, 72, 9>();
+    case 10: return exact_cols_occ<TX, KM, 80, 10>();
+    case 11: return exact_cols_occ<TX, KM, 88, 11>();
+    case 12: return exact_cols_occ<TX, KM, 96, 12>();
+    case 13: return exact_cols_occ<TX, KM, 104, 13>();
+    case 14: return exact_cols_occ<TX, KM, 112, 14>();
+    case 15: return exact_cols_occ<TX, KM, 120, 15>();
+    default: return exact_cols_occ<TX, KM, 128, 16>();
+  }
+}
+
 template <typename TX, typename T>
 void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K, int64_t M,
                int R, bool kmajor, int splits, Launch L) {
@@ -529,6 +565,27 @@ void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int6
     if (kmajor) gemm_launch<TX, T, true, 64, 128, 4, 8>(X, B, out, partials, batch, K, M, R, splits, L);
     else gemm_launch<TX, T, false, 64, 128, 4, 8>(X, B, out, partials, batch, K, M, R, splits, L);
   }
+}
+
+int gemm_simt_wave_splits(int64_t batch, int64_t K, int64_t M, int R, bool kmajor, size_t esz,
+                          int64_t cap) {
+  if (esz != 8 || R <= 32 || gemm_simt_bm(M, R, kmajor) != 64) return 0;
+  int nsm = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int occ = kmajor ? exact_cols_occ_for<double, true>(R) : exact_cols_occ_for<double, false>(R);
+  const int64_t wave = (int64_t)occ * nsm;
+  const int64_t tiles = cdiv(M, 64) * batch;
+  if (tiles >= wave) return 1;
+  int64_t sp = wave / tiles;                                      // whole waves only
+  sp = std::min<int64_t>(sp, std::max<int64_t>(1, K / 256));      // at least 256 k per split
+  sp = std::min<int64_t>(sp, cap / std::max<int64_t>(1, batch * M * R));
+  // the kernel rounds the chunk up to 16 k: keep only counts it runs as given
+  while (sp > 1 && cdiv(K, cdiv(cdiv(K, sp), 16) * 16) != sp) sp--;
+  return (int)std::max<int64_t>(sp, 1);
 }
 
 template <typename T>

@@ -267,6 +267,13 @@ cpals_status contract_first(cpals_ctx* c, int k0, int nk, void* const* facs, T* 
   int splits = 1;
   if (mtiles < 2 * 152) splits = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(2 * 152, mtiles), cdiv(K, 256)));
   while (splits > 1 && (size_t)splits * batch * M * R * sizeof(T) > c->gpart_bytes) splits--;
+  if (!tc) {
+    // float64 SIMT contractions are bound by the FP64 pipe: a grid of whole
+    // waves of resident CTAs leaves no SM idle in a partial last wave
+    const int ws = gemm_simt_wave_splits(batch, K, M, R, kmajor, sizeof(T),
+                                         (int64_t)(c->gpart_bytes / sizeof(T)));
+    if (ws > 0) splits = ws;
+  }
 
   if (tc) {
     const float* fl[kMaxModes];
@@ -937,7 +944,8 @@ __device__ bool loop_all_small(const LoopState* s, const double* scal) {
   return true;
 }
 
-__global__ void loop_init_kernel(LoopState* s, const double* scal, cudaGraphConditionalHandle hw) {
+__global__ void loop_init_kernel(LoopState* s, const double* scal, cudaGraphConditionalHandle hw,
+                                 cudaGraphConditionalHandle hs) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   s->t = 0;
   s->hit = 0;
@@ -947,15 +955,15 @@ __global__ void loop_init_kernel(LoopState* s, const double* scal, cudaGraphCond
   s->in_run = 0;
   s->next = loop_all_small(s, scal) ? 1 : 0;   // the test at the head of the first sweep
   s->t0 = global_ns();
+  cudaGraphSetConditional(hs, (unsigned)s->next);
   cudaGraphSetConditional(hw, s->max_sweeps > 0 ? 1u : 0u);
 }
 
-__global__ void loop_select_kernel(const LoopState* s, cudaGraphConditionalHandle hs) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(hs, (unsigned)s->next);
-}
-
+// The switch's value persists between iterations (its handle has no default
+// assignment): each decision sets it for the next iteration.
 __global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* status, double* ftr,
-                                   int* ktr, double* ttr, cudaGraphConditionalHandle hw) {
+                                   int* ktr, double* ttr, cudaGraphConditionalHandle hw,
+                                   cudaGraphConditionalHandle hs) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int ran = s->next;
   const double f = scal[0];
@@ -997,6 +1005,7 @@ __global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* 
         s->pending = ran;
         s->pending_f = f;
         s->next = 3;
+        cudaGraphSetConditional(hs, 3u);
         cudaGraphSetConditional(hw, 1u);
         return;
       } else {
@@ -1014,6 +1023,7 @@ __global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* 
   // last PP sweep for a gain of tol over the one before it
   const bool gain = !(s->tol > 0.0) || s->in_run < 2 || s->f_last - s->f_prev >= s->tol;
   s->next = ran != 0 ? ((small && gain) ? 2 : 0) : (small ? 1 : 0);
+  cudaGraphSetConditional(hs, (unsigned)s->next);
   cudaGraphSetConditional(hw, 1u);
 }
 
@@ -1059,34 +1069,33 @@ cpals_status loop_build(cpals_ctx* c, int slot, bool useV) {
   LoopState* st = static_cast<LoopState*>(c->loop_state);
   const double* scal = c->scal;
   const int* status = c->status;
-  cudaGraphNode_t n_init, n_while, n_sel, n_sw, n_dec;
-  {
-    void* args[] = {&st, &scal, &hw};
-    CK(add_kernel_node(&n_init, G, nullptr, 0, (void*)loop_init_kernel, args));
-  }
+  cudaGraphNode_t n_init, n_while, n_sw, n_dec;
   cudaGraphNodeParams wp = {};
   wp.type = cudaGraphNodeTypeConditional;
   wp.conditional.handle = hw;
   wp.conditional.type = cudaGraphCondTypeWhile;
   wp.conditional.size = 1;
-  CK(cudaGraphAddNode(&n_while, G, &n_init, nullptr, 1, &wp));
+  // the while node first (its body holds the switch handle), then the init
+  // kernel in front of it
+  CK(cudaGraphAddNode(&n_while, G, nullptr, nullptr, 0, &wp));
   cudaGraph_t B = wp.conditional.phGraph_out[0];
   CK(cudaGraphConditionalHandleCreate(&hs, B, 0, 0));
   {
-    void* args[] = {&st, &hs};
-    CK(add_kernel_node(&n_sel, B, nullptr, 0, (void*)loop_select_kernel, args));
+    void* args[] = {&st, &scal, &hw, &hs};
+    CK(add_kernel_node(&n_init, G, nullptr, 0, (void*)loop_init_kernel, args));
   }
+  CK(cudaGraphAddDependencies(G, &n_init, &n_while, nullptr, 1));
   cudaGraphNodeParams sp = {};
   sp.type = cudaGraphNodeTypeConditional;
   sp.conditional.handle = hs;
   sp.conditional.type = cudaGraphCondTypeSwitch;
   sp.conditional.size = 4;
-  CK(cudaGraphAddNode(&n_sw, B, &n_sel, nullptr, 1, &sp));
+  CK(cudaGraphAddNode(&n_sw, B, nullptr, nullptr, 0, &sp));
   {
     double* ftr = c->loop_fit;
     int* ktr = c->loop_kind;
     double* ttr = c->loop_time;
-    void* args[] = {&st, &scal, &status, &ftr, &ktr, &ttr, &hw};
+    void* args[] = {&st, &scal, &status, &ftr, &ktr, &ttr, &hw, &hs};
     CK(add_kernel_node(&n_dec, B, &n_sw, 1, (void*)loop_decide_kernel, args));
   }
   int64_t* cnt = c->loop_count[slot];
@@ -1161,7 +1170,7 @@ cpals_status run_device_loop(cpals_ctx* c, int max_sweeps, double eps, bool useV
     CK(cudaMemcpyAsync(kt.data(), c->loop_kind, (size_t)t * 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
-  int64_t l = 1 + 2 * ((int64_t)t + h->confirms) + h->confirms * c->loop_count[slot][3];
+  int64_t l = 1 + ((int64_t)t + h->confirms) + h->confirms * c->loop_count[slot][3];
   for (int i = 0; i < t; i++) {
     l += c->loop_count[slot][kt[i] == CPALS_SWEEP_ALS ? 0 : (kt[i] == CPALS_SWEEP_PP_INIT ? 1 : 2)];
     if (kt[i] == CPALS_SWEEP_PP_INIT) c->ops_built = true;
