@@ -196,6 +196,51 @@ cpals_status cpals_run_batch(cpals_ctx* const* ctxs, int n, int workers, int max
                              int use_V, const double* targets, double* fitness_out,
                              int* sweeps_out, int* status_out);
 
+/* ---- many small order-3 decompositions in one set of launches ----
+ * A batch holds n independent order-3 problems of different sizes
+ * (dims[3i..3i+2] <= 4096) and ranks (ranks[i] <= 64) and runs Algorithm 3
+ * on all of them at once: each stage of a sweep (a first-level
+ * contraction, a multi-TTV, the operator build, the PP correction of Eq. 3,
+ * the factorisation of Gamma^(n), the row solves, the Grams, the fitness,
+ * the decision of Algorithm 3) is one launch over every instance, and every
+ * instance keeps its own controller state on the device and takes part only
+ * in the stages of the sweep kind it runs.  One sweep of the batch is one
+ * captured CUDA graph.  precision: CPALS_FP64 or CPALS_FP32 for the
+ * contractions, operators and corrections; Gamma, its Cholesky factor, the
+ * solves, the Grams and the fitness are float64 either way.
+ * The batch owns its device memory and one stream; every call returns after
+ * its work has finished.  Errors: CPALS_E_INVALID (bad sizes or arguments),
+ * CPALS_E_UNSUPPORTED (another precision, not sm_103), CPALS_E_OOM,
+ * CPALS_E_STATE (run before every instance has a tensor and factors),
+ * CPALS_E_CUDA; cpals_batch_last_error describes the last failure. */
+typedef struct cpals_batch cpals_batch;
+cpals_status cpals_batch_create(int n, const int64_t* dims, const int* ranks, int precision,
+                                cpals_batch** out);
+void cpals_batch_destroy(cpals_batch* b);
+/* instance i's tensor: s0 s1 s2 values row-major, dtype 0 = float64,
+ * 1 = float32, host or device pointer; copied; ||X||^2 in float64 */
+cpals_status cpals_batch_set_tensor(cpals_batch* b, int i, const void* data, int dtype, int on_device);
+/* instance i's initial factors: three host float64 arrays s_n x R, copied */
+cpals_status cpals_batch_init_factors(cpals_batch* b, int i, const double* const* factors);
+/* Algorithm 3 on every instance from its initial factors for exactly
+ * max_sweeps sweeps (fewer for an instance whose Gamma lost positive
+ * definiteness or that met a non-finite value), with tolerance eps, the
+ * second-order terms when use_V != 0 and the stopping test inside PP runs
+ * (as cpals_set_pp_stop_tol; 0 = off).  Outputs (each nullable):
+ * fitness_out[n] the exact fitness of the final factors, sweeps_out[n],
+ * status_out[n] (CPALS_OK, CPALS_E_SINGULAR, CPALS_E_NUMERIC), and
+ * kind_trace / fitness_trace [n][max_sweeps] (CPALS_SWEEP_*; exact fitness
+ * after ALS sweeps, the M~ estimate after PP sweeps). */
+cpals_status cpals_batch_run(cpals_batch* b, int max_sweeps, double eps, int use_V, double pp_stop_tol,
+                             double* fitness_out, int* sweeps_out, int* status_out, int* kind_trace,
+                             double* fitness_trace);
+/* instance i's factors into three caller-owned host float64 arrays */
+cpals_status cpals_batch_get_factors(cpals_batch* b, int i, double* const* out);
+/* kernels of one batch sweep graph (one launch per stage over all instances)
+ * and kernels launched by the last run */
+cpals_status cpals_batch_stats(const cpals_batch* b, int64_t* launches_per_sweep, int64_t* launches_last_run);
+const char* cpals_batch_last_error(const cpals_batch* b);
+
 /* ---- Tucker-ALS and PP-Tucker-ALS (Sec. 2.4, Sec. 3.1.2, Algorithm 4) ----
  * Order-3 tensors, IEEE float64 (first-level TTMs optionally on the tensor
  * cores, cpals_tucker_set_precision), Tucker ranks 1 <= R_n <= min(48, s_n),

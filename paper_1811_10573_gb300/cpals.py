@@ -57,6 +57,15 @@ _SIGS = {
     "cpals_set_wait_limit": (C.c_int, [_ctx_p, C.c_uint64]),
     "cpals_set_device_loop": (C.c_int, [_ctx_p, C.c_int]),
     "cpals_set_pp_stop_tol": (C.c_int, [_ctx_p, C.c_double]),
+    "cpals_batch_create": (C.c_int, [C.c_int, _i64p, _ip, C.c_int, C.POINTER(_ctx_p)]),
+    "cpals_batch_destroy": (None, [_ctx_p]),
+    "cpals_batch_set_tensor": (C.c_int, [_ctx_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
+    "cpals_batch_init_factors": (C.c_int, [_ctx_p, C.c_int, C.POINTER(_dp)]),
+    "cpals_batch_run": (C.c_int, [_ctx_p, C.c_int, C.c_double, C.c_int, C.c_double, _dp, _ip, _ip, _ip,
+                                  _dp]),
+    "cpals_batch_get_factors": (C.c_int, [_ctx_p, C.c_int, C.POINTER(_dp)]),
+    "cpals_batch_stats": (C.c_int, [_ctx_p, _i64p, _i64p]),
+    "cpals_batch_last_error": (C.c_char_p, [_ctx_p]),
     "cpals_device_loop_active": (C.c_int, [_ctx_p]),
     "cpals_set_normal_arith": (C.c_int, [_ctx_p, C.c_int]),
     "cpals_set_step_size": (C.c_int, [_ctx_p, _dp]),
@@ -732,3 +741,88 @@ class Tucker:
         out = np.empty(tuple(self.ranks))
         self._ck(cpals_tucker_get_core(self.t, _dptr(out)))
         return out
+
+
+# ---------------------------------------------------------------- batches of small problems
+class Batch:
+    """n order-3 problems run by Algorithm 3 together (cpals_batch_*): every
+    sweep stage is one launch over all of them."""
+
+    def __init__(self, dims, ranks, precision="fp32"):
+        self.dims = [[int(d) for d in ds] for ds in dims]
+        self.ranks = [int(r) for r in ranks]
+        self.n = len(self.dims)
+        assert len(self.ranks) == self.n and all(len(d) == 3 for d in self.dims)
+        flat = np.ascontiguousarray(np.asarray(self.dims, dtype=np.int64).reshape(-1))
+        rk = np.ascontiguousarray(np.asarray(self.ranks, dtype=np.int32))
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        h = _ctx_p()
+        st = lib().cpals_batch_create(self.n, flat.ctypes.data_as(_i64p), rk.ctypes.data_as(_ip), prec,
+                                      C.byref(h))
+        if st != 0:
+            raise CPALSError(st, "cpals_batch_create failed")
+        self.h = h
+
+    def _ck(self, st):
+        if st != 0:
+            msg = lib().cpals_batch_last_error(self.h)
+            raise CPALSError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cpals_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_tensor(self, i, X):
+        if hasattr(X, "data_ptr"):
+            import torch
+            assert X.is_contiguous()
+            dt = {torch.float64: 0, torch.float32: 1}[X.dtype]
+            self._ck(lib().cpals_batch_set_tensor(self.h, i, X.data_ptr(), dt, 1 if X.is_cuda else 0))
+            return
+        X = np.ascontiguousarray(X)
+        dt = {np.dtype(np.float64): 0, np.dtype(np.float32): 1}[X.dtype]
+        self._ck(lib().cpals_batch_set_tensor(self.h, i, X.ctypes.data, dt, 0))
+
+    def init_factors(self, i, factors):
+        fs = [_f64(f) for f in factors]
+        for f, s in zip(fs, self.dims[i]):
+            assert f.shape == (s, self.ranks[i])
+        arr = (_dp * 3)(*[f.ctypes.data_as(_dp) for f in fs])
+        self._ck(lib().cpals_batch_init_factors(self.h, i, arr))
+
+    def run(self, max_sweeps, eps, use_V=True, pp_stop_tol=0.0):
+        fit = np.zeros(self.n)
+        sw = np.zeros(self.n, dtype=np.int32)
+        st = np.zeros(self.n, dtype=np.int32)
+        kt = np.zeros((self.n, max_sweeps), dtype=np.int32)
+        ft = np.zeros((self.n, max_sweeps))
+        self._ck(lib().cpals_batch_run(self.h, max_sweeps, eps, 1 if use_V else 0, pp_stop_tol, _dptr(fit),
+                                       sw.ctypes.data_as(_ip), st.ctypes.data_as(_ip),
+                                       kt.ctypes.data_as(_ip), _dptr(ft)))
+        kinds = [[SWEEP_KINDS[int(k)] for k in kt[i, :sw[i]]] for i in range(self.n)]
+        return {"fitness": fit, "sweeps": sw, "status": st, "kinds": kinds,
+                "trace": [ft[i, :sw[i]] for i in range(self.n)]}
+
+    def get_factors(self, i):
+        outs = [np.empty((s, self.ranks[i])) for s in self.dims[i]]
+        arr = (_dp * 3)(*[o.ctypes.data_as(_dp) for o in outs])
+        self._ck(lib().cpals_batch_get_factors(self.h, i, arr))
+        return outs
+
+    def stats(self):
+        a, b = C.c_int64(), C.c_int64()
+        self._ck(lib().cpals_batch_stats(self.h, C.byref(a), C.byref(b)))
+        return {"launches_per_sweep": a.value, "launches_last_run": b.value}

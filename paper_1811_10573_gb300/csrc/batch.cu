@@ -1,0 +1,1111 @@
+// Many small order-3 decompositions in one set of launches.
+//
+// A batch holds n independent order-3 problems of different sizes and ranks
+// (dims s0 x s1 x s2, rank R <= 64) and runs Algorithm 3 (PP-CP-ALS) on all
+// of them at once: every stage of a sweep -- a first-level contraction
+// (Sec. 2.5), a multi-TTV, the operator construction (Sec. 3.2.3), the PP
+// correction of Eq. 3, the factorisation of Gamma^(n), the row solves, the
+// Grams, the fitness (Sec. 5) and the decision of Algorithm 3 -- is one
+// launch over every instance (blockIdx.y = instance).  Each instance keeps
+// its own controller state on the device and takes part only in the stages
+// of the sweep kind it runs (ALS, PP initialisation = operator build + PP
+// sweep, PP approximated), so one captured graph is one sweep of the whole
+// batch, whatever kind each instance takes.  Contractions, operators and
+// corrections run in the batch's compute precision (float32 or float64);
+// the normal-equation work (Gamma, its Cholesky factor, the solves, the
+// Grams) and the fitness in float64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cpals.h"
+#include "internal.h"
+
+namespace {
+
+using cpals::Launch;
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+constexpr int kBR = 64;           // largest rank of a batch instance
+constexpr int kBT = 256;          // threads of the contraction and element kernels
+// Sweep kinds (as CPALS_SWEEP_*), the exact-fitness pass after the last
+// sweep, and a finished instance.
+enum Kind { K_ALS = 0, K_INIT = 1, K_PP = 2, K_EXACT = 3, K_DONE = -1 };
+
+// Per-instance layout: sizes and offsets into the batch's two arenas (T:
+// the compute precision; double: the float64 state).
+struct BI {
+  int s[3];
+  int R;
+  int splits;             // K splits of the MN-major ALS contraction
+  int pad;
+  int64_t x;              // X (s0 s1 s2)
+  int64_t ac[3], dac[3];  // compute copies of A, dA (s_n R)
+  int64_t ml, mr, krp, rhs, rhs2, part;
+  int64_t op01, op02, op12, mp[3];
+  int64_t a[3], ap[3], da[3];   // float64 factors (s_n R)
+  int64_t S, W;           // 3 R x R each (float64)
+  int64_t L, Z;           // R x R (float64)
+  int64_t rn;             // 2 smax row norms
+  int64_t sc;             // scalars: [0] fitness, [1] inner, [2] model, [3] ||X||^2,
+                          // [8 + 2n] ||dA^(n)||^2, [9 + 2n] ||A^(n)||^2
+};
+
+// Per-instance controller state of Algorithm 3 (device).
+struct BC {
+  int next;               // kind of the next sweep
+  int ran;                // kind of the sweep being run
+  int t;                  // sweeps done
+  int in_run;             // PP sweeps of the current PP run
+  int status;             // bit n: Gamma^(n) not positive definite; 1 << 8: non-finite
+  int pad;
+  double f_last, f_prev;
+};
+
+struct BParams {
+  const BI* bi;
+  BC* ctl;
+  double eps, tol;
+  int use_V, max_sweeps;
+  double* ftrace;         // n x max_sweeps
+  int* ktrace;
+};
+
+__device__ __forceinline__ bool runs_als(const BC& c) { return c.ran == K_ALS; }
+// the mode-2 right-hand side X_(01)^T (A^(0) (.) A^(1)): ALS sweeps and the exact fitness
+__device__ __forceinline__ bool runs_right(const BC& c) { return c.ran == K_ALS || c.ran == K_EXACT; }
+__device__ __forceinline__ bool runs_init(const BC& c) { return c.ran == K_INIT; }
+__device__ __forceinline__ bool runs_pp(const BC& c) { return c.ran == K_INIT || c.ran == K_PP; }
+
+// ---------------------------------------------------------------- contractions
+// Stage of a first-level contraction (Sec. 2.5, Sec. 3.2.3 level 2), all as
+// out[b][m][r] = sum_k X[b][k][m] B[k][r] (MN-major) or
+// out[m][r] = sum_k X[m][k] B[k][r] (K-major):
+//   CT_L   K-major, m = (x0 x1), k = x2, B = A^(2): M^(L) for ALS instances,
+//          M_p^(0,1) for instances building operators
+//   CT_R   MN-major, m = x2, k = (x0 x1), B = A^(0) (.) A^(1): the ALS
+//          right-hand side of mode 2, in K splits (partials)
+//   CT_12  MN-major, m = (x1 x2), k = x0, B = A^(0): M_p^(1,2)
+//   CT_02  batched MN-major, b = x0, k = x1, m = x2, B = A^(1): M_p^(0,2)
+enum CtStage { CT_L = 0, CT_R = 1, CT_12 = 2, CT_02 = 3 };
+
+template <typename T>
+struct CtShape {
+  bool act, kmajor;
+  int64_t batch, K, M, splits, kchunk;
+  const T* B;
+  T* out;
+};
+
+template <typename T>
+__device__ CtShape<T> ct_shape(int stage, const BI& b, const BC& c, T* tp) {
+  CtShape<T> sh;
+  const int64_t s0 = b.s[0], s1 = b.s[1], s2 = b.s[2];
+  sh.batch = 1;
+  sh.splits = 1;
+  sh.kmajor = false;
+  if (stage == CT_L) {
+    sh.act = runs_als(c) || runs_init(c);
+    sh.kmajor = true;
+    sh.M = s0 * s1;
+    sh.K = s2;
+    sh.B = tp + b.ac[2];
+    sh.out = tp + (runs_als(c) ? b.ml : b.op01);
+  } else if (stage == CT_R) {
+    sh.act = runs_right(c);
+    sh.M = s2;
+    sh.K = s0 * s1;
+    sh.B = tp + b.krp;
+    sh.out = tp + (b.splits > 1 ? b.part : b.mr);
+    sh.splits = b.splits;
+  } else if (stage == CT_12) {
+    sh.act = runs_init(c);
+    sh.M = s1 * s2;
+    sh.K = s0;
+    sh.B = tp + b.ac[0];
+    sh.out = tp + b.op12;
+  } else {
+    sh.act = runs_init(c);
+    sh.batch = s0;
+    sh.M = s2;
+    sh.K = s1;
+    sh.B = tp + b.ac[1];
+    sh.out = tp + b.op02;
+  }
+  sh.kchunk = cdiv(cdiv(sh.K, sh.splits), 16) * 16;
+  return sh;
+}
+
+// 64 x 64 output tiles (R <= 64), 256 threads, 4 x 4 outputs per thread; a
+// work unit is (batch entry, row tile, K split); CTAs past an instance's
+// units (or of an instance not in this stage) return at once.
+template <typename T>
+__global__ void __launch_bounds__(kBT) bgemm_kernel(BParams P, int stage, T* __restrict__ tp) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  const BI b = P.bi[blockIdx.y];
+  const BC c = P.ctl[blockIdx.y];
+  const CtShape<T> sh = ct_shape<T>(stage, b, c, tp);
+  if (!sh.act) return;
+  const int R = b.R;
+  const int64_t mtiles = cdiv(sh.M, BM);
+  const int64_t units = mtiles * sh.batch * sh.splits;
+  const int64_t u = blockIdx.x;
+  if (u >= units) return;
+  const int64_t mt = u % mtiles;
+  const int64_t rest = u / mtiles;
+  const int64_t z = rest % sh.splits;
+  const int64_t bb = rest / sh.splits;
+  const int64_t m0 = mt * BM;
+  const int64_t k0 = z * sh.kchunk, k1 = min(sh.K, k0 + sh.kchunk);
+  const T* X = tp + b.x + bb * sh.K * sh.M;
+  __shared__ T Xs[BK][BM + 1];
+  __shared__ T Bs[BK][BN];
+  const int tid = threadIdx.x, tn = tid % 16, tm = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = T(0);
+  for (int64_t kk = k0; kk < k1; kk += BK) {
+    for (int idx = tid; idx < BK * BM; idx += kBT) {
+      int k, m;
+      if (sh.kmajor) {
+        k = idx % BK;
+        m = idx / BK;
+      } else {
+        m = idx % BM;
+        k = idx / BM;
+      }
+      const int64_t gk = kk + k, gm = m0 + m;
+      T v = T(0);
+      if (gk < k1 && gm < sh.M) v = sh.kmajor ? X[gm * sh.K + gk] : X[gk * sh.M + gm];
+      Xs[k][m] = v;
+    }
+    for (int idx = tid; idx < BK * BN; idx += kBT) {
+      const int r = idx % BN, k = idx / BN;
+      const int64_t gk = kk + k;
+      Bs[k][r] = (gk < k1 && r < R) ? sh.B[gk * R + r] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; k++) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) av[i] = Xs[k][tm + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) bv[j] = Bs[k][tn + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  T* o = sh.out + (z * sh.batch + bb) * sh.M * R;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const int64_t m = m0 + tm + 16 * i;
+    if (m >= sh.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int r = tn + 16 * j;
+      if (r < R) o[m * R + r] = acc[i][j];
+    }
+  }
+}
+
+// M^(2) = sum of the K-split partials of CT_R in split order (ALS instances).
+template <typename T>
+__global__ void breduce_kernel(BParams P, T* __restrict__ tp) {
+  const BI b = P.bi[blockIdx.y];
+  if (!runs_right(P.ctl[blockIdx.y]) || b.splits <= 1) return;
+  const int64_t n = (int64_t)b.s[2] * b.R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T acc = T(0);
+    for (int z = 0; z < b.splits; z++) acc += tp[b.part + z * n + i];
+    tp[b.mr + i] = acc;
+  }
+}
+
+// Khatri-Rao product A^(0) (.) A^(1), row (x0 x1) = x0 s1 + x1 (ALS instances).
+template <typename T>
+__global__ void bkrp_kernel(BParams P, T* __restrict__ tp) {
+  const BI b = P.bi[blockIdx.y];
+  if (!runs_right(P.ctl[blockIdx.y])) return;
+  const int R = b.R;
+  const int64_t n = (int64_t)b.s[0] * b.s[1] * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i % R);
+    const int64_t row = i / R;
+    const int64_t x0 = row / b.s[1], x1 = row % b.s[1];
+    tp[b.krp + i] = tp[b.ac[0] + x0 * R + r] * tp[b.ac[1] + x1 * R + r];
+  }
+}
+
+// Multi-TTV (Sec. 2.5 lower level): out[o][q][r] = sum_x in[o][x][q][r] A[x][r].
+//   TT_ALS0  rhs = M^(L) contracted over x1 with A^(1) (mode 0, ALS)
+//   TT_ALS1  rhs = M^(L) contracted over x0 with A^(0) (mode 1, ALS)
+//   TT_MP    M_p^(0) = M_p^(0,1) over x1 with A^(1), M_p^(1) = M_p^(0,1)
+//            over x0 with A^(0), M_p^(2) = M_p^(0,2) over x0 with A^(0)
+//            (operator build; blockIdx.z picks the output)
+enum TtStage { TT_ALS0 = 0, TT_ALS1 = 1, TT_MP = 2 };
+
+template <typename T>
+__global__ void bttv_kernel(BParams P, int stage, T* __restrict__ tp) {
+  const BI b = P.bi[blockIdx.y];
+  const BC c = P.ctl[blockIdx.y];
+  const int R = b.R;
+  const int64_t s0 = b.s[0], s1 = b.s[1], s2 = b.s[2];
+  const T *in, *A;
+  T* out;
+  int64_t outer, inner;
+  int sw;
+  if (stage == TT_ALS0 || stage == TT_ALS1) {
+    if (!runs_als(c)) return;
+    in = tp + b.ml;
+    out = tp + b.rhs;
+    if (stage == TT_ALS0) {
+      A = tp + b.ac[1]; outer = s0; sw = (int)s1; inner = 1;
+    } else {
+      A = tp + b.ac[0]; outer = 1; sw = (int)s0; inner = s1;
+    }
+  } else {
+    if (!runs_init(c)) return;
+    const int w = blockIdx.z;
+    if (w == 0) {
+      in = tp + b.op01; A = tp + b.ac[1]; out = tp + b.mp[0]; outer = s0; sw = (int)s1; inner = 1;
+    } else if (w == 1) {
+      in = tp + b.op01; A = tp + b.ac[0]; out = tp + b.mp[1]; outer = 1; sw = (int)s0; inner = s1;
+    } else {
+      in = tp + b.op02; A = tp + b.ac[0]; out = tp + b.mp[2]; outer = 1; sw = (int)s0; inner = s2;
+    }
+  }
+  const int64_t n = outer * inner * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i % R);
+    const int64_t q = (i / R) % inner, o = i / (R * inner);
+    const T* src = in + (o * sw * inner + q) * R + r;
+    T acc = T(0);
+    for (int x = 0; x < sw; x++) acc = fma(src[(int64_t)x * inner * R], A[(int64_t)x * R + r], acc);
+    out[i] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- normal equations (float64)
+// Stage selector of the per-mode kernels: the ALS sweep's update of mode n,
+// or the PP sweep's (instances in PP initialisation or approximated sweeps).
+// NE_INIT: the Grams and norms of the initial factors (Algorithm 3 starts
+// with S^(n) = A^(n)T A^(n) and dA^(n) = A^(n)), for every instance.
+enum NeStage { NE_ALS = 0, NE_PP = 1, NE_INIT = 2 };
+
+__device__ __forceinline__ bool ne_active(int stage, const BC& c) {
+  if (stage == NE_INIT) return c.ran != K_DONE;
+  return stage == NE_ALS ? runs_als(c) : runs_pp(c);
+}
+
+// Gamma^(n) = S^(a) * S^(b) (the other two modes' Grams, Algorithm 1), its
+// Cholesky factor L (right-looking, in shared memory), and for PP sweeps with
+// the second-order terms Z = W^(a) * W^(b) (Eq. 3 for order 3: the one pair
+// {a, b}, W^(i) = A^(i)T dA^(i)), so that V^(n,a,b) = A^(n) Z.  One CTA per
+// instance; a non-positive pivot sets bit n of the instance's status.
+__global__ void __launch_bounds__(128) bchol_kernel(BParams P, int stage, int n, double* __restrict__ dp) {
+  BC& cc = P.ctl[blockIdx.y];
+  const BI b = P.bi[blockIdx.y];
+  if (!ne_active(stage, cc)) return;
+  const int R = b.R, RS = kBR + 1;
+  const int a0 = n == 0 ? 1 : 0, a1 = n == 2 ? 1 : 2;
+  const double* S = dp + b.S;
+  const double* W = dp + b.W;
+  __shared__ double G[kBR * (kBR + 1)];
+  __shared__ double il_sh;
+  __shared__ int bad;
+  const bool v = stage == NE_PP && P.use_V;
+  for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
+    const int i = idx / R, j = idx % R;
+    G[i * RS + j] = S[a0 * R * R + idx] * S[a1 * R * R + idx];
+    if (v) dp[b.Z + idx] = W[a0 * R * R + idx] * W[a1 * R * R + idx];
+  }
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < R; k++) {
+    if (threadIdx.x == 0) {
+      const double piv = G[k * RS + k];
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        bad = 1;
+      } else {
+        const double il = rsqrt(piv);
+        il_sh = il;
+        G[k * RS + k] = piv * il;
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double il = il_sh;
+    for (int i = k + 1 + threadIdx.x; i < R; i += blockDim.x) G[i * RS + k] *= il;
+    __syncthreads();
+    const int m = R - k - 1;                       // trailing rows k+1 .. R-1, lower triangle
+    for (int e = threadIdx.x; e < m * (m + 1) / 2; e += blockDim.x) {
+      int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+      while ((i + 1) * (i + 2) / 2 <= e) i++;
+      while (i * (i + 1) / 2 > e) i--;
+      const int j = e - i * (i + 1) / 2;            // 0 <= j <= i < m
+      const int gi = k + 1 + i, gj = k + 1 + j;
+      G[gi * RS + gj] = fma(-G[gi * RS + k], G[gj * RS + k], G[gi * RS + gj]);
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) atomicOr(&cc.status, 1 << n);
+    return;
+  }
+  for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
+    const int i = idx / R, j = idx % R;
+    dp[b.L + idx] = j <= i ? G[i * RS + j] : 0.0;
+  }
+}
+
+// Row solves of mode n: a Gamma = rhs (+ A_old Z for the PP second-order
+// terms) through L (forward then back substitution, one warp per row), the
+// new factor, dA^(n) = A_new - A_old (ALS) or A_new - A_p (PP), the compute
+// copies and the per-row ||dA||^2, ||A_new||^2.  The PP sweep's last mode
+// also keeps its full right-hand side (rhs2) for the fitness estimate.  A
+// mode whose factorisation failed keeps its factor.
+template <typename T>
+__global__ void __launch_bounds__(128) bsolve_kernel(BParams P, int stage, int n, T* __restrict__ tp,
+                                                     double* __restrict__ dp) {
+  const BI b = P.bi[blockIdx.y];
+  const BC c = P.ctl[blockIdx.y];
+  if (!ne_active(stage, c)) return;
+  const int R = b.R, s = b.s[n], RS = kBR + 1;
+  const bool failed = (c.status >> n) & 1;
+  const bool v = stage == NE_PP && P.use_V;
+  __shared__ double Ls[kBR * (kBR + 1)];
+  __shared__ double inv[kBR];
+  const double* Zs = dp + b.Z;                  // R x R, read through L1
+  if (!failed) {
+    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) Ls[(idx / R) * RS + idx % R] = dp[b.L + idx];
+    __syncthreads();
+    for (int i = threadIdx.x; i < R; i += blockDim.x) inv[i] = 1.0 / Ls[i * RS + i];
+    __syncthreads();
+  }
+  const T* rhs = tp + (stage == NE_ALS && n == 2 ? b.mr : b.rhs);
+  double* A = dp + b.a[n];
+  const double* ref = dp + (stage == NE_ALS ? b.a[n] : b.ap[n]);
+  double* dA = dp + b.da[n];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int y = blockIdx.x * 4 + warp; y < s; y += gridDim.x * 4) {
+    double bv[2], old[2];
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+      const int r = lane + 32 * q;
+      old[q] = r < R ? A[(int64_t)y * R + r] : 0.0;
+      bv[q] = r < R ? (double)rhs[(int64_t)y * R + r] : 0.0;
+    }
+    if (v && !failed) {
+      // second-order terms: b += A_old Z (A_old the factor before this update)
+#pragma unroll
+      for (int q = 0; q < 2; q++) {
+        const int r = lane + 32 * q;
+        double acc = bv[q];
+        for (int k = 0; k < R; k++) {
+          const double ak = __shfl_sync(0xffffffffu, old[k >> 5], k & 31);
+          if (r < R) acc = fma(ak, Zs[k * R + r], acc);
+        }
+        bv[q] = acc;
+      }
+      if (n == 2)
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+          const int r = lane + 32 * q;
+          if (r < R) tp[b.rhs2 + (int64_t)y * R + r] = (T)bv[q];
+        }
+    }
+    if (failed) {
+      bv[0] = old[0];
+      bv[1] = old[1];
+    } else {
+      for (int i = 0; i < R; i++) {             // L z = b
+        const double zi = __shfl_sync(0xffffffffu, bv[i >> 5], i & 31) * inv[i];
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+          const int r = lane + 32 * q;
+          if (r == i) bv[q] = zi;
+          else if (r > i && r < R) bv[q] = fma(-Ls[r * RS + i], zi, bv[q]);
+        }
+      }
+      for (int i = R - 1; i >= 0; i--) {        // L^T a = z
+        const double ai = __shfl_sync(0xffffffffu, bv[i >> 5], i & 31) * inv[i];
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+          const int r = lane + 32 * q;
+          if (r == i) bv[q] = ai;
+          else if (r < i) bv[q] = fma(-Ls[i * RS + r], ai, bv[q]);
+        }
+      }
+    }
+    double nd = 0.0, na = 0.0;
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+      const int r = lane + 32 * q;
+      if (r < R) {
+        const int64_t o = (int64_t)y * R + r;
+        const double d = failed ? dA[o] : bv[q] - (stage == NE_ALS ? old[q] : ref[o]);
+        A[o] = bv[q];
+        dA[o] = d;
+        tp[b.ac[n] + o] = (T)bv[q];
+        tp[b.dac[n] + o] = (T)d;
+        nd = fma(d, d, nd);
+        na = fma(bv[q], bv[q], na);
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      nd += __shfl_xor_sync(0xffffffffu, nd, off);
+      na += __shfl_xor_sync(0xffffffffu, na, off);
+    }
+    if (lane == 0) {
+      dp[b.rn + 2 * y] = nd;
+      dp[b.rn + 2 * y + 1] = na;
+    }
+  }
+}
+
+// Grams of mode n after its update: S^(n) = A^T A (both triangles) and, in
+// PP sweeps, W^(n) = A^T dA, each entry one float64 dot product over the
+// rows (kGramCtas CTAs per instance split the entries); CTA 0 also sums the
+// row norms into ||dA^(n)||^2 and ||A^(n)||^2.
+constexpr int kGramCtas = 8;
+
+__global__ void __launch_bounds__(256) bgram_kernel(BParams P, int stage, int n, double* __restrict__ dp) {
+  const BI b = P.bi[blockIdx.y];
+  const BC c = P.ctl[blockIdx.y];
+  if (!ne_active(stage, c)) return;
+  const int R = b.R, s = b.s[n];
+  const double* A = dp + b.a[n];
+  const double* dA = dp + b.da[n];
+  const int nS = R * (R + 1) / 2;
+  const int nW = stage == NE_PP ? R * R : 0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nS + nW; e += gridDim.x * blockDim.x) {
+    if (e < nS) {
+      int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+      while ((i + 1) * (i + 2) / 2 <= e) i++;
+      while (i * (i + 1) / 2 > e) i--;
+      const int j = e - i * (i + 1) / 2;        // j <= i
+      double acc = 0.0;
+      for (int y = 0; y < s; y++) acc = fma(A[(int64_t)y * R + i], A[(int64_t)y * R + j], acc);
+      dp[b.S + (int64_t)n * R * R + i * R + j] = acc;
+      dp[b.S + (int64_t)n * R * R + j * R + i] = acc;
+    } else {
+      const int f = e - nS, i = f / R, j = f % R;
+      double acc = 0.0;
+      for (int y = 0; y < s; y++) acc = fma(A[(int64_t)y * R + i], dA[(int64_t)y * R + j], acc);
+      dp[b.W + (int64_t)n * R * R + f] = acc;
+    }
+  }
+  if (blockIdx.x != 0) return;
+  __shared__ double rd[256], ra[256];
+  double x = 0.0, z = 0.0;
+  if (stage == NE_INIT) {
+    for (int64_t e = threadIdx.x; e < (int64_t)s * R; e += blockDim.x) z = fma(A[e], A[e], z);
+    x = z;
+  } else {
+    for (int y = threadIdx.x; y < s; y += blockDim.x) {
+      x += dp[b.rn + 2 * y];
+      z += dp[b.rn + 2 * y + 1];
+    }
+  }
+  rd[threadIdx.x] = x;
+  ra[threadIdx.x] = z;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      rd[threadIdx.x] += rd[threadIdx.x + st];
+      ra[threadIdx.x] += ra[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    dp[b.sc + 8 + 2 * n] = rd[0];
+    dp[b.sc + 9 + 2 * n] = ra[0];
+  }
+}
+
+// ---------------------------------------------------------------- PP sweep, fitness, controller
+// Eq. 3 first-order terms of mode n: rhs[y][r] = M_p^(n)[y][r] +
+// sum_{i != n} sum_x M_p^(i,n)(x, y, r) dA^(i)[x][r] with the operators
+// M_p^(0,1)[x0][x1][r], M_p^(0,2)[x0][x2][r], M_p^(1,2)[x1][x2][r].
+template <typename T>
+__global__ void bppcorr_kernel(BParams P, int n, T* __restrict__ tp) {
+  const BI b = P.bi[blockIdx.y];
+  if (!runs_pp(P.ctl[blockIdx.y])) return;
+  const int R = b.R;
+  const int64_t s0 = b.s[0], s1 = b.s[1], s2 = b.s[2];
+  // two terms: operator base for row y = base + y * ystride, x stride, extent, dA
+  int64_t base[2], ys[2], xs[2];
+  int sx[2];
+  const T* dA[2];
+  if (n == 0) {
+    base[0] = b.op01; ys[0] = s1 * R; xs[0] = R; sx[0] = (int)s1; dA[0] = tp + b.dac[1];
+    base[1] = b.op02; ys[1] = s2 * R; xs[1] = R; sx[1] = (int)s2; dA[1] = tp + b.dac[2];
+  } else if (n == 1) {
+    base[0] = b.op01; ys[0] = R; xs[0] = s1 * R; sx[0] = (int)s0; dA[0] = tp + b.dac[0];
+    base[1] = b.op12; ys[1] = s2 * R; xs[1] = R; sx[1] = (int)s2; dA[1] = tp + b.dac[2];
+  } else {
+    base[0] = b.op02; ys[0] = R; xs[0] = s2 * R; sx[0] = (int)s0; dA[0] = tp + b.dac[0];
+    base[1] = b.op12; ys[1] = R; xs[1] = s2 * R; sx[1] = (int)s1; dA[1] = tp + b.dac[1];
+  }
+  const int64_t tot = (int64_t)b.s[n] * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = i / R;
+    const int r = (int)(i % R);
+    T acc = tp[b.mp[n] + i];
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+      const T* op = tp + base[q] + y * ys[q] + r;
+      for (int x = 0; x < sx[q]; x++) acc = fma(op[(int64_t)x * xs[q]], dA[q][(int64_t)x * R + r], acc);
+    }
+    tp[b.rhs + i] = acc;
+  }
+}
+
+// The PP initialisation of Algorithm 3 after the operator build: A_p <- A,
+// dA <- 0 (float64 and compute copies), W <- 0, ||dA||^2 <- 0.
+template <typename T>
+__global__ void bprep_kernel(BParams P, T* __restrict__ tp, double* __restrict__ dp) {
+  const BI b = P.bi[blockIdx.y];
+  if (!runs_init(P.ctl[blockIdx.y])) return;
+  const int R = b.R;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  for (int n = 0; n < 3; n++)
+    for (int64_t i = g; i < (int64_t)b.s[n] * R; i += st) {
+      dp[b.ap[n] + i] = dp[b.a[n] + i];
+      dp[b.da[n] + i] = 0.0;
+      tp[b.dac[n] + i] = T(0);
+    }
+  for (int64_t i = g; i < 3 * (int64_t)R * R; i += st) dp[b.W + i] = 0.0;
+  if (g < 3) dp[b.sc + 8 + 2 * g] = 0.0;
+}
+
+// Fitness (Sec. 5): 1 - sqrt(||X||^2 - 2 <X, [[A]]> + ||[[A]]||^2) / ||X||, the
+// inner product from the last mode's right-hand side and new factor: exact
+// after ALS sweeps and in the exact pass (M^(2) = X_(01)^T (A^(0) (.) A^(1))),
+// the estimate from M~^(2) after PP sweeps (with the second-order terms when
+// they are on).  One CTA per instance, float64 sums.
+template <typename T>
+__global__ void __launch_bounds__(256) bfit_kernel(BParams P, T* __restrict__ tp, double* __restrict__ dp) {
+  const BI b = P.bi[blockIdx.y];
+  const BC c = P.ctl[blockIdx.y];
+  if (c.ran == K_DONE) return;
+  const int R = b.R;
+  const T* rhs = tp + (runs_right(c) ? b.mr : (P.use_V ? b.rhs2 : b.rhs));
+  const double* A2 = dp + b.a[2];
+  const double* S = dp + b.S;
+  double inner = 0.0, model = 0.0;
+  for (int64_t i = threadIdx.x; i < (int64_t)b.s[2] * R; i += blockDim.x)
+    inner = fma((double)rhs[i], A2[i], inner);
+  for (int i = threadIdx.x; i < R * R; i += blockDim.x) model += S[i] * S[R * R + i] * S[2 * R * R + i];
+  __shared__ double ri[256], rm[256];
+  ri[threadIdx.x] = inner;
+  rm[threadIdx.x] = model;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      ri[threadIdx.x] += ri[threadIdx.x + st];
+      rm[threadIdx.x] += rm[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double nx2 = dp[b.sc + 3];
+    const double res2 = nx2 - 2.0 * ri[0] + rm[0];
+    dp[b.sc + 0] = 1.0 - sqrt(fmax(res2, 0.0)) / sqrt(nx2);
+    dp[b.sc + 1] = ri[0];
+    dp[b.sc + 2] = rm[0];
+  }
+}
+
+__device__ bool b_all_small(const BParams& P, const BI& b, const double* dp) {
+  if (!(P.eps > 0.0)) return false;
+  for (int n = 0; n < 3; n++)
+    if (!(sqrt(dp[b.sc + 8 + 2 * n]) < P.eps * sqrt(dp[b.sc + 9 + 2 * n]))) return false;
+  return true;
+}
+
+// Algorithm 3's decision per instance after a sweep (one thread each): the
+// sweep is recorded (kind, the fitness it reports), then the next kind is
+// taken as the host loop of cpals_run does -- after an ALS sweep a PP
+// initialisation iff every ||dA^(i)|| < eps ||A^(i)||; inside a PP run
+// another PP sweep iff that still holds and, with a stopping tolerance, the
+// last PP sweep of the run (from its second on) raised the estimate by at
+// least tol; else an ALS sweep.  A non-finite value or a failed
+// factorisation ends the instance; so does its sweep budget.
+// first != 0: the decision before the first sweep (dA = A).
+__global__ void bdecide_kernel(BParams P, int n_inst, int first, double* __restrict__ dp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_inst) return;
+  BC& c = P.ctl[i];
+  const BI b = P.bi[i];
+  if (first) {
+    c.t = 0;
+    c.in_run = 0;
+    c.status = 0;
+    c.f_last = c.f_prev = -1e300;
+    c.ran = c.next = P.max_sweeps > 0 ? (b_all_small(P, b, dp) ? K_INIT : K_ALS) : K_DONE;
+    return;
+  }
+  if (c.ran == K_DONE || c.ran == K_EXACT) return;
+  const double f = dp[b.sc + 0];
+  const int t = c.t;
+  P.ftrace[(int64_t)i * P.max_sweeps + t] = f;
+  P.ktrace[(int64_t)i * P.max_sweeps + t] = c.ran;
+  c.t = t + 1;
+  c.f_prev = c.f_last;
+  c.f_last = f;
+  c.in_run = c.ran == K_ALS ? 0 : (c.ran == K_INIT ? 1 : c.in_run + 1);
+  bool finite = isfinite(f);
+  for (int n = 0; n < 3; n++) finite = finite && isfinite(dp[b.sc + 8 + 2 * n]) && isfinite(dp[b.sc + 9 + 2 * n]);
+  if (!finite) c.status |= 1 << 8;
+  if (c.status || c.t >= P.max_sweeps) {
+    c.ran = c.next = K_DONE;
+    return;
+  }
+  const bool small = b_all_small(P, b, dp);
+  const bool gain = !(P.tol > 0.0) || c.in_run < 2 || c.f_last - c.f_prev >= P.tol;
+  c.next = c.ran != K_ALS ? ((small && gain) ? K_PP : K_ALS) : (small ? K_INIT : K_ALS);
+  c.ran = c.next;
+}
+
+// The exact pass after the last sweep: every instance that ran takes the
+// exact fitness of its final factors (stage flag K_EXACT), then ends.
+__global__ void bexact_kernel(BParams P, int n_inst, int begin) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_inst) return;
+  BC& c = P.ctl[i];
+  if (begin) c.ran = c.t > 0 ? K_EXACT : K_DONE;
+  else c.ran = K_DONE;
+}
+
+// Compute copies and dA of the initial factors: Ac = dAc = A, dA = A, W = 0.
+template <typename T>
+__global__ void binit_kernel(BParams P, T* __restrict__ tp, double* __restrict__ dp) {
+  const BI b = P.bi[blockIdx.y];
+  const int R = b.R;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  for (int n = 0; n < 3; n++)
+    for (int64_t i = g; i < (int64_t)b.s[n] * R; i += st) {
+      const double a = dp[b.a[n] + i];
+      dp[b.da[n] + i] = a;
+      tp[b.ac[n] + i] = (T)a;
+      tp[b.dac[n] + i] = (T)a;
+    }
+  for (int64_t i = g; i < 3 * (int64_t)R * R; i += st) dp[b.W + i] = 0.0;
+}
+
+// ||X||^2 of instance i in float64 (one CTA, fixed order).
+template <typename T>
+__global__ void __launch_bounds__(256) bnormx_kernel(const T* __restrict__ X, int64_t n, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc = fma((double)X[i], (double)X[i], acc);
+  __shared__ double r[256];
+  r[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) r[threadIdx.x] += r[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = r[0];
+}
+
+template <typename TS, typename TD>
+__global__ void bconvert_kernel(const TS* __restrict__ s, TD* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = (TD)s[i];
+}
+
+}  // namespace
+
+// ====================================================================== host side
+struct cpals_batch {
+  int n = 0, prec = 0;
+  size_t esz = 4;
+  std::vector<BI> bi;
+  BI* d_bi = nullptr;
+  BC* d_ctl = nullptr;
+  void* tp = nullptr;
+  double* dp = nullptr;
+  int64_t tp_elems = 0, dp_elems = 0;
+  std::vector<char> have_x, have_a;
+  cudaStream_t stream = nullptr;
+  double* d_ftrace = nullptr;
+  int* d_ktrace = nullptr;
+  int64_t trace_cap = 0;
+  // grid extents (largest over the instances)
+  int64_t u_l = 1, u_r = 1, u_12 = 1, u_02 = 1, smax = 1, el_max = 1;
+  int64_t launches_sweep = 0, launches_run = 0;
+  std::string err;
+  cpals_status fail(cpals_status st, const std::string& m) {
+    err = m;
+    return st;
+  }
+  cpals_status cuda_fail(const char* what, cudaError_t e) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return CPALS_E_CUDA;
+  }
+};
+
+#define BCK(call)                                           \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return b->cuda_fail(#call, e_);  \
+  } while (0)
+
+namespace {
+
+int el_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, kBT), 64)); }
+
+// Launch every stage of one sweep of the whole batch (captured into a graph).
+template <typename T>
+int64_t sweep_launches(cpals_batch* b, const BParams& P) {
+  T* tp = static_cast<T*>(b->tp);
+  double* dp = b->dp;
+  cudaStream_t s = b->stream;
+  const unsigned N = (unsigned)b->n;
+  int64_t k = 0;
+  auto gemm = [&](int stage, int64_t units) {
+    bgemm_kernel<T><<<dim3((unsigned)units, N), kBT, 0, s>>>(P, stage, tp);
+    k++;
+  };
+  const dim3 gsolve((unsigned)cdiv(b->smax, 4), N), gel((unsigned)el_grid(b->el_max), N);
+  auto mode = [&](int stage, int n) {
+    bchol_kernel<<<dim3(1, N), 128, 0, s>>>(P, stage, n, dp);
+    bsolve_kernel<T><<<gsolve, 128, 0, s>>>(P, stage, n, tp, dp);
+    bgram_kernel<<<dim3(kGramCtas, N), 256, 0, s>>>(P, stage, n, dp);
+    k += 3;
+  };
+  // ALS sweep (Algorithm 1; binary dimension tree, Sec. 2.5); M^(L) doubles
+  // as M_p^(0,1) for the instances that build operators
+  gemm(CT_L, b->u_l);
+  bttv_kernel<T><<<gel, kBT, 0, s>>>(P, TT_ALS0, tp);
+  k++;
+  mode(NE_ALS, 0);
+  bttv_kernel<T><<<gel, kBT, 0, s>>>(P, TT_ALS1, tp);
+  k++;
+  mode(NE_ALS, 1);
+  bkrp_kernel<T><<<gel, kBT, 0, s>>>(P, tp);
+  gemm(CT_R, b->u_r);
+  breduce_kernel<T><<<gel, kBT, 0, s>>>(P, tp);
+  k += 2;
+  mode(NE_ALS, 2);
+  // operator build (Sec. 3.2.3) and the PP initialisation of Algorithm 3
+  gemm(CT_12, b->u_12);
+  gemm(CT_02, b->u_02);
+  bttv_kernel<T><<<dim3(gel.x, N, 3), kBT, 0, s>>>(P, TT_MP, tp);
+  bprep_kernel<T><<<gel, kBT, 0, s>>>(P, tp, dp);
+  k += 2;
+  // PP sweep (Eq. 3)
+  for (int n = 0; n < 3; n++) {
+    bppcorr_kernel<T><<<gel, kBT, 0, s>>>(P, n, tp);
+    k++;
+    mode(NE_PP, n);
+  }
+  bfit_kernel<T><<<dim3(1, N), 256, 0, s>>>(P, tp, dp);
+  bdecide_kernel<<<(unsigned)cdiv(b->n, 128), 128, 0, s>>>(P, b->n, 0, dp);
+  return k + 2;
+}
+
+// The exact fitness of every instance's final factors.
+template <typename T>
+int64_t exact_launches(cpals_batch* b, const BParams& P) {
+  T* tp = static_cast<T*>(b->tp);
+  cudaStream_t s = b->stream;
+  const unsigned N = (unsigned)b->n;
+  const dim3 gel((unsigned)el_grid(b->el_max), N);
+  bexact_kernel<<<(unsigned)cdiv(b->n, 128), 128, 0, s>>>(P, b->n, 1);
+  bkrp_kernel<T><<<gel, kBT, 0, s>>>(P, tp);
+  bgemm_kernel<T><<<dim3((unsigned)b->u_r, N), kBT, 0, s>>>(P, CT_R, tp);
+  breduce_kernel<T><<<gel, kBT, 0, s>>>(P, tp);
+  bfit_kernel<T><<<dim3(1, N), 256, 0, s>>>(P, tp, b->dp);
+  bexact_kernel<<<(unsigned)cdiv(b->n, 128), 128, 0, s>>>(P, b->n, 0);
+  return 6;
+}
+
+template <typename T>
+cpals_status run_impl(cpals_batch* b, int max_sweeps, double eps, int use_V, double tol) {
+  T* tp = static_cast<T*>(b->tp);
+  double* dp = b->dp;
+  cudaStream_t s = b->stream;
+  const unsigned N = (unsigned)b->n;
+  BParams P;
+  P.bi = b->d_bi;
+  P.ctl = b->d_ctl;
+  P.eps = eps;
+  P.tol = tol;
+  P.use_V = use_V;
+  P.max_sweeps = max_sweeps;
+  P.ftrace = b->d_ftrace;
+  P.ktrace = b->d_ktrace;
+  // Algorithm 3's start: dA <- A, S <- A^T A, the first decision
+  BCK(cudaMemsetAsync(b->d_ctl, 0, sizeof(BC) * b->n, s));
+  binit_kernel<T><<<dim3((unsigned)el_grid(b->el_max), N), kBT, 0, s>>>(P, tp, dp);
+  for (int n = 0; n < 3; n++) bgram_kernel<<<dim3(kGramCtas, N), 256, 0, s>>>(P, NE_INIT, n, dp);
+  bdecide_kernel<<<(unsigned)cdiv(b->n, 128), 128, 0, s>>>(P, b->n, 1, dp);
+  BCK(cudaGetLastError());
+  int64_t launches = 5;
+  // one captured graph is one sweep of every instance
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr, exx = nullptr;
+  BCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  const int64_t per = sweep_launches<T>(b, P);
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess) return b->cuda_fail("capture (batch sweep)", e);
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return b->cuda_fail("instantiate (batch sweep)", e);
+  BCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  const int64_t nex = exact_launches<T>(b, P);
+  e = cudaStreamEndCapture(s, &g);
+  if (e == cudaSuccess) {
+    e = cudaGraphInstantiate(&exx, g, 0);
+    cudaGraphDestroy(g);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphExecDestroy(ex);
+    return b->cuda_fail("capture (batch exact fitness)", e);
+  }
+  for (int t = 0; t < max_sweeps && e == cudaSuccess; t++) e = cudaGraphLaunch(ex, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exx, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaGraphExecDestroy(ex);
+  cudaGraphExecDestroy(exx);
+  if (e != cudaSuccess) return b->cuda_fail("batch run", e);
+  b->launches_sweep = per;
+  b->launches_run = launches + per * max_sweeps + nex;
+  return CPALS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cpals_status cpals_batch_create(int n, const int64_t* dims, const int* ranks, int precision,
+                                cpals_batch** out) {
+  if (!out) return CPALS_E_INVALID;
+  *out = nullptr;
+  if (n < 1 || n > 65535 || !dims || !ranks) return CPALS_E_INVALID;
+  if (precision != CPALS_FP64 && precision != CPALS_FP32) return CPALS_E_UNSUPPORTED;
+  for (int i = 0; i < n; i++) {
+    if (ranks[i] < 1 || ranks[i] > kBR) return CPALS_E_INVALID;
+    for (int k = 0; k < 3; k++)
+      if (dims[3 * i + k] < 1 || dims[3 * i + k] > 4096) return CPALS_E_INVALID;
+  }
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return CPALS_E_CUDA;
+  }
+  if (!(prop.major == 10 && prop.minor == 3)) return CPALS_E_UNSUPPORTED;
+  cpals_batch* b = new cpals_batch();
+  b->n = n;
+  b->prec = precision;
+  b->esz = precision == CPALS_FP64 ? 8 : 4;
+  b->bi.resize(n);
+  b->have_x.assign(n, 0);
+  b->have_a.assign(n, 0);
+  int64_t to = 0, d = 0;
+  for (int i = 0; i < n; i++) {
+    BI& q = b->bi[i];
+    memset(&q, 0, sizeof(q));
+    const int64_t s0 = dims[3 * i], s1 = dims[3 * i + 1], s2 = dims[3 * i + 2];
+    const int R = ranks[i];
+    q.s[0] = (int)s0;
+    q.s[1] = (int)s1;
+    q.s[2] = (int)s2;
+    q.R = R;
+    const int64_t K = s0 * s1;
+    q.splits = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(K, 1024), 64));
+    const int64_t sm = std::max(s0, std::max(s1, s2));
+    auto t = [&](int64_t e) { const int64_t o = to; to += (e + 1) / 2 * 2; return o; };
+    q.x = t(s0 * s1 * s2);
+    for (int k = 0; k < 3; k++) q.ac[k] = t(dims[3 * i + k] * R);
+    for (int k = 0; k < 3; k++) q.dac[k] = t(dims[3 * i + k] * R);
+    q.ml = t(K * R);
+    q.mr = t(s2 * R);
+    q.krp = t(K * R);
+    q.rhs = t(sm * R);
+    q.rhs2 = t(sm * R);
+    q.part = t((int64_t)q.splits * s2 * R);
+    q.op01 = t(s0 * s1 * R);
+    q.op02 = t(s0 * s2 * R);
+    q.op12 = t(s1 * s2 * R);
+    for (int k = 0; k < 3; k++) q.mp[k] = t(dims[3 * i + k] * R);
+    auto dd = [&](int64_t e) { const int64_t o = d; d += e; return o; };
+    for (int k = 0; k < 3; k++) q.a[k] = dd(dims[3 * i + k] * R);
+    for (int k = 0; k < 3; k++) q.ap[k] = dd(dims[3 * i + k] * R);
+    for (int k = 0; k < 3; k++) q.da[k] = dd(dims[3 * i + k] * R);
+    q.S = dd(3 * (int64_t)R * R);
+    q.W = dd(3 * (int64_t)R * R);
+    q.L = dd((int64_t)R * R);
+    q.Z = dd((int64_t)R * R);
+    q.rn = dd(2 * sm);
+    q.sc = dd(16);
+    b->u_l = std::max(b->u_l, cdiv(K, 64));
+    b->u_r = std::max(b->u_r, cdiv(s2, 64) * q.splits);
+    b->u_12 = std::max(b->u_12, cdiv(s1 * s2, 64));
+    b->u_02 = std::max(b->u_02, cdiv(s2, 64) * s0);
+    b->smax = std::max(b->smax, sm);
+    b->el_max = std::max(b->el_max, K * R);
+  }
+  b->tp_elems = to;
+  b->dp_elems = d;
+  auto bail = [&](cpals_status st) {
+    cpals_batch_destroy(b);
+    return st;
+  };
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(CPALS_E_CUDA);
+  if (cudaMalloc(&b->tp, (size_t)to * b->esz) != cudaSuccess ||
+      cudaMalloc((void**)&b->dp, (size_t)d * 8) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_bi, sizeof(BI) * n) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_ctl, sizeof(BC) * n) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(CPALS_E_OOM);
+  }
+  if (cudaMemcpy(b->d_bi, b->bi.data(), sizeof(BI) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(b->dp, 0, (size_t)d * 8) != cudaSuccess ||
+      cudaMemset(b->tp, 0, (size_t)to * b->esz) != cudaSuccess ||
+      cudaMemset(b->d_ctl, 0, sizeof(BC) * n) != cudaSuccess)
+    return bail(CPALS_E_CUDA);
+  *out = b;
+  return CPALS_OK;
+}
+
+void cpals_batch_destroy(cpals_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->tp) cudaFree(b->tp);
+  if (b->dp) cudaFree(b->dp);
+  if (b->d_bi) cudaFree(b->d_bi);
+  if (b->d_ctl) cudaFree(b->d_ctl);
+  if (b->d_ftrace) cudaFree(b->d_ftrace);
+  if (b->d_ktrace) cudaFree(b->d_ktrace);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+const char* cpals_batch_last_error(const cpals_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+cpals_status cpals_batch_set_tensor(cpals_batch* b, int i, const void* data, int dtype, int on_device) {
+  if (!b) return CPALS_E_INVALID;
+  if (i < 0 || i >= b->n || !data || (dtype != 0 && dtype != 1))
+    return b->fail(CPALS_E_INVALID, "bad tensor argument");
+  const BI& q = b->bi[i];
+  const int64_t n = (int64_t)q.s[0] * q.s[1] * q.s[2];
+  const size_t insz = dtype == 0 ? 8 : 4;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  char* dst = static_cast<char*>(b->tp) + (size_t)q.x * b->esz;
+  if (insz == b->esz) {
+    BCK(cudaMemcpyAsync(dst, data, n * insz, kind, b->stream));
+  } else {
+    // widen or narrow on the device through a temporary copy
+    void* tmp = nullptr;
+    if (cudaMalloc(&tmp, n * insz) != cudaSuccess) {
+      cudaGetLastError();
+      return b->fail(CPALS_E_OOM, "temporary tensor copy");
+    }
+    cudaError_t e = cudaMemcpyAsync(tmp, data, n * insz, kind, b->stream);
+    if (e == cudaSuccess) {
+      const int g = (int)std::min<int64_t>(cdiv(n, 256), 4096);
+      if (dtype == 0) bconvert_kernel<double, float><<<g, 256, 0, b->stream>>>((const double*)tmp, (float*)dst, n);
+      else bconvert_kernel<float, double><<<g, 256, 0, b->stream>>>((const float*)tmp, (double*)dst, n);
+      e = cudaStreamSynchronize(b->stream);
+    }
+    cudaFree(tmp);
+    if (e != cudaSuccess) return b->cuda_fail("batch set_tensor", e);
+  }
+  if (b->esz == 8) bnormx_kernel<double><<<1, 256, 0, b->stream>>>((const double*)dst, n, b->dp + q.sc + 3);
+  else bnormx_kernel<float><<<1, 256, 0, b->stream>>>((const float*)dst, n, b->dp + q.sc + 3);
+  BCK(cudaGetLastError());
+  BCK(cudaStreamSynchronize(b->stream));
+  b->have_x[i] = 1;
+  return CPALS_OK;
+}
+
+cpals_status cpals_batch_init_factors(cpals_batch* b, int i, const double* const* factors) {
+  if (!b) return CPALS_E_INVALID;
+  if (i < 0 || i >= b->n || !factors) return b->fail(CPALS_E_INVALID, "bad factor argument");
+  const BI& q = b->bi[i];
+  for (int n = 0; n < 3; n++) {
+    if (!factors[n]) return b->fail(CPALS_E_INVALID, "factor pointer is NULL");
+    BCK(cudaMemcpyAsync(b->dp + q.a[n], factors[n], (size_t)q.s[n] * q.R * 8, cudaMemcpyHostToDevice,
+                        b->stream));
+  }
+  BCK(cudaStreamSynchronize(b->stream));
+  b->have_a[i] = 1;
+  return CPALS_OK;
+}
+
+cpals_status cpals_batch_run(cpals_batch* b, int max_sweeps, double eps, int use_V, double pp_stop_tol,
+                             double* fitness_out, int* sweeps_out, int* status_out, int* kind_trace,
+                             double* fitness_trace) {
+  if (!b) return CPALS_E_INVALID;
+  if (max_sweeps < 1 || !(pp_stop_tol >= 0.0)) return b->fail(CPALS_E_INVALID, "bad run argument");
+  for (int i = 0; i < b->n; i++)
+    if (!b->have_x[i] || !b->have_a[i])
+      return b->fail(CPALS_E_STATE, "instance " + std::to_string(i) + " has no tensor or factors");
+  const int64_t cap = (int64_t)b->n * max_sweeps;
+  if (cap > b->trace_cap) {
+    if (b->d_ftrace) cudaFree(b->d_ftrace);
+    if (b->d_ktrace) cudaFree(b->d_ktrace);
+    b->d_ftrace = nullptr;
+    b->d_ktrace = nullptr;
+    b->trace_cap = 0;
+    if (cudaMalloc((void**)&b->d_ftrace, cap * 8) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_ktrace, cap * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return b->fail(CPALS_E_OOM, "trace buffers");
+    }
+    b->trace_cap = cap;
+  }
+  cpals_status st = b->esz == 8 ? run_impl<double>(b, max_sweeps, eps, use_V != 0, pp_stop_tol)
+                                : run_impl<float>(b, max_sweeps, eps, use_V != 0, pp_stop_tol);
+  if (st != CPALS_OK) return st;
+  std::vector<BC> ctl(b->n);
+  BCK(cudaMemcpy(ctl.data(), b->d_ctl, sizeof(BC) * b->n, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < b->n; i++) {
+    if (sweeps_out) sweeps_out[i] = ctl[i].t;
+    if (status_out)
+      status_out[i] = (ctl[i].status >> 8) & 1 ? CPALS_E_NUMERIC : (ctl[i].status ? CPALS_E_SINGULAR : CPALS_OK);
+    if (fitness_out) BCK(cudaMemcpy(&fitness_out[i], b->dp + b->bi[i].sc, 8, cudaMemcpyDeviceToHost));
+  }
+  if (kind_trace) BCK(cudaMemcpy(kind_trace, b->d_ktrace, cap * 4, cudaMemcpyDeviceToHost));
+  if (fitness_trace) BCK(cudaMemcpy(fitness_trace, b->d_ftrace, cap * 8, cudaMemcpyDeviceToHost));
+  return CPALS_OK;
+}
+
+cpals_status cpals_batch_get_factors(cpals_batch* b, int i, double* const* out) {
+  if (!b) return CPALS_E_INVALID;
+  if (i < 0 || i >= b->n || !out) return b->fail(CPALS_E_INVALID, "bad argument");
+  const BI& q = b->bi[i];
+  for (int n = 0; n < 3; n++) {
+    if (!out[n]) return b->fail(CPALS_E_INVALID, "out[n] is NULL");
+    BCK(cudaMemcpyAsync(out[n], b->dp + q.a[n], (size_t)q.s[n] * q.R * 8, cudaMemcpyDeviceToHost, b->stream));
+  }
+  BCK(cudaStreamSynchronize(b->stream));
+  return CPALS_OK;
+}
+
+cpals_status cpals_batch_stats(const cpals_batch* b, int64_t* launches_per_sweep, int64_t* launches_last_run) {
+  if (!b) return CPALS_E_INVALID;
+  if (launches_per_sweep) *launches_per_sweep = b->launches_sweep;
+  if (launches_last_run) *launches_last_run = b->launches_run;
+  return CPALS_OK;
+}
+
+}  // extern "C"
