@@ -744,6 +744,38 @@ class Tucker:
 
 
 # ---------------------------------------------------------------- batches of small problems
+def cpals_batch_create(n, dims, ranks, precision, out):
+    return lib().cpals_batch_create(n, dims, ranks, precision, out)
+
+
+def cpals_batch_destroy(b):
+    return lib().cpals_batch_destroy(b)
+
+
+def cpals_batch_set_tensor(b, i, ptr, dtype, on_device):
+    return lib().cpals_batch_set_tensor(b, i, ptr, dtype, on_device)
+
+
+def cpals_batch_init_factors(b, i, factors):
+    return lib().cpals_batch_init_factors(b, i, factors)
+
+
+def cpals_batch_run(b, max_sweeps, eps, use_V, pp_stop_tol, fit, sweeps, status, kinds, trace):
+    return lib().cpals_batch_run(b, max_sweeps, eps, use_V, pp_stop_tol, fit, sweeps, status, kinds, trace)
+
+
+def cpals_batch_get_factors(b, i, outs):
+    return lib().cpals_batch_get_factors(b, i, outs)
+
+
+def cpals_batch_stats(b, launches_per_sweep, launches_last_run):
+    return lib().cpals_batch_stats(b, launches_per_sweep, launches_last_run)
+
+
+def cpals_batch_last_error(b):
+    return lib().cpals_batch_last_error(b)
+
+
 class Batch:
     """n order-3 problems run by Algorithm 3 together (cpals_batch_*): every
     sweep stage is one launch over all of them."""
