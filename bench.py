@@ -564,6 +564,7 @@ def run_ours(args):
         "pp_vs_als_speedup_min": round(min(speed), 3) if speed else None,
         "per_precision": pm or None,
         "configs": {k: v.get("summary") for k, v in configs.items()} or None,
+        "batch": (batch or {}).get("summary"),
         "roofline_frac": roofline["frac"],
         "bench_wall_s": round(time.time() - t_start, 1),
     }
@@ -717,47 +718,81 @@ def run_config(cname, dist, runner):
 
 
 def run_batch_bench(args, dist, flush, prec, workers=16):
+    """256 order-3 tensors (s_n ~ U{32..160}, R ~ U{8..64}, 100 sweeps of
+    Algorithm 3 each): the fused batch (cpals_batch_*: one launch per sweep
+    stage over all instances, one graph per batch sweep, tiles from the
+    autotuner) in float32 and float64, against one context per tensor run
+    by host worker threads (cpals_run_batch) in float32 and in the given
+    precision."""
     import numpy as np
     import torch
 
     from paper_1811_10573_gb300 import cpals, synth
 
     probs = synth.batch_order3(count=256, seed=dist.rank)
-    ctxs = []
-    try:
-        for q in probs:
-            g = cpals.CPALS(q.dims, q.R, prec)
-            prep(g)
-            g.set_tensor(torch.from_numpy(np.ascontiguousarray(q.X)).cuda())
-            ctxs.append(g)
+    n = len(probs)
+    q0 = probs[0]
+    out = {"workload": "batch_order3: 256 order-3 tensors, s_n ~ U{32..160}, R ~ U{8..64}, "
+                       f"1e-2 relative noise, eps {q0.eps}, {q0.sweeps} sweeps each (Algorithm 3 per tensor), "
+                       f"stopping test {PP_STOP_TOL}"}
 
-        def timed(w):
-            for g, q in zip(ctxs, probs):
-                g.init_factors(q.A0)
-            flush.zero_()
-            torch.cuda.synchronize()
-            dist.barrier()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            fit, sw, st = cpals.run_batch(ctxs, workers=w, max_sweeps=probs[0].sweeps, eps=probs[0].eps)
-            e1.record()
-            torch.cuda.synchronize()
-            return dist.max(e0.elapsed_time(e1) / 1e3), fit, sw, st
+    def timed(fn):
+        flush.zero_()
+        torch.cuda.synchronize()
+        dist.barrier()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return dist.max(time.perf_counter() - t), r
 
-        timed(workers)                          # warm-up: every context captures its graphs
-        t_w, fit, sw, st = timed(workers)
-        t_1, fit1, sw1, st1 = timed(1)
-        same = bool(np.array_equal(fit, fit1) and np.array_equal(sw, sw1))
-        return {"workload": "batch_order3: 256 order-3 tensors, s_n ~ U{32..160}, R ~ U{8..64}, "
-                            "1e-2 relative noise, eps 0.1, 100 sweeps each (Algorithm 3 per tensor)",
-                "value": round(t_w, 4), "unit": "s", "workers": workers,
-                "decompositions_per_s": round(len(probs) / t_w, 1),
-                "sweeps_total": int(np.sum(sw)), "failed": int(np.sum(st != 0)),
-                "one_at_a_time_s": round(t_1, 4), "speedup_vs_one_at_a_time": round(t_1 / t_w, 2),
-                "same_results_as_one_at_a_time": same}
-    finally:
-        for g in ctxs:
-            g.close()
+    for bprec in ("fp32", "fp64"):
+        with cpals.Batch([q.dims for q in probs], [q.R for q in probs], bprec) as b:
+            for i, q in enumerate(probs):
+                b.set_tensor(i, np.ascontiguousarray(q.X))
+                b.init_factors(i, q.A0)
+            b.run(2, q0.eps, True, PP_STOP_TOL)                  # tile autotuning
+            dt, r = timed(lambda: b.run(q0.sweeps, q0.eps, True, PP_STOP_TOL))
+            ks = [k for kk in r["kinds"] for k in kk]
+            st = b.stats()
+            out["fused_" + bprec] = {
+                "value": round(dt, 4), "unit": "s", "decompositions_per_s": round(n / dt, 1),
+                "launches_per_sweep": st["launches_per_sweep"],
+                "launches_per_stage": 1, "kernel_launches_per_run": st["launches_last_run"],
+                "sweep_counts": {k: ks.count(k) for k in ("als", "pp_init", "pp_approx")},
+                "mean_final_fitness": round(float(np.mean(r["fitness"])), 6),
+                "failed": int(np.sum(r["status"] != 0)), "autotuner": b.tiles()}
+    for cprec in ("fp32", prec):
+        if "contexts_" + cprec in out:
+            continue
+        ctxs = []
+        try:
+            for q in probs:
+                g = cpals.CPALS(q.dims, q.R, cprec)
+                prep(g)
+                g.set_tensor(torch.from_numpy(np.ascontiguousarray(q.X)).cuda())
+                ctxs.append(g)
+
+            def go(w):
+                for g, q in zip(ctxs, probs):
+                    g.init_factors(q.A0)
+                return cpals.run_batch(ctxs, workers=w, max_sweeps=q0.sweeps, eps=q0.eps)
+
+            timed(lambda: go(workers))                       # warm-up: every context captures its graphs
+            dt, (fit, sw, stt) = timed(lambda: go(workers))
+            fe = np.array([g.fitness() for g in ctxs])
+            out["contexts_" + cprec] = {"value": round(dt, 4), "unit": "s", "workers": workers,
+                                        "decompositions_per_s": round(n / dt, 1),
+                                        "mean_final_fitness": round(float(np.mean(fe)), 6),
+                                        "failed": int(np.sum(stt != 0))}
+        finally:
+            for g in ctxs:
+                g.close()
+    f32 = out["fused_fp32"]
+    out["summary"] = {"fused_fp32_per_s": f32["decompositions_per_s"],
+                      "contexts_fp32_per_s": out["contexts_fp32"]["decompositions_per_s"],
+                      "fused_vs_contexts_fp32": round(f32["decompositions_per_s"] /
+                                                      out["contexts_fp32"]["decompositions_per_s"], 3)}
+    return out
 
 
 def run_tucker_bench(args, dist, flush, s=400, R=20, sweeps=20, eps=0.3):

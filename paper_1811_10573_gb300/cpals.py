@@ -66,6 +66,7 @@ _SIGS = {
     "cpals_batch_get_factors": (C.c_int, [_ctx_p, C.c_int, C.POINTER(_dp)]),
     "cpals_batch_stats": (C.c_int, [_ctx_p, _i64p, _i64p]),
     "cpals_batch_last_error": (C.c_char_p, [_ctx_p]),
+    "cpals_batch_tiles": (C.c_int, [_ctx_p, _ip, _fp, _ip]),
     "cpals_device_loop_active": (C.c_int, [_ctx_p]),
     "cpals_set_normal_arith": (C.c_int, [_ctx_p, C.c_int]),
     "cpals_set_step_size": (C.c_int, [_ctx_p, _dp]),
@@ -776,6 +777,10 @@ def cpals_batch_last_error(b):
     return lib().cpals_batch_last_error(b)
 
 
+def cpals_batch_tiles(b, tiles, ms, from_cache):
+    return lib().cpals_batch_tiles(b, tiles, ms, from_cache)
+
+
 class Batch:
     """n order-3 problems run by Algorithm 3 together (cpals_batch_*): every
     sweep stage is one launch over all of them."""
@@ -858,3 +863,11 @@ class Batch:
         a, b = C.c_int64(), C.c_int64()
         self._ck(lib().cpals_batch_stats(self.h, C.byref(a), C.byref(b)))
         return {"launches_per_sweep": a.value, "launches_last_run": b.value}
+
+    def tiles(self):
+        """The autotuner's tile choice for the two ALS contraction stages."""
+        t = np.zeros(2, dtype=np.int32)
+        ms = np.zeros(4, dtype=np.float32)
+        fc = C.c_int()
+        self._ck(lib().cpals_batch_tiles(self.h, t.ctypes.data_as(_ip), ms.ctypes.data_as(_fp), C.byref(fc)))
+        return {"tiles": t.tolist(), "ms": ms.tolist(), "from_cache": bool(fc.value)}

@@ -15,8 +15,11 @@
 // the normal-equation work (Gamma, its Cholesky factor, the solves, the
 // Grams) and the fitness in float64.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -140,11 +143,14 @@ __device__ CtShape<T> ct_shape(int stage, const BI& b, const BC& c, T* tp) {
 }
 
 // 64 x 64 output tiles (R <= 64), 256 threads, 4 x 4 outputs per thread; a
-// work unit is (batch entry, row tile, K split); CTAs past an instance's
-// units (or of an instance not in this stage) return at once.
-template <typename T>
+// work unit is (batch entry, row tile, K split); the CTAs of an instance
+// take its units in turn, those of an instance not in this stage return at
+// once.
+// Two tile shapes (the autotuner picks one per stage and batch): BM = 64
+// (4 x 4 outputs per thread) or BM = 128 (8 x 4).
+template <typename T, int BM, int TM>
 __global__ void __launch_bounds__(kBT) bgemm_kernel(BParams P, int stage, T* __restrict__ tp) {
-  constexpr int BM = 64, BN = 64, BK = 16;
+  constexpr int BN = 64, BK = 16;
   const BI b = P.bi[blockIdx.y];
   const BC c = P.ctl[blockIdx.y];
   const CtShape<T> sh = ct_shape<T>(stage, b, c, tp);
@@ -152,8 +158,9 @@ __global__ void __launch_bounds__(kBT) bgemm_kernel(BParams P, int stage, T* __r
   const int R = b.R;
   const int64_t mtiles = cdiv(sh.M, BM);
   const int64_t units = mtiles * sh.batch * sh.splits;
-  const int64_t u = blockIdx.x;
-  if (u >= units) return;
+  __shared__ T Xs[BK][BM + 1];
+  __shared__ T Bs[BK][BN];
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
   const int64_t mt = u % mtiles;
   const int64_t rest = u / mtiles;
   const int64_t z = rest % sh.splits;
@@ -161,12 +168,10 @@ __global__ void __launch_bounds__(kBT) bgemm_kernel(BParams P, int stage, T* __r
   const int64_t m0 = mt * BM;
   const int64_t k0 = z * sh.kchunk, k1 = min(sh.K, k0 + sh.kchunk);
   const T* X = tp + b.x + bb * sh.K * sh.M;
-  __shared__ T Xs[BK][BM + 1];
-  __shared__ T Bs[BK][BN];
   const int tid = threadIdx.x, tn = tid % 16, tm = tid / 16;
-  T acc[4][4];
+  T acc[TM][4];
 #pragma unroll
-  for (int i = 0; i < 4; i++)
+  for (int i = 0; i < TM; i++)
 #pragma unroll
     for (int j = 0; j < 4; j++) acc[i][j] = T(0);
   for (int64_t kk = k0; kk < k1; kk += BK) {
@@ -192,13 +197,13 @@ __global__ void __launch_bounds__(kBT) bgemm_kernel(BParams P, int stage, T* __r
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < BK; k++) {
-      T av[4], bv[4];
+      T av[TM], bv[4];
 #pragma unroll
-      for (int i = 0; i < 4; i++) av[i] = Xs[k][tm + 16 * i];
+      for (int i = 0; i < TM; i++) av[i] = Xs[k][tm + 16 * i];
 #pragma unroll
       for (int j = 0; j < 4; j++) bv[j] = Bs[k][tn + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; i++)
+      for (int i = 0; i < TM; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
@@ -206,7 +211,7 @@ __global__ void __launch_bounds__(kBT) bgemm_kernel(BParams P, int stage, T* __r
   }
   T* o = sh.out + (z * sh.batch + bb) * sh.M * R;
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
+  for (int i = 0; i < TM; i++) {
     const int64_t m = m0 + tm + 16 * i;
     if (m >= sh.M) continue;
 #pragma unroll
@@ -214,6 +219,7 @@ __global__ void __launch_bounds__(kBT) bgemm_kernel(BParams P, int stage, T* __r
       const int r = tn + 16 * j;
       if (r < R) o[m * R + r] = acc[i][j];
     }
+  }
   }
 }
 
@@ -302,11 +308,21 @@ __global__ void bttv_kernel(BParams P, int stage, T* __restrict__ tp) {
 // or the PP sweep's (instances in PP initialisation or approximated sweeps).
 // NE_INIT: the Grams and norms of the initial factors (Algorithm 3 starts
 // with S^(n) = A^(n)T A^(n) and dA^(n) = A^(n)), for every instance.
-enum NeStage { NE_ALS = 0, NE_PP = 1, NE_INIT = 2 };
+// NE_SWEEP: the update of mode n in whichever sweep kind the instance runs
+// (ALS: exact right-hand side, dA against the old factor; PP: Eq. 3's
+// right-hand side, dA against A_p, W^(n) for the second-order terms).
+enum NeStage { NE_ALS = 0, NE_PP = 1, NE_INIT = 2, NE_SWEEP = 3 };
 
 __device__ __forceinline__ bool ne_active(int stage, const BC& c) {
   if (stage == NE_INIT) return c.ran != K_DONE;
+  if (stage == NE_SWEEP) return runs_als(c) || runs_pp(c);
   return stage == NE_ALS ? runs_als(c) : runs_pp(c);
+}
+__device__ __forceinline__ bool ne_als(int stage, const BC& c) {
+  return stage == NE_ALS || (stage == NE_SWEEP && runs_als(c));
+}
+__device__ __forceinline__ bool ne_pp(int stage, const BC& c) {
+  return stage == NE_PP || (stage == NE_SWEEP && runs_pp(c));
 }
 
 // Gamma^(n) = S^(a) * S^(b) (the other two modes' Grams, Algorithm 1), its
@@ -325,7 +341,7 @@ __global__ void __launch_bounds__(128) bchol_kernel(BParams P, int stage, int n,
   __shared__ double G[kBR * (kBR + 1)];
   __shared__ double il_sh;
   __shared__ int bad;
-  const bool v = stage == NE_PP && P.use_V;
+  const bool v = ne_pp(stage, cc) && P.use_V;
   for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
     const int i = idx / R, j = idx % R;
     G[i * RS + j] = S[a0 * R * R + idx] * S[a1 * R * R + idx];
@@ -349,14 +365,11 @@ __global__ void __launch_bounds__(128) bchol_kernel(BParams P, int stage, int n,
     const double il = il_sh;
     for (int i = k + 1 + threadIdx.x; i < R; i += blockDim.x) G[i * RS + k] *= il;
     __syncthreads();
-    const int m = R - k - 1;                       // trailing rows k+1 .. R-1, lower triangle
-    for (int e = threadIdx.x; e < m * (m + 1) / 2; e += blockDim.x) {
-      int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-      while ((i + 1) * (i + 2) / 2 <= e) i++;
-      while (i * (i + 1) / 2 > e) i--;
-      const int j = e - i * (i + 1) / 2;            // 0 <= j <= i < m
-      const int gi = k + 1 + i, gj = k + 1 + j;
-      G[gi * RS + gj] = fma(-G[gi * RS + k], G[gj * RS + k], G[gi * RS + gj]);
+    // trailing update of the lower triangle: one warp per row, lanes over columns
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = k + 1 + warp; i < R; i += nw) {
+      const double lik = G[i * RS + k];
+      for (int j = k + 1 + lane; j <= i; j += 32) G[i * RS + j] = fma(-lik, G[j * RS + k], G[i * RS + j]);
     }
     __syncthreads();
   }
@@ -371,20 +384,26 @@ __global__ void __launch_bounds__(128) bchol_kernel(BParams P, int stage, int n,
 }
 
 // Row solves of mode n: a Gamma = rhs (+ A_old Z for the PP second-order
-// terms) through L (forward then back substitution, one warp per row), the
-// new factor, dA^(n) = A_new - A_old (ALS) or A_new - A_p (PP), the compute
-// copies and the per-row ||dA||^2, ||A_new||^2.  The PP sweep's last mode
-// also keeps its full right-hand side (rhs2) for the fitness estimate.  A
-// mode whose factorisation failed keeps its factor.
+// terms) through L (forward then back substitution), the new factor,
+// dA^(n) = A_new - A_old (ALS) or A_new - A_p (PP), the compute copies and
+// the per-row ||dA||^2, ||A_new||^2.  The PP sweep's last mode also keeps its
+// full right-hand side (rhs2) for the fitness estimate.  A mode whose
+// factorisation failed keeps its factor.  kSolveCtas CTAs of 8 warps per
+// instance share one copy of L each; a warp solves two rows at a time (two
+// independent substitution chains), lane r holding entries r and r + 32.
+constexpr int kSolveCtas = 4;
+constexpr int kSolveRows = 2;
+
 template <typename T>
-__global__ void __launch_bounds__(128) bsolve_kernel(BParams P, int stage, int n, T* __restrict__ tp,
+__global__ void __launch_bounds__(256) bsolve_kernel(BParams P, int stage, int n, T* __restrict__ tp,
                                                      double* __restrict__ dp) {
   const BI b = P.bi[blockIdx.y];
   const BC c = P.ctl[blockIdx.y];
   if (!ne_active(stage, c)) return;
   const int R = b.R, s = b.s[n], RS = kBR + 1;
   const bool failed = (c.status >> n) & 1;
-  const bool v = stage == NE_PP && P.use_V;
+  const bool als = ne_als(stage, c);
+  const bool v = ne_pp(stage, c) && P.use_V;
   __shared__ double Ls[kBR * (kBR + 1)];
   __shared__ double inv[kBR];
   const double* Zs = dp + b.Z;                  // R x R, read through L1
@@ -394,84 +413,119 @@ __global__ void __launch_bounds__(128) bsolve_kernel(BParams P, int stage, int n
     for (int i = threadIdx.x; i < R; i += blockDim.x) inv[i] = 1.0 / Ls[i * RS + i];
     __syncthreads();
   }
-  const T* rhs = tp + (stage == NE_ALS && n == 2 ? b.mr : b.rhs);
+  const T* rhs = tp + (als && n == 2 ? b.mr : b.rhs);
   double* A = dp + b.a[n];
-  const double* ref = dp + (stage == NE_ALS ? b.a[n] : b.ap[n]);
+  const double* ref = dp + (als ? b.a[n] : b.ap[n]);
   double* dA = dp + b.da[n];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int y = blockIdx.x * 4 + warp; y < s; y += gridDim.x * 4) {
-    double bv[2], old[2];
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int nq = (R + 31) >> 5;                 // 32-column chunks in use (warp-uniform)
+  for (int y0 = (blockIdx.x * (blockDim.x >> 5) + warp) * kSolveRows; y0 < s; y0 += nwarps * kSolveRows) {
+    double bv[kSolveRows][2], old[kSolveRows][2];
+    bool on[kSolveRows];
 #pragma unroll
-    for (int q = 0; q < 2; q++) {
-      const int r = lane + 32 * q;
-      old[q] = r < R ? A[(int64_t)y * R + r] : 0.0;
-      bv[q] = r < R ? (double)rhs[(int64_t)y * R + r] : 0.0;
-    }
-    if (v && !failed) {
-      // second-order terms: b += A_old Z (A_old the factor before this update)
+    for (int h = 0; h < kSolveRows; h++) {
+      const int y = y0 + h;
+      on[h] = y < s;
 #pragma unroll
       for (int q = 0; q < 2; q++) {
         const int r = lane + 32 * q;
-        double acc = bv[q];
-        for (int k = 0; k < R; k++) {
-          const double ak = __shfl_sync(0xffffffffu, old[k >> 5], k & 31);
-          if (r < R) acc = fma(ak, Zs[k * R + r], acc);
+        const bool ok = on[h] && r < R;
+        old[h][q] = ok ? A[(int64_t)y * R + r] : 0.0;
+        bv[h][q] = ok ? (double)rhs[(int64_t)y * R + r] : 0.0;
+      }
+    }
+    if (v && !failed) {
+      // second-order terms: b += A_old Z (A_old the factor before this update)
+      for (int k = 0; k < R; k++) {
+        double ak[kSolveRows];
+#pragma unroll
+        for (int h = 0; h < kSolveRows; h++) ak[h] = __shfl_sync(0xffffffffu, old[h][k >> 5], k & 31);
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+          if (q >= nq) break;
+          const int r = lane + 32 * q;
+          const double z = r < R ? Zs[k * R + r] : 0.0;
+#pragma unroll
+          for (int h = 0; h < kSolveRows; h++) bv[h][q] = fma(ak[h], z, bv[h][q]);
         }
-        bv[q] = acc;
       }
       if (n == 2)
 #pragma unroll
-        for (int q = 0; q < 2; q++) {
-          const int r = lane + 32 * q;
-          if (r < R) tp[b.rhs2 + (int64_t)y * R + r] = (T)bv[q];
-        }
+        for (int h = 0; h < kSolveRows; h++)
+#pragma unroll
+          for (int q = 0; q < 2; q++) {
+            const int r = lane + 32 * q;
+            if (on[h] && r < R) tp[b.rhs2 + (int64_t)(y0 + h) * R + r] = (T)bv[h][q];
+          }
     }
     if (failed) {
-      bv[0] = old[0];
-      bv[1] = old[1];
+#pragma unroll
+      for (int h = 0; h < kSolveRows; h++) {
+        bv[h][0] = old[h][0];
+        bv[h][1] = old[h][1];
+      }
     } else {
       for (int i = 0; i < R; i++) {             // L z = b
-        const double zi = __shfl_sync(0xffffffffu, bv[i >> 5], i & 31) * inv[i];
+        double zi[kSolveRows];
+#pragma unroll
+        for (int h = 0; h < kSolveRows; h++) zi[h] = __shfl_sync(0xffffffffu, bv[h][i >> 5], i & 31) * inv[i];
 #pragma unroll
         for (int q = 0; q < 2; q++) {
+          if (q >= nq || 32 * q + 31 < i) continue;   // no entry of this chunk is left to update
           const int r = lane + 32 * q;
-          if (r == i) bv[q] = zi;
-          else if (r > i && r < R) bv[q] = fma(-Ls[r * RS + i], zi, bv[q]);
+          const double l = (r > i && r < R) ? Ls[r * RS + i] : 0.0;
+#pragma unroll
+          for (int h = 0; h < kSolveRows; h++) {
+            if (r == i) bv[h][q] = zi[h];
+            else if (r > i && r < R) bv[h][q] = fma(-l, zi[h], bv[h][q]);
+          }
         }
       }
       for (int i = R - 1; i >= 0; i--) {        // L^T a = z
-        const double ai = __shfl_sync(0xffffffffu, bv[i >> 5], i & 31) * inv[i];
+        double ai[kSolveRows];
+#pragma unroll
+        for (int h = 0; h < kSolveRows; h++) ai[h] = __shfl_sync(0xffffffffu, bv[h][i >> 5], i & 31) * inv[i];
 #pragma unroll
         for (int q = 0; q < 2; q++) {
+          if (32 * q > i) continue;                    // every entry of this chunk is past i
           const int r = lane + 32 * q;
-          if (r == i) bv[q] = ai;
-          else if (r < i) bv[q] = fma(-Ls[i * RS + r], ai, bv[q]);
+          const double l = r < i ? Ls[i * RS + r] : 0.0;
+#pragma unroll
+          for (int h = 0; h < kSolveRows; h++) {
+            if (r == i) bv[h][q] = ai[h];
+            else if (r < i) bv[h][q] = fma(-l, ai[h], bv[h][q]);
+          }
         }
       }
     }
-    double nd = 0.0, na = 0.0;
 #pragma unroll
-    for (int q = 0; q < 2; q++) {
-      const int r = lane + 32 * q;
-      if (r < R) {
-        const int64_t o = (int64_t)y * R + r;
-        const double d = failed ? dA[o] : bv[q] - (stage == NE_ALS ? old[q] : ref[o]);
-        A[o] = bv[q];
-        dA[o] = d;
-        tp[b.ac[n] + o] = (T)bv[q];
-        tp[b.dac[n] + o] = (T)d;
-        nd = fma(d, d, nd);
-        na = fma(bv[q], bv[q], na);
+    for (int h = 0; h < kSolveRows; h++) {
+      const int y = y0 + h;
+      double nd = 0.0, na = 0.0;
+#pragma unroll
+      for (int q = 0; q < 2; q++) {
+        const int r = lane + 32 * q;
+        if (on[h] && r < R) {
+          const int64_t o = (int64_t)y * R + r;
+          const double d = failed ? dA[o] : bv[h][q] - (als ? old[h][q] : ref[o]);
+          A[o] = bv[h][q];
+          dA[o] = d;
+          tp[b.ac[n] + o] = (T)bv[h][q];
+          tp[b.dac[n] + o] = (T)d;
+          nd = fma(d, d, nd);
+          na = fma(bv[h][q], bv[h][q], na);
+        }
       }
-    }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      nd += __shfl_xor_sync(0xffffffffu, nd, off);
-      na += __shfl_xor_sync(0xffffffffu, na, off);
-    }
-    if (lane == 0) {
-      dp[b.rn + 2 * y] = nd;
-      dp[b.rn + 2 * y + 1] = na;
+      for (int off = 16; off > 0; off >>= 1) {
+        nd += __shfl_xor_sync(0xffffffffu, nd, off);
+        na += __shfl_xor_sync(0xffffffffu, na, off);
+      }
+      if (lane == 0 && on[h]) {
+        dp[b.rn + 2 * y] = nd;
+        dp[b.rn + 2 * y + 1] = na;
+      }
     }
   }
 }
@@ -489,14 +543,12 @@ __global__ void __launch_bounds__(256) bgram_kernel(BParams P, int stage, int n,
   const int R = b.R, s = b.s[n];
   const double* A = dp + b.a[n];
   const double* dA = dp + b.da[n];
-  const int nS = R * (R + 1) / 2;
-  const int nW = stage == NE_PP ? R * R : 0;
+  const int nS = R * R;                          // S: entries with j <= i only
+  const int nW = ne_pp(stage, c) ? R * R : 0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nS + nW; e += gridDim.x * blockDim.x) {
     if (e < nS) {
-      int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
-      while ((i + 1) * (i + 2) / 2 <= e) i++;
-      while (i * (i + 1) / 2 > e) i--;
-      const int j = e - i * (i + 1) / 2;        // j <= i
+      const int i = e / R, j = e % R;
+      if (j > i) continue;
       double acc = 0.0;
       for (int y = 0; y < s; y++) acc = fma(A[(int64_t)y * R + i], A[(int64_t)y * R + j], acc);
       dp[b.S + (int64_t)n * R * R + i * R + j] = acc;
@@ -541,7 +593,7 @@ __global__ void __launch_bounds__(256) bgram_kernel(BParams P, int stage, int n,
 // sum_{i != n} sum_x M_p^(i,n)(x, y, r) dA^(i)[x][r] with the operators
 // M_p^(0,1)[x0][x1][r], M_p^(0,2)[x0][x2][r], M_p^(1,2)[x1][x2][r].
 template <typename T>
-__global__ void bppcorr_kernel(BParams P, int n, T* __restrict__ tp) {
+__global__ void __launch_bounds__(256) bppcorr_kernel(BParams P, int n, T* __restrict__ tp) {
   const BI b = P.bi[blockIdx.y];
   if (!runs_pp(P.ctl[blockIdx.y])) return;
   const int R = b.R;
@@ -560,18 +612,34 @@ __global__ void bppcorr_kernel(BParams P, int n, T* __restrict__ tp) {
     base[0] = b.op02; ys[0] = R; xs[0] = s2 * R; sx[0] = (int)s0; dA[0] = tp + b.dac[0];
     base[1] = b.op12; ys[1] = R; xs[1] = s2 * R; sx[1] = (int)s1; dA[1] = tp + b.dac[1];
   }
+  // 32 consecutive outputs per CTA pass; the 8 warps split each sum over x
+  // (x = warp, warp + 8, ...) and add their partials in warp order
   const int64_t tot = (int64_t)b.s[n] * R;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t y = i / R;
-    const int r = (int)(i % R);
-    T acc = tp[b.mp[n] + i];
+  const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
+  __shared__ T part[8][33];
+  for (int64_t c0 = blockIdx.x * 32; c0 < tot; c0 += (int64_t)gridDim.x * 32) {
+    const int64_t i = c0 + o;
+    T acc = T(0);
+    if (i < tot) {
+      const int64_t y = i / R;
+      const int r = (int)(i % R);
 #pragma unroll
-    for (int q = 0; q < 2; q++) {
-      const T* op = tp + base[q] + y * ys[q] + r;
-      for (int x = 0; x < sx[q]; x++) acc = fma(op[(int64_t)x * xs[q]], dA[q][(int64_t)x * R + r], acc);
+      for (int q = 0; q < 2; q++) {
+        const T* op = tp + base[q] + y * ys[q] + r;
+        const T* d = dA[q] + r;
+#pragma unroll 4
+        for (int x = g; x < sx[q]; x += 8) acc = fma(op[(int64_t)x * xs[q]], d[(int64_t)x * R], acc);
+      }
     }
-    tp[b.rhs + i] = acc;
+    part[g][o] = acc;
+    __syncthreads();
+    if (g == 0 && i < tot) {
+      T sum = tp[b.mp[n] + i];
+#pragma unroll
+      for (int k = 0; k < 8; k++) sum += part[k][o];
+      tp[b.rhs + i] = sum;
+    }
+    __syncthreads();
   }
 }
 
@@ -749,6 +817,10 @@ struct cpals_batch {
   // grid extents (largest over the instances)
   int64_t u_l = 1, u_r = 1, u_12 = 1, u_02 = 1, smax = 1, el_max = 1;
   int64_t launches_sweep = 0, launches_run = 0;
+  // tile configuration of the M^(L) and mode-2 contraction stages (autotuner)
+  int tile[2] = {0, 0};
+  float tile_ms[2][2] = {{-1.f, -1.f}, {-1.f, -1.f}};
+  bool tuned = false, tile_from_cache = false;
   std::string err;
   cpals_status fail(cpals_status st, const std::string& m) {
     err = m;
@@ -760,6 +832,12 @@ struct cpals_batch {
   }
 };
 
+#define CKS_B(expr)                    \
+  do {                                 \
+    cpals_status s_ = (expr);          \
+    if (s_ != CPALS_OK) return s_;     \
+  } while (0)
+
 #define BCK(call)                                           \
   do {                                                      \
     cudaError_t e_ = (call);                                \
@@ -769,6 +847,89 @@ struct cpals_batch {
 namespace {
 
 int el_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, kBT), 64)); }
+constexpr int64_t kGemmCtas = 32;   // CTAs per instance of a contraction stage (they loop over its units)
+
+// One contraction stage with tile configuration cfg (0: 64-row tiles,
+// 1: 128-row tiles).
+template <typename T>
+void launch_gemm(const cpals_batch* b, const BParams& P, int stage, int64_t units, int cfg) {
+  const dim3 g((unsigned)std::min<int64_t>(units, kGemmCtas), (unsigned)b->n);
+  T* tp = static_cast<T*>(b->tp);
+  if (cfg == 1) bgemm_kernel<T, 128, 8><<<g, kBT, 0, b->stream>>>(P, stage, tp);
+  else bgemm_kernel<T, 64, 4><<<g, kBT, 0, b->stream>>>(P, stage, tp);
+}
+
+// Tile autotuner: for the two contraction stages every ALS sweep runs
+// (M^(L) and the mode-2 right-hand side) each tile configuration is timed
+// on the batch itself (CUDA events, one warm-up and three timed launches)
+// and the faster kept; results are cached per batch signature (sizes,
+// ranks, precision) for the life of the process, so later batches of the
+// same shapes reuse them without timing.
+std::mutex g_tune_mutex;
+std::map<uint64_t, std::array<int, 2>> g_tune_cache;
+
+uint64_t batch_signature(const cpals_batch* b) {
+  uint64_t h = 1469598103934665603ull ^ (uint64_t)b->esz;
+  auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+  for (const BI& q : b->bi) {
+    mix((uint64_t)q.s[0]);
+    mix((uint64_t)q.s[1]);
+    mix((uint64_t)q.s[2]);
+    mix((uint64_t)q.R);
+  }
+  return h;
+}
+
+template <typename T>
+cpals_status autotune(cpals_batch* b, const BParams& P) {
+  if (b->tuned) return CPALS_OK;
+  const uint64_t key = batch_signature(b);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      b->tile[0] = it->second[0];
+      b->tile[1] = it->second[1];
+      b->tuned = true;
+      b->tile_from_cache = true;
+      return CPALS_OK;
+    }
+  }
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  const int stages[2] = {CT_L, CT_R};
+  const int64_t units[2] = {b->u_l, b->u_r};
+  for (int st = 0; st < 2; st++) {
+    float best = 0.f;
+    for (int cfg = 0; cfg < 2; cfg++) {
+      launch_gemm<T>(b, P, stages[st], units[st], cfg);
+      cudaEventRecord(e0, b->stream);
+      for (int rep = 0; rep < 3; rep++) launch_gemm<T>(b, P, stages[st], units[st], cfg);
+      cudaEventRecord(e1, b->stream);
+      cudaError_t e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return b->cuda_fail("autotune", e);
+      }
+      b->tile_ms[st][cfg] = ms / 3.f;
+      if (cfg == 0 || ms < best) {
+        best = ms;
+        b->tile[st] = cfg;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->tuned = true;
+  b->tile_from_cache = false;
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  g_tune_cache[key] = {b->tile[0], b->tile[1]};
+  return CPALS_OK;
+}
 
 // Launch every stage of one sweep of the whole batch (captured into a graph).
 template <typename T>
@@ -779,42 +940,44 @@ int64_t sweep_launches(cpals_batch* b, const BParams& P) {
   const unsigned N = (unsigned)b->n;
   int64_t k = 0;
   auto gemm = [&](int stage, int64_t units) {
-    bgemm_kernel<T><<<dim3((unsigned)units, N), kBT, 0, s>>>(P, stage, tp);
+    const int cfg = stage == CT_L ? b->tile[0] : (stage == CT_R ? b->tile[1] : 0);
+    launch_gemm<T>(b, P, stage, units, cfg);
     k++;
   };
-  const dim3 gsolve((unsigned)cdiv(b->smax, 4), N), gel((unsigned)el_grid(b->el_max), N);
+  const dim3 gsolve((unsigned)std::min<int64_t>(kSolveCtas, cdiv(b->smax, 8 * kSolveRows)), N);
+  const dim3 gel((unsigned)el_grid(b->el_max), N);
   auto mode = [&](int stage, int n) {
     bchol_kernel<<<dim3(1, N), 128, 0, s>>>(P, stage, n, dp);
-    bsolve_kernel<T><<<gsolve, 128, 0, s>>>(P, stage, n, tp, dp);
+    bsolve_kernel<T><<<gsolve, 256, 0, s>>>(P, stage, n, tp, dp);
     bgram_kernel<<<dim3(kGramCtas, N), 256, 0, s>>>(P, stage, n, dp);
     k += 3;
   };
-  // ALS sweep (Algorithm 1; binary dimension tree, Sec. 2.5); M^(L) doubles
-  // as M_p^(0,1) for the instances that build operators
+  // M^(L) (ALS, Sec. 2.5), which doubles as M_p^(0,1) for the instances
+  // that build operators; the rest of the operator build (Sec. 3.2.3) and
+  // the PP initialisation of Algorithm 3
   gemm(CT_L, b->u_l);
-  bttv_kernel<T><<<gel, kBT, 0, s>>>(P, TT_ALS0, tp);
-  k++;
-  mode(NE_ALS, 0);
-  bttv_kernel<T><<<gel, kBT, 0, s>>>(P, TT_ALS1, tp);
-  k++;
-  mode(NE_ALS, 1);
-  bkrp_kernel<T><<<gel, kBT, 0, s>>>(P, tp);
-  gemm(CT_R, b->u_r);
-  breduce_kernel<T><<<gel, kBT, 0, s>>>(P, tp);
-  k += 2;
-  mode(NE_ALS, 2);
-  // operator build (Sec. 3.2.3) and the PP initialisation of Algorithm 3
   gemm(CT_12, b->u_12);
   gemm(CT_02, b->u_02);
   bttv_kernel<T><<<dim3(gel.x, N, 3), kBT, 0, s>>>(P, TT_MP, tp);
   bprep_kernel<T><<<gel, kBT, 0, s>>>(P, tp, dp);
   k += 2;
-  // PP sweep (Eq. 3)
-  for (int n = 0; n < 3; n++) {
-    bppcorr_kernel<T><<<gel, kBT, 0, s>>>(P, n, tp);
-    k++;
-    mode(NE_PP, n);
-  }
+  // modes 0, 1, 2 (Gauss-Seidel): each instance forms its right-hand side
+  // (ALS: the dimension tree; PP: Eq. 3), then one factorisation, solve and
+  // Gram stage serves both sweep kinds
+  bttv_kernel<T><<<gel, kBT, 0, s>>>(P, TT_ALS0, tp);
+  bppcorr_kernel<T><<<gel, kBT, 0, s>>>(P, 0, tp);
+  k += 2;
+  mode(NE_SWEEP, 0);
+  bttv_kernel<T><<<gel, kBT, 0, s>>>(P, TT_ALS1, tp);
+  bppcorr_kernel<T><<<gel, kBT, 0, s>>>(P, 1, tp);
+  k += 2;
+  mode(NE_SWEEP, 1);
+  bkrp_kernel<T><<<gel, kBT, 0, s>>>(P, tp);
+  gemm(CT_R, b->u_r);
+  breduce_kernel<T><<<gel, kBT, 0, s>>>(P, tp);
+  bppcorr_kernel<T><<<gel, kBT, 0, s>>>(P, 2, tp);
+  k += 3;
+  mode(NE_SWEEP, 2);
   bfit_kernel<T><<<dim3(1, N), 256, 0, s>>>(P, tp, dp);
   bdecide_kernel<<<(unsigned)cdiv(b->n, 128), 128, 0, s>>>(P, b->n, 0, dp);
   return k + 2;
@@ -829,7 +992,7 @@ int64_t exact_launches(cpals_batch* b, const BParams& P) {
   const dim3 gel((unsigned)el_grid(b->el_max), N);
   bexact_kernel<<<(unsigned)cdiv(b->n, 128), 128, 0, s>>>(P, b->n, 1);
   bkrp_kernel<T><<<gel, kBT, 0, s>>>(P, tp);
-  bgemm_kernel<T><<<dim3((unsigned)b->u_r, N), kBT, 0, s>>>(P, CT_R, tp);
+  launch_gemm<T>(b, P, CT_R, b->u_r, b->tile[1]);
   breduce_kernel<T><<<gel, kBT, 0, s>>>(P, tp);
   bfit_kernel<T><<<dim3(1, N), 256, 0, s>>>(P, tp, b->dp);
   bexact_kernel<<<(unsigned)cdiv(b->n, 128), 128, 0, s>>>(P, b->n, 0);
@@ -857,6 +1020,7 @@ cpals_status run_impl(cpals_batch* b, int max_sweeps, double eps, int use_V, dou
   for (int n = 0; n < 3; n++) bgram_kernel<<<dim3(kGramCtas, N), 256, 0, s>>>(P, NE_INIT, n, dp);
   bdecide_kernel<<<(unsigned)cdiv(b->n, 128), 128, 0, s>>>(P, b->n, 1, dp);
   BCK(cudaGetLastError());
+  CKS_B(autotune<T>(b, P));
   int64_t launches = 5;
   // one captured graph is one sweep of every instance
   cudaGraph_t g = nullptr;
@@ -1105,6 +1269,20 @@ cpals_status cpals_batch_stats(const cpals_batch* b, int64_t* launches_per_sweep
   if (!b) return CPALS_E_INVALID;
   if (launches_per_sweep) *launches_per_sweep = b->launches_sweep;
   if (launches_last_run) *launches_last_run = b->launches_run;
+  return CPALS_OK;
+}
+
+cpals_status cpals_batch_tiles(const cpals_batch* b, int* tiles, float* ms, int* from_cache) {
+  if (!b) return CPALS_E_INVALID;
+  if (!b->tuned) return CPALS_E_STATE;
+  for (int st = 0; st < 2; st++) {
+    if (tiles) tiles[st] = b->tile[st];
+    if (ms) {
+      ms[2 * st] = b->tile_ms[st][0];
+      ms[2 * st + 1] = b->tile_ms[st][1];
+    }
+  }
+  if (from_cache) *from_cache = b->tile_from_cache ? 1 : 0;
   return CPALS_OK;
 }
 

@@ -79,3 +79,22 @@ def test_batch_one_launch_per_stage(probs):
         s2, s6 = b2.stats(), b6.stats()
     assert s2["launches_per_sweep"] == s6["launches_per_sweep"] > 0
     assert s6["launches_last_run"] == s2["launches_last_run"]
+
+
+def test_batch_autotuner_cache_and_results(probs):
+    """The first run times both tile shapes of the two ALS contraction
+    stages; a second batch of the same shapes takes the cached choice
+    without timing.  The tile shape does not change any sum's order, so
+    both batches give bit-identical results."""
+    sub = probs[:3]
+    with _batch(sub, "fp32") as a:
+        ra = a.run(8, EPS)
+        ta = a.tiles()
+    with _batch(sub, "fp32") as b:
+        rb = b.run(8, EPS)
+        tb = b.tiles()
+    assert all(t in (0, 1) for t in ta["tiles"]) and tb["tiles"] == ta["tiles"]
+    assert tb["from_cache"]
+    assert np.array_equal(ra["fitness"], rb["fitness"])
+    for x, y in zip(ra["trace"], rb["trace"]):
+        assert np.array_equal(x, y)
