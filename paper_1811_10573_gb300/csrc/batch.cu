@@ -142,85 +142,122 @@ __device__ CtShape<T> ct_shape(int stage, const BI& b, const BC& c, T* tp) {
   return sh;
 }
 
-// 64 x 64 output tiles (R <= 64), 256 threads, 4 x 4 outputs per thread; a
-// work unit is (batch entry, row tile, K split); the CTAs of an instance
-// take its units in turn, those of an instance not in this stage return at
-// once.
-// Two tile shapes (the autotuner picks one per stage and batch): BM = 64
-// (4 x 4 outputs per thread) or BM = 128 (8 x 4).
+// Output tiles of BM rows x 16 NQ columns (NQ = ceil(R / 16), chosen per
+// instance, so an instance pays for at most 15 padded columns), 256 threads,
+// TM x NQ outputs per thread (rows tm + 16 i, columns tn + 16 j); a work unit
+// is (batch entry, row tile, K split); the CTAs of an instance take its
+// units in turn, those of an instance not in this stage return at once.  The
+// next K tile is fetched into registers while the current one is multiplied
+// from shared memory.  Two row-tile shapes (the autotuner picks one per
+// stage and batch): BM = 64 (TM = 4) or BM = 128 (TM = 8).
+template <typename T, int BM, int TM, int NQ, bool KM>
+__device__ __forceinline__ void bgemm_units(const CtShape<T>& sh, const T* __restrict__ Xbase, int R,
+                                            T (*Xs)[BM + 1], T (*Bs)[64]) {
+  constexpr int BK = 16, BN = 16 * NQ;
+  constexpr int XL = BK * BM / kBT;              // X elements a thread stages per K tile
+  constexpr int BL = (BK * BN + kBT - 1) / kBT;  // B elements a thread stages per K tile
+  const int64_t mtiles = cdiv(sh.M, BM);
+  const int64_t units = mtiles * sh.batch * sh.splits;
+  const int tid = threadIdx.x, tn = tid % 16, tm = tid / 16;
+  // the (k, m) of this thread's staged X elements within a tile: K-major
+  // (k = idx % 16, m = idx / 16) or MN-major (m = idx % BM, k = idx / BM)
+  const int xk = KM ? tid % BK : tid / BM;
+  const int xm = KM ? tid / BK : tid % BM;
+  constexpr int XSTEP_M = KM ? kBT / BK : 0, XSTEP_K = KM ? 0 : kBT / BM;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t mt = u % mtiles;
+    const int64_t rest = u / mtiles;
+    const int64_t z = rest % sh.splits;
+    const int64_t bb = rest / sh.splits;
+    const int64_t m0 = mt * BM;
+    const int64_t k0 = z * sh.kchunk, k1 = min(sh.K, k0 + sh.kchunk);
+    const int mrem = (int)min((int64_t)BM, sh.M - m0);        // rows of this tile
+    // element e sits at (xk + e XSTEP_K, xm + e XSTEP_M); its address at K
+    // offset kk is Xt + kk (K-major: stride K between rows; MN-major: M)
+    const T* Xt = Xbase + bb * sh.K * sh.M + (KM ? (m0 + xm) * sh.K + xk : (int64_t)xk * sh.M + m0 + xm);
+    const int64_t estride = KM ? (int64_t)XSTEP_M * sh.K : (int64_t)XSTEP_K * sh.M;
+    const int64_t kstride = KM ? 1 : sh.M;
+    T acc[TM][NQ];
+#pragma unroll
+    for (int i = 0; i < TM; i++)
+#pragma unroll
+      for (int j = 0; j < NQ; j++) acc[i][j] = T(0);
+    T xr[XL], br[BL];
+    auto fetch = [&](int64_t kk) {
+      const T* xp = Xt + (kk - k0) * kstride + k0 * kstride;
+#pragma unroll
+      for (int e = 0; e < XL; e++) {
+        const bool ok = kk + xk + e * XSTEP_K < k1 && xm + e * XSTEP_M < mrem;
+        xr[e] = ok ? xp[e * estride] : T(0);
+      }
+#pragma unroll
+      for (int e = 0; e < BL; e++) {
+        const int idx = tid + e * kBT;
+        const int r = idx % BN, k = idx / BN;
+        const int64_t gk = kk + k;
+        br[e] = (idx < BK * BN && gk < k1 && r < R) ? sh.B[gk * R + r] : T(0);
+      }
+    };
+    fetch(k0);
+    for (int64_t kk = k0; kk < k1; kk += BK) {
+      __syncthreads();                            // the previous tile is consumed
+#pragma unroll
+      for (int e = 0; e < XL; e++) Xs[xk + e * XSTEP_K][xm + e * XSTEP_M] = xr[e];
+#pragma unroll
+      for (int e = 0; e < BL; e++) {
+        const int idx = tid + e * kBT;
+        if (idx < BK * BN) Bs[idx / BN][idx % BN] = br[e];
+      }
+      __syncthreads();
+      if (kk + BK < k1) fetch(kk + BK);
+#pragma unroll
+      for (int k = 0; k < BK; k++) {
+        T av[TM], bv[NQ];
+#pragma unroll
+        for (int i = 0; i < TM; i++) av[i] = Xs[k][tm + 16 * i];
+#pragma unroll
+        for (int j = 0; j < NQ; j++) bv[j] = Bs[k][tn + 16 * j];
+#pragma unroll
+        for (int i = 0; i < TM; i++)
+#pragma unroll
+          for (int j = 0; j < NQ; j++) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+      }
+    }
+    T* o = sh.out + (z * sh.batch + bb) * sh.M * R;
+#pragma unroll
+    for (int i = 0; i < TM; i++) {
+      const int64_t m = m0 + tm + 16 * i;
+      if (m >= sh.M) continue;
+#pragma unroll
+      for (int j = 0; j < NQ; j++) {
+        const int r = tn + 16 * j;
+        if (r < R) o[m * R + r] = acc[i][j];
+      }
+    }
+  }
+}
+
+template <typename T, int BM, int TM, bool KM>
+__device__ __forceinline__ void bgemm_nq(const CtShape<T>& sh, const T* X, int R, T (*Xs)[BM + 1],
+                                         T (*Bs)[64]) {
+  switch ((R + 15) >> 4) {
+    case 1: bgemm_units<T, BM, TM, 1, KM>(sh, X, R, Xs, Bs); break;
+    case 2: bgemm_units<T, BM, TM, 2, KM>(sh, X, R, Xs, Bs); break;
+    case 3: bgemm_units<T, BM, TM, 3, KM>(sh, X, R, Xs, Bs); break;
+    default: bgemm_units<T, BM, TM, 4, KM>(sh, X, R, Xs, Bs); break;
+  }
+}
+
 template <typename T, int BM, int TM>
-__global__ void __launch_bounds__(kBT) bgemm_kernel(BParams P, int stage, T* __restrict__ tp) {
-  constexpr int BN = 64, BK = 16;
+__global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? (BM == 64 ? 3 : 2) : 1) bgemm_kernel(BParams P, int stage, T* __restrict__ tp) {
   const BI b = P.bi[blockIdx.y];
   const BC c = P.ctl[blockIdx.y];
   const CtShape<T> sh = ct_shape<T>(stage, b, c, tp);
   if (!sh.act) return;
-  const int R = b.R;
-  const int64_t mtiles = cdiv(sh.M, BM);
-  const int64_t units = mtiles * sh.batch * sh.splits;
-  __shared__ T Xs[BK][BM + 1];
-  __shared__ T Bs[BK][BN];
-  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-  const int64_t mt = u % mtiles;
-  const int64_t rest = u / mtiles;
-  const int64_t z = rest % sh.splits;
-  const int64_t bb = rest / sh.splits;
-  const int64_t m0 = mt * BM;
-  const int64_t k0 = z * sh.kchunk, k1 = min(sh.K, k0 + sh.kchunk);
-  const T* X = tp + b.x + bb * sh.K * sh.M;
-  const int tid = threadIdx.x, tn = tid % 16, tm = tid / 16;
-  T acc[TM][4];
-#pragma unroll
-  for (int i = 0; i < TM; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++) acc[i][j] = T(0);
-  for (int64_t kk = k0; kk < k1; kk += BK) {
-    for (int idx = tid; idx < BK * BM; idx += kBT) {
-      int k, m;
-      if (sh.kmajor) {
-        k = idx % BK;
-        m = idx / BK;
-      } else {
-        m = idx % BM;
-        k = idx / BM;
-      }
-      const int64_t gk = kk + k, gm = m0 + m;
-      T v = T(0);
-      if (gk < k1 && gm < sh.M) v = sh.kmajor ? X[gm * sh.K + gk] : X[gk * sh.M + gm];
-      Xs[k][m] = v;
-    }
-    for (int idx = tid; idx < BK * BN; idx += kBT) {
-      const int r = idx % BN, k = idx / BN;
-      const int64_t gk = kk + k;
-      Bs[k][r] = (gk < k1 && r < R) ? sh.B[gk * R + r] : T(0);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < BK; k++) {
-      T av[TM], bv[4];
-#pragma unroll
-      for (int i = 0; i < TM; i++) av[i] = Xs[k][tm + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; j++) bv[j] = Bs[k][tn + 16 * j];
-#pragma unroll
-      for (int i = 0; i < TM; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-  T* o = sh.out + (z * sh.batch + bb) * sh.M * R;
-#pragma unroll
-  for (int i = 0; i < TM; i++) {
-    const int64_t m = m0 + tm + 16 * i;
-    if (m >= sh.M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const int r = tn + 16 * j;
-      if (r < R) o[m * R + r] = acc[i][j];
-    }
-  }
-  }
+  __shared__ T Xs[16][BM + 1];
+  __shared__ T Bs[16][64];
+  if (sh.kmajor) bgemm_nq<T, BM, TM, true>(sh, tp + b.x, b.R, Xs, Bs);
+  else bgemm_nq<T, BM, TM, false>(sh, tp + b.x, b.R, Xs, Bs);
 }
 
 // M^(2) = sum of the K-split partials of CT_R in split order (ALS instances).
@@ -326,7 +363,8 @@ __device__ __forceinline__ bool ne_pp(int stage, const BC& c) {
 }
 
 // Gamma^(n) = S^(a) * S^(b) (the other two modes' Grams, Algorithm 1), its
-// Cholesky factor L (right-looking, in shared memory), and for PP sweeps with
+// Cholesky factor L (right-looking, in shared memory) and W = L^-1 (written
+// in place of L: the row solves use W alone), and for PP sweeps with
 // the second-order terms Z = W^(a) * W^(b) (Eq. 3 for order 3: the one pair
 // {a, b}, W^(i) = A^(i)T dA^(i)), so that V^(n,a,b) = A^(n) Z.  One CTA per
 // instance; a non-positive pivot sets bit n of the instance's status.
@@ -377,192 +415,246 @@ __global__ void __launch_bounds__(128) bchol_kernel(BParams P, int stage, int n,
     if (threadIdx.x == 0) atomicOr(&cc.status, 1 << n);
     return;
   }
+  // W = L^-1 (lower triangular), row by row: W[k] = V[k] / L[k][k] with
+  // V[i] = e_i - sum_{k<i} L[i][k] W[k] (right-looking: row k of V is final
+  // at step k and updates the rows below it).  V[i][c] (c <= i) lives in the
+  // unused upper part of G at G[c][i + 1]; dinv[k] = 1 / L[k][k].
+  __shared__ double dinv[kBR];
+  for (int i = threadIdx.x; i < R; i += blockDim.x) dinv[i] = 1.0 / G[i * RS + i];
   for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
-    const int i = idx / R, j = idx % R;
-    dp[b.L + idx] = j <= i ? G[i * RS + j] : 0.0;
+    const int i = idx / R, c = idx % R;
+    if (c <= i) G[c * RS + i + 1] = i == c ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k + 1 < R; k++) {
+    const int w = k + 1, cnt = (R - k - 1) * w;
+    const double dk = dinv[k];
+    for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+      const int i = k + 1 + idx / w, c = idx % w;
+      G[c * RS + i + 1] = fma(-G[i * RS + k] * dk, G[c * RS + k + 1], G[c * RS + i + 1]);
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
+    const int i = idx / R, c = idx % R;
+    dp[b.L + idx] = c <= i ? G[c * RS + i + 1] * dinv[i] : 0.0;
   }
 }
 
-// Row solves of mode n: a Gamma = rhs (+ A_old Z for the PP second-order
-// terms) through L (forward then back substitution), the new factor,
-// dA^(n) = A_new - A_old (ALS) or A_new - A_p (PP), the compute copies and
-// the per-row ||dA||^2, ||A_new||^2.  The PP sweep's last mode also keeps its
-// full right-hand side (rhs2) for the fitness estimate.  A mode whose
-// factorisation failed keeps its factor.  kSolveCtas CTAs of 8 warps per
-// instance share one copy of L each; a warp solves two rows at a time (two
-// independent substitution chains), lane r holding entries r and r + 32.
+// Row solves of mode n: a Gamma = b with b = rhs (+ A_old Z for the PP
+// second-order terms, formed in the compute precision T), through
+// Gamma^-1 = W^T W (W = L^-1 from the factorisation): u = b W^T, a = u W, so
+// every output is an independent dot product and no row runs a chain of R
+// dependent steps.  Then the new factor, dA^(n) = A_new - A_old (ALS) or
+// A_new - A_p (PP), the compute copies and the per-row ||dA||^2, ||A_new||^2.
+// The PP sweep's last mode also keeps its full right-hand side (rhs2) for the
+// fitness estimate.  A mode whose factorisation failed keeps its factor.
+// kSolveCtas CTAs of 256 threads per instance, each with its own copy of W
+// (and Z) in shared memory, take tiles of kSolveTR rows in turn; a row's 16
+// threads hold outputs r = l, l + 16, l + 32, l + 48.
 constexpr int kSolveCtas = 4;
-constexpr int kSolveRows = 2;
+constexpr int kSolveTR = 16;
+
+template <typename T>
+constexpr size_t bsolve_smem() {
+  return (size_t)kBR * (kBR + 1) * (sizeof(double) + sizeof(T)) + 2 * (size_t)kSolveTR * (kBR + 1) * sizeof(double);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) bsolve_kernel(BParams P, int stage, int n, T* __restrict__ tp,
                                                      double* __restrict__ dp) {
-  const BI b = P.bi[blockIdx.y];
+  const BI& b = P.bi[blockIdx.y];   // fields read once, indexed by mode
   const BC c = P.ctl[blockIdx.y];
   if (!ne_active(stage, c)) return;
   const int R = b.R, s = b.s[n], RS = kBR + 1;
   const bool failed = (c.status >> n) & 1;
   const bool als = ne_als(stage, c);
   const bool v = ne_pp(stage, c) && P.use_V;
-  __shared__ double Ls[kBR * (kBR + 1)];
-  __shared__ double inv[kBR];
-  const double* Zs = dp + b.Z;                  // R x R, read through L1
+  extern __shared__ __align__(16) unsigned char bs_raw[];
+  double* Ws = reinterpret_cast<double*>(bs_raw);              // W[j][k], k <= j
+  double* bt = Ws + kBR * RS;                                   // b of the tile's rows
+  double* ut = bt + kSolveTR * RS;                              // u = b W^T
+  T* Zs = reinterpret_cast<T*>(ut + kSolveTR * RS);             // Z in T
   if (!failed) {
-    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) Ls[(idx / R) * RS + idx % R] = dp[b.L + idx];
-    __syncthreads();
-    for (int i = threadIdx.x; i < R; i += blockDim.x) inv[i] = 1.0 / Ls[i * RS + i];
-    __syncthreads();
+    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
+      Ws[(idx / R) * RS + idx % R] = dp[b.L + idx];
+      if (v) Zs[(idx / R) * RS + idx % R] = (T)dp[b.Z + idx];
+    }
   }
   const T* rhs = tp + (als && n == 2 ? b.mr : b.rhs);
+  const T* Ac = tp + b.ac[n];                   // compute copy of the factor before the update
   double* A = dp + b.a[n];
   const double* ref = dp + (als ? b.a[n] : b.ap[n]);
   double* dA = dp + b.da[n];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
-  const int nq = (R + 31) >> 5;                 // 32-column chunks in use (warp-uniform)
-  for (int y0 = (blockIdx.x * (blockDim.x >> 5) + warp) * kSolveRows; y0 < s; y0 += nwarps * kSolveRows) {
-    double bv[kSolveRows][2], old[kSolveRows][2];
-    bool on[kSolveRows];
+  T* Anew_c = tp + b.ac[n];
+  T* dA_c = tp + b.dac[n];
+  T* rhs2 = tp + b.rhs2;
+  double* rn = dp + b.rn;
+  const int t = threadIdx.x >> 4, l = threadIdx.x & 15;
+  const int nq = (R + 15) >> 4;                 // 16-column chunks in use (block-uniform)
+  for (int y0 = blockIdx.x * kSolveTR; y0 < s; y0 += gridDim.x * kSolveTR) {
+    const int y = y0 + t;
+    const bool on = y < s;
+    __syncthreads();                            // W, Z staged; the previous tile's bt/ut consumed
+    if (!failed) {
+      // b = rhs + A_old Z
 #pragma unroll
-    for (int h = 0; h < kSolveRows; h++) {
-      const int y = y0 + h;
-      on[h] = y < s;
-#pragma unroll
-      for (int q = 0; q < 2; q++) {
-        const int r = lane + 32 * q;
-        const bool ok = on[h] && r < R;
-        old[h][q] = ok ? A[(int64_t)y * R + r] : 0.0;
-        bv[h][q] = ok ? (double)rhs[(int64_t)y * R + r] : 0.0;
+      for (int q = 0; q < 4; q++) {
+        const int r = l + 16 * q;
+        if (q >= nq || r >= R) continue;
+        double bv = on ? (double)rhs[(int64_t)y * R + r] : 0.0;
+        if (v && on) {
+          T acc = T(0);
+          const T* ar = Ac + (int64_t)y * R;
+          for (int k = 0; k < R; k++) acc = fma(ar[k], Zs[k * RS + r], acc);
+          bv += (double)acc;
+          if (n == 2) rhs2[(int64_t)y * R + r] = (T)bv;
+        }
+        bt[t * RS + r] = bv;
       }
     }
-    if (v && !failed) {
-      // second-order terms: b += A_old Z (A_old the factor before this update)
-      for (int k = 0; k < R; k++) {
-        double ak[kSolveRows];
+    __syncthreads();
+    if (!failed) {
+      // u_j = sum_{k <= j} b_k W[j][k]
 #pragma unroll
-        for (int h = 0; h < kSolveRows; h++) ak[h] = __shfl_sync(0xffffffffu, old[h][k >> 5], k & 31);
-#pragma unroll
-        for (int q = 0; q < 2; q++) {
-          if (q >= nq) break;
-          const int r = lane + 32 * q;
-          const double z = r < R ? Zs[k * R + r] : 0.0;
-#pragma unroll
-          for (int h = 0; h < kSolveRows; h++) bv[h][q] = fma(ak[h], z, bv[h][q]);
-        }
-      }
-      if (n == 2)
-#pragma unroll
-        for (int h = 0; h < kSolveRows; h++)
-#pragma unroll
-          for (int q = 0; q < 2; q++) {
-            const int r = lane + 32 * q;
-            if (on[h] && r < R) tp[b.rhs2 + (int64_t)(y0 + h) * R + r] = (T)bv[h][q];
-          }
-    }
-    if (failed) {
-#pragma unroll
-      for (int h = 0; h < kSolveRows; h++) {
-        bv[h][0] = old[h][0];
-        bv[h][1] = old[h][1];
-      }
-    } else {
-      for (int i = 0; i < R; i++) {             // L z = b
-        double zi[kSolveRows];
-#pragma unroll
-        for (int h = 0; h < kSolveRows; h++) zi[h] = __shfl_sync(0xffffffffu, bv[h][i >> 5], i & 31) * inv[i];
-#pragma unroll
-        for (int q = 0; q < 2; q++) {
-          if (q >= nq || 32 * q + 31 < i) continue;   // no entry of this chunk is left to update
-          const int r = lane + 32 * q;
-          const double l = (r > i && r < R) ? Ls[r * RS + i] : 0.0;
-#pragma unroll
-          for (int h = 0; h < kSolveRows; h++) {
-            if (r == i) bv[h][q] = zi[h];
-            else if (r > i && r < R) bv[h][q] = fma(-l, zi[h], bv[h][q]);
-          }
-        }
-      }
-      for (int i = R - 1; i >= 0; i--) {        // L^T a = z
-        double ai[kSolveRows];
-#pragma unroll
-        for (int h = 0; h < kSolveRows; h++) ai[h] = __shfl_sync(0xffffffffu, bv[h][i >> 5], i & 31) * inv[i];
-#pragma unroll
-        for (int q = 0; q < 2; q++) {
-          if (32 * q > i) continue;                    // every entry of this chunk is past i
-          const int r = lane + 32 * q;
-          const double l = r < i ? Ls[i * RS + r] : 0.0;
-#pragma unroll
-          for (int h = 0; h < kSolveRows; h++) {
-            if (r == i) bv[h][q] = ai[h];
-            else if (r < i) bv[h][q] = fma(-l, ai[h], bv[h][q]);
-          }
-        }
+      for (int q = 0; q < 4; q++) {
+        if (q >= nq) break;
+        const int j = l + 16 * q;
+        const int kend = min(16 * q + 15, R - 1);   // warp-uniform trip count
+        double u = 0.0;
+        for (int k = 0; k <= kend; k++)
+          if (k <= j) u = fma(bt[t * RS + k], Ws[j * RS + k], u);
+        if (j < R) ut[t * RS + j] = u;
       }
     }
+    __syncthreads();
+    double av[4];
 #pragma unroll
-    for (int h = 0; h < kSolveRows; h++) {
-      const int y = y0 + h;
-      double nd = 0.0, na = 0.0;
+    for (int q = 0; q < 4; q++) {
+      av[q] = 0.0;
+      if (q >= nq || failed) continue;
+      // a_r = sum_{j >= r} u_j W[j][r]
+      const int r = l + 16 * q;
+      double a = 0.0;
+      for (int j = 16 * q; j < R; j++)
+        if (j >= r) a = fma(ut[t * RS + j], Ws[j * RS + r], a);
+      av[q] = a;
+    }
+    double nd = 0.0, na = 0.0;
 #pragma unroll
-      for (int q = 0; q < 2; q++) {
-        const int r = lane + 32 * q;
-        if (on[h] && r < R) {
-          const int64_t o = (int64_t)y * R + r;
-          const double d = failed ? dA[o] : bv[h][q] - (als ? old[h][q] : ref[o]);
-          A[o] = bv[h][q];
-          dA[o] = d;
-          tp[b.ac[n] + o] = (T)bv[h][q];
-          tp[b.dac[n] + o] = (T)d;
-          nd = fma(d, d, nd);
-          na = fma(bv[h][q], bv[h][q], na);
-        }
-      }
+    for (int q = 0; q < 4; q++) {
+      const int r = l + 16 * q;
+      if (q >= nq || r >= R || !on) continue;
+      const int64_t o = (int64_t)y * R + r;
+      const double old = A[o];
+      const double an = failed ? old : av[q];
+      const double d = failed ? dA[o] : an - (als ? old : ref[o]);
+      A[o] = an;
+      dA[o] = d;
+      Anew_c[o] = (T)an;
+      dA_c[o] = (T)d;
+      nd = fma(d, d, nd);
+      na = fma(an, an, na);
+    }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        nd += __shfl_xor_sync(0xffffffffu, nd, off);
-        na += __shfl_xor_sync(0xffffffffu, na, off);
-      }
-      if (lane == 0 && on[h]) {
-        dp[b.rn + 2 * y] = nd;
-        dp[b.rn + 2 * y + 1] = na;
-      }
+    for (int off = 8; off > 0; off >>= 1) {
+      nd += __shfl_xor_sync(0xffffffffu, nd, off);
+      na += __shfl_xor_sync(0xffffffffu, na, off);
+    }
+    if (l == 0 && on) {
+      rn[2 * y] = nd;
+      rn[2 * y + 1] = na;
     }
   }
 }
 
-// Grams of mode n after its update: S^(n) = A^T A (both triangles) and, in
-// PP sweeps, W^(n) = A^T dA, each entry one float64 dot product over the
-// rows (kGramCtas CTAs per instance split the entries); CTA 0 also sums the
-// row norms into ||dA^(n)||^2 and ||A^(n)||^2.
-constexpr int kGramCtas = 8;
+// Grams of mode n after its update: S^(n) = A^T A (float64, both triangles)
+// and, in PP sweeps, W^(n) = A^T dA (in the compute precision: it only feeds
+// the second-order terms), in 32 x 32 output blocks, one CTA per block: the
+// lower-triangle blocks of S (1 or 3) and the blocks of W^(n) (1 or 4).  A
+// block's 256 threads hold 2 x 2 outputs each and stream the rows through
+// shared memory in chunks of 32; every entry is one dot product over the
+// rows in row order.  CTA 0 also sums the row norms into ||dA^(n)||^2 and
+// ||A^(n)||^2.
+constexpr int kGramCtas = 7;
 
-__global__ void __launch_bounds__(256) bgram_kernel(BParams P, int stage, int n, double* __restrict__ dp) {
-  const BI b = P.bi[blockIdx.y];
+template <typename U>
+__device__ void gram_block(const U* __restrict__ X, const U* __restrict__ Y, int s, int R, int i0, int j0,
+                           U* xs, U* ys, U (&acc)[2][2]) {
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+#pragma unroll
+  for (int a = 0; a < 2; a++)
+#pragma unroll
+    for (int c = 0; c < 2; c++) acc[a][c] = U(0);
+  for (int y0 = 0; y0 < s; y0 += 32) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+      const int yy = idx >> 5, cc = idx & 31, y = y0 + yy;
+      xs[yy * 33 + cc] = (y < s && i0 + cc < R) ? X[(int64_t)y * R + i0 + cc] : U(0);
+      ys[yy * 33 + cc] = (y < s && j0 + cc < R) ? Y[(int64_t)y * R + j0 + cc] : U(0);
+    }
+    __syncthreads();
+    const int ye = min(32, s - y0);
+    for (int yy = 0; yy < ye; yy++) {
+      const U x0 = xs[yy * 33 + ti], x1 = xs[yy * 33 + ti + 16];
+      const U z0 = ys[yy * 33 + tj], z1 = ys[yy * 33 + tj + 16];
+      acc[0][0] = fma(x0, z0, acc[0][0]);
+      acc[0][1] = fma(x0, z1, acc[0][1]);
+      acc[1][0] = fma(x1, z0, acc[1][0]);
+      acc[1][1] = fma(x1, z1, acc[1][1]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) bgram_kernel(BParams P, int stage, int n, T* __restrict__ tp,
+                                                    double* __restrict__ dp) {
+  const BI& b = P.bi[blockIdx.y];   // fields read once, indexed by mode
   const BC c = P.ctl[blockIdx.y];
   if (!ne_active(stage, c)) return;
   const int R = b.R, s = b.s[n];
-  const double* A = dp + b.a[n];
-  const double* dA = dp + b.da[n];
-  const int nS = R * R;                          // S: entries with j <= i only
-  const int nW = ne_pp(stage, c) ? R * R : 0;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nS + nW; e += gridDim.x * blockDim.x) {
-    if (e < nS) {
-      const int i = e / R, j = e % R;
-      if (j > i) continue;
-      double acc = 0.0;
-      for (int y = 0; y < s; y++) acc = fma(A[(int64_t)y * R + i], A[(int64_t)y * R + j], acc);
-      dp[b.S + (int64_t)n * R * R + i * R + j] = acc;
-      dp[b.S + (int64_t)n * R * R + j * R + i] = acc;
-    } else {
-      const int f = e - nS, i = f / R, j = f % R;
-      double acc = 0.0;
-      for (int y = 0; y < s; y++) acc = fma(A[(int64_t)y * R + i], dA[(int64_t)y * R + j], acc);
-      dp[b.W + (int64_t)n * R * R + f] = acc;
-    }
+  const int nb = (R + 31) >> 5;                 // 1 or 2 blocks per side (R <= 64)
+  const int nS = nb * (nb + 1) / 2;
+  const int nW = ne_pp(stage, c) ? nb * nb : 0;
+  const int blk = blockIdx.x;
+  __shared__ double gs[2 * 32 * 33];
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  if (blk < nS) {
+    // lower-triangle blocks (0,0), (1,0), (1,1)
+    const int bi = blk >= 1, bj = blk == 2;
+    const int i0 = 32 * bi, j0 = 32 * bj;
+    double acc[2][2];
+    const double* A = dp + b.a[n];
+    gram_block<double>(A, A, s, R, i0, j0, gs, gs + 32 * 33, acc);
+    double* S = dp + b.S + (int64_t)n * R * R;
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        const int i = i0 + ti + 16 * a, j = j0 + tj + 16 * e;
+        if (i < R && j < R) {
+          S[i * R + j] = acc[a][e];
+          if (bi != bj) S[j * R + i] = acc[a][e];
+        }
+      }
+  } else if (blk < nS + nW) {
+    const int f = blk - nS, i0 = 32 * (f / nb), j0 = 32 * (f % nb);
+    T acc[2][2];
+    T* gt = reinterpret_cast<T*>(gs);
+    gram_block<T>(tp + b.ac[n], tp + b.dac[n], s, R, i0, j0, gt, gt + 32 * 33, acc);
+    double* Wn = dp + b.W + (int64_t)n * R * R;
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        const int i = i0 + ti + 16 * a, j = j0 + tj + 16 * e;
+        if (i < R && j < R) Wn[i * R + j] = (double)acc[a][e];
+      }
   }
-  if (blockIdx.x != 0) return;
+  if (blk != 0) return;
   __shared__ double rd[256], ra[256];
   double x = 0.0, z = 0.0;
+  const double* A = dp + b.a[n];
   if (stage == NE_INIT) {
     for (int64_t e = threadIdx.x; e < (int64_t)s * R; e += blockDim.x) z = fma(A[e], A[e], z);
     x = z;
@@ -593,51 +685,64 @@ __global__ void __launch_bounds__(256) bgram_kernel(BParams P, int stage, int n,
 // sum_{i != n} sum_x M_p^(i,n)(x, y, r) dA^(i)[x][r] with the operators
 // M_p^(0,1)[x0][x1][r], M_p^(0,2)[x0][x2][r], M_p^(1,2)[x1][x2][r].
 template <typename T>
-__global__ void __launch_bounds__(256) bppcorr_kernel(BParams P, int n, T* __restrict__ tp) {
-  const BI b = P.bi[blockIdx.y];
+__global__ void __launch_bounds__(256, 4) bppcorr_kernel(BParams P, int n, T* __restrict__ tp) {
+  const BI& b = P.bi[blockIdx.y];   // fields read once, indexed by mode
   if (!runs_pp(P.ctl[blockIdx.y])) return;
   const int R = b.R;
-  const int64_t s0 = b.s[0], s1 = b.s[1], s2 = b.s[2];
+  const int s0 = b.s[0], s1 = b.s[1], s2 = b.s[2];
   // two terms: operator base for row y = base + y * ystride, x stride, extent, dA
-  int64_t base[2], ys[2], xs[2];
-  int sx[2];
-  const T* dA[2];
+  int64_t base0, base1;
+  int ys0, ys1, xs0, xs1, sx0, sx1;
+  const T *d0, *d1;
   if (n == 0) {
-    base[0] = b.op01; ys[0] = s1 * R; xs[0] = R; sx[0] = (int)s1; dA[0] = tp + b.dac[1];
-    base[1] = b.op02; ys[1] = s2 * R; xs[1] = R; sx[1] = (int)s2; dA[1] = tp + b.dac[2];
+    base0 = b.op01; ys0 = s1 * R; xs0 = R; sx0 = s1; d0 = tp + b.dac[1];
+    base1 = b.op02; ys1 = s2 * R; xs1 = R; sx1 = s2; d1 = tp + b.dac[2];
   } else if (n == 1) {
-    base[0] = b.op01; ys[0] = R; xs[0] = s1 * R; sx[0] = (int)s0; dA[0] = tp + b.dac[0];
-    base[1] = b.op12; ys[1] = s2 * R; xs[1] = R; sx[1] = (int)s2; dA[1] = tp + b.dac[2];
+    base0 = b.op01; ys0 = R; xs0 = s1 * R; sx0 = s0; d0 = tp + b.dac[0];
+    base1 = b.op12; ys1 = s2 * R; xs1 = R; sx1 = s2; d1 = tp + b.dac[2];
   } else {
-    base[0] = b.op02; ys[0] = R; xs[0] = s2 * R; sx[0] = (int)s0; dA[0] = tp + b.dac[0];
-    base[1] = b.op12; ys[1] = R; xs[1] = s2 * R; sx[1] = (int)s1; dA[1] = tp + b.dac[1];
+    base0 = b.op02; ys0 = R; xs0 = s2 * R; sx0 = s0; d0 = tp + b.dac[0];
+    base1 = b.op12; ys1 = R; xs1 = s2 * R; sx1 = s1; d1 = tp + b.dac[1];
   }
   // 32 consecutive outputs per CTA pass; the 8 warps split each sum over x
-  // (x = warp, warp + 8, ...) and add their partials in warp order
-  const int64_t tot = (int64_t)b.s[n] * R;
+  // (x = warp, warp + 8, ...), the two terms in separate accumulators so
+  // that both operators' loads are in flight together, and the partials
+  // are added in warp order
+  const int tot = b.s[n] * R;
   const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int sxm = min(sx0, sx1);
+  const T* mp = tp + b.mp[n];
+  T* rhs = tp + b.rhs;
   __shared__ T part[8][33];
-  for (int64_t c0 = blockIdx.x * 32; c0 < tot; c0 += (int64_t)gridDim.x * 32) {
-    const int64_t i = c0 + o;
-    T acc = T(0);
+  for (int c0 = blockIdx.x * 32; c0 < tot; c0 += gridDim.x * 32) {
+    const int i = c0 + o;
+    T acc0 = T(0), acc1 = T(0);
     if (i < tot) {
-      const int64_t y = i / R;
-      const int r = (int)(i % R);
-#pragma unroll
-      for (int q = 0; q < 2; q++) {
-        const T* op = tp + base[q] + y * ys[q] + r;
-        const T* d = dA[q] + r;
+      const int y = i / R, r = i - y * R;
+      // pointers stepped by 8 rows of x
+      const T* p0 = tp + base0 + (int64_t)y * ys0 + r + (int64_t)g * xs0;
+      const T* p1 = tp + base1 + (int64_t)y * ys1 + r + (int64_t)g * xs1;
+      const T* q0 = d0 + r + g * R;
+      const T* q1 = d1 + r + g * R;
+      const int64_t st0 = 8 * (int64_t)xs0, st1 = 8 * (int64_t)xs1;
+      const int stq = 8 * R;
+      int x = g;
 #pragma unroll 4
-        for (int x = g; x < sx[q]; x += 8) acc = fma(op[(int64_t)x * xs[q]], d[(int64_t)x * R], acc);
+      for (; x < sxm; x += 8) {
+        acc0 = fma(*p0, *q0, acc0);
+        acc1 = fma(*p1, *q1, acc1);
+        p0 += st0; p1 += st1; q0 += stq; q1 += stq;
       }
+      for (int x0 = x; x0 < sx0; x0 += 8, p0 += st0, q0 += stq) acc0 = fma(*p0, *q0, acc0);
+      for (int x1 = x; x1 < sx1; x1 += 8, p1 += st1, q1 += stq) acc1 = fma(*p1, *q1, acc1);
     }
-    part[g][o] = acc;
+    part[g][o] = acc0 + acc1;
     __syncthreads();
     if (g == 0 && i < tot) {
-      T sum = tp[b.mp[n] + i];
+      T sum = mp[i];
 #pragma unroll
       for (int k = 0; k < 8; k++) sum += part[k][o];
-      tp[b.rhs + i] = sum;
+      rhs[i] = sum;
     }
     __syncthreads();
   }
@@ -944,12 +1049,12 @@ int64_t sweep_launches(cpals_batch* b, const BParams& P) {
     launch_gemm<T>(b, P, stage, units, cfg);
     k++;
   };
-  const dim3 gsolve((unsigned)std::min<int64_t>(kSolveCtas, cdiv(b->smax, 8 * kSolveRows)), N);
+  const dim3 gsolve((unsigned)std::min<int64_t>(kSolveCtas, cdiv(b->smax, kSolveTR)), N);
   const dim3 gel((unsigned)el_grid(b->el_max), N);
   auto mode = [&](int stage, int n) {
     bchol_kernel<<<dim3(1, N), 128, 0, s>>>(P, stage, n, dp);
-    bsolve_kernel<T><<<gsolve, 256, 0, s>>>(P, stage, n, tp, dp);
-    bgram_kernel<<<dim3(kGramCtas, N), 256, 0, s>>>(P, stage, n, dp);
+    bsolve_kernel<T><<<gsolve, 256, bsolve_smem<T>(), s>>>(P, stage, n, tp, dp);
+    bgram_kernel<T><<<dim3(kGramCtas, N), 256, 0, s>>>(P, stage, n, tp, dp);
     k += 3;
   };
   // M^(L) (ALS, Sec. 2.5), which doubles as M_p^(0,1) for the instances
@@ -1017,7 +1122,7 @@ cpals_status run_impl(cpals_batch* b, int max_sweeps, double eps, int use_V, dou
   // Algorithm 3's start: dA <- A, S <- A^T A, the first decision
   BCK(cudaMemsetAsync(b->d_ctl, 0, sizeof(BC) * b->n, s));
   binit_kernel<T><<<dim3((unsigned)el_grid(b->el_max), N), kBT, 0, s>>>(P, tp, dp);
-  for (int n = 0; n < 3; n++) bgram_kernel<<<dim3(kGramCtas, N), 256, 0, s>>>(P, NE_INIT, n, dp);
+  for (int n = 0; n < 3; n++) bgram_kernel<T><<<dim3(kGramCtas, N), 256, 0, s>>>(P, NE_INIT, n, tp, dp);
   bdecide_kernel<<<(unsigned)cdiv(b->n, 128), 128, 0, s>>>(P, b->n, 1, dp);
   BCK(cudaGetLastError());
   CKS_B(autotune<T>(b, P));
@@ -1076,6 +1181,13 @@ cpals_status cpals_batch_create(int n, const int64_t* dims, const int* ranks, in
     return CPALS_E_CUDA;
   }
   if (!(prop.major == 10 && prop.minor == 3)) return CPALS_E_UNSUPPORTED;
+  if (cudaFuncSetAttribute(bsolve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bsolve_smem<float>()) != cudaSuccess ||
+      cudaFuncSetAttribute(bsolve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bsolve_smem<double>()) != cudaSuccess) {
+    cudaGetLastError();
+    return CPALS_E_CUDA;
+  }
   cpals_batch* b = new cpals_batch();
   b->n = n;
   b->prec = precision;
