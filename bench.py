@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tucker", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline and FP32/mixed only")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="only the 256-tensor batch entry (its own JSON line)")
     ap.add_argument("--host-loop", action="store_true",
                     help="Algorithm 3's decisions on the host in every run (for profilers)")
     return ap.parse_args()
@@ -952,10 +954,34 @@ def run_reference(args):
     }))
 
 
+def run_batch_only(args):
+    """The 256-tensor batch entry alone: fused batch in float32 and float64
+    against per-tensor contexts; the line's value is the fused float32
+    batch's decompositions per second."""
+    import torch
+
+    from paper_1811_10573_gb300 import build, cpals, harness
+
+    dist = harness.init()
+    torch.cuda.set_device(dist.local_rank)
+    build.build()
+    cpals.lib()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = run_batch_bench(args, dist, flush, args.precision)
+    if dist.rank == 0:
+        v = out["fused_fp32"]["decompositions_per_s"] * dist.world
+        print(json.dumps({"metric": "decompositions_per_s", "value": v, "unit": "1/s",
+                          "n_gpus": dist.world, "higher_is_better": True, "scaling": "weak",
+                          "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": "batch_order3_256"}, "batch": out}))
+
+
 if __name__ == "__main__":
     a = parse()
     HOST_LOOP = a.host_loop
     if a.impl == "reference":
         run_reference(a)
+    elif a.batch_only:
+        run_batch_only(a)
     else:
         run_ours(a)
