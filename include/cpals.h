@@ -40,7 +40,13 @@ typedef enum {
   CPALS_E_OOM = 2,         /* device allocation failed */
   CPALS_E_CUDA = 3,        /* CUDA runtime/driver error (text in cpals_last_error) */
   CPALS_E_STATE = 4,       /* call out of order (e.g. pp_sweep before pp_build_operators) */
-  CPALS_E_SINGULAR = 5,    /* Gamma not positive definite: the factor of that mode was left unchanged */
+  CPALS_E_SINGULAR = 5,    /* Gamma not positive definite and no pseudo-inverse path: the factor of
+                              that mode was left unchanged.  With IEEE float64 normal equations
+                              (FP64 contexts, or cpals_set_normal_arith) such a Gamma is replaced
+                              by its pseudo-inverse Gamma^dagger (Algorithm 1) instead: symmetric
+                              Jacobi eigendecomposition, eigenvalues at or below 1e-13 of the
+                              largest dropped; no error.  The double-float path (the default of
+                              FP32 and mixed contexts) reports this code. */
   CPALS_E_NUMERIC = 6,     /* NaN/Inf detected in a result */
   CPALS_E_TIMEOUT = 7,     /* a bounded device wait gave up */
   CPALS_E_UNSUPPORTED = 8  /* configuration outside what this build implements */
@@ -339,7 +345,9 @@ cpals_status cpals_pp_mttkrp(cpals_ctx* ctx, int n, int use_V, double* out);
 /* Solve X Gamma^(n) = rhs (Sec. 2.3 normal equations) with the Grams the
  * context currently holds, through the same factorisation and row-solve
  * kernels as a sweep, without changing any state.  rhs, out: s_n x R float64
- * host buffers.  CPALS_E_SINGULAR if Gamma^(n) is not positive definite. */
+ * host buffers.  A Gamma^(n) that is not positive definite is solved with its
+ * pseudo-inverse (IEEE float64 normal equations) or reported as
+ * CPALS_E_SINGULAR (double-float). */
 cpals_status cpals_normal_solve(cpals_ctx* ctx, int n, const double* rhs, double* out);
 
 /* Copy A_p^(n) (which = 0) or dA^(n) (which = 1) to a host float64 buffer. */

@@ -705,8 +705,8 @@ cpals_status check_status(cpals_ctx* c) {
       return c->fail(CPALS_E_NUMERIC, "non-finite factor in mode " + std::to_string(n));
   if (!std::isfinite(c->scal_h[0]))
     return c->fail(CPALS_E_NUMERIC, "non-finite fitness");
-  if (c->status_h[0]) {
-    const int bits = c->status_h[0];
+  if (c->status_h[0] & 0xffff) {        // bits 16 + n: Gamma^dagger used (not an error)
+    const int bits = c->status_h[0] & 0xffff;
     CK(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->stream));
     return c->fail(CPALS_E_SINGULAR, "Gamma not positive definite for mode mask " + std::to_string(bits) +
                                          "; those factors were left unchanged");
@@ -996,7 +996,7 @@ __global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* 
       bool finite = isfinite(f);
       for (int n = 0; n < s->N; n++)
         finite = finite && isfinite(scal[8 + 2 * n]) && isfinite(scal[9 + 2 * n]);
-      if (!finite || status[0]) {
+      if (!finite || (status[0] & 0xffff)) {
         s->err = finite ? 2 : 1;
         record(ran, f);
         stop = true;
@@ -1958,7 +1958,7 @@ cpals_status cpals_normal_solve(cpals_ctx* c, int n, const double* rhs, double* 
   }
   CKS(sync_read(c));
   CK(cudaMemcpy(out, c->dscr[1], cnt * 8, cudaMemcpyDeviceToHost));
-  if (c->status_h[0]) {
+  if (c->status_h[0] & 0xffff) {
     CK(cudaMemset(c->status, 0, 16));
     return c->fail(CPALS_E_SINGULAR, "Gamma not positive definite");
   }

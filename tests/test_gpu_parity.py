@@ -203,20 +203,83 @@ def test_order3_60_rank10_run_fp64():
             assert rel(a, b) < 1e-8
 
 
-def test_singular_gamma_reported():
-    """Identical columns in two factors make Gamma of the third mode singular:
-    CPALS_E_SINGULAR, and that factor is left unchanged."""
-    p = synth.make_problem("normal", [12, 10, 9], 3, seed=13, storage="f64")
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_singular_gamma_reported_double_float(prec):
+    """A zero column in the other two factors makes Gamma of mode 0 exactly
+    singular (a zero pivot).  The double-float normal equations have no
+    pseudo-inverse path: CPALS_E_SINGULAR, and that factor is left
+    unchanged."""
+    p = synth.make_problem("normal", [12, 10, 9], 3, seed=13, storage="f32")
     A0 = [a.copy() for a in p.A0]
     for n in (1, 2):
-        A0[n][:, 1] = A0[n][:, 0]
-    with cpals.CPALS(p.dims, p.R, "fp64") as g:
+        A0[n][:, 1] = 0.0
+    with cpals.CPALS(p.dims, p.R, prec) as g:
         g.set_tensor(p.X)
         g.init_factors(A0)
         with pytest.raises(cpals.CPALSError) as e:
             g.als_sweep()
         assert e.value.status == 5
-        np.testing.assert_array_equal(g.get_factors()[0], A0[0])
+        # kept as the double-float pair it was stored as (48-bit significand)
+        np.testing.assert_allclose(g.get_factors()[0], A0[0], rtol=1e-13, atol=0)
+
+
+def _zero_column_problem(R=5, col=2, seed=14):
+    p = synth.make_problem("normal", [12, 10, 9], R, seed=seed, storage="f64")
+    A0 = [a.copy() for a in p.A0]
+    A0[1][:, col] = 0.0
+    return p, A0
+
+
+def test_normal_solve_pinv_fp64():
+    """Gamma^(0) with a zero row and column (zero column in A^(1)): the
+    float64 path solves with Gamma^dagger (Algorithm 1) like the oracle's
+    eigen pseudo-inverse fallback, for a consistent and an arbitrary
+    right-hand side."""
+    p, A0 = _zero_column_problem()
+    g_ = np.random.default_rng(40)
+    with cpals.CPALS(p.dims, p.R, "fp64") as g:
+        g.set_tensor(p.X)
+        g.init_factors(A0)
+        S = [O.gram(a) for a in A0]
+        G = O.gamma(S, 0)
+        for rhs in (g_.standard_normal((p.dims[0], p.R)) @ G, g_.standard_normal((p.dims[0], p.R))):
+            info = O.SolveInfo()
+            ref = O.solve_normal(rhs, G, info)
+            assert info.singular
+            assert rel(g.normal_solve(0, rhs), ref) < 1e-11
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.2])
+def test_run_with_singular_gamma_fp64_equals_lower_rank(eps):
+    """A zero column in every initial factor keeps every Gamma^(n) singular
+    (a zero row and column) for the whole run; the float64 path then solves
+    through Gamma^dagger every mode.  In exact arithmetic the run is the
+    rank R - 1 decomposition without that column (its Gamma is the reduced
+    Gamma, its MTTKRP columns the reduced ones), so ALS (eps 0) and PP-ALS
+    (eps 0.2, second-order terms) must follow the oracle's rank R - 1 run
+    sweep for sweep, with the column exactly zero throughout."""
+    R, col = 5, 2
+    p = synth.make_problem("normal", [12, 10, 9], R, seed=14, storage="f64")
+    A0 = [a.copy() for a in p.A0]
+    for a in A0:
+        a[:, col] = 0.0
+    keep = [r for r in range(R) if r != col]
+    n = 12
+    A_or, tr = O.pp_cp_als(p.X, [a[:, keep] for a in A0], n, eps, use_V=True)
+    with cpals.CPALS(p.dims, R, "fp64") as g:
+        g.set_tensor(p.X)
+        g.init_factors(A0)
+        out = g.run(n, eps, True, 0.0)
+        A = g.get_factors()
+        f = g.fitness()
+    assert out["kinds"] == tr.kinds
+    np.testing.assert_allclose(out["fitness"], tr.seen, rtol=0, atol=1e-10)
+    assert abs(f - tr.fitness[-1]) < 1e-10
+    for a, b in zip(A, A_or):
+        assert np.all(a[:, col] == 0.0)
+        assert rel(a[:, keep], b) < 1e-8
+    if eps > 0:
+        assert "pp_approx" in out["kinds"]
 
 
 def test_call_order_errors():
