@@ -13,7 +13,8 @@
 // batch, whatever kind each instance takes.  Contractions, operators and
 // corrections run in the batch's compute precision (float32 or float64);
 // the normal-equation work (Gamma, its Cholesky factor, the solves, the
-// Grams) and the fitness in float64.
+// Grams) in float64 for float64 batches and in double-float for float32
+// batches; the fitness in float64.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -24,6 +25,7 @@
 #include <vector>
 
 #include "../../include/cpals.h"
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace {
@@ -55,6 +57,11 @@ struct BI {
   int64_t rn;             // 2 smax row norms
   int64_t sc;             // scalars: [0] fitness, [1] inner, [2] model, [3] ||X||^2,
                           // [8 + 2n] ||dA^(n)||^2, [9 + 2n] ||A^(n)||^2
+  // double-float normal equations of float32 batches (T arena): the factor's
+  // low words (its high words are the compute copy ac), A_p as high and low
+  // words, S^(n) and W = L^-1 as high and low words, W^(n) = A^T dA and Z
+  int64_t alo[3], aph[3], apl[3];
+  int64_t shi, slo, lih, lil, wg, zf;
 };
 
 // Per-instance controller state of Algorithm 3 (device).
@@ -680,6 +687,305 @@ __global__ void __launch_bounds__(256) bgram_kernel(BParams P, int stage, int n,
   }
 }
 
+// ---------------------------------------------------------------- normal equations (double-float)
+// Float32 batches run the normal-equation stages in double-float arithmetic
+// (hi + lo pairs of floats, 48-bit significand; dfloat.cuh) on the float32
+// pipes, as the float32 contexts do: GB300's float64 pipe runs at 1/64 of the
+// float32 rate.  Same stages, orders and layout as the float64 kernels above;
+// the float64 factor and Grams are still written (high + low words) for the
+// fitness, the PP set-up and the host.
+using namespace cpals::dfa;
+
+// Gamma^(n) = S^(a) * S^(b), its Cholesky factor and W = L^-1 (lower, in the
+// unused upper part of G as in the float64 kernel), all double-float; Z =
+// W^(a) * W^(b) in float for the second-order terms.  1 / L[k][k] is the
+// pivot's reciprocal square root, taken once.
+__global__ void __launch_bounds__(256) bchol_df_kernel(BParams P, int stage, int n, float* __restrict__ tp) {
+  BC& cc = P.ctl[blockIdx.y];
+  const BI& b = P.bi[blockIdx.y];
+  if (!ne_active(stage, cc)) return;
+  const int R = b.R, RS = kBR + 1, RR = R * R;
+  const int a0 = n == 0 ? 1 : 0, a1 = n == 2 ? 1 : 2;
+  const float* sh = tp + b.shi;
+  const float* sl = tp + b.slo;
+  const float* wg = tp + b.wg;
+  float* zf = tp + b.zf;
+  __shared__ float2 G[kBR * (kBR + 1)];
+  __shared__ float2 dinv[kBR];
+  __shared__ int bad;
+  const bool v = ne_pp(stage, cc) && P.use_V;
+  for (int idx = threadIdx.x; idx < RR; idx += blockDim.x) {
+    const int i = idx / R, j = idx % R;
+    const dfl x{sh[a0 * RR + idx], sl[a0 * RR + idx]}, y{sh[a1 * RR + idx], sl[a1 * RR + idx]};
+    G[i * RS + j] = pk(df_mul(x, y));
+    if (v) zf[idx] = wg[a0 * RR + idx] * wg[a1 * RR + idx];
+  }
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = 0; k < R; k++) {
+    if (threadIdx.x == 0) {
+      const dfl piv = upk(G[k * RS + k]);
+      if (!(piv.hi > 0.f) || !isfinite(piv.hi)) {
+        bad = 1;
+      } else {
+        const dfl il = df_rsqrt(piv);
+        dinv[k] = pk(il);
+        G[k * RS + k] = pk(df_mul(piv, il));
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const dfl il = upk(dinv[k]);
+    for (int i = k + 1 + threadIdx.x; i < R; i += blockDim.x) G[i * RS + k] = pk(df_mul(upk(G[i * RS + k]), il));
+    __syncthreads();
+    for (int i = k + 1 + warp; i < R; i += nw) {
+      const dfl lik = upk(G[i * RS + k]);
+      for (int j = k + 1 + lane; j <= i; j += 32)
+        G[i * RS + j] = pk(df_sub(upk(G[i * RS + j]), df_mul(lik, upk(G[j * RS + k]))));
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) atomicOr(&cc.status, 1 << n);
+    return;
+  }
+  for (int idx = threadIdx.x; idx < RR; idx += blockDim.x) {
+    const int i = idx / R, c = idx % R;
+    if (c <= i) G[c * RS + i + 1] = make_float2(i == c ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int k = 0; k + 1 < R; k++) {
+    const int w = k + 1, cnt = (R - k - 1) * w;
+    const dfl dk = upk(dinv[k]);
+    for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+      const int i = k + 1 + idx / w, c = idx % w;
+      const dfl f = df_mul(upk(G[i * RS + k]), dk);
+      G[c * RS + i + 1] = pk(df_sub(upk(G[c * RS + i + 1]), df_mul(f, upk(G[c * RS + k + 1]))));
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < RR; idx += blockDim.x) {
+    const int i = idx / R, c = idx % R;
+    const dfl val = c <= i ? df_mul(upk(G[c * RS + i + 1]), upk(dinv[i])) : dfl{0.f, 0.f};
+    tp[b.lih + idx] = val.hi;
+    tp[b.lil + idx] = val.lo;
+  }
+}
+
+// Row solves through W = L^-1 (u = b W^T, a = u W) in double-float; b = rhs
+// + A_old Z (float; the sum of two floats is exact as a double-float).  The
+// new factor keeps its high and low words (compute copy and alo) and its
+// float64 value; dA = A_new - A_old (ALS) or A_new - A_p (PP) in
+// double-float, its compute copy in float; row norms in float.
+constexpr size_t bsolve_df_smem() {
+  return (size_t)kBR * (kBR + 1) * (sizeof(float2) + sizeof(float)) +
+         2 * (size_t)kSolveTR * (kBR + 1) * sizeof(float2);
+}
+
+__global__ void __launch_bounds__(256) bsolve_df_kernel(BParams P, int stage, int n, float* __restrict__ tp,
+                                                        double* __restrict__ dp) {
+  const BI& b = P.bi[blockIdx.y];
+  const BC c = P.ctl[blockIdx.y];
+  if (!ne_active(stage, c)) return;
+  const int R = b.R, s = b.s[n], RS = kBR + 1;
+  const bool failed = (c.status >> n) & 1;
+  if (failed) return;                            // the mode keeps its factor and dA
+  const bool als = ne_als(stage, c);
+  const bool v = ne_pp(stage, c) && P.use_V;
+  extern __shared__ __align__(16) unsigned char bs_raw[];
+  float2* Ws = reinterpret_cast<float2*>(bs_raw);
+  float2* bt = Ws + kBR * RS;
+  float2* ut = bt + kSolveTR * RS;
+  float* Zs = reinterpret_cast<float*>(ut + kSolveTR * RS);
+  for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
+    const int o = (idx / R) * RS + idx % R;
+    Ws[o] = make_float2(tp[b.lih + idx], tp[b.lil + idx]);
+    if (v) Zs[o] = tp[b.zf + idx];
+  }
+  const float* rhs = tp + (als && n == 2 ? b.mr : b.rhs);
+  float* Ah = tp + b.ac[n];
+  float* Al = tp + b.alo[n];
+  const float* Rh = tp + (als ? b.ac[n] : b.aph[n]);
+  const float* Rl = tp + (als ? b.alo[n] : b.apl[n]);
+  float* dAc = tp + b.dac[n];
+  float* rhs2 = tp + b.rhs2;
+  double* A = dp + b.a[n];
+  double* rn = dp + b.rn;
+  const int t = threadIdx.x >> 4, l = threadIdx.x & 15;
+  const int nq = (R + 15) >> 4;
+  for (int y0 = blockIdx.x * kSolveTR; y0 < s; y0 += gridDim.x * kSolveTR) {
+    const int y = y0 + t;
+    const bool on = y < s;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int r = l + 16 * q;
+      if (q >= nq || r >= R) continue;
+      const float bv = on ? rhs[(int64_t)y * R + r] : 0.f;
+      dfl bd{bv, 0.f};
+      if (v && on) {
+        float acc = 0.f;
+        const float* ar = Ah + (int64_t)y * R;
+        for (int k = 0; k < R; k++) acc = fmaf(ar[k], Zs[k * RS + r], acc);
+        bd = two_sum(bv, acc);
+        if (n == 2) rhs2[(int64_t)y * R + r] = bd.hi;
+      }
+      bt[t * RS + r] = pk(bd);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      if (q >= nq) break;
+      const int j = l + 16 * q;
+      const int kend = min(16 * q + 15, R - 1);
+      dfl u{0.f, 0.f};
+      for (int k = 0; k <= kend; k++)
+        if (k <= j) u = df_add(u, df_mul(upk(bt[t * RS + k]), upk(Ws[j * RS + k])));
+      if (j < R) ut[t * RS + j] = pk(u);
+    }
+    __syncthreads();
+    float nd = 0.f, na = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      if (q >= nq) break;
+      const int r = l + 16 * q;
+      dfl a{0.f, 0.f};
+      for (int j = 16 * q; j < R; j++)
+        if (j >= r) a = df_add(a, df_mul(upk(ut[t * RS + j]), upk(Ws[j * RS + r])));
+      if (r >= R || !on) continue;
+      const int64_t o = (int64_t)y * R + r;
+      const dfl d = df_sub(a, dfl{Rh[o], Rl[o]});   // reads A_old before it is replaced
+      Ah[o] = a.hi;
+      Al[o] = a.lo;
+      A[o] = (double)a.hi + (double)a.lo;
+      dAc[o] = d.hi;
+      nd = fmaf(d.hi, d.hi, nd);
+      na = fmaf(a.hi, a.hi, na);
+    }
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) {
+      nd += __shfl_xor_sync(0xffffffffu, nd, off);
+      na += __shfl_xor_sync(0xffffffffu, na, off);
+    }
+    if (l == 0 && on) {
+      rn[2 * y] = nd;
+      rn[2 * y + 1] = na;
+    }
+  }
+}
+
+// Grams of mode n in double-float: S^(n) = A^T A from the factor's high and
+// low words (32 x 32 blocks as the float64 kernel, row order), written as
+// double-float and as float64; W^(n) = A^T dA in float; CTA 0 sums the row
+// norms.
+__global__ void __launch_bounds__(256) bgram_df_kernel(BParams P, int stage, int n, float* __restrict__ tp,
+                                                       double* __restrict__ dp) {
+  const BI& b = P.bi[blockIdx.y];
+  const BC c = P.ctl[blockIdx.y];
+  if (!ne_active(stage, c)) return;
+  const int R = b.R, s = b.s[n];
+  const int nb = (R + 31) >> 5;
+  const int nS = nb * (nb + 1) / 2;
+  const int nW = ne_pp(stage, c) ? nb * nb : 0;
+  const int blk = blockIdx.x;
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  __shared__ float2 xs[32 * 33], ys[32 * 33];
+  if (blk < nS) {
+    const int bi = blk >= 1, bj = blk == 2;
+    const int i0 = 32 * bi, j0 = 32 * bj;
+    const float* Ah = tp + b.ac[n];
+    const float* Al = tp + b.alo[n];
+    dfl acc[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+      for (int e = 0; e < 2; e++) acc[a][e] = dfl{0.f, 0.f};
+    for (int y0 = 0; y0 < s; y0 += 32) {
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+        const int yy = idx >> 5, cc = idx & 31, y = y0 + yy;
+        const bool okx = y < s && i0 + cc < R, oky = y < s && j0 + cc < R;
+        xs[yy * 33 + cc] = okx ? make_float2(Ah[(int64_t)y * R + i0 + cc], Al[(int64_t)y * R + i0 + cc])
+                               : make_float2(0.f, 0.f);
+        ys[yy * 33 + cc] = oky ? make_float2(Ah[(int64_t)y * R + j0 + cc], Al[(int64_t)y * R + j0 + cc])
+                               : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      const int ye = min(32, s - y0);
+      for (int yy = 0; yy < ye; yy++) {
+        const dfl x0 = upk(xs[yy * 33 + ti]), x1 = upk(xs[yy * 33 + ti + 16]);
+        const dfl z0 = upk(ys[yy * 33 + tj]), z1 = upk(ys[yy * 33 + tj + 16]);
+        acc[0][0] = df_add(acc[0][0], df_mul(x0, z0));
+        acc[0][1] = df_add(acc[0][1], df_mul(x0, z1));
+        acc[1][0] = df_add(acc[1][0], df_mul(x1, z0));
+        acc[1][1] = df_add(acc[1][1], df_mul(x1, z1));
+      }
+    }
+    float* shn = tp + b.shi + (int64_t)n * R * R;
+    float* sln = tp + b.slo + (int64_t)n * R * R;
+    double* S = dp + b.S + (int64_t)n * R * R;
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        const int i = i0 + ti + 16 * a, j = j0 + tj + 16 * e;
+        if (i < R && j < R) {
+          const dfl v = acc[a][e];
+          const double vd = (double)v.hi + (double)v.lo;
+          shn[i * R + j] = v.hi;
+          sln[i * R + j] = v.lo;
+          S[i * R + j] = vd;
+          if (bi != bj) {
+            shn[j * R + i] = v.hi;
+            sln[j * R + i] = v.lo;
+            S[j * R + i] = vd;
+          }
+        }
+      }
+  } else if (blk < nS + nW) {
+    const int f = blk - nS, i0 = 32 * (f / nb), j0 = 32 * (f % nb);
+    float acc[2][2];
+    float* gx = reinterpret_cast<float*>(xs);
+    gram_block<float>(tp + b.ac[n], tp + b.dac[n], s, R, i0, j0, gx, gx + 32 * 33, acc);
+    float* Wn = tp + b.wg + (int64_t)n * R * R;
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        const int i = i0 + ti + 16 * a, j = j0 + tj + 16 * e;
+        if (i < R && j < R) Wn[i * R + j] = acc[a][e];
+      }
+  }
+  if (blk != 0) return;
+  __shared__ double rd[256], ra[256];
+  double x = 0.0, z = 0.0;
+  if (stage == NE_INIT) {
+    const double* A = dp + b.a[n];
+    for (int64_t e = threadIdx.x; e < (int64_t)s * R; e += blockDim.x) z = fma(A[e], A[e], z);
+    x = z;
+  } else {
+    for (int y = threadIdx.x; y < s; y += blockDim.x) {
+      x += dp[b.rn + 2 * y];
+      z += dp[b.rn + 2 * y + 1];
+    }
+  }
+  rd[threadIdx.x] = x;
+  ra[threadIdx.x] = z;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      rd[threadIdx.x] += rd[threadIdx.x + st];
+      ra[threadIdx.x] += ra[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    dp[b.sc + 8 + 2 * n] = rd[0];
+    dp[b.sc + 9 + 2 * n] = ra[0];
+  }
+}
+
 // ---------------------------------------------------------------- PP sweep, fitness, controller
 // Eq. 3 first-order terms of mode n: rhs[y][r] = M_p^(n)[y][r] +
 // sum_{i != n} sum_x M_p^(i,n)(x, y, r) dA^(i)[x][r] with the operators
@@ -761,8 +1067,13 @@ __global__ void bprep_kernel(BParams P, T* __restrict__ tp, double* __restrict__
       dp[b.ap[n] + i] = dp[b.a[n] + i];
       dp[b.da[n] + i] = 0.0;
       tp[b.dac[n] + i] = T(0);
+      tp[b.aph[n] + i] = tp[b.ac[n] + i];
+      tp[b.apl[n] + i] = tp[b.alo[n] + i];
     }
-  for (int64_t i = g; i < 3 * (int64_t)R * R; i += st) dp[b.W + i] = 0.0;
+  for (int64_t i = g; i < 3 * (int64_t)R * R; i += st) {
+    dp[b.W + i] = 0.0;
+    tp[b.wg + i] = T(0);
+  }
   if (g < 3) dp[b.sc + 8 + 2 * g] = 0.0;
 }
 
@@ -877,8 +1188,12 @@ __global__ void binit_kernel(BParams P, T* __restrict__ tp, double* __restrict__
       dp[b.da[n] + i] = a;
       tp[b.ac[n] + i] = (T)a;
       tp[b.dac[n] + i] = (T)a;
+      if constexpr (sizeof(T) == 4) tp[b.alo[n] + i] = (T)(a - (double)(T)a);
     }
-  for (int64_t i = g; i < 3 * (int64_t)R * R; i += st) dp[b.W + i] = 0.0;
+  for (int64_t i = g; i < 3 * (int64_t)R * R; i += st) {
+    dp[b.W + i] = 0.0;
+    tp[b.wg + i] = T(0);
+  }
 }
 
 // ||X||^2 of instance i in float64 (one CTA, fixed order).
@@ -1052,9 +1367,15 @@ int64_t sweep_launches(cpals_batch* b, const BParams& P) {
   const dim3 gsolve((unsigned)std::min<int64_t>(kSolveCtas, cdiv(b->smax, kSolveTR)), N);
   const dim3 gel((unsigned)el_grid(b->el_max), N);
   auto mode = [&](int stage, int n) {
-    bchol_kernel<<<dim3(1, N), 128, 0, s>>>(P, stage, n, dp);
-    bsolve_kernel<T><<<gsolve, 256, bsolve_smem<T>(), s>>>(P, stage, n, tp, dp);
-    bgram_kernel<T><<<dim3(kGramCtas, N), 256, 0, s>>>(P, stage, n, tp, dp);
+    if constexpr (sizeof(T) == 4) {
+      bchol_df_kernel<<<dim3(1, N), 256, 0, s>>>(P, stage, n, tp);
+      bsolve_df_kernel<<<gsolve, 256, bsolve_df_smem(), s>>>(P, stage, n, tp, dp);
+      bgram_df_kernel<<<dim3(kGramCtas, N), 256, 0, s>>>(P, stage, n, tp, dp);
+    } else {
+      bchol_kernel<<<dim3(1, N), 128, 0, s>>>(P, stage, n, dp);
+      bsolve_kernel<T><<<gsolve, 256, bsolve_smem<T>(), s>>>(P, stage, n, tp, dp);
+      bgram_kernel<T><<<dim3(kGramCtas, N), 256, 0, s>>>(P, stage, n, tp, dp);
+    }
     k += 3;
   };
   // M^(L) (ALS, Sec. 2.5), which doubles as M_p^(0,1) for the instances
@@ -1122,7 +1443,10 @@ cpals_status run_impl(cpals_batch* b, int max_sweeps, double eps, int use_V, dou
   // Algorithm 3's start: dA <- A, S <- A^T A, the first decision
   BCK(cudaMemsetAsync(b->d_ctl, 0, sizeof(BC) * b->n, s));
   binit_kernel<T><<<dim3((unsigned)el_grid(b->el_max), N), kBT, 0, s>>>(P, tp, dp);
-  for (int n = 0; n < 3; n++) bgram_kernel<T><<<dim3(kGramCtas, N), 256, 0, s>>>(P, NE_INIT, n, tp, dp);
+  for (int n = 0; n < 3; n++) {
+    if constexpr (sizeof(T) == 4) bgram_df_kernel<<<dim3(kGramCtas, N), 256, 0, s>>>(P, NE_INIT, n, tp, dp);
+    else bgram_kernel<T><<<dim3(kGramCtas, N), 256, 0, s>>>(P, NE_INIT, n, tp, dp);
+  }
   bdecide_kernel<<<(unsigned)cdiv(b->n, 128), 128, 0, s>>>(P, b->n, 1, dp);
   BCK(cudaGetLastError());
   CKS_B(autotune<T>(b, P));
@@ -1184,7 +1508,9 @@ cpals_status cpals_batch_create(int n, const int64_t* dims, const int* ranks, in
   if (cudaFuncSetAttribute(bsolve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bsolve_smem<float>()) != cudaSuccess ||
       cudaFuncSetAttribute(bsolve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)bsolve_smem<double>()) != cudaSuccess) {
+                           (int)bsolve_smem<double>()) != cudaSuccess ||
+      cudaFuncSetAttribute(bsolve_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bsolve_df_smem()) != cudaSuccess) {
     cudaGetLastError();
     return CPALS_E_CUDA;
   }
@@ -1222,6 +1548,15 @@ cpals_status cpals_batch_create(int n, const int64_t* dims, const int* ranks, in
     q.op02 = t(s0 * s2 * R);
     q.op12 = t(s1 * s2 * R);
     for (int k = 0; k < 3; k++) q.mp[k] = t(dims[3 * i + k] * R);
+    for (int k = 0; k < 3; k++) q.alo[k] = t(dims[3 * i + k] * R);
+    for (int k = 0; k < 3; k++) q.aph[k] = t(dims[3 * i + k] * R);
+    for (int k = 0; k < 3; k++) q.apl[k] = t(dims[3 * i + k] * R);
+    q.shi = t(3 * (int64_t)R * R);
+    q.slo = t(3 * (int64_t)R * R);
+    q.lih = t((int64_t)R * R);
+    q.lil = t((int64_t)R * R);
+    q.wg = t(3 * (int64_t)R * R);
+    q.zf = t((int64_t)R * R);
     auto dd = [&](int64_t e) { const int64_t o = d; d += e; return o; };
     for (int k = 0; k < 3; k++) q.a[k] = dd(dims[3 * i + k] * R);
     for (int k = 0; k < 3; k++) q.ap[k] = dd(dims[3 * i + k] * R);

@@ -8,8 +8,8 @@ every sweep (exact after ALS sweeps, the M~ estimate after PP sweeps) within
 within 1e-10 -- with and without the stopping test inside PP runs.  The
 instances differ in every size and rank, so each stage launch covers
 instances in different sweep kinds at once.  In float32 (the contractions,
-operators and corrections; float64 normal equations) the final fitness stays
-within 1e-4 of the float64 batch.  One sweep of the batch launches the same
+operators and corrections; double-float normal equations) the final fitness
+stays within 1e-4 of the float64 batch.  One sweep of the batch launches the same
 number of kernels whatever the number of instances.
 """
 import numpy as np
