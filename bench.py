@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="headline and FP32/mixed only")
     ap.add_argument("--batch-only", action="store_true",
                     help="only the 256-tensor batch entry (its own JSON line)")
+    ap.add_argument("--no-contexts", action="store_true",
+                    help="batch entry: the fused batch only, without the per-tensor contexts")
     ap.add_argument("--host-loop", action="store_true",
                     help="Algorithm 3's decisions on the host in every run (for profilers)")
     return ap.parse_args()
@@ -763,7 +765,7 @@ def run_batch_bench(args, dist, flush, prec, workers=16):
                 "sweep_counts": {k: ks.count(k) for k in ("als", "pp_init", "pp_approx")},
                 "mean_final_fitness": round(float(np.mean(r["fitness"])), 6),
                 "failed": int(np.sum(r["status"] != 0)), "autotuner": b.tiles()}
-    for cprec in ("fp32", prec):
+    for cprec in (() if args.no_contexts else ("fp32", prec)):
         if "contexts_" + cprec in out:
             continue
         ctxs = []
@@ -790,10 +792,11 @@ def run_batch_bench(args, dist, flush, prec, workers=16):
             for g in ctxs:
                 g.close()
     f32 = out["fused_fp32"]
-    out["summary"] = {"fused_fp32_per_s": f32["decompositions_per_s"],
-                      "contexts_fp32_per_s": out["contexts_fp32"]["decompositions_per_s"],
-                      "fused_vs_contexts_fp32": round(f32["decompositions_per_s"] /
-                                                      out["contexts_fp32"]["decompositions_per_s"], 3)}
+    out["summary"] = {"fused_fp32_per_s": f32["decompositions_per_s"]}
+    if "contexts_fp32" in out:
+        c32 = out["contexts_fp32"]["decompositions_per_s"]
+        out["summary"].update({"contexts_fp32_per_s": c32,
+                               "fused_vs_contexts_fp32": round(f32["decompositions_per_s"] / c32, 3)})
     return out
 
 

@@ -245,14 +245,15 @@ cpals_status cpals_batch_get_factors(cpals_batch* b, int i, double* const* out);
 /* kernels of one batch sweep graph (one launch per stage over all instances)
  * and kernels launched by the last run */
 cpals_status cpals_batch_stats(const cpals_batch* b, int64_t* launches_per_sweep, int64_t* launches_last_run);
-/* The tile autotuner's choice for the batch's two contraction stages every
- * ALS sweep runs (M^(L), then the mode-2 right-hand side): tiles[2]
- * (0 = 64-row tiles with 4 x 4 outputs per thread, 1 = 128-row tiles with
- * 8 x 4), ms[4] the measured launch times (stage-major, -1 if not timed),
- * *from_cache 1 when the choice came from the process-wide cache of an
- * earlier batch with the same sizes, ranks and precision (nothing timed).
- * The tuning runs at the first cpals_batch_run.  Each argument nullable;
- * CPALS_E_STATE before the first run. */
+/* The tile autotuner's choice for the batch's four contraction stages
+ * (M^(L), the mode-2 right-hand side, M_p^(1,2), M_p^(0,2)): tiles[4]
+ * (0 = 64-row tiles with 4 outputs per thread per 16 columns, 1 = 128-row
+ * tiles with 8, 2 = 32-row tiles with 2; columns are 16 ceil(R / 16) per
+ * instance), ms[12] the measured launch times (stage-major, three shapes
+ * per stage, -1 if not timed), *from_cache 1 when the choice came from the
+ * process-wide cache of an earlier batch with the same sizes, ranks and
+ * precision (nothing timed).  The tuning runs at the first cpals_batch_run.
+ * Each argument nullable; CPALS_E_STATE before the first run. */
 cpals_status cpals_batch_tiles(const cpals_batch* b, int* tiles, float* ms, int* from_cache);
 const char* cpals_batch_last_error(const cpals_batch* b);
 

@@ -865,9 +865,9 @@ class Batch:
         return {"launches_per_sweep": a.value, "launches_last_run": b.value}
 
     def tiles(self):
-        """The autotuner's tile choice for the two ALS contraction stages."""
-        t = np.zeros(2, dtype=np.int32)
-        ms = np.zeros(4, dtype=np.float32)
+        """The autotuner's tile choice for the four contraction stages."""
+        t = np.zeros(4, dtype=np.int32)
+        ms = np.zeros(12, dtype=np.float32)
         fc = C.c_int()
         self._ck(lib().cpals_batch_tiles(self.h, t.ctypes.data_as(_ip), ms.ctypes.data_as(_fp), C.byref(fc)))
         return {"tiles": t.tolist(), "ms": ms.tolist(), "from_cache": bool(fc.value)}

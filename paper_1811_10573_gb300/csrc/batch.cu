@@ -36,6 +36,8 @@ __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 
 
 constexpr int kBR = 64;           // largest rank of a batch instance
 constexpr int kBT = 256;          // threads of the contraction and element kernels
+constexpr int kTuneStages = 4;    // contraction stages the autotuner tunes (CT_L, CT_R, CT_12, CT_02)
+constexpr int kTileCfgs = 3;      // row-tile shapes: 64, 128, 32 rows
 // Sweep kinds (as CPALS_SWEEP_*), the exact-fitness pass after the last
 // sweep, and a finished instance.
 enum Kind { K_ALS = 0, K_INIT = 1, K_PP = 2, K_EXACT = 3, K_DONE = -1 };
@@ -80,6 +82,8 @@ struct BParams {
   BC* ctl;
   double eps, tol;
   int use_V, max_sweeps;
+  int force;              // contraction stages run for every instance (autotuner timing only)
+  int pad;
   double* ftrace;         // n x max_sweeps
   int* ktrace;
 };
@@ -111,7 +115,7 @@ struct CtShape {
 };
 
 template <typename T>
-__device__ CtShape<T> ct_shape(int stage, const BI& b, const BC& c, T* tp) {
+__device__ CtShape<T> ct_shape(int stage, const BI& b, const BC& c, T* tp, bool force) {
   CtShape<T> sh;
   const int64_t s0 = b.s[0], s1 = b.s[1], s2 = b.s[2];
   sh.batch = 1;
@@ -146,6 +150,7 @@ __device__ CtShape<T> ct_shape(int stage, const BI& b, const BC& c, T* tp) {
     sh.out = tp + b.op02;
   }
   sh.kchunk = cdiv(cdiv(sh.K, sh.splits), 16) * 16;
+  sh.act = sh.act || force;
   return sh;
 }
 
@@ -155,8 +160,8 @@ __device__ CtShape<T> ct_shape(int stage, const BI& b, const BC& c, T* tp) {
 // is (batch entry, row tile, K split); the CTAs of an instance take its
 // units in turn, those of an instance not in this stage return at once.  The
 // next K tile is fetched into registers while the current one is multiplied
-// from shared memory.  Two row-tile shapes (the autotuner picks one per
-// stage and batch): BM = 64 (TM = 4) or BM = 128 (TM = 8).
+// from shared memory.  Three row-tile shapes (the autotuner picks one per
+// stage and batch): BM = 64 (TM = 4), 128 (TM = 8) or 32 (TM = 2).
 template <typename T, int BM, int TM, int NQ, bool KM>
 __device__ __forceinline__ void bgemm_units(const CtShape<T>& sh, const T* __restrict__ Xbase, int R,
                                             T (*Xs)[BM + 1], T (*Bs)[64]) {
@@ -256,10 +261,10 @@ __device__ __forceinline__ void bgemm_nq(const CtShape<T>& sh, const T* X, int R
 }
 
 template <typename T, int BM, int TM>
-__global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? (BM == 64 ? 3 : 2) : 1) bgemm_kernel(BParams P, int stage, T* __restrict__ tp) {
+__global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? (BM == 128 ? 2 : 3) : 1) bgemm_kernel(BParams P, int stage, T* __restrict__ tp) {
   const BI b = P.bi[blockIdx.y];
   const BC c = P.ctl[blockIdx.y];
-  const CtShape<T> sh = ct_shape<T>(stage, b, c, tp);
+  const CtShape<T> sh = ct_shape<T>(stage, b, c, tp, P.force != 0);
   if (!sh.act) return;
   __shared__ T Xs[16][BM + 1];
   __shared__ T Bs[16][64];
@@ -1238,8 +1243,9 @@ struct cpals_batch {
   int64_t u_l = 1, u_r = 1, u_12 = 1, u_02 = 1, smax = 1, el_max = 1;
   int64_t launches_sweep = 0, launches_run = 0;
   // tile configuration of the M^(L) and mode-2 contraction stages (autotuner)
-  int tile[2] = {0, 0};
-  float tile_ms[2][2] = {{-1.f, -1.f}, {-1.f, -1.f}};
+  int tile[kTuneStages] = {0, 0, 0, 0};
+  float tile_ms[kTuneStages][kTileCfgs] = {{-1.f, -1.f, -1.f}, {-1.f, -1.f, -1.f}, {-1.f, -1.f, -1.f},
+                                           {-1.f, -1.f, -1.f}};
   bool tuned = false, tile_from_cache = false;
   std::string err;
   cpals_status fail(cpals_status st, const std::string& m) {
@@ -1276,17 +1282,18 @@ void launch_gemm(const cpals_batch* b, const BParams& P, int stage, int64_t unit
   const dim3 g((unsigned)std::min<int64_t>(units, kGemmCtas), (unsigned)b->n);
   T* tp = static_cast<T*>(b->tp);
   if (cfg == 1) bgemm_kernel<T, 128, 8><<<g, kBT, 0, b->stream>>>(P, stage, tp);
+  else if (cfg == 2) bgemm_kernel<T, 32, 2><<<g, kBT, 0, b->stream>>>(P, stage, tp);
   else bgemm_kernel<T, 64, 4><<<g, kBT, 0, b->stream>>>(P, stage, tp);
 }
 
-// Tile autotuner: for the two contraction stages every ALS sweep runs
-// (M^(L) and the mode-2 right-hand side) each tile configuration is timed
-// on the batch itself (CUDA events, one warm-up and three timed launches)
-// and the faster kept; results are cached per batch signature (sizes,
+// Tile autotuner: for each of the four contraction stages (M^(L), the mode-2
+// right-hand side, M_p^(1,2), M_p^(0,2)) each tile configuration is timed on
+// the batch itself with every instance taking part (CUDA events, one
+// warm-up and three timed launches) and the fastest kept; results are cached per batch signature (sizes,
 // ranks, precision) for the life of the process, so later batches of the
 // same shapes reuse them without timing.
 std::mutex g_tune_mutex;
-std::map<uint64_t, std::array<int, 2>> g_tune_cache;
+std::map<uint64_t, std::array<int, kTuneStages>> g_tune_cache;
 
 uint64_t batch_signature(const cpals_batch* b) {
   uint64_t h = 1469598103934665603ull ^ (uint64_t)b->esz;
@@ -1308,8 +1315,7 @@ cpals_status autotune(cpals_batch* b, const BParams& P) {
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      b->tile[0] = it->second[0];
-      b->tile[1] = it->second[1];
+      for (int st = 0; st < kTuneStages; st++) b->tile[st] = it->second[st];
       b->tuned = true;
       b->tile_from_cache = true;
       return CPALS_OK;
@@ -1318,14 +1324,17 @@ cpals_status autotune(cpals_batch* b, const BParams& P) {
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
-  const int stages[2] = {CT_L, CT_R};
-  const int64_t units[2] = {b->u_l, b->u_r};
-  for (int st = 0; st < 2; st++) {
+  // every instance takes part in the timed launches (their outputs are
+  // scratch until the sweeps write them)
+  BParams Pf = P;
+  Pf.force = 1;
+  const int64_t units[kTuneStages] = {b->u_l, b->u_r, b->u_12, b->u_02};
+  for (int st = 0; st < kTuneStages; st++) {
     float best = 0.f;
-    for (int cfg = 0; cfg < 2; cfg++) {
-      launch_gemm<T>(b, P, stages[st], units[st], cfg);
+    for (int cfg = 0; cfg < kTileCfgs; cfg++) {
+      launch_gemm<T>(b, Pf, st, units[st], cfg);
       cudaEventRecord(e0, b->stream);
-      for (int rep = 0; rep < 3; rep++) launch_gemm<T>(b, P, stages[st], units[st], cfg);
+      for (int rep = 0; rep < 3; rep++) launch_gemm<T>(b, Pf, st, units[st], cfg);
       cudaEventRecord(e1, b->stream);
       cudaError_t e = cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -1347,7 +1356,7 @@ cpals_status autotune(cpals_batch* b, const BParams& P) {
   b->tuned = true;
   b->tile_from_cache = false;
   std::lock_guard<std::mutex> lk(g_tune_mutex);
-  g_tune_cache[key] = {b->tile[0], b->tile[1]};
+  g_tune_cache[key] = {b->tile[0], b->tile[1], b->tile[2], b->tile[3]};
   return CPALS_OK;
 }
 
@@ -1360,7 +1369,7 @@ int64_t sweep_launches(cpals_batch* b, const BParams& P) {
   const unsigned N = (unsigned)b->n;
   int64_t k = 0;
   auto gemm = [&](int stage, int64_t units) {
-    const int cfg = stage == CT_L ? b->tile[0] : (stage == CT_R ? b->tile[1] : 0);
+    const int cfg = b->tile[stage];
     launch_gemm<T>(b, P, stage, units, cfg);
     k++;
   };
@@ -1418,7 +1427,7 @@ int64_t exact_launches(cpals_batch* b, const BParams& P) {
   const dim3 gel((unsigned)el_grid(b->el_max), N);
   bexact_kernel<<<(unsigned)cdiv(b->n, 128), 128, 0, s>>>(P, b->n, 1);
   bkrp_kernel<T><<<gel, kBT, 0, s>>>(P, tp);
-  launch_gemm<T>(b, P, CT_R, b->u_r, b->tile[1]);
+  launch_gemm<T>(b, P, CT_R, b->u_r, b->tile[CT_R]);
   breduce_kernel<T><<<gel, kBT, 0, s>>>(P, tp);
   bfit_kernel<T><<<dim3(1, N), 256, 0, s>>>(P, tp, b->dp);
   bexact_kernel<<<(unsigned)cdiv(b->n, 128), 128, 0, s>>>(P, b->n, 0);
@@ -1431,7 +1440,7 @@ cpals_status run_impl(cpals_batch* b, int max_sweeps, double eps, int use_V, dou
   double* dp = b->dp;
   cudaStream_t s = b->stream;
   const unsigned N = (unsigned)b->n;
-  BParams P;
+  BParams P{};                       // force = 0: stages follow each instance's sweep kind
   P.bi = b->d_bi;
   P.ctl = b->d_ctl;
   P.eps = eps;
@@ -1722,12 +1731,10 @@ cpals_status cpals_batch_stats(const cpals_batch* b, int64_t* launches_per_sweep
 cpals_status cpals_batch_tiles(const cpals_batch* b, int* tiles, float* ms, int* from_cache) {
   if (!b) return CPALS_E_INVALID;
   if (!b->tuned) return CPALS_E_STATE;
-  for (int st = 0; st < 2; st++) {
+  for (int st = 0; st < kTuneStages; st++) {
     if (tiles) tiles[st] = b->tile[st];
-    if (ms) {
-      ms[2 * st] = b->tile_ms[st][0];
-      ms[2 * st + 1] = b->tile_ms[st][1];
-    }
+    if (ms)
+      for (int cfg = 0; cfg < kTileCfgs; cfg++) ms[kTileCfgs * st + cfg] = b->tile_ms[st][cfg];
   }
   if (from_cache) *from_cache = b->tile_from_cache ? 1 : 0;
   return CPALS_OK;

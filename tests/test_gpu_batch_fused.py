@@ -82,7 +82,7 @@ def test_batch_one_launch_per_stage(probs):
 
 
 def test_batch_autotuner_cache_and_results(probs):
-    """The first run times both tile shapes of the two ALS contraction
+    """The first run times the three tile shapes of the four contraction
     stages; a second batch of the same shapes takes the cached choice
     without timing.  The tile shape does not change any sum's order, so
     both batches give bit-identical results."""
@@ -93,7 +93,8 @@ def test_batch_autotuner_cache_and_results(probs):
     with _batch(sub, "fp32") as b:
         rb = b.run(8, EPS)
         tb = b.tiles()
-    assert all(t in (0, 1) for t in ta["tiles"]) and tb["tiles"] == ta["tiles"]
+    assert len(ta["tiles"]) == 4 and all(t in (0, 1, 2) for t in ta["tiles"]) and tb["tiles"] == ta["tiles"]
+    assert all(m > 0 for m in ta["ms"])
     assert tb["from_cache"]
     assert np.array_equal(ra["fitness"], rb["fitness"])
     for x, y in zip(ra["trace"], rb["trace"]):
