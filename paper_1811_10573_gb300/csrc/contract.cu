@@ -569,12 +569,23 @@ void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int6
 
 int gemm_simt_wave_splits(int64_t batch, int64_t K, int64_t M, int R, bool kmajor, size_t esz,
                           int64_t cap) {
-  if (esz != 8 || R <= 32 || gemm_simt_bm(M, R, kmajor) != 64) return 0;
+  if (esz != 8) return 0;
   int nsm = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
     cudaGetLastError();
     return 0;
+  }
+  if (R <= 32 || gemm_simt_bm(M, R, kmajor) != 64) {
+    // small float64 contractions: a CTA's time is its tile times its K chunk
+    // on one SM's FP64 pipe, so split K until every SM has a CTA, down to
+    // one 16-wide K step per split
+    const int64_t tiles = cdiv(M, gemm_simt_bm(M, R, kmajor)) * batch;
+    if (tiles >= nsm) return 1;
+    int64_t sp = std::min<int64_t>(cdiv(nsm, tiles), cdiv(K, 16));
+    sp = std::min<int64_t>(sp, cap / std::max<int64_t>(1, batch * M * R));
+    while (sp > 1 && cdiv(K, cdiv(cdiv(K, sp), 16) * 16) != sp) sp--;
+    return (int)std::max<int64_t>(sp, 1);
   }
   const int occ = kmajor ? exact_cols_occ_for<double, true>(R) : exact_cols_occ_for<double, false>(R);
   const int64_t wave = (int64_t)occ * nsm;
