@@ -156,15 +156,39 @@ __device__ CtShape<T> ct_shape(int stage, const BI& b, const BC& c, T* tp, bool 
 
 // Output tiles of BM rows x 16 NQ columns (NQ = ceil(R / 16), chosen per
 // instance, so an instance pays for at most 15 padded columns), 256 threads,
-// TM x NQ outputs per thread (rows tm + 16 i, columns tn + 16 j); a work unit
+// TM x NQ outputs per thread (rows tm TM + i, columns tn NQ + j, read from
+// shared memory as vectors); a work unit
 // is (batch entry, row tile, K split); the CTAs of an instance take its
 // units in turn, those of an instance not in this stage return at once.  The
 // next K tile is fetched into registers while the current one is multiplied
 // from shared memory.  Three row-tile shapes (the autotuner picks one per
 // stage and batch): BM = 64 (TM = 4), 128 (TM = 8) or 32 (TM = 2).
+// N consecutive T from shared memory in 16- or 8-byte loads where the size
+// allows (p aligned to the load size: the callers' row strides and offsets
+// are multiples of it).
+template <typename T, int N>
+__device__ __forceinline__ void lds_vec(const T* p, T (&v)[N]) {
+  if constexpr ((N * sizeof(T)) % 16 == 0) {
+    constexpr int W = 16 / sizeof(T);
+#pragma unroll
+    for (int q = 0; q < N / W; q++) {
+      const int4 x = reinterpret_cast<const int4*>(p)[q];
+      memcpy(&v[q * W], &x, 16);
+    }
+  } else if constexpr (N * sizeof(T) == 8) {
+    const int2 x = *reinterpret_cast<const int2*>(p);
+    memcpy(&v[0], &x, 8);
+  } else {
+#pragma unroll
+    for (int q = 0; q < N; q++) v[q] = p[q];
+  }
+}
+
+constexpr int kXPad = 4;           // row padding of the staged X tile (keeps 16-byte row alignment)
+
 template <typename T, int BM, int TM, int NQ, bool KM>
 __device__ __forceinline__ void bgemm_units(const CtShape<T>& sh, const T* __restrict__ Xbase, int R,
-                                            T (*Xs)[BM + 1], T (*Bs)[64]) {
+                                            T (*Xs)[BM + kXPad], T (*Bs)[64]) {
   constexpr int BK = 16, BN = 16 * NQ;
   constexpr int XL = BK * BM / kBT;              // X elements a thread stages per K tile
   constexpr int BL = (BK * BN + kBT - 1) / kBT;  // B elements a thread stages per K tile
@@ -225,10 +249,8 @@ __device__ __forceinline__ void bgemm_units(const CtShape<T>& sh, const T* __res
 #pragma unroll
       for (int k = 0; k < BK; k++) {
         T av[TM], bv[NQ];
-#pragma unroll
-        for (int i = 0; i < TM; i++) av[i] = Xs[k][tm + 16 * i];
-#pragma unroll
-        for (int j = 0; j < NQ; j++) bv[j] = Bs[k][tn + 16 * j];
+        lds_vec<T, TM>(&Xs[k][tm * TM], av);
+        lds_vec<T, NQ>(&Bs[k][tn * NQ], bv);
 #pragma unroll
         for (int i = 0; i < TM; i++)
 #pragma unroll
@@ -238,11 +260,11 @@ __device__ __forceinline__ void bgemm_units(const CtShape<T>& sh, const T* __res
     T* o = sh.out + (z * sh.batch + bb) * sh.M * R;
 #pragma unroll
     for (int i = 0; i < TM; i++) {
-      const int64_t m = m0 + tm + 16 * i;
+      const int64_t m = m0 + tm * TM + i;
       if (m >= sh.M) continue;
 #pragma unroll
       for (int j = 0; j < NQ; j++) {
-        const int r = tn + 16 * j;
+        const int r = tn * NQ + j;
         if (r < R) o[m * R + r] = acc[i][j];
       }
     }
@@ -250,7 +272,7 @@ __device__ __forceinline__ void bgemm_units(const CtShape<T>& sh, const T* __res
 }
 
 template <typename T, int BM, int TM, bool KM>
-__device__ __forceinline__ void bgemm_nq(const CtShape<T>& sh, const T* X, int R, T (*Xs)[BM + 1],
+__device__ __forceinline__ void bgemm_nq(const CtShape<T>& sh, const T* X, int R, T (*Xs)[BM + kXPad],
                                          T (*Bs)[64]) {
   switch ((R + 15) >> 4) {
     case 1: bgemm_units<T, BM, TM, 1, KM>(sh, X, R, Xs, Bs); break;
@@ -261,13 +283,13 @@ __device__ __forceinline__ void bgemm_nq(const CtShape<T>& sh, const T* X, int R
 }
 
 template <typename T, int BM, int TM>
-__global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? (BM == 128 ? 2 : 3) : 1) bgemm_kernel(BParams P, int stage, T* __restrict__ tp) {
+__global__ void __launch_bounds__(kBT, sizeof(T) == 4 ? (BM == 32 ? 3 : 2) : 1) bgemm_kernel(BParams P, int stage, T* __restrict__ tp) {
   const BI b = P.bi[blockIdx.y];
   const BC c = P.ctl[blockIdx.y];
   const CtShape<T> sh = ct_shape<T>(stage, b, c, tp, P.force != 0);
   if (!sh.act) return;
-  __shared__ T Xs[16][BM + 1];
-  __shared__ T Bs[16][64];
+  __shared__ __align__(16) T Xs[16][BM + kXPad];
+  __shared__ __align__(16) T Bs[16][64];
   if (sh.kmajor) bgemm_nq<T, BM, TM, true>(sh, tp + b.x, b.R, Xs, Bs);
   else bgemm_nq<T, BM, TM, false>(sh, tp + b.x, b.R, Xs, Bs);
 }
