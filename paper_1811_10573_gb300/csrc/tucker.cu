@@ -636,10 +636,14 @@ namespace {
 
 // out = in x_mode B for the layouts of the file comment (gemm_simt: K-major
 // contracts the trailing index, MN-major a leading or middle one); K is split
-// so that the grid covers the SMs at least twice
+// so that the grid covers the SMs at least twice.  Batched MN-major calls
+// with M, R <= 48 take bsmall_kernel: the rank-kept second-level TTMs and PP
+// terms, and also a first-level TTM of X whose trailing mode is at most 48
+// (exact outputs, no padded FMAs, one CTA per batch entry).
 void gemm(cpals_tucker* t, const double* in, const double* B, double* out, int64_t batch, int64_t K,
           int64_t M, int R, bool kmajor) {
-  if (!kmajor && batch > 1 && M <= kTuckerMaxRank && R <= kTuckerMaxRank && batch < (1ll << 31)) {
+  if (!kmajor && batch > 1 && M <= kTuckerMaxRank && R <= kTuckerMaxRank && batch < (1ll << 31) &&
+      K < (1ll << 31)) {
     bsmall_kernel<<<(unsigned)batch, 256, 0, t->stream>>>(in, B, (int)K, (int)M, R, out);
     t->launches++;
     return;
