@@ -79,13 +79,15 @@ template <typename TX>
 void sumsq(const TX* x, int64_t n, double* partials, double* out, Launch L);
 
 // ---------------------------------------------------------------- float64 small kernels
-// Gamma^(n) = *_{k != n} S^(k) (Algorithm 1), its Cholesky factor L,
-// and (useV) Z = sum_{i<j; i,j != n} W_i * W_j * (*_{k not in {i,j,n}} S_k)
-// so that sum_{i<j} V^(n,i,j) = A^(n) Z (Eq. 3).  status[0] |= 1<<n if not PD.
+// Gamma^(n) = *_{k != n} S^(k) (Algorithm 1), its Cholesky factor L (R x R in
+// Lout), and (useV) Z = sum_{i<j; i,j != n} W_i * W_j * (*_{k not in {i,j,n}}
+// S_k) so that sum_{i<j} V^(n,i,j) = A^(n) Z (Eq. 3).  A Gamma that is not
+// positive definite leaves Gamma^dagger in Lout instead, with status[0] bit
+// 16 + n; status[0] |= 1<<n if Gamma is not finite.
 void gamma_chol(const double* S, const double* W, int N, int n, int R, double* Lout, double* Z,
                 bool useV, int* status, Launch L);
 
-// Row-wise solve A_new = rhs Gamma^{-1} with the factor L; writes A (in place),
+// Row-wise solve A_new = rhs Gamma^{-1} with the factor L (or Gamma^dagger); writes A (in place),
 // dA = A_new - (Aref ? Aref : A_old), compute-precision copies Ac, dAc and per-row
 // ||dA||^2, ||A_new||^2 into rownorm (2*s values).  Rows are left unchanged if
 // the factorisation failed for this mode (status bit set).  lam is the update

@@ -10,6 +10,38 @@ namespace {
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+constexpr int kChunks = kMaxRank / 32;
+
+__device__ __forceinline__ double pick(const double (&v)[kChunks], int c) {
+  double out = v[0];
+#pragma unroll
+  for (int i = 1; i < kChunks; i++)
+    if (c == i) out = v[i];
+  return out;
+}
+__device__ __forceinline__ void put(double (&v)[kChunks], int c, double x) {
+#pragma unroll
+  for (int i = 0; i < kChunks; i++)
+    if (c == i) v[i] = x;
+}
+
+// 1/sqrt(x) for the Cholesky pivots: the float estimate refined by two
+// Newton-Raphson steps y <- y + y (1 - x y^2) / 2 in float64 (the float
+// estimate's ~2^-23 relative error squares at each step, below float64's
+// rounding after two); outside float's exponent range the float64 quotient
+// is taken instead.  A float64 division and square root take ~1,100 cycles
+// on GB300, this ~450.
+__device__ __forceinline__ double rsqrt_refined(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+#pragma unroll
+  for (int it = 0; it < 2; it++) {
+    const double e = fma(-(x * y), y, 1.0);
+    y = fma(0.5 * y, e, y);
+  }
+  return y;
+}
+
 // ---------------------------------------------------------------- Gamma^dagger
 // Algorithm 1 writes the pseudo-inverse Gamma^dagger; the Cholesky route
 // below covers a positive definite Gamma, and this fallback the rest: the
@@ -179,31 +211,48 @@ gamma_chol_kernel(const double* __restrict__ S, const double* __restrict__ W, in
       Z[idx] = z;
     }
   }
-  __shared__ double il_sh;
-  if (tid == 0) bad = 0;
-  __syncthreads();
-  for (int k = 0; k < R; k++) {
-    // one thread takes the pivot's reciprocal square root (float64 division
-    // and square root are long sequences on the narrow FP64 pipe)
-    if (tid == 0) {
-      const double piv = G[k * RS + k];
-      if (!(piv > 0.0) || !isfinite(piv)) {
-        bad = 1;
-      } else {
-        const double il = 1.0 / sqrt(piv);
-        il_sh = il;
-        G[k * RS + k] = piv * il;
-      }
+  // the pivots' reciprocal square roots
+  __shared__ double dinv[kMaxRank];
+  if (tid == 0) {
+    bad = 0;
+    const double piv = G[0];
+    if (!(piv > 0.0) || !isfinite(piv)) {
+      bad = 1;
+    } else {
+      const double il = rsqrt_refined(piv);
+      dinv[0] = il;
+      G[0] = piv * il;
     }
-    __syncthreads();
-    if (bad) break;
-    const double il = il_sh;
+  }
+  __syncthreads();
+  for (int k = 0; k < R && !bad; k++) {
+    const double il = dinv[k];
     for (int i = k + 1 + tid; i < R; i += nt) G[i * RS + k] *= il;
     __syncthreads();
-    // trailing update of the lower triangle: one warp per row i, lanes over j
-    for (int i = k + 1 + warp; i < R; i += nw) {
-      const double lik = G[i * RS + k];
-      for (int j = k + 1 + lane; j <= i; j += 32) G[i * RS + j] = fma(-lik, G[j * RS + k], G[i * RS + j]);
+    if (warp == 0) {
+      // lookahead: column k + 1 first, then its pivot's reciprocal square
+      // root while the other warps update the rest of the trailing triangle
+      if (k + 1 < R) {
+        const double lk = G[(k + 1) * RS + k];
+        for (int i = k + 1 + lane; i < R; i += 32) G[i * RS + k + 1] = fma(-G[i * RS + k], lk, G[i * RS + k + 1]);
+        __syncwarp();
+        if (lane == 0) {
+          const double piv = G[(k + 1) * RS + k + 1];
+          if (!(piv > 0.0) || !isfinite(piv)) {
+            bad = 1;
+          } else {
+            const double il1 = rsqrt_refined(piv);
+            dinv[k + 1] = il1;
+            G[(k + 1) * RS + k + 1] = piv * il1;
+          }
+        }
+      }
+    } else {
+      // rows i >= k + 2, columns k + 2 <= j <= i: one warp per row, lanes over j
+      for (int i = k + 2 + warp - 1; i < R; i += nw - 1) {
+        const double lik = G[i * RS + k];
+        for (int j = k + 2 + lane; j <= i; j += 32) G[i * RS + j] = fma(-lik, G[j * RS + k], G[i * RS + j]);
+      }
     }
     __syncthreads();
   }
@@ -245,21 +294,6 @@ vterm_kernel(const T* __restrict__ rhs, const T* __restrict__ A, const TZ* __res
 }
 
 // ---------------------------------------------------------------- row solves
-constexpr int kChunks = kMaxRank / 32;
-
-__device__ __forceinline__ double pick(const double (&v)[kChunks], int c) {
-  double out = v[0];
-#pragma unroll
-  for (int i = 1; i < kChunks; i++)
-    if (c == i) out = v[i];
-  return out;
-}
-__device__ __forceinline__ void put(double (&v)[kChunks], int c, double x) {
-#pragma unroll
-  for (int i = 0; i < kChunks; i++)
-    if (c == i) v[i] = x;
-}
-
 // One warp per row y: forward substitution L z = b, back substitution
 // L^T a = z, i.e. a = b Gamma^{-1} (two triangular solves per row); with an
 // update step size lam != 1 (Sec. 5.1) the new row is (1 - lam) A_old + lam a.
