@@ -1536,9 +1536,7 @@ cpals_status cpals_batch_create(int n, const int64_t* dims, const int* ranks, in
     return CPALS_E_CUDA;
   }
   if (!(prop.major == 10 && prop.minor == 3)) return CPALS_E_UNSUPPORTED;
-  if (cudaFuncSetAttribute(bsolve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)bsolve_smem<float>()) != cudaSuccess ||
-      cudaFuncSetAttribute(bsolve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(bsolve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bsolve_smem<double>()) != cudaSuccess ||
       cudaFuncSetAttribute(bsolve_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bsolve_df_smem()) != cudaSuccess) {
