@@ -379,10 +379,14 @@ cpals_status cpals_get_state(cpals_ctx* ctx, int which, int n, double* out);
 cpals_status cpals_set_controller(cpals_ctx* ctx, const float* params, int nparams, double confidence);
 
 /* Like cpals_run, with each next sweep chosen by the installed controller
- * (the eps rule where it stands in, or everywhere when none is installed).
+ * (the rule of cpals_run -- the eps test and, when set, the stopping test --
+ * where it stands in, or everywhere when none is installed).
  * source_trace[t] (may be NULL) is 1 where the network decided, 0 where the
  * rule did.  The reported fitness follows cpals_run (a PP estimate after PP
- * sweeps, confirmed exactly when it reaches the target). */
+ * sweeps, confirmed exactly when it reaches the target).  With the device
+ * loop on (the default), the history, features and forward pass run in the
+ * loop's decide kernel, one host synchronisation per run; otherwise one per
+ * sweep. */
 cpals_status cpals_run_controlled(cpals_ctx* ctx, int max_sweeps, double eps, int use_V,
                                   double target, double* fitness_trace, int* kind_trace,
                                   double* time_trace, int* source_trace, int* n_done,
@@ -402,6 +406,23 @@ cpals_status cpals_run_controlled(cpals_ctx* ctx, int max_sweeps, double eps, in
  * of about their size is kept by the context). */
 cpals_status cpals_controller_log(cpals_ctx* ctx, int steps, double eps, int use_V, float* features,
                                   int* labels, double* gains, double* costs, int* n_out);
+
+/* The input (CPALS_CTRL_FEATURES floats) and output probabilities (3) of
+ * the controller's last decision in the last cpals_run_controlled (device or
+ * host loop).  Each pointer nullable; CPALS_E_STATE before any controlled
+ * decision. */
+cpals_status cpals_controller_last(const cpals_ctx* ctx, float* features, float* probs);
+
+/* Labels of cpals_controller_log by the time to a target fitness instead of
+ * the four-sweep gain per second: with target > 0 each candidate action is
+ * followed by Algorithm 3's rule (eps test, stopping test, PP estimates at
+ * the target confirmed by the exact fitness) until the fitness reaches
+ * target or max_rollout sweeps have run; the label is the candidate with the
+ * shorter time to the target, else (neither reached it) the one with the
+ * higher exact fitness at the end of its trial.  gains/costs then hold the
+ * trial's fitness gain and duration.  target = 0 restores the default
+ * labels.  CPALS_E_INVALID for target < 0 or, with a target, max_rollout < 1. */
+cpals_status cpals_set_controller_labels(cpals_ctx* ctx, double target, int max_rollout);
 
 /* Full-batch Adam training of the controller on n logged samples (host
  * arrays: X [n][CPALS_CTRL_FEATURES], labels y in {0,1,2}, sample weights

@@ -89,6 +89,8 @@ _SIGS = {
     "cpals_tucker_cost_model": (C.c_int, [_i64p, _ip, C.c_int, _dp]),
     "cpals_run_controlled": (C.c_int, [_ctx_p, C.c_int, C.c_double, C.c_int, C.c_double, _dp,
                                        _ip, _dp, _ip, _ip, _ip]),
+    "cpals_set_controller_labels": (C.c_int, [_ctx_p, C.c_double, C.c_int]),
+    "cpals_controller_last": (C.c_int, [_ctx_p, _fp, _fp]),
     "cpals_controller_log": (C.c_int, [_ctx_p, C.c_int, C.c_double, C.c_int, _fp, _ip, _dp, _dp,
                                        _ip]),
     "cpals_mlp_train": (C.c_int, [_fp, _ip, _fp, C.c_int, _fp, C.c_int, C.c_int, C.c_double,
@@ -233,6 +235,14 @@ def cpals_run_controlled(ctx, max_sweeps, eps, use_V, target, ftrace, ktrace, tt
                          n_done, reached):
     return lib().cpals_run_controlled(ctx, max_sweeps, eps, use_V, target, ftrace, ktrace, ttrace,
                                       strace, n_done, reached)
+
+
+def cpals_controller_last(ctx, features, probs):
+    return lib().cpals_controller_last(ctx, features, probs)
+
+
+def cpals_set_controller_labels(ctx, target, max_rollout):
+    return lib().cpals_set_controller_labels(ctx, target, max_rollout)
 
 
 def cpals_controller_log(ctx, steps, eps, use_V, features, labels, gains, costs, n_out):
@@ -475,6 +485,18 @@ class CPALS:
         n = nd.value
         return {"fitness": ft[:n], "kinds": [SWEEP_KINDS[int(k)] for k in kt[:n]],
                 "times": tt[:n], "learned": st[:n].astype(bool), "reached": bool(rc.value)}
+
+    def controller_last(self):
+        """Input and output of the controller's last decision (cpals_controller_last)."""
+        x = np.zeros(CTRL_FEATURES, dtype=np.float32)
+        pr = np.zeros(3, dtype=np.float32)
+        self._ck(cpals_controller_last(self.ctx, _fptr(x), _fptr(pr)))
+        return x, pr
+
+    def set_controller_labels(self, target, max_rollout=0):
+        """Label the controller log by the time to `target` (0: four-sweep
+        gain per second); cpals_set_controller_labels."""
+        self._ck(cpals_set_controller_labels(self.ctx, float(target), int(max_rollout)))
 
     def controller_log(self, steps, eps, use_V=True):
         """Self-generated training log (cpals_controller_log)."""

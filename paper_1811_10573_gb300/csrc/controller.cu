@@ -12,6 +12,7 @@
 // stores its hidden activations and output/hidden deltas, a second kernel
 // gives each parameter its gradient as a sum over the samples in index order
 // (deterministic) and applies the Adam step.
+#include "ctrl_dev.cuh"
 #include "internal.h"
 
 namespace cpals {
@@ -20,6 +21,7 @@ namespace {
 
 constexpr int H = kCtrlHidden;
 constexpr int C = kCtrlClasses;
+static_assert(H == 32 && C == 3 && kCtrlFeatures == 20, "mlp_probs and ctrl_features are written for 20-32-3");
 
 struct Params {
   const float* W1;
@@ -32,34 +34,13 @@ __device__ __forceinline__ Params view(const float* p, int F) {
   return {p, p + H * F, p + H * F + H, p + H * F + H + C * H};
 }
 
-// out[i][c] = softmax(W2 relu(W1 x_i + b1) + b2)
+// out[i][c] = softmax(W2 relu(W1 x_i + b1) + b2) (the device loop's decide
+// kernel takes the same forward pass, mlp_probs)
 __global__ void mlp_forward_kernel(const float* __restrict__ params, int F,
                                    const float* __restrict__ X, int n, float* __restrict__ probs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const Params P = view(params, F);
-  const float* x = X + (size_t)i * F;
-  float h[H];
-#pragma unroll 4
-  for (int j = 0; j < H; j++) {
-    float a = P.b1[j];
-    for (int k = 0; k < F; k++) a = fmaf(P.W1[j * F + k], x[k], a);
-    h[j] = fmaxf(a, 0.f);
-  }
-  float z[C], zmax = -3.4e38f;
-  for (int c = 0; c < C; c++) {
-    float a = P.b2[c];
-#pragma unroll 4
-    for (int j = 0; j < H; j++) a = fmaf(P.W2[c * H + j], h[j], a);
-    z[c] = a;
-    zmax = fmaxf(zmax, a);
-  }
-  float s = 0.f;
-  for (int c = 0; c < C; c++) {
-    z[c] = __expf(z[c] - zmax);
-    s += z[c];
-  }
-  for (int c = 0; c < C; c++) probs[(size_t)i * C + c] = z[c] / s;
+  mlp_probs(params, F, X + (size_t)i * F, probs + (size_t)i * C);
 }
 
 // per sample: hidden activations, output delta w_i (p - onehot(y_i)) and

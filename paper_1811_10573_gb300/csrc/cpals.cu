@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/cpals.h"
+#include "ctrl_dev.cuh"
 #include "internal.h"
 
 using namespace cpals;
@@ -136,6 +137,9 @@ struct cpals_ctx {
   // the sweep kinds, its state and traces in device memory
   bool device_loop = true;
   double pp_stop_tol = 0.0;                // Algorithm 3's stopping test inside PP runs (0: off)
+  double label_target = 0.0;               // controller log: label by the time to this fitness (0: off)
+  bool ctrl_last_dev = false;              // the last controlled run took its decisions in the device loop
+  int label_rollout = 0;                   // controller log: sweep cap of a trial to the target
   cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};
   int64_t loop_count[2][4] = {{0}};        // kernels per branch (launch accounting)
   void* loop_state = nullptr;              // LoopState (device)
@@ -823,7 +827,6 @@ cpals_status snapshot_restore(cpals_ctx* c) {
 }
 
 // ---------------------------------------------------------------- controller features
-enum { ACT_PP = 0, ACT_ALS = 1, ACT_REBUILD = 2 };
 constexpr int kCtrlHorizon = 4;   // sweeps per trial in the controller log
 
 struct CtrlHist {
@@ -929,6 +932,14 @@ struct LoopState {
   double f_last, f_prev;   // fitness the algorithm saw after the last two sweeps
   int in_run;       // PP sweeps of the current PP run up to the last sweep (0 after ALS)
   unsigned long long t0;
+  // learned controller (cpals_run_controlled): on/off, confidence,
+  // parameters, its history, whether it took the next decision
+  int ctrl;
+  int src_next;
+  double conf;
+  const float* params;
+  CtrlState ch;
+  float last_x[20], last_p[3];   // the controller's last input and output
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -944,6 +955,33 @@ __device__ bool loop_all_small(const LoopState* s, const double* scal) {
   return true;
 }
 
+// The learned controller's decision (as cpals_run_controlled's host loop):
+// the network's most probable action when its probability reaches the
+// confidence and it is not a PP sweep without valid operators, else the
+// rule's branch; returns the branch (0 ALS, 1 rebuild + PP, 2 PP).
+__device__ int loop_ctrl_choose(LoopState* s, const double* scal, int rule_branch) {
+  // the history and the 8 + 2N scalars the features use, as local copies
+  // (features computed through the LoopState and scalar pointers directly
+  // came out as those of the run's first decision in this kernel)
+  float x[20], pr[3];
+  const CtrlState h = s->ch;
+  double sc[8 + 2 * kMaxModes];
+  for (int i = 0; i < 8 + 2 * s->N; i++) sc[i] = scal[i];
+  ctrl_features(h, sc, s->N, s->eps, x);
+  mlp_probs(s->params, 20, x, pr);
+  for (int i = 0; i < 20; i++) s->last_x[i] = x[i];
+  for (int i = 0; i < 3; i++) s->last_p[i] = pr[i];
+  int best = 0;
+  for (int k = 1; k < 3; k++)
+    if (pr[k] > pr[best]) best = k;
+  s->src_next = 0;
+  if (pr[best] >= s->conf && !(best == ACT_PP && !s->ch.pp_ready)) {
+    s->src_next = 1;
+    return best == ACT_ALS ? 0 : (best == ACT_REBUILD ? 1 : 2);
+  }
+  return rule_branch;
+}
+
 __global__ void loop_init_kernel(LoopState* s, const double* scal, cudaGraphConditionalHandle hw,
                                  cudaGraphConditionalHandle hs) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -954,6 +992,11 @@ __global__ void loop_init_kernel(LoopState* s, const double* scal, cudaGraphCond
   s->f_last = s->f_prev = -1e300;
   s->in_run = 0;
   s->next = loop_all_small(s, scal) ? 1 : 0;   // the test at the head of the first sweep
+  s->src_next = 0;
+  if (s->ctrl) {
+    ctrl_state_start(s->ch, scal[0]);
+    s->next = loop_ctrl_choose(s, scal, s->next);
+  }
   s->t0 = global_ns();
   cudaGraphSetConditional(hs, (unsigned)s->next);
   cudaGraphSetConditional(hw, s->max_sweeps > 0 ? 1u : 0u);
@@ -970,12 +1013,13 @@ __global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* 
   auto record = [&](int kind, double fv) {
     const int t = s->t;
     ftr[t] = fv;
-    ktr[t] = kind;
+    ktr[t] = kind | (s->src_next << 4);        // bit 4: the learned controller chose this sweep
     ttr[t] = (double)(global_ns() - s->t0) * 1e-9;
     s->t = t + 1;
     s->f_prev = s->f_last;
     s->f_last = fv;
     s->in_run = kind == 0 ? 0 : (kind == 1 ? 1 : s->in_run + 1);
+    if (s->ctrl) ctrl_push(s->ch, scal, s->N, kind == 0 ? ACT_ALS : (kind == 1 ? ACT_REBUILD : ACT_PP), fv);
   };
   bool stop = false;
   if (ran == 3) {
@@ -1023,6 +1067,7 @@ __global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* 
   // last PP sweep for a gain of tol over the one before it
   const bool gain = !(s->tol > 0.0) || s->in_run < 2 || s->f_last - s->f_prev >= s->tol;
   s->next = ran != 0 ? ((small && gain) ? 2 : 0) : (small ? 1 : 0);
+  if (s->ctrl) s->next = loop_ctrl_choose(s, scal, s->next);
   cudaGraphSetConditional(hs, (unsigned)s->next);
   cudaGraphSetConditional(hw, 1u);
 }
@@ -1119,7 +1164,7 @@ cpals_status loop_build(cpals_ctx* c, int slot, bool useV) {
 // Algorithm 3 with every decision on the device; one synchronisation at the end.
 cpals_status run_device_loop(cpals_ctx* c, int max_sweeps, double eps, bool useV, double target,
                              double* fitness_trace, int* kind_trace, double* time_trace, int* n_done,
-                             int* reached) {
+                             int* reached, bool controlled = false, int* source_trace = nullptr) {
   if (max_sweeps > c->loop_cap) {
     // larger traces: the graphs hold the trace pointers
     for (int i = 0; i < 2; i++)
@@ -1156,6 +1201,9 @@ cpals_status run_device_loop(cpals_ctx* c, int max_sweeps, double eps, bool useV
   h->eps = eps;
   h->target = target;
   h->tol = c->pp_stop_tol;
+  h->ctrl = controlled && c->ctrl_on ? 1 : 0;
+  h->conf = c->ctrl_conf;
+  h->params = c->ctrl_params;
   CK(cudaMemcpyAsync(c->loop_state, h, sizeof(LoopState), cudaMemcpyHostToDevice, c->stream));
   CK(cudaGraphLaunch(c->loop_exec[slot], c->stream));
   CK(cudaMemcpyAsync(h, c->loop_state, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
@@ -1172,11 +1220,13 @@ cpals_status run_device_loop(cpals_ctx* c, int max_sweeps, double eps, bool useV
   }
   int64_t l = 1 + ((int64_t)t + h->confirms) + h->confirms * c->loop_count[slot][3];
   for (int i = 0; i < t; i++) {
-    l += c->loop_count[slot][kt[i] == CPALS_SWEEP_ALS ? 0 : (kt[i] == CPALS_SWEEP_PP_INIT ? 1 : 2)];
-    if (kt[i] == CPALS_SWEEP_PP_INIT) c->ops_built = true;
+    const int kind = kt[i] & 0xf;
+    l += c->loop_count[slot][kind == CPALS_SWEEP_ALS ? 0 : (kind == CPALS_SWEEP_PP_INIT ? 1 : 2)];
+    if (kind == CPALS_SWEEP_PP_INIT) c->ops_built = true;
     if (fitness_trace) fitness_trace[i] = ft[i];
-    if (kind_trace) kind_trace[i] = kt[i];
+    if (kind_trace) kind_trace[i] = kind;
     if (time_trace) time_trace[i] = tt[i];
+    if (source_trace) source_trace[i] = (kt[i] >> 4) & 1;
   }
   c->launches += l;
   if (n_done) *n_done = t;
@@ -1660,17 +1710,35 @@ cpals_status cpals_run_controlled(cpals_ctx* c, int max_sweeps, double eps, int 
   CKS(ready(c));
   if (max_sweeps < 0 || !(eps > 0)) return c->fail(CPALS_E_INVALID, "max_sweeps < 0 or eps <= 0");
   Join j(c);
+  if (c->device_loop && c->graphs && !c->profiling && max_sweeps > 0 && c->loop_note.empty()) {
+    // the decisions inside the device loop's graph (features, forward pass
+    // and rule in its decide kernel): no host round trip per sweep
+    const std::string saved = c->err;
+    cpals_status st = run_device_loop(c, max_sweeps, eps, use_V != 0, target, fitness_trace, kind_trace,
+                                      time_trace, n_done, reached, true, source_trace);
+    c->ctrl_last_dev = true;
+    if (st != CPALS_E_CUDA || c->loop_exec[use_V ? 0 : 1]) return st;
+    c->loop_note = c->err;
+    c->err = saved;
+    cudaGetLastError();
+  }
+  c->ctrl_last_dev = false;
   const auto t0 = std::chrono::steady_clock::now();
   CtrlHist h;
   int t = 0, hit = 0;
+  double f_last = -1e300, f_prev = -1e300;     // fitness seen after the last two sweeps
+  int in_run = 0;                                // PP sweeps of the current PP run
+  const double tol = c->pp_stop_tol;
   cpals_status st = sync_read(c);
   // the current state: after cpals_init_factors dA = A, so the first sweep is exact
   h.res[0] = 1.0 - c->scal_h[0];
   while (st == CPALS_OK && t < max_sweeps && !hit) {
     // the paper's eps rule (Algorithm 3): stay in / enter the PP phase while
-    // every ||dA|| < eps ||A||
+    // every ||dA|| < eps ||A|| (and, with a stopping tolerance, while the PP
+    // run still gains, as in cpals_run)
     const bool small = all_small(c, eps);
-    const int rule = h.pp_ready ? (small ? ACT_PP : ACT_ALS) : (small ? ACT_REBUILD : ACT_ALS);
+    const bool gain = !(tol > 0.0) || in_run < 2 || f_last - f_prev >= tol;
+    const int rule = h.pp_ready ? ((small && gain) ? ACT_PP : ACT_ALS) : (small ? ACT_REBUILD : ACT_ALS);
     int act = rule, src = 0;
     if (c->ctrl_on) {
       ctrl_features(c, h, eps, c->ctrl_io_h);
@@ -1700,6 +1768,9 @@ cpals_status cpals_run_controlled(cpals_ctx* c, int max_sweeps, double eps, int 
     }
     if (target > 0 && f >= target) hit = 1;
     h.push(c, act, f);
+    f_prev = f_last;
+    f_last = f;
+    in_run = act == ACT_ALS ? 0 : (act == ACT_REBUILD ? 1 : in_run + 1);
     if (fitness_trace) fitness_trace[t] = f;
     if (kind_trace)
       kind_trace[t] = act == ACT_ALS ? CPALS_SWEEP_ALS : act == ACT_REBUILD ? CPALS_SWEEP_PP_INIT : CPALS_SWEEP_PP_APPROX;
@@ -1711,6 +1782,34 @@ cpals_status cpals_run_controlled(cpals_ctx* c, int max_sweeps, double eps, int 
   if (n_done) *n_done = t;
   if (reached) *reached = hit;
   return st;
+}
+
+cpals_status cpals_controller_last(const cpals_ctx* c, float* features, float* probs) {
+  if (!c) return CPALS_E_INVALID;
+  const float* x = nullptr;
+  const float* p = nullptr;
+  if (c->ctrl_last_dev && c->loop_state_h) {
+    const LoopState* h = static_cast<const LoopState*>(c->loop_state_h);
+    x = h->last_x;
+    p = h->last_p;
+  } else if (c->ctrl_io_h) {
+    x = c->ctrl_io_h;
+    p = c->ctrl_io_h + 32;
+  } else {
+    return CPALS_E_STATE;
+  }
+  if (features) memcpy(features, x, kCtrlFeatures * sizeof(float));
+  if (probs) memcpy(probs, p, kCtrlClasses * sizeof(float));
+  return CPALS_OK;
+}
+
+cpals_status cpals_set_controller_labels(cpals_ctx* c, double target, int max_rollout) {
+  if (!c) return CPALS_E_INVALID;
+  if (!(target >= 0.0) || (target > 0.0 && max_rollout < 1))
+    return c->fail(CPALS_E_INVALID, "controller labels: target >= 0 and, with a target, max_rollout >= 1");
+  c->label_target = target;
+  c->label_rollout = max_rollout;
+  return CPALS_OK;
 }
 
 cpals_status cpals_controller_log(cpals_ctx* c, int steps, double eps, int use_V, float* features,
@@ -1728,26 +1827,56 @@ cpals_status cpals_controller_log(cpals_ctx* c, int steps, double eps, int use_V
     double f0 = 0;
     st = exact_fitness(c, &f0);
     if (st != CPALS_OK) break;
+    if (c->label_target > 0.0 && f0 >= c->label_target) break;   // the trajectory is at the target
     ctrl_features(c, h, eps, features + (size_t)t * kCtrlFeatures);
-    // candidates over kCtrlHorizon sweeps: PP sweeps against ALS sweeps when
-    // a PP sweep is possible, else rebuild + PP sweep then PP sweeps against
-    // ALS sweeps (a horizon of several sweeps lifts the gains above the
-    // rounding of the fitness)
+    // candidates: a PP sweep when one is possible, else rebuild + PP sweep,
+    // against an ALS sweep
     const int cand[2] = {h.pp_ready ? ACT_PP : ACT_REBUILD, ACT_ALS};
-    const int depth = kCtrlHorizon;
+    const bool to_target = c->label_target > 0.0;
     double rate[3] = {-1e300, -1e300, -1e300};
+    double ttt[3] = {1e300, 1e300, 1e300};     // time to the target (to_target)
+    double fend[3] = {-1e300, -1e300, -1e300};  // exact fitness at the end of the trial
     for (int k = 0; k < 3; k++) {
       gains[(size_t)t * 3 + k] = std::nan("");
       costs[(size_t)t * 3 + k] = std::nan("");
     }
-    st = snapshot_take(c, cand[0] == ACT_REBUILD);
+    // a trial to the target may rebuild the operators later on: save them too
+    st = snapshot_take(c, to_target || cand[0] == ACT_REBUILD);
     for (int k = 0; k < 2 && st == CPALS_OK; k++) {
       if (k > 0) st = snapshot_restore(c);
       if (st != CPALS_OK) break;
       CK(cudaStreamSynchronize(c->stream));
       const auto ta = now();
-      for (int d = 0; d < depth && st == CPALS_OK; d++)
-        st = do_action(c, d == 0 ? cand[k] : (cand[k] == ACT_ALS ? ACT_ALS : ACT_PP), use_V != 0);
+      bool hit = false;
+      if (to_target) {
+        // the candidate, then Algorithm 3's rule (as the host loop of
+        // cpals_run) until the target or label_rollout sweeps
+        int act = cand[k], in_run = 0;
+        double fl = -1e300, fp = -1e300;
+        const double tol = c->pp_stop_tol;
+        for (int d = 0; d < c->label_rollout && st == CPALS_OK; d++) {
+          st = do_action(c, act, use_V != 0);
+          if (st != CPALS_OK) break;
+          double f = c->scal_h[0];
+          if (act != ACT_ALS && f >= c->label_target) st = exact_fitness(c, &f);   // confirm (Sec. 5)
+          if (st != CPALS_OK) break;
+          if (f >= c->label_target) {
+            hit = true;
+            break;
+          }
+          in_run = act == ACT_ALS ? 0 : (act == ACT_REBUILD ? 1 : in_run + 1);
+          fp = fl;
+          fl = f;
+          const bool small = all_small(c, eps);
+          const bool gain = !(tol > 0.0) || in_run < 2 || fl - fp >= tol;
+          act = act == ACT_ALS ? (small ? ACT_REBUILD : ACT_ALS) : (small && gain ? ACT_PP : ACT_ALS);
+        }
+      } else {
+        // kCtrlHorizon sweeps of the candidate's kind (a horizon of several
+        // sweeps lifts the gains above the rounding of the fitness)
+        for (int d = 0; d < kCtrlHorizon && st == CPALS_OK; d++)
+          st = do_action(c, d == 0 ? cand[k] : (cand[k] == ACT_ALS ? ACT_ALS : ACT_PP), use_V != 0);
+      }
       const double dt = std::chrono::duration<double>(now() - ta).count();
       if (st == CPALS_E_SINGULAR) {
         // a trial that breaks down (Gamma not positive definite) loses
@@ -1760,11 +1889,22 @@ cpals_status cpals_controller_log(cpals_ctx* c, int steps, double eps, int use_V
       gains[(size_t)t * 3 + cand[k]] = f - f0;
       costs[(size_t)t * 3 + cand[k]] = dt;
       rate[cand[k]] = (f - f0) / std::max(dt, 1e-9);
+      fend[cand[k]] = f;
+      if (hit) ttt[cand[k]] = dt;
     }
     if (st != CPALS_OK) break;
-    // label: the larger fitness gain per second (ties and breakdowns of the
-    // PP candidate to the exact sweep)
-    const int label = rate[cand[0]] > rate[ACT_ALS] && gains[(size_t)t * 3 + cand[0]] > 0 ? cand[0] : ACT_ALS;
+    int label;
+    if (to_target) {
+      // the shorter time to the target; if neither trial reached it, the
+      // higher fitness at the end of the trial (ties to the exact sweep)
+      const bool any = ttt[cand[0]] < 1e300 || ttt[ACT_ALS] < 1e300;
+      label = any ? (ttt[cand[0]] < ttt[ACT_ALS] ? cand[0] : ACT_ALS)
+                  : (fend[cand[0]] > fend[ACT_ALS] ? cand[0] : ACT_ALS);
+    } else {
+      // the larger fitness gain per second (ties and breakdowns of the PP
+      // candidate to the exact sweep)
+      label = rate[cand[0]] > rate[ACT_ALS] && gains[(size_t)t * 3 + cand[0]] > 0 ? cand[0] : ACT_ALS;
+    }
     labels[t] = label;
     // continue the trajectory with the labelled action
     st = snapshot_restore(c);

@@ -1,0 +1,116 @@
+// Learned sweep-type controller on the device: its history of the run, its
+// feature vector and the network's forward pass as device functions, so that
+// the decision can be taken inside the device loop of Algorithm 3 (one
+// thread, no host round trip).  The host loop of cpals_run_controlled keeps
+// its own copy of the history and features in cpals.cu; the formulas are the
+// same.  The forward pass is also the body of mlp_forward_kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace cpals {
+
+// actions (the network's classes)
+enum CtrlAction { ACT_PP = 0, ACT_ALS = 1, ACT_REBUILD = 2 };
+
+struct CtrlState {
+  double maxlr[2];        // largest log10 ||dA||/||A|| of the last two sweeps
+  double res[4];          // residual 1 - f of the last four sweeps (newest first; -1: none)
+  int since_build;        // sweeps since the operators were built
+  int pp_ready;           // operators built and only PP sweeps since
+  int last;               // last action (-1: none)
+  int pad;
+};
+
+__host__ __device__ inline void ctrl_state_start(CtrlState& h, double fitness) {
+  h.maxlr[0] = h.maxlr[1] = 0.0;
+  h.res[0] = 1.0 - fitness;
+  h.res[1] = h.res[2] = h.res[3] = -1.0;
+  h.since_build = 0;
+  h.pp_ready = 0;
+  h.last = -1;
+  h.pad = 0;
+}
+
+// after a sweep of kind `action` that left the scalars scal ([8 + 2n]
+// ||dA^(n)||^2, [9 + 2n] ||A^(n)||^2) and the fitness the algorithm saw
+__device__ inline void ctrl_push(CtrlState& h, const double* scal, int N, int action, double fitness) {
+  double m = -12.0;
+  for (int n = 0; n < N; n++) {
+    const double d = sqrt(scal[8 + 2 * n]), a = sqrt(scal[9 + 2 * n]);
+    m = fmax(m, log10(fmax(d / fmax(a, 1e-300), 1e-12)));
+  }
+  h.maxlr[1] = h.maxlr[0];
+  h.maxlr[0] = m;
+  for (int k = 3; k > 0; k--) h.res[k] = h.res[k - 1];
+  h.res[0] = 1.0 - fitness;
+  h.last = action;
+  if (action == ACT_ALS) {
+    h.pp_ready = 0;
+    h.since_build = 0;
+  } else if (action == ACT_REBUILD) {
+    h.pp_ready = 1;
+    h.since_build = 1;
+  } else {
+    h.since_build++;
+  }
+}
+
+// the network's input (F = 20 values, all O(1)): per-mode log10
+// ||dA||/||A|| (padded to 8 modes), the largest one of the two previous
+// sweeps, log10 of the last three residual decreases, sweeps since the
+// operators were built, whether a PP sweep is possible, the last action
+// (one-hot), log10 eps and log10 of the current residual
+__device__ inline void ctrl_features(const CtrlState& h, const double* scal, int N, double eps, float* x) {
+  for (int i = 0; i < 20; i++) x[i] = 0.f;
+  for (int n = 0; n < N && n < 8; n++) {
+    const double d = sqrt(scal[8 + 2 * n]), a = sqrt(scal[9 + 2 * n]);
+    const double lr = log10(fmax(d / fmax(a, 1e-300), 1e-12));
+    x[n] = (float)(fmin(fmax(lr, -12.0), 2.0) / 4.0);
+  }
+  x[8] = (float)(h.maxlr[0] / 4.0);
+  x[9] = (float)(h.maxlr[1] / 4.0);
+  for (int k = 0; k < 3; k++) {
+    const bool have = h.res[k] >= 0 && h.res[k + 1] >= 0;
+    const double dec = have ? fmax(h.res[k + 1] - h.res[k], 1e-16) : 1e-16;
+    x[10 + k] = (float)(log10(dec) / 8.0);
+  }
+  x[13] = (float)(h.pp_ready ? fmin((double)h.since_build, 20.0) / 10.0 : 0.0);
+  x[14] = h.pp_ready ? 1.f : 0.f;
+  if (h.last >= 0) x[15 + h.last] = 1.f;
+  x[18] = (float)(log10(fmax(eps, 1e-12)) / 2.0);
+  x[19] = (float)(log10(fmax(h.res[0] >= 0 ? h.res[0] : 1.0, 1e-16)) / 8.0);
+}
+
+// probs = softmax(W2 relu(W1 x + b1) + b2); parameters W1[H][F], b1[H],
+// W2[C][H], b2[C] with H = 32 hidden units and C = 3 classes
+__device__ inline void mlp_probs(const float* __restrict__ params, int F, const float* x, float* probs) {
+  constexpr int H = 32, C = 3;
+  const float* W1 = params;
+  const float* b1 = W1 + H * F;
+  const float* W2 = b1 + H;
+  const float* b2 = W2 + C * H;
+  float h[H];
+#pragma unroll 4
+  for (int j = 0; j < H; j++) {
+    float a = b1[j];
+    for (int k = 0; k < F; k++) a = fmaf(W1[j * F + k], x[k], a);
+    h[j] = fmaxf(a, 0.f);
+  }
+  float z[C], zmax = -3.4e38f;
+  for (int c = 0; c < C; c++) {
+    float a = b2[c];
+#pragma unroll 4
+    for (int j = 0; j < H; j++) a = fmaf(W2[c * H + j], h[j], a);
+    z[c] = a;
+    zmax = fmaxf(zmax, a);
+  }
+  float s = 0.f;
+  for (int c = 0; c < C; c++) {
+    z[c] = __expf(z[c] - zmax);
+    s += z[c];
+  }
+  for (int c = 0; c < C; c++) probs[c] = z[c] / s;
+}
+
+}  // namespace cpals

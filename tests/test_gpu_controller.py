@@ -82,17 +82,25 @@ def _ctx(p, prec):
     return g
 
 
+@pytest.mark.parametrize("to_target", [False, True], ids=["gain_rate", "time_to_target"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_controller_log_restores_state_between_trials(prec):
+def test_controller_log_restores_state_between_trials(prec, to_target):
     """After the log, the context holds exactly the state reached by applying
     the logged actions one after the other from the start: every trial was
-    undone (factors compared bit for bit)."""
+    undone (factors compared bit for bit), with either label rule (trials to
+    a target fitness run Algorithm 3 after the candidate, operator rebuilds
+    included, and the log ends where the trajectory reaches the target)."""
     p = _problem()
     with _ctx(p, prec) as g:
+        if to_target:
+            f_als = float(g.run(40, 0.0, True, 0.0)["fitness"][-1])
+            g.init_factors(p.A0)
+            g.set_pp_stop_tol(1e-6)
+            g.set_controller_labels(f_als - 1e-6, 40)
         log = g.controller_log(40, 0.1, True)
         A_log = g.get_factors()
     labels = log["labels"]
-    assert len(labels) == 40
+    assert 0 < len(labels) <= 40 if to_target else len(labels) == 40
     assert set(np.unique(labels)) <= {0, 1, 2}
     for t, lab in enumerate(labels):
         assert np.isfinite(log["gains"][t, lab]) and log["costs"][t, lab] > 0
@@ -134,3 +142,48 @@ def test_run_controlled_network_decides():
         out = g.run_controlled(30, 0.1, True, 0.0)
     assert out["kinds"] == ["als"] * 30 and np.all(out["learned"])
     np.testing.assert_array_equal(out["fitness"], ref["fitness"])
+
+
+def _forced(action):
+    """A network whose output bias always names one action (0 PP, 1 ALS,
+    2 rebuild + PP) with probability ~1."""
+    params = np.zeros(cpals.CTRL_PARAMS, dtype=np.float32)
+    b2 = [0.0, 0.0, 0.0]
+    b2[action] = 10.0
+    params[-3:] = b2
+    return params
+
+
+@pytest.mark.parametrize("net", ["always_als", "always_rebuild", "trained"])
+@pytest.mark.parametrize("tol", [0.0, 1e-5])
+def test_controlled_run_device_loop_equals_host_loop(net, tol):
+    """cpals_run_controlled with its decisions in the device loop (history,
+    features and forward pass in the decide kernel) against the host loop:
+    the same sweep kinds, the same learned/rule source of every decision and
+    bit-identical fitness traces and factors, for networks that always name
+    one action (ALS; operator rebuild + PP sweep) and for the committed
+    network, which decides by its features."""
+    p = _problem()
+    params = {"always_als": _forced(1), "always_rebuild": _forced(2)}.get(net)
+    if params is None:
+        params = controller.load()
+        if params is None:
+            pytest.skip("no committed controller parameters")
+    outs, facs = [], []
+    for loop in (True, False):
+        with _ctx(p, "fp64") as g:
+            g.set_pp_stop_tol(tol)
+            g.set_device_loop(loop)
+            g.set_controller(params, 0.6)
+            outs.append(g.run_controlled(60, 0.1, True, 0.0))
+            facs.append(g.get_factors())
+    dev, host = outs
+    assert dev["kinds"] == host["kinds"]
+    assert np.array_equal(dev["learned"], host["learned"])
+    assert np.array_equal(dev["fitness"], host["fitness"])
+    for a, b in zip(*facs):
+        assert np.array_equal(a, b)
+    if net == "always_als":
+        assert dev["kinds"] == ["als"] * 60 and np.all(dev["learned"])
+    if net == "always_rebuild":
+        assert dev["kinds"] == ["pp_init"] * 60 and np.all(dev["learned"])
