@@ -28,7 +28,10 @@ Pinned by ``tests/test_oracle_pins.py`` (brute-force TTMc, exact recovery
 of a tensor of exact multilinear rank, the non-decreasing core norm of HOOI,
 agreement of the Gram eigenvectors with the SVD, exactness of PP at dA = 0
 and its second-order error, and the core estimate a PP sweep returns against
-the exact core minus the order-3 product term of Sec. 3.1.2's expansion).
+the exact core minus the order-3 product term of Sec. 3.1.2's expansion;
+at order 4: brute-force TTMc, the full multilinear expansion of Y^(n) around
+A_p against the PP right-hand side, exact recovery, PP tracking HOOI).
+Every function is written for any order N.
 """
 from __future__ import annotations
 

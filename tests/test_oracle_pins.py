@@ -867,3 +867,73 @@ def test_pp_stop_tolerance_sequence():
             stops += r[t - 1] < eps and not gain_ok
     assert stops >= 1, "no PP run ended on the stopping test"
     assert kinds != tr.kinds
+
+
+# --- Tucker at order N > 3 (Sec. 2.4, Sec. 3.1.2, Sec. 3.2.2 for any N) -------
+
+def test_tucker_ttmc_brute_force_order4():
+    g = np.random.default_rng(71)
+    X = g.standard_normal((3, 2, 4, 3))
+    A = [g.standard_normal((s, r)) for s, r in zip(X.shape, (2, 2, 3, 2))]
+    for n in range(4):
+        Y = TO.ttmc(X, A, n)
+        ref = np.zeros(Y.shape)
+        for idx in itertools.product(*[range(s) for s in X.shape]):
+            for out in itertools.product(*[range(d) for d in Y.shape]):
+                if out[n] != idx[n]:
+                    continue
+                w = X[idx]
+                for k in range(4):
+                    if k != n:
+                        w *= A[k][idx[k], out[k]]
+                ref[out] += w
+        np.testing.assert_allclose(Y, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_pp_tucker_expansion_order4():
+    """Order 4: Y^(n)(A_p + dA) is the sum over every subset S of the other
+    modes of X x_{k in S} dA^(k)T x_{k not in S} A_p^(k)T (multilinearity);
+    Y~^(n) holds the terms with |S| <= 1 (Sec. 3.2.2), so the difference is
+    the sum of the terms with |S| >= 2, written out subset by subset."""
+    g = np.random.default_rng(72)
+    X = g.standard_normal((5, 4, 6, 3))
+    Ap = [np.linalg.qr(g.standard_normal((s, r)))[0] for s, r in zip(X.shape, (2, 3, 2, 2))]
+    ops, Mp = TO.pp_operators(X, Ap)
+    D = [0.1 * g.standard_normal(a.shape) for a in Ap]
+    A = [a + d for a, d in zip(Ap, D)]
+    for n in range(4):
+        others = [k for k in range(4) if k != n]
+        rest = np.zeros_like(Mp[n])
+        for size in (2, 3):
+            for S in itertools.combinations(others, size):
+                T = X
+                for k in others:
+                    T = TO.ttm(T, D[k] if k in S else Ap[k], k)
+                rest = rest + T
+        np.testing.assert_allclose(TO.ttmc(X, A, n) - TO.pp_ttmc(ops, Mp, D, n), rest,
+                                   rtol=1e-10, atol=1e-12)
+        zero = [np.zeros_like(a) for a in Ap]
+        np.testing.assert_allclose(TO.pp_ttmc(ops, Mp, zero, n), TO.ttmc(X, Ap, n), atol=1e-12)
+
+
+def test_tucker_hosvd_recovers_exact_multilinear_rank_order4():
+    p = synth.tucker_problem([9, 8, 7, 6], [3, 2, 2, 3], seed=6, noise=0.0)
+    A = TO.hosvd(p.X, p.R)
+    G = TO.core(p.X, A)
+    normX = float(np.linalg.norm(p.X))
+    assert TO.fitness(normX, G) > 1 - 1e-7
+    np.testing.assert_allclose(TO.reconstruct(G, A), p.X, rtol=0, atol=1e-10 * normX)
+
+
+def test_pp_tucker_als_tracks_hooi_order4():
+    p = synth.tucker_problem([10, 9, 8, 7], [3, 2, 2, 2], seed=7, noise=0.05)
+    A0 = TO.hosvd(p.X, p.R)
+    _, kinds, fit = TO.pp_tucker_als(p.X, A0, 12, eps=0.3)
+    A = [a.copy() for a in A0]
+    normX = float(np.linalg.norm(p.X))
+    als = []
+    for _ in range(12):
+        _, G = TO.als_sweep(p.X, A)
+        als.append(TO.fitness(normX, G))
+    assert "pp_approx" in kinds
+    assert max(abs(a - b) for a, b in zip(fit, als)) < 1e-6
