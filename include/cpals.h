@@ -258,10 +258,13 @@ cpals_status cpals_batch_tiles(const cpals_batch* b, int* tiles, float* ms, int*
 const char* cpals_batch_last_error(const cpals_batch* b);
 
 /* ---- Tucker-ALS and PP-Tucker-ALS (Sec. 2.4, Sec. 3.1.2, Algorithm 4) ----
- * Order-3 tensors, IEEE float64 (first-level TTMs optionally on the tensor
- * cores, cpals_tucker_set_precision), Tucker ranks 1 <= R_n <= min(48, s_n),
- * s_n <= 4096.  Factors are s_n x R_n float64 row-major with orthonormal
- * columns; the core is R_1 x R_2 x R_3 row-major.  Each factor update takes
+ * Tensors of order 3 to 8, IEEE float64 (order 3: first-level TTMs
+ * optionally on the tensor cores, cpals_tucker_set_precision), Tucker ranks
+ * 1 <= R_n <= min(48, s_n), s_n <= 4096.  Factors are s_n x R_n float64
+ * row-major with orthonormal columns; the core is R_1 x ... x R_N row-major.
+ * Order 3 uses a tuned dimension tree; higher orders contract X twice per
+ * HOOI sweep (Y^(1) and X x_1 A_1, then chains of smaller TTMs) and build
+ * the C(N,2) operators from three shared contractions of X.  Each factor update takes
  * the R_n leading eigenvectors of W = Y_(n) Y_(n)^T (Y^(n) the TTMc) in
  * decreasing eigenvalue order, each column signed to a non-negative inner
  * product with the column it replaces; the eigenvectors come from subspace
@@ -277,8 +280,8 @@ const char* cpals_batch_last_error(const cpals_batch* b);
  * non-positive pivot; CPALS_E_TIMEOUT if the tensor-core kernel gave up
  * waiting (mixed precision). */
 typedef struct cpals_tucker cpals_tucker;
-/* dims[0..2], ranks[0..2] (host, read only), N must be 3; *out receives the
- * context or NULL.  E_INVALID for bad sizes, E_UNSUPPORTED off sm_103,
+/* dims[0..N-1], ranks[0..N-1] (host, read only), 3 <= N <= 8; *out receives
+ * the context or NULL.  E_INVALID for bad sizes, E_UNSUPPORTED off sm_103,
  * E_OOM if the buffers do not fit. */
 cpals_status cpals_tucker_create(const int64_t* dims, int N, const int* ranks, cpals_tucker** out);
 /* frees everything the context owns; NULL is a no-op */
@@ -291,23 +294,23 @@ cpals_status cpals_tucker_set_iterations(cpals_tucker* t, int iters);
  * accumulation, converted to float64 for the rest of the sweep (relative
  * error about 1e-3 against float64).  CPALS_E_UNSUPPORTED if a contraction
  * shape is not aligned for the tensor-core kernel (s_3 and s_2 s_3 and s_3
- * multiples of 8), CPALS_E_INVALID for another value.  May be called before
- * or after cpals_tucker_set_tensor. */
+ * multiples of 8) or the order is not 3, CPALS_E_INVALID for another value.
+ * May be called before or after cpals_tucker_set_tensor. */
 cpals_status cpals_tucker_set_precision(cpals_tucker* t, int precision);
-/* data: row-major, last mode fastest, s_1 s_2 s_3 values; dtype 0 = float64,
+/* data: row-major, last mode fastest, s_1 ... s_N values; dtype 0 = float64,
  * 1 = float32 (widened); on_device selects a device or a host pointer.  The
  * tensor is copied (the caller keeps ownership) and ||X||^2 is formed in
  * float64.  Invalidates the PP operators.  E_INVALID for a NULL pointer or
  * another dtype. */
 cpals_status cpals_tucker_set_tensor(cpals_tucker* t, const void* data, int dtype, int on_device);
-/* three host arrays s_n x R_n (orthonormal columns; e.g. the HOSVD), copied;
+/* N host arrays s_n x R_n (orthonormal columns; e.g. the HOSVD), copied;
  * dA <- A, as Algorithm 4 starts.  E_INVALID for a NULL pointer. */
 cpals_status cpals_tucker_init_factors(cpals_tucker* t, const double* const* factors);
 /* one HOOI sweep (Algorithm 2); *fitness (nullable) exact */
 cpals_status cpals_tucker_als_sweep(cpals_tucker* t, double* fitness);
 /* Y_p^(i,n) and Y_p^(n) at the current factors; A_p <- A, dA <- 0 */
 cpals_status cpals_tucker_pp_build_operators(cpals_tucker* t);
-/* one PP approximated sweep; *fitness (nullable) the estimate from Y~^(3) */
+/* one PP approximated sweep; *fitness (nullable) the estimate from Y~^(N) */
 cpals_status cpals_tucker_pp_sweep(cpals_tucker* t, double* fitness);
 /* Algorithm 4 for max_sweeps sweeps (eps as in cpals_run); traces nullable,
  * length max_sweeps; kinds CPALS_SWEEP_* */
@@ -315,10 +318,10 @@ cpals_status cpals_tucker_run(cpals_tucker* t, int max_sweeps, double eps, doubl
                               int* kind_trace, int* n_done);
 /* exact fitness at the current factors (also refreshes the core) */
 cpals_status cpals_tucker_fitness(cpals_tucker* t, double* out);
-/* copies the factors into three caller-owned host buffers of s_n x R_n */
+/* copies the factors into N caller-owned host buffers of s_n x R_n */
 cpals_status cpals_tucker_get_factors(cpals_tucker* t, double* const* out);
 /* the core of the last sweep or fitness call into a caller-owned host
- * buffer of R_1 R_2 R_3 values (in PP sweeps the estimate from Y~^(3)) */
+ * buffer of R_1 ... R_N values (in PP sweeps the estimate from Y~^(N)) */
 cpals_status cpals_tucker_get_core(cpals_tucker* t, double* out);
 /* message of the last failure on this context (owned by the context, valid
  * until its next call; "" if none) */

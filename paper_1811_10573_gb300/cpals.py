@@ -631,7 +631,7 @@ def cpals_tucker_set_tensor(t, ptr, dtype, on_device):
 
 
 def cpals_tucker_init_factors(t, factors):
-    arr = (_dp * 3)(*[_dptr(f) for f in factors])
+    arr = (_dp * len(factors))(*[_dptr(f) for f in factors])
     return lib().cpals_tucker_init_factors(t, arr)
 
 
@@ -669,8 +669,9 @@ def cpals_tucker_last_error(t):
 
 
 class Tucker:
-    """Order-3 Tucker-ALS / PP-Tucker-ALS context in float64 (owns its device
-    memory); precision "mixed" puts the first-level TTMs on the tensor cores."""
+    """Tucker-ALS / PP-Tucker-ALS context in float64 for orders 3 to 8 (owns
+    its device memory); precision "mixed" (order 3) puts the first-level
+    TTMs on the tensor cores."""
 
     def __init__(self, dims, ranks, precision="fp64"):
         self.dims = [int(d) for d in dims]
@@ -756,7 +757,7 @@ class Tucker:
 
     def get_factors(self):
         out = [np.empty((s, r)) for s, r in zip(self.dims, self.ranks)]
-        arr = (_dp * 3)(*[_dptr(o) for o in out])
+        arr = (_dp * len(out))(*[_dptr(o) for o in out])
         self._ck(cpals_tucker_get_factors(self.t, arr))
         return out
 

@@ -1,7 +1,9 @@
 // Tucker-ALS (HOOI, Algorithm 2) and pairwise-perturbation Tucker-ALS
-// (Algorithm 4) for order-3 tensors in IEEE float64.
+// (Algorithm 4) for tensors of order 3 to 8 in IEEE float64.  Order 3 has the
+// tuned layouts below; higher orders use the generic contraction chains of
+// the "order N > 3" section.
 //
-// Per sweep (Sec. 2.4 with the dimension tree of Sec. 2.5):
+// Order-3 sweep (Sec. 2.4 with the dimension tree of Sec. 2.5):
 //   T  = X x_3 A3        [x1][x2][r3]   first level for modes 1 and 2
 //   Y1 = T x_2 A2        [x1][r3][r2]
 //   Y2 = T x_1 A1        [x2][r3][r1]   (A1 already updated)
@@ -521,6 +523,22 @@ __global__ void add_transposed_kernel(const double* __restrict__ in, double* __r
 }
 
 // Xb[i] = bf16(X[i]) (through float, round to nearest)
+// out[x][a][r][b] (=, or += with add) in[x][a][b][r]: moves the rank index r
+// of a contracted mode from the end of the layout to its place among the
+// other rank indices (order N > 3: the PP terms and M_p^(n))
+__global__ void permute_rank_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t nx,
+                                    int64_t na, int nr, int64_t nb, int add) {
+  const int64_t total = nx * na * nr * nb;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = o % nb;
+    const int64_t r = (o / nb) % nr;
+    const int64_t xa = o / (nb * nr);          // x * na + a
+    const double v = in[(xa * nb + b) * nr + r];
+    out[o] = add ? out[o] + v : v;
+  }
+}
+
 __global__ void to_bf16_kernel(const double* __restrict__ X, __nv_bfloat16* __restrict__ Xb, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -544,10 +562,15 @@ __global__ void factor_bt_kernel(const double* __restrict__ A, int64_t K, int R,
   }
 }
 
+struct RankList {
+  int n;
+  int R[kMaxModes];
+};
+
 // scal[0] = fitness, scal[1] = ||G||^2, scal[2 + 2n] = ||dA^(n)||^2,
 // scal[3 + 2n] = ||A^(n)||^2 (sums of the per-column parts)
 __global__ void tucker_scalars_kernel(const double* __restrict__ G, int64_t ng, double normX2,
-                                      const double* __restrict__ part, int R0, int R1, int R2,
+                                      const double* __restrict__ part, RankList rl,
                                       double* __restrict__ scal) {
   __shared__ double red[256];
   double g = 0.0;
@@ -562,10 +585,9 @@ __global__ void tucker_scalars_kernel(const double* __restrict__ G, int64_t ng, 
     const double gn = red[0];
     scal[0] = 1.0 - sqrt(fmax(normX2 - gn, 0.0)) / sqrt(normX2);
     scal[1] = gn;
-    const int Rs[3] = {R0, R1, R2};
-    for (int n = 0; n < 3; n++) {
+    for (int n = 0; n < rl.n; n++) {
       double nd = 0.0, na = 0.0;
-      for (int r = 0; r < Rs[n]; r++) {
+      for (int r = 0; r < rl.R[n]; r++) {
         nd += part[2 * (kTuckerMaxRank * n + r)];
         na += part[2 * (kTuckerMaxRank * n + r) + 1];
       }
@@ -581,8 +603,9 @@ __global__ void tucker_scalars_kernel(const double* __restrict__ G, int64_t ng, 
 using namespace cpals;
 
 struct cpals_tucker {
-  int64_t s[3] = {0, 0, 0};
-  int R[3] = {0, 0, 0};
+  int N = 3;
+  int64_t s[kMaxModes] = {};
+  int R[kMaxModes] = {};
   int iters = 8;                       // subspace iterations per factor update
   cudaStream_t stream = nullptr;
   int64_t launches = 0;
@@ -590,18 +613,21 @@ struct cpals_tucker {
   double* X = nullptr;
   double normX2 = 0.0;
   bool have_tensor = false, have_factors = false, ops_built = false;
-  double* A[3] = {nullptr, nullptr, nullptr};
-  double* Ap[3] = {nullptr, nullptr, nullptr};
-  double* dA[3] = {nullptr, nullptr, nullptr};
+  double* A[kMaxModes] = {};
+  double* Ap[kMaxModes] = {};
+  double* dA[kMaxModes] = {};
   double *T = nullptr, *U = nullptr, *Y = nullptr, *Yt = nullptr, *G = nullptr;
   double *W = nullptr, *Z = nullptr, *Q = nullptr, *C = nullptr, *V = nullptr, *lam = nullptr;
-  double* part = nullptr;              // 3 * kTuckerMaxRank * 2 column norms
+  double* part = nullptr;              // kMaxModes * kTuckerMaxRank * 2 column norms
   double* C2 = nullptr;                // partial Grams of the convergence test
   double* rpart = nullptr;             // per-CTA residual sums
   double* gpart = nullptr;             // K-split partial sums of the contractions
   int64_t gpart_cap = 0;
-  double* ops[3] = {nullptr, nullptr, nullptr};   // (1,2), (1,3), (2,3) in 1-based mode pairs
-  double* Mp[3] = {nullptr, nullptr, nullptr};
+  double* ops[kMaxModes * (kMaxModes - 1) / 2] = {};   // pairs i < n in lexicographic order
+  double* Mp[kMaxModes] = {};
+  // order N > 3: intermediates of the contraction chains (each up to the
+  // largest single-mode contraction of X)
+  double *Pa = nullptr, *Pb = nullptr, *Ya = nullptr, *Yb = nullptr;
   double* scal = nullptr;
   double* scal_h = nullptr;
   // tensor-core first level (CPALS_MIXED_BF16)
@@ -730,13 +756,19 @@ cpals_status eig_update(cpals_tucker* t, int n, const double* Yn, int64_t K, con
   return CPALS_OK;
 }
 
-cpals_status finish_sweep(cpals_tucker* t, const double* Y3) {
-  // G = Y3 x_3 A3: out[m = (r1, r2)][r3] = sum_x3 Y3[x3][m] A3[x3][r3]
-  gemm(t, Y3, t->A[2], t->G, 1, t->s[2], (int64_t)t->R[0] * t->R[1], t->R[2], false);
-  tucker_scalars_kernel<<<1, 256, 0, t->stream>>>(t->G, (int64_t)t->R[0] * t->R[1] * t->R[2], t->normX2,
-                                                  t->part, t->R[0], t->R[1], t->R[2], t->scal);
+// Y: Y^(N-1) as [x_{N-1}][r_0 .. r_{N-2}]
+cpals_status finish_sweep(cpals_tucker* t, const double* Y) {
+  // G = Y x_{N-1} A^(N-1): out[m = (r_0 .. r_{N-2})][r_{N-1}] = sum_x Y[x][m] A[x][r]
+  const int N = t->N;
+  int64_t m = 1;
+  for (int k = 0; k + 1 < N; k++) m *= t->R[k];
+  gemm(t, Y, t->A[N - 1], t->G, 1, t->s[N - 1], m, t->R[N - 1], false);
+  RankList rl;
+  rl.n = N;
+  for (int k = 0; k < kMaxModes; k++) rl.R[k] = k < N ? t->R[k] : 0;
+  tucker_scalars_kernel<<<1, 256, 0, t->stream>>>(t->G, m * t->R[N - 1], t->normX2, t->part, rl, t->scal);
   t->launches += 1;
-  TK(cudaMemcpyAsync(t->scal_h, t->scal, 8 * 8, cudaMemcpyDeviceToHost, t->stream));
+  TK(cudaMemcpyAsync(t->scal_h, t->scal, (2 + 2 * N) * 8, cudaMemcpyDeviceToHost, t->stream));
   TK(cudaMemcpyAsync(t->status_h, t->status, 8, cudaMemcpyDeviceToHost, t->stream));
   TK(cudaStreamSynchronize(t->stream));
   TK(cudaGetLastError());
@@ -828,6 +860,221 @@ cpals_status tucker_pp(cpals_tucker* t) {
   return finish_sweep(t, t->Y);
 }
 
+// ---------------------------------------------------------------- order N > 3
+// Tensors in these chains are row-major over a layout: the modes still at
+// full size in increasing order, then the rank indices of the contracted
+// modes in the order they were contracted.  Contracting the full mode at
+// position p with A (s x R) is one gemm (batch = sizes before p, K = s, M =
+// sizes after p, K-major when p is last) and appends that mode's rank index;
+// contracting modes in increasing order therefore leaves the ranks in
+// increasing mode order.  Canonical layouts: Y^(n) [x_n][r_k, k != n];
+// operators Y_p^(i,n), i < n, [x_i][x_n][r_k, k not in {i, n}]; the core
+// [r_0 .. r_{N-1}].
+struct Layout {
+  int n = 0;
+  int mode[kMaxModes];
+  bool rank[kMaxModes];
+};
+
+Layout full_layout(const cpals_tucker* t) {
+  Layout l;
+  l.n = t->N;
+  for (int k = 0; k < t->N; k++) {
+    l.mode[k] = k;
+    l.rank[k] = false;
+  }
+  return l;
+}
+
+int64_t entry_size(const cpals_tucker* t, const Layout& l, int p) {
+  return l.rank[p] ? t->R[l.mode[p]] : t->s[l.mode[p]];
+}
+
+// out = in x_j A (A: s_j x R_j); returns the new layout
+Layout ttm_step(cpals_tucker* t, const double* in, const Layout& l, int j, const double* A, double* out) {
+  int p = -1;
+  for (int q = 0; q < l.n; q++)
+    if (l.mode[q] == j && !l.rank[q]) p = q;
+  int64_t pre = 1, post = 1;
+  for (int q = 0; q < p; q++) pre *= entry_size(t, l, q);
+  for (int q = p + 1; q < l.n; q++) post *= entry_size(t, l, q);
+  if (post == 1) gemm(t, in, A, out, 1, t->s[j], pre, t->R[j], true);
+  else gemm(t, in, A, out, pre, t->s[j], post, t->R[j], false);
+  Layout o;
+  o.n = 0;
+  for (int q = 0; q < l.n; q++) {
+    if (q == p) continue;
+    o.mode[o.n] = l.mode[q];
+    o.rank[o.n] = l.rank[q];
+    o.n++;
+  }
+  o.mode[o.n] = j;
+  o.rank[o.n] = true;
+  o.n++;
+  return o;
+}
+
+// src x_{k in modes} (in the given order) with factors F[k]; intermediates
+// alternate between b0 and b1 (src is never written), the last step writes
+// dst when given.  Returns the result's pointer.
+const double* ttm_chain(cpals_tucker* t, const double* src, Layout& l, const int* modes, int nm,
+                        double* const* F, double* b0, double* b1, double* dst) {
+  const double* cur = src;
+  for (int q = 0; q < nm; q++) {
+    double* out = (q + 1 == nm && dst) ? dst : ((q & 1) ? b1 : b0);
+    l = ttm_step(t, cur, l, modes[q], F[modes[q]], out);
+    cur = out;
+  }
+  return cur;
+}
+
+int pair_index(int N, int i, int n) {   // i < n, lexicographic
+  int idx = 0;
+  for (int a = 0; a < i; a++) idx += N - 1 - a;
+  return idx + (n - i - 1);
+}
+
+void permute_rank(cpals_tucker* t, const double* in, double* out, int n, int i, bool add) {
+  // in [x_n][r_k, k not in {n, i}][r_i] -> out [x_n][r_k, k != n] (increasing k)
+  int64_t a = 1, b = 1;
+  for (int k = 0; k < t->N; k++) {
+    if (k == n || k == i) continue;
+    if (k < i) a *= t->R[k];
+    else b *= t->R[k];
+  }
+  const int64_t total = t->s[n] * a * t->R[i] * b;
+  permute_rank_kernel<<<(unsigned)std::min<int64_t>(cdivt(total, 256), 1216), 256, 0, t->stream>>>(
+      in, out, t->s[n], a, t->R[i], b, add ? 1 : 0);
+  t->launches++;
+}
+
+int64_t others_rank(const cpals_tucker* t, int n) {
+  int64_t K = 1;
+  for (int k = 0; k < t->N; k++)
+    if (k != n) K *= t->R[k];
+  return K;
+}
+
+Layout op_layout(const cpals_tucker* t, int i, int n) {   // Y_p^(i,n), i < n
+  Layout l;
+  l.n = 0;
+  l.mode[l.n] = i;
+  l.rank[l.n++] = false;
+  l.mode[l.n] = n;
+  l.rank[l.n++] = false;
+  for (int k = 0; k < t->N; k++)
+    if (k != i && k != n) {
+      l.mode[l.n] = k;
+      l.rank[l.n++] = true;
+    }
+  return l;
+}
+
+// HOOI sweep, order N: P_0 = X, P_{n+1} = P_n x_n A^(n) (the updated factor;
+// [x_{n+1} .. x_{N-1}][r_0 .. r_n]) and Y^(n) = P_n x_{k > n} A^(k), so each
+// sweep contracts X twice at full size (Y^(0)'s first step and P_1).
+cpals_status tucker_als_n(cpals_tucker* t) {
+  const int N = t->N;
+  const double* P = t->X;
+  Layout lp = full_layout(t);
+  double* pbuf[2] = {t->Pa, t->Pb};
+  int pi = 0;
+  const double* Y = P;
+  for (int n = 0; n < N; n++) {
+    Y = P;
+    if (n + 1 < N) {
+      Layout ly = lp;
+      int modes[kMaxModes], nm = 0;
+      for (int k = n + 1; k < N; k++) modes[nm++] = k;
+      Y = ttm_chain(t, P, ly, modes, nm, t->A, t->Ya, t->Yb, nullptr);
+    }
+    TKS(eig_update(t, n, Y, others_rank(t, n), nullptr));
+    if (n + 1 < N) {
+      double* out = pbuf[pi];
+      pi ^= 1;
+      lp = ttm_step(t, P, lp, n, t->A[n], out);
+      P = out;
+    }
+  }
+  return finish_sweep(t, Y);
+}
+
+// PP operators, order N (Sec. 3.2.2): Y_p^(i,n) = X x_{k not in {i,n}} A_p^(k)
+// for every pair, grouped by the smallest contracted mode k0 (0, 1 or 2),
+// whose contraction of X the group shares; then Y_p^(n) from one operator
+// holding mode n; dA <- 0.
+cpals_status tucker_build_n(cpals_tucker* t) {
+  const int N = t->N;
+  for (int n = 0; n < N; n++)
+    TK(cudaMemcpyAsync(t->Ap[n], t->A[n], t->s[n] * t->R[n] * 8, cudaMemcpyDeviceToDevice, t->stream));
+  for (int k0 = 0; k0 < 3; k0++) {
+    bool first = true;
+    Layout lt;
+    for (int i = 0; i < N; i++)
+      for (int n = i + 1; n < N; n++) {
+        if (i == k0 || n == k0) continue;
+        bool group = true;                 // every mode below k0 is kept
+        for (int j = 0; j < k0; j++) group = group && (j == i || j == n);
+        if (!group) continue;
+        if (first) {
+          lt = ttm_step(t, t->X, full_layout(t), k0, t->Ap[k0], t->Pa);
+          first = false;
+        }
+        Layout l = lt;
+        int modes[kMaxModes], nm = 0;
+        for (int j = k0 + 1; j < N; j++)
+          if (j != i && j != n) modes[nm++] = j;
+        ttm_chain(t, t->Pa, l, modes, nm, t->Ap, t->Ya, t->Yb, t->ops[pair_index(N, i, n)]);
+      }
+  }
+  for (int n = 0; n < N; n++) {
+    const int i = n == 0 ? 1 : 0;
+    const int lo = std::min(i, n), hi = std::max(i, n);
+    ttm_step(t, t->ops[pair_index(N, lo, hi)], op_layout(t, lo, hi), i, t->Ap[i], t->Ya);
+    permute_rank(t, t->Ya, t->Mp[n], n, i, false);
+  }
+  for (int n = 0; n < N; n++) TK(cudaMemsetAsync(t->dA[n], 0, t->s[n] * t->R[n] * 8, t->stream));
+  t->ops_built = true;
+  return CPALS_OK;
+}
+
+// PP sweep, order N: Y~^(n) = Y_p^(n) + sum_{i != n} Y_p^(i,n) x_i dA^(i)
+// (Sec. 3.2.2) in the canonical layout, then the factor update as in ALS.
+cpals_status tucker_pp_n(cpals_tucker* t) {
+  const int N = t->N;
+  for (int n = 0; n < N; n++) {
+    const int64_t sz = t->s[n] * others_rank(t, n);
+    axpy_kernel<<<(unsigned)std::min<int64_t>(cdivt(sz, 256), 1216), 256, 0, t->stream>>>(t->Mp[n], t->Pa, sz, 0);
+    t->launches++;
+    for (int i = 0; i < N; i++) {
+      if (i == n) continue;
+      const int lo = std::min(i, n), hi = std::max(i, n);
+      ttm_step(t, t->ops[pair_index(N, lo, hi)], op_layout(t, lo, hi), i, t->dA[i], t->Ya);
+      permute_rank(t, t->Ya, t->Pa, n, i, true);
+    }
+    TKS(eig_update(t, n, t->Pa, others_rank(t, n), t->Ap[n]));
+  }
+  return finish_sweep(t, t->Pa);
+}
+
+// Y^(N-1) at the current factors (the exact fitness), order N
+const double* tucker_last_ttmc_n(cpals_tucker* t) {
+  Layout l = full_layout(t);
+  int modes[kMaxModes];
+  for (int k = 0; k + 1 < t->N; k++) modes[k] = k;
+  return ttm_chain(t, t->X, l, modes, t->N - 1, t->A, t->Pa, t->Pb, nullptr);
+}
+
+cpals_status run_als(cpals_tucker* t) { return t->N == 3 ? tucker_als(t) : tucker_als_n(t); }
+cpals_status run_build(cpals_tucker* t) { return t->N == 3 ? tucker_build(t) : tucker_build_n(t); }
+cpals_status run_pp(cpals_tucker* t) { return t->N == 3 ? tucker_pp(t) : tucker_pp_n(t); }
+
+int64_t prod_dims(const cpals_tucker* t) {
+  int64_t n = 1;
+  for (int k = 0; k < t->N; k++) n *= t->s[k];
+  return n;
+}
+
 cpals_status tk_ready(cpals_tucker* t) {
   if (!t) return CPALS_E_INVALID;
   if (!t->have_tensor) return t->fail(CPALS_E_STATE, "no tensor");
@@ -842,8 +1089,8 @@ extern "C" {
 cpals_status cpals_tucker_create(const int64_t* dims, int N, const int* ranks, cpals_tucker** out) {
   if (!out) return CPALS_E_INVALID;
   *out = nullptr;
-  if (!dims || !ranks || N != 3) return CPALS_E_INVALID;
-  for (int n = 0; n < 3; n++)
+  if (!dims || !ranks || N < 3 || N > kMaxModes) return CPALS_E_INVALID;
+  for (int n = 0; n < N; n++)
     if (dims[n] < 1 || dims[n] > 4096 || ranks[n] < 1 || ranks[n] > kTuckerMaxRank || ranks[n] > dims[n])
       return CPALS_E_INVALID;
   int dev = 0;
@@ -854,29 +1101,44 @@ cpals_status cpals_tucker_create(const int64_t* dims, int N, const int* ranks, c
   }
   if (!(prop.major == 10 && prop.minor == 3)) return CPALS_E_UNSUPPORTED;
   cpals_tucker* t = new cpals_tucker();
-  for (int n = 0; n < 3; n++) {
+  t->N = N;
+  int64_t nx = 1, smax = 1, nr = 1;
+  for (int n = 0; n < N; n++) {
     t->s[n] = dims[n];
     t->R[n] = ranks[n];
+    nx *= dims[n];
+    nr *= ranks[n];
+    smax = std::max<int64_t>(smax, dims[n]);
   }
+  // the largest single-mode contraction of X (order N: every chain
+  // intermediate, operator and Y^(n) is at most this size)
+  int64_t inter = 0;
+  for (int n = 0; n < N; n++) inter = std::max<int64_t>(inter, nx / dims[n] * ranks[n]);
   const int64_t s1 = dims[0], s2 = dims[1], s3 = dims[2];
-  const int64_t smax = std::max(s1, std::max(s2, s3));
   const int R1 = ranks[0], R2 = ranks[1], R3 = ranks[2];
-  const int64_t Ymax = std::max(s1 * R2 * R3, std::max(s2 * R1 * R3, s3 * R1 * R2));
+  const int64_t Ymax = N == 3 ? std::max(s1 * R2 * R3, std::max(s2 * R1 * R3, s3 * R1 * R2)) : inter;
   bool ok = cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking) == cudaSuccess;
   auto al = [&](double** p, int64_t n) {
     if (ok) ok = cudaMalloc((void**)p, (size_t)std::max<int64_t>(n, 1) * 8) == cudaSuccess;
   };
-  al(&t->X, s1 * s2 * s3);
-  for (int n = 0; n < 3; n++) {
+  al(&t->X, nx);
+  for (int n = 0; n < N; n++) {
     al(&t->A[n], dims[n] * ranks[n]);
     al(&t->Ap[n], dims[n] * ranks[n]);
     al(&t->dA[n], dims[n] * ranks[n]);
   }
-  al(&t->T, s1 * s2 * R3);
-  al(&t->U, s2 * s3 * R1);
-  al(&t->Y, Ymax);
-  al(&t->Yt, Ymax);
-  al(&t->G, (int64_t)R1 * R2 * R3);
+  if (N == 3) {
+    al(&t->T, s1 * s2 * R3);
+    al(&t->U, s2 * s3 * R1);
+    al(&t->Y, Ymax);
+    al(&t->Yt, Ymax);
+  } else {
+    al(&t->Pa, inter);
+    al(&t->Pb, inter);
+    al(&t->Ya, inter);
+    al(&t->Yb, inter);
+  }
+  al(&t->G, nr);
   al(&t->W, smax * smax);
   al(&t->Z, smax * kTuckerMaxRank);
   al(&t->Q, smax * kTuckerMaxRank);
@@ -887,17 +1149,14 @@ cpals_status cpals_tucker_create(const int64_t* dims, int N, const int* ranks, c
   al(&t->gpart, t->gpart_cap);
   al(&t->V, kTuckerMaxRank * kTuckerMaxRank);
   al(&t->lam, kTuckerMaxRank);
-  al(&t->part, 3 * 2 * kTuckerMaxRank);
-  al(&t->ops[0], s1 * s2 * R3);
-  al(&t->ops[1], s1 * s3 * R2);
-  al(&t->ops[2], s2 * s3 * R1);
-  al(&t->Mp[0], s1 * R3 * R2);
-  al(&t->Mp[1], s2 * R3 * R1);
-  al(&t->Mp[2], s3 * R1 * R2);
-  al(&t->scal, 16);
+  al(&t->part, kMaxModes * 2 * kTuckerMaxRank);
+  for (int i = 0; i < N; i++)
+    for (int n = i + 1; n < N; n++) al(&t->ops[pair_index(N, i, n)], dims[i] * dims[n] * (nr / ranks[i] / ranks[n]));
+  for (int n = 0; n < N; n++) al(&t->Mp[n], dims[n] * (nr / ranks[n]));
+  al(&t->scal, 32);
   if (ok) ok = cudaMalloc((void**)&t->status, 16) == cudaSuccess && cudaMemset(t->status, 0, 16) == cudaSuccess;
-  if (ok) ok = cudaMallocHost((void**)&t->scal_h, 16 * 8) == cudaSuccess;
-  if (ok) ok = cudaMemset(t->part, 0, 3 * 2 * kTuckerMaxRank * 8) == cudaSuccess;
+  if (ok) ok = cudaMallocHost((void**)&t->scal_h, 32 * 8) == cudaSuccess;
+  if (ok) ok = cudaMemset(t->part, 0, kMaxModes * 2 * kTuckerMaxRank * 8) == cudaSuccess;
   if (ok) ok = setup_small_kernels() == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -915,10 +1174,11 @@ void cpals_tucker_destroy(cpals_tucker* t) {
     if (p) cudaFree(p);
   };
   F(t->X);
-  for (int n = 0; n < 3; n++) {
-    F(t->A[n]); F(t->Ap[n]); F(t->dA[n]); F(t->ops[n]); F(t->Mp[n]);
+  for (int n = 0; n < kMaxModes; n++) {
+    F(t->A[n]); F(t->Ap[n]); F(t->dA[n]); F(t->Mp[n]);
   }
-  F(t->T); F(t->U); F(t->Y); F(t->Yt); F(t->G); F(t->W); F(t->Z); F(t->Q); F(t->C); F(t->C2); F(t->rpart);
+  for (double* o : t->ops) F(o);
+  F(t->T); F(t->U); F(t->Y); F(t->Yt); F(t->G); F(t->Pa); F(t->Pb); F(t->Ya); F(t->Yb); F(t->W); F(t->Z); F(t->Q); F(t->C); F(t->C2); F(t->rpart);
   F(t->V); F(t->lam); F(t->part); F(t->gpart); F(t->scal); F(t->status);
   F(t->Xb); F(t->Bt); F(t->outf); F(t->gpartf); F(t->umma_sched);
   if (t->scal_h) cudaFreeHost(t->scal_h);
@@ -940,6 +1200,7 @@ cpals_status cpals_tucker_set_precision(cpals_tucker* t, int precision) {
     return CPALS_OK;
   }
   if (precision != CPALS_MIXED_BF16) return t->fail(CPALS_E_INVALID, "precision must be FP64 or MIXED_BF16");
+  if (t->N != 3) return t->fail(CPALS_E_UNSUPPORTED, "tensor-core TTMs: order 3 only");
   const int64_t s1 = t->s[0], s2 = t->s[1], s3 = t->s[2];
   if (!umma_supported(s3, s1 * s2, true, t->R[2]) || !umma_supported(s1, s2 * s3, false, t->R[0]) ||
       !umma_supported(s2, s3, false, t->R[1]))
@@ -977,7 +1238,7 @@ cpals_status cpals_tucker_set_precision(cpals_tucker* t, int precision) {
 
 cpals_status cpals_tucker_set_tensor(cpals_tucker* t, const void* data, int dtype, int on_device) {
   if (!t || !data || (dtype != 0 && dtype != 1)) return t ? t->fail(CPALS_E_INVALID, "bad tensor") : CPALS_E_INVALID;
-  const int64_t n = t->s[0] * t->s[1] * t->s[2];
+  const int64_t n = prod_dims(t);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (dtype == 0) {
     TK(cudaMemcpyAsync(t->X, data, n * 8, kind, t->stream));
@@ -992,11 +1253,11 @@ cpals_status cpals_tucker_set_tensor(cpals_tucker* t, const void* data, int dtyp
     cudaFree(tmp);
     TK(e);
   }
-  sumsq<double>(t->X, n, t->gpart, t->scal + 15, t->L());
-  TK(cudaMemcpyAsync(t->scal_h + 15, t->scal + 15, 8, cudaMemcpyDeviceToHost, t->stream));
+  sumsq<double>(t->X, n, t->gpart, t->scal + 31, t->L());
+  TK(cudaMemcpyAsync(t->scal_h + 31, t->scal + 31, 8, cudaMemcpyDeviceToHost, t->stream));
   TK(cudaStreamSynchronize(t->stream));
   TK(cudaGetLastError());
-  t->normX2 = t->scal_h[15];
+  t->normX2 = t->scal_h[31];
   if (t->mixed) {
     to_bf16_kernel<<<1216, 256, 0, t->stream>>>(t->X, t->Xb, n);
     t->launches++;
@@ -1010,14 +1271,14 @@ cpals_status cpals_tucker_set_tensor(cpals_tucker* t, const void* data, int dtyp
 
 cpals_status cpals_tucker_init_factors(cpals_tucker* t, const double* const* factors) {
   if (!t || !factors) return t ? t->fail(CPALS_E_INVALID, "factors is NULL") : CPALS_E_INVALID;
-  for (int n = 0; n < 3; n++) {
+  for (int n = 0; n < t->N; n++) {
     if (!factors[n]) return t->fail(CPALS_E_INVALID, "factor pointer is NULL");
     TK(cudaMemcpyAsync(t->A[n], factors[n], t->s[n] * t->R[n] * 8, cudaMemcpyHostToDevice, t->stream));
     // Algorithm 4 starts from dA <- A
     TK(cudaMemcpyAsync(t->dA[n], t->A[n], t->s[n] * t->R[n] * 8, cudaMemcpyDeviceToDevice, t->stream));
   }
   TK(cudaStreamSynchronize(t->stream));
-  for (int n = 0; n < 3; n++) {
+  for (int n = 0; n < t->N; n++) {
     t->scal_h[2 + 2 * n] = t->R[n];       // ||dA||^2 = ||A||^2 = R for orthonormal columns
     t->scal_h[3 + 2 * n] = t->R[n];
   }
@@ -1028,14 +1289,14 @@ cpals_status cpals_tucker_init_factors(cpals_tucker* t, const double* const* fac
 
 cpals_status cpals_tucker_als_sweep(cpals_tucker* t, double* fitness) {
   TKS(tk_ready(t));
-  TKS(tucker_als(t));
+  TKS(run_als(t));
   if (fitness) *fitness = t->scal_h[0];
   return CPALS_OK;
 }
 
 cpals_status cpals_tucker_pp_build_operators(cpals_tucker* t) {
   TKS(tk_ready(t));
-  TKS(tucker_build(t));
+  TKS(run_build(t));
   TK(cudaStreamSynchronize(t->stream));
   TK(cudaGetLastError());
   return CPALS_OK;
@@ -1044,7 +1305,7 @@ cpals_status cpals_tucker_pp_build_operators(cpals_tucker* t) {
 cpals_status cpals_tucker_pp_sweep(cpals_tucker* t, double* fitness) {
   TKS(tk_ready(t));
   if (!t->ops_built) return t->fail(CPALS_E_STATE, "PP operators not built");
-  TKS(tucker_pp(t));
+  TKS(run_pp(t));
   if (fitness) *fitness = t->scal_h[0];
   return CPALS_OK;
 }
@@ -1054,7 +1315,7 @@ cpals_status cpals_tucker_run(cpals_tucker* t, int max_sweeps, double eps, doubl
   TKS(tk_ready(t));
   if (max_sweeps < 0) return t->fail(CPALS_E_INVALID, "max_sweeps < 0");
   auto small = [&]() {
-    for (int n = 0; n < 3; n++)
+    for (int n = 0; n < t->N; n++)
       if (!(t->scal_h[2 + 2 * n] < eps * eps * t->scal_h[3 + 2 * n])) return false;
     return true;
   };
@@ -1067,20 +1328,20 @@ cpals_status cpals_tucker_run(cpals_tucker* t, int max_sweeps, double eps, doubl
   };
   while (st == CPALS_OK && k < max_sweeps) {
     if (eps > 0 && small()) {
-      st = tucker_build(t);
+      st = run_build(t);
       if (st != CPALS_OK) break;
       // dA <- 0 after the operators are formed (Algorithm 4)
-      for (int n = 0; n < 3; n++) t->scal_h[2 + 2 * n] = 0.0;
+      for (int n = 0; n < t->N; n++) t->scal_h[2 + 2 * n] = 0.0;
       bool first = true;
       while (st == CPALS_OK && k < max_sweeps && small()) {
-        st = tucker_pp(t);
+        st = run_pp(t);
         if (st != CPALS_OK) break;
         record(first ? CPALS_SWEEP_PP_INIT : CPALS_SWEEP_PP_APPROX);
         first = false;
       }
       if (st != CPALS_OK || k >= max_sweeps) break;
     }
-    st = tucker_als(t);
+    st = run_als(t);
     if (st != CPALS_OK) break;
     record(CPALS_SWEEP_ALS);
   }
@@ -1091,18 +1352,22 @@ cpals_status cpals_tucker_run(cpals_tucker* t, int max_sweeps, double eps, doubl
 cpals_status cpals_tucker_fitness(cpals_tucker* t, double* out) {
   TKS(tk_ready(t));
   if (!out) return t->fail(CPALS_E_INVALID, "out is NULL");
-  // exact: Y3 and the core at the current factors
-  const int64_t s1 = t->s[0], s2 = t->s[1], s3 = t->s[2];
-  TKS(first_level(t, t->A[0], t->U, 1, s1, s2 * s3, t->R[0], false));
-  gemm(t, t->U, t->A[1], t->Yt, 1, s2, s3 * t->R[0], t->R[1], false);
-  TKS(finish_sweep(t, t->Yt));
+  // exact: Y^(N-1) and the core at the current factors
+  if (t->N == 3) {
+    const int64_t s1 = t->s[0], s2 = t->s[1], s3 = t->s[2];
+    TKS(first_level(t, t->A[0], t->U, 1, s1, s2 * s3, t->R[0], false));
+    gemm(t, t->U, t->A[1], t->Yt, 1, s2, s3 * t->R[0], t->R[1], false);
+    TKS(finish_sweep(t, t->Yt));
+  } else {
+    TKS(finish_sweep(t, tucker_last_ttmc_n(t)));
+  }
   *out = t->scal_h[0];
   return CPALS_OK;
 }
 
 cpals_status cpals_tucker_get_factors(cpals_tucker* t, double* const* out) {
   if (!t || !out) return CPALS_E_INVALID;
-  for (int n = 0; n < 3; n++) {
+  for (int n = 0; n < t->N; n++) {
     if (!out[n]) return t->fail(CPALS_E_INVALID, "NULL buffer");
     TK(cudaMemcpyAsync(out[n], t->A[n], t->s[n] * t->R[n] * 8, cudaMemcpyDeviceToHost, t->stream));
   }
@@ -1112,7 +1377,9 @@ cpals_status cpals_tucker_get_factors(cpals_tucker* t, double* const* out) {
 
 cpals_status cpals_tucker_get_core(cpals_tucker* t, double* out) {
   if (!t || !out) return CPALS_E_INVALID;
-  TK(cudaMemcpyAsync(out, t->G, (size_t)t->R[0] * t->R[1] * t->R[2] * 8, cudaMemcpyDeviceToHost, t->stream));
+  int64_t nr = 1;
+  for (int n = 0; n < t->N; n++) nr *= t->R[n];
+  TK(cudaMemcpyAsync(out, t->G, (size_t)nr * 8, cudaMemcpyDeviceToHost, t->stream));
   TK(cudaStreamSynchronize(t->stream));
   return CPALS_OK;
 }

@@ -45,9 +45,9 @@ def test_invalid_arguments_rejected_on_host(lib):
 
 
 def test_tucker_invalid_arguments_rejected_on_host(lib):
-    # order other than 3, an empty mode, a rank above its mode size or above
-    # 48, a mode above 4096: rejected before any device call
-    for dims, ranks in [([4, 5], [2, 2]), ([4, 5, 6, 7], [2, 2, 2, 2]), ([4, 0, 6], [2, 1, 2]),
+    # order below 3 or above 8, an empty mode, a rank above its mode size or
+    # above 48, a mode above 4096: rejected before any device call
+    for dims, ranks in [([4, 5], [2, 2]), ([2] * 9, [1] * 9), ([4, 5, 6, 0], [2, 2, 2, 1]), ([4, 0, 6], [2, 1, 2]),
                         ([4, 5, 6], [5, 2, 2]), ([60, 60, 60], [49, 2, 2]), ([4, 5, 6], [2, 0, 2]),
                         ([5000, 5, 6], [2, 2, 2])]:
         st, t = cpals.cpals_tucker_create(dims, ranks)

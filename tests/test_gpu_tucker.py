@@ -202,3 +202,67 @@ def test_tucker_rank_extremes(dims, ranks):
         for a, b in zip(t.get_factors(), A):
             assert np.max(np.abs(a - b)) < 1e-9
         np.testing.assert_allclose(t.get_core(), G, rtol=0, atol=1e-9 * np.max(np.abs(G)))
+
+
+ORDER_N = [([20, 18, 16, 14], [3, 3, 2, 2]), ([10, 9, 8, 7, 6], [2, 3, 2, 2, 2])]
+
+
+@pytest.mark.parametrize("dims,ranks", ORDER_N, ids=["order4", "order5"])
+def test_tucker_order_n_als_and_pp_sweeps(dims, ranks):
+    """Orders 4 and 5 (the generic contraction chains): HOOI sweeps, then an
+    operator build and PP sweeps (Sec. 3.2.2), each against the oracle fed
+    with the same state: factors within 1e-10, the core within 1e-9 of its
+    largest entry, fitness within 1e-10."""
+    p, A0, t = _setup(dims, ranks, seed=11)
+    with t:
+        normX = float(np.linalg.norm(p.X))
+        for sweep in range(2):
+            A = t.get_factors()
+            f = t.als_sweep()
+            _, G = TO.als_sweep(p.X, A)
+            for n, (a, b) in enumerate(zip(t.get_factors(), A)):
+                assert np.max(np.abs(a - b)) < 1e-10, (sweep, n)
+            np.testing.assert_allclose(t.get_core(), G, rtol=0, atol=1e-9 * np.max(np.abs(G)))
+            assert abs(f - TO.fitness(normX, G)) < 1e-10
+        t.pp_build_operators()
+        Ap = t.get_factors()
+        ops, Mp = TO.pp_operators(p.X, Ap)
+        A = [a.copy() for a in Ap]
+        dA = [np.zeros_like(a) for a in Ap]
+        for sweep in range(3):
+            f = t.pp_sweep()
+            G = TO.pp_sweep(ops, Mp, A, Ap, dA)
+            for n, (a, b) in enumerate(zip(t.get_factors(), A)):
+                assert np.max(np.abs(a - b)) < 1e-10, (sweep, n)
+            np.testing.assert_allclose(t.get_core(), G, rtol=0, atol=1e-9 * np.max(np.abs(G)))
+            assert abs(f - TO.fitness(normX, G)) < 1e-10
+        assert abs(t.fitness() - TO.fitness(normX, TO.core(p.X, t.get_factors()))) < 1e-10
+
+
+def test_tucker_order4_run_matches_oracle():
+    """Algorithm 4 at order 4 from a random orthonormal start: the same sweep
+    kinds as the oracle's, the exact fitness after every ALS sweep within
+    1e-10 and the final factors within 1e-9."""
+    dims, ranks = [24, 20, 18, 16], [3, 2, 2, 2]
+    p = synth.tucker_problem(dims, ranks, seed=12, noise=0.3)
+    A_ref, kinds, fit = TO.pp_tucker_als(p.X, p.A0, 14, eps=0.3)
+    assert kinds[0] == "als" and "pp_approx" in kinds
+    with cpals.Tucker(dims, ranks) as t:
+        t.set_iterations(100)
+        t.set_tensor(np.ascontiguousarray(p.X))
+        t.init_factors(p.A0)
+        out = t.run(14, 0.3)
+        assert out["kinds"] == kinds
+        for k, (f, fr) in enumerate(zip(out["fitness"], fit)):
+            if kinds[k] == "als":
+                assert abs(f - fr) < 1e-10, k
+        for a, b in zip(t.get_factors(), A_ref):
+            assert np.max(np.abs(a - b)) < 1e-9
+        assert abs(t.fitness() - fit[-1]) < 1e-10
+
+
+def test_tucker_order4_mixed_unsupported():
+    with cpals.Tucker([16, 16, 16, 16], [2, 2, 2, 2]) as t:
+        with pytest.raises(cpals.CPALSError) as e:
+            t._ck(cpals.cpals_tucker_set_precision(t.t, cpals.PRECISIONS["mixed"]))
+        assert e.value.status == 8
