@@ -811,7 +811,6 @@ def run_tucker_bench(args, dist, flush, s=400, R=20, sweeps=20, eps=0.3):
     from paper_1811_10573_gb300 import cpals, synth
 
     p = synth.tucker_problem([s] * 3, [R] * 3, seed=dist.rank, noise=0.3)
-    Xd = torch.from_numpy(np.ascontiguousarray(p.X)).cuda()
 
     def ev_time(fn):
         flush.zero_()
@@ -823,8 +822,9 @@ def run_tucker_bench(args, dist, flush, s=400, R=20, sweeps=20, eps=0.3):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3, out
 
-    def one(precision):
-        with cpals.Tucker([s] * 3, [R] * 3, precision) as t:
+    def one(precision, p):
+        Xd = torch.from_numpy(np.ascontiguousarray(p.X)).cuda()
+        with cpals.Tucker([int(d) for d in p.X.shape], p.R, precision) as t:
             t.set_tensor(Xd)
             t.init_factors(p.A0)
             for _ in range(3):
@@ -851,9 +851,13 @@ def run_tucker_bench(args, dist, flush, s=400, R=20, sweeps=20, eps=0.3):
 
     out = {"workload": f"tucker_order3_{s}_rank{R}: X = [[G; A1, A2, A3]] + 0.3 relative noise, "
                        f"random orthonormal start, {sweeps} sweeps",
-           "fp64": one("fp64")}
-    out["mixed"] = one("mixed")
+           "fp64": one("fp64", p)}
+    out["mixed"] = one("mixed", p)
     out["mixed"]["note"] = "first-level TTMs on the tensor cores (X bf16, factor hi + lo), the rest float64"
+    # order 4 (the generic contraction chains): 100^4, ranks 5 = 0.05 s, float64
+    p4 = synth.tucker_problem([100] * 4, [5] * 4, seed=dist.rank, noise=0.3)
+    out["order4"] = {"workload": f"tucker_order4_100_rank5: X = [[G; A1..A4]] + 0.3 relative noise, "
+                                 f"random orthonormal start, {sweeps} sweeps", "fp64": one("fp64", p4)}
     return out
 
 
