@@ -50,6 +50,9 @@ gemm_simt_kernel(const TX* __restrict__ X, const T* __restrict__ B, T* __restric
   for (int i = 0; i < TM; i++)
 #pragma unroll
     for (int j = 0; j < TN; j++) acc[i][j] = T(0);
+  // warps whose rows are all padding (in the last row tile) skip their FMAs,
+  // which frees the FP64 pipe for the SM's other CTAs
+  const int wlive = __reduce_max_sync(0xffffffffu, m0 + tm < M ? 1 : 0);
 
   for (int64_t kk = k0; kk < k1; kk += BK) {
     if (KMAJOR) {
@@ -71,17 +74,19 @@ gemm_simt_kernel(const TX* __restrict__ X, const T* __restrict__ B, T* __restric
       Bs[k][r] = (gk < k1 && r < R) ? B[gk * R + r] : T(0);
     }
     __syncthreads();
+    if (wlive > 0) {
 #pragma unroll
-    for (int k = 0; k < BK; k++) {
-      T a[TM], bb[TN];
+      for (int k = 0; k < BK; k++) {
+        T a[TM], bb[TN];
 #pragma unroll
-      for (int i = 0; i < TM; i++) a[i] = Xs[k][tm + i * THR_M];
+        for (int i = 0; i < TM; i++) a[i] = Xs[k][tm + i * THR_M];
 #pragma unroll
-      for (int j = 0; j < TN; j++) bb[j] = Bs[k][tn + j * THR_N];
+        for (int j = 0; j < TN; j++) bb[j] = Bs[k][tn + j * THR_N];
 #pragma unroll
-      for (int i = 0; i < TM; i++)
+        for (int i = 0; i < TM; i++)
 #pragma unroll
-        for (int j = 0; j < TN; j++) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+          for (int j = 0; j < TN; j++) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+      }
     }
     __syncthreads();
   }
@@ -591,7 +596,9 @@ int gemm_simt_wave_splits(int64_t batch, int64_t K, int64_t M, int R, bool kmajo
   const int64_t wave = (int64_t)occ * nsm;
   const int64_t tiles = cdiv(M, 64) * batch;
   if (tiles >= wave) return 1;
-  int64_t sp = wave / tiles;                                      // whole waves only
+  // about four waves: the CTAs of a partly padded row tile finish early (their
+  // padding warps skip the FMAs) and the block scheduler refills their SMs
+  int64_t sp = 4 * wave / tiles;
   sp = std::min<int64_t>(sp, std::max<int64_t>(1, K / 256));      // at least 256 k per split
   sp = std::min<int64_t>(sp, cap / std::max<int64_t>(1, batch * M * R));
   // the kernel rounds the chunk up to 16 k: keep only counts it runs as given

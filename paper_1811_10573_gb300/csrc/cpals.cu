@@ -1344,6 +1344,8 @@ cpals_status cpals_create(const int64_t* dims, int N, int R, int precision, cpal
   // split-K partials: enough for 2*152 tiles' worth of outputs of 128 rows
   c->gpart_bytes = std::max<size_t>((size_t)2 * 152 * 128 * R * esz, (size_t)4 * c->smax * R * esz);
   c->gpart_bytes = std::max<size_t>(c->gpart_bytes, (size_t)8 * std::min(c->PL, c->PR) * R * esz);
+  // float64 contractions split into about four waves of 64-row tiles
+  if (esz == 8) c->gpart_bytes = std::max<size_t>(c->gpart_bytes, (size_t)4 * 3 * 152 * 64 * R * esz);
   AL(c->gpart, c->gpart_bytes);
   if (precision == CPALS_MIXED_BF16) {
     c->Bt_elems = 2 * (size_t)c->Rpad * (size_t)(cdiv(Pmax, 8) * 8);

@@ -28,9 +28,9 @@ void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int6
                int R, bool kmajor, int splits, Launch L);
 
 // K splits for a float64 gemm_simt: with R > 32 (64-row exact-column tiles)
-// the grid fills whole waves of resident CTAs (one wave when the output alone
-// does not fill the GPU; 1 when it does); otherwise K is split until every SM
-// has a CTA (at least 16 k per split).  0 for other types.
+// the grid is about four waves of resident CTAs when the output alone does
+// not fill the GPU (1 when it does); otherwise K is split until every SM has
+// a CTA (at least 16 k per split).  0 for other types.
 int gemm_simt_wave_splits(int64_t batch, int64_t K, int64_t M, int R, bool kmajor, size_t esz,
                           int64_t cap);
 
