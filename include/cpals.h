@@ -40,13 +40,12 @@ typedef enum {
   CPALS_E_OOM = 2,         /* device allocation failed */
   CPALS_E_CUDA = 3,        /* CUDA runtime/driver error (text in cpals_last_error) */
   CPALS_E_STATE = 4,       /* call out of order (e.g. pp_sweep before pp_build_operators) */
-  CPALS_E_SINGULAR = 5,    /* Gamma not positive definite and no pseudo-inverse path: the factor of
-                              that mode was left unchanged.  With IEEE float64 normal equations
-                              (FP64 contexts, or cpals_set_normal_arith) such a Gamma is replaced
-                              by its pseudo-inverse Gamma^dagger (Algorithm 1) instead: symmetric
-                              Jacobi eigendecomposition, eigenvalues at or below 1e-13 of the
-                              largest dropped; no error.  The double-float path (the default of
-                              FP32 and mixed contexts) reports this code. */
+  CPALS_E_SINGULAR = 5,    /* Gamma has a non-finite entry: the factor of that mode was left
+                              unchanged.  A finite Gamma that is not positive definite is no
+                              error: every path (float64 and double-float normal equations, the
+                              fused batch) replaces its inverse by the pseudo-inverse
+                              Gamma^dagger (Algorithm 1): symmetric Jacobi eigendecomposition in
+                              float64, eigenvalues at or below 1e-13 of the largest dropped. */
   CPALS_E_NUMERIC = 6,     /* NaN/Inf detected in a result */
   CPALS_E_TIMEOUT = 7,     /* a bounded device wait gave up */
   CPALS_E_UNSUPPORTED = 8  /* configuration outside what this build implements */
@@ -229,8 +228,9 @@ cpals_status cpals_batch_set_tensor(cpals_batch* b, int i, const void* data, int
 /* instance i's initial factors: three host float64 arrays s_n x R, copied */
 cpals_status cpals_batch_init_factors(cpals_batch* b, int i, const double* const* factors);
 /* Algorithm 3 on every instance from its initial factors for exactly
- * max_sweeps sweeps (fewer for an instance whose Gamma lost positive
- * definiteness or that met a non-finite value), with tolerance eps, the
+ * max_sweeps sweeps (fewer for an instance that met a non-finite value; a
+ * Gamma that is not positive definite is solved through Gamma^dagger), with
+ * tolerance eps, the
  * second-order terms when use_V != 0 and the stopping test inside PP runs
  * (as cpals_set_pp_stop_tol; 0 = off).  Outputs (each nullable):
  * fitness_out[n] the exact fitness of the final factors, sweeps_out[n],
@@ -350,8 +350,7 @@ cpals_status cpals_pp_mttkrp(cpals_ctx* ctx, int n, int use_V, double* out);
  * context currently holds, through the same factorisation and row-solve
  * kernels as a sweep, without changing any state.  rhs, out: s_n x R float64
  * host buffers.  A Gamma^(n) that is not positive definite is solved with its
- * pseudo-inverse (IEEE float64 normal equations) or reported as
- * CPALS_E_SINGULAR (double-float). */
+ * pseudo-inverse Gamma^dagger in every precision. */
 cpals_status cpals_normal_solve(cpals_ctx* ctx, int n, const double* rhs, double* out);
 
 /* Copy A_p^(n) (which = 0) or dA^(n) (which = 1) to a host float64 buffer. */

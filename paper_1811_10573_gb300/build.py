@@ -19,6 +19,7 @@ LIB = os.path.join(HERE, "libcpals.so")
 SOURCES = ["contract.cu", "small.cu", "dfloat.cu", "cpals.cu", "umma.cu", "noalloc.cu", "controller.cu",
            "tucker.cu", "batch.cu"]
 HEADERS = [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "dfloat.cuh"), os.path.join(CSRC, "ctrl_dev.cuh"),
+           os.path.join(CSRC, "jacobi.cuh"),
            os.path.join(ROOT, "include", "cpals.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

@@ -27,10 +27,13 @@
 #include "../../include/cpals.h"
 #include "dfloat.cuh"
 #include "internal.h"
+#include "jacobi.cuh"
 
 namespace {
 
 using cpals::Launch;
+using cpals::pinv_weights;
+using cpals::sym_eig_jacobi;
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -72,7 +75,8 @@ struct BC {
   int ran;                // kind of the sweep being run
   int t;                  // sweeps done
   int in_run;             // PP sweeps of the current PP run
-  int status;             // bit n: Gamma^(n) not positive definite; 1 << 8: non-finite
+  int status;             // bit n: Gamma^(n) not finite; 1 << 8: non-finite fitness or
+                          // factor norms; bit 16 + n: Gamma^(n) solved through Gamma^dagger
   int pad;
   double f_last, f_prev;
 };
@@ -446,9 +450,37 @@ __global__ void __launch_bounds__(128) bchol_kernel(BParams P, int stage, int n,
     __syncthreads();
   }
   if (bad) {
-    if (threadIdx.x == 0) atomicOr(&cc.status, 1 << n);
+    // not positive definite: Gamma = V diag(w) V^T (cyclic Jacobi) and the
+    // dense factor W = diag(w^+)^(1/2) V^T in place of L^-1, so that the
+    // solve's W^T W is Algorithm 1's Gamma^dagger (status bit 16 + n); V is
+    // accumulated in the factor's own storage.  A non-finite Gamma is an
+    // error (bit n).
+    __shared__ double wq[kBR];
+    double* V = dp + b.L;
+    int fin = 1;
+    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
+      const int i = idx / R, j = idx % R;
+      const double g = S[a0 * R * R + idx] * S[a1 * R * R + idx];
+      G[i * RS + j] = g;
+      V[idx] = i == j ? 1.0 : 0.0;
+      fin &= isfinite(g) ? 1 : 0;
+    }
+    if (!__syncthreads_and(fin)) {
+      if (threadIdx.x == 0) atomicOr(&cc.status, 1 << n);
+      return;
+    }
+    sym_eig_jacobi(G, RS, V, R, R);
+    pinv_weights(G, RS, R, true, wq);
+    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
+      const int k = idx / R, c = idx % R;
+      G[k * RS + c] = wq[k] * V[c * R + k];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) V[idx] = G[(idx / R) * RS + idx % R];
+    if (threadIdx.x == 0) atomicOr(&cc.status, 1 << (16 + n));
     return;
   }
+  if (threadIdx.x == 0 && ((cc.status >> (16 + n)) & 1)) atomicAnd(&cc.status, ~(1 << (16 + n)));
   // W = L^-1 (lower triangular), row by row: W[k] = V[k] / L[k][k] with
   // V[i] = e_i - sum_{k<i} L[i][k] W[k] (right-looking: row k of V is final
   // at step k and updates the rows below it).  V[i][c] (c <= i) lives in the
@@ -502,10 +534,11 @@ __global__ void __launch_bounds__(256) bsolve_kernel(BParams P, int stage, int n
   if (!ne_active(stage, c)) return;
   const int R = b.R, s = b.s[n], RS = kBR + 1;
   const bool failed = (c.status >> n) & 1;
+  const bool dense = (c.status >> (16 + n)) & 1;   // W from Gamma^dagger: no zero triangle
   const bool als = ne_als(stage, c);
   const bool v = ne_pp(stage, c) && P.use_V;
   extern __shared__ __align__(16) unsigned char bs_raw[];
-  double* Ws = reinterpret_cast<double*>(bs_raw);              // W[j][k], k <= j
+  double* Ws = reinterpret_cast<double*>(bs_raw);              // W[j][k], k <= j unless dense
   double* bt = Ws + kBR * RS;                                   // b of the tile's rows
   double* ut = bt + kSolveTR * RS;                              // u = b W^T
   T* Zs = reinterpret_cast<T*>(ut + kSolveTR * RS);             // Z in T
@@ -554,10 +587,10 @@ __global__ void __launch_bounds__(256) bsolve_kernel(BParams P, int stage, int n
       for (int q = 0; q < 4; q++) {
         if (q >= nq) break;
         const int j = l + 16 * q;
-        const int kend = min(16 * q + 15, R - 1);   // warp-uniform trip count
+        const int kend = dense ? R - 1 : min(16 * q + 15, R - 1);   // warp-uniform trip count
         double u = 0.0;
         for (int k = 0; k <= kend; k++)
-          if (k <= j) u = fma(bt[t * RS + k], Ws[j * RS + k], u);
+          if (dense || k <= j) u = fma(bt[t * RS + k], Ws[j * RS + k], u);
         if (j < R) ut[t * RS + j] = u;
       }
     }
@@ -570,8 +603,8 @@ __global__ void __launch_bounds__(256) bsolve_kernel(BParams P, int stage, int n
       // a_r = sum_{j >= r} u_j W[j][r]
       const int r = l + 16 * q;
       double a = 0.0;
-      for (int j = 16 * q; j < R; j++)
-        if (j >= r) a = fma(ut[t * RS + j], Ws[j * RS + r], a);
+      for (int j = dense ? 0 : 16 * q; j < R; j++)
+        if (dense || j >= r) a = fma(ut[t * RS + j], Ws[j * RS + r], a);
       av[q] = a;
     }
     double nd = 0.0, na = 0.0;
@@ -727,7 +760,8 @@ using namespace cpals::dfa;
 // unused upper part of G as in the float64 kernel), all double-float; Z =
 // W^(a) * W^(b) in float for the second-order terms.  1 / L[k][k] is the
 // pivot's reciprocal square root, taken once.
-__global__ void __launch_bounds__(256) bchol_df_kernel(BParams P, int stage, int n, float* __restrict__ tp) {
+__global__ void __launch_bounds__(256) bchol_df_kernel(BParams P, int stage, int n, float* __restrict__ tp,
+                                                       double* __restrict__ dp) {
   BC& cc = P.ctl[blockIdx.y];
   const BI& b = P.bi[blockIdx.y];
   if (!ne_active(stage, cc)) return;
@@ -774,9 +808,38 @@ __global__ void __launch_bounds__(256) bchol_df_kernel(BParams P, int stage, int
     __syncthreads();
   }
   if (bad) {
-    if (threadIdx.x == 0) atomicOr(&cc.status, 1 << n);
+    // not positive definite: the dense factor W = diag(w^+)^(1/2) V^T of
+    // Gamma^dagger as in the float64 kernel, from Gamma in float64 (G's
+    // storage reused), V in the float64 scratch dp[b.L]; written as
+    // double-float (status bit 16 + n)
+    __shared__ double wq[kBR];
+    double* Gd = reinterpret_cast<double*>(G);
+    double* V = dp + b.L;
+    int fin = 1;
+    for (int idx = threadIdx.x; idx < RR; idx += blockDim.x) {
+      const int i = idx / R, j = idx % R;
+      const double g = ((double)sh[a0 * RR + idx] + (double)sl[a0 * RR + idx]) *
+                       ((double)sh[a1 * RR + idx] + (double)sl[a1 * RR + idx]);
+      Gd[i * RS + j] = g;
+      V[idx] = i == j ? 1.0 : 0.0;
+      fin &= isfinite(g) ? 1 : 0;
+    }
+    if (!__syncthreads_and(fin)) {
+      if (threadIdx.x == 0) atomicOr(&cc.status, 1 << n);
+      return;
+    }
+    sym_eig_jacobi(Gd, RS, V, R, R);
+    pinv_weights(Gd, RS, R, true, wq);
+    for (int idx = threadIdx.x; idx < RR; idx += blockDim.x) {
+      const int k = idx / R, c = idx % R;
+      const dfl f = df_of(wq[k] * V[c * R + k]);
+      tp[b.lih + idx] = f.hi;
+      tp[b.lil + idx] = f.lo;
+    }
+    if (threadIdx.x == 0) atomicOr(&cc.status, 1 << (16 + n));
     return;
   }
+  if (threadIdx.x == 0 && ((cc.status >> (16 + n)) & 1)) atomicAnd(&cc.status, ~(1 << (16 + n)));
   for (int idx = threadIdx.x; idx < RR; idx += blockDim.x) {
     const int i = idx / R, c = idx % R;
     if (c <= i) G[c * RS + i + 1] = make_float2(i == c ? 1.f : 0.f, 0.f);
@@ -818,6 +881,7 @@ __global__ void __launch_bounds__(256) bsolve_df_kernel(BParams P, int stage, in
   const int R = b.R, s = b.s[n], RS = kBR + 1;
   const bool failed = (c.status >> n) & 1;
   if (failed) return;                            // the mode keeps its factor and dA
+  const bool dense = (c.status >> (16 + n)) & 1;   // W from Gamma^dagger: no zero triangle
   const bool als = ne_als(stage, c);
   const bool v = ne_pp(stage, c) && P.use_V;
   extern __shared__ __align__(16) unsigned char bs_raw[];
@@ -865,10 +929,10 @@ __global__ void __launch_bounds__(256) bsolve_df_kernel(BParams P, int stage, in
     for (int q = 0; q < 4; q++) {
       if (q >= nq) break;
       const int j = l + 16 * q;
-      const int kend = min(16 * q + 15, R - 1);
+      const int kend = dense ? R - 1 : min(16 * q + 15, R - 1);
       dfl u{0.f, 0.f};
       for (int k = 0; k <= kend; k++)
-        if (k <= j) u = df_add(u, df_mul(upk(bt[t * RS + k]), upk(Ws[j * RS + k])));
+        if (dense || k <= j) u = df_add(u, df_mul(upk(bt[t * RS + k]), upk(Ws[j * RS + k])));
       if (j < R) ut[t * RS + j] = pk(u);
     }
     __syncthreads();
@@ -878,8 +942,8 @@ __global__ void __launch_bounds__(256) bsolve_df_kernel(BParams P, int stage, in
       if (q >= nq) break;
       const int r = l + 16 * q;
       dfl a{0.f, 0.f};
-      for (int j = 16 * q; j < R; j++)
-        if (j >= r) a = df_add(a, df_mul(upk(ut[t * RS + j]), upk(Ws[j * RS + r])));
+      for (int j = dense ? 0 : 16 * q; j < R; j++)
+        if (dense || j >= r) a = df_add(a, df_mul(upk(ut[t * RS + j]), upk(Ws[j * RS + r])));
       if (r >= R || !on) continue;
       const int64_t o = (int64_t)y * R + r;
       const dfl d = df_sub(a, dfl{Rh[o], Rl[o]});   // reads A_old before it is replaced
@@ -1183,7 +1247,7 @@ __global__ void bdecide_kernel(BParams P, int n_inst, int first, double* __restr
   bool finite = isfinite(f);
   for (int n = 0; n < 3; n++) finite = finite && isfinite(dp[b.sc + 8 + 2 * n]) && isfinite(dp[b.sc + 9 + 2 * n]);
   if (!finite) c.status |= 1 << 8;
-  if (c.status || c.t >= P.max_sweeps) {
+  if ((c.status & 0xffff) || c.t >= P.max_sweeps) {   // bits 16 + n: Gamma^dagger used
     c.ran = c.next = K_DONE;
     return;
   }
@@ -1399,7 +1463,7 @@ int64_t sweep_launches(cpals_batch* b, const BParams& P) {
   const dim3 gel((unsigned)el_grid(b->el_max), N);
   auto mode = [&](int stage, int n) {
     if constexpr (sizeof(T) == 4) {
-      bchol_df_kernel<<<dim3(1, N), 256, 0, s>>>(P, stage, n, tp);
+      bchol_df_kernel<<<dim3(1, N), 256, 0, s>>>(P, stage, n, tp, dp);
       bsolve_df_kernel<<<gsolve, 256, bsolve_df_smem(), s>>>(P, stage, n, tp, dp);
       bgram_df_kernel<<<dim3(kGramCtas, N), 256, 0, s>>>(P, stage, n, tp, dp);
     } else {
@@ -1721,7 +1785,8 @@ cpals_status cpals_batch_run(cpals_batch* b, int max_sweeps, double eps, int use
   for (int i = 0; i < b->n; i++) {
     if (sweeps_out) sweeps_out[i] = ctl[i].t;
     if (status_out)
-      status_out[i] = (ctl[i].status >> 8) & 1 ? CPALS_E_NUMERIC : (ctl[i].status ? CPALS_E_SINGULAR : CPALS_OK);
+      status_out[i] = (ctl[i].status >> 8) & 1 ? CPALS_E_NUMERIC
+                                                : ((ctl[i].status & 0xffff) ? CPALS_E_SINGULAR : CPALS_OK);
     if (fitness_out) BCK(cudaMemcpy(&fitness_out[i], b->dp + b->bi[i].sc, 8, cudaMemcpyDeviceToHost));
   }
   if (kind_trace) BCK(cudaMemcpy(kind_trace, b->d_ktrace, cap * 4, cudaMemcpyDeviceToHost));

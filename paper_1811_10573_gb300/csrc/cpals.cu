@@ -712,7 +712,7 @@ cpals_status check_status(cpals_ctx* c) {
   if (c->status_h[0] & 0xffff) {        // bits 16 + n: Gamma^dagger used (not an error)
     const int bits = c->status_h[0] & 0xffff;
     CK(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->stream));
-    return c->fail(CPALS_E_SINGULAR, "Gamma not positive definite for mode mask " + std::to_string(bits) +
+    return c->fail(CPALS_E_SINGULAR, "Gamma not finite for mode mask " + std::to_string(bits) +
                                          "; those factors were left unchanged");
   }
   return CPALS_OK;
@@ -958,56 +958,77 @@ __device__ bool loop_all_small(const LoopState* s, const double* scal) {
 // The learned controller's decision (as cpals_run_controlled's host loop):
 // the network's most probable action when its probability reaches the
 // confidence and it is not a PP sweep without valid operators, else the
-// rule's branch; returns the branch (0 ALS, 1 rebuild + PP, 2 PP).
+// rule's branch; returns the branch (0 ALS, 1 rebuild + PP, 2 PP) on every
+// lane.  One warp: lane 0 forms the features, the lanes the hidden units.
 __device__ int loop_ctrl_choose(LoopState* s, const double* scal, int rule_branch) {
-  // the history and the 8 + 2N scalars the features use, as local copies
-  // (features computed through the LoopState and scalar pointers directly
-  // came out as those of the run's first decision in this kernel)
-  float x[20], pr[3];
-  const CtrlState h = s->ch;
-  double sc[8 + 2 * kMaxModes];
-  for (int i = 0; i < 8 + 2 * s->N; i++) sc[i] = scal[i];
-  ctrl_features(h, sc, s->N, s->eps, x);
-  mlp_probs(s->params, 20, x, pr);
-  for (int i = 0; i < 20; i++) s->last_x[i] = x[i];
-  for (int i = 0; i < 3; i++) s->last_p[i] = pr[i];
-  int best = 0;
-  for (int k = 1; k < 3; k++)
-    if (pr[k] > pr[best]) best = k;
-  s->src_next = 0;
-  if (pr[best] >= s->conf && !(best == ACT_PP && !s->ch.pp_ready)) {
-    s->src_next = 1;
-    return best == ACT_ALS ? 0 : (best == ACT_REBUILD ? 1 : 2);
+  __shared__ float x[20], hsm[32], pr[3];
+  __shared__ int out;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    // the history and the 8 + 2N scalars the features use, as local copies
+    // (features computed through the LoopState and scalar pointers directly
+    // came out as those of the run's first decision in this kernel)
+    const CtrlState h = s->ch;
+    double sc[8 + 2 * kMaxModes];
+    for (int i = 0; i < 8 + 2 * s->N; i++) sc[i] = scal[i];
+    ctrl_features(h, sc, s->N, s->eps, x);
   }
-  return rule_branch;
+  __syncwarp();
+  mlp_probs_warp<20>(s->params, x, hsm, pr);
+  if (lane == 0) {
+    for (int i = 0; i < 20; i++) s->last_x[i] = x[i];
+    for (int i = 0; i < 3; i++) s->last_p[i] = pr[i];
+    int best = 0;
+    for (int k = 1; k < 3; k++)
+      if (pr[k] > pr[best]) best = k;
+    s->src_next = 0;
+    out = rule_branch;
+    if (pr[best] >= s->conf && !(best == ACT_PP && !s->ch.pp_ready)) {
+      s->src_next = 1;
+      out = best == ACT_ALS ? 0 : (best == ACT_REBUILD ? 1 : 2);
+    }
+  }
+  __syncwarp();
+  return out;
 }
 
+// One warp (the node's 32 threads): lane 0 runs the rule, the warp the
+// controller when there is one.
 __global__ void loop_init_kernel(LoopState* s, const double* scal, cudaGraphConditionalHandle hw,
                                  cudaGraphConditionalHandle hs) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  s->t = 0;
-  s->hit = 0;
-  s->err = 0;
-  s->confirms = 0;
-  s->f_last = s->f_prev = -1e300;
-  s->in_run = 0;
-  s->next = loop_all_small(s, scal) ? 1 : 0;   // the test at the head of the first sweep
-  s->src_next = 0;
-  if (s->ctrl) {
-    ctrl_state_start(s->ch, scal[0]);
-    s->next = loop_ctrl_choose(s, scal, s->next);
+  if (threadIdx.x >= 32 || blockIdx.x != 0) return;
+  __shared__ int ask, rule;
+  if (threadIdx.x == 0) {
+    s->t = 0;
+    s->hit = 0;
+    s->err = 0;
+    s->confirms = 0;
+    s->f_last = s->f_prev = -1e300;
+    s->in_run = 0;
+    s->next = loop_all_small(s, scal) ? 1 : 0;   // the test at the head of the first sweep
+    s->src_next = 0;
+    if (s->ctrl) ctrl_state_start(s->ch, scal[0]);
+    ask = s->ctrl;
+    rule = s->next;
   }
-  s->t0 = global_ns();
-  cudaGraphSetConditional(hs, (unsigned)s->next);
-  cudaGraphSetConditional(hw, s->max_sweeps > 0 ? 1u : 0u);
+  __syncwarp();
+  if (ask) {
+    const int nx = loop_ctrl_choose(s, scal, rule);
+    if (threadIdx.x == 0) s->next = nx;
+  }
+  if (threadIdx.x == 0) {
+    s->t0 = global_ns();
+    cudaGraphSetConditional(hs, (unsigned)s->next);
+    cudaGraphSetConditional(hw, s->max_sweeps > 0 ? 1u : 0u);
+  }
 }
 
-// The switch's value persists between iterations (its handle has no default
-// assignment): each decision sets it for the next iteration.
-__global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* status, double* ftr,
-                                   int* ktr, double* ttr, cudaGraphConditionalHandle hw,
-                                   cudaGraphConditionalHandle hs) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Lane 0's part of the decision after a sweep: records the sweep, ends the
+// loop or sets the rule's next branch.  Returns 1 when the learned
+// controller is to take the decision (the caller sets the switch then).
+__device__ int loop_decide_rule(LoopState* s, const double* scal, const int* status, double* ftr,
+                                int* ktr, double* ttr, cudaGraphConditionalHandle hw,
+                                cudaGraphConditionalHandle hs) {
   int ran = s->next;
   const double f = scal[0];
   auto record = [&](int kind, double fv) {
@@ -1051,7 +1072,7 @@ __global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* 
         s->next = 3;
         cudaGraphSetConditional(hs, 3u);
         cudaGraphSetConditional(hw, 1u);
-        return;
+        return 0;
       } else {
         if (ran == 0 && s->target > 0.0 && f >= s->target) s->hit = 1;
         record(ran, f);
@@ -1060,17 +1081,40 @@ __global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* 
   }
   if (stop || s->hit || s->t >= s->max_sweeps) {
     cudaGraphSetConditional(hw, 0u);
-    return;
+    return 0;
   }
   const bool small = loop_all_small(s, scal);
   // from the third sweep of a PP run on, the stopping test also asks the
   // last PP sweep for a gain of tol over the one before it
   const bool gain = !(s->tol > 0.0) || s->in_run < 2 || s->f_last - s->f_prev >= s->tol;
   s->next = ran != 0 ? ((small && gain) ? 2 : 0) : (small ? 1 : 0);
-  if (s->ctrl) s->next = loop_ctrl_choose(s, scal, s->next);
+  if (s->ctrl) return 1;
   cudaGraphSetConditional(hs, (unsigned)s->next);
   cudaGraphSetConditional(hw, 1u);
+  return 0;
 }
+
+// The switch's value persists between iterations (its handle has no default
+// assignment): each decision sets it for the next iteration.
+__global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* status, double* ftr,
+                                   int* ktr, double* ttr, cudaGraphConditionalHandle hw,
+                                   cudaGraphConditionalHandle hs) {
+  if (threadIdx.x >= 32 || blockIdx.x != 0) return;
+  __shared__ int ask, rule;
+  if (threadIdx.x == 0) {
+    ask = loop_decide_rule(s, scal, status, ftr, ktr, ttr, hw, hs);
+    rule = s->next;
+  }
+  __syncwarp();
+  if (!ask) return;
+  const int nx = loop_ctrl_choose(s, scal, rule);
+  if (threadIdx.x == 0) {
+    s->next = nx;
+    cudaGraphSetConditional(hs, (unsigned)nx);
+    cudaGraphSetConditional(hw, 1u);
+  }
+}
+
 
 cudaError_t add_kernel_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
                             void* func, void** args) {
@@ -1880,8 +1924,10 @@ cpals_status cpals_controller_log(cpals_ctx* c, int steps, double eps, int use_V
           st = do_action(c, d == 0 ? cand[k] : (cand[k] == ACT_ALS ? ACT_ALS : ACT_PP), use_V != 0);
       }
       const double dt = std::chrono::duration<double>(now() - ta).count();
-      if (st == CPALS_E_SINGULAR) {
-        // a trial that breaks down (Gamma not positive definite) loses
+      if (st == CPALS_E_SINGULAR || st == CPALS_E_NUMERIC) {
+        // a trial that breaks down (a non-finite Gamma, factor or fitness:
+        // approximated sweeps can diverge) loses; the next trial and the
+        // labelled action start from the snapshot
         st = CPALS_OK;
         continue;
       }
@@ -2102,7 +2148,7 @@ cpals_status cpals_normal_solve(cpals_ctx* c, int n, const double* rhs, double* 
   CK(cudaMemcpy(out, c->dscr[1], cnt * 8, cudaMemcpyDeviceToHost));
   if (c->status_h[0] & 0xffff) {
     CK(cudaMemset(c->status, 0, 16));
-    return c->fail(CPALS_E_SINGULAR, "Gamma not positive definite");
+    return c->fail(CPALS_E_SINGULAR, "Gamma not finite");
   }
   return CPALS_OK;
 }

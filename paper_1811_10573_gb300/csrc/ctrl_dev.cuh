@@ -113,4 +113,43 @@ __device__ inline void mlp_probs(const float* __restrict__ params, int F, const 
   for (int c = 0; c < C; c++) probs[c] = z[c] / s;
 }
 
+// The same forward pass on one warp (all 32 lanes call it): lane j forms
+// hidden unit j (the network has exactly 32) with mlp_probs' order of terms,
+// and lane 0 forms the outputs in mlp_probs' order too, so the
+// probabilities are bitwise those of mlp_probs.  x: the F inputs and hs:
+// 32 floats of scratch, both in shared memory; probs is written by lane 0
+// and visible to every lane on return.
+template <int F>
+__device__ inline void mlp_probs_warp(const float* __restrict__ params, const float* x, float* hs,
+                                      float* probs) {
+  constexpr int H = 32, C = 3;
+  const int j = threadIdx.x & 31;
+  const float* W1 = params;
+  const float* b1 = W1 + H * F;
+  const float* W2 = b1 + H;
+  const float* b2 = W2 + C * H;
+  float a = b1[j];
+#pragma unroll
+  for (int k = 0; k < F; k++) a = fmaf(W1[j * F + k], x[k], a);
+  hs[j] = fmaxf(a, 0.f);
+  __syncwarp();
+  if (j == 0) {
+    float z[C], zmax = -3.4e38f;
+    for (int c = 0; c < C; c++) {
+      float acc = b2[c];
+#pragma unroll
+      for (int q = 0; q < H; q++) acc = fmaf(W2[c * H + q], hs[q], acc);
+      z[c] = acc;
+      zmax = fmaxf(zmax, acc);
+    }
+    float sum = 0.f;
+    for (int c = 0; c < C; c++) {
+      z[c] = __expf(z[c] - zmax);
+      sum += z[c];
+    }
+    for (int c = 0; c < C; c++) probs[c] = z[c] / sum;
+  }
+  __syncwarp();
+}
+
 }  // namespace cpals

@@ -18,6 +18,7 @@
 
 #include "dfloat.cuh"
 #include "internal.h"
+#include "jacobi.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -869,6 +870,65 @@ __device__ __forceinline__ void dot2_acc(dfl& s, dfl a, dfl b) {
   s.lo = __fadd_rn(s.lo, __fadd_rn(t.lo, e));
 }
 
+// ---------------------------------------------------------------- Gamma^dagger
+// Algorithm 1 writes the pseudo-inverse Gamma^dagger (Sec. 2.3).  When the
+// factorisation above met a pivot that is not positive (status bit n), this
+// CTA takes Gamma in float64 (from Gpk, else the Grams' hi + lo), finds
+// Gamma = V diag(w) V^T by cyclic Jacobi and writes the factor
+// W = diag(w^+)^(1/2) V^T in place of L^-1 (dense, row stride R|1), so that
+// the row solve's a = W^T W b is b Gamma^dagger; eigenvalues at or below
+// 1e-13 of the largest are dropped.  Status: bit n cleared and bit 16 + n
+// set (the solve then runs over the dense W); a non-finite Gamma keeps bit n
+// (an error).  Without a failed pivot the CTA only clears bit 16 + n.  V is
+// accumulated in Wout's storage (R x R float64 fits in R x (R|1) float2).
+__global__ void __launch_bounds__(512)
+pinv_df_kernel(const float* __restrict__ Shi, const float* __restrict__ Slo,
+               const float2* __restrict__ Gpk, int N, int n, int R, float2* __restrict__ Wout,
+               int* __restrict__ status) {
+  extern __shared__ double Gd[];
+  __shared__ double w[kMaxRank];
+  const int st = *reinterpret_cast<volatile int*>(status);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (!((st >> n) & 1)) {
+    if (tid == 0 && ((st >> (16 + n)) & 1)) atomicAnd(status, ~(1 << (16 + n)));
+    return;
+  }
+  const int RR = R * R, RS = R | 1;
+  double* V = reinterpret_cast<double*>(Wout);
+  int fin = 1;
+  for (int idx = tid; idx < RR; idx += nt) {
+    const int i = idx / R, j = idx % R;
+    double g = 1.0;
+    if (Gpk) {
+      const int a = max(i, j), b = min(i, j);
+      const float2 v = Gpk[col_start(b, R) + a - b];
+      g = (double)v.x + (double)v.y;
+    } else {
+      for (int k = 0; k < N; k++)
+        if (k != n) g *= (double)Shi[(int64_t)k * RR + idx] + (double)Slo[(int64_t)k * RR + idx];
+    }
+    Gd[i * RS + j] = g;
+    V[idx] = i == j ? 1.0 : 0.0;
+    fin &= isfinite(g) ? 1 : 0;
+  }
+  if (!__syncthreads_and(fin)) return;
+  sym_eig_jacobi(Gd, RS, V, R, R);
+  pinv_weights(Gd, RS, R, true, w);
+  for (int idx = tid; idx < RR; idx += nt) {
+    const int k = idx / R, c = idx % R;
+    Gd[k * RS + c] = w[k] * V[c * R + k];
+  }
+  __syncthreads();                             // every read of V precedes the first write of W
+  for (int idx = tid; idx < RR; idx += nt) {
+    const int k = idx / R, c = idx % R;
+    Wout[k * RS + c] = pk(df_of(Gd[k * RS + c]));
+  }
+  if (tid == 0) {
+    atomicAnd(status, ~(1 << n));
+    atomicOr(status, 1 << (16 + n));
+  }
+}
+
 // Row y of the normal equations, a Gamma = b (b = rhs, plus A_old Z for the
 // second-order PP terms), solved as a = W^T (W b) with W = L^-1 from the
 // factorisation kernel: two triangular products instead of two substitution
@@ -904,6 +964,7 @@ solve_inv_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float
   __shared__ float as[kRB][kMaxRank];
   __shared__ float2 red[kRB][2][kMaxRank / 32];
   const bool failed = (status[0] >> n) & 1;
+  const bool dense = (status[0] >> (16 + n)) & 1;   // W = diag(w^+)^(1/2) V^T, not L^-1
   const int Rp = (R + 31) / 32 * 32;
   const int h = threadIdx.x >= Rp;              // half of the terms
   const int r = threadIdx.x - h * Rp, lane = r & 31, warp = r >> 5, nwarp = Rp >> 5;
@@ -944,10 +1005,11 @@ solve_inv_df_kernel(const float* __restrict__ rhs, double* __restrict__ A, float
     return;
   }
   // y_r = sum_{c <= r} W_rc b_c: half 0 takes c < m, half 1 c >= m
-  const int wend = min(R, 32 * warp + 32);      // W row r is zero beyond column r
+  const int wend = dense ? R : min(R, 32 * warp + 32);   // L^-1 row r is zero beyond column r
   const int c1a = h ? m : 0, c1b = h ? wend : min(m, wend);
   // a_r = sum_{c >= r} W_cr y_c: half 0 takes c < m, half 1 c >= m
-  const int c2a = h ? max(m, 32 * warp) : 32 * warp, c2b = h ? R : m;
+  const int wbeg = dense ? 0 : 32 * warp;
+  const int c2a = h ? max(m, wbeg) : wbeg, c2b = h ? R : m;
   for (int y0 = blockIdx.x * kRB; y0 < s; y0 += gridDim.x * kRB) {
     float oh[kRB], ol[kRB];
     dfl a[kRB];
@@ -1076,6 +1138,9 @@ cudaError_t setup_df_kernels() {
                                        (int)chol_inv_smem(kMaxRank));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(solve_inv_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sv);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pinv_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kMaxRank * RSmax * sizeof(double)));
   return e;
 }
 
@@ -1119,6 +1184,9 @@ void chol_df(const float* Shi, const float* Slo, const float* W, const float2* G
   const int threads = std::min(CPALS_CHOL_THREADS, std::max(192, (T / 8 + 31) / 32 * 32));
   chol_inv_df_kernel<<<5, threads, chol_inv_smem(R), L.stream>>>(Shi, Slo, W, Gpk, N, n, R, Winv,
                                                                  Z, useV ? 1 : 0, status);
+  (*L.counter)++;
+  pinv_df_kernel<<<1, 512, (size_t)R * (R | 1) * sizeof(double), L.stream>>>(Shi, Slo, Gpk, N, n, R,
+                                                                             Winv, status);
   (*L.counter)++;
 }
 

@@ -3,6 +3,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "jacobi.cuh"
 
 namespace cpals {
 
@@ -45,25 +46,18 @@ __device__ __forceinline__ double rsqrt_refined(double x) {
 // ---------------------------------------------------------------- Gamma^dagger
 // Algorithm 1 writes the pseudo-inverse Gamma^dagger; the Cholesky route
 // below covers a positive definite Gamma, and this fallback the rest: the
-// symmetric eigendecomposition Gamma = V diag(w) V^T by the cyclic Jacobi
-// method (Golub & Van Loan, the symmetric Schur 2 x 2 rotation and the
-// round-robin parallel ordering: R/2 disjoint rotations per round, R - 1
-// rounds per sweep, sweeps until the off-diagonal Frobenius norm is below
-// 1e-15 of the total), then Gamma^dagger = V diag(w^+) V^T with eigenvalues at
-// or below 1e-13 of the largest dropped.  G (shared memory, row stride RS)
-// is rebuilt from the Grams (the factorisation overwrote it); V lives in
-// Pout, which receives Gamma^dagger at the end.  Returns false if Gamma has a
+// symmetric eigendecomposition Gamma = V diag(w) V^T (cyclic Jacobi,
+// sym_eig_jacobi), then Gamma^dagger = V diag(w^+) V^T with eigenvalues at or
+// below 1e-13 of the largest dropped.  G (shared memory, row stride RS) is
+// rebuilt from the Grams (the factorisation overwrote it); V lives in Pout,
+// which receives Gamma^dagger at the end.  Returns false if Gamma has a
 // non-finite entry.
-constexpr int kJacobiSweeps = 30;
+static_assert(kMaxRank <= kJacobiMaxRank, "Jacobi scratch");
 
 __device__ bool gamma_pinv(const double* __restrict__ S, int N, int n, int R, double* G,
                            double* __restrict__ Pout) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int RR = R * R, RS = R | 1;
-  __shared__ double rc[kMaxRank / 2 + 1], rs_[kMaxRank / 2 + 1];
-  __shared__ int rp[kMaxRank / 2 + 1], rq[kMaxRank / 2 + 1];
-  __shared__ double red[2][32];
   __shared__ double w[kMaxRank];
   int fin = 1;
   for (int idx = tid; idx < RR; idx += nt) {
@@ -76,93 +70,8 @@ __device__ bool gamma_pinv(const double* __restrict__ S, int N, int n, int R, do
     fin &= isfinite(g) ? 1 : 0;
   }
   if (!__syncthreads_and(fin)) return false;
-  const int m = R + (R & 1);                  // round-robin players (one idle when R is odd)
-  for (int sweep = 0; sweep < kJacobiSweeps; sweep++) {
-    double off = 0.0, tot = 0.0;
-    for (int idx = tid; idx < RR; idx += nt) {
-      const int i = idx / R, j = idx % R;
-      const double v = G[i * RS + j];
-      tot = fma(v, v, tot);
-      if (i != j) off = fma(v, v, off);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    }
-    if (lane == 0) {
-      red[0][warp] = off;
-      red[1][warp] = tot;
-    }
-    __syncthreads();
-    off = 0.0;
-    tot = 0.0;
-    for (int k = 0; k < nw; k++) {
-      off += red[0][k];
-      tot += red[1][k];
-    }
-    __syncthreads();                            // red is reused by the next sweep
-    if (off <= 1e-30 * tot) break;
-    for (int rd = 0; rd < m - 1; rd++) {
-      for (int k = tid; k < m / 2; k += nt) {
-        const int a = k == 0 ? m - 1 : (rd + k) % (m - 1);
-        const int b = k == 0 ? rd : (rd - k + m - 1) % (m - 1);
-        const int p = min(a, b), q = max(a, b);
-        double c = 1.0, s = 0.0;
-        if (q < R) {
-          const double apq = G[p * RS + q];
-          if (apq != 0.0) {
-            const double th = (G[q * RS + q] - G[p * RS + p]) / (2.0 * apq);
-            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(fma(th, th, 1.0)));
-            c = 1.0 / sqrt(fma(t, t, 1.0));
-            s = t * c;
-          }
-        }
-        rp[k] = p;
-        rq[k] = q;
-        rc[k] = c;
-        rs_[k] = s;
-      }
-      __syncthreads();
-      // rows p and q of every pair: G <- J^T G
-      for (int e = tid; e < (m / 2) * R; e += nt) {
-        const int k = e / R, j = e % R;
-        const double s = rs_[k];
-        if (rq[k] >= R || s == 0.0) continue;
-        const double c = rc[k];
-        double* gp = G + rp[k] * RS + j;
-        double* gq = G + rq[k] * RS + j;
-        const double x = *gp, y = *gq;
-        *gp = c * x - s * y;
-        *gq = s * x + c * y;
-      }
-      __syncthreads();
-      // columns p and q: G <- G J, V <- V J
-      for (int e = tid; e < (m / 2) * R; e += nt) {
-        const int k = e / R, i = e % R;
-        const double s = rs_[k];
-        if (rq[k] >= R || s == 0.0) continue;
-        const double c = rc[k];
-        const int p = rp[k], q = rq[k];
-        const double x = G[i * RS + p], y = G[i * RS + q];
-        G[i * RS + p] = c * x - s * y;
-        G[i * RS + q] = s * x + c * y;
-        const double vx = Pout[i * R + p], vy = Pout[i * R + q];
-        Pout[i * R + p] = c * vx - s * vy;
-        Pout[i * R + q] = s * vx + c * vy;
-      }
-      __syncthreads();
-    }
-  }
-  // w^+ with the relative cut-off, then Gamma^dagger = V diag(w^+) V^T
-  for (int i = tid; i < R; i += nt) w[i] = G[i * RS + i];
-  __syncthreads();
-  double wmax = 0.0;
-  for (int i = 0; i < R; i++) wmax = fmax(wmax, w[i]);
-  const double cut = 1e-13 * wmax;
-  __syncthreads();
-  for (int i = tid; i < R; i += nt) w[i] = w[i] > cut ? 1.0 / w[i] : 0.0;
-  __syncthreads();
+  sym_eig_jacobi(G, RS, Pout, R, R);
+  pinv_weights(G, RS, R, false, w);
   for (int idx = tid; idx < RR; idx += nt) {
     const int i = idx / R, j = idx % R;
     double acc = 0.0;

@@ -99,3 +99,44 @@ def test_batch_autotuner_cache_and_results(probs):
     assert np.array_equal(ra["fitness"], rb["fitness"])
     for x, y in zip(ra["trace"], rb["trace"]):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_singular_gamma_pinv(prec):
+    """An instance whose initial factors share a zero column keeps every
+    Gamma^(n) singular (a zero row and column); the batch's normal equations
+    then solve through Gamma^dagger (Algorithm 1: a Jacobi eigendecomposition
+    and the dense factor diag(w^+)^(1/2) V^T), so that instance is the
+    oracle's rank R - 1 run without the column (float64: sweep for sweep
+    within 1e-10; float32: final fitness within 1e-4) with the column exactly
+    zero, while the regular instance in the same launches is unaffected."""
+    R, col = 5, 2
+    qs = synth.batch_order3(count=2, seed=11, smin=10, smax=16, rmin=R, rmax=R)
+    keep = [r for r in range(R) if r != col]
+    A0s = [[a.copy() for a in q.A0] for q in qs]
+    for a in A0s[1]:
+        a[:, col] = 0.0
+    b = cpals.Batch([q.dims for q in qs], [R, R], prec)
+    with b:
+        for i, q in enumerate(qs):
+            b.set_tensor(i, np.ascontiguousarray(q.X))
+            b.init_factors(i, A0s[i])
+        out = b.run(SWEEPS, EPS, True, 0.0)
+        facs = [b.get_factors(i) for i in range(2)]
+    assert list(out["status"]) == [0, 0]
+    refs = [O.pp_cp_als(qs[0].X.astype(np.float64), A0s[0], SWEEPS, EPS, use_V=True),
+            O.pp_cp_als(qs[1].X.astype(np.float64), [a[:, keep] for a in A0s[1]], SWEEPS, EPS,
+                        use_V=True)]
+    for a in facs[1]:
+        assert np.all(a[:, col] == 0.0)
+    for i, (A_or, tr) in enumerate(refs):
+        got = facs[i] if i == 0 else [a[:, keep] for a in facs[i]]
+        if prec == "fp64":
+            assert out["kinds"][i] == tr.kinds, i
+            np.testing.assert_allclose(out["trace"][i], tr.seen, rtol=0, atol=1e-10)
+            assert abs(out["fitness"][i] - tr.fitness[-1]) < 1e-10, i
+            for a, ref in zip(got, A_or):
+                assert np.max(np.abs(a - ref)) / np.max(np.abs(ref)) < 1e-8, i
+        else:
+            assert abs(out["fitness"][i] - tr.fitness[-1]) < 1e-4, i
+    assert "pp_approx" in refs[1][1].kinds
