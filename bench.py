@@ -45,6 +45,7 @@ CSRC = os.path.join(ROOT, "paper_1811_10573_gb300", "csrc")
 # FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2070 MHz
 # (the 1.25 TFLOP/s FP64 figure of the part at its maximum SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # Algorithm 3's stopping test inside PP runs (fitness-difference form): a PP
 # run goes on only while each sweep gains at least the target's own margin
 PP_STOP_TOL = 1e-6
@@ -495,13 +496,20 @@ def run_ours(args):
                     "hbm_gbs": round(fl["bytes"] / sec / 1e9, 1), **common,
                     "peak_src": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (the part's "
                                 "1.25 TFLOP/s FP64 rate); not a measured peak"}
+    elif hp == "fp32":
+        ach = fl["flops"] / sec / 1e12
+        roofline = {"bound": "alu", "achieved": round(ach, 3), "peak": round(FP32_PEAK_TFLOPS, 3),
+                    "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                    "kernel": "first-level contraction (float32 FMA, gemm_f32 / gemm_simt)",
+                    "hbm_gbs": round(fl["bytes"] / sec / 1e9, 1), **common,
+                    "peak_src": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz; "
+                                "not a measured peak"}
     else:
         ach = fl["bytes"] / sec / 1e9
         roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": round(ach / pk["hbm_gbs"], 4),
-                    "traffic": committed_traffic("umma_gemm", name, hp, "umma.cu") if hp == "mixed" else None,
-                    "kernel": "first-level contraction (tcgen05 bf16)" if hp == "mixed"
-                    else "first-level contraction (float32 FMA, gemm_simt)",
+                    "traffic": committed_traffic("umma_gemm", name, hp, "umma.cu"),
+                    "kernel": "first-level contraction (tcgen05 bf16)",
                     "tflops": round(fl["flops"] / sec / 1e12, 2), **common,
                     "peak_src": pk["src"] + " (copy bandwidth)"}
     pc_ach = pc["bytes"] / (pc["total_ms"] / 1e3) / 1e9 if pc["total_ms"] > 0 else 0.0
@@ -616,7 +624,7 @@ def precision_block(prec, ctx, dims, R, seeds, probs, Xd, target, f_star, runner
         per[str(s)] = e
     # the tensor-core roofline: CUDA events around every first-level
     # contraction of one more PP-ALS run of the first seed (host loop)
-    g.set_profiling(prec == "mixed")
+    g.set_profiling(prec in ("mixed", "fp32"))
     g.set_tensor(Xd[seeds[0]])
     runner.run(g, probs[seeds[0]].A0, max_sweeps, eps, target[seeds[0]])
     g.reset_stats()
@@ -661,6 +669,15 @@ def precision_block(prec, ctx, dims, R, seeds, probs, Xd, target, f_star, runner
                               "tflops": round(st["flops"] / (st["total_ms"] / 1e3) / 1e12, 2),
                               "peak_src": pk["src"] + " (copy bandwidth)"}
         summ["roofline_tc_frac"] = out["roofline_tc"]["frac"]
+    if prec == "fp32" and st["total_ms"] > 0:
+        ach = st["flops"] / (st["total_ms"] / 1e3) / 1e12
+        out["roofline_fp32"] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(FP32_PEAK_TFLOPS, 3),
+                                "unit": "TFLOP/s", "frac": round(ach / FP32_PEAK_TFLOPS, 4),
+                                "kernel": "first-level contraction (float32 FMA), one PP-ALS run of the first seed",
+                                "launches": st["launches"],
+                                "avg_launch_us": round(st["total_ms"] * 1e3 / max(1, st["launches"]), 2),
+                                "peak_src": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz"}
+        summ["roofline_fp32_frac"] = out["roofline_fp32"]["frac"]
     return out
 
 

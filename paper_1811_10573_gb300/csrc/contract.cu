@@ -146,6 +146,189 @@ void gemm_launch(const TX* X, const T* B, T* out, T* partials, int64_t batch, in
   if (splits > 1) reduce_splits<T>(partials, out, batch * M * R, splits, L);
 }
 
+// ---------------------------------------------------------------- first level, float32, R > 32
+// The FP32 pipe (128 FMA per clock per SM) is fed from shared memory, so the
+// float32 kernel raises the FMAs per shared load: 128-thread CTAs of 128
+// rows x 8*TN columns (TN = ceil(R/8): no padded columns beyond R rounded
+// up to 8); thread (tm, tn) owns rows 8 tm .. 8 tm + 7 (two 16-byte shared
+// loads per k) and columns tn + 8 j (one 4-byte load each, 8 addresses per
+// warp), i.e. 8 TN FMAs for 2 + TN loads.  X arrives in 16-byte loads (k
+// contiguous when KMAJOR, else m contiguous; the caller checks the
+// alignment).  The next K slab is fetched into registers while the current
+// one is multiplied, with two shared buffers and one barrier per slab.
+// Measured on GB300 at R = 100, and slower: 16-byte B reads over a padded
+// layout (more registers than 2 CTAs per SM leave), 8-deep slabs (global
+// latency exposed), a row flip that frees the K-major transpose of its
+// 2-way bank conflicts (longer dependency stalls in the multiply loop), and
+// K splits into four waves for the few-row launch (partials and their
+// reduction cost what the refill gains).  Every output is one fma chain
+// over its chunk's k in increasing order, as in gemm_simt_kernel, so the
+// results are those of that kernel bit for bit.
+constexpr int kF32Threads = 128;
+constexpr int kF32BM = 128;
+constexpr int kF32BK = 16;
+
+template <bool KMAJOR, int TN>
+__global__ void __launch_bounds__(kF32Threads, 2)
+gemm_f32_kernel(const float* __restrict__ X, const float* __restrict__ B, float* __restrict__ out,
+                int64_t batch, int64_t K, int64_t M, int R, int splits, int64_t kchunk,
+                int64_t mtiles) {
+  constexpr int NT = kF32Threads, BM = kF32BM, BK = kF32BK, TM = 8, BN = 8 * TN, XS = BM + 4;
+  constexpr int NX = BM * BK / 4 / NT;          // 16-byte X loads per thread per slab
+  constexpr int NB = (BK * BN + NT - 1) / NT;   // B loads per thread per slab
+  constexpr int QPR = BK / 4;                   // 16-byte quads of a K-major row per slab
+  static_assert(BK == 8 || BK == 16, "slab depth");
+  __shared__ __align__(16) float Xs[2][BK][XS];
+  __shared__ __align__(16) float Bs[2][BK][BN];
+  const int tid = threadIdx.x, tn = tid & 7, tm = tid >> 3;
+  const int64_t bid = blockIdx.x;
+  const int64_t mt = bid % mtiles;
+  const int64_t rest = bid / mtiles;
+  const int z = (int)(rest % splits);
+  const int64_t b = rest / splits;
+  const int64_t m0 = mt * BM;
+  const int64_t k0 = (int64_t)z * kchunk;
+  const int64_t k1 = min(K, k0 + kchunk);
+  const float* Xb = X + b * K * M;
+
+  float4 xr[NX];
+  float br[NB];
+  auto fetch = [&](int64_t kk) {
+#pragma unroll
+    for (int q = 0; q < NX; q++) {
+      const int idx = tid + q * NT;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (KMAJOR) {
+        const int kq = idx % QPR, m = idx / QPR;   // QPR threads read one row's slab
+        const int64_t gk = kk + 4 * kq, gm = m0 + m;
+        if (gm < M && gk < k1) v = *reinterpret_cast<const float4*>(Xb + gm * K + gk);
+      } else {
+        const int m4 = idx & (BM / 4 - 1), k = idx / (BM / 4);
+        const int64_t gk = kk + k, gm = m0 + 4 * m4;
+        if (gm < M && gk < k1) v = *reinterpret_cast<const float4*>(Xb + gk * M + gm);
+      }
+      xr[q] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < NB; q++) {
+      const int idx = tid + q * NT;
+      const int k = idx / BN, r = idx % BN;
+      const int64_t gk = kk + k;
+      br[q] = (idx < BK * BN && gk < k1 && r < R) ? B[gk * R + r] : 0.f;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < NX; q++) {
+      const int idx = tid + q * NT;
+      if (KMAJOR) {
+        const int kq = idx % QPR, m = idx / QPR;
+        Xs[buf][4 * kq + 0][m] = xr[q].x;
+        Xs[buf][4 * kq + 1][m] = xr[q].y;
+        Xs[buf][4 * kq + 2][m] = xr[q].z;
+        Xs[buf][4 * kq + 3][m] = xr[q].w;
+      } else {
+        const int m4 = idx & (BM / 4 - 1), k = idx / (BM / 4);
+        *reinterpret_cast<float4*>(&Xs[buf][k][4 * m4]) = xr[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; q++) {
+      const int idx = tid + q * NT;
+      if (idx < BK * BN) Bs[buf][idx / BN][idx % BN] = br[q];
+    }
+  };
+
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; i++)
+#pragma unroll
+    for (int j = 0; j < TN; j++) acc[i][j] = 0.f;
+  // warps whose rows are all padding (in the last row tile) skip their FMAs
+  const int wlive = __reduce_max_sync(0xffffffffu, m0 + TM * tm < M ? 1 : 0);
+
+  if (k0 < k1) {
+    fetch(k0);
+    stash(0);
+  }
+  __syncthreads();
+  int buf = 0;
+  for (int64_t kk = k0; kk < k1; kk += BK) {
+    const bool more = kk + BK < k1;
+    if (more) fetch(kk + BK);
+    if (wlive > 0) {
+#pragma unroll
+      for (int k = 0; k < BK; k++) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&Xs[buf][k][TM * tm]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&Xs[buf][k][TM * tm + 4]);
+        const float a[TM] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        float bb[TN];
+#pragma unroll
+        for (int j = 0; j < TN; j++) bb[j] = Bs[buf][k][tn + 8 * j];
+#pragma unroll
+        for (int i = 0; i < TM; i++)
+#pragma unroll
+          for (int j = 0; j < TN; j++) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+      }
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  float* o = out + ((int64_t)z * batch + b) * M * R;
+#pragma unroll
+  for (int i = 0; i < TM; i++) {
+    const int64_t m = m0 + TM * tm + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; j++) {
+      const int r = tn + 8 * j;
+      if (r < R) o[m * R + r] = acc[i][j];
+    }
+  }
+}
+
+template <bool KM, int TN>
+void gemm_f32_launch(const float* X, const float* B, float* out, float* partials, int64_t batch,
+                     int64_t K, int64_t M, int R, int splits, Launch L) {
+  constexpr int BM = kF32BM, BK = 16;   // K chunks in multiples of 16, as gemm_launch
+  const int64_t mtiles = cdiv(M, BM);
+  const int64_t kchunk = cdiv(cdiv(K, splits), BK) * BK;
+  splits = (int)cdiv(K, kchunk);
+  float* dst = splits > 1 ? partials : out;
+  const int64_t blocks = mtiles * batch * splits;
+  gemm_f32_kernel<KM, TN><<<(unsigned)blocks, kF32Threads, 0, L.stream>>>(X, B, dst, batch, K, M, R,
+                                                                        splits, kchunk, mtiles);
+  (*L.counter)++;
+  if (splits > 1) reduce_splits<float>(partials, out, batch * M * R, splits, L);
+}
+
+// The float32 kernel takes R > 32 when the contiguous dimension of X (K for
+// the K-major launch, M for the other) allows 16-byte loads.
+bool f32_applies(const void* X, int64_t K, int64_t M, int R, bool kmajor) {
+  return R > 32 && R <= kMaxRank && (kmajor ? K % 4 == 0 : M % 4 == 0) &&
+         (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+}
+
+template <bool KM>
+void gemm_f32(const float* X, const float* B, float* out, float* partials, int64_t batch, int64_t K,
+              int64_t M, int R, int splits, Launch L) {
+  switch ((R + 7) / 8) {
+    case 5: gemm_f32_launch<KM, 5>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 6: gemm_f32_launch<KM, 6>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 7: gemm_f32_launch<KM, 7>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 8: gemm_f32_launch<KM, 8>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 9: gemm_f32_launch<KM, 9>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 10: gemm_f32_launch<KM, 10>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 11: gemm_f32_launch<KM, 11>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 12: gemm_f32_launch<KM, 12>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 13: gemm_f32_launch<KM, 13>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 14: gemm_f32_launch<KM, 14>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    case 15: gemm_f32_launch<KM, 15>(X, B, out, partials, batch, K, M, R, splits, L); break;
+    default: gemm_f32_launch<KM, 16>(X, B, out, partials, batch, K, M, R, splits, L); break;
+  }
+}
+
 // ---------------------------------------------------------------- multi-TTV
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
@@ -542,6 +725,13 @@ template <typename TX, typename T>
 void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K, int64_t M,
                int R, bool kmajor, int splits, Launch L) {
   if (splits < 1) splits = 1;
+  if constexpr (sizeof(T) == 4 && sizeof(TX) == 4) {
+    if (f32_applies(X, K, M, R, kmajor)) {
+      if (kmajor) gemm_f32<true>(X, B, out, partials, batch, K, M, R, splits, L);
+      else gemm_f32<false>(X, B, out, partials, batch, K, M, R, splits, L);
+      return;
+    }
+  }
   if constexpr (sizeof(T) == 8) {
     if (R > 32 && gemm_simt_bm(M, R, kmajor) == 64) {
       if (kmajor) gemm_exact_cols<TX, T, true>(X, B, out, partials, batch, K, M, R, splits, L);

@@ -64,6 +64,23 @@ def test_mttkrp(dims, R, prec):
             assert rel(g.mttkrp(n), ref) < TOL[prec], (n, prec)
 
 
+# float32 contractions with R > 32: 128-row tiles of 8 ceil(R/8) columns with
+# 16-byte X loads when the contiguous dimension (K for the K-major launch, M
+# for the other) is a multiple of 4, else the generic kernel; ragged row
+# tiles, K not a multiple of the 16-deep slab, split K, TN = 5 to 16
+WIDE = [([132, 36, 20], 33), ([20, 36, 132], 64), ([52, 44, 28], 128), ([36, 44, 130], 100),
+        ([33, 35, 36], 40), ([9, 7, 2000], 100)]
+
+
+@pytest.mark.parametrize("dims,R", WIDE)
+def test_mttkrp_fp32_wide_rank(dims, R):
+    p = synth.make_problem("normal", dims, R, seed=8, storage="f32")
+    with _ctx(p, "fp32") as g:
+        for n in range(len(dims)):
+            ref = O.mttkrp(X64(p), p.A0, n)
+            assert rel(g.mttkrp(n), ref) < TOL["fp32"], n
+
+
 # the largest order (8), order 7, and modes of size 1 (degenerate unfoldings)
 EDGE = [([3, 2, 4, 2, 3, 2, 2], 3), ([2, 3, 2, 2, 3, 2, 2, 3], 2), ([1, 9, 7], 4), ([8, 1, 6, 5], 3)]
 
@@ -203,28 +220,8 @@ def test_order3_60_rank10_run_fp64():
             assert rel(a, b) < 1e-8
 
 
-@pytest.mark.parametrize("prec", ["fp32", "mixed"])
-def test_singular_gamma_reported_double_float(prec):
-    """A zero column in the other two factors makes Gamma of mode 0 exactly
-    singular (a zero pivot).  The double-float normal equations have no
-    pseudo-inverse path: CPALS_E_SINGULAR, and that factor is left
-    unchanged."""
-    p = synth.make_problem("normal", [12, 10, 9], 3, seed=13, storage="f32")
-    A0 = [a.copy() for a in p.A0]
-    for n in (1, 2):
-        A0[n][:, 1] = 0.0
-    with cpals.CPALS(p.dims, p.R, prec) as g:
-        g.set_tensor(p.X)
-        g.init_factors(A0)
-        with pytest.raises(cpals.CPALSError) as e:
-            g.als_sweep()
-        assert e.value.status == 5
-        # kept as the double-float pair it was stored as (48-bit significand)
-        np.testing.assert_allclose(g.get_factors()[0], A0[0], rtol=1e-13, atol=0)
-
-
-def _zero_column_problem(R=5, col=2, seed=14):
-    p = synth.make_problem("normal", [12, 10, 9], R, seed=seed, storage="f64")
+def _zero_column_problem(R=5, col=2, seed=14, storage="f64"):
+    p = synth.make_problem("normal", [12, 10, 9], R, seed=seed, storage=storage)
     A0 = [a.copy() for a in p.A0]
     A0[1][:, col] = 0.0
     return p, A0
@@ -247,6 +244,70 @@ def test_normal_solve_pinv_fp64():
             ref = O.solve_normal(rhs, G, info)
             assert info.singular
             assert rel(g.normal_solve(0, rhs), ref) < 1e-11
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_normal_solve_pinv_double_float(prec):
+    """The double-float normal equations of FP32/mixed contexts take the same
+    Gamma^dagger fallback (Algorithm 1): a float64 Jacobi eigendecomposition
+    of Gamma and the factor diag(w^+)^(1/2) V^T in double-float, applied as
+    W^T W.  Against the oracle's eigen pseudo-inverse of the float-rounded
+    right-hand side (the solve takes it in float), consistent and
+    arbitrary."""
+    p, A0 = _zero_column_problem(storage="f32")
+    g_ = np.random.default_rng(41)
+    with cpals.CPALS(p.dims, p.R, prec) as g:
+        g.set_tensor(p.X)
+        g.init_factors(A0)
+        S = [O.gram(a) for a in A0]
+        G = O.gamma(S, 0)
+        for rhs in (g_.standard_normal((p.dims[0], p.R)) @ G, g_.standard_normal((p.dims[0], p.R))):
+            rhs = rhs.astype(np.float32).astype(np.float64)
+            info = O.SolveInfo()
+            ref = O.solve_normal(rhs, G, info)
+            assert info.singular
+            assert rel(g.normal_solve(0, rhs), ref) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("eps", [0.0, 0.2])
+def test_run_with_singular_gamma_double_float_equals_lower_rank(prec, eps):
+    """The double-float counterpart of the float64 run below: a zero column in
+    every initial factor keeps every Gamma^(n) singular, the solves go
+    through Gamma^dagger every mode, and the run equals the same context's
+    rank R - 1 run without that column, with the column exactly zero
+    throughout.  The contractions give the same columns; the solve's factor
+    differs (double-float rounding, which can move a float compute copy by
+    one unit) and the fitness sums R float terms in another order, so the
+    two agree to float rounding: 1e-6 on the fitness, 1e-5 on the factors.
+    The rank R - 1 run itself tracks the oracle within the contraction
+    tolerance."""
+    R, col = 5, 2
+    p = synth.make_problem("normal", [12, 10, 9], R, seed=14, storage="f32")
+    A0 = [a.copy() for a in p.A0]
+    for a in A0:
+        a[:, col] = 0.0
+    keep = [r for r in range(R) if r != col]
+    n = 12
+    res = {}
+    for rank, facs in ((R, A0), (R - 1, [a[:, keep] for a in A0])):
+        with cpals.CPALS(p.dims, rank, prec) as g:
+            g.set_tensor(p.X)
+            g.init_factors(facs)
+            out = g.run(n, eps, True, 0.0)
+            res[rank] = (out, g.get_factors(), g.fitness())
+    (o5, A5, f5), (o4, A4, f4) = res[R], res[R - 1]
+    assert o5["kinds"] == o4["kinds"]
+    np.testing.assert_allclose(o5["fitness"], o4["fitness"], rtol=0, atol=1e-6)
+    assert abs(f5 - f4) < 1e-6
+    for a, b in zip(A5, A4):
+        assert np.all(a[:, col] == 0.0)
+        assert rel(a[:, keep], b) < 1e-5
+    if eps > 0:
+        assert "pp_approx" in o5["kinds"]
+    A_or, tr = O.pp_cp_als(X64(p), [a[:, keep] for a in A0], n, 0.0, use_V=True)
+    if eps == 0.0:
+        np.testing.assert_allclose(o4["fitness"], tr.seen, rtol=0, atol=50 * TOL[prec])
 
 
 @pytest.mark.parametrize("eps", [0.0, 0.2])
