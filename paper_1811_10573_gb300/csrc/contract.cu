@@ -330,6 +330,39 @@ void gemm_f32(const float* X, const float* B, float* out, float* partials, int64
 }
 
 // ---------------------------------------------------------------- multi-TTV
+// Many outputs per o and a short contracted mode (the operator tree's upper
+// levels on small-mode tensors, e.g. 24^5 x R parents): each thread forms
+// VEC consecutive outputs over all x in order, so a warp reads 32 VEC
+// consecutive values per x and no cross-warp reduction is needed.
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kThreads)
+ttv_cols_kernel(const T* __restrict__ in, const T* __restrict__ A, T* __restrict__ out, int sw,
+                int64_t QR, int R, int64_t chunks) {
+  const int64_t o = blockIdx.x / chunks;
+  const int64_t f = ((blockIdx.x % chunks) * kThreads + threadIdx.x) * VEC;
+  if (f >= QR) return;
+  const T* base = in + o * sw * QR + f;
+  const int r = (int)(f % R);
+  if constexpr (VEC == 4) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+    for (int x = 0; x < sw; x++) {
+      const float4 v = *reinterpret_cast<const float4*>(base + (int64_t)x * QR);
+      const float4 a = __ldg(reinterpret_cast<const float4*>(A + (int64_t)x * R + r));
+      acc.x = fmaf(v.x, a.x, acc.x);
+      acc.y = fmaf(v.y, a.y, acc.y);
+      acc.z = fmaf(v.z, a.z, acc.z);
+      acc.w = fmaf(v.w, a.w, acc.w);
+    }
+    *reinterpret_cast<float4*>(out + o * QR + f) = acc;
+  } else {
+    T acc = T(0);
+#pragma unroll 8
+    for (int x = 0; x < sw; x++) acc = fma(base[(int64_t)x * QR], __ldg(A + (int64_t)x * R + r), acc);
+    out[o * QR + f] = acc;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 ttv_kernel(const T* __restrict__ in, const T* __restrict__ A, T* __restrict__ out, int sw,
@@ -799,6 +832,20 @@ int gemm_simt_wave_splits(int64_t batch, int64_t K, int64_t M, int R, bool kmajo
 template <typename T>
 void ttv(const T* in, const T* A, T* out, int64_t outer, int sw, int64_t inner, int R, Launch L) {
   const int64_t QR = inner * R;
+  if (sw <= 64 && outer * QR >= (int64_t)152 * 64 * kThreads) {
+    // enough outputs for every thread to own some: no split of x
+    if (sizeof(T) == 4 && R % 4 == 0) {
+      const int64_t chunks = cdiv(QR, 4 * kThreads);
+      ttv_cols_kernel<float, 4><<<(unsigned)(outer * chunks), kThreads, 0, L.stream>>>(
+          (const float*)in, (const float*)A, (float*)out, sw, QR, R, chunks);
+    } else {
+      const int64_t chunks = cdiv(QR, kThreads);
+      ttv_cols_kernel<T, 1><<<(unsigned)(outer * chunks), kThreads, 0, L.stream>>>(in, A, out, sw, QR, R,
+                                                                                  chunks);
+    }
+    (*L.counter)++;
+    return;
+  }
   if (sizeof(T) == 4 && R % 4 == 0) {
     const int64_t chunks = cdiv(QR, 128);
     ttv4_kernel<<<(unsigned)(outer * chunks), kThreads, 0, L.stream>>>(

@@ -21,7 +21,7 @@ namespace {
 
 constexpr int H = kCtrlHidden;
 constexpr int C = kCtrlClasses;
-static_assert(H == 32 && C == 3 && kCtrlFeatures == 20, "mlp_probs and ctrl_features are written for 20-32-3");
+static_assert(H == 32 && C == 3 && kCtrlFeatures == 20, "mlp_probs and ctrl_feature are written for 20-32-3");
 
 struct Params {
   const float* W1;

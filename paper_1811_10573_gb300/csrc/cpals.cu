@@ -255,11 +255,13 @@ void ev_harvest(cpals_ctx* c) {
 // their factors' Khatri-Rao product (Sec. 2.5; Sec. 3.2.3 level 2).
 // kmajor: the contracted modes are the trailing ones (out is M x R, M = the rest);
 // else out[b][m][r] with b = modes before, m = modes after the contracted block.
+// tc_ok = false keeps a MIXED_BF16 contraction on the SIMT float32 kernels
+// (float32 X).
 template <typename T>
 cpals_status contract_first(cpals_ctx* c, int k0, int nk, void* const* facs, T* out,
-                            int64_t batch, int64_t K, int64_t M, bool kmajor) {
+                            int64_t batch, int64_t K, int64_t M, bool kmajor, bool tc_ok = true) {
   const int R = c->R;
-  const bool tc = c->prec == CPALS_MIXED_BF16 && umma_supported(K, M, kmajor, R);
+  const bool tc = c->prec == CPALS_MIXED_BF16 && tc_ok && umma_supported(K, M, kmajor, R);
   const size_t xsz = c->prec == CPALS_FP64 ? 8 : (tc ? 2 : 4);
   // algorithmic bytes: read X once, read B once, write the output once
   const double bytes = (double)batch * K * M * xsz + (double)batch * M * R * sizeof(T) +
@@ -526,7 +528,12 @@ cpals_status pp_build_launch(cpals_ctx* c) {
     for (int k = w + 1; k < N; k++) M *= c->dims[k];
     const bool kmajor = (w == N - 1);
     if (kmajor) { M = batch; batch = 1; }
-    CKS(contract_first<T>(c, w, 1, c->Ac, dst, batch, c->dims[w], M, kmajor));
+    // a short contracted mode (K below 64) with a large output leaves the
+    // tcgen05 kernel nothing but its per-tile cost (the TMEM round trip and
+    // epilogue of every 128-row tile): measured 2.76 ms per launch against
+    // about 0.6 ms on the SIMT float32 kernel for the 24^6 tree's K = 24
+    // (the operators then carry float32 X in MIXED_BF16)
+    CKS(contract_first<T>(c, w, 1, c->Ac, dst, batch, c->dims[w], M, kmajor, c->dims[w] >= 64));
   }
   // levels 3 .. N-1: one multi-TTV per child
   for (int l = 3; l <= N - 1; l++) {
@@ -959,19 +966,17 @@ __device__ bool loop_all_small(const LoopState* s, const double* scal) {
 // the network's most probable action when its probability reaches the
 // confidence and it is not a PP sweep without valid operators, else the
 // rule's branch; returns the branch (0 ALS, 1 rebuild + PP, 2 PP) on every
-// lane.  One warp: lane 0 forms the features, the lanes the hidden units.
-__device__ int loop_ctrl_choose(LoopState* s, const double* scal, int rule_branch) {
+// lane.  One warp: lane i forms feature i from the history and the modes'
+// lr (ctrl_mode_lr, shared), lane j hidden unit j.
+__device__ int loop_ctrl_choose(LoopState* s, const double* lr, int rule_branch) {
   __shared__ float x[20], hsm[32], pr[3];
   __shared__ int out;
   const int lane = threadIdx.x & 31;
-  if (lane == 0) {
-    // the history and the 8 + 2N scalars the features use, as local copies
-    // (features computed through the LoopState and scalar pointers directly
-    // came out as those of the run's first decision in this kernel)
+  if (lane < 20) {
+    // the history as a local copy (features formed through the loop state's
+    // pointer came out as those of the run's first decision in this kernel)
     const CtrlState h = s->ch;
-    double sc[8 + 2 * kMaxModes];
-    for (int i = 0; i < 8 + 2 * s->N; i++) sc[i] = scal[i];
-    ctrl_features(h, sc, s->N, s->eps, x);
+    x[lane] = ctrl_feature(h, lr, s->N, s->eps, lane);
   }
   __syncwarp();
   mlp_probs_warp<20>(s->params, x, hsm, pr);
@@ -992,12 +997,22 @@ __device__ int loop_ctrl_choose(LoopState* s, const double* scal, int rule_branc
   return out;
 }
 
+// lr[n] = ctrl_mode_lr of the current scalars, mode n on lane n (the whole
+// warp calls it; shared lr visible on return)
+__device__ void loop_mode_lr(const LoopState* s, const double* scal, double* lr) {
+  const int lane = threadIdx.x & 31, N = s->N;
+  if (lane < N) lr[lane] = ctrl_mode_lr(scal, lane);
+  __syncwarp();
+}
+
 // One warp (the node's 32 threads): lane 0 runs the rule, the warp the
 // controller when there is one.
 __global__ void loop_init_kernel(LoopState* s, const double* scal, cudaGraphConditionalHandle hw,
                                  cudaGraphConditionalHandle hs) {
   if (threadIdx.x >= 32 || blockIdx.x != 0) return;
   __shared__ int ask, rule;
+  __shared__ double lr[kMaxModes];
+  if (s->ctrl) loop_mode_lr(s, scal, lr);
   if (threadIdx.x == 0) {
     s->t = 0;
     s->hit = 0;
@@ -1013,7 +1028,7 @@ __global__ void loop_init_kernel(LoopState* s, const double* scal, cudaGraphCond
   }
   __syncwarp();
   if (ask) {
-    const int nx = loop_ctrl_choose(s, scal, rule);
+    const int nx = loop_ctrl_choose(s, lr, rule);
     if (threadIdx.x == 0) s->next = nx;
   }
   if (threadIdx.x == 0) {
@@ -1026,8 +1041,8 @@ __global__ void loop_init_kernel(LoopState* s, const double* scal, cudaGraphCond
 // Lane 0's part of the decision after a sweep: records the sweep, ends the
 // loop or sets the rule's next branch.  Returns 1 when the learned
 // controller is to take the decision (the caller sets the switch then).
-__device__ int loop_decide_rule(LoopState* s, const double* scal, const int* status, double* ftr,
-                                int* ktr, double* ttr, cudaGraphConditionalHandle hw,
+__device__ int loop_decide_rule(LoopState* s, const double* scal, const double* lr, const int* status,
+                                double* ftr, int* ktr, double* ttr, cudaGraphConditionalHandle hw,
                                 cudaGraphConditionalHandle hs) {
   int ran = s->next;
   const double f = scal[0];
@@ -1040,7 +1055,7 @@ __device__ int loop_decide_rule(LoopState* s, const double* scal, const int* sta
     s->f_prev = s->f_last;
     s->f_last = fv;
     s->in_run = kind == 0 ? 0 : (kind == 1 ? 1 : s->in_run + 1);
-    if (s->ctrl) ctrl_push(s->ch, scal, s->N, kind == 0 ? ACT_ALS : (kind == 1 ? ACT_REBUILD : ACT_PP), fv);
+    if (s->ctrl) ctrl_push(s->ch, lr, s->N, kind == 0 ? ACT_ALS : (kind == 1 ? ACT_REBUILD : ACT_PP), fv);
   };
   bool stop = false;
   if (ran == 3) {
@@ -1101,13 +1116,16 @@ __global__ void loop_decide_kernel(LoopState* s, const double* scal, const int* 
                                    cudaGraphConditionalHandle hs) {
   if (threadIdx.x >= 32 || blockIdx.x != 0) return;
   __shared__ int ask, rule;
+  __shared__ double lr[kMaxModes];
+  // the modes' lr of the sweep just done: its record and the next features
+  if (s->ctrl) loop_mode_lr(s, scal, lr);
   if (threadIdx.x == 0) {
-    ask = loop_decide_rule(s, scal, status, ftr, ktr, ttr, hw, hs);
+    ask = loop_decide_rule(s, scal, lr, status, ftr, ktr, ttr, hw, hs);
     rule = s->next;
   }
   __syncwarp();
   if (!ask) return;
-  const int nx = loop_ctrl_choose(s, scal, rule);
+  const int nx = loop_ctrl_choose(s, lr, rule);
   if (threadIdx.x == 0) {
     s->next = nx;
     cudaGraphSetConditional(hs, (unsigned)nx);

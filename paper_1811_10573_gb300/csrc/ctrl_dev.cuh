@@ -1,7 +1,7 @@
 // Learned sweep-type controller on the device: its history of the run, its
 // feature vector and the network's forward pass as device functions, so that
-// the decision can be taken inside the device loop of Algorithm 3 (one
-// thread, no host round trip).  The host loop of cpals_run_controlled keeps
+// the decision can be taken inside the device loop of Algorithm 3 (one warp,
+// no host round trip).  The host loop of cpals_run_controlled keeps
 // its own copy of the history and features in cpals.cu; the formulas are the
 // same.  The forward pass is also the body of mlp_forward_kernel.
 #pragma once
@@ -32,14 +32,18 @@ __host__ __device__ inline void ctrl_state_start(CtrlState& h, double fitness) {
   h.pad = 0;
 }
 
-// after a sweep of kind `action` that left the scalars scal ([8 + 2n]
-// ||dA^(n)||^2, [9 + 2n] ||A^(n)||^2) and the fitness the algorithm saw
-__device__ inline void ctrl_push(CtrlState& h, const double* scal, int N, int action, double fitness) {
+// log10 ||dA^(n)|| / ||A^(n)|| of mode n (floored at 1e-12) from the scalars
+// scal ([8 + 2n] ||dA^(n)||^2, [9 + 2n] ||A^(n)||^2)
+__device__ inline double ctrl_mode_lr(const double* scal, int n) {
+  const double d = sqrt(scal[8 + 2 * n]), a = sqrt(scal[9 + 2 * n]);
+  return log10(fmax(d / fmax(a, 1e-300), 1e-12));
+}
+
+// after a sweep of kind `action` whose modes gave lr[n] = ctrl_mode_lr and
+// the fitness the algorithm saw
+__device__ inline void ctrl_push(CtrlState& h, const double* lr, int N, int action, double fitness) {
   double m = -12.0;
-  for (int n = 0; n < N; n++) {
-    const double d = sqrt(scal[8 + 2 * n]), a = sqrt(scal[9 + 2 * n]);
-    m = fmax(m, log10(fmax(d / fmax(a, 1e-300), 1e-12)));
-  }
+  for (int n = 0; n < N; n++) m = fmax(m, lr[n]);
   h.maxlr[1] = h.maxlr[0];
   h.maxlr[0] = m;
   for (int k = 3; k > 0; k--) h.res[k] = h.res[k - 1];
@@ -56,30 +60,27 @@ __device__ inline void ctrl_push(CtrlState& h, const double* scal, int N, int ac
   }
 }
 
-// the network's input (F = 20 values, all O(1)): per-mode log10
-// ||dA||/||A|| (padded to 8 modes), the largest one of the two previous
-// sweeps, log10 of the last three residual decreases, sweeps since the
-// operators were built, whether a PP sweep is possible, the last action
-// (one-hot), log10 eps and log10 of the current residual
-__device__ inline void ctrl_features(const CtrlState& h, const double* scal, int N, double eps, float* x) {
-  for (int i = 0; i < 20; i++) x[i] = 0.f;
-  for (int n = 0; n < N && n < 8; n++) {
-    const double d = sqrt(scal[8 + 2 * n]), a = sqrt(scal[9 + 2 * n]);
-    const double lr = log10(fmax(d / fmax(a, 1e-300), 1e-12));
-    x[n] = (float)(fmin(fmax(lr, -12.0), 2.0) / 4.0);
-  }
-  x[8] = (float)(h.maxlr[0] / 4.0);
-  x[9] = (float)(h.maxlr[1] / 4.0);
-  for (int k = 0; k < 3; k++) {
+// feature i of the network's input (F = 20 values, all O(1)): per-mode
+// log10 ||dA||/||A|| (padded to 8 modes), the largest one of the two
+// previous sweeps, log10 of the last three residual decreases, sweeps since
+// the operators were built, whether a PP sweep is possible, the last action
+// (one-hot), log10 eps and log10 of the current residual.  One value per
+// call, so that a warp forms all twenty at once (the float64 logarithms and
+// square roots run on GB300's narrow FP64 pipe).
+__device__ inline float ctrl_feature(const CtrlState& h, const double* lr, int N, double eps, int i) {
+  if (i < 8) return i < N ? (float)(fmin(fmax(lr[i], -12.0), 2.0) / 4.0) : 0.f;
+  if (i < 10) return (float)(h.maxlr[i - 8] / 4.0);
+  if (i < 13) {
+    const int k = i - 10;
     const bool have = h.res[k] >= 0 && h.res[k + 1] >= 0;
     const double dec = have ? fmax(h.res[k + 1] - h.res[k], 1e-16) : 1e-16;
-    x[10 + k] = (float)(log10(dec) / 8.0);
+    return (float)(log10(dec) / 8.0);
   }
-  x[13] = (float)(h.pp_ready ? fmin((double)h.since_build, 20.0) / 10.0 : 0.0);
-  x[14] = h.pp_ready ? 1.f : 0.f;
-  if (h.last >= 0) x[15 + h.last] = 1.f;
-  x[18] = (float)(log10(fmax(eps, 1e-12)) / 2.0);
-  x[19] = (float)(log10(fmax(h.res[0] >= 0 ? h.res[0] : 1.0, 1e-16)) / 8.0);
+  if (i == 13) return (float)(h.pp_ready ? fmin((double)h.since_build, 20.0) / 10.0 : 0.0);
+  if (i == 14) return h.pp_ready ? 1.f : 0.f;
+  if (i < 18) return h.last == i - 15 ? 1.f : 0.f;
+  if (i == 18) return (float)(log10(fmax(eps, 1e-12)) / 2.0);
+  return (float)(log10(fmax(h.res[0] >= 0 ? h.res[0] : 1.0, 1e-16)) / 8.0);
 }
 
 // probs = softmax(W2 relu(W1 x + b1) + b2); parameters W1[H][F], b1[H],

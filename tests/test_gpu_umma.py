@@ -104,16 +104,19 @@ def test_mttkrp_order4(dims, R):
 @pytest.mark.parametrize("dims,R", SHAPES3[:4])
 def test_pp_operators_order3(dims, R):
     """Level 2 of the operator tree = three single-mode contractions of X
-    (K-major for the last mode, batched MN-major for the others)."""
+    (K-major for the last mode, batched MN-major for the others): on the
+    tensor cores (bf16 X, hi + lo B) when the contracted mode has at least 64
+    entries, else on the SIMT float32 kernels (float32 X and factor)."""
     p = synth.make_problem("normal", dims, R, seed=23, storage="f32")
-    Xb = bf16(p.X)
     with _ctx(p) as g:
         g.pp_build_operators()
         A32 = [a.astype(np.float32) for a in p.A0]
-        B = [bsplit(a) for a in A32]
-        refs = {(0, 1): np.einsum("ijk,kr->ijr", Xb, B[2]),
-                (0, 2): np.einsum("ijk,jr->ikr", Xb, B[1]),
-                (1, 2): np.einsum("ijk,ir->jkr", Xb, B[0])}
+        X = {w: (bf16(p.X) if dims[w] >= 64 else np.asarray(p.X, dtype=np.float32).astype(np.float64))
+             for w in range(3)}
+        B = {w: (bsplit(A32[w]) if dims[w] >= 64 else A32[w].astype(np.float64)) for w in range(3)}
+        refs = {(0, 1): np.einsum("ijk,kr->ijr", X[2], B[2]),
+                (0, 2): np.einsum("ijk,jr->ikr", X[1], B[1]),
+                (1, 2): np.einsum("ijk,ir->jkr", X[0], B[0])}
         for (i, n), ref in refs.items():
             assert rel(g.get_operator(i, n), ref) < TOL, (i, n)
 
