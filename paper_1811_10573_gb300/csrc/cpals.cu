@@ -531,8 +531,8 @@ cpals_status pp_build_launch(cpals_ctx* c) {
     // a short contracted mode (K below 64) with a large output leaves the
     // tcgen05 kernel nothing but its per-tile cost (the TMEM round trip and
     // epilogue of every 128-row tile): measured 2.76 ms per launch against
-    // about 0.6 ms on the SIMT float32 kernel for the 24^6 tree's K = 24
-    // (the operators then carry float32 X in MIXED_BF16)
+    // 1.05 ms on the SIMT float32 kernel for the 24^6 tree's K = 24 (the
+    // operators then carry float32 X in MIXED_BF16)
     CKS(contract_first<T>(c, w, 1, c->Ac, dst, batch, c->dims[w], M, kmajor, c->dims[w] >= 64));
   }
   // levels 3 .. N-1: one multi-TTV per child
