@@ -161,6 +161,12 @@ cpals_status cpals_get_factors(cpals_ctx* ctx, double* const* out);
 /* out_N[n] = ||dA^(n)||_F / ||A^(n)||_F (the quantities Algorithm 3 tests). */
 cpals_status cpals_get_dA_ratios(cpals_ctx* ctx, double* out_N);
 
+/* *mask: bit n set when the last factorisation of mode n met a Gamma^(n) that
+ * is not positive definite and the update went through Gamma^dagger
+ * (Algorithm 1's pseudo-inverse; see CPALS_E_SINGULAR).  Waits for the
+ * context's stream. */
+cpals_status cpals_pinv_modes(cpals_ctx* ctx, int* mask);
+
 /* Run Algorithm 3 for at most max_sweeps sweeps with tolerance eps (eps <= 0
  * gives plain ALS).  Each ALS sweep, PP initialisation sweep (build + one PP
  * pass) and PP approximated sweep counts as one sweep.  If target > 0 the run

@@ -40,6 +40,7 @@ _SIGS = {
     "cpals_fitness": (C.c_int, [_ctx_p, _dp]),
     "cpals_get_factors": (C.c_int, [_ctx_p, C.POINTER(_dp)]),
     "cpals_get_dA_ratios": (C.c_int, [_ctx_p, _dp]),
+    "cpals_pinv_modes": (C.c_int, [_ctx_p, _ip]),
     "cpals_run_batch": (C.c_int, [C.POINTER(_ctx_p), C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
                                   _dp, _dp, _ip, _ip]),
     "cpals_run": (C.c_int, [_ctx_p, C.c_int, C.c_double, C.c_int, C.c_double, _dp, _ip, _dp,
@@ -187,6 +188,10 @@ def cpals_get_factors(ctx, outs):
 
 def cpals_get_dA_ratios(ctx, out):
     return lib().cpals_get_dA_ratios(ctx, _dptr(out))
+
+
+def cpals_pinv_modes(ctx, mask):
+    return lib().cpals_pinv_modes(ctx, C.byref(mask))
 
 
 def cpals_run(ctx, max_sweeps, eps, use_V, target, ftrace, ktrace, ttrace, n_done, reached):
@@ -453,6 +458,12 @@ class CPALS:
         out = np.empty(self.N)
         self._ck(cpals_get_dA_ratios(self.ctx, out))
         return out
+
+    def pinv_modes(self):
+        """Bit n: the last update of mode n went through Gamma^dagger."""
+        m = C.c_int()
+        self._ck(cpals_pinv_modes(self.ctx, m))
+        return m.value
 
     def run(self, max_sweeps, eps, use_V=True, target=0.0):
         ft = np.zeros(max_sweeps)

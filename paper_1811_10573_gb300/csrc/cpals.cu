@@ -1667,6 +1667,14 @@ cpals_status cpals_get_dA_ratios(cpals_ctx* c, double* out) {
   return CPALS_OK;
 }
 
+cpals_status cpals_pinv_modes(cpals_ctx* c, int* mask) {
+  if (!c || !mask) return CPALS_E_INVALID;
+  Join j(c);
+  CKS(sync_read(c));
+  *mask = (c->status_h[0] >> 16) & 0xffff;
+  return CPALS_OK;
+}
+
 cpals_status cpals_run(cpals_ctx* c, int max_sweeps, double eps, int use_V, double target,
                        double* fitness_trace, int* kind_trace, double* time_trace, int* n_done,
                        int* reached) {

@@ -210,6 +210,7 @@ def test_order3_60_rank10_run_fp64():
     with _ctx(p, "fp64") as g:
         out = g.run(p.sweeps, p.eps, use_V=True)
         assert out["kinds"] == tr.kinds
+        assert g.pinv_modes() == 0                 # every Gamma positive definite
         # the GPU reports the exact fitness after ALS sweeps and the estimate
         # from M~^(N) after PP sweeps, as the oracle's trace of what the
         # algorithm sees does
@@ -244,6 +245,7 @@ def test_normal_solve_pinv_fp64():
             ref = O.solve_normal(rhs, G, info)
             assert info.singular
             assert rel(g.normal_solve(0, rhs), ref) < 1e-11
+            assert g.pinv_modes() & 1
 
 
 @pytest.mark.parametrize("prec", ["fp32", "mixed"])
@@ -267,6 +269,7 @@ def test_normal_solve_pinv_double_float(prec):
             ref = O.solve_normal(rhs, G, info)
             assert info.singular
             assert rel(g.normal_solve(0, rhs), ref) < 1e-10
+            assert g.pinv_modes() & 1
 
 
 @pytest.mark.parametrize("prec", ["fp32", "mixed"])
@@ -295,6 +298,7 @@ def test_run_with_singular_gamma_double_float_equals_lower_rank(prec, eps):
             g.set_tensor(p.X)
             g.init_factors(facs)
             out = g.run(n, eps, True, 0.0)
+            assert g.pinv_modes() == (7 if rank == R else 0)
             res[rank] = (out, g.get_factors(), g.fitness())
     (o5, A5, f5), (o4, A4, f4) = res[R], res[R - 1]
     assert o5["kinds"] == o4["kinds"]
@@ -331,6 +335,7 @@ def test_run_with_singular_gamma_fp64_equals_lower_rank(eps):
         g.set_tensor(p.X)
         g.init_factors(A0)
         out = g.run(n, eps, True, 0.0)
+        assert g.pinv_modes() == 7
         A = g.get_factors()
         f = g.fitness()
     assert out["kinds"] == tr.kinds
