@@ -108,6 +108,20 @@ def test_als_sweeps_fp64(dims, R):
 @pytest.mark.parametrize("dims,R", [([40, 33, 27], 9), ([11, 13, 9, 10], 6), ([6, 7, 5, 6, 4], 4),
                                     ([5, 6, 4, 5, 3, 4], 3)])
 def test_pp_operators(dims, R, prec):
+    _check_operators(dims, R, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+def test_pp_operators_short_modes_large(prec):
+    """Order 5 with short modes: the operator tree's level-3 node (0, 3) has
+    7.1 M entries and contracts a mode of 12, which takes the
+    thread-per-output TTV (float64 scalar; float 16-byte with R % 4 = 0);
+    in mixed precision the single-mode contractions of X (K = 12 and 48)
+    run on the SIMT float32 kernels."""
+    _check_operators([48, 12, 12, 48, 48], 64, prec)
+
+
+def _check_operators(dims, R, prec):
     storage = "f64" if prec == "fp64" else "f32"
     p = synth.make_problem("normal", dims, R, seed=7, storage=storage)
     with _ctx(p, prec) as g:
