@@ -695,13 +695,30 @@ int gemm_simt_splits(int64_t batch, int64_t K, int64_t M, int R, bool kmajor, in
 }
 
 // float64 contractions with R > 32: 64-row tiles whose column tile is R
-// rounded up to a multiple of 8 (8 thread columns of TN = ceil(R/8) each), so
-// the FP64 pipe, the bound of these kernels, runs almost no padded FMAs
-// (R = 100: 104 columns instead of 128).  Each output's k order is the same
-// as with any other tile, so the results are unchanged bit for bit.
+// rounded up to a multiple of 8 (8 thread columns of TN = ceil(R/8) each), or
+// R itself when R = 4 (mod 8) above 64, so the FP64 pipe, the bound of these
+// kernels, runs few or no padded FMAs (R = 100: 100 columns instead of 128).
+// Each output's k order is the same as with any other tile.
+// R = 4 (mod 8) above 64 (R = 100 would pad 4 columns to 104): 64-row tiles
+// of exactly R columns, 4 thread columns of R/4 each and 64 thread rows of
+// one row.
+constexpr bool exact4(int R) { return R > 64 && R % 8 == 4; }
+
 template <typename TX, typename T, bool KM>
-void gemm_exact_cols(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K,
-                     int64_t M, int R, int splits, Launch L) {
+void gemm_exact_launch(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K,
+                       int64_t M, int R, int splits, Launch L) {
+  if (exact4(R)) {
+    switch (R) {
+      case 68: gemm_launch<TX, T, KM, 64, 68, 1, 17>(X, B, out, partials, batch, K, M, R, splits, L); return;
+      case 76: gemm_launch<TX, T, KM, 64, 76, 1, 19>(X, B, out, partials, batch, K, M, R, splits, L); return;
+      case 84: gemm_launch<TX, T, KM, 64, 84, 1, 21>(X, B, out, partials, batch, K, M, R, splits, L); return;
+      case 92: gemm_launch<TX, T, KM, 64, 92, 1, 23>(X, B, out, partials, batch, K, M, R, splits, L); return;
+      case 100: gemm_launch<TX, T, KM, 64, 100, 1, 25>(X, B, out, partials, batch, K, M, R, splits, L); return;
+      case 108: gemm_launch<TX, T, KM, 64, 108, 1, 27>(X, B, out, partials, batch, K, M, R, splits, L); return;
+      case 116: gemm_launch<TX, T, KM, 64, 116, 1, 29>(X, B, out, partials, batch, K, M, R, splits, L); return;
+      default: gemm_launch<TX, T, KM, 64, 124, 1, 31>(X, B, out, partials, batch, K, M, R, splits, L); return;
+    }
+  }
   switch ((R + 7) / 8) {
     case 5: gemm_launch<TX, T, KM, 64, 40, 2, 5>(X, B, out, partials, batch, K, M, R, splits, L); break;
     case 6: gemm_launch<TX, T, KM, 64, 48, 2, 6>(X, B, out, partials, batch, K, M, R, splits, L); break;
@@ -720,13 +737,13 @@ void gemm_exact_cols(const TX* X, const T* B, T* out, T* partials, int64_t batch
 
 // Resident CTAs per SM of the float64 configuration gemm_exact_cols launches
 // for R (queried once per configuration).
-template <typename TX, bool KM, int BN, int TN>
+template <typename TX, bool KM, int BN, int TN, int TM = 2>
 int exact_cols_occ() {
   static int occ = 0;
   if (occ == 0) {
     int o = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &o, gemm_simt_kernel<TX, double, KM, 64, BN, 16, 2, TN>, kThreads, 0) != cudaSuccess ||
+            &o, gemm_simt_kernel<TX, double, KM, 64, BN, 16, TM, TN>, kThreads, 0) != cudaSuccess ||
         o < 1) {
       cudaGetLastError();
       o = 1;
@@ -738,6 +755,18 @@ int exact_cols_occ() {
 
 template <typename TX, bool KM>
 int exact_cols_occ_for(int R) {
+  if (exact4(R)) {
+    switch (R) {
+      case 68: return exact_cols_occ<TX, KM, 68, 17, 1>();
+      case 76: return exact_cols_occ<TX, KM, 76, 19, 1>();
+      case 84: return exact_cols_occ<TX, KM, 84, 21, 1>();
+      case 92: return exact_cols_occ<TX, KM, 92, 23, 1>();
+      case 100: return exact_cols_occ<TX, KM, 100, 25, 1>();
+      case 108: return exact_cols_occ<TX, KM, 108, 27, 1>();
+      case 116: return exact_cols_occ<TX, KM, 116, 29, 1>();
+      default: return exact_cols_occ<TX, KM, 124, 31, 1>();
+    }
+  }
   switch ((R + 7) / 8) {
     case 5: return exact_cols_occ<TX, KM, 40, 5>();
     case 6: return exact_cols_occ<TX, KM, 48, 6>();
@@ -754,9 +783,54 @@ int exact_cols_occ_for(int R) {
   }
 }
 
+int sm_count() {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      return 0;
+    }
+    nsm = n;
+  }
+  return nsm;
+}
+
+// A K-major launch of one batch whose 64-row tiles fill w whole waves of
+// resident CTAs and part of one more (R = 100 at 400^3: 2,500 tiles, 8.2
+// waves of 304) runs as two launches: the whole waves, then the remaining
+// rows with K split so that they fill one wave, their partials summed by
+// reduce_splits (part_cap: values the partials buffer holds; 0 keeps one
+// launch).  The last wave then takes a fraction of a CTA's time instead of
+// a whole one with most SMs idle.
+template <typename TX, typename T, bool KM>
+void gemm_exact_cols(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K,
+                     int64_t M, int R, int splits, Launch L, int64_t part_cap) {
+  if (KM && batch == 1 && splits == 1 && part_cap > 0) {
+    const int64_t wave = (int64_t)exact_cols_occ_for<TX, true>(R) * sm_count();
+    const int64_t tiles = cdiv(M, 64);
+    const int64_t full = wave > 0 ? tiles / wave * wave : 0;
+    if (full > 0 && full < tiles) {
+      const int64_t rows = M - full * 64;
+      int64_t sp = wave / (tiles - full);
+      sp = std::min<int64_t>(sp, K / 16);
+      sp = std::min<int64_t>(sp, part_cap / std::max<int64_t>(1, rows * R));
+      while (sp > 1 && cdiv(K, cdiv(cdiv(K, sp), 16) * 16) != sp) sp--;
+      if (sp >= 2) {
+        gemm_exact_launch<TX, T, KM>(X, B, out, partials, 1, K, full * 64, R, 1, L);
+        gemm_exact_launch<TX, T, KM>(X + full * 64 * K, B, out + full * 64 * R, partials, 1, K, rows, R,
+                                     (int)sp, L);
+        return;
+      }
+    }
+  }
+  gemm_exact_launch<TX, T, KM>(X, B, out, partials, batch, K, M, R, splits, L);
+}
+
 template <typename TX, typename T>
 void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K, int64_t M,
-               int R, bool kmajor, int splits, Launch L) {
+               int R, bool kmajor, int splits, Launch L, int64_t part_cap) {
   if (splits < 1) splits = 1;
   if constexpr (sizeof(T) == 4 && sizeof(TX) == 4) {
     if (f32_applies(X, K, M, R, kmajor)) {
@@ -767,8 +841,8 @@ void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int6
   }
   if constexpr (sizeof(T) == 8) {
     if (R > 32 && gemm_simt_bm(M, R, kmajor) == 64) {
-      if (kmajor) gemm_exact_cols<TX, T, true>(X, B, out, partials, batch, K, M, R, splits, L);
-      else gemm_exact_cols<TX, T, false>(X, B, out, partials, batch, K, M, R, splits, L);
+      if (kmajor) gemm_exact_cols<TX, T, true>(X, B, out, partials, batch, K, M, R, splits, L, part_cap);
+      else gemm_exact_cols<TX, T, false>(X, B, out, partials, batch, K, M, R, splits, L, part_cap);
       return;
     }
   }
@@ -927,9 +1001,9 @@ void sumsq(const TX* x, int64_t n, double* partials, double* out, Launch L) {
 template void reduce_splits<float>(const float*, float*, int64_t, int, Launch);
 template void reduce_splits<double>(const double*, double*, int64_t, int, Launch);
 template void gemm_simt<double, double>(const double*, const double*, double*, double*, int64_t,
-                                        int64_t, int64_t, int, bool, int, Launch);
+                                        int64_t, int64_t, int, bool, int, Launch, int64_t);
 template void gemm_simt<float, float>(const float*, const float*, float*, float*, int64_t, int64_t,
-                                      int64_t, int, bool, int, Launch);
+                                      int64_t, int, bool, int, Launch, int64_t);
 template void ttv<double>(const double*, const double*, double*, int64_t, int, int64_t, int, Launch);
 template void ttv<float>(const float*, const float*, float*, int64_t, int, int64_t, int, Launch);
 template void pp_correct<double>(const double*, const PPTerm<double>*, int, double*, int, int, Launch);

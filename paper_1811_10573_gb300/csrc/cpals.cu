@@ -302,7 +302,8 @@ cpals_status contract_first(cpals_ctx* c, int k0, int nk, void* const* facs, T* 
     B = P<const T>(c->krp);
   }
   ev_begin(c, idx);
-  gemm_simt<T, T>(P<const T>(c->X), B, out, P<T>(c->gpart), batch, K, M, R, kmajor, splits, c->L());
+  gemm_simt<T, T>(P<const T>(c->X), B, out, P<T>(c->gpart), batch, K, M, R, kmajor, splits, c->L(),
+                  (int64_t)(c->gpart_bytes / sizeof(T)));
   ev_end(c, idx, bytes, flops);
   return CPALS_OK;
 }

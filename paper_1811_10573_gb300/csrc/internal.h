@@ -22,10 +22,12 @@ constexpr int kMaxRank = 128;
 //   kmajor:  out[m][r]    = sum_k X[m*K + k]          * B[k][r]   (batch must be 1)
 //   !kmajor: out[b][m][r] = sum_k X[(b*K + k)*M + m]  * B[k][r]
 // splits > 1 splits K; partials (splits*batch*M*R values) then holds the
-// partial sums and a deterministic reduction writes out.
+// partial sums and a deterministic reduction writes out.  part_cap > 0 (the
+// values partials holds) lets a float64 K-major launch of one batch with
+// splits == 1 split K for the rows of its last, partial wave.
 template <typename TX, typename T>
 void gemm_simt(const TX* X, const T* B, T* out, T* partials, int64_t batch, int64_t K, int64_t M,
-               int R, bool kmajor, int splits, Launch L);
+               int R, bool kmajor, int splits, Launch L, int64_t part_cap = 0);
 
 // K splits for a float64 gemm_simt: with R > 32 (64-row exact-column tiles)
 // the grid is about four waves of resident CTAs when the output alone does
