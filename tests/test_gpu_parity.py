@@ -81,19 +81,21 @@ def test_mttkrp_fp32_wide_rank(dims, R):
             assert rel(g.mttkrp(n), ref) < TOL["fp32"], n
 
 
-# float64 contractions with R = 4 (mod 8) above 64 (exact R-column tiles) and
-# a K-major launch whose 64-row tiles fill whole waves and part of another
-# (40,000 and 32,300 rows): the last wave's rows run with K split in two
-TAIL = [([200, 200, 40], 100), ([190, 170, 48], 92), ([64, 48, 40], 68)]
+# float64 contractions with R = 4 (mod 8) above 64 (exact R-column tiles), and
+# K-major launches whose 64-row tiles fill whole waves and part of another
+# (40,000 and 32,300 rows): the last wave's rows run as a second launch with
+# K split in two; the same 40,000-row shape on the float32 kernel (one launch)
+TAIL = [([200, 200, 40], 100, "fp64"), ([190, 170, 48], 92, "fp64"), ([64, 48, 40], 68, "fp64"),
+        ([200, 200, 40], 100, "fp32")]
 
 
-@pytest.mark.parametrize("dims,R", TAIL)
-def test_mttkrp_fp64_exact_tiles_and_tail_split(dims, R):
-    p = synth.make_problem("normal", dims, R, seed=9, storage="f64")
-    with _ctx(p, "fp64") as g:
+@pytest.mark.parametrize("dims,R,prec", TAIL)
+def test_mttkrp_exact_tiles_and_tail_split(dims, R, prec):
+    p = synth.make_problem("normal", dims, R, seed=9, storage="f64" if prec == "fp64" else "f32")
+    with _ctx(p, prec) as g:
         for n in range(len(dims)):
             ref = O.mttkrp(X64(p), p.A0, n)
-            assert rel(g.mttkrp(n), ref) < TOL["fp64"], n
+            assert rel(g.mttkrp(n), ref) < TOL[prec], n
 
 
 # the largest order (8), order 7, and modes of size 1 (degenerate unfoldings)
